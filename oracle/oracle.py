@@ -1,0 +1,276 @@
+"""ctypes front end of the C oracle in ``xyl_oracle.c`` (test infrastructure only).
+
+Every routine here only marshals numpy arrays into the C functions; the
+arithmetic lives in the C file, which cites the passages it follows.  Parity
+status of each function is recorded in its docstring; all of them are pinned by
+``tests/test_oracle_*.py`` against closed forms, exact special cases, brute force
+or published known-answer values.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "xyl_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OP_MET, OP_OR, OP_PT, OP_MEASURE = 1, 2, 4, 8
+ACC_FIELDS = ("n", "e", "e2", "absm", "mx", "my", "m2", "m4", "chik")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = C.CDLL(_LIB_PATH)
+        P = C.c_void_p
+        i32p, u32p, u64p, f64p, i64p = (C.POINTER(C.c_int32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint64),
+                                        C.POINTER(C.c_double), C.POINTER(C.c_int64))
+        lib.orc_philox.argtypes = [u32p, u32p, u32p]
+        lib.orc_philox.restype = None
+        lib.orc_disp_table.argtypes = [C.c_int, C.c_double, i32p, i32p, u64p, i32p]
+        lib.orc_disp_sample.argtypes = [C.c_int, C.c_double, C.c_uint64, C.c_uint32, C.c_int64, i32p]
+        lib.orc_levy_graph.argtypes = [C.c_int, C.c_int, C.c_double, C.c_uint64, C.c_uint32, C.c_int,
+                                       i32p, i32p, i32p, u64p]
+        lib.orc_pick_partner_counts.argtypes = [C.c_int, C.c_int, C.c_double, C.c_uint64, i32p, i32p, i32p,
+                                                C.c_int, C.c_int, C.c_int64, i64p]
+        lib.orc_slo_color.argtypes = [C.c_int, C.c_int64, i32p, i32p, i32p]
+        lib.orc_csr.argtypes = [C.c_int, C.c_int64, i32p, i32p, i32p, C.c_int, i32p, i32p, i32p, i32p]
+        lib.orc_sim_new.argtypes = [C.c_int, C.c_int64, i32p, i32p, i32p, i32p, C.c_int, C.c_int, f64p, f64p,
+                                    C.c_uint64, C.c_uint32, C.c_int]
+        lib.orc_sim_new.restype = P
+        lib.orc_sim_free.argtypes = [P]
+        lib.orc_sim_init.argtypes = [P, C.c_int]
+        lib.orc_sim_sweeps.argtypes = [P, C.c_int, C.c_uint, C.c_int]
+        lib.orc_sim_get_angles.argtypes = [P, f64p]
+        lib.orc_sim_set_angles.argtypes = [P, f64p]
+        lib.orc_sim_get_energies.argtypes = [P, f64p]
+        lib.orc_sim_get_labels.argtypes = [P, i32p]
+        lib.orc_sim_get_acc.argtypes = [P, f64p, u64p, u64p, u64p, u64p]
+        lib.orc_sim_reset_acc.argtypes = [P]
+        lib.orc_sim_set_delta.argtypes = [P, f64p]
+        lib.orc_sim_set_tie_eps.argtypes = [P, C.c_double]
+        lib.orc_sim_get_ties.argtypes = [P, i64p, i64p, f64p]
+        lib.orc_sim_sweep_index.argtypes = [P]
+        lib.orc_sim_sweep_index.restype = C.c_uint64
+        _lib = lib
+        return lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def philox(ctr, key) -> np.ndarray:
+    """Philox4x32-10 block for counter ``ctr`` (4 words) and key (2 words).
+
+    Pinned by the Random123 known-answer vectors (tests/golden/philox_kat.txt)."""
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib.orc_philox(_ptr(c, C.c_uint32), _ptr(k, C.c_uint32), _ptr(out, C.c_uint32))
+    return out
+
+
+def disp_table(L: int, rho: float):
+    """Displacement table of the link law (Eq. Levyi): (dx, dy, B, n_near).
+
+    Pinned by the proposal-law chi^2 test against an independent count of
+    minimum-image distances, and by exact integer-weight invariants."""
+    lib = _load()
+    n = L * L - 1
+    dx = np.zeros(n, np.int32); dy = np.zeros(n, np.int32); B = np.zeros(n, np.uint64)
+    nn = np.zeros(1, np.int32)
+    rc = lib.orc_disp_table(L, rho, _ptr(dx, C.c_int32), _ptr(dy, C.c_int32), _ptr(B, C.c_uint64),
+                            _ptr(nn, C.c_int32))
+    if rc:
+        raise ValueError("bad lattice size")
+    return dx, dy, B, int(nn[0])
+
+
+def disp_sample(L: int, rho: float, seed: int, sample: int, n_draws: int) -> np.ndarray:
+    """Table entries proposed by ``n_draws`` consecutive graph-stream draws."""
+    lib = _load()
+    out = np.zeros(n_draws, np.int32)
+    rc = lib.orc_disp_sample(L, rho, seed, sample, n_draws, _ptr(out, C.c_int32))
+    if rc:
+        raise ValueError("bad lattice size")
+    return out
+
+
+def levy_graph(L: int, z: int, rho: float, seed: int, sample: int = 0, max_restarts: int = 100):
+    """Fixed-degree Levy graph: (ei, ej, restarts, draws), links in creation order.
+
+    Pinned by exact degree / symmetry / no-self-loop / no-multi-edge checks, the
+    first-link law (brute force over many seeds) and the accepted-link law."""
+    lib = _load()
+    n = L * L
+    ne = n * z // 2
+    ei = np.zeros(ne, np.int32); ej = np.zeros(ne, np.int32)
+    rs = np.zeros(1, np.int32); dr = np.zeros(1, np.uint64)
+    rc = lib.orc_levy_graph(L, z, rho, seed, sample, max_restarts, _ptr(ei, C.c_int32), _ptr(ej, C.c_int32),
+                            _ptr(rs, C.c_int32), _ptr(dr, C.c_uint64))
+    if rc == -1:
+        raise ValueError("bad graph arguments")
+    if rc == -3:
+        raise RuntimeError("graph construction hit a dead end on every restart")
+    return ei, ej, int(rs[0]), int(dr[0])
+
+
+def pick_partner_counts(L, z, rho, seed, deg, adj, unsat, i, n_trials):
+    """Outcome counts of the partner draw of site ``i`` from a given pairing
+    state (index n = dead end).  Pinned against the exact conditional law."""
+    lib = _load()
+    n = L * L
+    deg = np.ascontiguousarray(deg, np.int32); adj = np.ascontiguousarray(adj, np.int32).reshape(-1)
+    unsat = np.ascontiguousarray(unsat, np.int32)
+    counts = np.zeros(n + 1, np.int64)
+    rc = lib.orc_pick_partner_counts(L, z, rho, seed, _ptr(deg, C.c_int32), _ptr(adj, C.c_int32),
+                                     _ptr(unsat, C.c_int32), len(unsat), i, n_trials, _ptr(counts, C.c_int64))
+    if rc:
+        raise ValueError("bad lattice size")
+    return counts
+
+
+def slo_color(n: int, ei, ej):
+    """Smallest-last colouring: (colour per site, number of colours).
+
+    Pinned by properness, the degeneracy bound and hand-checked small graphs."""
+    lib = _load()
+    ei = np.ascontiguousarray(ei, np.int32); ej = np.ascontiguousarray(ej, np.int32)
+    col = np.zeros(n, np.int32)
+    q = lib.orc_slo_color(n, len(ei), _ptr(ei, C.c_int32), _ptr(ej, C.c_int32), _ptr(col, C.c_int32))
+    return col, int(q)
+
+
+def csr(n: int, ei, ej, color, n_colors: int):
+    """Colour-sorted CSR: (perm, row_ptr, col, color_ptr)."""
+    lib = _load()
+    ei = np.ascontiguousarray(ei, np.int32); ej = np.ascontiguousarray(ej, np.int32)
+    color = np.ascontiguousarray(color, np.int32)
+    perm = np.zeros(n, np.int32); row_ptr = np.zeros(n + 1, np.int32)
+    col = np.zeros(2 * len(ei), np.int32); cptr = np.zeros(n_colors + 1, np.int32)
+    lib.orc_csr(n, len(ei), _ptr(ei, C.c_int32), _ptr(ej, C.c_int32), _ptr(color, C.c_int32), n_colors,
+                _ptr(perm, C.c_int32), _ptr(row_ptr, C.c_int32), _ptr(col, C.c_int32), _ptr(cptr, C.c_int32))
+    return perm, row_ptr, col, cptr
+
+
+def lattice_xy(L: int) -> np.ndarray:
+    """(x, y) of site id = x + L*y."""
+    ids = np.arange(L * L, dtype=np.int32)
+    return np.stack([ids % L, ids // L], axis=1).astype(np.int32).reshape(-1)
+
+
+class Sim:
+    """Sequential sampler (Metropolis + overrelaxation + PT + measurement).
+
+    ``beta``/``delta`` are per temperature slot; replica r starts at slot r.
+    ``u24=True`` selects the 24-bit uniforms used by the single-precision kernel.
+    Pinned by the chain, ring and small-graph exact results, beta = 0 exact
+    moments, the low-temperature limit, the high-temperature series and exact
+    energy conservation of overrelaxation."""
+
+    def __init__(self, n, ei, ej, color, beta, delta, seed, sample=0, xy=None, L=None, u24=False):
+        self._lib = _load()
+        self.n = int(n)
+        self.R = len(beta)
+        self._keep = [np.ascontiguousarray(ei, np.int32), np.ascontiguousarray(ej, np.int32),
+                      np.ascontiguousarray(color, np.int32)]
+        xy_arr = None if xy is None else np.ascontiguousarray(xy, np.int32)
+        b = np.ascontiguousarray(beta, np.float64); d = np.ascontiguousarray(delta, np.float64)
+        self._h = self._lib.orc_sim_new(
+            self.n, len(self._keep[0]), _ptr(self._keep[0], C.c_int32), _ptr(self._keep[1], C.c_int32),
+            _ptr(self._keep[2], C.c_int32), None if xy_arr is None else _ptr(xy_arr, C.c_int32),
+            int(L or 0), self.R, _ptr(b, C.c_double), _ptr(d, C.c_double), seed, sample, 1 if u24 else 0)
+        if not self._h:
+            raise MemoryError("oracle allocation failed")
+
+    def close(self):
+        if self._h:
+            self._lib.orc_sim_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, aligned=False):
+        self._lib.orc_sim_init(self._h, 1 if aligned else 0)
+
+    def sweeps(self, n, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1):
+        self._lib.orc_sim_sweeps(self._h, int(n), int(ops), int(measure_every))
+
+    def angles(self) -> np.ndarray:
+        out = np.zeros((self.R, self.n), np.float64)
+        self._lib.orc_sim_get_angles(self._h, _ptr(out, C.c_double))
+        return out
+
+    def set_angles(self, a):
+        a = np.ascontiguousarray(a, np.float64).reshape(self.R, self.n)
+        self._lib.orc_sim_set_angles(self._h, _ptr(a, C.c_double))
+
+    def energies(self) -> np.ndarray:
+        out = np.zeros(self.R, np.float64)
+        self._lib.orc_sim_get_energies(self._h, _ptr(out, C.c_double))
+        return out
+
+    def labels(self) -> np.ndarray:
+        out = np.zeros(self.R, np.int32)
+        self._lib.orc_sim_get_labels(self._h, _ptr(out, C.c_int32))
+        return out
+
+    def set_delta(self, delta):
+        d = np.ascontiguousarray(delta, np.float64)
+        self._lib.orc_sim_set_delta(self._h, _ptr(d, C.c_double))
+
+    def set_tie_eps(self, eps):
+        self._lib.orc_sim_set_tie_eps(self._h, float(eps))
+
+    def ties(self):
+        ft = np.zeros(self.R, np.int64); fp = np.zeros(1, np.int64); mm = np.zeros(1, np.float64)
+        self._lib.orc_sim_get_ties(self._h, _ptr(ft, C.c_int64), _ptr(fp, C.c_int64), _ptr(mm, C.c_double))
+        return ft, int(fp[0]), float(mm[0])
+
+    def accumulators(self):
+        acc = np.zeros((self.R, len(ACC_FIELDS)), np.float64)
+        ma = np.zeros(self.R, np.uint64); mt = np.zeros(self.R, np.uint64)
+        pa = np.zeros(self.R, np.uint64); pt = np.zeros(self.R, np.uint64)
+        self._lib.orc_sim_get_acc(self._h, _ptr(acc, C.c_double), _ptr(ma, C.c_uint64), _ptr(mt, C.c_uint64),
+                                  _ptr(pa, C.c_uint64), _ptr(pt, C.c_uint64))
+        return {"acc": acc, "met_acc": ma, "met_try": mt, "pt_acc": pa, "pt_try": pt}
+
+    def reset_acc(self):
+        self._lib.orc_sim_reset_acc(self._h)
+
+    @property
+    def sweep_index(self) -> int:
+        return int(self._lib.orc_sim_sweep_index(self._h))
+
+
+def graph_sim(ei, ej, n, beta, delta, seed, sample=0, xy=None, L=None, u24=False):
+    """Sampler on an explicit edge list, coloured by ``slo_color``."""
+    color, _ = slo_color(n, ei, ej)
+    return Sim(n, ei, ej, color, beta, delta, seed, sample=sample, xy=xy, L=L, u24=u24)

@@ -1,0 +1,936 @@
+/*
+ * xyl_oracle.c -- plain, sequential, FP64 reference sampler for the XY model on
+ * dilute Levy graphs (Ibanez Berganza & Leuzzi, "Critical behavior of the XY
+ * model in complex topologies").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file; only the test-suite, the package smoke check and the
+ * benchmark's CPU-baseline leg do.  It shares no code, header or table with the
+ * CUDA path: every routine below is written out here on its own.
+ *
+ * What it computes, in the order the method runs:
+ *   philox()            Philox4x32-10 counter-based generator (Salmon, Moraes,
+ *                       Dror & Shaw, SC'11), the random source of every step.
+ *   disp_table_*()      Link-length law of the dilute Levy graph, Eq. (Levyi):
+ *                       P(J_ij = 1) proportional to |r_i - r_j|^-rho, minimum
+ *                       image distances on the periodic L x L lattice (Sec. II).
+ *   orc_levy_graph()    Fixed-degree (every site exactly z links) sequential
+ *                       pairing of unsaturated sites, each new link drawn with
+ *                       the law above among the eligible partners.
+ *   orc_slo_color()     Smallest-last-ordering colouring (App. B, "Graph
+ *                       coloring").
+ *   orc_csr()           Colour-sorted CSR (App. B, "Memory management": sites of
+ *                       one colour stored consecutively).
+ *   orc_sim_*()         Monte Carlo sweeps of H = -sum_{i<j} J_ij S_i.S_j,
+ *                       Eq. (HXY): single-spin Metropolis over the colour classes
+ *                       in sequence (App. B), overrelaxation (App. B, "Improved
+ *                       equilibrium dynamics"), parallel-tempering swaps every
+ *                       sweep (same passage), and the observables of Sec. III
+ *                       (energy, magnetisation m, |m|, m^2, m^4, and the
+ *                       Fourier sum at k_min = 2 pi / L used by xi_2).
+ *
+ * The oracle keeps each spin as an angle theta (the paper's own storage,
+ * App. B) and evaluates the energy as -sum cos(theta_i - theta_j); the CUDA path
+ * keeps unit vectors.  The two agree up to rounding.
+ *
+ * Readings of points the paper leaves open are listed with each routine.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon et al., SC'11): 10 rounds of the 4x32 Philox S-box,
+ * multipliers 0xD2511F53 / 0xCD9E8D57, key schedule Weyl increments
+ * 0x9E3779B9 / 0xBB67AE85 applied between rounds.                            */
+/* ------------------------------------------------------------------------- */
+void orc_philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Random-stream purposes, stored in the top byte of counter word 2. */
+enum { PURPOSE_GRAPH = 0, PURPOSE_INIT = 1, PURPOSE_MET = 2, PURPOSE_PT = 3 };
+
+static void draw_block(uint32_t w0, uint32_t w1, uint32_t purpose, uint32_t sub,
+                       uint32_t sample, const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t ctr[4] = { w0, w1, (purpose << 24) | (sub & 0xFFFFFFu), sample };
+    orc_philox(ctr, key, out);
+}
+
+/* 53-bit uniform in [0,1) from two words (hi word first). */
+static double u53(uint32_t hi, uint32_t lo)
+{
+    uint64_t v = (((uint64_t)hi << 32) | (uint64_t)lo) >> 11;
+    return (double)v * 0x1.0p-53;
+}
+
+/* 24-bit uniform in [0,1) from one word. */
+static double u24(uint32_t x)
+{
+    return (double)(x >> 8) * 0x1.0p-24;
+}
+
+static uint64_t mulhi64(uint64_t a, uint64_t b)
+{
+    return (uint64_t)(((unsigned __int128)a * (unsigned __int128)b) >> 64);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Link-length law, Eq. (Levyi).                                              */
+/*                                                                            */
+/* Reading: the normalisation runs over partner SITES, so a distance r that   */
+/* occurs g(r) times around a site carries total weight g(r) r^-rho; this is  */
+/* the only reading under which the per-pair law P(J_ij) ~ |r_i-r_j|^-rho     */
+/* holds.  Displacements (dx,dy) take dx,dy in {-L/2+1,...,L/2} (even L), so  */
+/* every other site appears exactly once and r_max = (L/2) sqrt(2) as in      */
+/* Sec. II.  Table order: the "near" displacements (dx^2+dy^2 <= 8) first,    */
+/* then the rest, each group in raster order (dy outer, dx inner, ascending). */
+/* Integer boundaries B_k = floor(2^64 * S_k / S), S_k the FP64 running sum   */
+/* of the weights before entry k, make every later decision an integer one.   */
+/* ------------------------------------------------------------------------- */
+#define NEAR_R2 8
+
+typedef struct {
+    int L, n;          /* lattice size, number of displacements (L*L - 1) */
+    int n_near;        /* entries [0, n_near) are the near group */
+    int *dx, *dy;      /* displacement of entry k */
+    uint64_t *B;       /* B[k] = lower boundary of entry k, B[0] = 0 */
+    int *index_of;     /* raster cell (dy+L/2-1)*L + (dx+L/2-1) -> entry, -1 at origin */
+} disp_table;
+
+static void disp_table_free(disp_table *t)
+{
+    free(t->dx); free(t->dy); free(t->B); free(t->index_of);
+}
+
+static int disp_table_build(disp_table *t, int L, double rho)
+{
+    memset(t, 0, sizeof(*t));
+    t->L = L;
+    t->n = L * L - 1;
+    t->dx = (int *)malloc(sizeof(int) * (size_t)t->n);
+    t->dy = (int *)malloc(sizeof(int) * (size_t)t->n);
+    t->B = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)t->n);
+    t->index_of = (int *)malloc(sizeof(int) * (size_t)L * (size_t)L);
+    if (!t->dx || !t->dy || !t->B || !t->index_of) { disp_table_free(t); return -1; }
+    int half = L / 2, k = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int dy = -half + 1; dy <= half; ++dy) {
+            for (int dx = -half + 1; dx <= half; ++dx) {
+                int r2 = dx * dx + dy * dy;
+                if (r2 == 0) continue;
+                int near = r2 <= NEAR_R2;
+                if ((pass == 0) != near) continue;
+                t->dx[k] = dx; t->dy[k] = dy;
+                t->index_of[(dy + half - 1) * L + (dx + half - 1)] = k;
+                ++k;
+            }
+        }
+        if (pass == 0) t->n_near = k;
+    }
+    t->index_of[(half - 1) * L + (half - 1)] = -1;
+    /* running FP64 sums of r^-rho in table order */
+    double *S = (double *)malloc(sizeof(double) * (size_t)(t->n + 1));
+    if (!S) { disp_table_free(t); return -1; }
+    S[0] = 0.0;
+    for (int m = 0; m < t->n; ++m) {
+        double r2 = (double)(t->dx[m] * t->dx[m] + t->dy[m] * t->dy[m]);
+        S[m + 1] = S[m] + pow(r2, -0.5 * rho);
+    }
+    const double two64 = 18446744073709551616.0;
+    t->B[0] = 0;
+    for (int m = 1; m < t->n; ++m) {
+        double q = (S[m] / S[t->n]) * two64;
+        t->B[m] = (q >= two64) ? UINT64_MAX : (uint64_t)q;
+    }
+    free(S);
+    return 0;
+}
+
+/* integer weight of entry k: B[k+1] - B[k], with B[n] = 2^64 */
+static uint64_t disp_weight(const disp_table *t, int k)
+{
+    uint64_t hi = (k + 1 < t->n) ? t->B[k + 1] : 0; /* 2^64 wraps to 0 */
+    return hi - t->B[k];
+}
+
+/* entry whose interval [B_k, B_{k+1}) holds u, searched among [lo, n) */
+static int disp_locate(const disp_table *t, uint64_t u, int lo)
+{
+    /* largest k in [lo, n) with B[k] <= u (B is non-decreasing, B[lo] <= u) */
+    int a = lo, b = t->n - 1;
+    while (a < b) {
+        int mid = a + (b - a + 1) / 2;
+        if (t->B[mid] <= u) a = mid; else b = mid - 1;
+    }
+    return a;
+}
+
+/* table entry of the displacement from site i to site j */
+static int disp_between(const disp_table *t, int i, int j)
+{
+    int L = t->L, half = L / 2;
+    int dx = (j % L) - (i % L), dy = (j / L) - (i / L);
+    if (dx > half) dx -= L;
+    if (dx <= -half) dx += L;
+    if (dy > half) dy -= L;
+    if (dy <= -half) dy += L;
+    return t->index_of[(dy + half - 1) * L + (dx + half - 1)];
+}
+
+/* Exported for the link-law tests: the table in table order. */
+int orc_disp_table(int L, double rho, int32_t *dx, int32_t *dy, uint64_t *B, int32_t *n_near)
+{
+    if (L < 4 || (L & 1)) return -1;
+    disp_table t;
+    if (disp_table_build(&t, L, rho)) return -1;
+    for (int k = 0; k < t.n; ++k) { dx[k] = t.dx[k]; dy[k] = t.dy[k]; B[k] = t.B[k]; }
+    *n_near = t.n_near;
+    disp_table_free(&t);
+    return 0;
+}
+
+/* Exported for the proposal-law test: n_draws table samples from one stream. */
+int orc_disp_sample(int L, double rho, uint64_t seed, uint32_t sample, int64_t n_draws, int32_t *entry)
+{
+    if (L < 4 || (L & 1)) return -1;
+    disp_table t;
+    if (disp_table_build(&t, L, rho)) return -1;
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    for (int64_t d = 0; d < n_draws; d += 2) {
+        uint32_t x[4];
+        draw_block((uint32_t)(d >> 1), (uint32_t)((uint64_t)d >> 33), PURPOSE_GRAPH, 0, sample, key, x);
+        entry[d] = disp_locate(&t, ((uint64_t)x[1] << 32) | x[0], 0);
+        if (d + 1 < n_draws) entry[d + 1] = disp_locate(&t, ((uint64_t)x[3] << 32) | x[2], 0);
+    }
+    disp_table_free(&t);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Fixed-degree Levy graph by sequential pairing of unsaturated sites.        */
+/*                                                                            */
+/* Reading (the paper gives no construction procedure): while some site has  */
+/* fewer than z links, pick a site i uniformly among the unsaturated ones,    */
+/* then pick its partner j among the ELIGIBLE sites (j != i, fewer than z     */
+/* links, not yet linked to i) with probability proportional to the integer   */
+/* weight of the displacement i -> j; add the link.  If i has no eligible     */
+/* partner the attempt is a dead end and the whole graph restarts with the    */
+/* restart count in the random counter.  The draw protocol (identical in any  */
+/* implementation that must reproduce the same graph):                        */
+/*   * one stream of 64-bit draws U_0, U_1, ...: block b of Philox with       */
+/*     counter (b_lo, b_hi, GRAPH<<24 | restart, sample) gives                */
+/*     U_2b = w1:w0 and U_2b+1 = w3:w2;                                       */
+/*   * i = unsat[mulhi(U, M)], M = number of unsaturated sites;               */
+/*   * E = total weight of eligible near entries, F = total weight of far     */
+/*     entries; up to 64 times: t = floor(U (E+F) / 2^64); t < E selects the  */
+/*     near entry by cumulative weight (near order); otherwise the far entry  */
+/*     whose interval holds B[n_near] + t - E is proposed and kept if         */
+/*     eligible (a rejection costs one attempt);                              */
+/*   * after 64 rejections: enumerate the unsaturated sites in list order,    */
+/*     S = sum of eligible weights, t = mulhi(U, S), pick by cumulative       */
+/*     weight; S == 0 is the dead end.                                        */
+/* All three branches draw j with the same law: weight of i -> j over the     */
+/* eligible sites.  The unsaturated list starts as 0..N-1; a site that        */
+/* saturates is replaced by the last entry (i before j).                      */
+/* ------------------------------------------------------------------------- */
+#define PAIR_MAX_REJECT 64
+
+typedef struct {
+    uint32_t key[2];
+    uint32_t sample, restart;
+    uint64_t block;
+    int half;
+    uint32_t buf[4];
+    uint64_t n_draws;
+} u64_stream;
+
+static uint64_t stream_next(u64_stream *s)
+{
+    uint64_t v;
+    if (s->half == 0) {
+        draw_block((uint32_t)s->block, (uint32_t)(s->block >> 32), PURPOSE_GRAPH, s->restart,
+                   s->sample, s->key, s->buf);
+        v = ((uint64_t)s->buf[1] << 32) | s->buf[0];
+        s->half = 1;
+    } else {
+        v = ((uint64_t)s->buf[3] << 32) | s->buf[2];
+        s->half = 0;
+        s->block++;
+    }
+    s->n_draws++;
+    return v;
+}
+
+typedef struct {
+    int n, z;
+    int *deg;
+    int *adj;       /* n * z */
+    int *unsat;     /* unsaturated sites */
+    int *where;     /* position in unsat, -1 when saturated */
+    int m;          /* number of unsaturated sites */
+} pair_state;
+
+static int adjacent(const pair_state *p, int i, int j)
+{
+    for (int a = 0; a < p->deg[i]; ++a)
+        if (p->adj[(size_t)i * p->z + a] == j) return 1;
+    return 0;
+}
+
+static int eligible(const pair_state *p, int i, int j)
+{
+    return j != i && p->deg[j] < p->z && !adjacent(p, i, j);
+}
+
+static void saturate_check(pair_state *p, int v)
+{
+    if (p->deg[v] < p->z) return;
+    int pos = p->where[v], last = p->unsat[p->m - 1];
+    p->unsat[pos] = last;
+    p->where[last] = pos;
+    p->where[v] = -1;
+    p->m--;
+}
+
+static int site_shift(int L, int i, int dx, int dy)
+{
+    int x = ((i % L) + dx + L) % L, y = ((i / L) + dy + L) % L;
+    return x + L * y;
+}
+
+/* Partner of site i, or -1 at a dead end. */
+static int pick_partner(const disp_table *t, const pair_state *p, int i, u64_stream *s)
+{
+    int L = t->L;
+    unsigned __int128 E = 0;
+    for (int k = 0; k < t->n_near; ++k) {
+        int j = site_shift(L, i, t->dx[k], t->dy[k]);
+        if (eligible(p, i, j)) E += disp_weight(t, k);
+    }
+    unsigned __int128 F = (t->n_near < t->n) ? ((unsigned __int128)1 << 64) - t->B[t->n_near] : 0;
+    if (E + F > 0) {
+        for (int attempt = 0; attempt < PAIR_MAX_REJECT; ++attempt) {
+            uint64_t u = stream_next(s);
+            unsigned __int128 tt = ((unsigned __int128)u * (E + F)) >> 64;
+            if (tt < E) {
+                unsigned __int128 cum = 0;
+                for (int k = 0; k < t->n_near; ++k) {
+                    int j = site_shift(L, i, t->dx[k], t->dy[k]);
+                    if (!eligible(p, i, j)) continue;
+                    cum += disp_weight(t, k);
+                    if (cum > tt) return j;
+                }
+                return -2; /* unreachable: cumulative weight covers tt */
+            }
+            uint64_t pos = t->B[t->n_near] + (uint64_t)(tt - E);
+            int k = disp_locate(t, pos, t->n_near);
+            int j = site_shift(L, i, t->dx[k], t->dy[k]);
+            if (eligible(p, i, j)) return j;
+        }
+    }
+    /* exhaustive fallback over the unsaturated list */
+    unsigned __int128 S = 0;
+    for (int a = 0; a < p->m; ++a) {
+        int j = p->unsat[a];
+        if (eligible(p, i, j)) S += disp_weight(t, disp_between(t, i, j));
+    }
+    if (S == 0) return -1;
+    uint64_t u = stream_next(s);
+    unsigned __int128 tt = ((unsigned __int128)u * S) >> 64;
+    unsigned __int128 cum = 0;
+    for (int a = 0; a < p->m; ++a) {
+        int j = p->unsat[a];
+        if (!eligible(p, i, j)) continue;
+        cum += disp_weight(t, disp_between(t, i, j));
+        if (cum > tt) return j;
+    }
+    return -2;
+}
+
+/*
+ * Test hook for the partner law: from a given pairing state (deg, adjacency
+ * rows of width z, unsaturated list), draw the partner of site i n_trials times
+ * from one graph stream and count the outcomes (counts[n] = dead ends).
+ */
+int orc_pick_partner_counts(int L, int z, double rho, uint64_t seed, const int32_t *deg, const int32_t *adj,
+                            const int32_t *unsat, int m, int i, int64_t n_trials, int64_t *counts)
+{
+    if (L < 4 || (L & 1)) return -1;
+    disp_table t;
+    if (disp_table_build(&t, L, rho)) return -1;
+    int n = L * L;
+    pair_state p;
+    p.n = n; p.z = z; p.m = m;
+    p.deg = (int *)malloc(sizeof(int) * (size_t)n);
+    p.adj = (int *)malloc(sizeof(int) * (size_t)n * (size_t)z);
+    p.unsat = (int *)malloc(sizeof(int) * (size_t)n);
+    p.where = (int *)malloc(sizeof(int) * (size_t)n);
+    for (int v = 0; v < n; ++v) { p.deg[v] = deg[v]; p.where[v] = -1; }
+    for (int64_t a = 0; a < (int64_t)n * z; ++a) p.adj[a] = adj[a];
+    for (int a = 0; a < m; ++a) { p.unsat[a] = unsat[a]; p.where[unsat[a]] = a; }
+    u64_stream s;
+    memset(&s, 0, sizeof(s));
+    s.key[0] = (uint32_t)seed; s.key[1] = (uint32_t)(seed >> 32);
+    for (int64_t k = 0; k < n_trials; ++k) {
+        int j = pick_partner(&t, &p, i, &s);
+        counts[j < 0 ? n : j]++;
+    }
+    free(p.deg); free(p.adj); free(p.unsat); free(p.where);
+    disp_table_free(&t);
+    return 0;
+}
+
+/*
+ * Build one fixed-degree Levy graph.  Writes the N*z/2 links in the order they
+ * were made (ei[e], ej[e]; ei is the site that chose).  Returns 0, or -1 on bad
+ * arguments, -3 when max_restarts attempts all ended in a dead end.
+ */
+int orc_levy_graph(int L, int z, double rho, uint64_t seed, uint32_t sample, int max_restarts,
+                   int32_t *ei, int32_t *ej, int32_t *restarts_out, uint64_t *draws_out)
+{
+    if (L < 4 || (L & 1) || z < 1 || z > L * L - 1 || ((int64_t)L * L * z) % 2) return -1;
+    disp_table t;
+    if (disp_table_build(&t, L, rho)) return -1;
+    int n = L * L;
+    pair_state p;
+    p.n = n; p.z = z;
+    p.deg = (int *)malloc(sizeof(int) * (size_t)n);
+    p.adj = (int *)malloc(sizeof(int) * (size_t)n * (size_t)z);
+    p.unsat = (int *)malloc(sizeof(int) * (size_t)n);
+    p.where = (int *)malloc(sizeof(int) * (size_t)n);
+    int rc = -3;
+    uint64_t total_draws = 0;
+    for (int restart = 0; restart < max_restarts; ++restart) {
+        for (int v = 0; v < n; ++v) { p.deg[v] = 0; p.unsat[v] = v; p.where[v] = v; }
+        p.m = n;
+        u64_stream s;
+        memset(&s, 0, sizeof(s));
+        s.key[0] = (uint32_t)seed; s.key[1] = (uint32_t)(seed >> 32);
+        s.sample = sample; s.restart = (uint32_t)restart;
+        int64_t e = 0, dead = 0;
+        while (p.m > 0) {
+            int i = p.unsat[mulhi64(stream_next(&s), (uint64_t)p.m)];
+            int j = pick_partner(&t, &p, i, &s);
+            if (j < 0) { dead = 1; break; }
+            p.adj[(size_t)i * z + p.deg[i]++] = j;
+            p.adj[(size_t)j * z + p.deg[j]++] = i;
+            ei[e] = i; ej[e] = j; ++e;
+            saturate_check(&p, i);
+            saturate_check(&p, j);
+        }
+        total_draws += s.n_draws;
+        if (!dead) {
+            if (restarts_out) *restarts_out = restart;
+            rc = 0;
+            break;
+        }
+    }
+    if (draws_out) *draws_out = total_draws;
+    free(p.deg); free(p.adj); free(p.unsat); free(p.where);
+    disp_table_free(&t);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Smallest-last-ordering colouring (App. B "Graph coloring"; Matula & Beck). */
+/* Reading of the unpublished variant: repeatedly remove a vertex of minimum  */
+/* degree in the remaining graph (ties: smallest id), then colour vertices in */
+/* reverse removal order with the smallest colour no coloured neighbour has.  */
+/* A binary heap of (degree, id) with stale entries skipped does the removal. */
+/* ------------------------------------------------------------------------- */
+typedef struct { int deg, id; } heap_item;
+
+static int heap_less(heap_item a, heap_item b)
+{
+    return a.deg < b.deg || (a.deg == b.deg && a.id < b.id);
+}
+
+static void heap_push(heap_item *h, int64_t *size, heap_item v)
+{
+    int64_t k = (*size)++;
+    h[k] = v;
+    while (k > 0) {
+        int64_t up = (k - 1) / 2;
+        if (!heap_less(h[k], h[up])) break;
+        heap_item tmp = h[k]; h[k] = h[up]; h[up] = tmp;
+        k = up;
+    }
+}
+
+static heap_item heap_pop(heap_item *h, int64_t *size)
+{
+    heap_item top = h[0];
+    h[0] = h[--(*size)];
+    int64_t k = 0;
+    for (;;) {
+        int64_t l = 2 * k + 1, r = l + 1, best = k;
+        if (l < *size && heap_less(h[l], h[best])) best = l;
+        if (r < *size && heap_less(h[r], h[best])) best = r;
+        if (best == k) break;
+        heap_item tmp = h[k]; h[k] = h[best]; h[best] = tmp;
+        k = best;
+    }
+    return top;
+}
+
+/* adjacency (any order) from an edge list */
+static int build_adjacency(int n, int64_t ne, const int32_t *ei, const int32_t *ej, int **ptr_out, int **nbr_out)
+{
+    int *ptr = (int *)calloc((size_t)n + 1, sizeof(int));
+    int *nbr = (int *)malloc(sizeof(int) * (size_t)(2 * ne + 1));
+    int *fill = (int *)calloc((size_t)n, sizeof(int));
+    if (!ptr || !nbr || !fill) { free(ptr); free(nbr); free(fill); return -1; }
+    for (int64_t e = 0; e < ne; ++e) { ptr[ei[e] + 1]++; ptr[ej[e] + 1]++; }
+    for (int v = 0; v < n; ++v) ptr[v + 1] += ptr[v];
+    for (int64_t e = 0; e < ne; ++e) {
+        nbr[ptr[ei[e]] + fill[ei[e]]++] = ej[e];
+        nbr[ptr[ej[e]] + fill[ej[e]]++] = ei[e];
+    }
+    free(fill);
+    *ptr_out = ptr; *nbr_out = nbr;
+    return 0;
+}
+
+int orc_slo_color(int n, int64_t ne, const int32_t *ei, const int32_t *ej, int32_t *color)
+{
+    int *ptr, *nbr;
+    if (build_adjacency(n, ne, ei, ej, &ptr, &nbr)) return -1;
+    int *deg = (int *)malloc(sizeof(int) * (size_t)n);
+    char *gone = (char *)calloc((size_t)n, 1);
+    int *order = (int *)malloc(sizeof(int) * (size_t)n);
+    heap_item *h = (heap_item *)malloc(sizeof(heap_item) * (size_t)(n + 2 * ne + 1));
+    int64_t hs = 0;
+    for (int v = 0; v < n; ++v) {
+        deg[v] = ptr[v + 1] - ptr[v];
+        heap_item it = { deg[v], v };
+        heap_push(h, &hs, it);
+    }
+    int removed = 0;
+    while (removed < n) {
+        heap_item it = heap_pop(h, &hs);
+        if (gone[it.id] || it.deg != deg[it.id]) continue;
+        int v = it.id;
+        gone[v] = 1;
+        order[removed++] = v;
+        for (int a = ptr[v]; a < ptr[v + 1]; ++a) {
+            int u = nbr[a];
+            if (gone[u]) continue;
+            deg[u]--;
+            heap_item nu = { deg[u], u };
+            heap_push(h, &hs, nu);
+        }
+    }
+    for (int v = 0; v < n; ++v) color[v] = -1;
+    int n_colors = 0;
+    char *used = (char *)calloc((size_t)n + 2, 1);
+    for (int k = n - 1; k >= 0; --k) {
+        int v = order[k];
+        for (int a = ptr[v]; a < ptr[v + 1]; ++a)
+            if (color[nbr[a]] >= 0) used[color[nbr[a]]] = 1;
+        int c = 0;
+        while (used[c]) ++c;
+        color[v] = c;
+        if (c + 1 > n_colors) n_colors = c + 1;
+        for (int a = ptr[v]; a < ptr[v + 1]; ++a)
+            if (color[nbr[a]] >= 0) used[color[nbr[a]]] = 0;
+    }
+    free(used); free(h); free(order); free(gone); free(deg); free(ptr); free(nbr);
+    return n_colors;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Colour-sorted CSR (App. B "Memory management").  New id = rank of the site */
+/* by (colour, original id); perm[new] = original id; rows list neighbour new */
+/* ids ascending; color_ptr[c] = first new id of colour c.                    */
+/* ------------------------------------------------------------------------- */
+static int cmp_int(const void *a, const void *b)
+{
+    int x = *(const int *)a, y = *(const int *)b;
+    return (x > y) - (x < y);
+}
+
+int orc_csr(int n, int64_t ne, const int32_t *ei, const int32_t *ej, const int32_t *color, int n_colors,
+            int32_t *perm, int32_t *row_ptr, int32_t *col, int32_t *color_ptr)
+{
+    int *ptr, *nbr;
+    if (build_adjacency(n, ne, ei, ej, &ptr, &nbr)) return -1;
+    int *inv = (int *)malloc(sizeof(int) * (size_t)n);
+    int k = 0;
+    for (int c = 0; c < n_colors; ++c) {
+        color_ptr[c] = k;
+        for (int v = 0; v < n; ++v)
+            if (color[v] == c) { perm[k] = v; inv[v] = k; ++k; }
+    }
+    color_ptr[n_colors] = k;
+    row_ptr[0] = 0;
+    for (int a = 0; a < n; ++a) {
+        int v = perm[a], d = ptr[v + 1] - ptr[v];
+        for (int b = 0; b < d; ++b) col[row_ptr[a] + b] = inv[nbr[ptr[v] + b]];
+        qsort(col + row_ptr[a], (size_t)d, sizeof(int32_t), cmp_int);
+        row_ptr[a + 1] = row_ptr[a] + d;
+    }
+    free(inv); free(ptr); free(nbr);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Monte Carlo sampler.                                                       */
+/*                                                                            */
+/* Sweep t (App. B; readings where the paper is silent):                      */
+/*   1. Metropolis pass: colours c = 0..Q-1 in turn; within a colour the      */
+/*      sites are mutually unlinked, so the order inside it does not matter   */
+/*      (ascending id here).  Proposal theta' = theta + Delta (2u - 1), Delta */
+/*      per temperature slot; accept iff dE <= 0 or u' < exp(-beta dE), with  */
+/*      dE = -sum_j [cos(theta'-theta_j) - cos(theta-theta_j)], Eq. (HXY).    */
+/*   2. Overrelaxation pass, same colour order: the spin is reflected about   */
+/*      its local field h = sum_j S_j (theta' = 2 arg(h) - theta), left as it */
+/*      is when h = 0.  One Metropolis and one OR pass per sweep.             */
+/*   3. Parallel tempering after the sweep: pairs of slots (k, k+1) with      */
+/*      k = t mod 2, 4, ...; accept iff u < exp((beta_k - beta_{k+1})         */
+/*      (E_k - E_{k+1})) where E_k is the energy of the replica at slot k;    */
+/*      an accepted swap exchanges which replica sits at the two slots.       */
+/*   4. Measurement when (t+1) is a multiple of measure_every, per slot.      */
+/* Random draws: Metropolis of site i (original id), sweep t, replica r:      */
+/* Philox counter (i, t, MET<<24 | r, sample); 53-bit mode uses u53(w0,w1)    */
+/* for the step and u53(w2,w3) for the test, 24-bit mode u24(w0), u24(w1).    */
+/* Initial angle theta = 2 pi u - pi from counter (i, 0, INIT<<24 | r,        */
+/* sample).  PT pair k at sweep t: counter (k, t, PT<<24, sample), u53(w0,w1).*/
+/* ------------------------------------------------------------------------- */
+enum { OP_MET = 1u, OP_OR = 2u, OP_PT = 4u, OP_MEASURE = 8u };
+enum { ACC_N, ACC_E, ACC_E2, ACC_ABSM, ACC_MX, ACC_MY, ACC_M2, ACC_M4, ACC_CHIK, ACC_COUNT };
+
+typedef struct {
+    int n, R, L, Q;
+    int *ptr, *nbr;           /* adjacency by original id */
+    int *cls_ptr, *cls;       /* colour classes, ascending id inside a class */
+    int64_t n_bonds;
+    int *bi, *bj;             /* bond list */
+    double *cx, *sx, *cy, *sy;/* Fourier phases cos/sin(2 pi x/L), (2 pi y/L) */
+    double *beta, *delta;     /* per slot */
+    uint32_t key[2], sample;
+    int u24_mode;
+    double *theta;            /* [R][n] */
+    int *slot_of, *rep_at;
+    uint64_t t;
+    double *E;                /* per replica energy after the last sweep */
+    double *acc;              /* [R][ACC_COUNT] per slot */
+    uint64_t *met_acc, *met_try, *pt_acc, *pt_try;
+    double tie_eps;
+    int64_t *first_tie;       /* per replica: first sweep with a near-tie Metropolis test */
+    int64_t first_pt_tie;
+    double min_margin;        /* smallest Metropolis margin seen */
+} orc_sim;
+
+static double wrap_angle(double a)
+{
+    while (a >= ORC_PI) a -= 2.0 * ORC_PI;
+    while (a < -ORC_PI) a += 2.0 * ORC_PI;
+    return a;
+}
+
+void orc_sim_free(orc_sim *s)
+{
+    if (!s) return;
+    free(s->ptr); free(s->nbr); free(s->cls_ptr); free(s->cls); free(s->bi); free(s->bj);
+    free(s->cx); free(s->sx); free(s->cy); free(s->sy); free(s->beta); free(s->delta);
+    free(s->theta); free(s->slot_of); free(s->rep_at); free(s->E); free(s->acc);
+    free(s->met_acc); free(s->met_try); free(s->pt_acc); free(s->pt_try); free(s->first_tie);
+    free(s);
+}
+
+/* xy: 2n lattice coordinates (x, y) or NULL (then x = id, y = 0, period L = n). */
+orc_sim *orc_sim_new(int n, int64_t ne, const int32_t *ei, const int32_t *ej, const int32_t *color,
+                     const int32_t *xy, int L, int R, const double *beta, const double *delta,
+                     uint64_t seed, uint32_t sample, int u24_mode)
+{
+    orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
+    if (!s) return NULL;
+    s->n = n; s->R = R; s->u24_mode = u24_mode;
+    s->key[0] = (uint32_t)seed; s->key[1] = (uint32_t)(seed >> 32); s->sample = sample;
+    if (build_adjacency(n, ne, ei, ej, &s->ptr, &s->nbr)) { orc_sim_free(s); return NULL; }
+    int Q = 0;
+    for (int v = 0; v < n; ++v) if (color[v] + 1 > Q) Q = color[v] + 1;
+    s->Q = Q;
+    s->cls_ptr = (int *)calloc((size_t)Q + 1, sizeof(int));
+    s->cls = (int *)malloc(sizeof(int) * (size_t)n);
+    int k = 0;
+    for (int c = 0; c < Q; ++c) {
+        s->cls_ptr[c] = k;
+        for (int v = 0; v < n; ++v) if (color[v] == c) s->cls[k++] = v;
+    }
+    s->cls_ptr[Q] = k;
+    s->n_bonds = ne;
+    s->bi = (int *)malloc(sizeof(int) * (size_t)(ne + 1));
+    s->bj = (int *)malloc(sizeof(int) * (size_t)(ne + 1));
+    for (int64_t e = 0; e < ne; ++e) { s->bi[e] = ei[e]; s->bj[e] = ej[e]; }
+    s->L = xy ? L : n;
+    s->cx = (double *)malloc(sizeof(double) * (size_t)n);
+    s->sx = (double *)malloc(sizeof(double) * (size_t)n);
+    s->cy = (double *)malloc(sizeof(double) * (size_t)n);
+    s->sy = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int v = 0; v < n; ++v) {
+        int x = xy ? xy[2 * v] : v, y = xy ? xy[2 * v + 1] : 0;
+        double ax = 2.0 * ORC_PI * (double)x / (double)s->L;
+        double ay = 2.0 * ORC_PI * (double)y / (double)s->L;
+        s->cx[v] = cos(ax); s->sx[v] = sin(ax);
+        s->cy[v] = cos(ay); s->sy[v] = sin(ay);
+    }
+    s->beta = (double *)malloc(sizeof(double) * (size_t)R);
+    s->delta = (double *)malloc(sizeof(double) * (size_t)R);
+    for (int r = 0; r < R; ++r) { s->beta[r] = beta[r]; s->delta[r] = delta[r]; }
+    s->theta = (double *)calloc((size_t)R * (size_t)n, sizeof(double));
+    s->slot_of = (int *)malloc(sizeof(int) * (size_t)R);
+    s->rep_at = (int *)malloc(sizeof(int) * (size_t)R);
+    s->E = (double *)calloc((size_t)R, sizeof(double));
+    s->acc = (double *)calloc((size_t)R * ACC_COUNT, sizeof(double));
+    s->met_acc = (uint64_t *)calloc((size_t)R, sizeof(uint64_t));
+    s->met_try = (uint64_t *)calloc((size_t)R, sizeof(uint64_t));
+    s->pt_acc = (uint64_t *)calloc((size_t)R, sizeof(uint64_t));
+    s->pt_try = (uint64_t *)calloc((size_t)R, sizeof(uint64_t));
+    s->first_tie = (int64_t *)malloc(sizeof(int64_t) * (size_t)R);
+    s->tie_eps = 0.0;
+    for (int r = 0; r < R; ++r) { s->slot_of[r] = r; s->rep_at[r] = r; s->first_tie[r] = -1; }
+    s->first_pt_tie = -1;
+    s->min_margin = INFINITY;
+    return s;
+}
+
+void orc_sim_set_delta(orc_sim *s, const double *delta)
+{
+    for (int k = 0; k < s->R; ++k) s->delta[k] = delta[k];
+}
+
+void orc_sim_set_tie_eps(orc_sim *s, double eps) { s->tie_eps = eps; }
+
+static double energy_of(const orc_sim *s, int r)
+{
+    const double *th = s->theta + (size_t)r * s->n;
+    double E = 0.0;
+    for (int64_t e = 0; e < s->n_bonds; ++e) E -= cos(th[s->bi[e]] - th[s->bj[e]]);
+    return E;
+}
+
+/* aligned != 0: every angle 0; else the INIT draws.  Resets the sweep count,
+ * the slot labels and every accumulator. */
+void orc_sim_init(orc_sim *s, int aligned)
+{
+    for (int r = 0; r < s->R; ++r) {
+        for (int v = 0; v < s->n; ++v) {
+            double th = 0.0;
+            if (!aligned) {
+                uint32_t x[4];
+                draw_block((uint32_t)v, 0, PURPOSE_INIT, (uint32_t)r, s->sample, s->key, x);
+                double u = s->u24_mode ? u24(x[0]) : u53(x[0], x[1]);
+                th = 2.0 * ORC_PI * u - ORC_PI;
+            }
+            s->theta[(size_t)r * s->n + v] = th;
+        }
+        s->slot_of[r] = r; s->rep_at[r] = r; s->first_tie[r] = -1;
+    }
+    s->t = 0;
+    s->first_pt_tie = -1;
+    s->min_margin = INFINITY;
+    memset(s->acc, 0, sizeof(double) * (size_t)s->R * ACC_COUNT);
+    memset(s->met_acc, 0, sizeof(uint64_t) * (size_t)s->R);
+    memset(s->met_try, 0, sizeof(uint64_t) * (size_t)s->R);
+    memset(s->pt_acc, 0, sizeof(uint64_t) * (size_t)s->R);
+    memset(s->pt_try, 0, sizeof(uint64_t) * (size_t)s->R);
+    for (int r = 0; r < s->R; ++r) s->E[r] = energy_of(s, r);
+}
+
+static void note_tie(orc_sim *s, int r, double margin)
+{
+    if (margin < s->min_margin) s->min_margin = margin;
+    if (margin < s->tie_eps && s->first_tie[r] < 0) s->first_tie[r] = (int64_t)s->t;
+}
+
+static void metropolis_site(orc_sim *s, int r, int v)
+{
+    double *th = s->theta + (size_t)r * s->n;
+    int slot = s->slot_of[r];
+    uint32_t x[4];
+    draw_block((uint32_t)v, (uint32_t)s->t, PURPOSE_MET, (uint32_t)r, s->sample, s->key, x);
+    double ud = s->u24_mode ? u24(x[0]) : u53(x[0], x[1]);
+    double ua = s->u24_mode ? u24(x[1]) : u53(x[2], x[3]);
+    double old = th[v];
+    double prop = old + s->delta[slot] * (2.0 * ud - 1.0);
+    double dE = 0.0;
+    for (int a = s->ptr[v]; a < s->ptr[v + 1]; ++a) {
+        double tj = th[s->nbr[a]];
+        dE -= cos(prop - tj) - cos(old - tj);
+    }
+    int accept;
+    if (dE <= 0.0) {
+        accept = 1;
+        note_tie(s, r, -dE);
+    } else {
+        double a = exp(-s->beta[slot] * dE);
+        accept = ua < a;
+        double margin = fabs(ua - a);
+        if (dE < margin) margin = dE;
+        note_tie(s, r, margin);
+    }
+    s->met_try[slot]++;
+    if (accept) {
+        th[v] = wrap_angle(prop);
+        s->met_acc[slot]++;
+    }
+}
+
+static void overrelax_site(orc_sim *s, int r, int v)
+{
+    double *th = s->theta + (size_t)r * s->n;
+    double hx = 0.0, hy = 0.0;
+    for (int a = s->ptr[v]; a < s->ptr[v + 1]; ++a) {
+        hx += cos(th[s->nbr[a]]);
+        hy += sin(th[s->nbr[a]]);
+    }
+    if (hx == 0.0 && hy == 0.0) return;
+    th[v] = wrap_angle(2.0 * atan2(hy, hx) - th[v]);
+}
+
+static void parallel_tempering(orc_sim *s)
+{
+    for (int k = (int)(s->t & 1u); k + 1 < s->R; k += 2) {
+        int a = s->rep_at[k], b = s->rep_at[k + 1];
+        double x = (s->beta[k] - s->beta[k + 1]) * (s->E[a] - s->E[b]);
+        uint32_t w[4];
+        draw_block((uint32_t)k, (uint32_t)s->t, PURPOSE_PT, 0, s->sample, s->key, w);
+        double u = u53(w[0], w[1]);
+        double p = exp(x);
+        int accept = u < p;
+        if (x < 0.0 && fabs(u - p) < s->tie_eps && s->first_pt_tie < 0) s->first_pt_tie = (int64_t)s->t;
+        s->pt_try[k]++;
+        if (accept) {
+            s->rep_at[k] = b; s->rep_at[k + 1] = a;
+            s->slot_of[b] = k; s->slot_of[a] = k + 1;
+            s->pt_acc[k]++;
+        }
+    }
+}
+
+/* Observables of Sec. III for replica r: e, m, |F(k_min)|^2 (two directions). */
+static void observe(const orc_sim *s, int r, double out[ACC_COUNT])
+{
+    const double *th = s->theta + (size_t)r * s->n;
+    double mx = 0, my = 0;
+    double fxr_a = 0, fxi_a = 0, fyr_a = 0, fyi_a = 0; /* k along x: spin x / y comps */
+    double fxr_b = 0, fxi_b = 0, fyr_b = 0, fyi_b = 0; /* k along y */
+    for (int v = 0; v < s->n; ++v) {
+        double c = cos(th[v]), sn = sin(th[v]);
+        mx += c; my += sn;
+        fxr_a += c * s->cx[v]; fxi_a += c * s->sx[v];
+        fyr_a += sn * s->cx[v]; fyi_a += sn * s->sx[v];
+        fxr_b += c * s->cy[v]; fxi_b += c * s->sy[v];
+        fyr_b += sn * s->cy[v]; fyi_b += sn * s->sy[v];
+    }
+    double N = (double)s->n;
+    double e = s->E[r] / N;
+    mx /= N; my /= N;
+    double m2 = mx * mx + my * my;
+    double fa = fxr_a * fxr_a + fxi_a * fxi_a + fyr_a * fyr_a + fyi_a * fyi_a;
+    double fb = fxr_b * fxr_b + fxi_b * fxi_b + fyr_b * fyr_b + fyi_b * fyi_b;
+    out[ACC_N] = 1.0;
+    out[ACC_E] = e;
+    out[ACC_E2] = e * e;
+    out[ACC_ABSM] = sqrt(m2);
+    out[ACC_MX] = mx;
+    out[ACC_MY] = my;
+    out[ACC_M2] = m2;
+    out[ACC_M4] = m2 * m2;
+    out[ACC_CHIK] = (fa + fb) / (2.0 * N);
+}
+
+void orc_sim_sweeps(orc_sim *s, int n_sweeps, unsigned ops, int measure_every)
+{
+    for (int it = 0; it < n_sweeps; ++it) {
+        for (int r = 0; r < s->R; ++r) {
+            if (ops & OP_MET)
+                for (int c = 0; c < s->Q; ++c)
+                    for (int a = s->cls_ptr[c]; a < s->cls_ptr[c + 1]; ++a) metropolis_site(s, r, s->cls[a]);
+            if (ops & OP_OR)
+                for (int c = 0; c < s->Q; ++c)
+                    for (int a = s->cls_ptr[c]; a < s->cls_ptr[c + 1]; ++a) overrelax_site(s, r, s->cls[a]);
+            s->E[r] = energy_of(s, r);
+        }
+        if (ops & OP_PT) parallel_tempering(s);
+        if ((ops & OP_MEASURE) && measure_every > 0 && ((s->t + 1) % (uint64_t)measure_every) == 0) {
+            for (int k = 0; k < s->R; ++k) {
+                double o[ACC_COUNT];
+                observe(s, s->rep_at[k], o);
+                for (int q = 0; q < ACC_COUNT; ++q) s->acc[(size_t)k * ACC_COUNT + q] += o[q];
+            }
+        }
+        s->t++;
+    }
+}
+
+void orc_sim_get_angles(const orc_sim *s, double *out)
+{
+    memcpy(out, s->theta, sizeof(double) * (size_t)s->R * (size_t)s->n);
+}
+
+void orc_sim_set_angles(orc_sim *s, const double *in)
+{
+    memcpy(s->theta, in, sizeof(double) * (size_t)s->R * (size_t)s->n);
+    for (int r = 0; r < s->R; ++r) s->E[r] = energy_of(s, r);
+}
+
+void orc_sim_get_energies(const orc_sim *s, double *out)
+{
+    for (int r = 0; r < s->R; ++r) out[r] = s->E[r];
+}
+
+void orc_sim_get_labels(const orc_sim *s, int32_t *rep_at)
+{
+    for (int k = 0; k < s->R; ++k) rep_at[k] = s->rep_at[k];
+}
+
+void orc_sim_get_acc(const orc_sim *s, double *acc, uint64_t *met_acc, uint64_t *met_try,
+                     uint64_t *pt_acc, uint64_t *pt_try)
+{
+    memcpy(acc, s->acc, sizeof(double) * (size_t)s->R * ACC_COUNT);
+    memcpy(met_acc, s->met_acc, sizeof(uint64_t) * (size_t)s->R);
+    memcpy(met_try, s->met_try, sizeof(uint64_t) * (size_t)s->R);
+    memcpy(pt_acc, s->pt_acc, sizeof(uint64_t) * (size_t)s->R);
+    memcpy(pt_try, s->pt_try, sizeof(uint64_t) * (size_t)s->R);
+}
+
+void orc_sim_reset_acc(orc_sim *s)
+{
+    memset(s->acc, 0, sizeof(double) * (size_t)s->R * ACC_COUNT);
+    memset(s->met_acc, 0, sizeof(uint64_t) * (size_t)s->R);
+    memset(s->met_try, 0, sizeof(uint64_t) * (size_t)s->R);
+    memset(s->pt_acc, 0, sizeof(uint64_t) * (size_t)s->R);
+    memset(s->pt_try, 0, sizeof(uint64_t) * (size_t)s->R);
+}
+
+void orc_sim_get_ties(const orc_sim *s, int64_t *first_tie, int64_t *first_pt_tie, double *min_margin)
+{
+    for (int r = 0; r < s->R; ++r) first_tie[r] = s->first_tie[r];
+    *first_pt_tie = s->first_pt_tie;
+    *min_margin = s->min_margin;
+}
+
+uint64_t orc_sim_sweep_index(const orc_sim *s) { return s->t; }
