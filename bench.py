@@ -1,0 +1,329 @@
+"""Benchmark: site-updates/s of the FP32 batched sampler vs the FP64 plain kernel.
+
+One step = `sweeps_per_step` whole sweeps (Metropolis pass + overrelaxation pass
+over every colour class, parallel-tempering swap attempt and FP64 measurement
+after every sweep) of the workload's full batch.  Default workload: one Levy
+graph, L=128 (16384 sites), z=6, rho=3.5, 16 temperatures geometric in
+[0.8, 1.6], swap attempt every sweep.  A site-update is one Metropolis or one
+overrelaxation update of one spin of one replica.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the sequential CPU
+oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "site-updates/s FP32-batched vs FP64-plain on one GB300; % of memory roofline"
+UNIT = "site-updates/s"
+OPS_ALL = 1 | 2 | 4 | 8
+L2_FLUSH_BYTES = 256 << 20
+# algorithmic bytes per site-update (FP32 float2 spins, z = 6, R replicas sharing one CSR):
+# compulsory HBM model = own spin read 8 B + write 8 B + 6 x 4 B of indices / R
+# L2-level gather model = (z + 1) spin reads + 1 write (8 B each) + 6 x 4 B of indices / R
+def hbm_bytes_per_update(R):
+    return 16.0 + 24.0 / R
+
+
+def l2_bytes_per_update(R):
+    return 64.0 + 24.0 / R
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(device_index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _profile_traffic():
+    """DRAM bytes per launch of the batched kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "batched_kernel_C2.md")
+    src = os.path.join(ROOT, "paper_1211_3991_gb300", "csrc", "batched.cu")
+    if not os.path.exists(path):
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha256") != digest:
+        return None
+    try:
+        return {"bytes_per_sweep": float(vals["dram_bytes_per_sweep"]), "sweeps_per_launch": float(vals["sweeps_per_launch"])}
+    except (KeyError, ValueError):
+        return None
+
+
+def run_oracle_sample(cfg, sweeps, sample_index=0):
+    """The sequential FP64 oracle on one sample of the workload; returns (updates, seconds)."""
+    import oracle
+    from paper_1211_3991_gb300 import workloads as wl
+    L, rho, _ = cfg.graphs[sample_index]
+    ei, ej, _, _ = oracle.levy_graph(L, wl.Z, rho, wl.GRAPH_SEED, wl.graph_stream_id(cfg, sample_index))
+    color, _ = oracle.slo_color(L * L, ei, ej)
+    sim = oracle.Sim(L * L, ei, ej, color, cfg.betas(), cfg.deltas(), wl.SPIN_SEED, sample=wl.sample_id(sample_index),
+                     xy=oracle.lattice_xy(L), L=L)
+    sim.init()
+    t0 = time.perf_counter()
+    sim.sweeps(sweeps, OPS_ALL, 1)
+    dt = time.perf_counter() - t0
+    sim.close()
+    return L * L * cfg.n_temps * 2 * sweeps, dt
+
+
+def reference_arm(args, cfg):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    per_step = args.ref_sweeps
+    for _ in range(args.warmup):
+        run_oracle_sample(cfg, per_step)
+    ups, secs = 0, 0.0
+    for _ in range(args.steps):
+        u, dt = run_oracle_sample(cfg, per_step)
+        ups += u
+        secs += dt
+    value = ups / secs
+    sample = f"{per_step} sweeps of sample 0 of {cfg.name} ({cfg.description}) per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{cfg.name}: {cfg.description}", "engine": "sequential FP64 CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="C2")
+    ap.add_argument("--sweeps-per-step", type=int, default=0, help="0 = calibrate to about 50 ms per step")
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--cluster", type=int, default=0)
+    ap.add_argument("--group", type=int, default=0)
+    ap.add_argument("--ref-sweeps", type=int, default=4)
+    ap.add_argument("--cpu-sweeps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+
+    from paper_1211_3991_gb300 import workloads as wl
+    cfg = wl.config(args.config)
+    if args.impl == "reference":
+        reference_arm(args, cfg)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1211_3991_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1211_3991_gb300 import xyl
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    # weak scaling: every rank runs its own disorder realisations (sample ids offset by rank)
+    if world > 1:
+        cfg.graphs = [(L, rho, s + rank * cfg.n_samples) for (L, rho, s) in cfg.graphs]
+    graphs = wl.build_graphs(cfg)
+    stream = torch.cuda.current_stream()
+    tune = dict(block=args.block, cluster=args.cluster, group=args.group)
+    plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, **tune)
+    plan.bind(stream)
+    plan.init_spins(stream=stream)
+    updates_per_sweep = cfg.spins_per_sweep() * 2
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def timed_steps(p, n_steps, sweeps):
+        total_ms, launches = 0.0, 0
+        for _ in range(n_steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            p.sweep(sweeps, OPS_ALL, 1, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            total_ms += a.elapsed_time(b)
+            launches += p.last_launch_count()
+        return total_ms, launches
+
+    # calibrate the step length
+    sweeps = args.sweeps_per_step
+    if sweeps <= 0:
+        ms, _ = timed_steps(plan, 1, 50)
+        sweeps = int(min(20000, max(50, round(50.0 / max(ms / 50, 1e-6) / 10) * 10)))
+    for _ in range(args.warmup):
+        timed_steps(plan, 1, sweeps)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    clocks = ClockSampler(local)
+    total_ms, launches = timed_steps(plan, args.steps, sweeps)
+    clock_info = clocks.stop()
+    barrier()
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    units = updates_per_sweep * sweeps * args.steps * world
+    value = units / (max_ms / 1e3)
+
+    # end to end through the public API with host buffers: per step the slot
+    # half-widths go host->device, the step's measurements come back device->host
+    import numpy as np
+    deltas = np.array(cfg.deltas(), np.float64)
+    h2d = d2h = 0
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for s in range(cfg.n_samples):
+            plan.set_delta(s, deltas, stream=stream)
+        h2d = deltas.nbytes * cfg.n_samples
+        plan.sweep(sweeps, OPS_ALL, 1, stream=stream)
+        obs = plan.read_observables(stream=stream)
+        d2h = sum(v.nbytes for v in obs.values())
+        plan.reset_observables(stream=stream)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": updates_per_sweep * sweeps * args.steps / e2e_s * world, "unit": UNIT,
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    status, _ = plan.status(stream=stream)
+    if status != 0:
+        raise SystemExit(f"device status {status}")
+
+    # FP64 plain kernel on the same workload, same GPU
+    fp64 = None
+    if not args.no_fp64:
+        p64, _ = wl.make_plan(cfg, xyl.FP64_PLAIN, graphs=graphs)
+        p64.bind(stream)
+        p64.init_spins(stream=stream)
+        s64 = max(10, sweeps // 20)
+        timed_steps(p64, 1, s64)
+        n64 = max(3, min(args.steps, 5))
+        ms64, _ = timed_steps(p64, n64, s64)
+        fp64 = updates_per_sweep * s64 * n64 / (ms64 / 1e3)
+        del p64
+
+    peak, peak_kind = _peaks()
+    R = cfg.n_temps
+    avg_launch_s = (total_ms / 1e3) / max(1, launches)
+    per_launch_updates = updates_per_sweep * sweeps * args.steps / max(1, launches)
+    achieved = hbm_bytes_per_update(R) * per_launch_updates / avg_launch_s / 1e9
+    prof = _profile_traffic()
+    traffic = None if prof is None else prof["bytes_per_sweep"] * sweeps * args.steps / max(1, launches)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": peak_kind, "bytes_per_update": hbm_bytes_per_update(R),
+                "kernel": "batched_kernel"}
+    l2_achieved = l2_bytes_per_update(R) * per_launch_updates / avg_launch_s / 1e9
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        ups, secs = run_oracle_sample(cfg, args.cpu_sweeps)
+        cpu = {"value": ups / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_sweeps} sweeps of sample 0 of {cfg.name} ({ups} site-updates, {secs:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{cfg.name}: {cfg.description}", "engine": "FP32_BATCHED",
+                       "sweeps_per_step": sweeps, "samples_per_rank": cfg.n_samples, "temperatures": R,
+                       "l2": "flushed (256 MiB write) between timed steps",
+                       "cluster": plan_shape(plan), "parallelism": f"dp{world} (independent samples per rank)"},
+            "fp64_plain": {"value": fp64, "unit": UNIT, "ratio_fp32_batched_over_fp64_plain":
+                           (value / world / fp64) if fp64 else None},
+            "roofline": roofline,
+            "roofline_l2_model": {"bytes_per_update": l2_bytes_per_update(R), "achieved_GBps": l2_achieved},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clock_info,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def plan_shape(plan):
+    return {"units": plan.unit_count()}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,277 @@
+/*
+ * xyl.h -- C ABI of the GB300 (sm_103a) Monte Carlo library for the XY model on
+ * dilute Levy graphs (Ibanez Berganza & Leuzzi, "Critical behavior of the XY
+ * model in complex topologies").
+ *
+ * Model, Eq. (HXY): H = -sum_{i<j} J_ij S_i . S_j with S_i a unit 2-vector and
+ * J_ij in {0,1} the adjacency of the graph.  Graph, Eq. (Levyi): sites of a
+ * periodic L x L square lattice; a link lands at distance r with probability
+ * proportional to r^-rho; here every site carries exactly z links.
+ *
+ * Conventions for every entry point:
+ *   * The return value is a status: XYL_OK (0) or a negative XYL_E* code; the
+ *     thread-local message of the last failure is xyl_last_error().  Nothing
+ *     aborts, nothing prints.
+ *   * Graph handles live in host memory and are owned by the library
+ *     (xyl_graph_free).  Plans are host objects owned by the library
+ *     (xyl_plan_free).
+ *   * ALL device memory is owned by the caller: xyl_plan_create reports the
+ *     workspace size, the caller allocates it (any allocator) and passes the
+ *     device pointer to xyl_bind.  The library never allocates or frees device
+ *     memory after that.
+ *   * `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device calls are asynchronous on that stream, except the
+ *     xyl_read_* / xyl_export_state calls, which synchronise it before
+ *     returning host data.
+ *   * Sites have two numberings: the ORIGINAL id (x + L*y on the lattice, or the
+ *     caller's id for xyl_graph_from_edges) and the colour-sorted id of the CSR.
+ *     Random streams and every host-visible per-site array use original ids.
+ */
+#ifndef XYL_H
+#define XYL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define XYL_OK 0
+#define XYL_EINVAL (-1)   /* bad argument */
+#define XYL_ENOSPC (-2)   /* workspace too small */
+#define XYL_EGRAPH (-3)   /* no valid graph within the restart limit */
+#define XYL_ECUDA (-4)    /* a CUDA runtime call failed */
+#define XYL_ETIMEOUT (-5) /* a bounded device-side wait gave up */
+#define XYL_ESTATE (-6)   /* wrong call order (e.g. sweep before bind) */
+
+/* ---- sweep operations (bit mask) --------------------------------------- */
+#define XYL_OP_MET 1u     /* Metropolis pass over the colour classes (App. B) */
+#define XYL_OP_OR 2u      /* overrelaxation pass (App. B, Creutz reflection) */
+#define XYL_OP_PT 4u      /* parallel-tempering swap attempt after the sweep */
+#define XYL_OP_MEASURE 8u /* accumulate the Sec. III observables */
+
+/* ---- engines ------------------------------------------------------------ */
+#define XYL_FP64_PLAIN 0   /* FP64 unit vectors, one launch per colour phase */
+#define XYL_FP32_BATCHED 1 /* FP32 unit vectors, persistent resident engine */
+#define XYL_FP32_PLAIN 2   /* FP32 arithmetic on the per-phase launch structure */
+
+/* ---- accumulator layout: per (sample, temperature slot), FP64 ----------- */
+#define XYL_ACC_N 0     /* number of measurements */
+#define XYL_ACC_E 1     /* sum of e = E/N */
+#define XYL_ACC_E2 2    /* sum of e^2 */
+#define XYL_ACC_ABSM 3  /* sum of |m| */
+#define XYL_ACC_MX 4    /* sum of m_x */
+#define XYL_ACC_MY 5    /* sum of m_y */
+#define XYL_ACC_M2 6    /* sum of m^2 */
+#define XYL_ACC_M4 7    /* sum of m^4 */
+#define XYL_ACC_CHIK 8  /* sum of (|F(k1)|^2 + |F(k2)|^2) / (2N), k = 2 pi / L */
+#define XYL_ACC_COUNT 9
+
+typedef struct xyl_graph xyl_graph;
+typedef struct xyl_plan xyl_plan;
+
+/* Thread-local description of the last failure ("" if none). */
+const char *xyl_last_error(void);
+
+/* ABI version of this header (major * 100 + minor). */
+int xyl_version(void);
+
+/* ========================================================================= */
+/* Graphs (host)                                                             */
+/* ========================================================================= */
+
+/*
+ * xyl_build_graph_csr -- one dilute Levy graph, Eq. (Levyi), and its
+ * colour-sorted CSR (App. B "Graph coloring", "Memory management").
+ *   L         even lattice side >= 4; N = L*L sites, periodic boundaries.
+ *   z         links per site (every site exactly z); N*z must be even.
+ *   rho       decay exponent of the link-length law r^-rho (minimum-image
+ *             Euclidean r, displacements dx,dy in {-L/2+1..L/2}).
+ *   seed      64-bit key of the graph random stream; sample_id selects an
+ *             independent stream (disorder realisation).
+ *   out       receives a new handle (free with xyl_graph_free).
+ * Construction: sequential pairing; a uniformly chosen unsaturated site links
+ * to an eligible partner (unsaturated, not yet linked, not itself) drawn with
+ * the link law restricted to eligible partners; a dead end restarts the whole
+ * graph (at most 100 restarts, then XYL_EGRAPH).  Colouring: smallest-last
+ * ordering, ties by smallest id, greedy colours in reverse removal order.
+ * Errors: XYL_EINVAL for bad sizes, XYL_EGRAPH as above.
+ */
+int xyl_build_graph_csr(int32_t L, int32_t z, double rho, uint64_t seed, uint32_t sample_id, xyl_graph **out);
+
+/*
+ * xyl_graph_from_edges -- a graph from an explicit simple edge list (for the
+ * chain, ring and small-graph checks).  edges: 2*n_edges ids in [0,n), no
+ * self-loops or repeated pairs (XYL_EINVAL otherwise).  xy: 2n lattice
+ * coordinates used by the Fourier sums at k = 2 pi / L, or NULL (then x = id,
+ * y = 0 and the period is n).  Coloured and packed like xyl_build_graph_csr.
+ */
+int xyl_graph_from_edges(int32_t n, int64_t n_edges, const int32_t *edges, const int32_t *xy, int32_t L,
+                         xyl_graph **out);
+
+/* Sizes of a graph; any output pointer may be NULL.  restarts: pairing restarts used. */
+int xyl_graph_info(const xyl_graph *g, int32_t *n, int64_t *n_edges, int32_t *n_colors, int32_t *max_deg,
+                   int32_t *restarts);
+
+/*
+ * xyl_graph_export_csr -- copy out the colour-sorted CSR (host buffers owned by
+ * the caller): perm[n] (colour-sorted id -> original id), row_ptr[n+1],
+ * col[2*n_edges] (colour-sorted neighbour ids, ascending within a row),
+ * color_ptr[n_colors+1] (first colour-sorted id of each colour).
+ */
+int xyl_graph_export_csr(const xyl_graph *g, int32_t *perm, int32_t *row_ptr, int32_t *col, int32_t *color_ptr);
+
+/* Links in creation order (ei chose ej), original ids; n_edges entries each. */
+int xyl_graph_export_edges(const xyl_graph *g, int32_t *ei, int32_t *ej);
+
+void xyl_graph_free(xyl_graph *g);
+
+/* ========================================================================= */
+/* Plans: a batch of samples x temperature slots bound to one workspace       */
+/* ========================================================================= */
+
+typedef struct {
+    const xyl_graph *graph; /* borrowed for the duration of xyl_plan_create */
+    uint32_t sample_id;     /* keys the spin random streams of this sample */
+    int32_t n_temps;        /* temperature slots = replicas of this sample */
+    const double *beta;     /* n_temps inverse temperatures (slot order) */
+    const double *delta;    /* n_temps Metropolis half-widths (slot order) */
+} xyl_sample;
+
+typedef struct {
+    int32_t block;           /* threads per CTA of the batched engine (0 = tuned default) */
+    int32_t cluster;         /* CTAs per cluster of the batched engine (0 = tuned default) */
+    int32_t group;           /* replicas per cluster, a power of two dividing every n_temps (0 = default) */
+    int32_t recompute_every; /* FP64 energy recompute + renormalise every this many sweeps (0 = never) */
+    int32_t reserved[4];
+} xyl_tuning;
+
+/*
+ * xyl_plan_create -- lay out a batch of n_samples samples (each with its own
+ * graph and temperature slots) for one engine.  Replica r of a sample starts at
+ * slot r.  seed keys every spin/Metropolis/PT random stream.  tune may be NULL.
+ * *workspace_bytes receives the device bytes xyl_bind needs.
+ * Errors: XYL_EINVAL (empty batch, bad slot count, unknown engine).
+ */
+int xyl_plan_create(const xyl_sample *samples, int32_t n_samples, int32_t engine, uint64_t seed,
+                    const xyl_tuning *tune, xyl_plan **out, size_t *workspace_bytes);
+
+/*
+ * xyl_bind -- attach a caller-owned device workspace (>= workspace_bytes,
+ * 256-byte aligned) and upload graphs, tables and temperatures into it.  The
+ * workspace must outlive the plan's use.  Synchronises `stream`.
+ * Errors: XYL_ENOSPC, XYL_EINVAL (misaligned), XYL_ECUDA.
+ */
+int xyl_bind(xyl_plan *p, void *d_workspace, size_t bytes, void *stream);
+
+/*
+ * xyl_init_spins -- theta = 2 pi u - pi from the INIT stream of each (site,
+ * replica, sample), stored as unit vectors; aligned != 0 sets every spin to
+ * (1, 0) instead.  Resets the sweep counter, the slot labels, the per-slot
+ * accumulators and the status word.
+ */
+int xyl_init_spins(xyl_plan *p, int32_t aligned, void *stream);
+
+/*
+ * xyl_sweep -- n_sweeps Monte Carlo sweeps (App. B).  One sweep: the Metropolis
+ * pass (XYL_OP_MET) runs the colour classes in turn, each site proposing
+ * theta + Delta (2u - 1) and accepting iff dE <= 0 or u' < exp(-beta dE); the
+ * overrelaxation pass (XYL_OP_OR) then reflects each spin about its local
+ * field, s' = 2 (s.h) h / |h|^2 - s (unchanged when h = 0); the energy and the
+ * Fourier/magnetisation sums of each replica are fused into the last pass.
+ * XYL_OP_PT: swap attempts between slots (k, k+1), k = t mod 2, 4, ...,
+ * accepted iff u < exp((beta_k - beta_k+1)(E_k - E_k+1)) in FP64.
+ * XYL_OP_MEASURE: when (t+1) is a multiple of measure_every, add the Sec. III
+ * observables of the replica at each slot to that slot's FP64 accumulators.
+ * Must include XYL_OP_MET or XYL_OP_OR.  Errors: XYL_EINVAL, XYL_ESTATE,
+ * XYL_ECUDA; a device wait that gives up sets the status word (see
+ * xyl_read_status) and later calls return XYL_ETIMEOUT.
+ */
+int xyl_sweep(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_every, void *stream);
+
+/*
+ * xyl_sweep_units -- XYL_FP32_BATCHED only: run xyl_sweep on the work units
+ * [first_unit, first_unit + n_units) of the batch (a unit is one group of
+ * replicas of one sample; units are numbered sample by sample).  All units of
+ * a sample must be included for parallel tempering to proceed: a sample whose
+ * groups are split across calls makes the in-kernel wait for the missing
+ * groups give up after about a second, set the status word to XYL_ETIMEOUT
+ * and return (the GPU context stays usable; xyl_init_spins clears it).
+ * Errors: XYL_EINVAL (wrong engine or range), XYL_ESTATE, XYL_ECUDA.
+ */
+int xyl_sweep_units(xyl_plan *p, int32_t first_unit, int32_t n_units, int32_t n_sweeps, uint32_t ops,
+                    int32_t measure_every, void *stream);
+
+/* Number of work units of a batched plan (0 for other engines). */
+int32_t xyl_unit_count(const xyl_plan *p);
+
+/*
+ * xyl_pt_swap -- one parallel-tempering step (App. B "Improved equilibrium
+ * dynamics") at the current sweep index, from freshly recomputed FP64
+ * energies; does not advance the sweep counter.
+ */
+int xyl_pt_swap(xyl_plan *p, void *stream);
+
+/*
+ * xyl_measure -- recompute every replica's energy, magnetisation and Fourier
+ * sums in FP64 from the stored spins and add one measurement (Sec. III
+ * observables) to each slot's accumulators.
+ */
+int xyl_measure(xyl_plan *p, void *stream);
+
+/*
+ * xyl_recompute -- FP64 recomputation of every replica's energy from its spins
+ * and renormalisation |s| = 1; records the largest |E_fused - E_fp64| seen.
+ */
+int xyl_recompute(xyl_plan *p, void *stream);
+
+/* Replace the Metropolis half-widths of one sample's slots (n_temps values). */
+int xyl_set_delta(xyl_plan *p, int32_t sample, const double *delta, void *stream);
+
+/*
+ * xyl_read_observables -- per-slot accumulators, slot-major over the batch
+ * (sample 0 slots, sample 1 slots, ...).  acc: [slots][XYL_ACC_COUNT];
+ * met_acc/met_try: accepted / attempted Metropolis updates per slot; pt_acc /
+ * pt_try: accepted / attempted swaps of pair (k, k+1) stored at slot k.  Any
+ * pointer may be NULL.  Synchronises `stream`.
+ */
+int xyl_read_observables(xyl_plan *p, double *acc, uint64_t *met_acc, uint64_t *met_try, uint64_t *pt_acc,
+                         uint64_t *pt_try, void *stream);
+
+/* Zero the per-slot accumulators and counters (e.g. between bins). */
+int xyl_reset_observables(xyl_plan *p, void *stream);
+
+/* Energy of every replica after the last sweep / recompute (FP64), replica-major over the batch. */
+int xyl_read_energies(xyl_plan *p, double *E, void *stream);
+
+/* replica_at_slot[k] for every slot of the batch (slot-major). */
+int xyl_read_labels(xyl_plan *p, int32_t *replica_at_slot, void *stream);
+
+/* Spin vectors of one replica, original site order: sxy[2*i], sxy[2*i+1] (FP64). */
+int xyl_read_spins(xyl_plan *p, int32_t sample, int32_t replica, double *sxy, void *stream);
+
+/* Overwrite the spin vectors of one replica (original site order). */
+int xyl_write_spins(xyl_plan *p, int32_t sample, int32_t replica, const double *sxy, void *stream);
+
+/* Status word (0 = fine, else an XYL_E* code recorded on the device) and the sweep index of sample 0. */
+int xyl_read_status(xyl_plan *p, int32_t *status, uint64_t *sweep_index, void *stream);
+
+/* Bytes of a checkpoint: spins, labels, sweep counters, accumulators, counters. */
+size_t xyl_state_bytes(const xyl_plan *p);
+
+/* Copy the whole sampler state to / from a host buffer of xyl_state_bytes(). */
+int xyl_export_state(xyl_plan *p, void *host, size_t bytes, void *stream);
+int xyl_import_state(xyl_plan *p, const void *host, size_t bytes, void *stream);
+
+/* Number of kernel launches the last xyl_sweep call issued (graph nodes count). */
+int64_t xyl_last_launch_count(const xyl_plan *p);
+
+void xyl_plan_free(xyl_plan *p);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XYL_H */

@@ -1,0 +1,333 @@
+// Batched FP32 engine: one launch runs many whole sweep + swap + measure
+// cycles for a batch of samples.
+//
+// Work decomposition.  The replicas of a sample are split into groups of Rg
+// (a power of two).  Each (sample, group) unit is owned by one thread-block
+// cluster of G CTAs.  Inside a unit, every colour class is cut into G
+// contiguous chunks; CTA k updates chunk k for all Rg replicas, one thread per
+// (site, replica) with the replica index fastest, so the lanes that share a
+// site read one contiguous Rg x 8-byte segment of each neighbour's row.
+// Spins are interleaved [sample][site][replica] float2 in global memory (kept
+// L2-resident for the batch sizes this engine serves); they are read and
+// written through L2 (ld/st .cg), and colour phases are separated by cluster
+// barriers (release/acquire at cluster scope).
+//
+// Sweep (App. B): Metropolis over colours 0..Q-1, then overrelaxation over
+// colours 0..Q-1; the last pass also accumulates each replica's energy (links
+// to lower colours, counted once at their upper endpoint), magnetisation and
+// Fourier sums.  Then the groups of a sample meet at a bounded global barrier,
+// every CTA reads the sample's energies and takes the same PT decisions
+// (FP64, deterministic), and the first CTA of group 0 adds the measurement.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "engines.h"
+
+namespace cg = cooperative_groups;
+
+namespace xyl {
+namespace {
+
+constexpr unsigned int kBarrierPolls = 1u << 21;  // about a second of polling
+constexpr int kMaxReplicas = 256;
+
+struct BatchedParams {
+    const int2 *units;   // (sample, group) per cluster
+    int unit_begin;
+    int G, Rg, log2Rg;
+    int n_sweeps;
+    uint32_t ops;
+    int measure_every;
+};
+
+__device__ __forceinline__ float2 ld_spin(const float2 *p) { return __ldcg(p); }
+__device__ __forceinline__ void st_spin(float2 *p, float2 v) { __stcg(p, v); }
+
+struct SharedState {
+    double obs[32][kObsStride];            // per group replica: fused sums of this CTA
+    unsigned long long met[32];            // per group replica: accepted Metropolis moves
+    double E[kMaxReplicas];                // energies of every replica of the sample
+    float beta[kMaxReplicas];              // per slot
+    float delta[kMaxReplicas];             // per slot
+    int slot_of[kMaxReplicas];
+    int rep_at[kMaxReplicas];
+    int abort_flag;
+};
+
+// One colour phase of one pass for this CTA's chunk.
+template <bool IS_MET, bool FUSE>
+__device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, SharedState &sh, const BatchedParams &bp,
+                                      int group, int rank, int c, uint32_t t)
+{
+    const int cb = __ldg(P.color_ptr + d.color_off + c), ce = __ldg(P.color_ptr + d.color_off + c + 1);
+    const int nc = ce - cb;
+    const int chunk = (nc + bp.G - 1) / bp.G;
+    const int lo = cb + rank * chunk;
+    const int hi = min(ce, lo + chunk);
+    const int items = hi > lo ? (hi - lo) << bp.log2Rg : 0;
+    float2 *sp = reinterpret_cast<float2 *>(P.spins) + d.spin_off;
+    const int32_t *rp = P.row_ptr + d.row_off;
+    const int32_t *cl = P.col + d.col_off;
+    const int R = d.R;
+    const int rl = threadIdx.x & (bp.Rg - 1);
+    const int r = group * bp.Rg + rl;
+
+    float acc[kObsCount];
+#pragma unroll
+    for (int f = 0; f < kObsCount; ++f) acc[f] = 0.0f;
+    unsigned int n_acc = 0;
+
+    for (int q = threadIdx.x; q < items; q += blockDim.x) {
+        const int i = lo + (q >> bp.log2Rg);
+        const float2 si = ld_spin(sp + (int64_t)i * R + r);
+        float hx = 0.f, hy = 0.f, lx = 0.f, ly = 0.f;
+        const int rb = __ldg(rp + i), re = __ldg(rp + i + 1);
+        for (int k = rb; k < re; ++k) {
+            const int j = __ldg(cl + k);
+            const float2 sj = ld_spin(sp + (int64_t)j * R + r);
+            hx += sj.x;
+            hy += sj.y;
+            if (FUSE && j < cb) {
+                lx += sj.x;
+                ly += sj.y;
+            }
+        }
+        float nx, ny;
+        if (IS_MET) {
+            const int slot = sh.slot_of[r];
+            const Words4 x = philox_draw((uint32_t)__ldg(P.perm + d.site_off + i), t, kPurposeMet, (uint32_t)r,
+                                         d.sample_id, P.key);
+            const bool ok = metropolis_step(si.x, si.y, hx, hy, sh.beta[slot], sh.delta[slot], x, nx, ny);
+            if (ok) {
+                st_spin(sp + (int64_t)i * R + r, make_float2(nx, ny));
+                ++n_acc;
+            } else {
+                nx = si.x;
+                ny = si.y;
+            }
+        } else {
+            overrelax_step(si.x, si.y, hx, hy, nx, ny);
+            st_spin(sp + (int64_t)i * R + r, make_float2(nx, ny));
+        }
+        if (FUSE) {
+            const float4 ph = __ldg(reinterpret_cast<const float4 *>(P.phase) + d.site_off + i);
+            acc[kObsE] -= nx * lx + ny * ly;
+            acc[kObsMx] += nx;
+            acc[kObsMy] += ny;
+            acc[kObsF1xRe] += nx * ph.x; acc[kObsF1xIm] += nx * ph.y;
+            acc[kObsF1yRe] += ny * ph.x; acc[kObsF1yIm] += ny * ph.y;
+            acc[kObsF2xRe] += nx * ph.z; acc[kObsF2xIm] += nx * ph.w;
+            acc[kObsF2yRe] += ny * ph.z; acc[kObsF2yIm] += ny * ph.w;
+        }
+    }
+    // lanes l and l ^ o (o >= Rg) hold the same replica
+    if (IS_MET) {
+        for (int o = 16; o >= bp.Rg; o >>= 1) n_acc += __shfl_xor_sync(0xffffffffu, n_acc, o);
+        if ((threadIdx.x & 31) < bp.Rg && n_acc) atomicAdd(&sh.met[rl], (unsigned long long)n_acc);
+    }
+    if (FUSE) {
+#pragma unroll
+        for (int f = 0; f < kObsCount; ++f) {
+            float v = acc[f];
+            for (int o = 16; o >= bp.Rg; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) < bp.Rg) atomicAdd(&sh.obs[rl][f], (double)v);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) batched_kernel(DevPlan P, BatchedParams bp)
+{
+    __shared__ SharedState sh;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int unit = bp.unit_begin + (int)(blockIdx.x / bp.G);
+    const int rank = (int)cluster.block_rank();
+    const int2 ug = bp.units[unit];
+    const int s = ug.x, group = ug.y;
+    const DevSample d = P.samples[s];
+    const int R = d.R;
+    const int n_groups = R / bp.Rg;
+    const bool leader = (group == 0 && rank == 0);
+
+    for (int k = threadIdx.x; k < R; k += blockDim.x) {
+        sh.slot_of[k] = P.slot_of[d.rep_off + k];
+        sh.rep_at[k] = P.rep_at[d.rep_off + k];
+        sh.beta[k] = (float)P.beta[d.rep_off + k];
+        sh.delta[k] = (float)P.delta[d.rep_off + k];
+    }
+    for (int q = threadIdx.x; q < 32 * kObsStride; q += blockDim.x) (&sh.obs[0][0])[q] = 0.0;
+    if (threadIdx.x < 32) sh.met[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) sh.abort_flag = 0;
+    uint32_t t = P.sweep[s];
+    __syncthreads();
+
+    const bool met = bp.ops & XYL_OP_MET, orx = bp.ops & XYL_OP_OR;
+    for (int it = 0; it < bp.n_sweeps; ++it) {
+        if (met) {
+            for (int c = 0; c < d.Q; ++c) {
+                if (orx) phase<true, false>(P, d, sh, bp, group, rank, c, t);
+                else phase<true, true>(P, d, sh, bp, group, rank, c, t);
+                cluster.sync();
+            }
+        }
+        if (orx) {
+            for (int c = 0; c < d.Q; ++c) {
+                phase<false, true>(P, d, sh, bp, group, rank, c, t);
+                cluster.sync();
+            }
+        }
+        // publish this CTA's partial sums and acceptance counts
+        const int buf = (int)(t & 1u);
+        double *obs_s = P.obs + ((size_t)buf * P.total_R + d.rep_off) * kObsStride;
+        for (int q = threadIdx.x; q < bp.Rg * kObsCount; q += blockDim.x) {
+            const int rl = q / kObsCount, f = q % kObsCount;
+            atomicAdd(obs_s + (size_t)(group * bp.Rg + rl) * kObsStride + f, sh.obs[rl][f]);
+            sh.obs[rl][f] = 0.0;
+        }
+        if (met && threadIdx.x < bp.Rg) {
+            const int r = group * bp.Rg + threadIdx.x;
+            if (sh.met[threadIdx.x]) atomicAdd(&P.met_acc[d.rep_off + sh.slot_of[r]], sh.met[threadIdx.x]);
+            sh.met[threadIdx.x] = 0ull;
+        }
+        cluster.sync();
+        if (n_groups > 1) {
+            if (rank == 0 && threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(&P.barrier[s], 1u);
+                if (!wait_counter_at_least(&P.barrier[s], (unsigned int)(n_groups * (it + 1)), kBarrierPolls)) {
+                    atomicExch(P.status, XYL_ETIMEOUT);
+                    sh.abort_flag = 1;
+                }
+                __threadfence();
+            }
+            cluster.sync();
+            // the decision comes from rank 0's shared flag so that every CTA of
+            // the cluster takes the same branch (a cluster barrier has no timeout)
+            const int *flag0 = cluster.map_shared_rank(&sh.abort_flag, 0);
+            const int abort_now = *(volatile const int *)flag0;
+            cluster.sync();  // rank 0 stays resident until every CTA has read its flag
+            if (abort_now) break;
+        }
+        for (int k = threadIdx.x; k < R; k += blockDim.x) sh.E[k] = __ldcg(obs_s + (size_t)k * kObsStride + kObsE);
+        __syncthreads();
+        // parallel tempering, identical in every CTA
+        if (bp.ops & XYL_OP_PT) {
+            for (int p = threadIdx.x; 2 * p + (int)(t & 1u) + 1 < R; p += blockDim.x) {
+                const int k = 2 * p + (int)(t & 1u);
+                const int a = sh.rep_at[k], b = sh.rep_at[k + 1];
+                const double x = (P.beta[d.rep_off + k] - P.beta[d.rep_off + k + 1]) * (sh.E[a] - sh.E[b]);
+                const Words4 w = philox_draw((uint32_t)k, t, kPurposePt, 0u, d.sample_id, P.key);
+                const bool accept = uniform53(w.w0, w.w1) < exp(x);
+                if (leader) P.pt_try[d.rep_off + k] += 1ull;
+                if (accept) {
+                    sh.rep_at[k] = b;
+                    sh.rep_at[k + 1] = a;
+                    sh.slot_of[b] = k;
+                    sh.slot_of[a] = k + 1;
+                    if (leader) P.pt_acc[d.rep_off + k] += 1ull;
+                }
+            }
+            __syncthreads();
+        }
+        if (leader) {
+            const bool measure = (bp.ops & XYL_OP_MEASURE) && bp.measure_every > 0 &&
+                                 ((t + 1u) % (uint32_t)bp.measure_every) == 0u;
+            const double invN = 1.0 / (double)d.N;
+            for (int k = threadIdx.x; k < R; k += blockDim.x) {
+                const int r = sh.rep_at[k];
+                P.rep_at[d.rep_off + k] = r;
+                P.slot_of[d.rep_off + r] = k;
+                P.last_E[d.rep_off + k] = sh.E[k];
+                if (met) P.met_try[d.rep_off + k] += (unsigned long long)d.N;
+                if (measure) {
+                    const double *o = obs_s + (size_t)r * kObsStride;
+                    double ov[kObsCount];
+#pragma unroll
+                    for (int f = 0; f < kObsCount; ++f) ov[f] = __ldcg(o + f);
+                    const double e = ov[kObsE] * invN;
+                    const double mx = ov[kObsMx] * invN, my = ov[kObsMy] * invN;
+                    const double m2 = mx * mx + my * my;
+                    const double f1 = ov[kObsF1xRe] * ov[kObsF1xRe] + ov[kObsF1xIm] * ov[kObsF1xIm] +
+                                      ov[kObsF1yRe] * ov[kObsF1yRe] + ov[kObsF1yIm] * ov[kObsF1yIm];
+                    const double f2 = ov[kObsF2xRe] * ov[kObsF2xRe] + ov[kObsF2xIm] * ov[kObsF2xIm] +
+                                      ov[kObsF2yRe] * ov[kObsF2yRe] + ov[kObsF2yIm] * ov[kObsF2yIm];
+                    double *a = P.acc + (size_t)(d.rep_off + k) * kAccCount;
+                    a[XYL_ACC_N] += 1.0;
+                    a[XYL_ACC_E] += e;
+                    a[XYL_ACC_E2] += e * e;
+                    a[XYL_ACC_ABSM] += sqrt(m2);
+                    a[XYL_ACC_MX] += mx;
+                    a[XYL_ACC_MY] += my;
+                    a[XYL_ACC_M2] += m2;
+                    a[XYL_ACC_M4] += m2 * m2;
+                    a[XYL_ACC_CHIK] += (f1 + f2) * 0.5 * invN;
+                }
+            }
+        }
+        // clear this group's slots of the buffer the next sweep fills: every
+        // reader of it finished before the barrier just passed
+        if (rank == 0) {
+            double *nxt = P.obs + ((size_t)(buf ^ 1) * P.total_R + d.rep_off + group * bp.Rg) * kObsStride;
+            for (int q = threadIdx.x; q < bp.Rg * kObsStride; q += blockDim.x) nxt[q] = 0.0;
+        }
+        ++t;
+        cluster.sync();
+    }
+    if (leader && threadIdx.x == 0) P.sweep[s] = t;
+}
+
+}  // namespace
+
+size_t batched_smem_bytes(const PlanShape &, const BatchedShape &) { return sizeof(SharedState); }
+
+// Also opts the kernel into clusters wider than 8; call before the first launch.
+cudaError_t batched_max_active_clusters(const PlanShape &, const BatchedShape &B, int *clusters)
+{
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(B.G, 1, 1);
+    cfg.blockDim = dim3(B.block, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = B.G;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (B.G > 8) {
+        cudaError_t e = cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaOccupancyMaxActiveClusters(clusters, batched_kernel, &cfg);
+}
+
+cudaError_t launch_batched(const DevPlan &P, const PlanShape &, const BatchedShape &B, const int2 *d_units,
+                           int unit_begin, int unit_count, int n_sweeps, uint32_t ops, int measure_every,
+                           cudaStream_t st)
+{
+    if (unit_count <= 0) return cudaSuccess;
+    BatchedParams bp;
+    bp.units = d_units;
+    bp.unit_begin = unit_begin;
+    bp.G = B.G;
+    bp.Rg = B.Rg;
+    bp.log2Rg = 0;
+    while ((1 << bp.log2Rg) < B.Rg) ++bp.log2Rg;
+    bp.n_sweeps = n_sweeps;
+    bp.ops = ops;
+    bp.measure_every = measure_every;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3((unsigned)(B.G * unit_count), 1, 1);
+    cfg.blockDim = dim3((unsigned)B.block, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = B.G;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, batched_kernel, P, bp);
+}
+
+}  // namespace xyl

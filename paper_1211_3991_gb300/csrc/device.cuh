@@ -1,0 +1,155 @@
+// Device-side descriptors and the per-spin update arithmetic shared by the
+// engines of libxyl.  Spins are unit 2-vectors; the Hamiltonian is
+// H = -sum_{i<j} J_ij S_i . S_j, Eq. (HXY).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/xyl.h"
+#include "philox.cuh"
+
+namespace xyl {
+
+// Per-replica sums produced by the last pass of a sweep (FP64 slots):
+// energy, magnetisation and the Fourier sums at k1 = (2pi/L, 0), k2 = (0, 2pi/L)
+// for both spin components (Sec. III, definition of xi_2).
+enum ObsField : int {
+    kObsE = 0,
+    kObsMx, kObsMy,
+    kObsF1xRe, kObsF1xIm, kObsF1yRe, kObsF1yIm,   // k1: spin x / spin y components
+    kObsF2xRe, kObsF2xIm, kObsF2yRe, kObsF2yIm,   // k2
+    kObsCount
+};
+constexpr int kObsStride = 12;  // padded
+constexpr int kAccCount = XYL_ACC_COUNT;
+
+struct DevSample {
+    int32_t N, Q, R, L;
+    uint32_t sample_id;
+    int32_t max_deg;
+    int32_t color_off;   // into color_ptr (Q + 1 entries per sample)
+    int32_t rep_off;     // into per-replica and per-slot arrays (R per sample)
+    int64_t site_off;    // into perm / phase arrays (N per sample)
+    int64_t row_off;     // into row_ptr (N + 1 per sample)
+    int64_t col_off;     // into col (nnz per sample)
+    int64_t spin_off;    // into the spin array, in vectors
+};
+
+struct DevPlan {
+    const DevSample *samples;
+    int32_t n_samples;
+    int32_t total_R;
+    const int32_t *row_ptr;
+    const int32_t *col;        // colour-sorted ids local to the sample
+    const int32_t *perm;       // colour-sorted id -> original id
+    const int32_t *color_ptr;
+    const void *phase;         // per site (cos kx, sin kx, cos ky, sin ky): float4 or double4_32a
+    void *spins;               // float2 / double2
+    const double *beta;        // per slot
+    const double *delta;       // per slot
+    int32_t *slot_of;          // per replica: slot it sits at
+    int32_t *rep_at;           // per slot: replica sitting there
+    double *obs;               // [2][total_R][kObsStride] per-replica sums of the current sweep
+    double *last_E;            // [total_R] energy after the last sweep
+    double *acc;               // [total_R slots][kAccCount]
+    unsigned long long *met_acc, *met_try, *pt_acc, *pt_try;  // per slot
+    uint32_t *sweep;           // per sample sweep counter
+    int32_t *status;           // 0 or an XYL_E* code
+    unsigned int *barrier;     // per sample arrival counters (batched engine)
+    double *drift;             // largest |E_fused - E_fp64| seen by a recompute
+    uint64_t key;              // Philox key of the spin streams
+};
+
+template <typename Real> struct Vec2T;
+template <> struct Vec2T<float> { using type = float2; };
+template <> struct Vec2T<double> { using type = double2; };
+template <typename Real> using Vec2 = typename Vec2T<Real>::type;
+
+template <typename Real> struct Vec4T;
+template <> struct Vec4T<float> { using type = float4; };
+template <> struct Vec4T<double> { using type = double4_32a; };
+template <typename Real> using Vec4 = typename Vec4T<Real>::type;
+
+// ---------------------------------------------------------------------------
+// Metropolis step of one spin (App. B): proposal = rotation of s by
+// delta = Delta (2u - 1); dE = -(s' - s) . h; accept iff dE <= 0 or
+// u' < exp(-beta dE).  FP64 uses 53-bit uniforms from (w0,w1) and (w2,w3);
+// FP32 uses 24-bit uniforms from w0 and w1, hardware sincos/exp and
+// renormalises the rotated proposal.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool metropolis_step(double sx, double sy, double hx, double hy, double beta,
+                                                double half_width, Words4 x, double &nx, double &ny)
+{
+    const double ud = uniform53(x.w0, x.w1), ua = uniform53(x.w2, x.w3);
+    double sn, cs;
+    sincos(half_width * (2.0 * ud - 1.0), &sn, &cs);
+    nx = cs * sx - sn * sy;
+    ny = sn * sx + cs * sy;
+    const double dE = -((nx - sx) * hx + (ny - sy) * hy);
+    return dE <= 0.0 || ua < exp(-beta * dE);
+}
+
+__device__ __forceinline__ bool metropolis_step(float sx, float sy, float hx, float hy, float beta,
+                                                float half_width, Words4 x, float &nx, float &ny)
+{
+    const float ud = uniform24(x.w0), ua = uniform24(x.w1);
+    float sn, cs;
+    __sincosf(half_width * (2.0f * ud - 1.0f), &sn, &cs);
+    float px = cs * sx - sn * sy, py = sn * sx + cs * sy;
+    const float inv = rsqrtf(px * px + py * py);
+    nx = px * inv;
+    ny = py * inv;
+    const float dE = -((nx - sx) * hx + (ny - sy) * hy);
+    return dE <= 0.0f || ua < __expf(-beta * dE);
+}
+
+// Overrelaxation (App. B; Creutz): reflection of s about the local field h,
+// s' = 2 (s.h) h / |h|^2 - s; s unchanged when h = 0.
+__device__ __forceinline__ void overrelax_step(double sx, double sy, double hx, double hy, double &nx, double &ny)
+{
+    const double h2 = hx * hx + hy * hy;
+    if (h2 > 0.0) {
+        const double k = 2.0 * (sx * hx + sy * hy) / h2;
+        nx = k * hx - sx;
+        ny = k * hy - sy;
+    } else {
+        nx = sx;
+        ny = sy;
+    }
+}
+
+__device__ __forceinline__ void overrelax_step(float sx, float sy, float hx, float hy, float &nx, float &ny)
+{
+    const float h2 = hx * hx + hy * hy;
+    if (h2 > 0.0f) {
+        const float k = __fdividef(2.0f * (sx * hx + sy * hy), h2);
+        nx = k * hx - sx;
+        ny = k * hy - sy;
+    } else {
+        nx = sx;
+        ny = sy;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Bounded spin on a monotone counter; returns false after `limit` polls.
+__device__ __forceinline__ bool wait_counter_at_least(const unsigned int *ctr, unsigned int target, unsigned int limit)
+{
+    for (unsigned int it = 0; it < limit; ++it) {
+        unsigned int v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+        if (v >= target) return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+
+}  // namespace xyl

@@ -1,0 +1,44 @@
+// Launchers of the device engines (host side), shared by the API layer.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace xyl {
+
+enum Layout : int { kReplicaMajor = 0, kInterleaved = 1 };
+
+struct PlanShape {
+    int n_samples = 0;
+    int max_R = 0;
+    int max_Q = 0;
+    int max_class = 0;
+    int max_N = 0;
+    int layout = kReplicaMajor;
+    bool fp64 = false;
+};
+
+// Batched-engine launch shape chosen by the tuner.
+struct BatchedShape {
+    int G = 1;        // CTAs per cluster (one team per replica group)
+    int Rg = 1;       // replicas per group (power of two, divides every R)
+    int block = 512;  // threads per CTA
+};
+
+cudaError_t launch_init(const DevPlan &P, const PlanShape &S, int aligned, cudaStream_t st);
+cudaError_t launch_finalize(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every, int advance,
+                            int obs_buf_from_sweep, cudaStream_t st);
+cudaError_t launch_recompute(const DevPlan &P, const PlanShape &S, int renormalise, int obs_buf_from_sweep,
+                             cudaStream_t st);
+cudaError_t launch_plain_sweep(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every,
+                               cudaStream_t st, int64_t *launches);
+
+// Batched engine: one launch per wave of samples; `units` lists (sample, group) per cluster.
+cudaError_t launch_batched(const DevPlan &P, const PlanShape &S, const BatchedShape &B, const int2 *d_units,
+                           int unit_begin, int unit_count, int n_sweeps, uint32_t ops, int measure_every,
+                           cudaStream_t st);
+cudaError_t batched_max_active_clusters(const PlanShape &S, const BatchedShape &B, int *clusters);
+size_t batched_smem_bytes(const PlanShape &S, const BatchedShape &B);
+
+}  // namespace xyl

@@ -1,0 +1,146 @@
+// Plain engine: one launch per colour phase, one thread per (site, replica),
+// replica-major spins ([sample][replica][site]).  This is the straightforward
+// GPU form of the colour-sequential sweep of App. B ("generalised red-black
+// Gauss-Seidel"): sites of one colour are mutually unlinked and update
+// together; colours run one after another.  Instantiated in FP64 (the
+// reference GPU kernel) and FP32.
+#include <cuda_runtime.h>
+
+#include "engines.h"
+
+namespace xyl {
+namespace {
+
+constexpr int kPlainBlock = 256;
+
+template <typename Real>
+__device__ __forceinline__ Vec2<Real> make_vec2(Real x, Real y);
+template <> __device__ __forceinline__ float2 make_vec2<float>(float x, float y) { return make_float2(x, y); }
+template <> __device__ __forceinline__ double2 make_vec2<double>(double x, double y) { return make_double2(x, y); }
+
+// One colour phase of the Metropolis (IS_MET) or overrelaxation pass.  With
+// FUSE the replica's energy (links to lower colours, counted at their upper
+// endpoint), magnetisation and Fourier sums are reduced into obs[0].
+template <typename Real, bool IS_MET, bool FUSE>
+__global__ void __launch_bounds__(kPlainBlock) plain_phase_kernel(DevPlan P, int c)
+{
+    using V = Vec2<Real>;
+    using V4 = Vec4<Real>;
+    const int s = blockIdx.z, r = blockIdx.y;
+    const DevSample d = P.samples[s];
+    if (r >= d.R || c >= d.Q) return;
+    const int cb = P.color_ptr[d.color_off + c], ce = P.color_ptr[d.color_off + c + 1];
+    const int base = cb + (int)blockIdx.x * kPlainBlock;
+    if (base >= ce) return;
+    const int i = base + (int)threadIdx.x;
+    const bool active = i < ce;
+    V *sp = reinterpret_cast<V *>(P.spins) + d.spin_off + (int64_t)r * d.N;
+    const int32_t *rp = P.row_ptr + d.row_off;
+    const int32_t *cl = P.col + d.col_off;
+    const int slot = P.slot_of[d.rep_off + r];
+
+    Real nx = 0, ny = 0, lx = 0, ly = 0;
+    bool accepted = false;
+    if (active) {
+        const V si = sp[i];
+        Real hx = 0, hy = 0;
+        const int rb = rp[i], re = rp[i + 1];
+        for (int k = rb; k < re; ++k) {
+            const int j = cl[k];
+            const V sj = sp[j];
+            hx += sj.x;
+            hy += sj.y;
+            if (FUSE && j < cb) {
+                lx += sj.x;
+                ly += sj.y;
+            }
+        }
+        if (IS_MET) {
+            const Words4 x = philox_draw((uint32_t)P.perm[d.site_off + i], P.sweep[s], kPurposeMet, (uint32_t)r,
+                                         d.sample_id, P.key);
+            accepted = metropolis_step(si.x, si.y, hx, hy, (Real)P.beta[d.rep_off + slot],
+                                       (Real)P.delta[d.rep_off + slot], x, nx, ny);
+            if (accepted) {
+                sp[i] = make_vec2<Real>(nx, ny);
+            } else {
+                nx = si.x;
+                ny = si.y;
+            }
+        } else {
+            overrelax_step(si.x, si.y, hx, hy, nx, ny);
+            sp[i] = make_vec2<Real>(nx, ny);
+        }
+    }
+    if (IS_MET) {
+        const unsigned int votes = __ballot_sync(0xffffffffu, accepted);
+        if ((threadIdx.x & 31) == 0 && votes)
+            atomicAdd(&P.met_acc[d.rep_off + slot], (unsigned long long)__popc(votes));
+    }
+    if (FUSE) {
+        __shared__ double part[kPlainBlock / 32][kObsCount];
+        V4 ph = {0, 0, 0, 0};
+        if (active) ph = reinterpret_cast<const V4 *>(P.phase)[d.site_off + i];
+        Real v[kObsCount];
+        v[kObsE] = active ? -(nx * lx + ny * ly) : (Real)0;
+        v[kObsMx] = nx;
+        v[kObsMy] = ny;
+        v[kObsF1xRe] = nx * ph.x; v[kObsF1xIm] = nx * ph.y;
+        v[kObsF1yRe] = ny * ph.x; v[kObsF1yIm] = ny * ph.y;
+        v[kObsF2xRe] = nx * ph.z; v[kObsF2xIm] = nx * ph.w;
+        v[kObsF2yRe] = ny * ph.z; v[kObsF2yIm] = ny * ph.w;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int f = 0; f < kObsCount; ++f) {
+            const Real w = warp_sum(v[f]);
+            if (lane == 0) part[warp][f] = (double)w;
+        }
+        __syncthreads();
+        if (threadIdx.x < kObsCount) {
+            double total = 0.0;
+#pragma unroll
+            for (int w = 0; w < kPlainBlock / 32; ++w) total += part[w][threadIdx.x];
+            atomicAdd(&P.obs[(size_t)(d.rep_off + r) * kObsStride + threadIdx.x], total);
+        }
+    }
+}
+
+template <typename Real>
+cudaError_t sweep_impl(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every, cudaStream_t st,
+                       int64_t *launches)
+{
+    dim3 grid((S.max_class + kPlainBlock - 1) / kPlainBlock, S.max_R, S.n_samples);
+    const bool met = ops & XYL_OP_MET, orx = ops & XYL_OP_OR;
+    int64_t n = 0;
+    if (met) {
+        for (int c = 0; c < S.max_Q; ++c) {
+            if (orx)
+                plain_phase_kernel<Real, true, false><<<grid, kPlainBlock, 0, st>>>(P, c);
+            else
+                plain_phase_kernel<Real, true, true><<<grid, kPlainBlock, 0, st>>>(P, c);
+            ++n;
+        }
+    }
+    if (orx) {
+        for (int c = 0; c < S.max_Q; ++c) {
+            plain_phase_kernel<Real, false, true><<<grid, kPlainBlock, 0, st>>>(P, c);
+            ++n;
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_finalize(P, S, ops, measure_every, 1, 0, st);
+    ++n;
+    if (launches) *launches += n;
+    return e;
+}
+
+}  // namespace
+
+cudaError_t launch_plain_sweep(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every,
+                               cudaStream_t st, int64_t *launches)
+{
+    return S.fp64 ? sweep_impl<double>(P, S, ops, measure_every, st, launches)
+                  : sweep_impl<float>(P, S, ops, measure_every, st, launches);
+}
+
+}  // namespace xyl

@@ -1,0 +1,774 @@
+// C ABI of libxyl: plans, workspace layout, bind, sweeps (captured into CUDA
+// graphs), standalone PT / measurement / recompute, read-back and checkpoint.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "engines.h"
+#include "internal.h"
+
+using namespace xyl;
+
+namespace {
+
+struct HostSample {
+    int32_t N = 0, Q = 0, R = 0, L = 0, max_deg = 0;
+    uint32_t sample_id = 0;
+    std::vector<double> beta, delta;
+    std::vector<int32_t> perm, row_ptr, col, color_ptr, xy;
+};
+
+struct Region {
+    size_t off = 0, bytes = 0;
+};
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+const int kGraphChunk = 32;  // sweeps per captured graph of the plain engine
+
+}  // namespace
+
+struct xyl_plan {
+    int engine = 0;
+    uint64_t seed = 0;
+    std::vector<HostSample> hs;
+    PlanShape shape;
+    BatchedShape bshape;
+    int recompute_every = 0;
+    int64_t sweeps_since_recompute = 0;
+    int total_R = 0;
+    int64_t total_N = 0, total_nnz = 0, total_spins = 0;
+    int total_Q1 = 0;
+    std::vector<int2> units;
+    int wave_units = 0;
+    size_t ws_bytes = 0;
+    char *ws = nullptr;
+    bool bound = false;
+    DevPlan dev{};
+    Region r_samples, r_row_ptr, r_col, r_perm, r_color_ptr, r_phase, r_spins, r_beta, r_delta, r_slot_of, r_rep_at,
+        r_obs, r_last_E, r_acc, r_met_acc, r_met_try, r_pt_acc, r_pt_try, r_sweep, r_status, r_barrier, r_drift,
+        r_units;
+    cudaStream_t capture_stream = nullptr;
+    std::map<std::tuple<int, uint32_t, int>, cudaGraphExec_t> graphs;
+    int64_t last_launches = 0;
+    int64_t launches_per_graph_plain = 0;
+
+    size_t spin_elem() const { return shape.fp64 ? sizeof(double2) : sizeof(float2); }
+
+    void drop_graphs()
+    {
+        for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+        graphs.clear();
+    }
+    ~xyl_plan()
+    {
+        drop_graphs();
+        if (capture_stream) cudaStreamDestroy(capture_stream);
+    }
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(XYL_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define XYL_CUDA(call, what)                          \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+void layout(xyl_plan *p)
+{
+    size_t off = 0;
+    auto take = [&](Region &r, size_t bytes) {
+        r.off = off;
+        r.bytes = bytes;
+        off = align_up(off + std::max<size_t>(bytes, 1));
+    };
+    const size_t S = p->hs.size();
+    take(p->r_samples, S * sizeof(DevSample));
+    take(p->r_row_ptr, (p->total_N + S) * sizeof(int32_t));
+    take(p->r_col, p->total_nnz * sizeof(int32_t));
+    take(p->r_perm, p->total_N * sizeof(int32_t));
+    take(p->r_color_ptr, p->total_Q1 * sizeof(int32_t));
+    take(p->r_phase, p->total_N * (p->shape.fp64 ? sizeof(double4_32a) : sizeof(float4)));
+    take(p->r_spins, p->total_spins * p->spin_elem());
+    take(p->r_beta, p->total_R * sizeof(double));
+    take(p->r_delta, p->total_R * sizeof(double));
+    take(p->r_slot_of, p->total_R * sizeof(int32_t));
+    take(p->r_rep_at, p->total_R * sizeof(int32_t));
+    take(p->r_obs, 2 * (size_t)p->total_R * kObsStride * sizeof(double));
+    take(p->r_last_E, p->total_R * sizeof(double));
+    take(p->r_acc, (size_t)p->total_R * kAccCount * sizeof(double));
+    take(p->r_met_acc, p->total_R * sizeof(unsigned long long));
+    take(p->r_met_try, p->total_R * sizeof(unsigned long long));
+    take(p->r_pt_acc, p->total_R * sizeof(unsigned long long));
+    take(p->r_pt_try, p->total_R * sizeof(unsigned long long));
+    take(p->r_sweep, S * sizeof(uint32_t));
+    take(p->r_status, sizeof(int32_t));
+    take(p->r_barrier, S * sizeof(unsigned int));
+    take(p->r_drift, sizeof(double));
+    take(p->r_units, std::max<size_t>(p->units.size(), 1) * sizeof(int2));
+    p->ws_bytes = off;
+}
+
+template <typename T>
+T *at(xyl_plan *p, const Region &r)
+{
+    return reinterpret_cast<T *>(p->ws + r.off);
+}
+
+int check_bound(xyl_plan *p, const char *who)
+{
+    if (!p) return fail(XYL_EINVAL, "%s: NULL plan", who);
+    if (!p->bound) return fail(XYL_ESTATE, "%s: plan is not bound to a workspace", who);
+    return XYL_OK;
+}
+
+int pick_batched_shape(xyl_plan *p, const xyl_tuning *tune)
+{
+    // replicas per cluster: largest power of two <= 32 dividing every sample's R
+    int g = 32;
+    for (auto &h : p->hs)
+        while (g > 1 && h.R % g) g >>= 1;
+    if (tune && tune->group > 0) {
+        const int want = tune->group;
+        if (want > 32 || (want & (want - 1))) return fail(XYL_EINVAL, "group=%d must be a power of two <= 32", want);
+        for (auto &h : p->hs)
+            if (h.R % want) return fail(XYL_EINVAL, "group=%d does not divide n_temps=%d", want, h.R);
+        g = want;
+    }
+    int max_N = 0;
+    for (auto &h : p->hs) max_N = std::max(max_N, h.N);
+    // default cluster width: enough CTAs that a phase has a few thousand items per CTA
+    int G = 1;
+    const double items_per_phase = (double)max_N * g / std::max(1, p->shape.max_Q);
+    while (G < 16 && items_per_phase / (G * 2) >= 1024.0) G *= 2;
+    int block = 512;
+    if (tune && tune->cluster > 0) {
+        if (tune->cluster > 16) return fail(XYL_EINVAL, "cluster=%d exceeds 16", tune->cluster);
+        G = tune->cluster;
+    }
+    if (tune && tune->block > 0) {
+        if (tune->block % 32 || tune->block > 1024) return fail(XYL_EINVAL, "block=%d must be a multiple of 32 <= 1024", tune->block);
+        block = tune->block;
+    }
+    p->bshape.G = G;
+    p->bshape.Rg = g;
+    p->bshape.block = block;
+    p->units.clear();
+    for (size_t s = 0; s < p->hs.size(); ++s)
+        for (int k = 0; k < p->hs[s].R / g; ++k) p->units.push_back(make_int2((int)s, k));
+    return XYL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int xyl_plan_create(const xyl_sample *samples, int32_t n_samples, int32_t engine, uint64_t seed,
+                    const xyl_tuning *tune, xyl_plan **out, size_t *workspace_bytes)
+{
+    clear_error();
+    if (!out) return fail(XYL_EINVAL, "xyl_plan_create: out is NULL");
+    *out = nullptr;
+    if (!samples || n_samples < 1) return fail(XYL_EINVAL, "xyl_plan_create: empty batch");
+    if (engine != XYL_FP64_PLAIN && engine != XYL_FP32_BATCHED && engine != XYL_FP32_PLAIN)
+        return fail(XYL_EINVAL, "xyl_plan_create: unknown engine %d", engine);
+    auto *p = new xyl_plan();
+    p->engine = engine;
+    p->seed = seed;
+    p->shape.fp64 = (engine == XYL_FP64_PLAIN);
+    p->shape.layout = (engine == XYL_FP32_BATCHED) ? kInterleaved : kReplicaMajor;
+    p->recompute_every = tune ? std::max(0, tune->recompute_every) : 0;
+    for (int s = 0; s < n_samples; ++s) {
+        const xyl_sample &in = samples[s];
+        const xyl_graph *g = in.graph;
+        if (!g || in.n_temps < 1 || !in.beta || !in.delta) {
+            delete p;
+            return fail(XYL_EINVAL, "xyl_plan_create: sample %d has no graph, slots or temperatures", s);
+        }
+        if (engine == XYL_FP32_BATCHED && in.n_temps > 256) {
+            delete p;
+            return fail(XYL_EINVAL, "xyl_plan_create: batched engine supports at most 256 slots per sample");
+        }
+        HostSample h;
+        h.N = g->n; h.Q = g->n_colors; h.R = in.n_temps; h.L = g->L; h.max_deg = g->max_deg;
+        h.sample_id = in.sample_id;
+        h.beta.assign(in.beta, in.beta + in.n_temps);
+        h.delta.assign(in.delta, in.delta + in.n_temps);
+        for (int k = 0; k < in.n_temps; ++k) {
+            if (!std::isfinite(h.beta[k]) || h.beta[k] < 0 || !std::isfinite(h.delta[k]) || h.delta[k] < 0) {
+                delete p;
+                return fail(XYL_EINVAL, "xyl_plan_create: sample %d slot %d has a bad beta/delta", s, k);
+            }
+        }
+        h.perm = g->perm; h.row_ptr = g->row_ptr; h.col = g->col; h.color_ptr = g->color_ptr; h.xy = g->xy;
+        p->total_R += h.R;
+        p->total_N += h.N;
+        p->total_nnz += (int64_t)h.col.size();
+        p->total_spins += (int64_t)h.N * h.R;
+        p->total_Q1 += h.Q + 1;
+        p->shape.max_R = std::max(p->shape.max_R, h.R);
+        p->shape.max_Q = std::max(p->shape.max_Q, h.Q);
+        p->shape.max_N = std::max(p->shape.max_N, h.N);
+        for (int c = 0; c < h.Q; ++c)
+            p->shape.max_class = std::max(p->shape.max_class, h.color_ptr[c + 1] - h.color_ptr[c]);
+        p->hs.push_back(std::move(h));
+    }
+    p->shape.n_samples = n_samples;
+    if (engine == XYL_FP32_BATCHED) {
+        const int rc = pick_batched_shape(p, tune);
+        if (rc) { delete p; return rc; }
+    }
+    layout(p);
+    if (workspace_bytes) *workspace_bytes = p->ws_bytes;
+    *out = p;
+    return XYL_OK;
+}
+
+int xyl_bind(xyl_plan *p, void *d_workspace, size_t bytes, void *stream)
+{
+    clear_error();
+    if (!p || !d_workspace) return fail(XYL_EINVAL, "xyl_bind: NULL plan or workspace");
+    if (bytes < p->ws_bytes) return fail(XYL_ENOSPC, "xyl_bind: workspace %zu B < required %zu B", bytes, p->ws_bytes);
+    if (reinterpret_cast<uintptr_t>(d_workspace) % kAlign) return fail(XYL_EINVAL, "xyl_bind: workspace not 256-byte aligned");
+    cudaStream_t st = as_stream(stream);
+    p->drop_graphs();
+    p->ws = static_cast<char *>(d_workspace);
+    // host images of the constant tables
+    const size_t S = p->hs.size();
+    std::vector<DevSample> ds(S);
+    std::vector<int32_t> row_ptr, col, perm, color_ptr;
+    row_ptr.reserve(p->total_N + S); col.reserve(p->total_nnz); perm.reserve(p->total_N); color_ptr.reserve(p->total_Q1);
+    std::vector<float4> ph32;
+    std::vector<double4_32a> ph64;
+    std::vector<double> beta, delta;
+    int64_t site_off = 0, row_off = 0, col_off = 0, spin_off = 0;
+    int color_off = 0, rep_off = 0;
+    for (size_t s = 0; s < S; ++s) {
+        const HostSample &h = p->hs[s];
+        DevSample &d = ds[s];
+        d.N = h.N; d.Q = h.Q; d.R = h.R; d.L = h.L; d.sample_id = h.sample_id; d.max_deg = h.max_deg;
+        d.color_off = color_off; d.rep_off = rep_off; d.site_off = site_off; d.row_off = row_off;
+        d.col_off = col_off; d.spin_off = spin_off;
+        row_ptr.insert(row_ptr.end(), h.row_ptr.begin(), h.row_ptr.end());
+        col.insert(col.end(), h.col.begin(), h.col.end());
+        perm.insert(perm.end(), h.perm.begin(), h.perm.end());
+        color_ptr.insert(color_ptr.end(), h.color_ptr.begin(), h.color_ptr.end());
+        for (int i = 0; i < h.N; ++i) {
+            const int v = h.perm[i];
+            const double ax = 2.0 * M_PI * (double)h.xy[2 * v] / (double)h.L;
+            const double ay = 2.0 * M_PI * (double)h.xy[2 * v + 1] / (double)h.L;
+            if (p->shape.fp64)
+                ph64.push_back(make_double4_32a(std::cos(ax), std::sin(ax), std::cos(ay), std::sin(ay)));
+            else
+                ph32.push_back(make_float4((float)std::cos(ax), (float)std::sin(ax), (float)std::cos(ay), (float)std::sin(ay)));
+        }
+        beta.insert(beta.end(), h.beta.begin(), h.beta.end());
+        delta.insert(delta.end(), h.delta.begin(), h.delta.end());
+        site_off += h.N; row_off += h.N + 1; col_off += (int64_t)h.col.size(); spin_off += (int64_t)h.N * h.R;
+        color_off += h.Q + 1; rep_off += h.R;
+    }
+    auto up = [&](const Region &r, const void *src, size_t n) -> cudaError_t {
+        if (!n) return cudaSuccess;
+        return cudaMemcpyAsync(p->ws + r.off, src, n, cudaMemcpyHostToDevice, st);
+    };
+    XYL_CUDA(up(p->r_samples, ds.data(), ds.size() * sizeof(DevSample)), "xyl_bind: upload");
+    XYL_CUDA(up(p->r_row_ptr, row_ptr.data(), row_ptr.size() * 4), "xyl_bind: upload");
+    XYL_CUDA(up(p->r_col, col.data(), col.size() * 4), "xyl_bind: upload");
+    XYL_CUDA(up(p->r_perm, perm.data(), perm.size() * 4), "xyl_bind: upload");
+    XYL_CUDA(up(p->r_color_ptr, color_ptr.data(), color_ptr.size() * 4), "xyl_bind: upload");
+    if (p->shape.fp64)
+        XYL_CUDA(up(p->r_phase, ph64.data(), ph64.size() * sizeof(double4_32a)), "xyl_bind: upload");
+    else
+        XYL_CUDA(up(p->r_phase, ph32.data(), ph32.size() * sizeof(float4)), "xyl_bind: upload");
+    XYL_CUDA(up(p->r_beta, beta.data(), beta.size() * 8), "xyl_bind: upload");
+    XYL_CUDA(up(p->r_delta, delta.data(), delta.size() * 8), "xyl_bind: upload");
+    if (!p->units.empty()) XYL_CUDA(up(p->r_units, p->units.data(), p->units.size() * sizeof(int2)), "xyl_bind: upload");
+    // everything mutable starts zeroed
+    const Region *zero[] = {&p->r_spins, &p->r_slot_of, &p->r_rep_at, &p->r_obs, &p->r_last_E, &p->r_acc,
+                            &p->r_met_acc, &p->r_met_try, &p->r_pt_acc, &p->r_pt_try, &p->r_sweep, &p->r_status,
+                            &p->r_barrier, &p->r_drift};
+    for (const Region *r : zero) XYL_CUDA(cudaMemsetAsync(p->ws + r->off, 0, r->bytes, st), "xyl_bind: memset");
+    DevPlan &P = p->dev;
+    P.samples = at<DevSample>(p, p->r_samples);
+    P.n_samples = (int32_t)S;
+    P.total_R = p->total_R;
+    P.row_ptr = at<int32_t>(p, p->r_row_ptr);
+    P.col = at<int32_t>(p, p->r_col);
+    P.perm = at<int32_t>(p, p->r_perm);
+    P.color_ptr = at<int32_t>(p, p->r_color_ptr);
+    P.phase = p->ws + p->r_phase.off;
+    P.spins = p->ws + p->r_spins.off;
+    P.beta = at<double>(p, p->r_beta);
+    P.delta = at<double>(p, p->r_delta);
+    P.slot_of = at<int32_t>(p, p->r_slot_of);
+    P.rep_at = at<int32_t>(p, p->r_rep_at);
+    P.obs = at<double>(p, p->r_obs);
+    P.last_E = at<double>(p, p->r_last_E);
+    P.acc = at<double>(p, p->r_acc);
+    P.met_acc = at<unsigned long long>(p, p->r_met_acc);
+    P.met_try = at<unsigned long long>(p, p->r_met_try);
+    P.pt_acc = at<unsigned long long>(p, p->r_pt_acc);
+    P.pt_try = at<unsigned long long>(p, p->r_pt_try);
+    P.sweep = at<uint32_t>(p, p->r_sweep);
+    P.status = at<int32_t>(p, p->r_status);
+    P.barrier = at<unsigned int>(p, p->r_barrier);
+    P.drift = at<double>(p, p->r_drift);
+    P.key = p->seed;
+    if (!p->capture_stream) XYL_CUDA(cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking), "xyl_bind: stream");
+    if (p->engine == XYL_FP32_BATCHED) {
+        int clusters = 0;
+        XYL_CUDA(batched_max_active_clusters(p->shape, p->bshape, &clusters), "xyl_bind: occupancy");
+        if (clusters < 1)
+            return fail(XYL_EINVAL, "xyl_bind: a cluster of %d CTAs x %d threads cannot be resident", p->bshape.G,
+                        p->bshape.block);
+        const int n_groups = p->hs[0].R / p->bshape.Rg;
+        bool uniform_groups = true;
+        for (auto &h : p->hs) uniform_groups &= (h.R / p->bshape.Rg == n_groups);
+        int groups_max = 1;
+        for (auto &h : p->hs) groups_max = std::max(groups_max, h.R / p->bshape.Rg);
+        if (groups_max > 1) {
+            if (!uniform_groups)
+                return fail(XYL_EINVAL, "xyl_bind: batched engine with several groups needs equal n_temps");
+            const int samples_per_wave = clusters / n_groups;
+            if (samples_per_wave < 1)
+                return fail(XYL_EINVAL, "xyl_bind: %d clusters of %d CTAs cannot be co-resident (max %d)", n_groups,
+                            p->bshape.G, clusters);
+            p->wave_units = samples_per_wave * n_groups;
+        } else {
+            p->wave_units = (int)p->units.size();
+        }
+    }
+    XYL_CUDA(cudaStreamSynchronize(st), "xyl_bind: sync");
+    p->bound = true;
+    return XYL_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int buffer_mode(const xyl_plan *p) { return p->engine == XYL_FP32_BATCHED ? 1 : 0; }
+
+int zero_region(xyl_plan *p, const Region &r, cudaStream_t st)
+{
+    XYL_CUDA(cudaMemsetAsync(p->ws + r.off, 0, r.bytes, st), "memset");
+    return XYL_OK;
+}
+
+// Enqueue the work of `n` sweeps (no graph).
+int issue_sweeps(xyl_plan *p, int n, uint32_t ops, int measure_every, cudaStream_t st, int64_t *launches)
+{
+    if (p->engine == XYL_FP32_BATCHED) {
+        XYL_CUDA(cudaMemsetAsync(p->ws + p->r_barrier.off, 0, p->r_barrier.bytes, st), "sweep: barrier reset");
+        const int total = (int)p->units.size();
+        for (int u = 0; u < total; u += p->wave_units) {
+            const int cnt = std::min(p->wave_units, total - u);
+            XYL_CUDA(launch_batched(p->dev, p->shape, p->bshape, at<int2>(p, p->r_units), u, cnt, n, ops, measure_every, st),
+                     "sweep: batched launch");
+            ++*launches;
+        }
+        return XYL_OK;
+    }
+    for (int k = 0; k < n; ++k)
+        XYL_CUDA(launch_plain_sweep(p->dev, p->shape, ops, measure_every, st, launches), "sweep: plain launch");
+    return XYL_OK;
+}
+
+int run_captured(xyl_plan *p, int n, uint32_t ops, int measure_every, cudaStream_t st)
+{
+    const auto key = std::make_tuple(n, ops, measure_every);
+    auto it = p->graphs.find(key);
+    int64_t launches = 0;
+    if (it == p->graphs.end()) {
+        XYL_CUDA(cudaStreamBeginCapture(p->capture_stream, cudaStreamCaptureModeThreadLocal), "sweep: begin capture");
+        const int rc = issue_sweeps(p, n, ops, measure_every, p->capture_stream, &launches);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(p->capture_stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (ec != cudaSuccess) return cuda_fail(ec, "sweep: end capture");
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) return cuda_fail(ei, "sweep: instantiate");
+        it = p->graphs.emplace(key, exec).first;
+        p->launches_per_graph_plain = launches;
+    }
+    XYL_CUDA(cudaGraphLaunch(it->second, st), "sweep: graph launch");
+    return XYL_OK;
+}
+
+int64_t launches_of(xyl_plan *p, int n, uint32_t ops)
+{
+    if (p->engine == XYL_FP32_BATCHED)
+        return ((int64_t)p->units.size() + p->wave_units - 1) / p->wave_units;
+    const int64_t per_sweep = (int64_t)(((ops & XYL_OP_MET) ? p->shape.max_Q : 0) +
+                                        ((ops & XYL_OP_OR) ? p->shape.max_Q : 0) + 1);
+    return per_sweep * n;
+}
+
+int do_recompute(xyl_plan *p, int renormalise, cudaStream_t st)
+{
+    XYL_CUDA(launch_recompute(p->dev, p->shape, renormalise, buffer_mode(p), st), "recompute");
+    return zero_region(p, p->r_obs, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int xyl_init_spins(xyl_plan *p, int32_t aligned, void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_init_spins");
+    if (rc) return rc;
+    cudaStream_t st = as_stream(stream);
+    const Region *zero[] = {&p->r_obs, &p->r_last_E, &p->r_acc, &p->r_met_acc, &p->r_met_try, &p->r_pt_acc,
+                            &p->r_pt_try, &p->r_status, &p->r_barrier};
+    for (const Region *r : zero)
+        if ((rc = zero_region(p, *r, st))) return rc;
+    XYL_CUDA(launch_init(p->dev, p->shape, aligned, st), "xyl_init_spins: launch");
+    if ((rc = do_recompute(p, 0, st))) return rc;
+    if ((rc = zero_region(p, p->r_drift, st))) return rc;
+    p->sweeps_since_recompute = 0;
+    return XYL_OK;
+}
+
+int xyl_sweep(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_every, void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_sweep");
+    if (rc) return rc;
+    if (n_sweeps < 0) return fail(XYL_EINVAL, "xyl_sweep: n_sweeps < 0");
+    if (!(ops & (XYL_OP_MET | XYL_OP_OR))) return fail(XYL_EINVAL, "xyl_sweep: ops must include MET or OR");
+    if (ops & ~(XYL_OP_MET | XYL_OP_OR | XYL_OP_PT | XYL_OP_MEASURE)) return fail(XYL_EINVAL, "xyl_sweep: unknown op bits");
+    if ((ops & XYL_OP_MEASURE) && measure_every < 1) return fail(XYL_EINVAL, "xyl_sweep: measure_every must be >= 1");
+    if (!(ops & XYL_OP_MEASURE)) measure_every = 1;
+    cudaStream_t st = as_stream(stream);
+    p->last_launches = 0;
+    int left = n_sweeps;
+    while (left > 0) {
+        int n = left;
+        if (p->recompute_every > 0) n = (int)std::min<int64_t>(n, p->recompute_every - p->sweeps_since_recompute);
+        int chunk = n;
+        if (p->engine != XYL_FP32_BATCHED) chunk = std::min(n, kGraphChunk);
+        if ((rc = run_captured(p, chunk, ops, measure_every, st))) return rc;
+        p->last_launches += launches_of(p, chunk, ops);
+        left -= chunk;
+        p->sweeps_since_recompute += chunk;
+        if (p->recompute_every > 0 && p->sweeps_since_recompute >= p->recompute_every) {
+            if ((rc = do_recompute(p, 1, st))) return rc;
+            p->last_launches += 1;
+            p->sweeps_since_recompute = 0;
+        }
+    }
+    return XYL_OK;
+}
+
+int xyl_sweep_units(xyl_plan *p, int32_t first_unit, int32_t n_units, int32_t n_sweeps, uint32_t ops,
+                    int32_t measure_every, void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_sweep_units");
+    if (rc) return rc;
+    if (p->engine != XYL_FP32_BATCHED) return fail(XYL_EINVAL, "xyl_sweep_units: batched engine only");
+    const int total = (int)p->units.size();
+    if (first_unit < 0 || n_units < 1 || first_unit + n_units > total || n_sweeps < 0)
+        return fail(XYL_EINVAL, "xyl_sweep_units: bad unit range [%d, %d) of %d", first_unit, first_unit + n_units, total);
+    if (!(ops & (XYL_OP_MET | XYL_OP_OR))) return fail(XYL_EINVAL, "xyl_sweep_units: ops must include MET or OR");
+    if ((ops & XYL_OP_MEASURE) && measure_every < 1) return fail(XYL_EINVAL, "xyl_sweep_units: measure_every must be >= 1");
+    if (!(ops & XYL_OP_MEASURE)) measure_every = 1;
+    cudaStream_t st = as_stream(stream);
+    XYL_CUDA(cudaMemsetAsync(p->ws + p->r_barrier.off, 0, p->r_barrier.bytes, st), "xyl_sweep_units: barrier reset");
+    p->last_launches = 0;
+    for (int u = first_unit; u < first_unit + n_units; u += p->wave_units) {
+        const int cnt = std::min(p->wave_units, first_unit + n_units - u);
+        XYL_CUDA(launch_batched(p->dev, p->shape, p->bshape, at<int2>(p, p->r_units), u, cnt, n_sweeps, ops,
+                                measure_every, st), "xyl_sweep_units: launch");
+        ++p->last_launches;
+    }
+    return XYL_OK;
+}
+
+int32_t xyl_unit_count(const xyl_plan *p)
+{
+    return (p && p->engine == XYL_FP32_BATCHED) ? (int32_t)p->units.size() : 0;
+}
+
+int xyl_pt_swap(xyl_plan *p, void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_pt_swap");
+    if (rc) return rc;
+    cudaStream_t st = as_stream(stream);
+    XYL_CUDA(launch_recompute(p->dev, p->shape, 0, buffer_mode(p), st), "xyl_pt_swap: recompute");
+    XYL_CUDA(launch_finalize(p->dev, p->shape, XYL_OP_PT, 1, 0, buffer_mode(p), st), "xyl_pt_swap: finalize");
+    return XYL_OK;
+}
+
+int xyl_measure(xyl_plan *p, void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_measure");
+    if (rc) return rc;
+    cudaStream_t st = as_stream(stream);
+    XYL_CUDA(launch_recompute(p->dev, p->shape, 0, buffer_mode(p), st), "xyl_measure: recompute");
+    XYL_CUDA(launch_finalize(p->dev, p->shape, XYL_OP_MEASURE, 1, 0, buffer_mode(p), st), "xyl_measure: finalize");
+    return XYL_OK;
+}
+
+int xyl_recompute(xyl_plan *p, void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_recompute");
+    if (rc) return rc;
+    return do_recompute(p, 1, as_stream(stream));
+}
+
+int xyl_set_delta(xyl_plan *p, int32_t sample, const double *delta, void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_set_delta");
+    if (rc) return rc;
+    if (sample < 0 || sample >= (int)p->hs.size() || !delta) return fail(XYL_EINVAL, "xyl_set_delta: bad sample");
+    HostSample &h = p->hs[sample];
+    int rep_off = 0;
+    for (int s = 0; s < sample; ++s) rep_off += p->hs[s].R;
+    for (int k = 0; k < h.R; ++k) {
+        if (!std::isfinite(delta[k]) || delta[k] < 0) return fail(XYL_EINVAL, "xyl_set_delta: bad delta");
+        h.delta[k] = delta[k];
+    }
+    cudaStream_t st = as_stream(stream);
+    XYL_CUDA(cudaMemcpyAsync(p->ws + p->r_delta.off + rep_off * sizeof(double), h.delta.data(), h.R * sizeof(double),
+                             cudaMemcpyHostToDevice, st), "xyl_set_delta: copy");
+    XYL_CUDA(cudaStreamSynchronize(st), "xyl_set_delta: sync");
+    // graphs hold kernel arguments only (pointers), so they stay valid
+    return XYL_OK;
+}
+
+static int read_region(xyl_plan *p, const Region &r, void *dst, cudaStream_t st)
+{
+    if (!dst) return XYL_OK;
+    XYL_CUDA(cudaMemcpyAsync(dst, p->ws + r.off, r.bytes, cudaMemcpyDeviceToHost, st), "read");
+    return XYL_OK;
+}
+
+static int finish_read(xyl_plan *p, cudaStream_t st)
+{
+    XYL_CUDA(cudaStreamSynchronize(st), "read: sync");
+    int32_t status = 0;
+    XYL_CUDA(cudaMemcpy(&status, p->ws + p->r_status.off, sizeof(status), cudaMemcpyDeviceToHost), "read: status");
+    if (status) return fail(status, "device status word is %d", status);
+    return XYL_OK;
+}
+
+int xyl_read_observables(xyl_plan *p, double *acc, uint64_t *met_acc, uint64_t *met_try, uint64_t *pt_acc,
+                         uint64_t *pt_try, void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_read_observables");
+    if (rc) return rc;
+    cudaStream_t st = as_stream(stream);
+    if ((rc = read_region(p, p->r_acc, acc, st))) return rc;
+    if ((rc = read_region(p, p->r_met_acc, met_acc, st))) return rc;
+    if ((rc = read_region(p, p->r_met_try, met_try, st))) return rc;
+    if ((rc = read_region(p, p->r_pt_acc, pt_acc, st))) return rc;
+    if ((rc = read_region(p, p->r_pt_try, pt_try, st))) return rc;
+    return finish_read(p, st);
+}
+
+int xyl_reset_observables(xyl_plan *p, void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_reset_observables");
+    if (rc) return rc;
+    cudaStream_t st = as_stream(stream);
+    const Region *zero[] = {&p->r_acc, &p->r_met_acc, &p->r_met_try, &p->r_pt_acc, &p->r_pt_try};
+    for (const Region *r : zero)
+        if ((rc = zero_region(p, *r, st))) return rc;
+    return XYL_OK;
+}
+
+int xyl_read_energies(xyl_plan *p, double *E, void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_read_energies");
+    if (rc) return rc;
+    cudaStream_t st = as_stream(stream);
+    if ((rc = read_region(p, p->r_last_E, E, st))) return rc;
+    return finish_read(p, st);
+}
+
+int xyl_read_labels(xyl_plan *p, int32_t *replica_at_slot, void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_read_labels");
+    if (rc) return rc;
+    cudaStream_t st = as_stream(stream);
+    if ((rc = read_region(p, p->r_rep_at, replica_at_slot, st))) return rc;
+    return finish_read(p, st);
+}
+
+static int spin_copy(xyl_plan *p, int32_t sample, int32_t replica, double *out, const double *in, cudaStream_t st)
+{
+    if (sample < 0 || sample >= (int)p->hs.size()) return fail(XYL_EINVAL, "spins: bad sample %d", sample);
+    const HostSample &h = p->hs[sample];
+    if (replica < 0 || replica >= h.R) return fail(XYL_EINVAL, "spins: bad replica %d", replica);
+    int64_t spin_off = 0;
+    for (int s = 0; s < sample; ++s) spin_off += (int64_t)p->hs[s].N * p->hs[s].R;
+    const size_t elem = p->spin_elem();
+    char *base = p->ws + p->r_spins.off + spin_off * elem;
+    std::vector<char> buf((size_t)h.N * elem);
+    const bool inter = p->shape.layout == kInterleaved;
+    char *dev = inter ? base + (size_t)replica * elem : base + (size_t)replica * h.N * elem;
+    const size_t pitch = inter ? (size_t)h.R * elem : elem;
+    if (out) {
+        XYL_CUDA(cudaMemcpy2DAsync(buf.data(), elem, dev, pitch, elem, h.N, cudaMemcpyDeviceToHost, st), "spins: copy");
+        XYL_CUDA(cudaStreamSynchronize(st), "spins: sync");
+        for (int i = 0; i < h.N; ++i) {
+            const int v = h.perm[i];
+            if (p->shape.fp64) {
+                const double2 s = reinterpret_cast<const double2 *>(buf.data())[i];
+                out[2 * v] = s.x; out[2 * v + 1] = s.y;
+            } else {
+                const float2 s = reinterpret_cast<const float2 *>(buf.data())[i];
+                out[2 * v] = s.x; out[2 * v + 1] = s.y;
+            }
+        }
+        return finish_read(p, st);
+    }
+    for (int i = 0; i < h.N; ++i) {
+        const int v = h.perm[i];
+        if (p->shape.fp64)
+            reinterpret_cast<double2 *>(buf.data())[i] = make_double2(in[2 * v], in[2 * v + 1]);
+        else
+            reinterpret_cast<float2 *>(buf.data())[i] = make_float2((float)in[2 * v], (float)in[2 * v + 1]);
+    }
+    XYL_CUDA(cudaMemcpy2DAsync(dev, pitch, buf.data(), elem, elem, h.N, cudaMemcpyHostToDevice, st), "spins: copy");
+    XYL_CUDA(cudaStreamSynchronize(st), "spins: sync");
+    return XYL_OK;
+}
+
+int xyl_read_spins(xyl_plan *p, int32_t sample, int32_t replica, double *sxy, void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_read_spins");
+    if (rc) return rc;
+    if (!sxy) return fail(XYL_EINVAL, "xyl_read_spins: NULL output");
+    return spin_copy(p, sample, replica, sxy, nullptr, as_stream(stream));
+}
+
+int xyl_write_spins(xyl_plan *p, int32_t sample, int32_t replica, const double *sxy, void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_write_spins");
+    if (rc) return rc;
+    if (!sxy) return fail(XYL_EINVAL, "xyl_write_spins: NULL input");
+    cudaStream_t st = as_stream(stream);
+    if ((rc = spin_copy(p, sample, replica, nullptr, sxy, st))) return rc;
+    return do_recompute(p, 0, st);
+}
+
+int xyl_read_status(xyl_plan *p, int32_t *status, uint64_t *sweep_index, void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_read_status");
+    if (rc) return rc;
+    cudaStream_t st = as_stream(stream);
+    XYL_CUDA(cudaStreamSynchronize(st), "xyl_read_status: sync");
+    int32_t s = 0;
+    uint32_t t = 0;
+    XYL_CUDA(cudaMemcpy(&s, p->ws + p->r_status.off, sizeof(s), cudaMemcpyDeviceToHost), "xyl_read_status");
+    XYL_CUDA(cudaMemcpy(&t, p->ws + p->r_sweep.off, sizeof(t), cudaMemcpyDeviceToHost), "xyl_read_status");
+    if (status) *status = s;
+    if (sweep_index) *sweep_index = t;
+    return XYL_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+std::vector<const Region *> state_regions(xyl_plan *p)
+{
+    return {&p->r_spins, &p->r_slot_of, &p->r_rep_at, &p->r_sweep, &p->r_last_E, &p->r_acc,
+            &p->r_met_acc, &p->r_met_try, &p->r_pt_acc, &p->r_pt_try, &p->r_drift};
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t xyl_state_bytes(const xyl_plan *p)
+{
+    if (!p) return 0;
+    size_t n = 16;
+    for (const Region *r : state_regions(const_cast<xyl_plan *>(p))) n += r->bytes;
+    return n;
+}
+
+int xyl_export_state(xyl_plan *p, void *host, size_t bytes, void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_export_state");
+    if (rc) return rc;
+    if (!host || bytes < xyl_state_bytes(p)) return fail(XYL_ENOSPC, "xyl_export_state: buffer too small");
+    cudaStream_t st = as_stream(stream);
+    char *dst = static_cast<char *>(host);
+    const uint64_t magic = 0x584C5953544154ull, size = xyl_state_bytes(p);
+    std::memcpy(dst, &magic, 8);
+    std::memcpy(dst + 8, &size, 8);
+    size_t off = 16;
+    for (const Region *r : state_regions(p)) {
+        XYL_CUDA(cudaMemcpyAsync(dst + off, p->ws + r->off, r->bytes, cudaMemcpyDeviceToHost, st), "xyl_export_state");
+        off += r->bytes;
+    }
+    return finish_read(p, st);
+}
+
+int xyl_import_state(xyl_plan *p, const void *host, size_t bytes, void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_import_state");
+    if (rc) return rc;
+    if (!host || bytes < xyl_state_bytes(p)) return fail(XYL_EINVAL, "xyl_import_state: buffer too small");
+    const char *src = static_cast<const char *>(host);
+    uint64_t magic = 0, size = 0;
+    std::memcpy(&magic, src, 8);
+    std::memcpy(&size, src + 8, 8);
+    if (magic != 0x584C5953544154ull || size != xyl_state_bytes(p))
+        return fail(XYL_EINVAL, "xyl_import_state: not a checkpoint of this plan");
+    cudaStream_t st = as_stream(stream);
+    size_t off = 16;
+    for (const Region *r : state_regions(p)) {
+        XYL_CUDA(cudaMemcpyAsync(p->ws + r->off, src + off, r->bytes, cudaMemcpyHostToDevice, st), "xyl_import_state");
+        off += r->bytes;
+    }
+    XYL_CUDA(cudaMemsetAsync(p->ws + p->r_obs.off, 0, p->r_obs.bytes, st), "xyl_import_state");
+    XYL_CUDA(cudaMemsetAsync(p->ws + p->r_status.off, 0, p->r_status.bytes, st), "xyl_import_state");
+    XYL_CUDA(cudaStreamSynchronize(st), "xyl_import_state: sync");
+    return XYL_OK;
+}
+
+int64_t xyl_last_launch_count(const xyl_plan *p) { return p ? p->last_launches : 0; }
+
+void xyl_plan_free(xyl_plan *p) { delete p; }
+
+}  // extern "C"

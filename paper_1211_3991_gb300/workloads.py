@@ -1,0 +1,117 @@
+"""Synthetic workloads: graph sizes, decay exponents, temperature grids, seeds.
+
+Pure configuration (no method arithmetic), shared by the benchmark and the
+tests.  The paper measures on synthetic Levy graphs of its own ensemble only
+(Sec. IV: L = 16..384, 2^21 sweeps, measurements every 32 sweeps); these
+configurations keep its structure at the sizes the benchmark names:
+
+  C1  one graph, L=16, z=6, rho=3.5, one temperature T=1.0
+  C2  one graph, L=128, z=6, rho=3.5, 16 temperatures geometric in [0.8, 1.6], PT every sweep
+  C3  256 graphs per rho in {2.5, 3.5, 4.5}, L=64, 24 temperatures geometric in [1.5, 3.5]
+  C4  8 graphs per L in {32, 48, 64, 96, 128, 192}, rho=3.0, 20 temperatures in [1.5, 3.5], FP64 recompute every 100 sweeps
+  C5  64 graphs per rho in {2.5, 4.5}, L=512, 32 temperatures in [1.5, 3.5]
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import math
+import os
+from dataclasses import dataclass, field
+
+Z = 6
+GRAPH_SEED = 1
+SPIN_SEED = 2
+
+
+def geometric_temperatures(t_min: float, t_max: float, n: int):
+    if n == 1:
+        return [t_min]
+    return [t_min * (t_max / t_min) ** (k / (n - 1)) for k in range(n)]
+
+
+@dataclass
+class Config:
+    name: str
+    graphs: list            # (L, rho, sample_id) per sample
+    temperatures: list
+    recompute_every: int = 0
+    description: str = ""
+    delta: list = field(default_factory=list)
+
+    @property
+    def n_samples(self):
+        return len(self.graphs)
+
+    @property
+    def n_temps(self):
+        return len(self.temperatures)
+
+    @property
+    def sites(self):
+        return sum(L * L for L, _, _ in self.graphs)
+
+    def spins_per_sweep(self):
+        return self.sites * self.n_temps
+
+    def betas(self):
+        return [1.0 / t for t in self.temperatures]
+
+    def deltas(self):
+        """Metropolis half-width per slot: a fixed starting value, grown with T
+        (near 50% acceptance is tuned on the host before measuring)."""
+        if self.delta:
+            return list(self.delta)
+        return [min(math.pi, 1.2 * math.sqrt(t)) for t in self.temperatures]
+
+
+def config(name: str) -> Config:
+    if name == "C1":
+        return Config("C1", [(16, 3.5, 0)], [1.0], description="L=16 z=6 rho=3.5, T=1.0, one replica")
+    if name == "C2":
+        return Config("C2", [(128, 3.5, 0)], geometric_temperatures(0.8, 1.6, 16),
+                      description="L=128 z=6 rho=3.5, 16 T geometric in [0.8,1.6], PT every sweep")
+    if name == "C3":
+        g = [(64, rho, s) for rho in (2.5, 3.5, 4.5) for s in range(256)]
+        return Config("C3", g, geometric_temperatures(1.5, 3.5, 24),
+                      description="256 graphs x rho in {2.5,3.5,4.5}, L=64, 24 T")
+    if name == "C4":
+        g = [(L, 3.0, s) for L in (32, 48, 64, 96, 128, 192) for s in range(8)]
+        return Config("C4", g, geometric_temperatures(1.5, 3.5, 20), recompute_every=100,
+                      description="8 graphs x L in {32,48,64,96,128,192}, rho=3.0, 20 T, FP64 recompute every 100")
+    if name == "C5":
+        g = [(512, rho, s) for rho in (2.5, 4.5) for s in range(64)]
+        return Config("C5", g, geometric_temperatures(1.5, 3.5, 32),
+                      description="64 graphs x rho in {2.5,4.5}, L=512, 32 T")
+    raise KeyError(name)
+
+
+def sample_id(index: int) -> int:
+    """Distinct random-stream id per sample of a batch."""
+    return index
+
+
+def build_graphs(cfg: Config, threads: int = 0):
+    """Build every graph of a configuration with the library (parallel host threads)."""
+    from . import xyl
+    threads = threads or min(32, os.cpu_count() or 1)
+
+    def one(k):
+        L, rho, s = cfg.graphs[k]
+        # distinct graph streams per (rho, index) through the sample id
+        return xyl.build_graph_csr(L, Z, rho, GRAPH_SEED, graph_stream_id(cfg, k))
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        return list(ex.map(one, range(cfg.n_samples)))
+
+
+def graph_stream_id(cfg: Config, k: int) -> int:
+    return k
+
+
+def make_plan(cfg: Config, engine, graphs=None, seed=SPIN_SEED, **tuning):
+    from . import xyl
+    graphs = graphs if graphs is not None else build_graphs(cfg)
+    samples = [(g, sample_id(k), cfg.betas(), cfg.deltas()) for k, g in enumerate(graphs)]
+    if "recompute_every" not in tuning:
+        tuning["recompute_every"] = cfg.recompute_every
+    return xyl.Plan(samples, engine=engine, seed=seed, **tuning), graphs

@@ -1,0 +1,293 @@
+"""ctypes binding of libxyl (include/xyl.h): argument marshalling only.
+
+Every function keeps the C name without the ``xyl_`` prefix.  Device memory
+(the plan workspace) and streams come from PyTorch; all compute runs in the
+library's CUDA kernels.  Loading fails loudly when ``libxyl.so`` is missing:
+there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libxyl.so")
+
+OK, EINVAL, ENOSPC, EGRAPH, ECUDA, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
+OP_MET, OP_OR, OP_PT, OP_MEASURE = 1, 2, 4, 8
+FP64_PLAIN, FP32_BATCHED, FP32_PLAIN = 0, 1, 2
+ACC_FIELDS = ("n", "e", "e2", "absm", "mx", "my", "m2", "m4", "chik")
+
+EXPORTED = (
+    "xyl_last_error", "xyl_version", "xyl_build_graph_csr", "xyl_graph_from_edges", "xyl_graph_info",
+    "xyl_graph_export_csr", "xyl_graph_export_edges", "xyl_graph_free", "xyl_plan_create", "xyl_bind",
+    "xyl_init_spins", "xyl_sweep", "xyl_pt_swap", "xyl_measure", "xyl_recompute", "xyl_set_delta",
+    "xyl_read_observables", "xyl_reset_observables", "xyl_read_energies", "xyl_read_labels", "xyl_read_spins",
+    "xyl_write_spins", "xyl_read_status", "xyl_state_bytes", "xyl_export_state", "xyl_import_state",
+    "xyl_last_launch_count", "xyl_plan_free", "xyl_sweep_units", "xyl_unit_count",
+)
+
+
+class XylError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"xyl error {code}: {msg}")
+        self.code = code
+
+
+class Sample(C.Structure):
+    _fields_ = [("graph", C.c_void_p), ("sample_id", C.c_uint32), ("n_temps", C.c_int32),
+                ("beta", C.POINTER(C.c_double)), ("delta", C.POINTER(C.c_double))]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("block", C.c_int32), ("cluster", C.c_int32), ("group", C.c_int32),
+                ("recompute_every", C.c_int32), ("reserved", C.c_int32 * 4)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load():
+    """Load libxyl.so (built by ``paper_1211_3991_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_1211_3991_gb300.build.build() first")
+        lib = C.CDLL(LIB_PATH)
+        P, i32, i64, u32, u64, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_double
+        pi32, pi64, pu64, pf64 = C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_uint64), C.POINTER(C.c_double)
+        sig = {
+            "xyl_last_error": ([], C.c_char_p),
+            "xyl_version": ([], C.c_int),
+            "xyl_build_graph_csr": ([i32, i32, f64, u64, u32, C.POINTER(P)], C.c_int),
+            "xyl_graph_from_edges": ([i32, i64, pi32, pi32, i32, C.POINTER(P)], C.c_int),
+            "xyl_graph_info": ([P, pi32, pi64, pi32, pi32, pi32], C.c_int),
+            "xyl_graph_export_csr": ([P, pi32, pi32, pi32, pi32], C.c_int),
+            "xyl_graph_export_edges": ([P, pi32, pi32], C.c_int),
+            "xyl_graph_free": ([P], None),
+            "xyl_plan_create": ([C.POINTER(Sample), i32, i32, u64, C.POINTER(Tuning), C.POINTER(P),
+                                 C.POINTER(C.c_size_t)], C.c_int),
+            "xyl_bind": ([P, P, C.c_size_t, P], C.c_int),
+            "xyl_init_spins": ([P, i32, P], C.c_int),
+            "xyl_sweep": ([P, i32, u32, i32, P], C.c_int),
+            "xyl_pt_swap": ([P, P], C.c_int),
+            "xyl_measure": ([P, P], C.c_int),
+            "xyl_recompute": ([P, P], C.c_int),
+            "xyl_set_delta": ([P, i32, pf64, P], C.c_int),
+            "xyl_read_observables": ([P, pf64, pu64, pu64, pu64, pu64, P], C.c_int),
+            "xyl_reset_observables": ([P, P], C.c_int),
+            "xyl_read_energies": ([P, pf64, P], C.c_int),
+            "xyl_read_labels": ([P, pi32, P], C.c_int),
+            "xyl_read_spins": ([P, i32, i32, pf64, P], C.c_int),
+            "xyl_write_spins": ([P, i32, i32, pf64, P], C.c_int),
+            "xyl_read_status": ([P, pi32, pu64, P], C.c_int),
+            "xyl_state_bytes": ([P], C.c_size_t),
+            "xyl_export_state": ([P, P, C.c_size_t, P], C.c_int),
+            "xyl_import_state": ([P, P, C.c_size_t, P], C.c_int),
+            "xyl_last_launch_count": ([P], C.c_int64),
+            "xyl_plan_free": ([P], None),
+            "xyl_sweep_units": ([P, i32, i32, i32, u32, i32, P], C.c_int),
+            "xyl_unit_count": ([P], C.c_int32),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != OK:
+        raise XylError(rc, load().xyl_last_error().decode())
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+# ----------------------------------------------------------------- graphs
+class Graph:
+    """Owner of an ``xyl_graph`` handle."""
+
+    def __init__(self, handle):
+        self.handle = C.c_void_p(handle)
+        n = C.c_int32(); ne = C.c_int64(); q = C.c_int32(); md = C.c_int32(); rs = C.c_int32()
+        _check(load().xyl_graph_info(self.handle, C.byref(n), C.byref(ne), C.byref(q), C.byref(md), C.byref(rs)))
+        self.n, self.n_edges, self.n_colors, self.max_deg, self.restarts = n.value, ne.value, q.value, md.value, rs.value
+
+    def __del__(self):
+        try:
+            if self.handle:
+                load().xyl_graph_free(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+    def csr(self):
+        perm = np.zeros(self.n, np.int32); row_ptr = np.zeros(self.n + 1, np.int32)
+        col = np.zeros(2 * self.n_edges, np.int32); cptr = np.zeros(self.n_colors + 1, np.int32)
+        _check(load().xyl_graph_export_csr(self.handle, _p(perm, C.c_int32), _p(row_ptr, C.c_int32),
+                                           _p(col, C.c_int32), _p(cptr, C.c_int32)))
+        return perm, row_ptr, col, cptr
+
+    def edges(self):
+        ei = np.zeros(self.n_edges, np.int32); ej = np.zeros(self.n_edges, np.int32)
+        _check(load().xyl_graph_export_edges(self.handle, _p(ei, C.c_int32), _p(ej, C.c_int32)))
+        return ei, ej
+
+
+def build_graph_csr(L: int, z: int, rho: float, seed: int, sample_id: int = 0) -> Graph:
+    h = C.c_void_p()
+    _check(load().xyl_build_graph_csr(L, z, rho, seed, sample_id, C.byref(h)))
+    return Graph(h.value)
+
+
+def graph_from_edges(n: int, edges, xy=None, L: int = 0) -> Graph:
+    e = np.ascontiguousarray(np.asarray(edges, np.int32).reshape(-1))
+    xy_a = None if xy is None else np.ascontiguousarray(np.asarray(xy, np.int32).reshape(-1))
+    h = C.c_void_p()
+    _check(load().xyl_graph_from_edges(n, len(e) // 2, _p(e, C.c_int32) if len(e) else None,
+                                       None if xy_a is None else _p(xy_a, C.c_int32), L, C.byref(h)))
+    return Graph(h.value)
+
+
+# ----------------------------------------------------------------- plans
+class Plan:
+    """A batch of samples bound to a torch-allocated device workspace.
+
+    ``samples``: list of (Graph, sample_id, beta[list], delta[list])."""
+
+    def __init__(self, samples, engine=FP32_BATCHED, seed=0, block=0, cluster=0, group=0, recompute_every=0,
+                 device=None):
+        import torch
+        lib = load()
+        self._keep = []
+        arr = (Sample * len(samples))()
+        self.n_temps = []
+        self.sizes = []
+        for k, (g, sid, beta, delta) in enumerate(samples):
+            b = np.ascontiguousarray(beta, np.float64); d = np.ascontiguousarray(delta, np.float64)
+            if b.ndim != 1 or b.shape != d.shape:
+                raise XylError(EINVAL, f"sample {k}: beta and delta need one value per slot")
+            self._keep += [g, b, d]
+            arr[k] = Sample(g.handle, sid, len(b), _p(b, C.c_double), _p(d, C.c_double))
+            self.n_temps.append(len(b))
+            self.sizes.append(g.n)
+        tune = Tuning(block, cluster, group, recompute_every)
+        h = C.c_void_p(); nbytes = C.c_size_t()
+        _check(lib.xyl_plan_create(arr, len(samples), engine, seed, C.byref(tune), C.byref(h), C.byref(nbytes)))
+        self.handle = h
+        self.engine = engine
+        self.workspace_bytes = nbytes.value
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.workspace = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=dev)
+        self.total_slots = sum(self.n_temps)
+
+    def __del__(self):
+        try:
+            if self.handle:
+                load().xyl_plan_free(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+    def bind(self, stream=None):
+        _check(load().xyl_bind(self.handle, C.c_void_p(self.workspace.data_ptr()), self.workspace.numel(),
+                               _stream(stream)))
+        return self
+
+    def init_spins(self, aligned=False, stream=None):
+        _check(load().xyl_init_spins(self.handle, 1 if aligned else 0, _stream(stream)))
+
+    def sweep(self, n, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1, stream=None):
+        _check(load().xyl_sweep(self.handle, int(n), int(ops), int(measure_every), _stream(stream)))
+
+    def sweep_units(self, first, count, n, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1, stream=None):
+        _check(load().xyl_sweep_units(self.handle, int(first), int(count), int(n), int(ops), int(measure_every),
+                                      _stream(stream)))
+
+    def unit_count(self) -> int:
+        return int(load().xyl_unit_count(self.handle))
+
+    # same method names as the oracle sampler, so tests drive both the same way
+    def sweeps(self, n, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1):
+        self.sweep(n, ops, measure_every)
+
+    def pt_swap(self, stream=None):
+        _check(load().xyl_pt_swap(self.handle, _stream(stream)))
+
+    def measure(self, stream=None):
+        _check(load().xyl_measure(self.handle, _stream(stream)))
+
+    def recompute(self, stream=None):
+        _check(load().xyl_recompute(self.handle, _stream(stream)))
+
+    def set_delta(self, sample, delta, stream=None):
+        d = np.ascontiguousarray(delta, np.float64)
+        _check(load().xyl_set_delta(self.handle, sample, _p(d, C.c_double), _stream(stream)))
+
+    def read_observables(self, stream=None):
+        n = self.total_slots
+        acc = np.zeros((n, len(ACC_FIELDS)), np.float64)
+        ma, mt, pa, pt = (np.zeros(n, np.uint64) for _ in range(4))
+        _check(load().xyl_read_observables(self.handle, _p(acc, C.c_double), _p(ma, C.c_uint64), _p(mt, C.c_uint64),
+                                           _p(pa, C.c_uint64), _p(pt, C.c_uint64), _stream(stream)))
+        return {"acc": acc, "met_acc": ma, "met_try": mt, "pt_acc": pa, "pt_try": pt}
+
+    accumulators = read_observables
+
+    def reset_observables(self, stream=None):
+        _check(load().xyl_reset_observables(self.handle, _stream(stream)))
+
+    reset_acc = reset_observables
+
+    def energies(self, stream=None):
+        out = np.zeros(self.total_slots, np.float64)
+        _check(load().xyl_read_energies(self.handle, _p(out, C.c_double), _stream(stream)))
+        return out
+
+    def labels(self, stream=None):
+        out = np.zeros(self.total_slots, np.int32)
+        _check(load().xyl_read_labels(self.handle, _p(out, C.c_int32), _stream(stream)))
+        return out
+
+    def spins(self, sample, replica, stream=None):
+        out = np.zeros(2 * self.sizes[sample], np.float64)
+        _check(load().xyl_read_spins(self.handle, sample, replica, _p(out, C.c_double), _stream(stream)))
+        return out.reshape(-1, 2)
+
+    def write_spins(self, sample, replica, sxy, stream=None):
+        a = np.ascontiguousarray(np.asarray(sxy, np.float64).reshape(-1))
+        _check(load().xyl_write_spins(self.handle, sample, replica, _p(a, C.c_double), _stream(stream)))
+
+    def status(self, stream=None):
+        s = C.c_int32(); t = C.c_uint64()
+        _check(load().xyl_read_status(self.handle, C.byref(s), C.byref(t), _stream(stream)))
+        return s.value, t.value
+
+    def export_state(self, stream=None) -> bytes:
+        n = load().xyl_state_bytes(self.handle)
+        buf = (C.c_char * n)()
+        _check(load().xyl_export_state(self.handle, C.cast(buf, C.c_void_p), n, _stream(stream)))
+        return bytes(buf)
+
+    def import_state(self, blob: bytes, stream=None):
+        buf = C.create_string_buffer(blob, len(blob))
+        _check(load().xyl_import_state(self.handle, C.cast(buf, C.c_void_p), len(blob), _stream(stream)))
+
+    def last_launch_count(self) -> int:
+        return int(load().xyl_last_launch_count(self.handle))

@@ -1,0 +1,129 @@
+"""Host-side checks of libxyl (no GPU needed).
+
+* the shared library loads and exports every entry point include/xyl.h declares;
+* the library's graph builder and the oracle's build edge-for-edge identical
+  graphs and bit-identical colour-sorted CSR at every configuration size;
+* argument validation and call-order errors.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def xyl():
+    from paper_1211_3991_gb300 import build
+    build.build()
+    from paper_1211_3991_gb300 import xyl as mod
+    mod.load()
+    return mod
+
+
+def _header_functions():
+    text = open(os.path.join(ROOT, "include", "xyl.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(xyl_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(xyl):
+    names = _header_functions()
+    assert len(names) >= 25
+    lib = xyl.load()
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(names) == set(xyl.EXPORTED)
+
+
+def _oracle_csr(orc, L, rho, seed, sid):
+    ei, ej, restarts, _ = orc.levy_graph(L, 6, rho, seed, sid)
+    col, q = orc.slo_color(L * L, ei, ej)
+    return (ei, ej), orc.csr(L * L, ei, ej, col, q), restarts
+
+
+CASES = [(16, 3.5, 1, 0), (128, 3.5, 1, 0)] + [(64, rho, 1, s) for rho in (2.5, 3.5, 4.5) for s in (0, 1, 255)] + \
+        [(L, 3.0, 1, 3) for L in (32, 48, 64, 96, 128, 192)] + [(512, 2.5, 1, 0), (512, 4.5, 1, 64)] + \
+        [(4, 3.5, 9, 0), (6, 2.0, 9, 1), (8, 7.0, 9, 2)]
+
+
+@pytest.mark.parametrize("L,rho,seed,sid", CASES)
+def test_graph_and_csr_bit_exact_vs_oracle(xyl, orc, L, rho, seed, sid):
+    g = xyl.build_graph_csr(L, 6, rho, seed, sid)
+    (oi, oj), ocsr, restarts = _oracle_csr(orc, L, rho, seed, sid)
+    ei, ej = g.edges()
+    assert np.array_equal(ei, oi) and np.array_equal(ej, oj)
+    for mine, theirs in zip(g.csr(), ocsr):
+        assert mine.dtype == theirs.dtype and np.array_equal(mine, theirs)
+    assert g.restarts == restarts
+    assert g.max_deg == 6 and g.n_edges == L * L * 3
+
+
+def test_graph_from_edges_matches_oracle_colouring(xyl, orc):
+    rng = np.random.default_rng(4)
+    n = 40
+    pairs = set()
+    while len(pairs) < 90:
+        a, b = rng.integers(0, n, 2)
+        if a != b:
+            pairs.add((int(min(a, b)), int(max(a, b))))
+    edges = np.array(sorted(pairs), np.int32)
+    g = xyl.graph_from_edges(n, edges)
+    col, q = orc.slo_color(n, edges[:, 0], edges[:, 1])
+    for mine, theirs in zip(g.csr(), orc.csr(n, edges[:, 0], edges[:, 1], col, q)):
+        assert np.array_equal(mine, theirs)
+
+
+def test_graph_from_edges_rejects_bad_input(xyl):
+    with pytest.raises(xyl.XylError) as e:
+        xyl.graph_from_edges(3, [[0, 0]])
+    assert e.value.code == xyl.EINVAL
+    with pytest.raises(xyl.XylError):
+        xyl.graph_from_edges(3, [[0, 1], [1, 0]])
+    with pytest.raises(xyl.XylError):
+        xyl.graph_from_edges(3, [[0, 3]])
+
+
+@pytest.mark.parametrize("args", [(5, 6, 3.5), (2, 1, 3.5), (16, 0, 3.5), (4, 16, 3.5), (16, 6, float("nan"))])
+def test_build_graph_rejects_bad_sizes(xyl, args):
+    with pytest.raises(xyl.XylError) as e:
+        xyl.build_graph_csr(*args, 1)
+    assert e.value.code == xyl.EINVAL
+
+
+def test_dead_end_limit_reports_egraph(xyl, orc):
+    """13-regular graphs on 16 sites: most seeds need restarts and a few exhaust
+    all 100 (host-side failure, no GPU involved); both builders agree on every
+    outcome and on the number of restarts."""
+    fails = 0
+    for seed in range(40):
+        try:
+            g = xyl.build_graph_csr(4, 13, 3.5, seed, 0)
+            lib = g.restarts
+        except xyl.XylError as e:
+            assert e.code == xyl.EGRAPH
+            lib = None
+        try:
+            theirs = orc.levy_graph(4, 13, 3.5, seed, 0)[2]
+        except RuntimeError:
+            theirs = None
+        assert lib == theirs
+        fails += lib is None
+    assert fails >= 1
+
+
+def test_plan_validation_without_gpu(xyl):
+    g = xyl.build_graph_csr(16, 6, 3.5, 1, 0)
+    with pytest.raises(xyl.XylError) as e:
+        xyl.Plan([(g, 0, [1.0, 0.5], [1.0])], engine=xyl.FP32_BATCHED, device="cpu")
+    with pytest.raises(xyl.XylError):
+        xyl.Plan([(g, 0, [1.0], [1.0])], engine=7, device="cpu")
+    with pytest.raises(xyl.XylError):
+        xyl.Plan([(g, 0, [1.0, 2.0, 3.0], [1.0] * 3)], engine=xyl.FP32_BATCHED, group=2, device="cpu")
+    p = xyl.Plan([(g, 0, [1.0, 0.9], [1.0, 1.0])], engine=xyl.FP32_BATCHED, device="cpu")
+    assert p.workspace_bytes > 256 * 2 * 8
+    with pytest.raises(xyl.XylError) as e:
+        p.sweep(1, stream=0)
+    assert e.value.code == xyl.ESTATE
