@@ -71,6 +71,13 @@ def _load():
         lib.orc_sim_set_delta.argtypes = [P, f64p]
         lib.orc_sim_set_tie_eps.argtypes = [P, C.c_double]
         lib.orc_sim_get_ties.argtypes = [P, i64p, i64p, f64p]
+        lib.orc_sim_get_vectors.argtypes = [P, f64p]
+        lib.orc_sim_set_vectors.argtypes = [P, f64p]
+        lib.orc_sim_set_labels.argtypes = [P, i32p, C.c_uint64]
+        lib.orc_sim_get_tie_counts.argtypes = [P, i64p]
+        lib.orc_sim_clear_ties.argtypes = [P]
+        lib.orc_sincos_series.argtypes = [C.c_double, f64p, f64p]
+        lib.orc_sincos_series.restype = None
         lib.orc_sim_sweep_index.argtypes = [P]
         lib.orc_sim_sweep_index.restype = C.c_uint64
         _lib = lib
@@ -91,6 +98,16 @@ def philox(ctr, key) -> np.ndarray:
     out = np.zeros(4, dtype=np.uint32)
     lib.orc_philox(_ptr(c, C.c_uint32), _ptr(k, C.c_uint32), _ptr(out, C.c_uint32))
     return out
+
+
+def sincos_series(x: float):
+    """sin, cos by the Maclaurin series used for the Metropolis step.
+
+    Pinned against libm (tests/test_oracle_philox.py)."""
+    lib = _load()
+    sn = np.zeros(1); cs = np.zeros(1)
+    lib.orc_sincos_series(float(x), _ptr(sn, C.c_double), _ptr(cs, C.c_double))
+    return float(sn[0]), float(cs[0])
 
 
 def disp_table(L: int, rho: float):
@@ -231,6 +248,27 @@ class Sim:
     def set_angles(self, a):
         a = np.ascontiguousarray(a, np.float64).reshape(self.R, self.n)
         self._lib.orc_sim_set_angles(self._h, _ptr(a, C.c_double))
+
+    def vectors(self) -> np.ndarray:
+        out = np.zeros((self.R, self.n, 2), np.float64)
+        self._lib.orc_sim_get_vectors(self._h, _ptr(out, C.c_double))
+        return out
+
+    def set_vectors(self, v):
+        v = np.ascontiguousarray(v, np.float64).reshape(self.R, self.n, 2)
+        self._lib.orc_sim_set_vectors(self._h, _ptr(v, C.c_double))
+
+    def set_labels(self, rep_at, sweep_index):
+        a = np.ascontiguousarray(rep_at, np.int32)
+        self._lib.orc_sim_set_labels(self._h, _ptr(a, C.c_int32), int(sweep_index))
+
+    def tie_counts(self) -> np.ndarray:
+        out = np.zeros(self.R, np.int64)
+        self._lib.orc_sim_get_tie_counts(self._h, _ptr(out, C.c_int64))
+        return out
+
+    def clear_ties(self):
+        self._lib.orc_sim_clear_ties(self._h)
 
     def energies(self) -> np.ndarray:
         out = np.zeros(self.R, np.float64)

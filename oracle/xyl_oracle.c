@@ -21,6 +21,7 @@
  *                       coloring").
  *   orc_csr()           Colour-sorted CSR (App. B, "Memory management": sites of
  *                       one colour stored consecutively).
+ *   orc_sincos_series() sin/cos of the Metropolis step by their Maclaurin series.
  *   orc_sim_*()         Monte Carlo sweeps of H = -sum_{i<j} J_ij S_i.S_j,
  *                       Eq. (HXY): single-spin Metropolis over the colour classes
  *                       in sequence (App. B), overrelaxation (App. B, "Improved
@@ -29,9 +30,11 @@
  *                       (energy, magnetisation m, |m|, m^2, m^4, and the
  *                       Fourier sum at k_min = 2 pi / L used by xi_2).
  *
- * The oracle keeps each spin as an angle theta (the paper's own storage,
- * App. B) and evaluates the energy as -sum cos(theta_i - theta_j); the CUDA path
- * keeps unit vectors.  The two agree up to rounding.
+ * Spins are FP64 unit vectors, the form in which Eq. (HXY) is written.  The
+ * overrelaxation map is chaotic (rounding differences grow about tenfold per
+ * sweep), so every arithmetic step of a sweep is fixed here -- operand order,
+ * no contraction, the series for sin/cos -- and an implementation doing the
+ * same steps reproduces the trajectory bit for bit.
  *
  * Readings of points the paper leaves open are listed with each routine.
  */
@@ -595,34 +598,87 @@ int orc_csr(int n, int64_t ne, const int32_t *ei, const int32_t *ej, const int32
 }
 
 /* ------------------------------------------------------------------------- */
+/* sin and cos of |x| <= pi (about) by their Maclaurin series:                */
+/*   sin x = x sum_k (-1)^k x^2k / (2k+1)!,  k = 0..14                        */
+/*   cos x =   sum_k (-1)^k x^2k / (2k)!,    k = 0..15                        */
+/* coefficients by the factorial recurrence a_k = a_{k-1} / (n (n+1)), Horner */
+/* in y = x^2 with IEEE fused multiply-add.  Truncation < 3e-17 at |x| = pi;  */
+/* pinned against libm to 2e-15 absolute.  Every rounding step is fixed, so   */
+/* any implementation of these steps gives the same bits.                     */
+/* ------------------------------------------------------------------------- */
+#define SIN_TERMS 15
+#define COS_TERMS 16
+static double sin_coef[SIN_TERMS], cos_coef[COS_TERMS];
+static int series_ready = 0;
+
+static void series_init(void)
+{
+    if (series_ready) return;
+    double a = 1.0;
+    sin_coef[0] = 1.0;
+    for (int k = 1; k < SIN_TERMS; ++k) {
+        a = a / (double)((2 * k) * (2 * k + 1));
+        sin_coef[k] = (k & 1) ? -a : a;
+    }
+    a = 1.0;
+    cos_coef[0] = 1.0;
+    for (int k = 1; k < COS_TERMS; ++k) {
+        a = a / (double)((2 * k - 1) * (2 * k));
+        cos_coef[k] = (k & 1) ? -a : a;
+    }
+    series_ready = 1;
+}
+
+void orc_sincos_series(double x, double *sn, double *cs)
+{
+    series_init();
+    const double y = x * x;
+    double p = sin_coef[SIN_TERMS - 1];
+    for (int k = SIN_TERMS - 2; k >= 0; --k) p = fma(p, y, sin_coef[k]);
+    double q = cos_coef[COS_TERMS - 1];
+    for (int k = COS_TERMS - 2; k >= 0; --k) q = fma(q, y, cos_coef[k]);
+    *sn = x * p;
+    *cs = q;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Monte Carlo sampler.                                                       */
+/*                                                                            */
+/* Spins are FP64 unit vectors S_i = (x_i, y_i), as in Eq. (HXY),             */
+/* H = -sum_{i<j} J_ij S_i . S_j.                                             */
 /*                                                                            */
 /* Sweep t (App. B; readings where the paper is silent):                      */
 /*   1. Metropolis pass: colours c = 0..Q-1 in turn; within a colour the      */
 /*      sites are mutually unlinked, so the order inside it does not matter   */
-/*      (ascending id here).  Proposal theta' = theta + Delta (2u - 1), Delta */
-/*      per temperature slot; accept iff dE <= 0 or u' < exp(-beta dE), with  */
-/*      dE = -sum_j [cos(theta'-theta_j) - cos(theta-theta_j)], Eq. (HXY).    */
-/*   2. Overrelaxation pass, same colour order: the spin is reflected about   */
-/*      its local field h = sum_j S_j (theta' = 2 arg(h) - theta), left as it */
-/*      is when h = 0.  One Metropolis and one OR pass per sweep.             */
+/*      (ascending id here).  The local field h = sum_j S_j is summed over    */
+/*      the neighbours in ascending colour-sorted id.  Proposal: S rotated by */
+/*      delta = Delta (2u - 1), Delta per temperature slot:                   */
+/*        x' = c x - s y,  y' = s x + c y   (c, s = cos, sin of delta);       */
+/*      dE = -((x' - x) h_x + (y' - y) h_y); accept iff dE <= 0 or            */
+/*      u' < exp(-beta dE).                                                   */
+/*   2. Overrelaxation pass, same colour order: reflection about the local    */
+/*      field, k = 2 (x h_x + y h_y) / (h_x^2 + h_y^2), S' = k h - S; the spin */
+/*      is left as it is when h = 0.  One Metropolis and one OR pass a sweep. */
 /*   3. Parallel tempering after the sweep: pairs of slots (k, k+1) with      */
 /*      k = t mod 2, 4, ...; accept iff u < exp((beta_k - beta_{k+1})         */
 /*      (E_k - E_{k+1})) where E_k is the energy of the replica at slot k;    */
 /*      an accepted swap exchanges which replica sits at the two slots.       */
 /*   4. Measurement when (t+1) is a multiple of measure_every, per slot.      */
+/* Every expression is evaluated as written (no contraction): products, then  */
+/* sums, left to right.                                                       */
 /* Random draws: Metropolis of site i (original id), sweep t, replica r:      */
 /* Philox counter (i, t, MET<<24 | r, sample); 53-bit mode uses u53(w0,w1)    */
 /* for the step and u53(w2,w3) for the test, 24-bit mode u24(w0), u24(w1).    */
 /* Initial angle theta = 2 pi u - pi from counter (i, 0, INIT<<24 | r,        */
-/* sample).  PT pair k at sweep t: counter (k, t, PT<<24, sample), u53(w0,w1).*/
+/* sample), S = (cos theta, sin theta) by the series above.  PT pair k at     */
+/* sweep t: counter (k, t, PT<<24, sample), u53(w0,w1).                       */
 /* ------------------------------------------------------------------------- */
 enum { OP_MET = 1u, OP_OR = 2u, OP_PT = 4u, OP_MEASURE = 8u };
 enum { ACC_N, ACC_E, ACC_E2, ACC_ABSM, ACC_MX, ACC_MY, ACC_M2, ACC_M4, ACC_CHIK, ACC_COUNT };
 
 typedef struct {
     int n, R, L, Q;
-    int *ptr, *nbr;           /* adjacency by original id */
+    int *ptr, *nbr;           /* neighbours of each original id, ascending colour-sorted id */
     int *cls_ptr, *cls;       /* colour classes, ascending id inside a class */
     int64_t n_bonds;
     int *bi, *bj;             /* bond list */
@@ -630,7 +686,7 @@ typedef struct {
     double *beta, *delta;     /* per slot */
     uint32_t key[2], sample;
     int u24_mode;
-    double *theta;            /* [R][n] */
+    double *vx, *vy;          /* spin vectors [R][n] */
     int *slot_of, *rep_at;
     uint64_t t;
     double *E;                /* per replica energy after the last sweep */
@@ -638,25 +694,26 @@ typedef struct {
     uint64_t *met_acc, *met_try, *pt_acc, *pt_try;
     double tie_eps;
     int64_t *first_tie;       /* per replica: first sweep with a near-tie Metropolis test */
+    int64_t *n_ties;          /* per replica: near-tie Metropolis tests since the last clear */
     int64_t first_pt_tie;
     double min_margin;        /* smallest Metropolis margin seen */
 } orc_sim;
-
-static double wrap_angle(double a)
-{
-    while (a >= ORC_PI) a -= 2.0 * ORC_PI;
-    while (a < -ORC_PI) a += 2.0 * ORC_PI;
-    return a;
-}
 
 void orc_sim_free(orc_sim *s)
 {
     if (!s) return;
     free(s->ptr); free(s->nbr); free(s->cls_ptr); free(s->cls); free(s->bi); free(s->bj);
     free(s->cx); free(s->sx); free(s->cy); free(s->sy); free(s->beta); free(s->delta);
-    free(s->theta); free(s->slot_of); free(s->rep_at); free(s->E); free(s->acc);
-    free(s->met_acc); free(s->met_try); free(s->pt_acc); free(s->pt_try); free(s->first_tie);
+    free(s->vx); free(s->vy); free(s->slot_of); free(s->rep_at); free(s->E); free(s->acc);
+    free(s->met_acc); free(s->met_try); free(s->pt_acc); free(s->pt_try); free(s->first_tie); free(s->n_ties);
     free(s);
+}
+
+static const int *g_rank_for_sort;
+static int cmp_by_rank(const void *a, const void *b)
+{
+    int x = g_rank_for_sort[*(const int *)a], y = g_rank_for_sort[*(const int *)b];
+    return (x > y) - (x < y);
 }
 
 /* xy: 2n lattice coordinates (x, y) or NULL (then x = id, y = 0, period L = n). */
@@ -664,6 +721,7 @@ orc_sim *orc_sim_new(int n, int64_t ne, const int32_t *ei, const int32_t *ej, co
                      const int32_t *xy, int L, int R, const double *beta, const double *delta,
                      uint64_t seed, uint32_t sample, int u24_mode)
 {
+    series_init();
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     if (!s) return NULL;
     s->n = n; s->R = R; s->u24_mode = u24_mode;
@@ -680,6 +738,14 @@ orc_sim *orc_sim_new(int n, int64_t ne, const int32_t *ei, const int32_t *ej, co
         for (int v = 0; v < n; ++v) if (color[v] == c) s->cls[k++] = v;
     }
     s->cls_ptr[Q] = k;
+    /* colour-sorted id of each site = its position in the class list; order each
+     * neighbour list by it */
+    int *rank = (int *)malloc(sizeof(int) * (size_t)n);
+    for (int a = 0; a < n; ++a) rank[s->cls[a]] = a;
+    g_rank_for_sort = rank;
+    for (int v = 0; v < n; ++v)
+        qsort(s->nbr + s->ptr[v], (size_t)(s->ptr[v + 1] - s->ptr[v]), sizeof(int), cmp_by_rank);
+    free(rank);
     s->n_bonds = ne;
     s->bi = (int *)malloc(sizeof(int) * (size_t)(ne + 1));
     s->bj = (int *)malloc(sizeof(int) * (size_t)(ne + 1));
@@ -699,7 +765,8 @@ orc_sim *orc_sim_new(int n, int64_t ne, const int32_t *ei, const int32_t *ej, co
     s->beta = (double *)malloc(sizeof(double) * (size_t)R);
     s->delta = (double *)malloc(sizeof(double) * (size_t)R);
     for (int r = 0; r < R; ++r) { s->beta[r] = beta[r]; s->delta[r] = delta[r]; }
-    s->theta = (double *)calloc((size_t)R * (size_t)n, sizeof(double));
+    s->vx = (double *)calloc((size_t)R * (size_t)n, sizeof(double));
+    s->vy = (double *)calloc((size_t)R * (size_t)n, sizeof(double));
     s->slot_of = (int *)malloc(sizeof(int) * (size_t)R);
     s->rep_at = (int *)malloc(sizeof(int) * (size_t)R);
     s->E = (double *)calloc((size_t)R, sizeof(double));
@@ -709,8 +776,9 @@ orc_sim *orc_sim_new(int n, int64_t ne, const int32_t *ei, const int32_t *ej, co
     s->pt_acc = (uint64_t *)calloc((size_t)R, sizeof(uint64_t));
     s->pt_try = (uint64_t *)calloc((size_t)R, sizeof(uint64_t));
     s->first_tie = (int64_t *)malloc(sizeof(int64_t) * (size_t)R);
+    s->n_ties = (int64_t *)calloc((size_t)R, sizeof(int64_t));
     s->tie_eps = 0.0;
-    for (int r = 0; r < R; ++r) { s->slot_of[r] = r; s->rep_at[r] = r; s->first_tie[r] = -1; }
+    for (int r = 0; r < R; ++r) { s->slot_of[r] = r; s->rep_at[r] = r; s->first_tie[r] = -1; s->vx[(size_t)r * n] = 1.0; }
     s->first_pt_tie = -1;
     s->min_margin = INFINITY;
     return s;
@@ -725,28 +793,38 @@ void orc_sim_set_tie_eps(orc_sim *s, double eps) { s->tie_eps = eps; }
 
 static double energy_of(const orc_sim *s, int r)
 {
-    const double *th = s->theta + (size_t)r * s->n;
+    const double *x = s->vx + (size_t)r * s->n, *y = s->vy + (size_t)r * s->n;
     double E = 0.0;
-    for (int64_t e = 0; e < s->n_bonds; ++e) E -= cos(th[s->bi[e]] - th[s->bj[e]]);
+    for (int64_t e = 0; e < s->n_bonds; ++e) {
+        int i = s->bi[e], j = s->bj[e];
+        E -= x[i] * x[j] + y[i] * y[j];
+    }
     return E;
 }
 
-/* aligned != 0: every angle 0; else the INIT draws.  Resets the sweep count,
+static void refresh_energies(orc_sim *s)
+{
+    for (int r = 0; r < s->R; ++r) s->E[r] = energy_of(s, r);
+}
+
+/* aligned != 0: every spin (1, 0); else the INIT draws.  Resets the sweep count,
  * the slot labels and every accumulator. */
 void orc_sim_init(orc_sim *s, int aligned)
 {
     for (int r = 0; r < s->R; ++r) {
         for (int v = 0; v < s->n; ++v) {
-            double th = 0.0;
+            double sn = 0.0, cs = 1.0;
             if (!aligned) {
                 uint32_t x[4];
                 draw_block((uint32_t)v, 0, PURPOSE_INIT, (uint32_t)r, s->sample, s->key, x);
                 double u = s->u24_mode ? u24(x[0]) : u53(x[0], x[1]);
-                th = 2.0 * ORC_PI * u - ORC_PI;
+                double th = 2.0 * ORC_PI * u - ORC_PI;
+                orc_sincos_series(th, &sn, &cs);
             }
-            s->theta[(size_t)r * s->n + v] = th;
+            s->vx[(size_t)r * s->n + v] = cs;
+            s->vy[(size_t)r * s->n + v] = sn;
         }
-        s->slot_of[r] = r; s->rep_at[r] = r; s->first_tie[r] = -1;
+        s->slot_of[r] = r; s->rep_at[r] = r; s->first_tie[r] = -1; s->n_ties[r] = 0;
     }
     s->t = 0;
     s->first_pt_tie = -1;
@@ -756,30 +834,44 @@ void orc_sim_init(orc_sim *s, int aligned)
     memset(s->met_try, 0, sizeof(uint64_t) * (size_t)s->R);
     memset(s->pt_acc, 0, sizeof(uint64_t) * (size_t)s->R);
     memset(s->pt_try, 0, sizeof(uint64_t) * (size_t)s->R);
-    for (int r = 0; r < s->R; ++r) s->E[r] = energy_of(s, r);
+    refresh_energies(s);
 }
 
 static void note_tie(orc_sim *s, int r, double margin)
 {
     if (margin < s->min_margin) s->min_margin = margin;
-    if (margin < s->tie_eps && s->first_tie[r] < 0) s->first_tie[r] = (int64_t)s->t;
+    if (margin < s->tie_eps) {
+        s->n_ties[r]++;
+        if (s->first_tie[r] < 0) s->first_tie[r] = (int64_t)s->t;
+    }
+}
+
+static void local_field(const orc_sim *s, const double *x, const double *y, int v, double *hx, double *hy)
+{
+    double ax = 0.0, ay = 0.0;
+    for (int a = s->ptr[v]; a < s->ptr[v + 1]; ++a) {
+        ax += x[s->nbr[a]];
+        ay += y[s->nbr[a]];
+    }
+    *hx = ax; *hy = ay;
 }
 
 static void metropolis_site(orc_sim *s, int r, int v)
 {
-    double *th = s->theta + (size_t)r * s->n;
+    double *x = s->vx + (size_t)r * s->n, *y = s->vy + (size_t)r * s->n;
     int slot = s->slot_of[r];
-    uint32_t x[4];
-    draw_block((uint32_t)v, (uint32_t)s->t, PURPOSE_MET, (uint32_t)r, s->sample, s->key, x);
-    double ud = s->u24_mode ? u24(x[0]) : u53(x[0], x[1]);
-    double ua = s->u24_mode ? u24(x[1]) : u53(x[2], x[3]);
-    double old = th[v];
-    double prop = old + s->delta[slot] * (2.0 * ud - 1.0);
-    double dE = 0.0;
-    for (int a = s->ptr[v]; a < s->ptr[v + 1]; ++a) {
-        double tj = th[s->nbr[a]];
-        dE -= cos(prop - tj) - cos(old - tj);
-    }
+    uint32_t w[4];
+    draw_block((uint32_t)v, (uint32_t)s->t, PURPOSE_MET, (uint32_t)r, s->sample, s->key, w);
+    double ud = s->u24_mode ? u24(w[0]) : u53(w[0], w[1]);
+    double ua = s->u24_mode ? u24(w[1]) : u53(w[2], w[3]);
+    double hx, hy;
+    local_field(s, x, y, v, &hx, &hy);
+    double d = s->delta[slot] * (2.0 * ud - 1.0);
+    double sn, cs;
+    orc_sincos_series(d, &sn, &cs);
+    double nx = cs * x[v] - sn * y[v];
+    double ny = sn * x[v] + cs * y[v];
+    double dE = -((nx - x[v]) * hx + (ny - y[v]) * hy);
     int accept;
     if (dE <= 0.0) {
         accept = 1;
@@ -793,21 +885,25 @@ static void metropolis_site(orc_sim *s, int r, int v)
     }
     s->met_try[slot]++;
     if (accept) {
-        th[v] = wrap_angle(prop);
+        x[v] = nx;
+        y[v] = ny;
         s->met_acc[slot]++;
     }
 }
 
 static void overrelax_site(orc_sim *s, int r, int v)
 {
-    double *th = s->theta + (size_t)r * s->n;
-    double hx = 0.0, hy = 0.0;
-    for (int a = s->ptr[v]; a < s->ptr[v + 1]; ++a) {
-        hx += cos(th[s->nbr[a]]);
-        hy += sin(th[s->nbr[a]]);
+    double *x = s->vx + (size_t)r * s->n, *y = s->vy + (size_t)r * s->n;
+    double hx, hy;
+    local_field(s, x, y, v, &hx, &hy);
+    double h2 = hx * hx + hy * hy;
+    if (h2 > 0.0) {
+        double k = 2.0 * (x[v] * hx + y[v] * hy) / h2;
+        double nx = k * hx - x[v];
+        double ny = k * hy - y[v];
+        x[v] = nx;
+        y[v] = ny;
     }
-    if (hx == 0.0 && hy == 0.0) return;
-    th[v] = wrap_angle(2.0 * atan2(hy, hx) - th[v]);
 }
 
 static void parallel_tempering(orc_sim *s)
@@ -833,12 +929,12 @@ static void parallel_tempering(orc_sim *s)
 /* Observables of Sec. III for replica r: e, m, |F(k_min)|^2 (two directions). */
 static void observe(const orc_sim *s, int r, double out[ACC_COUNT])
 {
-    const double *th = s->theta + (size_t)r * s->n;
+    const double *x = s->vx + (size_t)r * s->n, *y = s->vy + (size_t)r * s->n;
     double mx = 0, my = 0;
     double fxr_a = 0, fxi_a = 0, fyr_a = 0, fyi_a = 0; /* k along x: spin x / y comps */
     double fxr_b = 0, fxi_b = 0, fyr_b = 0, fyi_b = 0; /* k along y */
     for (int v = 0; v < s->n; ++v) {
-        double c = cos(th[v]), sn = sin(th[v]);
+        double c = x[v], sn = y[v];
         mx += c; my += sn;
         fxr_a += c * s->cx[v]; fxi_a += c * s->sx[v];
         fyr_a += sn * s->cx[v]; fyi_a += sn * s->sx[v];
@@ -886,15 +982,41 @@ void orc_sim_sweeps(orc_sim *s, int n_sweeps, unsigned ops, int measure_every)
     }
 }
 
+/* angles atan2(y, x) of every spin, [R][n] */
 void orc_sim_get_angles(const orc_sim *s, double *out)
 {
-    memcpy(out, s->theta, sizeof(double) * (size_t)s->R * (size_t)s->n);
+    for (size_t q = 0; q < (size_t)s->R * (size_t)s->n; ++q) out[q] = atan2(s->vy[q], s->vx[q]);
 }
 
+/* spins from angles in (-pi, pi] via the series; energies refreshed */
 void orc_sim_set_angles(orc_sim *s, const double *in)
 {
-    memcpy(s->theta, in, sizeof(double) * (size_t)s->R * (size_t)s->n);
-    for (int r = 0; r < s->R; ++r) s->E[r] = energy_of(s, r);
+    for (size_t q = 0; q < (size_t)s->R * (size_t)s->n; ++q) {
+        double th = in[q];
+        while (th > ORC_PI) th -= 2.0 * ORC_PI;
+        while (th < -ORC_PI) th += 2.0 * ORC_PI;
+        orc_sincos_series(th, &s->vy[q], &s->vx[q]);
+    }
+    refresh_energies(s);
+}
+
+/* spin vectors as (x, y) pairs, [R][n][2] */
+void orc_sim_get_vectors(const orc_sim *s, double *out)
+{
+    for (size_t q = 0; q < (size_t)s->R * (size_t)s->n; ++q) { out[2 * q] = s->vx[q]; out[2 * q + 1] = s->vy[q]; }
+}
+
+void orc_sim_set_vectors(orc_sim *s, const double *in)
+{
+    for (size_t q = 0; q < (size_t)s->R * (size_t)s->n; ++q) { s->vx[q] = in[2 * q]; s->vy[q] = in[2 * q + 1]; }
+    refresh_energies(s);
+}
+
+/* replica at each slot, and the sweep index of the next sweep */
+void orc_sim_set_labels(orc_sim *s, const int32_t *rep_at, uint64_t t)
+{
+    for (int k = 0; k < s->R; ++k) { s->rep_at[k] = rep_at[k]; s->slot_of[rep_at[k]] = k; }
+    s->t = t;
 }
 
 void orc_sim_get_energies(const orc_sim *s, double *out)
@@ -931,6 +1053,18 @@ void orc_sim_get_ties(const orc_sim *s, int64_t *first_tie, int64_t *first_pt_ti
     for (int r = 0; r < s->R; ++r) first_tie[r] = s->first_tie[r];
     *first_pt_tie = s->first_pt_tie;
     *min_margin = s->min_margin;
+}
+
+void orc_sim_get_tie_counts(const orc_sim *s, int64_t *n_ties)
+{
+    for (int r = 0; r < s->R; ++r) n_ties[r] = s->n_ties[r];
+}
+
+void orc_sim_clear_ties(orc_sim *s)
+{
+    for (int r = 0; r < s->R; ++r) { s->first_tie[r] = -1; s->n_ties[r] = 0; }
+    s->first_pt_tie = -1;
+    s->min_margin = INFINITY;
 }
 
 uint64_t orc_sim_sweep_index(const orc_sim *s) { return s->t; }
