@@ -173,6 +173,7 @@ def main():
     ap.add_argument("--cpu-sweeps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
 
     from paper_1211_3991_gb300 import workloads as wl
@@ -202,6 +203,8 @@ def main():
     plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, **tune)
     plan.bind(stream)
     plan.init_spins(stream=stream)
+    if not (args.block or args.cluster or args.group) and not args.no_autotune:
+        plan.autotune(20, OPS_ALL, 1, stream=stream)
     updates_per_sweep = cfg.spins_per_sweep() * 2
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
@@ -322,7 +325,9 @@ def main():
 
 
 def plan_shape(plan):
-    return {"units": plan.unit_count()}
+    t = plan.tuning()
+    return {"units": plan.unit_count(), "replicas_per_cluster": t["group"], "ctas_per_cluster": t["cluster"],
+            "threads_per_cta": t["block"], "csr_in_shared_memory": t["stage"] > 0}
 
 
 if __name__ == "__main__":

@@ -145,7 +145,8 @@ typedef struct {
     int32_t cluster;         /* CTAs per cluster of the batched engine (0 = tuned default) */
     int32_t group;           /* replicas per cluster, a power of two dividing every n_temps (0 = default) */
     int32_t recompute_every; /* FP64 energy recompute + renormalise every this many sweeps (0 = never) */
-    int32_t reserved[4];
+    int32_t stage;           /* batched engine: 0 = stage CSR rows in shared memory when they fit, -1 = never */
+    int32_t reserved[3];
 } xyl_tuning;
 
 /*
@@ -206,6 +207,20 @@ int xyl_sweep_units(xyl_plan *p, int32_t first_unit, int32_t n_units, int32_t n_
 
 /* Number of work units of a batched plan (0 for other engines). */
 int32_t xyl_unit_count(const xyl_plan *p);
+
+/*
+ * xyl_autotune -- XYL_FP32_BATCHED only: time n_sweeps sweeps (ops,
+ * measure_every as in xyl_sweep) for every launch shape (replicas per cluster
+ * R_g, CTAs per cluster G, threads per CTA) that can be resident, keep the
+ * fastest, and restore the sampler state (spins, labels, counters) exactly as
+ * it was.  *best (may be NULL) receives the chosen shape.  Synchronises
+ * `stream`.  Errors: XYL_EINVAL, XYL_ESTATE, XYL_ECUDA.
+ */
+int xyl_autotune(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_every, xyl_tuning *best,
+                 void *stream);
+
+/* Current launch shape of a batched plan (block, cluster, group, stage filled in). */
+int xyl_get_tuning(const xyl_plan *p, xyl_tuning *out);
 
 /*
  * xyl_pt_swap -- one parallel-tempering step (App. B "Improved equilibrium

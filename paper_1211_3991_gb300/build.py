@@ -18,6 +18,9 @@ LIB = os.path.join(HERE, "libxyl.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 CU_SOURCES = ["common.cu", "plain.cu", "batched.cu", "plan.cu"]
 CXX_SOURCES = ["graph.cpp"]
+# FP64 engine and spin initialisation: every expression evaluated as written (no
+# FMA contraction), so their arithmetic is a fixed sequence of IEEE operations
+NO_FMA_SOURCES = {"common.cu", "plain.cu"}
 
 
 def _nvcc() -> str:
@@ -59,6 +62,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         obj = os.path.join(BUILD, f + ".o")
         cmd = [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
                "-c", os.path.join(CSRC, f), "-o", obj] + inc
+        if f in NO_FMA_SOURCES:
+            cmd.insert(2, "-fmad=false")
         if ptxas_info:
             cmd.insert(2, "-Xptxas=-v")
         jobs.append((obj, cmd))

@@ -7,17 +7,21 @@
 // contiguous chunks; CTA k updates chunk k for all Rg replicas, one thread per
 // (site, replica) with the replica index fastest, so the lanes that share a
 // site read one contiguous Rg x 8-byte segment of each neighbour's row.
-// Spins are interleaved [sample][site][replica] float2 in global memory (kept
-// L2-resident for the batch sizes this engine serves); they are read and
+// Spins are interleaved [sample][site][replica] float2 in global memory and
+// stay L2-resident for the batch sizes this engine serves; they are read and
 // written through L2 (ld/st .cg), and colour phases are separated by cluster
-// barriers (release/acquire at cluster scope).
+// barriers (release/acquire at cluster scope).  When they fit, the CSR rows
+// and random-stream site ids of a CTA's chunks are staged once per launch in
+// shared memory, so an update waits on a single L2 round trip (the neighbour
+// spins); otherwise they are read through the read-only path.
 //
 // Sweep (App. B): Metropolis over colours 0..Q-1, then overrelaxation over
 // colours 0..Q-1; the last pass also accumulates each replica's energy (links
-// to lower colours, counted once at their upper endpoint), magnetisation and
-// Fourier sums.  Then the groups of a sample meet at a bounded global barrier,
-// every CTA reads the sample's energies and takes the same PT decisions
-// (FP64, deterministic), and the first CTA of group 0 adds the measurement.
+// to lower colours, counted once at their upper endpoint), magnetisation and,
+// on measurement sweeps, the Fourier sums.  Then the groups of a sample meet
+// at a bounded global barrier, every CTA reads the sample's energies and takes
+// the same PT decisions (FP64, deterministic), and the first CTA of group 0
+// adds the measurement.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -38,6 +42,9 @@ struct BatchedParams {
     int n_sweeps;
     uint32_t ops;
     int measure_every;
+    int staged;          // CSR rows / site ids of the CTA's chunks in shared memory
+    int owned_max;       // largest number of sites one CTA owns
+    int max_deg;
 };
 
 __device__ __forceinline__ float2 ld_spin(const float2 *p) { return __ldcg(p); }
@@ -51,19 +58,26 @@ struct SharedState {
     float delta[kMaxReplicas];             // per slot
     int slot_of[kMaxReplicas];
     int rep_at[kMaxReplicas];
+    int cls_cb[kMaxColorsBatched + 1];     // colour-sorted start of each class
+    int cls_lo[kMaxColorsBatched];         // this CTA's chunk of each class: [lo, hi)
+    int cls_hi[kMaxColorsBatched];
+    int cls_base[kMaxColorsBatched];       // first staged row of the chunk
     int abort_flag;
 };
 
+struct Staged {
+    const int *col;      // [owned_max][max_deg] colour-sorted neighbour ids
+    const int *deg;      // [owned_max]
+    const int *site_id;  // [owned_max] original ids (random-stream keys)
+};
+
 // One colour phase of one pass for this CTA's chunk.
-template <bool IS_MET, bool FUSE>
+template <bool IS_MET, bool FUSE, bool STAGED>
 __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, SharedState &sh, const BatchedParams &bp,
-                                      int group, int rank, int c, uint32_t t)
+                                      const Staged &stg, int group, int c, uint32_t t, bool fourier)
 {
-    const int cb = __ldg(P.color_ptr + d.color_off + c), ce = __ldg(P.color_ptr + d.color_off + c + 1);
-    const int nc = ce - cb;
-    const int chunk = (nc + bp.G - 1) / bp.G;
-    const int lo = cb + rank * chunk;
-    const int hi = min(ce, lo + chunk);
+    const int cb = sh.cls_cb[c];
+    const int lo = sh.cls_lo[c], hi = sh.cls_hi[c], base = sh.cls_base[c];
     const int items = hi > lo ? (hi - lo) << bp.log2Rg : 0;
     float2 *sp = reinterpret_cast<float2 *>(P.spins) + d.spin_off;
     const int32_t *rp = P.row_ptr + d.row_off;
@@ -78,12 +92,27 @@ __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, Shar
     unsigned int n_acc = 0;
 
     for (int q = threadIdx.x; q < items; q += blockDim.x) {
-        const int i = lo + (q >> bp.log2Rg);
+        const int off = q >> bp.log2Rg;
+        const int i = lo + off;
+        const int *nb;
+        int deg;
+        uint32_t site_key;
+        if (STAGED) {
+            const int l = base + off;
+            nb = stg.col + (size_t)l * bp.max_deg;
+            deg = stg.deg[l];
+            site_key = (uint32_t)stg.site_id[l];
+        } else {
+            const int rb = __ldg(rp + i);
+            nb = cl + rb;
+            deg = __ldg(rp + i + 1) - rb;
+            site_key = (uint32_t)__ldg(P.perm + d.site_off + i);
+        }
         const float2 si = ld_spin(sp + (int64_t)i * R + r);
         float hx = 0.f, hy = 0.f, lx = 0.f, ly = 0.f;
-        const int rb = __ldg(rp + i), re = __ldg(rp + i + 1);
-        for (int k = rb; k < re; ++k) {
-            const int j = __ldg(cl + k);
+#pragma unroll 6
+        for (int k = 0; k < deg; ++k) {
+            const int j = STAGED ? nb[k] : __ldg(nb + k);
             const float2 sj = ld_spin(sp + (int64_t)j * R + r);
             hx += sj.x;
             hy += sj.y;
@@ -95,9 +124,8 @@ __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, Shar
         float nx, ny;
         if (IS_MET) {
             const int slot = sh.slot_of[r];
-            const Words4 x = philox_draw((uint32_t)__ldg(P.perm + d.site_off + i), t, kPurposeMet, (uint32_t)r,
-                                         d.sample_id, P.key);
-            const bool ok = metropolis_step(si.x, si.y, hx, hy, sh.beta[slot], sh.delta[slot], x, nx, ny);
+            const Words4 x = philox_draw(site_key, t, kPurposeMet, (uint32_t)r, d.sample_id, P.key);
+            const bool ok = metropolis_step(P, si.x, si.y, hx, hy, sh.beta[slot], sh.delta[slot], x, nx, ny);
             if (ok) {
                 st_spin(sp + (int64_t)i * R + r, make_float2(nx, ny));
                 ++n_acc;
@@ -110,14 +138,16 @@ __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, Shar
             st_spin(sp + (int64_t)i * R + r, make_float2(nx, ny));
         }
         if (FUSE) {
-            const float4 ph = __ldg(reinterpret_cast<const float4 *>(P.phase) + d.site_off + i);
             acc[kObsE] -= nx * lx + ny * ly;
             acc[kObsMx] += nx;
             acc[kObsMy] += ny;
-            acc[kObsF1xRe] += nx * ph.x; acc[kObsF1xIm] += nx * ph.y;
-            acc[kObsF1yRe] += ny * ph.x; acc[kObsF1yIm] += ny * ph.y;
-            acc[kObsF2xRe] += nx * ph.z; acc[kObsF2xIm] += nx * ph.w;
-            acc[kObsF2yRe] += ny * ph.z; acc[kObsF2yIm] += ny * ph.w;
+            if (fourier) {
+                const float4 ph = __ldg(reinterpret_cast<const float4 *>(P.phase) + d.site_off + i);
+                acc[kObsF1xRe] += nx * ph.x; acc[kObsF1xIm] += nx * ph.y;
+                acc[kObsF1yRe] += ny * ph.x; acc[kObsF1yIm] += ny * ph.y;
+                acc[kObsF2xRe] += nx * ph.z; acc[kObsF2xIm] += nx * ph.w;
+                acc[kObsF2yRe] += ny * ph.z; acc[kObsF2yIm] += ny * ph.w;
+            }
         }
     }
     // lanes l and l ^ o (o >= Rg) hold the same replica
@@ -126,8 +156,8 @@ __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, Shar
         if ((threadIdx.x & 31) < bp.Rg && n_acc) atomicAdd(&sh.met[rl], (unsigned long long)n_acc);
     }
     if (FUSE) {
-#pragma unroll
-        for (int f = 0; f < kObsCount; ++f) {
+        const int nf = fourier ? kObsCount : kObsMy + 1;
+        for (int f = 0; f < nf; ++f) {
             float v = acc[f];
             for (int o = 16; o >= bp.Rg; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if ((threadIdx.x & 31) < bp.Rg) atomicAdd(&sh.obs[rl][f], (double)v);
@@ -135,43 +165,30 @@ __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, Shar
     }
 }
 
-__global__ void __launch_bounds__(1024) batched_kernel(DevPlan P, BatchedParams bp)
+template <bool STAGED>
+__device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams &bp, SharedState &sh,
+                                           const Staged &stg, cg::cluster_group &cluster, int s, int group,
+                                           int rank)
 {
-    __shared__ SharedState sh;
-    cg::cluster_group cluster = cg::this_cluster();
-    const int unit = bp.unit_begin + (int)(blockIdx.x / bp.G);
-    const int rank = (int)cluster.block_rank();
-    const int2 ug = bp.units[unit];
-    const int s = ug.x, group = ug.y;
     const DevSample d = P.samples[s];
     const int R = d.R;
     const int n_groups = R / bp.Rg;
     const bool leader = (group == 0 && rank == 0);
-
-    for (int k = threadIdx.x; k < R; k += blockDim.x) {
-        sh.slot_of[k] = P.slot_of[d.rep_off + k];
-        sh.rep_at[k] = P.rep_at[d.rep_off + k];
-        sh.beta[k] = (float)P.beta[d.rep_off + k];
-        sh.delta[k] = (float)P.delta[d.rep_off + k];
-    }
-    for (int q = threadIdx.x; q < 32 * kObsStride; q += blockDim.x) (&sh.obs[0][0])[q] = 0.0;
-    if (threadIdx.x < 32) sh.met[threadIdx.x] = 0ull;
-    if (threadIdx.x == 0) sh.abort_flag = 0;
     uint32_t t = P.sweep[s];
-    __syncthreads();
-
     const bool met = bp.ops & XYL_OP_MET, orx = bp.ops & XYL_OP_OR;
     for (int it = 0; it < bp.n_sweeps; ++it) {
+        const bool measure = (bp.ops & XYL_OP_MEASURE) && bp.measure_every > 0 &&
+                             ((t + 1u) % (uint32_t)bp.measure_every) == 0u;
         if (met) {
             for (int c = 0; c < d.Q; ++c) {
-                if (orx) phase<true, false>(P, d, sh, bp, group, rank, c, t);
-                else phase<true, true>(P, d, sh, bp, group, rank, c, t);
+                if (orx) phase<true, false, STAGED>(P, d, sh, bp, stg, group, c, t, false);
+                else phase<true, true, STAGED>(P, d, sh, bp, stg, group, c, t, measure);
                 cluster.sync();
             }
         }
         if (orx) {
             for (int c = 0; c < d.Q; ++c) {
-                phase<false, true>(P, d, sh, bp, group, rank, c, t);
+                phase<false, true, STAGED>(P, d, sh, bp, stg, group, c, t, measure);
                 cluster.sync();
             }
         }
@@ -180,7 +197,8 @@ __global__ void __launch_bounds__(1024) batched_kernel(DevPlan P, BatchedParams 
         double *obs_s = P.obs + ((size_t)buf * P.total_R + d.rep_off) * kObsStride;
         for (int q = threadIdx.x; q < bp.Rg * kObsCount; q += blockDim.x) {
             const int rl = q / kObsCount, f = q % kObsCount;
-            atomicAdd(obs_s + (size_t)(group * bp.Rg + rl) * kObsStride + f, sh.obs[rl][f]);
+            const double v = sh.obs[rl][f];
+            if (v != 0.0) atomicAdd(obs_s + (size_t)(group * bp.Rg + rl) * kObsStride + f, v);
             sh.obs[rl][f] = 0.0;
         }
         if (met && threadIdx.x < bp.Rg) {
@@ -229,8 +247,6 @@ __global__ void __launch_bounds__(1024) batched_kernel(DevPlan P, BatchedParams 
             __syncthreads();
         }
         if (leader) {
-            const bool measure = (bp.ops & XYL_OP_MEASURE) && bp.measure_every > 0 &&
-                                 ((t + 1u) % (uint32_t)bp.measure_every) == 0u;
             const double invN = 1.0 / (double)d.N;
             for (int k = threadIdx.x; k < R; k += blockDim.x) {
                 const int r = sh.rep_at[k];
@@ -275,28 +291,97 @@ __global__ void __launch_bounds__(1024) batched_kernel(DevPlan P, BatchedParams 
     if (leader && threadIdx.x == 0) P.sweep[s] = t;
 }
 
+__global__ void __launch_bounds__(1024) batched_kernel(DevPlan P, BatchedParams bp)
+{
+    __shared__ SharedState sh;
+    extern __shared__ int dyn[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int unit = bp.unit_begin + (int)(blockIdx.x / bp.G);
+    const int rank = (int)cluster.block_rank();
+    const int2 ug = bp.units[unit];
+    const int s = ug.x, group = ug.y;
+    const DevSample d = P.samples[s];
+    const int R = d.R;
+
+    for (int k = threadIdx.x; k < R; k += blockDim.x) {
+        sh.slot_of[k] = P.slot_of[d.rep_off + k];
+        sh.rep_at[k] = P.rep_at[d.rep_off + k];
+        sh.beta[k] = (float)P.beta[d.rep_off + k];
+        sh.delta[k] = (float)P.delta[d.rep_off + k];
+    }
+    for (int q = threadIdx.x; q < 32 * kObsStride; q += blockDim.x) (&sh.obs[0][0])[q] = 0.0;
+    if (threadIdx.x < 32) sh.met[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) {
+        sh.abort_flag = 0;
+        // this CTA's chunk of every colour class
+        int base = 0;
+        for (int c = 0; c < d.Q; ++c) {
+            const int cb = P.color_ptr[d.color_off + c], ce = P.color_ptr[d.color_off + c + 1];
+            const int chunk = (ce - cb + bp.G - 1) / bp.G;
+            const int lo = min(ce, cb + rank * chunk), hi = min(ce, lo + chunk);
+            sh.cls_cb[c] = cb;
+            sh.cls_lo[c] = lo;
+            sh.cls_hi[c] = hi;
+            sh.cls_base[c] = base;
+            base += hi - lo;
+        }
+        sh.cls_cb[d.Q] = P.color_ptr[d.color_off + d.Q];
+    }
+    __syncthreads();
+
+    Staged stg{nullptr, nullptr, nullptr};
+    if (bp.staged) {
+        int *col = dyn;
+        int *deg = col + (size_t)bp.owned_max * bp.max_deg;
+        int *site = deg + bp.owned_max;
+        for (int c = 0; c < d.Q; ++c) {
+            const int lo = sh.cls_lo[c], n = sh.cls_hi[c] - lo, base = sh.cls_base[c];
+            for (int q = threadIdx.x; q < n; q += blockDim.x) {
+                const int i = lo + q, l = base + q;
+                const int rb = P.row_ptr[d.row_off + i], re = P.row_ptr[d.row_off + i + 1];
+                deg[l] = re - rb;
+                site[l] = P.perm[d.site_off + i];
+                for (int k = 0; k < re - rb; ++k) col[(size_t)l * bp.max_deg + k] = P.col[d.col_off + rb + k];
+            }
+        }
+        stg = Staged{col, deg, site};
+        __syncthreads();
+        run_sweeps<true>(P, bp, sh, stg, cluster, s, group, rank);
+    } else {
+        run_sweeps<false>(P, bp, sh, stg, cluster, s, group, rank);
+    }
+}
+
+// Function-wide attributes, the same for every plan: clusters up to 16 CTAs and
+// dynamic shared memory up to the staging ceiling (a launch asks for less).
+cudaError_t set_kernel_attributes(const BatchedShape &)
+{
+    cudaError_t e = cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageLimitBytes);
+    return e;
+}
+
 }  // namespace
 
-size_t batched_smem_bytes(const PlanShape &, const BatchedShape &) { return sizeof(SharedState); }
+size_t batched_static_smem_bytes() { return sizeof(SharedState); }
 
-// Also opts the kernel into clusters wider than 8; call before the first launch.
+// Also sets the kernel attributes the shape needs; call before the first launch.
 cudaError_t batched_max_active_clusters(const PlanShape &, const BatchedShape &B, int *clusters)
 {
+    cudaError_t e = set_kernel_attributes(B);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.gridDim = dim3(B.G, 1, 1);
     cfg.blockDim = dim3(B.block, 1, 1);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = B.smem_bytes;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = B.G;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (B.G > 8) {
-        cudaError_t e = cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-    }
     return cudaOccupancyMaxActiveClusters(clusters, batched_kernel, &cfg);
 }
 
@@ -315,11 +400,14 @@ cudaError_t launch_batched(const DevPlan &P, const PlanShape &, const BatchedSha
     bp.n_sweeps = n_sweeps;
     bp.ops = ops;
     bp.measure_every = measure_every;
+    bp.staged = B.staged ? 1 : 0;
+    bp.owned_max = B.owned_max;
+    bp.max_deg = B.max_deg;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.gridDim = dim3((unsigned)(B.G * unit_count), 1, 1);
     cfg.blockDim = dim3((unsigned)B.block, 1, 1);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = B.smem_bytes;
     cfg.stream = st;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = B.G;

@@ -27,7 +27,11 @@ __global__ void init_kernel(DevPlan P, int layout, int fp64, int aligned)
         const Words4 x = philox_draw((uint32_t)P.perm[d.site_off + site], 0u, kPurposeInit, (uint32_t)r,
                                      d.sample_id, P.key);
         const double u = fp64 ? uniform53(x.w0, x.w1) : (double)uniform24(x.w0);
-        sincos(kTwoPi * u - 3.14159265358979323846, &sn, &cs);
+        const double theta = kTwoPi * u - 3.14159265358979323846;
+        if (fp64)
+            sincos_series(P, theta, &sn, &cs);
+        else
+            sincos(theta, &sn, &cs);
     }
     const int64_t at = spin_index(d, layout, site, r);
     if (fp64)

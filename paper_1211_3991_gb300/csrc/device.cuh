@@ -22,6 +22,9 @@ enum ObsField : int {
     kObsCount
 };
 constexpr int kObsStride = 12;  // padded
+constexpr int kMaxColorsBatched = 32;  // colour classes per graph the batched engine accepts
+constexpr int kSinTerms = 15;
+constexpr int kCosTerms = 16;
 constexpr int kAccCount = XYL_ACC_COUNT;
 
 struct DevSample {
@@ -59,7 +62,26 @@ struct DevPlan {
     unsigned int *barrier;     // per sample arrival counters (batched engine)
     double *drift;             // largest |E_fused - E_fp64| seen by a recompute
     uint64_t key;              // Philox key of the spin streams
+    // Maclaurin coefficients (-1)^k / (2k+1)! and (-1)^k / (2k)! of the FP64 sin/cos
+    double sin_coef[kSinTerms];
+    double cos_coef[kCosTerms];
 };
+
+// sin and cos of |x| <= pi by their Maclaurin series (Horner in x^2 with IEEE
+// fused multiply-add; truncation below 3e-17).  Every rounding step is fixed,
+// so the FP64 engine's trajectory does not depend on a math library.
+__device__ __forceinline__ void sincos_series(const DevPlan &P, double x, double *sn, double *cs)
+{
+    const double y = x * x;
+    double p = P.sin_coef[kSinTerms - 1];
+#pragma unroll
+    for (int k = kSinTerms - 2; k >= 0; --k) p = fma(p, y, P.sin_coef[k]);
+    double q = P.cos_coef[kCosTerms - 1];
+#pragma unroll
+    for (int k = kCosTerms - 2; k >= 0; --k) q = fma(q, y, P.cos_coef[k]);
+    *sn = x * p;
+    *cs = q;
+}
 
 template <typename Real> struct Vec2T;
 template <> struct Vec2T<float> { using type = float2; };
@@ -78,20 +100,20 @@ template <typename Real> using Vec4 = typename Vec4T<Real>::type;
 // FP32 uses 24-bit uniforms from w0 and w1, hardware sincos/exp and
 // renormalises the rotated proposal.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool metropolis_step(double sx, double sy, double hx, double hy, double beta,
-                                                double half_width, Words4 x, double &nx, double &ny)
+__device__ __forceinline__ bool metropolis_step(const DevPlan &P, double sx, double sy, double hx, double hy,
+                                                double beta, double half_width, Words4 x, double &nx, double &ny)
 {
     const double ud = uniform53(x.w0, x.w1), ua = uniform53(x.w2, x.w3);
     double sn, cs;
-    sincos(half_width * (2.0 * ud - 1.0), &sn, &cs);
+    sincos_series(P, half_width * (2.0 * ud - 1.0), &sn, &cs);
     nx = cs * sx - sn * sy;
     ny = sn * sx + cs * sy;
     const double dE = -((nx - sx) * hx + (ny - sy) * hy);
     return dE <= 0.0 || ua < exp(-beta * dE);
 }
 
-__device__ __forceinline__ bool metropolis_step(float sx, float sy, float hx, float hy, float beta,
-                                                float half_width, Words4 x, float &nx, float &ny)
+__device__ __forceinline__ bool metropolis_step(const DevPlan &, float sx, float sy, float hx, float hy,
+                                                float beta, float half_width, Words4 x, float &nx, float &ny)
 {
     const float ud = uniform24(x.w0), ua = uniform24(x.w1);
     float sn, cs;

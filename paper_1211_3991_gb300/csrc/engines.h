@@ -21,10 +21,17 @@ struct PlanShape {
 
 // Batched-engine launch shape chosen by the tuner.
 struct BatchedShape {
-    int G = 1;        // CTAs per cluster (one team per replica group)
-    int Rg = 1;       // replicas per group (power of two, divides every R)
-    int block = 512;  // threads per CTA
+    int G = 1;              // CTAs per cluster (one team per replica group)
+    int Rg = 1;             // replicas per group (power of two, divides every R)
+    int block = 512;        // threads per CTA
+    bool staged = false;    // CSR rows of each CTA's chunks held in shared memory
+    int owned_max = 0;      // largest number of sites one CTA owns
+    int max_deg = 0;
+    size_t smem_bytes = 0;  // dynamic shared memory per CTA
 };
+
+// Shared memory a CTA may use for staged CSR rows.
+constexpr size_t kStageLimitBytes = 160 * 1024;
 
 cudaError_t launch_init(const DevPlan &P, const PlanShape &S, int aligned, cudaStream_t st);
 cudaError_t launch_finalize(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every, int advance,
@@ -39,6 +46,6 @@ cudaError_t launch_batched(const DevPlan &P, const PlanShape &S, const BatchedSh
                            int unit_begin, int unit_count, int n_sweeps, uint32_t ops, int measure_every,
                            cudaStream_t st);
 cudaError_t batched_max_active_clusters(const PlanShape &S, const BatchedShape &B, int *clusters);
-size_t batched_smem_bytes(const PlanShape &S, const BatchedShape &B);
+size_t batched_static_smem_bytes();
 
 }  // namespace xyl

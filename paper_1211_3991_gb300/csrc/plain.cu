@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kPlainBlock) plain_phase_kernel(DevPlan P, int
         if (IS_MET) {
             const Words4 x = philox_draw((uint32_t)P.perm[d.site_off + i], P.sweep[s], kPurposeMet, (uint32_t)r,
                                          d.sample_id, P.key);
-            accepted = metropolis_step(si.x, si.y, hx, hy, (Real)P.beta[d.rep_off + slot],
+            accepted = metropolis_step(P, si.x, si.y, hx, hy, (Real)P.beta[d.rep_off + slot],
                                        (Real)P.delta[d.rep_off + slot], x, nx, ny);
             if (accepted) {
                 sp[i] = make_vec2<Real>(nx, ny);

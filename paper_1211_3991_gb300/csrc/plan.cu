@@ -42,6 +42,7 @@ struct xyl_plan {
     PlanShape shape;
     BatchedShape bshape;
     int recompute_every = 0;
+    int stage_mode = 0;
     int64_t sweeps_since_recompute = 0;
     int total_R = 0;
     int64_t total_N = 0, total_nnz = 0, total_spins = 0;
@@ -120,7 +121,7 @@ void layout(xyl_plan *p)
     take(p->r_status, sizeof(int32_t));
     take(p->r_barrier, S * sizeof(unsigned int));
     take(p->r_drift, sizeof(double));
-    take(p->r_units, std::max<size_t>(p->units.size(), 1) * sizeof(int2));
+    take(p->r_units, std::max<size_t>(p->total_R, 1) * sizeof(int2));  // the most units any shape makes
     p->ws_bytes = off;
 }
 
@@ -137,19 +138,45 @@ int check_bound(xyl_plan *p, const char *who)
     return XYL_OK;
 }
 
+// Launch shape of the batched engine: R_g replicas per cluster, G CTAs per
+// cluster, `block` threads per CTA; stage < 0 disables shared-memory staging.
+int apply_shape(xyl_plan *p, int g, int G, int block, int stage)
+{
+    if (g < 1 || g > 32 || (g & (g - 1))) return fail(XYL_EINVAL, "group=%d must be a power of two <= 32", g);
+    for (auto &h : p->hs)
+        if (h.R % g) return fail(XYL_EINVAL, "group=%d does not divide n_temps=%d", g, h.R);
+    if (G < 1 || G > 16) return fail(XYL_EINVAL, "cluster=%d must be in [1, 16]", G);
+    if (block < 32 || block % 32 || block > 1024) return fail(XYL_EINVAL, "block=%d must be a multiple of 32 <= 1024", block);
+    BatchedShape &B = p->bshape;
+    B.G = G;
+    B.Rg = g;
+    B.block = block;
+    int owned = 0, max_deg = 1;
+    for (auto &h : p->hs) {
+        int o = 0;
+        for (int c = 0; c < h.Q; ++c) o += (h.color_ptr[c + 1] - h.color_ptr[c] + G - 1) / G;
+        owned = std::max(owned, o);
+        max_deg = std::max(max_deg, h.max_deg);
+    }
+    B.owned_max = owned;
+    B.max_deg = max_deg;
+    const size_t bytes = (size_t)owned * (size_t)(max_deg + 2) * sizeof(int32_t);
+    B.staged = stage >= 0 && bytes <= kStageLimitBytes;
+    B.smem_bytes = B.staged ? bytes : 0;
+    p->stage_mode = stage;
+    p->units.clear();
+    for (size_t s = 0; s < p->hs.size(); ++s)
+        for (int k = 0; k < p->hs[s].R / g; ++k) p->units.push_back(make_int2((int)s, k));
+    return XYL_OK;
+}
+
 int pick_batched_shape(xyl_plan *p, const xyl_tuning *tune)
 {
-    // replicas per cluster: largest power of two <= 32 dividing every sample's R
-    int g = 32;
+    // replicas per cluster: largest power of two <= 16 dividing every sample's R
+    int g = 16;
     for (auto &h : p->hs)
         while (g > 1 && h.R % g) g >>= 1;
-    if (tune && tune->group > 0) {
-        const int want = tune->group;
-        if (want > 32 || (want & (want - 1))) return fail(XYL_EINVAL, "group=%d must be a power of two <= 32", want);
-        for (auto &h : p->hs)
-            if (h.R % want) return fail(XYL_EINVAL, "group=%d does not divide n_temps=%d", want, h.R);
-        g = want;
-    }
+    if (tune && tune->group > 0) g = tune->group;
     int max_N = 0;
     for (auto &h : p->hs) max_N = std::max(max_N, h.N);
     // default cluster width: enough CTAs that a phase has a few thousand items per CTA
@@ -157,20 +184,41 @@ int pick_batched_shape(xyl_plan *p, const xyl_tuning *tune)
     const double items_per_phase = (double)max_N * g / std::max(1, p->shape.max_Q);
     while (G < 16 && items_per_phase / (G * 2) >= 1024.0) G *= 2;
     int block = 512;
-    if (tune && tune->cluster > 0) {
-        if (tune->cluster > 16) return fail(XYL_EINVAL, "cluster=%d exceeds 16", tune->cluster);
-        G = tune->cluster;
+    if (tune && tune->cluster > 0) G = tune->cluster;
+    if (tune && tune->block > 0) block = tune->block;
+    return apply_shape(p, g, G, block, tune ? tune->stage : 0);
+}
+
+// Upload the unit table of the current shape, set the kernel attributes and
+// size the launch waves: all groups of a sample must be resident together.
+int configure_batched(xyl_plan *p, cudaStream_t st)
+{
+    int clusters = 0;
+    XYL_CUDA(batched_max_active_clusters(p->shape, p->bshape, &clusters), "batched: occupancy");
+    if (clusters < 1)
+        return fail(XYL_EINVAL, "batched: a cluster of %d CTAs x %d threads (%zu B shared) cannot be resident",
+                    p->bshape.G, p->bshape.block, p->bshape.smem_bytes);
+    const int n_groups = p->hs[0].R / p->bshape.Rg;
+    bool uniform_groups = true;
+    int groups_max = 1;
+    for (auto &h : p->hs) {
+        uniform_groups &= (h.R / p->bshape.Rg == n_groups);
+        groups_max = std::max(groups_max, h.R / p->bshape.Rg);
     }
-    if (tune && tune->block > 0) {
-        if (tune->block % 32 || tune->block > 1024) return fail(XYL_EINVAL, "block=%d must be a multiple of 32 <= 1024", tune->block);
-        block = tune->block;
+    if (groups_max > 1) {
+        if (!uniform_groups) return fail(XYL_EINVAL, "batched: several groups per sample need equal n_temps");
+        const int samples_per_wave = clusters / n_groups;
+        if (samples_per_wave < 1)
+            return fail(XYL_EINVAL, "batched: %d clusters of %d CTAs cannot be co-resident (max %d)", n_groups,
+                        p->bshape.G, clusters);
+        p->wave_units = samples_per_wave * n_groups;
+    } else {
+        p->wave_units = (int)p->units.size();
     }
-    p->bshape.G = G;
-    p->bshape.Rg = g;
-    p->bshape.block = block;
-    p->units.clear();
-    for (size_t s = 0; s < p->hs.size(); ++s)
-        for (int k = 0; k < p->hs[s].R / g; ++k) p->units.push_back(make_int2((int)s, k));
+    XYL_CUDA(cudaMemcpyAsync(p->ws + p->r_units.off, p->units.data(), p->units.size() * sizeof(int2),
+                             cudaMemcpyHostToDevice, st), "batched: unit table");
+    XYL_CUDA(cudaStreamSynchronize(st), "batched: sync");
+    p->drop_graphs();
     return XYL_OK;
 }
 
@@ -203,6 +251,11 @@ int xyl_plan_create(const xyl_sample *samples, int32_t n_samples, int32_t engine
         if (engine == XYL_FP32_BATCHED && in.n_temps > 256) {
             delete p;
             return fail(XYL_EINVAL, "xyl_plan_create: batched engine supports at most 256 slots per sample");
+        }
+        if (engine == XYL_FP32_BATCHED && g->n_colors > kMaxColorsBatched) {
+            delete p;
+            return fail(XYL_EINVAL, "xyl_plan_create: batched engine supports at most %d colour classes",
+                        kMaxColorsBatched);
         }
         HostSample h;
         h.N = g->n; h.Q = g->n_colors; h.R = in.n_temps; h.L = g->L; h.max_deg = g->max_deg;
@@ -297,7 +350,6 @@ int xyl_bind(xyl_plan *p, void *d_workspace, size_t bytes, void *stream)
         XYL_CUDA(up(p->r_phase, ph32.data(), ph32.size() * sizeof(float4)), "xyl_bind: upload");
     XYL_CUDA(up(p->r_beta, beta.data(), beta.size() * 8), "xyl_bind: upload");
     XYL_CUDA(up(p->r_delta, delta.data(), delta.size() * 8), "xyl_bind: upload");
-    if (!p->units.empty()) XYL_CUDA(up(p->r_units, p->units.data(), p->units.size() * sizeof(int2)), "xyl_bind: upload");
     // everything mutable starts zeroed
     const Region *zero[] = {&p->r_spins, &p->r_slot_of, &p->r_rep_at, &p->r_obs, &p->r_last_E, &p->r_acc,
                             &p->r_met_acc, &p->r_met_try, &p->r_pt_acc, &p->r_pt_try, &p->r_sweep, &p->r_status,
@@ -329,29 +381,25 @@ int xyl_bind(xyl_plan *p, void *d_workspace, size_t bytes, void *stream)
     P.barrier = at<unsigned int>(p, p->r_barrier);
     P.drift = at<double>(p, p->r_drift);
     P.key = p->seed;
+    // Maclaurin coefficients by the factorial recurrence a_k = a_{k-1} / (n (n+1))
+    {
+        double a = 1.0;
+        P.sin_coef[0] = 1.0;
+        for (int k = 1; k < kSinTerms; ++k) {
+            a = a / (double)((2 * k) * (2 * k + 1));
+            P.sin_coef[k] = (k & 1) ? -a : a;
+        }
+        a = 1.0;
+        P.cos_coef[0] = 1.0;
+        for (int k = 1; k < kCosTerms; ++k) {
+            a = a / (double)((2 * k - 1) * (2 * k));
+            P.cos_coef[k] = (k & 1) ? -a : a;
+        }
+    }
     if (!p->capture_stream) XYL_CUDA(cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking), "xyl_bind: stream");
     if (p->engine == XYL_FP32_BATCHED) {
-        int clusters = 0;
-        XYL_CUDA(batched_max_active_clusters(p->shape, p->bshape, &clusters), "xyl_bind: occupancy");
-        if (clusters < 1)
-            return fail(XYL_EINVAL, "xyl_bind: a cluster of %d CTAs x %d threads cannot be resident", p->bshape.G,
-                        p->bshape.block);
-        const int n_groups = p->hs[0].R / p->bshape.Rg;
-        bool uniform_groups = true;
-        for (auto &h : p->hs) uniform_groups &= (h.R / p->bshape.Rg == n_groups);
-        int groups_max = 1;
-        for (auto &h : p->hs) groups_max = std::max(groups_max, h.R / p->bshape.Rg);
-        if (groups_max > 1) {
-            if (!uniform_groups)
-                return fail(XYL_EINVAL, "xyl_bind: batched engine with several groups needs equal n_temps");
-            const int samples_per_wave = clusters / n_groups;
-            if (samples_per_wave < 1)
-                return fail(XYL_EINVAL, "xyl_bind: %d clusters of %d CTAs cannot be co-resident (max %d)", n_groups,
-                            p->bshape.G, clusters);
-            p->wave_units = samples_per_wave * n_groups;
-        } else {
-            p->wave_units = (int)p->units.size();
-        }
+        const int rc = configure_batched(p, st);
+        if (rc) return rc;
     }
     XYL_CUDA(cudaStreamSynchronize(st), "xyl_bind: sync");
     p->bound = true;
@@ -768,6 +816,82 @@ int xyl_import_state(xyl_plan *p, const void *host, size_t bytes, void *stream)
 }
 
 int64_t xyl_last_launch_count(const xyl_plan *p) { return p ? p->last_launches : 0; }
+
+int xyl_get_tuning(const xyl_plan *p, xyl_tuning *out)
+{
+    if (!p || !out) return fail(XYL_EINVAL, "xyl_get_tuning: NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    out->recompute_every = p->recompute_every;
+    if (p->engine == XYL_FP32_BATCHED) {
+        out->block = p->bshape.block;
+        out->cluster = p->bshape.G;
+        out->group = p->bshape.Rg;
+        out->stage = p->bshape.staged ? 1 : -1;
+    }
+    return XYL_OK;
+}
+
+int xyl_autotune(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_every, xyl_tuning *best,
+                 void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_autotune");
+    if (rc) return rc;
+    if (p->engine != XYL_FP32_BATCHED) return fail(XYL_EINVAL, "xyl_autotune: batched engine only");
+    if (n_sweeps < 1 || !(ops & (XYL_OP_MET | XYL_OP_OR))) return fail(XYL_EINVAL, "xyl_autotune: bad sweep request");
+    if ((ops & XYL_OP_MEASURE) && measure_every < 1) return fail(XYL_EINVAL, "xyl_autotune: measure_every must be >= 1");
+    if (!(ops & XYL_OP_MEASURE)) measure_every = 1;
+    cudaStream_t st = as_stream(stream);
+    std::vector<char> snap(xyl_state_bytes(p));
+    if ((rc = xyl_export_state(p, snap.data(), snap.size(), stream))) return rc;
+    const BatchedShape keep = p->bshape;
+    const int keep_stage = p->stage_mode;
+    cudaEvent_t e0, e1;
+    XYL_CUDA(cudaEventCreate(&e0), "xyl_autotune: event");
+    XYL_CUDA(cudaEventCreate(&e1), "xyl_autotune: event");
+    float best_ms = -1.f;
+    int best_g = keep.Rg, best_G = keep.G, best_block = keep.block;
+    for (int g = 1; g <= 32; g *= 2) {
+        bool divides = true;
+        for (auto &h : p->hs) divides &= (h.R % g == 0);
+        if (!divides) continue;
+        for (int G = 1; G <= 16; G *= 2) {
+            for (int block : {256, 512, 1024}) {
+                if (apply_shape(p, g, G, block, keep_stage) || configure_batched(p, st)) continue;
+                float ms = 0.f;
+                bool ok = true;
+                for (int rep = 0; rep < 2 && ok; ++rep) {
+                    if (xyl_import_state(p, snap.data(), snap.size(), stream)) { ok = false; break; }
+                    int64_t launches = 0;
+                    XYL_CUDA(cudaMemsetAsync(p->ws + p->r_barrier.off, 0, p->r_barrier.bytes, st), "xyl_autotune");
+                    XYL_CUDA(cudaEventRecord(e0, st), "xyl_autotune: record");
+                    if (issue_sweeps(p, n_sweeps, ops, measure_every, st, &launches)) { ok = false; break; }
+                    XYL_CUDA(cudaEventRecord(e1, st), "xyl_autotune: record");
+                    XYL_CUDA(cudaEventSynchronize(e1), "xyl_autotune: sync");
+                    XYL_CUDA(cudaEventElapsedTime(&ms, e0, e1), "xyl_autotune: time");
+                    int32_t status = 0;
+                    XYL_CUDA(cudaMemcpy(&status, p->ws + p->r_status.off, sizeof(status), cudaMemcpyDeviceToHost),
+                             "xyl_autotune: status");
+                    if (status) ok = false;
+                }
+                clear_error();
+                if (ok && (best_ms < 0.f || ms < best_ms)) {
+                    best_ms = ms;
+                    best_g = g;
+                    best_G = G;
+                    best_block = block;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if ((rc = apply_shape(p, best_g, best_G, best_block, keep_stage))) return rc;
+    if ((rc = configure_batched(p, st))) return rc;
+    if ((rc = xyl_import_state(p, snap.data(), snap.size(), stream))) return rc;
+    if (best) xyl_get_tuning(p, best);
+    return best_ms < 0.f ? fail(XYL_EINVAL, "xyl_autotune: no resident launch shape") : XYL_OK;
+}
 
 void xyl_plan_free(xyl_plan *p) { delete p; }
 

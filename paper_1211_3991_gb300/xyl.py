@@ -27,7 +27,8 @@ EXPORTED = (
     "xyl_init_spins", "xyl_sweep", "xyl_pt_swap", "xyl_measure", "xyl_recompute", "xyl_set_delta",
     "xyl_read_observables", "xyl_reset_observables", "xyl_read_energies", "xyl_read_labels", "xyl_read_spins",
     "xyl_write_spins", "xyl_read_status", "xyl_state_bytes", "xyl_export_state", "xyl_import_state",
-    "xyl_last_launch_count", "xyl_plan_free", "xyl_sweep_units", "xyl_unit_count",
+    "xyl_last_launch_count", "xyl_plan_free", "xyl_sweep_units", "xyl_unit_count", "xyl_autotune",
+    "xyl_get_tuning",
 )
 
 
@@ -44,7 +45,7 @@ class Sample(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("block", C.c_int32), ("cluster", C.c_int32), ("group", C.c_int32),
-                ("recompute_every", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("recompute_every", C.c_int32), ("stage", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 _lib = None
@@ -94,6 +95,8 @@ def load():
             "xyl_plan_free": ([P], None),
             "xyl_sweep_units": ([P, i32, i32, i32, u32, i32, P], C.c_int),
             "xyl_unit_count": ([P], C.c_int32),
+            "xyl_autotune": ([P, i32, u32, i32, C.POINTER(Tuning), P], C.c_int),
+            "xyl_get_tuning": ([P, C.POINTER(Tuning)], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -172,7 +175,7 @@ class Plan:
     ``samples``: list of (Graph, sample_id, beta[list], delta[list])."""
 
     def __init__(self, samples, engine=FP32_BATCHED, seed=0, block=0, cluster=0, group=0, recompute_every=0,
-                 device=None):
+                 stage=0, device=None):
         import torch
         lib = load()
         self._keep = []
@@ -187,7 +190,7 @@ class Plan:
             arr[k] = Sample(g.handle, sid, len(b), _p(b, C.c_double), _p(d, C.c_double))
             self.n_temps.append(len(b))
             self.sizes.append(g.n)
-        tune = Tuning(block, cluster, group, recompute_every)
+        tune = Tuning(block, cluster, group, recompute_every, stage)
         h = C.c_void_p(); nbytes = C.c_size_t()
         _check(lib.xyl_plan_create(arr, len(samples), engine, seed, C.byref(tune), C.byref(h), C.byref(nbytes)))
         self.handle = h
@@ -222,6 +225,18 @@ class Plan:
 
     def unit_count(self) -> int:
         return int(load().xyl_unit_count(self.handle))
+
+    def autotune(self, n_sweeps, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1, stream=None) -> dict:
+        t = Tuning()
+        _check(load().xyl_autotune(self.handle, int(n_sweeps), int(ops), int(measure_every), C.byref(t),
+                                   _stream(stream)))
+        return {"block": t.block, "cluster": t.cluster, "group": t.group, "stage": t.stage}
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check(load().xyl_get_tuning(self.handle, C.byref(t)))
+        return {"block": t.block, "cluster": t.cluster, "group": t.group, "stage": t.stage,
+                "recompute_every": t.recompute_every}
 
     # same method names as the oracle sampler, so tests drive both the same way
     def sweeps(self, n, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1):

@@ -3,10 +3,12 @@
 All calls go through the C ABI (ctypes binding).  Bars:
 * FP64 engine vs oracle (53-bit uniforms): every angle within 1e-9 rad, labels
   identical, over the first 10 sweeps (C1, C2).
-* FP32 engines vs oracle (24-bit uniforms): per-sweep energy per spin within
-  1e-5 for every (replica, sweep) before that replica's trajectory separates;
-  the first separation must follow a decision the oracle flags as a near tie
-  (|u - exp(-beta dE)| < 1e-4), and at least half of all pairs are compared.
+* FP32 engines vs oracle (24-bit uniforms): overrelaxation is chaotic (FP32 vs
+  FP64 trajectories decorrelate within about eight sweeps), so every sweep
+  starts the oracle from the GPU's own spins and labels; energy per spin then
+  agrees within 1e-5 and 99% of angles within 1e-4 rad for every (replica,
+  sweep), except where the oracle flags a near-tie decision
+  (|u - exp(-beta dE)| < 3e-5) that FP32 rounding may flip (at most 20%).
 * long runs: <e>, chi, U4, <|m|>, chi(k_min) within 3 sigma (binned jackknife)
   of the oracle.
 * kernels alone against the chain / ring / quadrature / beta = 0 exact results.
@@ -86,39 +88,48 @@ def test_fp64_trajectory_matches_oracle(env, orc, name):
 
 
 # --------------------------------------------------------------- FP32 engines
-def _fp32_compare(plan, sims, samples, n_sweeps, ops, N_of):
-    """Per (sample, replica, sweep): energies agree before the trajectories part."""
-    compared = total = 0
-    first_split = {}
+FP32_TIE_EPS = 3e-5  # > 5x the worst FP32 error of exp(-beta dE) per decision
+
+
+def _fp32_per_sweep(plan, sims, samples, n_sweeps, ops, N_of):
+    """Every sweep starts the oracle from the GPU's own spins and labels, runs
+    one sweep on both, and compares energy per spin (1e-5) and angles (1e-4).
+    A miss is allowed only where the oracle flags a near-tie decision in that
+    sweep (FP32 rounding can flip such a decision); misses stay rare."""
+    compared = explained = 0
+    worst = 0.0
     for t in range(n_sweeps):
+        t_gpu = plan.status()[1]
+        labels = plan.labels()
+        for s in samples:
+            sim = sims[s]
+            sim.set_vectors(np.stack([plan.spins(s, r) for r in range(sim.R)]))
+            sim.set_labels(labels[_rep_slice(plan, s)], t_gpu)
+            sim.set_tie_eps(FP32_TIE_EPS)
+            sim.clear_ties()
         plan.sweep(1, ops)
         E = plan.energies()
+        labels_after = plan.labels()
         for s in samples:
             sim = sims[s]
             sim.sweeps(1, ops)
-            R = sim.R
-            ang = _gpu_angles(plan, s, R)
-            gap = _angle_gap(ang, sim.angles()).max(axis=1)
-            Eg = E[_rep_slice(plan, s)]
-            Eo = sim.energies()
-            for r in range(R):
-                total += 1
-                key = (s, r)
-                if key in first_split:
-                    continue
-                if gap[r] > 1e-3:
-                    first_split[key] = t
-                    continue
+            ties = sim.tie_counts()
+            _, pt_tie, _ = sim.ties()
+            # spins whose local field nearly cancels have an ill-conditioned
+            # reflection: judge angles by their 99th percentile, energies exactly
+            gap = np.percentile(_angle_gap(_gpu_angles(plan, s, sim.R), sim.angles()), 99, axis=1)
+            dE = np.abs(E[_rep_slice(plan, s)] - sim.energies()) / N_of(s)
+            for r in range(sim.R):
                 compared += 1
-                assert abs(Eg[r] - Eo[r]) / N_of(s) < 1e-5, (s, r, t, Eg[r], Eo[r])
-    # the earliest separation of each sample follows a flagged near tie
-    for s in samples:
-        ties, pt_tie, _ = sims[s].ties()
-        splits = [first_split[k] for k in first_split if k[0] == s]
-        if splits:
-            flagged = [x for x in list(ties) + [pt_tie] if x >= 0]
-            assert flagged and min(flagged) <= min(splits), (s, min(splits), flagged)
-    return compared, total
+                if dE[r] < 1e-5 and gap[r] < 1e-4:
+                    worst = max(worst, dE[r])
+                    continue
+                assert ties[r] > 0, (s, r, t, dE[r], gap[r])
+                explained += 1
+            if not np.array_equal(labels_after[_rep_slice(plan, s)], sim.labels()):
+                assert pt_tie >= 0 or ties.sum() > 0, (s, t)
+    assert explained <= 0.2 * compared, (explained, compared)
+    return compared, explained, worst
 
 
 @pytest.mark.parametrize("engine_name", ["FP32_BATCHED", "FP32_PLAIN"])
@@ -131,9 +142,9 @@ def test_fp32_energy_matches_oracle(env, orc, name, engine_name):
     plan.init_spins()
     sims = {0: _oracle_for(orc, wl, cfg, 0, u24=True)}
     assert _angle_gap(_gpu_angles(plan, 0, cfg.n_temps), sims[0].angles()).max() < 1e-6
-    compared, total = _fp32_compare(plan, sims, [0], 10, ALL, lambda s: cfg.graphs[s][0] ** 2)
-    assert compared >= 0.5 * total, (compared, total)
-    assert plan.status()[0] == 0
+    compared, explained, worst = _fp32_per_sweep(plan, sims, [0], 10, ALL, lambda s: cfg.graphs[s][0] ** 2)
+    print(f"{name} {engine_name}: {compared} replica-sweeps, {explained} near-tie misses, worst |dE|/N {worst:.2e}")
+    assert plan.status() == (0, 10)
 
 
 # --------------------------------------------------------------- long runs
@@ -173,6 +184,7 @@ def test_long_run_statistics_c1(env, orc, engine_name):
         a, da = jackknife(ob, fn)
         b, db = jackknife(gb, fn)
         assert abs(a - b) < 3 * np.hypot(da, db), (key, a, da, b, db)
+    plan.sweeps(200, NO_PT)
     st = plan.read_observables()
     rate = st["met_acc"][0] / st["met_try"][0]
     assert 0.35 < rate < 0.65
@@ -280,8 +292,9 @@ def test_full_size_batched_sampled_parity(env, orc, name, sampled):
     plan.init_spins()
     sims = {k: _oracle_for(orc, wl, cfg, k, u24=True) for k in sampled}
     n_sweeps = 2 if name == "C5" else 3
-    compared, total = _fp32_compare(plan, sims, sampled, n_sweeps, ALL, lambda s: cfg.graphs[s][0] ** 2)
-    assert compared >= 0.5 * total, (compared, total)
+    compared, explained, worst = _fp32_per_sweep(plan, sims, sampled, n_sweeps, ALL,
+                                                 lambda s: cfg.graphs[s][0] ** 2)
+    print(f"{name}: {compared} replica-sweeps, {explained} near-tie misses, worst |dE|/N {worst:.2e}")
     status, t = plan.status()
     assert status == 0 and t == n_sweeps
     # invariants over the whole batch
@@ -354,3 +367,44 @@ def test_split_sample_wait_times_out_and_recovers(env):
     plan.init_spins()
     plan.sweep(5, ALL)
     assert plan.status() == (0, 5)
+
+
+def test_launch_shape_does_not_change_the_trajectory(env):
+    """Per-site arithmetic does not depend on the launch shape: replica groups,
+    cluster width, block size and CSR staging give bit-identical spins."""
+    xyl, wl = env
+    cfg = wl.config("C2")
+    graphs = wl.build_graphs(cfg)
+    shapes = [dict(group=16, cluster=16, block=512), dict(group=1, cluster=8, block=256),
+              dict(group=4, cluster=4, block=1024, stage=-1), dict(group=2, cluster=16, block=512)]
+    ref = None
+    for shp in shapes:
+        p, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, **shp)
+        p.bind()
+        p.init_spins()
+        p.sweep(6, ALL)
+        got = (np.stack([p.spins(0, r) for r in range(cfg.n_temps)]), p.labels())
+        if ref is None:
+            ref = got
+        else:
+            assert np.array_equal(got[0], ref[0]), shp
+            assert np.array_equal(got[1], ref[1]), shp
+
+
+def test_autotune_restores_state(env):
+    xyl, wl = env
+    cfg = wl.config("C2")
+    graphs = wl.build_graphs(cfg)
+    a, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs)
+    b, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs)
+    for p in (a, b):
+        p.bind()
+        p.init_spins()
+        p.sweep(3, ALL)
+    best = a.autotune(10)
+    assert best == {k: a.tuning()[k] for k in best}
+    assert a.status() == b.status() == (0, 3)
+    for p in (a, b):
+        p.sweep(4, ALL)
+    for r in range(cfg.n_temps):
+        assert np.array_equal(a.spins(0, r), b.spins(0, r))
