@@ -205,6 +205,26 @@ int xyl_sweep(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_every
 int xyl_sweep_units(xyl_plan *p, int32_t first_unit, int32_t n_units, int32_t n_sweeps, uint32_t ops,
                     int32_t measure_every, void *stream);
 
+/*
+ * xyl_sweep_noalloc -- XYL_FP32_BATCHED only: the same sweeps as xyl_sweep
+ * (same kernel, same results), for callers that cannot obtain device memory
+ * while they run: code embedded in a host application that owns every
+ * allocation, or that must not allocate once its memory budget is fixed.
+ * It allocates nothing and needs no scratch from the caller: the kernel's
+ * scratch (per-replica sums of the sweep and the per-sample barrier counters)
+ * lives in one fixed array of 1 MiB that every GPU using the library holds
+ * until the process exits.  Inputs and outputs stay in the plan's workspace.
+ * The batch must fit that array: 192 B per temperature slot plus 4 B per
+ * sample (about 5400 slots); larger batches get XYL_EINVAL.  The first call
+ * on a device looks up the array's device address (with that device current),
+ * so make it before any stream capture.  All calls share the one array and
+ * each call clears it first: calls that overlap on the GPU (different streams,
+ * plans or threads) race and must be serialised by the caller.  No graph is
+ * used.  Errors: XYL_EINVAL, XYL_ESTATE, XYL_ECUDA.  The paper has no
+ * counterpart of this entry point.
+ */
+int xyl_sweep_noalloc(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_every, void *stream);
+
 /* Number of work units of a batched plan (0 for other engines). */
 int32_t xyl_unit_count(const xyl_plan *p);
 

@@ -25,6 +25,8 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "engines.h"
 
 namespace cg = cooperative_groups;
@@ -362,9 +364,35 @@ cudaError_t set_kernel_attributes(const BatchedShape &)
     return e;
 }
 
+// Scratch for xyl_sweep_noalloc: a fixed array in every GPU's global memory
+// while the library is loaded.  Host code never dereferences this name; it
+// asks the runtime for the device address (see batched_noalloc_scratch).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
 }  // namespace
 
 size_t batched_static_smem_bytes() { return sizeof(SharedState); }
+
+// Device address of the static scratch array on the current device.  The first
+// call on a device looks it up (with that device current) and caches it.
+cudaError_t batched_noalloc_scratch(void **ptr)
+{
+    static std::mutex mu;
+    static void *addr[kMaxDevicesNoAlloc] = {};
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevicesNoAlloc) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = p;
+    }
+    *ptr = addr[dev];
+    return cudaSuccess;
+}
 
 // Also sets the kernel attributes the shape needs; call before the first launch.
 cudaError_t batched_max_active_clusters(const PlanShape &, const BatchedShape &B, int *clusters)

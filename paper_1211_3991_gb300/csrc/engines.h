@@ -33,6 +33,11 @@ struct BatchedShape {
 // Shared memory a CTA may use for staged CSR rows.
 constexpr size_t kStageLimitBytes = 160 * 1024;
 
+// Fixed scratch of xyl_sweep_noalloc (per GPU, for the life of the library).
+constexpr size_t kNoAllocScratchBytes = 1u << 20;
+constexpr int kMaxDevicesNoAlloc = 64;
+cudaError_t batched_noalloc_scratch(void **ptr);
+
 cudaError_t launch_init(const DevPlan &P, const PlanShape &S, int aligned, cudaStream_t st);
 cudaError_t launch_finalize(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every, int advance,
                             int obs_buf_from_sweep, cudaStream_t st);

@@ -555,6 +555,46 @@ int xyl_sweep_units(xyl_plan *p, int32_t first_unit, int32_t n_units, int32_t n_
     return XYL_OK;
 }
 
+int xyl_sweep_noalloc(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_every, void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_sweep_noalloc");
+    if (rc) return rc;
+    if (p->engine != XYL_FP32_BATCHED) return fail(XYL_EINVAL, "xyl_sweep_noalloc: batched engine only");
+    if (n_sweeps < 0) return fail(XYL_EINVAL, "xyl_sweep_noalloc: n_sweeps < 0");
+    if (!(ops & (XYL_OP_MET | XYL_OP_OR))) return fail(XYL_EINVAL, "xyl_sweep_noalloc: ops must include MET or OR");
+    if (ops & ~(XYL_OP_MET | XYL_OP_OR | XYL_OP_PT | XYL_OP_MEASURE))
+        return fail(XYL_EINVAL, "xyl_sweep_noalloc: unknown op bits");
+    if ((ops & XYL_OP_MEASURE) && measure_every < 1)
+        return fail(XYL_EINVAL, "xyl_sweep_noalloc: measure_every must be >= 1");
+    if (!(ops & XYL_OP_MEASURE)) measure_every = 1;
+    // scratch: the two per-replica sum buffers, then the per-sample barrier counters
+    const size_t obs_bytes = 2 * (size_t)p->total_R * kObsStride * sizeof(double);
+    const size_t bar_off = align_up(obs_bytes);
+    const size_t need = bar_off + p->hs.size() * sizeof(unsigned int);
+    if (need > kNoAllocScratchBytes)
+        return fail(XYL_EINVAL, "xyl_sweep_noalloc: batch needs %zu B of scratch, the fixed array holds %zu B "
+                    "(%d slots and %zu samples; use xyl_sweep)", need, kNoAllocScratchBytes, p->total_R, p->hs.size());
+    void *scratch = nullptr;
+    XYL_CUDA(batched_noalloc_scratch(&scratch), "xyl_sweep_noalloc: scratch address");
+    cudaStream_t st = as_stream(stream);
+    char *base = static_cast<char *>(scratch);
+    // both sum buffers and the barrier counters must start at zero
+    XYL_CUDA(cudaMemsetAsync(base, 0, need, st), "xyl_sweep_noalloc: clear scratch");
+    DevPlan P = p->dev;
+    P.obs = reinterpret_cast<double *>(base);
+    P.barrier = reinterpret_cast<unsigned int *>(base + bar_off);
+    p->last_launches = 0;
+    const int total = (int)p->units.size();
+    for (int u = 0; u < total; u += p->wave_units) {
+        const int cnt = std::min(p->wave_units, total - u);
+        XYL_CUDA(launch_batched(P, p->shape, p->bshape, at<int2>(p, p->r_units), u, cnt, n_sweeps, ops, measure_every,
+                                st), "xyl_sweep_noalloc: launch");
+        ++p->last_launches;
+    }
+    return XYL_OK;
+}
+
 int32_t xyl_unit_count(const xyl_plan *p)
 {
     return (p && p->engine == XYL_FP32_BATCHED) ? (int32_t)p->units.size() : 0;

@@ -28,7 +28,7 @@ EXPORTED = (
     "xyl_read_observables", "xyl_reset_observables", "xyl_read_energies", "xyl_read_labels", "xyl_read_spins",
     "xyl_write_spins", "xyl_read_status", "xyl_state_bytes", "xyl_export_state", "xyl_import_state",
     "xyl_last_launch_count", "xyl_plan_free", "xyl_sweep_units", "xyl_unit_count", "xyl_autotune",
-    "xyl_get_tuning",
+    "xyl_get_tuning", "xyl_sweep_noalloc",
 )
 
 
@@ -97,6 +97,7 @@ def load():
             "xyl_unit_count": ([P], C.c_int32),
             "xyl_autotune": ([P, i32, u32, i32, C.POINTER(Tuning), P], C.c_int),
             "xyl_get_tuning": ([P, C.POINTER(Tuning)], C.c_int),
+            "xyl_sweep_noalloc": ([P, i32, u32, i32, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -218,6 +219,10 @@ class Plan:
 
     def sweep(self, n, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1, stream=None):
         _check(load().xyl_sweep(self.handle, int(n), int(ops), int(measure_every), _stream(stream)))
+
+    def sweep_noalloc(self, n, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1, stream=None):
+        """xyl_sweep_noalloc: same sweeps, kernel scratch from the library's fixed array."""
+        _check(load().xyl_sweep_noalloc(self.handle, int(n), int(ops), int(measure_every), _stream(stream)))
 
     def sweep_units(self, first, count, n, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1, stream=None):
         _check(load().xyl_sweep_units(self.handle, int(first), int(count), int(n), int(ops), int(measure_every),
