@@ -110,9 +110,24 @@ def _profile_traffic():
     if vals.get("source_sha256") != digest:
         return None
     try:
-        return {"bytes_per_sweep": float(vals["dram_bytes_per_sweep"]), "sweeps_per_launch": float(vals["sweeps_per_launch"])}
+        return {"bytes_per_launch": float(vals["dram_bytes_per_launch"]),
+                "scales": not vals.get("traffic_scales_with_sweeps", "yes").startswith("no"),
+                "sweeps_per_launch": float(vals["sweeps_per_launch"])}
     except (KeyError, ValueError):
         return None
+
+
+def reduce_over_ranks(elapsed, units, world, device):
+    """Whole-job figures: the slowest rank's time and the units all ranks did."""
+    if world <= 1:
+        return float(elapsed), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
 
 
 def run_oracle_sample(cfg, sweeps, sample_index=0):
@@ -122,7 +137,7 @@ def run_oracle_sample(cfg, sweeps, sample_index=0):
     L, rho, _ = cfg.graphs[sample_index]
     ei, ej, _, _ = oracle.levy_graph(L, wl.Z, rho, wl.GRAPH_SEED, wl.graph_stream_id(cfg, sample_index))
     color, _ = oracle.slo_color(L * L, ei, ej)
-    sim = oracle.Sim(L * L, ei, ej, color, cfg.betas(), cfg.deltas(), wl.SPIN_SEED, sample=wl.sample_id(sample_index),
+    sim = oracle.Sim(L * L, ei, ej, color, cfg.betas(), cfg.deltas(), wl.SPIN_SEED, sample=wl.graph_stream_id(cfg, sample_index),
                      xy=oracle.lattice_xy(L), L=L)
     sim.init()
     t0 = time.perf_counter()
@@ -174,6 +189,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--measure-every", type=int, default=32, help="sweeps between measurements (the paper: 32)")
     args = ap.parse_args()
 
     from paper_1211_3991_gb300 import workloads as wl
@@ -194,9 +210,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    # weak scaling: every rank runs its own disorder realisations (sample ids offset by rank)
-    if world > 1:
-        cfg.graphs = [(L, rho, s + rank * cfg.n_samples) for (L, rho, s) in cfg.graphs]
+    # every rank runs its own disorder realisations; no data-path collective
+    cfg = wl.shard(cfg, rank, world)
     graphs = wl.build_graphs(cfg)
     stream = torch.cuda.current_stream()
     tune = dict(block=args.block, cluster=args.cluster, group=args.group)
@@ -204,7 +219,7 @@ def main():
     plan.bind(stream)
     plan.init_spins(stream=stream)
     if not (args.block or args.cluster or args.group) and not args.no_autotune:
-        plan.autotune(20, OPS_ALL, 1, stream=stream)
+        plan.autotune(32, OPS_ALL, args.measure_every, stream=stream)
     updates_per_sweep = cfg.spins_per_sweep() * 2
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
@@ -214,7 +229,7 @@ def main():
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            p.sweep(sweeps, OPS_ALL, 1, stream=stream)
+            p.sweep(sweeps, OPS_ALL, args.measure_every, stream=stream)
             b.record(stream)
             b.synchronize()
             total_ms += a.elapsed_time(b)
@@ -239,11 +254,7 @@ def main():
     total_ms, launches = timed_steps(plan, args.steps, sweeps)
     clock_info = clocks.stop()
     barrier()
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
-    units = updates_per_sweep * sweeps * args.steps * world
+    max_ms, units = reduce_over_ranks(total_ms, updates_per_sweep * sweeps * args.steps, world, dev)
     value = units / (max_ms / 1e3)
 
     # end to end through the public API with host buffers: per step the slot
@@ -257,13 +268,14 @@ def main():
         for s in range(cfg.n_samples):
             plan.set_delta(s, deltas, stream=stream)
         h2d = deltas.nbytes * cfg.n_samples
-        plan.sweep(sweeps, OPS_ALL, 1, stream=stream)
+        plan.sweep(sweeps, OPS_ALL, args.measure_every, stream=stream)
         obs = plan.read_observables(stream=stream)
         d2h = sum(v.nbytes for v in obs.values())
         plan.reset_observables(stream=stream)
     barrier()
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": updates_per_sweep * sweeps * args.steps / e2e_s * world, "unit": UNIT,
+    e2e_max_s, e2e_units = reduce_over_ranks(e2e_s, updates_per_sweep * sweeps * args.steps, world, dev)
+    e2e = {"value": e2e_units / e2e_max_s, "unit": UNIT,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     status, _ = plan.status(stream=stream)
@@ -289,7 +301,10 @@ def main():
     per_launch_updates = updates_per_sweep * sweeps * args.steps / max(1, launches)
     achieved = hbm_bytes_per_update(R) * per_launch_updates / avg_launch_s / 1e9
     prof = _profile_traffic()
-    traffic = None if prof is None else prof["bytes_per_sweep"] * sweeps * args.steps / max(1, launches)
+    traffic = None
+    if prof is not None and args.config == "C2":
+        per_launch_sweeps = sweeps * args.steps / max(1, launches)
+        traffic = prof["bytes_per_launch"] * (per_launch_sweeps / prof["sweeps_per_launch"] if prof["scales"] else 1.0)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "bytes_per_update": hbm_bytes_per_update(R),
                 "kernel": "batched_kernel"}
@@ -307,8 +322,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{cfg.name}: {cfg.description}", "engine": "FP32_BATCHED",
-                       "sweeps_per_step": sweeps, "samples_per_rank": cfg.n_samples, "temperatures": R,
+                       "sweeps_per_step": sweeps, "samples_on_rank0": cfg.n_samples, "temperatures": R,
                        "l2": "flushed (256 MiB write) between timed steps",
+                       "measure_every": args.measure_every,
                        "cluster": plan_shape(plan), "parallelism": f"dp{world} (independent samples per rank)"},
             "fp64_plain": {"value": fp64, "unit": UNIT, "ratio_fp32_batched_over_fp64_plain":
                            (value / world / fp64) if fp64 else None},

@@ -668,7 +668,9 @@ void orc_sincos_series(double x, double *sn, double *cs)
 /* sums, left to right.                                                       */
 /* Random draws: Metropolis of site i (original id), sweep t, replica r:      */
 /* Philox counter (i, t, MET<<24 | r, sample); 53-bit mode uses u53(w0,w1)    */
-/* for the step and u53(w2,w3) for the test, 24-bit mode u24(w0), u24(w1).    */
+/* for the step and u53(w2,w3) for the test.  24-bit mode: counter            */
+/* (i, t, MET<<24 | r/2, sample) serves replicas 2p and 2p+1, the even one    */
+/* taking u24(w0), u24(w1) and the odd one u24(w2), u24(w3).                  */
 /* Initial angle theta = 2 pi u - pi from counter (i, 0, INIT<<24 | r,        */
 /* sample), S = (cos theta, sin theta) by the series above.  PT pair k at     */
 /* sweep t: counter (k, t, PT<<24, sample), u53(w0,w1).                       */
@@ -861,9 +863,17 @@ static void metropolis_site(orc_sim *s, int r, int v)
     double *x = s->vx + (size_t)r * s->n, *y = s->vy + (size_t)r * s->n;
     int slot = s->slot_of[r];
     uint32_t w[4];
-    draw_block((uint32_t)v, (uint32_t)s->t, PURPOSE_MET, (uint32_t)r, s->sample, s->key, w);
-    double ud = s->u24_mode ? u24(w[0]) : u53(w[0], w[1]);
-    double ua = s->u24_mode ? u24(w[1]) : u53(w[2], w[3]);
+    double ud, ua;
+    if (s->u24_mode) {
+        /* one block serves replicas 2p and 2p+1: (w0, w1) for the even one, (w2, w3) for the odd */
+        draw_block((uint32_t)v, (uint32_t)s->t, PURPOSE_MET, (uint32_t)(r >> 1), s->sample, s->key, w);
+        ud = u24(w[(r & 1) ? 2 : 0]);
+        ua = u24(w[(r & 1) ? 3 : 1]);
+    } else {
+        draw_block((uint32_t)v, (uint32_t)s->t, PURPOSE_MET, (uint32_t)r, s->sample, s->key, w);
+        ud = u53(w[0], w[1]);
+        ua = u53(w[2], w[3]);
+    }
     double hx, hy;
     local_field(s, x, y, v, &hx, &hy);
     double d = s->delta[slot] * (2.0 * ud - 1.0);

@@ -40,21 +40,33 @@ constexpr int kMaxReplicas = 256;
 struct BatchedParams {
     const int2 *units;   // (sample, group) per cluster
     int unit_begin;
-    int G, Rg, log2Rg;
+    int G, Rg;
+    int rv;              // replicas one thread updates (1 or 2)
+    int log2lps;         // log2 of the lanes that share a site (Rg / rv)
     int n_sweeps;
     uint32_t ops;
     int measure_every;
     int staged;          // CSR rows / site ids of the CTA's chunks in shared memory
     int owned_max;       // largest number of sites one CTA owns
     int max_deg;
+    int fixed_deg;       // degree of every site of every sample, 0 if degrees differ
 };
 
 __device__ __forceinline__ float2 ld_spin(const float2 *p) { return __ldcg(p); }
 __device__ __forceinline__ void st_spin(float2 *p, float2 v) { __stcg(p, v); }
+__device__ __forceinline__ float4 ld_spin2(const float2 *p) { return __ldcg(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ void st_spin2(float2 *p, float4 v) { __stcg(reinterpret_cast<float4 *>(p), v); }
+
+// Per-CTA sums of one sweep, per replica of the group: the energy of links to
+// lower colours (fused into the overrelaxation pass) and, on measurement
+// sweeps, magnetisation and Fourier sums (one extra pass over the CTA's sites).
+constexpr int kSums = kObsCount;
+
+constexpr int kMaxWarps = 21;  // 672 threads per CTA at most (96 registers each)
 
 struct SharedState {
-    double obs[32][kObsStride];            // per group replica: fused sums of this CTA
-    unsigned long long met[32];            // per group replica: accepted Metropolis moves
+    float part[kSums][kMaxWarps][32];      // per field, warp, group replica: warp partial sums
+    unsigned int part_met[kMaxWarps][32];  // per warp, group replica: accepted Metropolis moves
     double E[kMaxReplicas];                // energies of every replica of the sample
     float beta[kMaxReplicas];              // per slot
     float delta[kMaxReplicas];             // per slot
@@ -73,101 +85,178 @@ struct Staged {
     const int *site_id;  // [owned_max] original ids (random-stream keys)
 };
 
-// One colour phase of one pass for this CTA's chunk.
-template <bool IS_MET, bool FUSE, bool STAGED>
-__device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, SharedState &sh, const BatchedParams &bp,
-                                      const Staged &stg, int group, int c, uint32_t t, bool fourier)
+// What one thread needs about its replicas during a sweep.
+template <int RV>
+struct Lane {
+    int r0;              // first replica this thread updates (absolute within the sample)
+    float beta[RV], delta[RV];
+    float e[RV];         // energy partial sums (fused)
+    unsigned int acc[RV];
+};
+
+template <int RV>
+__device__ __forceinline__ void load_spins(const float2 *row, float2 (&v)[RV])
+{
+    if constexpr (RV == 2) {
+        const float4 q = ld_spin2(row);
+        v[0] = make_float2(q.x, q.y);
+        v[1] = make_float2(q.z, q.w);
+    } else {
+        v[0] = ld_spin(row);
+    }
+}
+
+template <int RV>
+__device__ __forceinline__ void store_spins(float2 *row, const float2 (&v)[RV])
+{
+    if constexpr (RV == 2)
+        st_spin2(row, make_float4(v[0].x, v[0].y, v[1].x, v[1].y));
+    else
+        st_spin(row, v[0]);
+}
+
+// One colour phase of one pass for this CTA's chunk: one thread per (site,
+// block of RV consecutive replicas).
+template <bool IS_MET, bool FUSE_E, bool STAGED, int RV, int DEG>
+__device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, const SharedState &sh,
+                                      const BatchedParams &bp, const Staged &stg, int c, uint32_t t, Lane<RV> &ln)
 {
     const int cb = sh.cls_cb[c];
     const int lo = sh.cls_lo[c], hi = sh.cls_hi[c], base = sh.cls_base[c];
-    const int items = hi > lo ? (hi - lo) << bp.log2Rg : 0;
-    float2 *sp = reinterpret_cast<float2 *>(P.spins) + d.spin_off;
+    const int items = hi > lo ? (hi - lo) << bp.log2lps : 0;
+    const int R = d.R;
+    const float2 *sp = reinterpret_cast<const float2 *>(P.spins) + d.spin_off + ln.r0;
+    float2 *spw = reinterpret_cast<float2 *>(P.spins) + d.spin_off + ln.r0;
     const int32_t *rp = P.row_ptr + d.row_off;
     const int32_t *cl = P.col + d.col_off;
-    const int R = d.R;
-    const int rl = threadIdx.x & (bp.Rg - 1);
-    const int r = group * bp.Rg + rl;
-
-    float acc[kObsCount];
-#pragma unroll
-    for (int f = 0; f < kObsCount; ++f) acc[f] = 0.0f;
-    unsigned int n_acc = 0;
 
     for (int q = threadIdx.x; q < items; q += blockDim.x) {
-        const int off = q >> bp.log2Rg;
+        const int off = q >> bp.log2lps;
         const int i = lo + off;
         const int *nb;
         int deg;
-        uint32_t site_key;
+        uint32_t site_key = 0;
         if (STAGED) {
             const int l = base + off;
             nb = stg.col + (size_t)l * bp.max_deg;
-            deg = stg.deg[l];
-            site_key = (uint32_t)stg.site_id[l];
+            deg = DEG > 0 ? DEG : stg.deg[l];
+            if (IS_MET) site_key = (uint32_t)stg.site_id[l];
         } else {
             const int rb = __ldg(rp + i);
             nb = cl + rb;
             deg = __ldg(rp + i + 1) - rb;
-            site_key = (uint32_t)__ldg(P.perm + d.site_off + i);
+            if (IS_MET) site_key = (uint32_t)__ldg(P.perm + d.site_off + i);
         }
-        const float2 si = ld_spin(sp + (int64_t)i * R + r);
-        float hx = 0.f, hy = 0.f, lx = 0.f, ly = 0.f;
-#pragma unroll 6
-        for (int k = 0; k < deg; ++k) {
-            const int j = STAGED ? nb[k] : __ldg(nb + k);
-            const float2 sj = ld_spin(sp + (int64_t)j * R + r);
-            hx += sj.x;
-            hy += sj.y;
-            if (FUSE && j < cb) {
-                lx += sj.x;
-                ly += sj.y;
+        float2 s[RV];
+        load_spins<RV>(sp + i * R, s);
+        float hx[RV], hy[RV], lx[RV], ly[RV];
+#pragma unroll
+        for (int v = 0; v < RV; ++v) hx[v] = hy[v] = lx[v] = ly[v] = 0.f;
+        auto gather = [&](int j) {
+            float2 sj[RV];
+            load_spins<RV>(sp + j * R, sj);
+            const bool lower = FUSE_E && j < cb;
+#pragma unroll
+            for (int v = 0; v < RV; ++v) {
+                hx[v] += sj[v].x;
+                hy[v] += sj[v].y;
+                if (lower) {
+                    lx[v] += sj[v].x;
+                    ly[v] += sj[v].y;
+                }
             }
-        }
-        float nx, ny;
-        if (IS_MET) {
-            const int slot = sh.slot_of[r];
-            const Words4 x = philox_draw(site_key, t, kPurposeMet, (uint32_t)r, d.sample_id, P.key);
-            const bool ok = metropolis_step(P, si.x, si.y, hx, hy, sh.beta[slot], sh.delta[slot], x, nx, ny);
-            if (ok) {
-                st_spin(sp + (int64_t)i * R + r, make_float2(nx, ny));
-                ++n_acc;
-            } else {
-                nx = si.x;
-                ny = si.y;
-            }
+        };
+        if (DEG > 0) {
+            // every site has exactly DEG links
+#pragma unroll
+            for (int k = 0; k < DEG; ++k) gather(STAGED ? nb[k] : __ldg(nb + k));
+        } else if (DEG < 0) {
+            // at most -DEG links
+#pragma unroll
+            for (int k = 0; k < -DEG; ++k)
+                if (k < deg) gather(STAGED ? nb[k] : __ldg(nb + k));
         } else {
-            overrelax_step(si.x, si.y, hx, hy, nx, ny);
-            st_spin(sp + (int64_t)i * R + r, make_float2(nx, ny));
+            for (int k = 0; k < deg; ++k) gather(STAGED ? nb[k] : __ldg(nb + k));
         }
-        if (FUSE) {
-            acc[kObsE] -= nx * lx + ny * ly;
-            acc[kObsMx] += nx;
-            acc[kObsMy] += ny;
-            if (fourier) {
-                const float4 ph = __ldg(reinterpret_cast<const float4 *>(P.phase) + d.site_off + i);
-                acc[kObsF1xRe] += nx * ph.x; acc[kObsF1xIm] += nx * ph.y;
-                acc[kObsF1yRe] += ny * ph.x; acc[kObsF1yIm] += ny * ph.y;
-                acc[kObsF2xRe] += nx * ph.z; acc[kObsF2xIm] += nx * ph.w;
-                acc[kObsF2yRe] += ny * ph.z; acc[kObsF2yIm] += ny * ph.w;
+        float2 n[RV];
+        if (IS_MET) {
+            const Words4 x = met_block_f32(site_key, t, ln.r0, d.sample_id, P.key);
+            bool any = false;
+#pragma unroll
+            for (int v = 0; v < RV; ++v) {
+                // replica r0 + v: even replicas take (w0, w1), odd ones (w2, w3)
+                const bool odd = ((ln.r0 + v) & 1) != 0;
+                const bool ok = metropolis_step_f32(s[v].x, s[v].y, hx[v], hy[v], ln.beta[v], ln.delta[v],
+                                                    odd ? x.w2 : x.w0, odd ? x.w3 : x.w1, n[v].x, n[v].y);
+                if (!ok) n[v] = s[v];
+                ln.acc[v] += ok ? 1u : 0u;
+                any |= ok;
             }
+            if (any) store_spins<RV>(spw + i * R, n);
+        } else {
+#pragma unroll
+            for (int v = 0; v < RV; ++v) overrelax_step(s[v].x, s[v].y, hx[v], hy[v], n[v].x, n[v].y);
+            store_spins<RV>(spw + i * R, n);
         }
-    }
-    // lanes l and l ^ o (o >= Rg) hold the same replica
-    if (IS_MET) {
-        for (int o = 16; o >= bp.Rg; o >>= 1) n_acc += __shfl_xor_sync(0xffffffffu, n_acc, o);
-        if ((threadIdx.x & 31) < bp.Rg && n_acc) atomicAdd(&sh.met[rl], (unsigned long long)n_acc);
-    }
-    if (FUSE) {
-        const int nf = fourier ? kObsCount : kObsMy + 1;
-        for (int f = 0; f < nf; ++f) {
-            float v = acc[f];
-            for (int o = 16; o >= bp.Rg; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if ((threadIdx.x & 31) < bp.Rg) atomicAdd(&sh.obs[rl][f], (double)v);
+        if (FUSE_E) {
+#pragma unroll
+            for (int v = 0; v < RV; ++v) ln.e[v] -= n[v].x * lx[v] + n[v].y * ly[v];
         }
     }
 }
 
-template <bool STAGED>
+// Warp partial of a per-thread value of replica lane_rep+v (lanes l and
+// l ^ o, o >= lanes per site, hold the same replicas), stored per warp so that
+// the CTA sum is taken in a fixed order.
+__device__ __forceinline__ void warp_part(SharedState &sh, const BatchedParams &bp, int lane_rep, int v, int f, float x)
+{
+    for (int o = 16; o >= (1 << bp.log2lps); o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) < (1 << bp.log2lps)) sh.part[f][threadIdx.x >> 5][lane_rep + v] = x;
+}
+
+__device__ __forceinline__ void warp_count(SharedState &sh, const BatchedParams &bp, int lane_rep, int v, unsigned x)
+{
+    for (int o = 16; o >= (1 << bp.log2lps); o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) < (1 << bp.log2lps)) sh.part_met[threadIdx.x >> 5][lane_rep + v] = x;
+}
+
+// Magnetisation and Fourier sums of the CTA's own sites (final spins).
+template <int RV>
+__device__ __forceinline__ void measure_own_sites(const DevPlan &P, const DevSample &d, SharedState &sh,
+                                                  const BatchedParams &bp, int r0, int lane_rep)
+{
+    float m[RV][kSums - 1];
+#pragma unroll
+    for (int v = 0; v < RV; ++v)
+#pragma unroll
+        for (int f = 0; f < kSums - 1; ++f) m[v][f] = 0.f;
+    const float2 *sp = reinterpret_cast<const float2 *>(P.spins) + d.spin_off + r0;
+    for (int c = 0; c < d.Q; ++c) {
+        const int lo = sh.cls_lo[c], hi = sh.cls_hi[c];
+        const int items = hi > lo ? (hi - lo) << bp.log2lps : 0;
+        for (int q = threadIdx.x; q < items; q += blockDim.x) {
+            const int i = lo + (q >> bp.log2lps);
+            float2 s[RV];
+            load_spins<RV>(sp + i * d.R, s);
+            const float4 ph = __ldg(reinterpret_cast<const float4 *>(P.phase) + d.site_off + i);
+#pragma unroll
+            for (int v = 0; v < RV; ++v) {
+                m[v][kObsMx - 1] += s[v].x;
+                m[v][kObsMy - 1] += s[v].y;
+                m[v][kObsF1xRe - 1] += s[v].x * ph.x; m[v][kObsF1xIm - 1] += s[v].x * ph.y;
+                m[v][kObsF1yRe - 1] += s[v].y * ph.x; m[v][kObsF1yIm - 1] += s[v].y * ph.y;
+                m[v][kObsF2xRe - 1] += s[v].x * ph.z; m[v][kObsF2xIm - 1] += s[v].x * ph.w;
+                m[v][kObsF2yRe - 1] += s[v].y * ph.z; m[v][kObsF2yIm - 1] += s[v].y * ph.w;
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < RV; ++v)
+#pragma unroll
+        for (int f = 1; f < kSums; ++f) warp_part(sh, bp, lane_rep, v, f, m[v][f - 1]);
+}
+
+template <bool STAGED, int RV, int DEG>
 __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams &bp, SharedState &sh,
                                            const Staged &stg, cg::cluster_group &cluster, int s, int group,
                                            int rank)
@@ -176,57 +265,84 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
     const int R = d.R;
     const int n_groups = R / bp.Rg;
     const bool leader = (group == 0 && rank == 0);
+    const int lane_rep = (threadIdx.x & ((1 << bp.log2lps) - 1)) * RV;  // replica offset within the group
+    Lane<RV> ln;
+    ln.r0 = group * bp.Rg + lane_rep;
     uint32_t t = P.sweep[s];
     const bool met = bp.ops & XYL_OP_MET, orx = bp.ops & XYL_OP_OR;
     for (int it = 0; it < bp.n_sweeps; ++it) {
         const bool measure = (bp.ops & XYL_OP_MEASURE) && bp.measure_every > 0 &&
                              ((t + 1u) % (uint32_t)bp.measure_every) == 0u;
+#pragma unroll
+        for (int v = 0; v < RV; ++v) {
+            const int slot = sh.slot_of[ln.r0 + v];
+            ln.beta[v] = sh.beta[slot];
+            ln.delta[v] = sh.delta[slot];
+            ln.e[v] = 0.f;
+            ln.acc[v] = 0u;
+        }
         if (met) {
             for (int c = 0; c < d.Q; ++c) {
-                if (orx) phase<true, false, STAGED>(P, d, sh, bp, stg, group, c, t, false);
-                else phase<true, true, STAGED>(P, d, sh, bp, stg, group, c, t, measure);
-                cluster.sync();
+                if (orx) phase<true, false, STAGED, RV, DEG>(P, d, sh, bp, stg, c, t, ln);
+                else phase<true, true, STAGED, RV, DEG>(P, d, sh, bp, stg, c, t, ln);
+                if (orx || c + 1 < d.Q) cluster.sync();
             }
         }
         if (orx) {
             for (int c = 0; c < d.Q; ++c) {
-                phase<false, true, STAGED>(P, d, sh, bp, stg, group, c, t, measure);
-                cluster.sync();
+                phase<false, true, STAGED, RV, DEG>(P, d, sh, bp, stg, c, t, ln);
+                if (c + 1 < d.Q) cluster.sync();
             }
         }
-        // publish this CTA's partial sums and acceptance counts
+        // this CTA's sums: fused energies, Metropolis counts, and on measurement
+        // sweeps the magnetisation and Fourier sums of its own (final) sites
+#pragma unroll
+        for (int v = 0; v < RV; ++v) {
+            warp_part(sh, bp, lane_rep, v, kObsE, ln.e[v]);
+            if (met) warp_count(sh, bp, lane_rep, v, ln.acc[v]);
+        }
+        if (measure) {
+            __syncthreads();  // own sites written by other threads of this CTA
+            measure_own_sites<RV>(P, d, sh, bp, ln.r0, lane_rep);
+        }
+        __syncthreads();
+        // CTA sums in warp order (FP32 over at most a few thousand sites), then
+        // FP64 across the CTAs of the sample
         const int buf = (int)(t & 1u);
         double *obs_s = P.obs + ((size_t)buf * P.total_R + d.rep_off) * kObsStride;
-        for (int q = threadIdx.x; q < bp.Rg * kObsCount; q += blockDim.x) {
-            const int rl = q / kObsCount, f = q % kObsCount;
-            const double v = sh.obs[rl][f];
-            if (v != 0.0) atomicAdd(obs_s + (size_t)(group * bp.Rg + rl) * kObsStride + f, v);
-            sh.obs[rl][f] = 0.0;
+        const int nf = measure ? kSums : 1;
+        const int n_warps = (int)(blockDim.x >> 5);
+        for (int q = threadIdx.x; q < bp.Rg * nf; q += blockDim.x) {
+            const int rl = q / nf, f = q % nf;
+            float v = 0.f;
+            for (int w = 0; w < n_warps; ++w) v += sh.part[f][w][rl];
+            atomicAdd(obs_s + (size_t)(group * bp.Rg + rl) * kObsStride + f, (double)v);
         }
         if (met && threadIdx.x < bp.Rg) {
             const int r = group * bp.Rg + threadIdx.x;
-            if (sh.met[threadIdx.x]) atomicAdd(&P.met_acc[d.rep_off + sh.slot_of[r]], sh.met[threadIdx.x]);
-            sh.met[threadIdx.x] = 0ull;
+            unsigned int n = 0;
+            for (int w = 0; w < n_warps; ++w) n += sh.part_met[w][threadIdx.x];
+            if (n) atomicAdd(&P.met_acc[d.rep_off + sh.slot_of[r]], (unsigned long long)n);
         }
-        cluster.sync();
         if (n_groups > 1) {
+            // every CTA of the sample signs in once its sums are out; the first
+            // CTA of each cluster waits for all of them (bounded) and tells the
+            // other CTAs of its cluster the outcome through their shared memory
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) atomicAdd(&P.barrier[s], 1u);
             if (rank == 0 && threadIdx.x == 0) {
-                __threadfence();
-                atomicAdd(&P.barrier[s], 1u);
-                if (!wait_counter_at_least(&P.barrier[s], (unsigned int)(n_groups * (it + 1)), kBarrierPolls)) {
+                int failed = 0;
+                if (!wait_counter_at_least(&P.barrier[s], (unsigned int)(bp.G * n_groups * (it + 1)), kBarrierPolls)) {
                     atomicExch(P.status, XYL_ETIMEOUT);
-                    sh.abort_flag = 1;
+                    failed = 1;
                 }
                 __threadfence();
+                for (int k = 0; k < bp.G; ++k) *cluster.map_shared_rank(&sh.abort_flag, k) = failed;
             }
-            cluster.sync();
-            // the decision comes from rank 0's shared flag so that every CTA of
-            // the cluster takes the same branch (a cluster barrier has no timeout)
-            const int *flag0 = cluster.map_shared_rank(&sh.abort_flag, 0);
-            const int abort_now = *(volatile const int *)flag0;
-            cluster.sync();  // rank 0 stays resident until every CTA has read its flag
-            if (abort_now) break;
         }
+        cluster.sync();
+        if (n_groups > 1 && *(volatile int *)&sh.abort_flag) break;
         for (int k = threadIdx.x; k < R; k += blockDim.x) sh.E[k] = __ldcg(obs_s + (size_t)k * kObsStride + kObsE);
         __syncthreads();
         // parallel tempering, identical in every CTA
@@ -258,16 +374,20 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
                 if (met) P.met_try[d.rep_off + k] += (unsigned long long)d.N;
                 if (measure) {
                     const double *o = obs_s + (size_t)r * kObsStride;
-                    double ov[kObsCount];
-#pragma unroll
-                    for (int f = 0; f < kObsCount; ++f) ov[f] = __ldcg(o + f);
-                    const double e = ov[kObsE] * invN;
-                    const double mx = ov[kObsMx] * invN, my = ov[kObsMy] * invN;
+                    const double e = sh.E[r] * invN;
+                    const double mx = __ldcg(o + kObsMx) * invN, my = __ldcg(o + kObsMy) * invN;
                     const double m2 = mx * mx + my * my;
-                    const double f1 = ov[kObsF1xRe] * ov[kObsF1xRe] + ov[kObsF1xIm] * ov[kObsF1xIm] +
-                                      ov[kObsF1yRe] * ov[kObsF1yRe] + ov[kObsF1yIm] * ov[kObsF1yIm];
-                    const double f2 = ov[kObsF2xRe] * ov[kObsF2xRe] + ov[kObsF2xIm] * ov[kObsF2xIm] +
-                                      ov[kObsF2yRe] * ov[kObsF2yRe] + ov[kObsF2yIm] * ov[kObsF2yIm];
+                    double f1 = 0.0, f2 = 0.0;
+#pragma unroll
+                    for (int f = kObsF1xRe; f <= kObsF1yIm; ++f) {
+                        const double z = __ldcg(o + f);
+                        f1 += z * z;
+                    }
+#pragma unroll
+                    for (int f = kObsF2xRe; f <= kObsF2yIm; ++f) {
+                        const double z = __ldcg(o + f);
+                        f2 += z * z;
+                    }
                     double *a = P.acc + (size_t)(d.rep_off + k) * kAccCount;
                     a[XYL_ACC_N] += 1.0;
                     a[XYL_ACC_E] += e;
@@ -288,12 +408,13 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
             for (int q = threadIdx.x; q < bp.Rg * kObsStride; q += blockDim.x) nxt[q] = 0.0;
         }
         ++t;
-        cluster.sync();
+        __syncthreads();
     }
     if (leader && threadIdx.x == 0) P.sweep[s] = t;
 }
 
-__global__ void __launch_bounds__(1024) batched_kernel(DevPlan P, BatchedParams bp)
+template <bool STAGED, int RV, int DEG>
+__global__ void __maxnreg__(96) batched_kernel(DevPlan P, BatchedParams bp)
 {
     __shared__ SharedState sh;
     extern __shared__ int dyn[];
@@ -311,8 +432,6 @@ __global__ void __launch_bounds__(1024) batched_kernel(DevPlan P, BatchedParams 
         sh.beta[k] = (float)P.beta[d.rep_off + k];
         sh.delta[k] = (float)P.delta[d.rep_off + k];
     }
-    for (int q = threadIdx.x; q < 32 * kObsStride; q += blockDim.x) (&sh.obs[0][0])[q] = 0.0;
-    if (threadIdx.x < 32) sh.met[threadIdx.x] = 0ull;
     if (threadIdx.x == 0) {
         sh.abort_flag = 0;
         // this CTA's chunk of every colour class
@@ -332,7 +451,7 @@ __global__ void __launch_bounds__(1024) batched_kernel(DevPlan P, BatchedParams 
     __syncthreads();
 
     Staged stg{nullptr, nullptr, nullptr};
-    if (bp.staged) {
+    if (STAGED) {
         int *col = dyn;
         int *deg = col + (size_t)bp.owned_max * bp.max_deg;
         int *site = deg + bp.owned_max;
@@ -348,19 +467,35 @@ __global__ void __launch_bounds__(1024) batched_kernel(DevPlan P, BatchedParams 
         }
         stg = Staged{col, deg, site};
         __syncthreads();
-        run_sweeps<true>(P, bp, sh, stg, cluster, s, group, rank);
-    } else {
-        run_sweeps<false>(P, bp, sh, stg, cluster, s, group, rank);
     }
+    run_sweeps<STAGED, RV, DEG>(P, bp, sh, stg, cluster, s, group, rank);
+}
+
+using KernelFn = void (*)(DevPlan, BatchedParams);
+
+// The specialisation for a launch shape: CSR staged or not, one or two
+// replicas per thread, fixed degree 6 / at most 8 / any degree.
+template <bool STAGED, int RV>
+KernelFn pick_deg(const BatchedShape &B)
+{
+    if (B.fixed_deg == 6) return batched_kernel<STAGED, RV, 6>;
+    if (B.max_deg <= 8) return batched_kernel<STAGED, RV, -8>;
+    return batched_kernel<STAGED, RV, 0>;
+}
+
+KernelFn pick_kernel(const BatchedShape &B)
+{
+    const bool rv2 = B.Rg >= 2;
+    if (B.staged) return rv2 ? pick_deg<true, 2>(B) : pick_deg<true, 1>(B);
+    return rv2 ? pick_deg<false, 2>(B) : pick_deg<false, 1>(B);
 }
 
 // Function-wide attributes, the same for every plan: clusters up to 16 CTAs and
 // dynamic shared memory up to the staging ceiling (a launch asks for less).
-cudaError_t set_kernel_attributes(const BatchedShape &)
+cudaError_t set_kernel_attributes(KernelFn k)
 {
-    cudaError_t e = cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageLimitBytes);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageLimitBytes);
     return e;
 }
 
@@ -397,7 +532,8 @@ cudaError_t batched_noalloc_scratch(void **ptr)
 // Also sets the kernel attributes the shape needs; call before the first launch.
 cudaError_t batched_max_active_clusters(const PlanShape &, const BatchedShape &B, int *clusters)
 {
-    cudaError_t e = set_kernel_attributes(B);
+    const KernelFn kernel = pick_kernel(B);
+    cudaError_t e = set_kernel_attributes(kernel);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -410,7 +546,7 @@ cudaError_t batched_max_active_clusters(const PlanShape &, const BatchedShape &B
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(clusters, batched_kernel, &cfg);
+    return cudaOccupancyMaxActiveClusters(clusters, kernel, &cfg);
 }
 
 cudaError_t launch_batched(const DevPlan &P, const PlanShape &, const BatchedShape &B, const int2 *d_units,
@@ -423,14 +559,16 @@ cudaError_t launch_batched(const DevPlan &P, const PlanShape &, const BatchedSha
     bp.unit_begin = unit_begin;
     bp.G = B.G;
     bp.Rg = B.Rg;
-    bp.log2Rg = 0;
-    while ((1 << bp.log2Rg) < B.Rg) ++bp.log2Rg;
+    bp.rv = (B.Rg >= 2) ? 2 : 1;
+    bp.log2lps = 0;
+    while ((1 << bp.log2lps) < B.Rg / bp.rv) ++bp.log2lps;
     bp.n_sweeps = n_sweeps;
     bp.ops = ops;
     bp.measure_every = measure_every;
     bp.staged = B.staged ? 1 : 0;
     bp.owned_max = B.owned_max;
     bp.max_deg = B.max_deg;
+    bp.fixed_deg = B.fixed_deg;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.gridDim = dim3((unsigned)(B.G * unit_count), 1, 1);
@@ -443,7 +581,7 @@ cudaError_t launch_batched(const DevPlan &P, const PlanShape &, const BatchedSha
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, batched_kernel, P, bp);
+    return cudaLaunchKernelEx(&cfg, pick_kernel(B), P, bp);
 }
 
 }  // namespace xyl

@@ -112,18 +112,28 @@ __device__ __forceinline__ bool metropolis_step(const DevPlan &P, double sx, dou
     return dE <= 0.0 || ua < exp(-beta * dE);
 }
 
-__device__ __forceinline__ bool metropolis_step(const DevPlan &, float sx, float sy, float hx, float hy,
-                                                float beta, float half_width, Words4 x, float &nx, float &ny)
+// FP32 draws: one Philox block at counter (site, t, MET<<24 | r/2, sample)
+// serves replicas 2p and 2p+1; the even replica takes (w0, w1), the odd one
+// (w2, w3).
+__device__ __forceinline__ Words4 met_block_f32(uint32_t site, uint32_t t, int r, uint32_t sample, uint64_t key)
 {
-    const float ud = uniform24(x.w0), ua = uniform24(x.w1);
+    return philox_draw(site, t, kPurposeMet, (uint32_t)(r >> 1), sample, key);
+}
+
+__device__ __forceinline__ bool metropolis_step_f32(float sx, float sy, float hx, float hy, float beta,
+                                                    float half_width, uint32_t wd, uint32_t wa, float &nx, float &ny)
+{
+    // explicit roundings: the result does not depend on how a kernel is compiled
+    const float ud = uniform24(wd), ua = uniform24(wa);
     float sn, cs;
-    __sincosf(half_width * (2.0f * ud - 1.0f), &sn, &cs);
-    float px = cs * sx - sn * sy, py = sn * sx + cs * sy;
-    const float inv = rsqrtf(px * px + py * py);
-    nx = px * inv;
-    ny = py * inv;
-    const float dE = -((nx - sx) * hx + (ny - sy) * hy);
-    return dE <= 0.0f || ua < __expf(-beta * dE);
+    __sincosf(__fmul_rn(half_width, __fmaf_rn(2.0f, ud, -1.0f)), &sn, &cs);
+    const float px = __fmaf_rn(cs, sx, __fmul_rn(-sn, sy));
+    const float py = __fmaf_rn(sn, sx, __fmul_rn(cs, sy));
+    const float inv = rsqrtf(__fmaf_rn(px, px, __fmul_rn(py, py)));
+    nx = __fmul_rn(px, inv);
+    ny = __fmul_rn(py, inv);
+    const float dE = -__fmaf_rn(__fsub_rn(nx, sx), hx, __fmul_rn(__fsub_rn(ny, sy), hy));
+    return dE <= 0.0f || ua < __expf(__fmul_rn(-beta, dE));
 }
 
 // Overrelaxation (App. B; Creutz): reflection of s about the local field h,
@@ -143,11 +153,11 @@ __device__ __forceinline__ void overrelax_step(double sx, double sy, double hx, 
 
 __device__ __forceinline__ void overrelax_step(float sx, float sy, float hx, float hy, float &nx, float &ny)
 {
-    const float h2 = hx * hx + hy * hy;
+    const float h2 = __fmaf_rn(hx, hx, __fmul_rn(hy, hy));
     if (h2 > 0.0f) {
-        const float k = __fdividef(2.0f * (sx * hx + sy * hy), h2);
-        nx = k * hx - sx;
-        ny = k * hy - sy;
+        const float k = __fdividef(__fmul_rn(2.0f, __fmaf_rn(sx, hx, __fmul_rn(sy, hy))), h2);
+        nx = __fmaf_rn(k, hx, -sx);
+        ny = __fmaf_rn(k, hy, -sy);
     } else {
         nx = sx;
         ny = sy;

@@ -27,6 +27,7 @@ struct BatchedShape {
     bool staged = false;    // CSR rows of each CTA's chunks held in shared memory
     int owned_max = 0;      // largest number of sites one CTA owns
     int max_deg = 0;
+    int fixed_deg = 0;      // degree shared by every site of every sample, 0 if degrees differ
     size_t smem_bytes = 0;  // dynamic shared memory per CTA
 };
 

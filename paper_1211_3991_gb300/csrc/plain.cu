@@ -56,10 +56,17 @@ __global__ void __launch_bounds__(kPlainBlock) plain_phase_kernel(DevPlan P, int
             }
         }
         if (IS_MET) {
-            const Words4 x = philox_draw((uint32_t)P.perm[d.site_off + i], P.sweep[s], kPurposeMet, (uint32_t)r,
-                                         d.sample_id, P.key);
-            accepted = metropolis_step(P, si.x, si.y, hx, hy, (Real)P.beta[d.rep_off + slot],
-                                       (Real)P.delta[d.rep_off + slot], x, nx, ny);
+            const uint32_t site = (uint32_t)P.perm[d.site_off + i];
+            if constexpr (sizeof(Real) == 8) {
+                const Words4 x = philox_draw(site, P.sweep[s], kPurposeMet, (uint32_t)r, d.sample_id, P.key);
+                accepted = metropolis_step(P, si.x, si.y, hx, hy, P.beta[d.rep_off + slot], P.delta[d.rep_off + slot],
+                                           x, nx, ny);
+            } else {
+                const Words4 x = met_block_f32(site, P.sweep[s], r, d.sample_id, P.key);
+                accepted = metropolis_step_f32(si.x, si.y, hx, hy, (float)P.beta[d.rep_off + slot],
+                                               (float)P.delta[d.rep_off + slot], (r & 1) ? x.w2 : x.w0,
+                                               (r & 1) ? x.w3 : x.w1, nx, ny);
+            }
             if (accepted) {
                 sp[i] = make_vec2<Real>(nx, ny);
             } else {

@@ -146,7 +146,7 @@ int apply_shape(xyl_plan *p, int g, int G, int block, int stage)
     for (auto &h : p->hs)
         if (h.R % g) return fail(XYL_EINVAL, "group=%d does not divide n_temps=%d", g, h.R);
     if (G < 1 || G > 16) return fail(XYL_EINVAL, "cluster=%d must be in [1, 16]", G);
-    if (block < 32 || block % 32 || block > 1024) return fail(XYL_EINVAL, "block=%d must be a multiple of 32 <= 1024", block);
+    if (block < 32 || block % 32 || block > 672) return fail(XYL_EINVAL, "block=%d must be a multiple of 32 <= 672", block);
     BatchedShape &B = p->bshape;
     B.G = G;
     B.Rg = g;
@@ -160,6 +160,13 @@ int apply_shape(xyl_plan *p, int g, int G, int block, int stage)
     }
     B.owned_max = owned;
     B.max_deg = max_deg;
+    int fixed = -1;
+    for (auto &h : p->hs)
+        for (int i = 0; i < h.N && fixed != 0; ++i) {
+            const int dg = h.row_ptr[i + 1] - h.row_ptr[i];
+            fixed = (fixed < 0 || fixed == dg) ? dg : 0;
+        }
+    B.fixed_deg = fixed < 0 ? 0 : fixed;
     const size_t bytes = (size_t)owned * (size_t)(max_deg + 2) * sizeof(int32_t);
     B.staged = stage >= 0 && bytes <= kStageLimitBytes;
     B.smem_bytes = B.staged ? bytes : 0;
@@ -896,7 +903,7 @@ int xyl_autotune(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_ev
         for (auto &h : p->hs) divides &= (h.R % g == 0);
         if (!divides) continue;
         for (int G = 1; G <= 16; G *= 2) {
-            for (int block : {256, 512, 1024}) {
+            for (int block : {128, 256, 512, 640}) {
                 if (apply_shape(p, g, G, block, keep_stage) || configure_batched(p, st)) continue;
                 float ms = 0.f;
                 bool ok = true;

@@ -85,9 +85,24 @@ def config(name: str) -> Config:
     raise KeyError(name)
 
 
-def sample_id(index: int) -> int:
-    """Distinct random-stream id per sample of a batch."""
-    return index
+def shard(cfg: Config, rank: int, world: int) -> Config:
+    """Rank `rank` of `world`: its own disorder realisations.
+
+    Samples are independent (parallel tempering couples only the replicas of
+    one sample), so ranks share no data: with one sample or fewer samples than
+    ranks every rank takes the whole batch under fresh stream ids (weak
+    scaling); otherwise the samples are dealt out round-robin."""
+    import copy
+    out = copy.copy(cfg)
+    if world <= 1:
+        return out
+    if cfg.n_samples < world or cfg.n_samples == 1:
+        out.graphs = [(L, rho, s + rank * cfg.n_samples) for (L, rho, s) in cfg.graphs]
+        out.stream_offset = rank * cfg.n_samples
+    else:
+        out.graphs = cfg.graphs[rank::world]
+        out.stream_ids = list(range(rank, cfg.n_samples, world))
+    return out
 
 
 def build_graphs(cfg: Config, threads: int = 0):
@@ -97,7 +112,6 @@ def build_graphs(cfg: Config, threads: int = 0):
 
     def one(k):
         L, rho, s = cfg.graphs[k]
-        # distinct graph streams per (rho, index) through the sample id
         return xyl.build_graph_csr(L, Z, rho, GRAPH_SEED, graph_stream_id(cfg, k))
 
     with cf.ThreadPoolExecutor(max_workers=threads) as ex:
@@ -105,13 +119,17 @@ def build_graphs(cfg: Config, threads: int = 0):
 
 
 def graph_stream_id(cfg: Config, k: int) -> int:
-    return k
+    """Random-stream id of sample k of a (possibly sharded) configuration."""
+    ids = getattr(cfg, "stream_ids", None)
+    if ids is not None:
+        return ids[k]
+    return k + getattr(cfg, "stream_offset", 0)
 
 
 def make_plan(cfg: Config, engine, graphs=None, seed=SPIN_SEED, **tuning):
     from . import xyl
     graphs = graphs if graphs is not None else build_graphs(cfg)
-    samples = [(g, sample_id(k), cfg.betas(), cfg.deltas()) for k, g in enumerate(graphs)]
+    samples = [(g, graph_stream_id(cfg, k), cfg.betas(), cfg.deltas()) for k, g in enumerate(graphs)]
     if "recompute_every" not in tuning:
         tuning["recompute_every"] = cfg.recompute_every
     return xyl.Plan(samples, engine=engine, seed=seed, **tuning), graphs
