@@ -52,6 +52,11 @@ struct BatchedParams {
     int fixed_deg;       // degree of every site of every sample, 0 if degrees differ
 };
 
+// Cluster barrier in two halves (release on arrival, acquire on wait), so a
+// CTA can do work that does not depend on the other CTAs in between.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ float2 ld_spin(const float2 *p) { return __ldcg(p); }
 __device__ __forceinline__ void st_spin(float2 *p, float2 v) { __stcg(p, v); }
 __device__ __forceinline__ float4 ld_spin2(const float2 *p) { return __ldcg(reinterpret_cast<const float4 *>(p)); }
@@ -117,9 +122,27 @@ __device__ __forceinline__ void store_spins(float2 *row, const float2 (&v)[RV])
 
 // One colour phase of one pass for this CTA's chunk: one thread per (site,
 // block of RV consecutive replicas).
+// Philox block of this thread's first item in colour c (Metropolis pass).
+template <bool STAGED>
+__device__ __forceinline__ Words4 first_draw(const DevPlan &P, const DevSample &d, const SharedState &sh,
+                                             const BatchedParams &bp, const Staged &stg, int c, uint32_t t, int r0)
+{
+    const int lo = sh.cls_lo[c], hi = sh.cls_hi[c];
+    const int items = hi > lo ? (hi - lo) << bp.log2lps : 0;
+    Words4 x{0u, 0u, 0u, 0u};
+    if ((int)threadIdx.x < items) {
+        const int off = (int)threadIdx.x >> bp.log2lps;
+        const uint32_t site = STAGED ? (uint32_t)stg.site_id[sh.cls_base[c] + off]
+                                     : (uint32_t)__ldg(P.perm + d.site_off + lo + off);
+        x = met_block_f32(site, t, r0, d.sample_id, P.key);
+    }
+    return x;
+}
+
 template <bool IS_MET, bool FUSE_E, bool STAGED, int RV, int DEG>
 __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, const SharedState &sh,
-                                      const BatchedParams &bp, const Staged &stg, int c, uint32_t t, Lane<RV> &ln)
+                                      const BatchedParams &bp, const Staged &stg, int c, uint32_t t, Lane<RV> &ln,
+                                      const Words4 &first)
 {
     const int cb = sh.cls_cb[c];
     const int lo = sh.cls_lo[c], hi = sh.cls_hi[c], base = sh.cls_base[c];
@@ -180,7 +203,7 @@ __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, cons
         }
         float2 n[RV];
         if (IS_MET) {
-            const Words4 x = met_block_f32(site_key, t, ln.r0, d.sample_id, P.key);
+            const Words4 x = (q == (int)threadIdx.x) ? first : met_block_f32(site_key, t, ln.r0, d.sample_id, P.key);
             bool any = false;
 #pragma unroll
             for (int v = 0; v < RV; ++v) {
@@ -270,6 +293,7 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
     ln.r0 = group * bp.Rg + lane_rep;
     uint32_t t = P.sweep[s];
     const bool met = bp.ops & XYL_OP_MET, orx = bp.ops & XYL_OP_OR;
+    Words4 first = first_draw<STAGED>(P, d, sh, bp, stg, 0, t, ln.r0);
     for (int it = 0; it < bp.n_sweeps; ++it) {
         const bool measure = (bp.ops & XYL_OP_MEASURE) && bp.measure_every > 0 &&
                              ((t + 1u) % (uint32_t)bp.measure_every) == 0u;
@@ -282,15 +306,22 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
             ln.acc[v] = 0u;
         }
         if (met) {
+            // the next phase's first Philox block is drawn while the cluster
+            // barrier of the previous phase completes
             for (int c = 0; c < d.Q; ++c) {
-                if (orx) phase<true, false, STAGED, RV, DEG>(P, d, sh, bp, stg, c, t, ln);
-                else phase<true, true, STAGED, RV, DEG>(P, d, sh, bp, stg, c, t, ln);
-                if (orx || c + 1 < d.Q) cluster.sync();
+                if (orx) phase<true, false, STAGED, RV, DEG>(P, d, sh, bp, stg, c, t, ln, first);
+                else phase<true, true, STAGED, RV, DEG>(P, d, sh, bp, stg, c, t, ln, first);
+                if (orx || c + 1 < d.Q) {
+                    cluster_arrive();
+                    if (c + 1 < d.Q) first = first_draw<STAGED>(P, d, sh, bp, stg, c + 1, t, ln.r0);
+                    cluster_wait();
+                }
             }
         }
         if (orx) {
+            const Words4 none{0u, 0u, 0u, 0u};
             for (int c = 0; c < d.Q; ++c) {
-                phase<false, true, STAGED, RV, DEG>(P, d, sh, bp, stg, c, t, ln);
+                phase<false, true, STAGED, RV, DEG>(P, d, sh, bp, stg, c, t, ln, none);
                 if (c + 1 < d.Q) cluster.sync();
             }
         }
@@ -341,7 +372,9 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
                 for (int k = 0; k < bp.G; ++k) *cluster.map_shared_rank(&sh.abort_flag, k) = failed;
             }
         }
-        cluster.sync();
+        cluster_arrive();
+        if (met) first = first_draw<STAGED>(P, d, sh, bp, stg, 0, t + 1u, ln.r0);  // next sweep's first draw
+        cluster_wait();
         if (n_groups > 1 && *(volatile int *)&sh.abort_flag) break;
         for (int k = threadIdx.x; k < R; k += blockDim.x) sh.E[k] = __ldcg(obs_s + (size_t)k * kObsStride + kObsE);
         __syncthreads();

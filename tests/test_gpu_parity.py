@@ -418,3 +418,68 @@ def test_autotune_restores_state(env):
         p.sweep(4, ALL)
     for r in range(cfg.n_temps):
         assert np.array_equal(a.spins(0, r), b.spins(0, r))
+
+
+def test_long_run_statistics_reduced_c3(env, orc):
+    """One C3 graph (L=64, rho=3.5) with four temperatures of C3's range under
+    parallel tempering: per slot <e>, chi, U4 and <|m|> of the FP32 batched
+    engine agree with the FP64 oracle within 3 sigma (binned jackknife)."""
+    xyl, wl = env
+    cfg = wl.config("C3")
+    cfg.graphs = cfg.graphs[256:257]
+    cfg.stream_ids = [256]
+    cfg.temperatures = wl.geometric_temperatures(1.5, 3.5, 4)
+    sim = _oracle_for(orc, wl, cfg, 0, u24=False)
+    plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED)
+    plan.bind()
+    plan.init_spins()
+    for s in (sim, plan):
+        s.sweeps(500, ALL)
+        s.reset_acc()
+    ob = bin_means(run_bins(sim, 60, 100, ALL))
+    gb = bin_means(run_bins(plan, 60, 100, ALL))
+    N = 64 * 64
+    fns = {
+        "e": lambda m: m[ACC["e"]],
+        "chi": lambda m: N * (m[ACC["m2"]] - m[ACC["mx"]] ** 2 - m[ACC["my"]] ** 2),
+        "U4": lambda m: m[ACC["m4"]] / m[ACC["m2"]] ** 2 - 1,
+        "absm": lambda m: m[ACC["absm"]],
+    }
+    for k in range(4):
+        for key, fn in fns.items():
+            a, da = jackknife(ob[:, k, :], fn)
+            b, db = jackknife(gb[:, k, :], fn)
+            assert abs(a - b) < 3 * np.hypot(da, db), (k, key, a, da, b, db)
+
+
+@pytest.mark.parametrize("engine_name", ENGINES)
+def test_degenerate_inputs(env, engine_name):
+    """No links, a single site, a zero Metropolis step, an odd number of slots."""
+    xyl, _ = env
+    eng = getattr(xyl, engine_name)
+    # isolated spins: zero field, zero energy; overrelaxation leaves them alone and
+    # every Metropolis move is accepted (dE = 0)
+    p = _edge_plan(xyl, [], 5, [1.0, 0.5, 2.0], [1.0, 1.0, 1.0], eng)
+    s0 = np.stack([p.spins(0, r) for r in range(3)])
+    p.sweep(3, 2 | 4 | 8)
+    assert np.array_equal(np.stack([p.spins(0, r) for r in range(3)]), s0)
+    assert np.all(p.energies() == 0.0)
+    p.sweep(3, ALL)
+    st = p.read_observables()
+    assert np.array_equal(st["met_acc"], st["met_try"])
+    assert np.all(st["pt_acc"][:2] == st["pt_try"][:2])  # equal energies: every swap accepted
+    assert np.allclose(np.hypot(*np.stack([p.spins(0, r) for r in range(3)]).reshape(-1, 2).T), 1, atol=1e-6)
+    # one site, one slot
+    p = _edge_plan(xyl, [], 1, [1.0], [0.5], eng)
+    p.sweep(4, ALL)
+    st = p.read_observables()
+    assert st["acc"][0, ACC["n"]] == 4 and abs(st["acc"][0, ACC["m2"]] - 4.0) < 1e-5
+    # Delta = 0: proposals equal the current spin, so Metropolis changes nothing
+    g = xyl.build_graph_csr(8, 6, 3.5, 1, 0)
+    p = xyl.Plan([(g, 0, [1.0, 0.7, 0.4], [0.0, 0.0, 0.0])], engine=eng, seed=4)
+    p.bind()
+    p.init_spins()
+    s0 = np.stack([p.spins(0, r) for r in range(3)])
+    p.sweep(5, 1 | 4 | 8)
+    assert np.max(np.abs(np.stack([p.spins(0, r) for r in range(3)]) - s0)) < 1e-6
+    assert p.status() == (0, 5)
