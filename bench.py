@@ -94,20 +94,33 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _profile_traffic():
-    """DRAM bytes per launch of the batched kernel from the committed ncu summary,
-    valid only while the kernel source is unchanged since the capture."""
-    path = os.path.join(ROOT, "profiles", "batched_kernel_C2.md")
-    src = os.path.join(ROOT, "paper_1211_3991_gb300", "csrc", "batched.cu")
-    if not os.path.exists(path):
+KERNEL_SOURCES = {
+    "batched_kernel": ["batched.cu"],
+    "resident_kernel": ["resident.cu"],
+}
+SHARED_SOURCES = ["engines.h", "device.cuh", "philox.cuh", "sweep_tail.cuh"]
+
+
+def kernel_source_digest(kernel):
+    """SHA-256 over a kernel's source file and the headers it includes."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel] + SHARED_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1211_3991_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def _profile_traffic(kernel, config):
+    """DRAM bytes per launch of `kernel` on `config` from the committed ncu
+    summary, valid only while the kernel's sources are unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{config}.md")
+    if not os.path.exists(path) or kernel not in KERNEL_SOURCES:
         return None
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
     vals = {}
     for line in open(path):
         if ":" in line and line.startswith("- "):
             k, v = line[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("source_sha256") != digest:
+    if vals.get("source_sha256") != kernel_source_digest(kernel):
         return None
     try:
         return {"bytes_per_launch": float(vals["dram_bytes_per_launch"]),
@@ -184,6 +197,8 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--cluster", type=int, default=0)
     ap.add_argument("--group", type=int, default=0)
+    ap.add_argument("--resident", type=int, default=0, choices=[-1, 0, 1],
+                    help="1 = spins in shared memory for a launch, -1 = global-memory shape, 0 = library/autotuner")
     ap.add_argument("--ref-sweeps", type=int, default=4)
     ap.add_argument("--cpu-sweeps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -214,7 +229,7 @@ def main():
     cfg = wl.shard(cfg, rank, world)
     graphs = wl.build_graphs(cfg)
     stream = torch.cuda.current_stream()
-    tune = dict(block=args.block, cluster=args.cluster, group=args.group)
+    tune = dict(block=args.block, cluster=args.cluster, group=args.group, resident=args.resident)
     plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, **tune)
     plan.bind(stream)
     plan.init_spins(stream=stream)
@@ -300,14 +315,14 @@ def main():
     avg_launch_s = (total_ms / 1e3) / max(1, launches)
     per_launch_updates = updates_per_sweep * sweeps * args.steps / max(1, launches)
     achieved = hbm_bytes_per_update(R) * per_launch_updates / avg_launch_s / 1e9
-    prof = _profile_traffic()
+    prof = _profile_traffic(kernel_name(plan), args.config)
     traffic = None
-    if prof is not None and args.config == "C2":
+    if prof is not None:
         per_launch_sweeps = sweeps * args.steps / max(1, launches)
         traffic = prof["bytes_per_launch"] * (per_launch_sweeps / prof["sweeps_per_launch"] if prof["scales"] else 1.0)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "bytes_per_update": hbm_bytes_per_update(R),
-                "kernel": "batched_kernel"}
+                "kernel": kernel_name(plan)}
     l2_achieved = l2_bytes_per_update(R) * per_launch_updates / avg_launch_s / 1e9
 
     cpu = None
@@ -342,8 +357,12 @@ def main():
 
 def plan_shape(plan):
     t = plan.tuning()
-    return {"units": plan.unit_count(), "replicas_per_cluster": t["group"], "ctas_per_cluster": t["cluster"],
-            "threads_per_cta": t["block"], "csr_in_shared_memory": t["stage"] > 0}
+    return {"spins_in_shared_memory": t["resident"] > 0, "units": plan.unit_count(), "replicas_per_group": t["group"],
+            "ctas_per_cluster": t["cluster"], "threads_per_cta": t["block"], "csr_in_shared_memory": t["stage"] > 0}
+
+
+def kernel_name(plan):
+    return "resident_kernel" if plan.tuning()["resident"] > 0 else "batched_kernel"
 
 
 if __name__ == "__main__":

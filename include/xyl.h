@@ -146,8 +146,24 @@ typedef struct {
     int32_t group;           /* replicas per cluster, a power of two dividing every n_temps (0 = default) */
     int32_t recompute_every; /* FP64 energy recompute + renormalise every this many sweeps (0 = never) */
     int32_t stage;           /* batched engine: 0 = stage CSR rows in shared memory when they fit, -1 = never */
-    int32_t reserved[3];
+    int32_t resident;        /* batched engine: 1 = resident shape, -1 = never, 0 = library's choice (below) */
+    int32_t reserved[2];
 } xyl_tuning;
+
+/*
+ * Resident shape of the batched engine.  One CTA owns a group of `group`
+ * replicas of one sample and keeps their spins of every site in shared memory
+ * for the whole launch ((n + 1) x group x 8 bytes, with the per-warp partial
+ * sums, within 220 KB); the n_temps / group CTAs of a sample form one cluster
+ * (at most 16), so every sample must have the same n_temps and degree <= 8.
+ * Colour phases then touch no global memory; the CSR rows (16-bit ids) and
+ * the site ids are staged beside the spins when they fit (stage >= 0), else
+ * read from global memory.  Spins are bit-equal to the global-memory shape's
+ * from the same state.  On input `cluster` is ignored for this shape; on output
+ * (xyl_get_tuning, xyl_autotune) it holds the cluster size.  The library's
+ * choice (resident = 0) is the resident shape when it fits with group >= 1,
+ * else the global-memory shape.
+ */
 
 /*
  * xyl_plan_create -- lay out a batch of n_samples samples (each with its own
@@ -199,7 +215,9 @@ int xyl_sweep(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_every
  * a sample must be included for parallel tempering to proceed: a sample whose
  * groups are split across calls makes the in-kernel wait for the missing
  * groups give up after about a second, set the status word to XYL_ETIMEOUT
- * and return (the GPU context stays usable; xyl_init_spins clears it).
+ * and return (the GPU context stays usable; xyl_init_spins clears it).  In
+ * the resident shape a cluster is a whole sample, so the range must cover
+ * whole samples (XYL_EINVAL otherwise).
  * Errors: XYL_EINVAL (wrong engine or range), XYL_ESTATE, XYL_ECUDA.
  */
 int xyl_sweep_units(xyl_plan *p, int32_t first_unit, int32_t n_units, int32_t n_sweeps, uint32_t ops,

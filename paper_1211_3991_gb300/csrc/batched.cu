@@ -28,6 +28,7 @@
 #include <mutex>
 
 #include "engines.h"
+#include "sweep_tail.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -35,7 +36,6 @@ namespace xyl {
 namespace {
 
 constexpr unsigned int kBarrierPolls = 1u << 21;  // about a second of polling
-constexpr int kMaxReplicas = 256;
 
 struct BatchedParams {
     const int2 *units;   // (sample, group) per cluster
@@ -51,11 +51,6 @@ struct BatchedParams {
     int max_deg;
     int fixed_deg;       // degree of every site of every sample, 0 if degrees differ
 };
-
-// Cluster barrier in two halves (release on arrival, acquire on wait), so a
-// CTA can do work that does not depend on the other CTAs in between.
-__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
-__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ float2 ld_spin(const float2 *p) { return __ldcg(p); }
 __device__ __forceinline__ void st_spin(float2 *p, float2 v) { __stcg(p, v); }
@@ -378,62 +373,7 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
         if (n_groups > 1 && *(volatile int *)&sh.abort_flag) break;
         for (int k = threadIdx.x; k < R; k += blockDim.x) sh.E[k] = __ldcg(obs_s + (size_t)k * kObsStride + kObsE);
         __syncthreads();
-        // parallel tempering, identical in every CTA
-        if (bp.ops & XYL_OP_PT) {
-            for (int p = threadIdx.x; 2 * p + (int)(t & 1u) + 1 < R; p += blockDim.x) {
-                const int k = 2 * p + (int)(t & 1u);
-                const int a = sh.rep_at[k], b = sh.rep_at[k + 1];
-                const double x = (P.beta[d.rep_off + k] - P.beta[d.rep_off + k + 1]) * (sh.E[a] - sh.E[b]);
-                const Words4 w = philox_draw((uint32_t)k, t, kPurposePt, 0u, d.sample_id, P.key);
-                const bool accept = uniform53(w.w0, w.w1) < exp(x);
-                if (leader) P.pt_try[d.rep_off + k] += 1ull;
-                if (accept) {
-                    sh.rep_at[k] = b;
-                    sh.rep_at[k + 1] = a;
-                    sh.slot_of[b] = k;
-                    sh.slot_of[a] = k + 1;
-                    if (leader) P.pt_acc[d.rep_off + k] += 1ull;
-                }
-            }
-            __syncthreads();
-        }
-        if (leader) {
-            const double invN = 1.0 / (double)d.N;
-            for (int k = threadIdx.x; k < R; k += blockDim.x) {
-                const int r = sh.rep_at[k];
-                P.rep_at[d.rep_off + k] = r;
-                P.slot_of[d.rep_off + r] = k;
-                P.last_E[d.rep_off + k] = sh.E[k];
-                if (met) P.met_try[d.rep_off + k] += (unsigned long long)d.N;
-                if (measure) {
-                    const double *o = obs_s + (size_t)r * kObsStride;
-                    const double e = sh.E[r] * invN;
-                    const double mx = __ldcg(o + kObsMx) * invN, my = __ldcg(o + kObsMy) * invN;
-                    const double m2 = mx * mx + my * my;
-                    double f1 = 0.0, f2 = 0.0;
-#pragma unroll
-                    for (int f = kObsF1xRe; f <= kObsF1yIm; ++f) {
-                        const double z = __ldcg(o + f);
-                        f1 += z * z;
-                    }
-#pragma unroll
-                    for (int f = kObsF2xRe; f <= kObsF2yIm; ++f) {
-                        const double z = __ldcg(o + f);
-                        f2 += z * z;
-                    }
-                    double *a = P.acc + (size_t)(d.rep_off + k) * kAccCount;
-                    a[XYL_ACC_N] += 1.0;
-                    a[XYL_ACC_E] += e;
-                    a[XYL_ACC_E2] += e * e;
-                    a[XYL_ACC_ABSM] += sqrt(m2);
-                    a[XYL_ACC_MX] += mx;
-                    a[XYL_ACC_MY] += my;
-                    a[XYL_ACC_M2] += m2;
-                    a[XYL_ACC_M4] += m2 * m2;
-                    a[XYL_ACC_CHIK] += (f1 + f2) * 0.5 * invN;
-                }
-            }
-        }
+        pt_and_record(P, d, sh.E, sh.rep_at, sh.slot_of, t, bp.ops, leader, met, measure, obs_s);
         // clear this group's slots of the buffer the next sweep fills: every
         // reader of it finished before the barrier just passed
         if (rank == 0) {

@@ -29,10 +29,19 @@ struct BatchedShape {
     int max_deg = 0;
     int fixed_deg = 0;      // degree shared by every site of every sample, 0 if degrees differ
     size_t smem_bytes = 0;  // dynamic shared memory per CTA
+    // resident shape: one CTA per replica group holds the group's spins of
+    // every site in shared memory; the groups of a sample form one cluster
+    bool resident = false;
+    int cpc = 1;            // CTAs per cluster of the resident shape (groups per sample)
+    int rs_csr_w = 0;       // staged CSR row width (16-bit ids), 0 = rows from global memory
+    bool rs_ids = false;    // random-stream site ids staged (16-bit)
+    size_t rs_off_ids = 0, rs_off_col = 0, rs_off_part = 0, rs_off_met = 0;
 };
 
 // Shared memory a CTA may use for staged CSR rows.
 constexpr size_t kStageLimitBytes = 160 * 1024;
+// Dynamic shared memory of a resident-shape CTA (spins, staged tables, partial sums).
+constexpr size_t kResidentDynLimitBytes = 220 * 1024;
 
 // Fixed scratch of xyl_sweep_noalloc (per GPU, for the life of the library).
 constexpr size_t kNoAllocScratchBytes = 1u << 20;
@@ -53,5 +62,11 @@ cudaError_t launch_batched(const DevPlan &P, const PlanShape &S, const BatchedSh
                            cudaStream_t st);
 cudaError_t batched_max_active_clusters(const PlanShape &S, const BatchedShape &B, int *clusters);
 size_t batched_static_smem_bytes();
+
+// Resident shape: one launch over samples [sample_begin, sample_begin + sample_count).
+cudaError_t launch_resident(const DevPlan &P, const BatchedShape &B, int sample_begin, int sample_count,
+                            int n_sweeps, uint32_t ops, int measure_every, cudaStream_t st);
+cudaError_t resident_max_active_clusters(const BatchedShape &B, int *clusters);
+size_t resident_static_smem_bytes();
 
 }  // namespace xyl

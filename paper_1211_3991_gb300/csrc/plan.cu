@@ -43,6 +43,7 @@ struct xyl_plan {
     BatchedShape bshape;
     int recompute_every = 0;
     int stage_mode = 0;
+    int resident_req = 0;   // the caller's resident setting: 1 only, -1 never, 0 either
     int64_t sweeps_since_recompute = 0;
     int total_R = 0;
     int64_t total_N = 0, total_nnz = 0, total_spins = 0;
@@ -138,9 +139,59 @@ int check_bound(xyl_plan *p, const char *who)
     return XYL_OK;
 }
 
-// Launch shape of the batched engine: R_g replicas per cluster, G CTAs per
-// cluster, `block` threads per CTA; stage < 0 disables shared-memory staging.
-int apply_shape(xyl_plan *p, int g, int G, int block, int stage)
+// Shared-memory layout of the resident shape for groups of g replicas and
+// `block` threads: spins (with one zero row) | warp partial sums | accepted
+// counts | 16-bit site ids | 16-bit CSR rows, the last two when they fit.
+// Returns false when the shape does not apply to this batch.
+bool resident_fit(const xyl_plan *p, int g, int block, int stage, BatchedShape &B)
+{
+    const int R0 = p->hs[0].R;
+    int max_N = 0, max_deg = 0;
+    for (auto &h : p->hs) {
+        if (h.R != R0) return false;
+        max_N = std::max(max_N, h.N);
+        max_deg = std::max(max_deg, h.max_deg);
+    }
+    if (R0 % g || R0 / g > 16 || max_deg > 8) return false;
+    auto a16 = [](size_t v) { return (v + 15) / 16 * 16; };
+    const size_t n_warps = (size_t)block / 32;
+    const size_t spins = a16((size_t)(max_N + 1) * g * sizeof(float2));
+    const size_t part = a16((size_t)kObsCount * n_warps * g * sizeof(float));
+    const size_t met = a16(n_warps * g * sizeof(unsigned));
+    size_t off = spins + part + met;
+    if (off > kResidentDynLimitBytes) return false;
+    B.rs_off_part = spins;
+    B.rs_off_met = spins + part;
+    B.rs_ids = false;
+    B.rs_csr_w = 0;
+    B.rs_off_ids = B.rs_off_col = 0;
+    if (max_N <= 65535) {  // ids and the padding id N fit 16 bits
+        const size_t ids = a16((size_t)max_N * sizeof(uint16_t));
+        if (off + ids <= kResidentDynLimitBytes) {
+            B.rs_ids = true;
+            B.rs_off_ids = off;
+            off += ids;
+        }
+        const int W = B.fixed_deg == 6 ? 6 : 8;
+        const size_t col = a16((size_t)max_N * W * sizeof(uint16_t));
+        if (stage >= 0 && off + col <= kResidentDynLimitBytes) {
+            B.rs_csr_w = W;
+            B.rs_off_col = off;
+            off += col;
+        }
+    }
+    B.resident = true;
+    B.cpc = R0 / g;
+    B.G = 1;
+    B.staged = B.rs_csr_w != 0;
+    B.smem_bytes = off;
+    return true;
+}
+
+// Launch shape of the batched engine: R_g replicas per group, G CTAs per
+// cluster, `block` threads per CTA; stage < 0 disables shared-memory staging;
+// resident != 0 asks for the resident shape (G is then ignored).
+int apply_shape(xyl_plan *p, int g, int G, int block, int stage, int resident)
 {
     if (g < 1 || g > 32 || (g & (g - 1))) return fail(XYL_EINVAL, "group=%d must be a power of two <= 32", g);
     for (auto &h : p->hs)
@@ -148,17 +199,12 @@ int apply_shape(xyl_plan *p, int g, int G, int block, int stage)
     if (G < 1 || G > 16) return fail(XYL_EINVAL, "cluster=%d must be in [1, 16]", G);
     if (block < 32 || block % 32 || block > 672) return fail(XYL_EINVAL, "block=%d must be a multiple of 32 <= 672", block);
     BatchedShape &B = p->bshape;
+    B = BatchedShape{};
     B.G = G;
     B.Rg = g;
     B.block = block;
-    int owned = 0, max_deg = 1;
-    for (auto &h : p->hs) {
-        int o = 0;
-        for (int c = 0; c < h.Q; ++c) o += (h.color_ptr[c + 1] - h.color_ptr[c] + G - 1) / G;
-        owned = std::max(owned, o);
-        max_deg = std::max(max_deg, h.max_deg);
-    }
-    B.owned_max = owned;
+    int max_deg = 1;
+    for (auto &h : p->hs) max_deg = std::max(max_deg, h.max_deg);
     B.max_deg = max_deg;
     int fixed = -1;
     for (auto &h : p->hs)
@@ -167,18 +213,50 @@ int apply_shape(xyl_plan *p, int g, int G, int block, int stage)
             fixed = (fixed < 0 || fixed == dg) ? dg : 0;
         }
     B.fixed_deg = fixed < 0 ? 0 : fixed;
-    const size_t bytes = (size_t)owned * (size_t)(max_deg + 2) * sizeof(int32_t);
-    B.staged = stage >= 0 && bytes <= kStageLimitBytes;
-    B.smem_bytes = B.staged ? bytes : 0;
     p->stage_mode = stage;
     p->units.clear();
     for (size_t s = 0; s < p->hs.size(); ++s)
         for (int k = 0; k < p->hs[s].R / g; ++k) p->units.push_back(make_int2((int)s, k));
+    if (resident) {
+        if (!resident_fit(p, g, block, stage, B))
+            return fail(XYL_EINVAL, "resident shape with group=%d does not fit this batch (equal n_temps, n_temps/group "
+                        "<= 16, degree <= 8, spins within %zu B of shared memory)", g, kResidentDynLimitBytes);
+        return XYL_OK;
+    }
+    int owned = 0;
+    for (auto &h : p->hs) {
+        int o = 0;
+        for (int c = 0; c < h.Q; ++c) o += (h.color_ptr[c + 1] - h.color_ptr[c] + G - 1) / G;
+        owned = std::max(owned, o);
+    }
+    B.owned_max = owned;
+    const size_t bytes = (size_t)owned * (size_t)(max_deg + 2) * sizeof(int32_t);
+    B.staged = stage >= 0 && bytes <= kStageLimitBytes;
+    B.smem_bytes = B.staged ? bytes : 0;
     return XYL_OK;
 }
 
 int pick_batched_shape(xyl_plan *p, const xyl_tuning *tune)
 {
+    const int mode = tune ? tune->resident : 0;
+    const int stage = tune ? tune->stage : 0;
+    int block = 512;
+    if (tune && tune->block > 0) block = tune->block;
+    if (mode >= 0) {
+        // resident: the largest group that fits (pairs of replicas share a Philox block)
+        int pick = 0;
+        for (int g = 32; g >= 1 && !pick; g >>= 1) {
+            if (tune && tune->group > 0 && g != tune->group) continue;
+            bool divides = true;
+            for (auto &h : p->hs) divides &= (h.R % g == 0);
+            if (divides && apply_shape(p, g, 1, block, stage, 1) == XYL_OK) pick = g;
+        }
+        if (pick) return XYL_OK;
+        if (mode == 1)
+            return fail(XYL_EINVAL, "resident shape does not fit this batch (equal n_temps, n_temps/group <= 16, "
+                        "degree <= 8, spins within %zu B of shared memory)", kResidentDynLimitBytes);
+        clear_error();
+    }
     // replicas per cluster: largest power of two <= 16 dividing every sample's R
     int g = 16;
     for (auto &h : p->hs)
@@ -190,10 +268,8 @@ int pick_batched_shape(xyl_plan *p, const xyl_tuning *tune)
     int G = 1;
     const double items_per_phase = (double)max_N * g / std::max(1, p->shape.max_Q);
     while (G < 16 && items_per_phase / (G * 2) >= 1024.0) G *= 2;
-    int block = 512;
     if (tune && tune->cluster > 0) G = tune->cluster;
-    if (tune && tune->block > 0) block = tune->block;
-    return apply_shape(p, g, G, block, tune ? tune->stage : 0);
+    return apply_shape(p, g, G, block, stage, 0);
 }
 
 // Upload the unit table of the current shape, set the kernel attributes and
@@ -201,6 +277,21 @@ int pick_batched_shape(xyl_plan *p, const xyl_tuning *tune)
 int configure_batched(xyl_plan *p, cudaStream_t st)
 {
     int clusters = 0;
+    if (p->bshape.resident) {
+        // clusters never wait on one another: one launch, the hardware queues the rest
+        XYL_CUDA(resident_max_active_clusters(p->bshape, &clusters), "batched: occupancy");
+        if (clusters < 1)
+            return fail(XYL_EINVAL, "batched: a resident cluster of %d CTAs x %d threads (%zu B shared) cannot be resident",
+                        p->bshape.cpc, p->bshape.block, p->bshape.smem_bytes);
+        p->wave_units = (int)p->units.size();
+        XYL_CUDA(cudaMemcpyAsync(p->ws + p->r_units.off, p->units.data(), p->units.size() * sizeof(int2),
+                                 cudaMemcpyHostToDevice, st), "batched: unit table");
+        // the global-memory shape expects the buffer of its next sweep cleared
+        XYL_CUDA(cudaMemsetAsync(p->ws + p->r_obs.off, 0, p->r_obs.bytes, st), "batched: obs");
+        XYL_CUDA(cudaStreamSynchronize(st), "batched: sync");
+        p->drop_graphs();
+        return XYL_OK;
+    }
     XYL_CUDA(batched_max_active_clusters(p->shape, p->bshape, &clusters), "batched: occupancy");
     if (clusters < 1)
         return fail(XYL_EINVAL, "batched: a cluster of %d CTAs x %d threads (%zu B shared) cannot be resident",
@@ -224,6 +315,7 @@ int configure_batched(xyl_plan *p, cudaStream_t st)
     }
     XYL_CUDA(cudaMemcpyAsync(p->ws + p->r_units.off, p->units.data(), p->units.size() * sizeof(int2),
                              cudaMemcpyHostToDevice, st), "batched: unit table");
+    XYL_CUDA(cudaMemsetAsync(p->ws + p->r_obs.off, 0, p->r_obs.bytes, st), "batched: obs");
     XYL_CUDA(cudaStreamSynchronize(st), "batched: sync");
     p->drop_graphs();
     return XYL_OK;
@@ -248,6 +340,7 @@ int xyl_plan_create(const xyl_sample *samples, int32_t n_samples, int32_t engine
     p->shape.fp64 = (engine == XYL_FP64_PLAIN);
     p->shape.layout = (engine == XYL_FP32_BATCHED) ? kInterleaved : kReplicaMajor;
     p->recompute_every = tune ? std::max(0, tune->recompute_every) : 0;
+    p->resident_req = tune ? tune->resident : 0;
     for (int s = 0; s < n_samples; ++s) {
         const xyl_sample &in = samples[s];
         const xyl_graph *g = in.graph;
@@ -428,6 +521,12 @@ int zero_region(xyl_plan *p, const Region &r, cudaStream_t st)
 // Enqueue the work of `n` sweeps (no graph).
 int issue_sweeps(xyl_plan *p, int n, uint32_t ops, int measure_every, cudaStream_t st, int64_t *launches)
 {
+    if (p->engine == XYL_FP32_BATCHED && p->bshape.resident) {
+        XYL_CUDA(launch_resident(p->dev, p->bshape, 0, (int)p->hs.size(), n, ops, measure_every, st),
+                 "sweep: resident launch");
+        ++*launches;
+        return XYL_OK;
+    }
     if (p->engine == XYL_FP32_BATCHED) {
         XYL_CUDA(cudaMemsetAsync(p->ws + p->r_barrier.off, 0, p->r_barrier.bytes, st), "sweep: barrier reset");
         const int total = (int)p->units.size();
@@ -472,6 +571,7 @@ int run_captured(xyl_plan *p, int n, uint32_t ops, int measure_every, cudaStream
 
 int64_t launches_of(xyl_plan *p, int n, uint32_t ops)
 {
+    if (p->engine == XYL_FP32_BATCHED && p->bshape.resident) return 1;
     if (p->engine == XYL_FP32_BATCHED)
         return ((int64_t)p->units.size() + p->wave_units - 1) / p->wave_units;
     const int64_t per_sweep = (int64_t)(((ops & XYL_OP_MET) ? p->shape.max_Q : 0) +
@@ -551,8 +651,18 @@ int xyl_sweep_units(xyl_plan *p, int32_t first_unit, int32_t n_units, int32_t n_
     if ((ops & XYL_OP_MEASURE) && measure_every < 1) return fail(XYL_EINVAL, "xyl_sweep_units: measure_every must be >= 1");
     if (!(ops & XYL_OP_MEASURE)) measure_every = 1;
     cudaStream_t st = as_stream(stream);
-    XYL_CUDA(cudaMemsetAsync(p->ws + p->r_barrier.off, 0, p->r_barrier.bytes, st), "xyl_sweep_units: barrier reset");
     p->last_launches = 0;
+    if (p->bshape.resident) {
+        // a resident cluster is a whole sample: whole samples only
+        const int ng = p->bshape.cpc;
+        if (first_unit % ng || n_units % ng)
+            return fail(XYL_EINVAL, "xyl_sweep_units: the resident shape runs whole samples (%d units each)", ng);
+        XYL_CUDA(launch_resident(p->dev, p->bshape, first_unit / ng, n_units / ng, n_sweeps, ops, measure_every, st),
+                 "xyl_sweep_units: launch");
+        p->last_launches = 1;
+        return XYL_OK;
+    }
+    XYL_CUDA(cudaMemsetAsync(p->ws + p->r_barrier.off, 0, p->r_barrier.bytes, st), "xyl_sweep_units: barrier reset");
     for (int u = first_unit; u < first_unit + n_units; u += p->wave_units) {
         const int cnt = std::min(p->wave_units, first_unit + n_units - u);
         XYL_CUDA(launch_batched(p->dev, p->shape, p->bshape, at<int2>(p, p->r_units), u, cnt, n_sweeps, ops,
@@ -592,6 +702,12 @@ int xyl_sweep_noalloc(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measu
     P.obs = reinterpret_cast<double *>(base);
     P.barrier = reinterpret_cast<unsigned int *>(base + bar_off);
     p->last_launches = 0;
+    if (p->bshape.resident) {
+        XYL_CUDA(launch_resident(P, p->bshape, 0, (int)p->hs.size(), n_sweeps, ops, measure_every, st),
+                 "xyl_sweep_noalloc: launch");
+        p->last_launches = 1;
+        return XYL_OK;
+    }
     const int total = (int)p->units.size();
     for (int u = 0; u < total; u += p->wave_units) {
         const int cnt = std::min(p->wave_units, total - u);
@@ -871,9 +987,10 @@ int xyl_get_tuning(const xyl_plan *p, xyl_tuning *out)
     out->recompute_every = p->recompute_every;
     if (p->engine == XYL_FP32_BATCHED) {
         out->block = p->bshape.block;
-        out->cluster = p->bshape.G;
+        out->cluster = p->bshape.resident ? p->bshape.cpc : p->bshape.G;
         out->group = p->bshape.Rg;
         out->stage = p->bshape.staged ? 1 : -1;
+        out->resident = p->bshape.resident ? 1 : -1;
     }
     return XYL_OK;
 }
@@ -897,47 +1014,52 @@ int xyl_autotune(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_ev
     XYL_CUDA(cudaEventCreate(&e0), "xyl_autotune: event");
     XYL_CUDA(cudaEventCreate(&e1), "xyl_autotune: event");
     float best_ms = -1.f;
-    int best_g = keep.Rg, best_G = keep.G, best_block = keep.block;
-    for (int g = 1; g <= 32; g *= 2) {
-        bool divides = true;
-        for (auto &h : p->hs) divides &= (h.R % g == 0);
-        if (!divides) continue;
-        for (int G = 1; G <= 16; G *= 2) {
-            for (int block : {128, 256, 512, 640}) {
-                if (apply_shape(p, g, G, block, keep_stage) || configure_batched(p, st)) continue;
-                float ms = 0.f;
-                bool ok = true;
-                for (int rep = 0; rep < 2 && ok; ++rep) {
-                    if (xyl_import_state(p, snap.data(), snap.size(), stream)) { ok = false; break; }
-                    int64_t launches = 0;
-                    XYL_CUDA(cudaMemsetAsync(p->ws + p->r_barrier.off, 0, p->r_barrier.bytes, st), "xyl_autotune");
-                    XYL_CUDA(cudaEventRecord(e0, st), "xyl_autotune: record");
-                    if (issue_sweeps(p, n_sweeps, ops, measure_every, st, &launches)) { ok = false; break; }
-                    XYL_CUDA(cudaEventRecord(e1, st), "xyl_autotune: record");
-                    XYL_CUDA(cudaEventSynchronize(e1), "xyl_autotune: sync");
-                    XYL_CUDA(cudaEventElapsedTime(&ms, e0, e1), "xyl_autotune: time");
-                    int32_t status = 0;
-                    XYL_CUDA(cudaMemcpy(&status, p->ws + p->r_status.off, sizeof(status), cudaMemcpyDeviceToHost),
-                             "xyl_autotune: status");
-                    if (status) ok = false;
-                }
-                clear_error();
-                if (ok && (best_ms < 0.f || ms < best_ms)) {
-                    best_ms = ms;
-                    best_g = g;
-                    best_G = G;
-                    best_block = block;
+    int best_g = keep.Rg, best_G = keep.G, best_block = keep.block, best_res = keep.resident ? 1 : 0;
+    for (int res = 0; res <= 1; ++res) {
+        if ((p->resident_req < 0 && res) || (p->resident_req > 0 && !res)) continue;
+        for (int g = 1; g <= 32; g *= 2) {
+            bool divides = true;
+            for (auto &h : p->hs) divides &= (h.R % g == 0);
+            if (!divides) continue;
+            for (int G = 1; G <= (res ? 1 : 16); G *= 2) {
+                for (int block : {128, 256, 384, 512, 640}) {
+                    if (res ? block == 128 : block == 384) continue;
+                    if (apply_shape(p, g, G, block, keep_stage, res) || configure_batched(p, st)) continue;
+                    float ms = 0.f;
+                    bool ok = true;
+                    for (int rep = 0; rep < 2 && ok; ++rep) {
+                        if (xyl_import_state(p, snap.data(), snap.size(), stream)) { ok = false; break; }
+                        int64_t launches = 0;
+                        XYL_CUDA(cudaMemsetAsync(p->ws + p->r_barrier.off, 0, p->r_barrier.bytes, st), "xyl_autotune");
+                        XYL_CUDA(cudaEventRecord(e0, st), "xyl_autotune: record");
+                        if (issue_sweeps(p, n_sweeps, ops, measure_every, st, &launches)) { ok = false; break; }
+                        XYL_CUDA(cudaEventRecord(e1, st), "xyl_autotune: record");
+                        XYL_CUDA(cudaEventSynchronize(e1), "xyl_autotune: sync");
+                        XYL_CUDA(cudaEventElapsedTime(&ms, e0, e1), "xyl_autotune: time");
+                        int32_t status = 0;
+                        XYL_CUDA(cudaMemcpy(&status, p->ws + p->r_status.off, sizeof(status), cudaMemcpyDeviceToHost),
+                                 "xyl_autotune: status");
+                        if (status) ok = false;
+                    }
+                    clear_error();
+                    if (ok && (best_ms < 0.f || ms < best_ms)) {
+                        best_ms = ms;
+                        best_g = g;
+                        best_G = G;
+                        best_block = block;
+                        best_res = res;
+                    }
                 }
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if ((rc = apply_shape(p, best_g, best_G, best_block, keep_stage))) return rc;
+    if ((rc = apply_shape(p, best_g, best_G, best_block, keep_stage, best_res))) return rc;
     if ((rc = configure_batched(p, st))) return rc;
     if ((rc = xyl_import_state(p, snap.data(), snap.size(), stream))) return rc;
     if (best) xyl_get_tuning(p, best);
-    return best_ms < 0.f ? fail(XYL_EINVAL, "xyl_autotune: no resident launch shape") : XYL_OK;
+    return best_ms < 0.f ? fail(XYL_EINVAL, "xyl_autotune: no launch shape ran") : XYL_OK;
 }
 
 void xyl_plan_free(xyl_plan *p) { delete p; }

@@ -45,7 +45,8 @@ class Sample(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("block", C.c_int32), ("cluster", C.c_int32), ("group", C.c_int32),
-                ("recompute_every", C.c_int32), ("stage", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("recompute_every", C.c_int32), ("stage", C.c_int32), ("resident", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 _lib = None
@@ -176,7 +177,7 @@ class Plan:
     ``samples``: list of (Graph, sample_id, beta[list], delta[list])."""
 
     def __init__(self, samples, engine=FP32_BATCHED, seed=0, block=0, cluster=0, group=0, recompute_every=0,
-                 stage=0, device=None):
+                 stage=0, resident=0, device=None):
         import torch
         lib = load()
         self._keep = []
@@ -191,7 +192,7 @@ class Plan:
             arr[k] = Sample(g.handle, sid, len(b), _p(b, C.c_double), _p(d, C.c_double))
             self.n_temps.append(len(b))
             self.sizes.append(g.n)
-        tune = Tuning(block, cluster, group, recompute_every, stage)
+        tune = Tuning(block, cluster, group, recompute_every, stage, resident)
         h = C.c_void_p(); nbytes = C.c_size_t()
         _check(lib.xyl_plan_create(arr, len(samples), engine, seed, C.byref(tune), C.byref(h), C.byref(nbytes)))
         self.handle = h
@@ -235,13 +236,13 @@ class Plan:
         t = Tuning()
         _check(load().xyl_autotune(self.handle, int(n_sweeps), int(ops), int(measure_every), C.byref(t),
                                    _stream(stream)))
-        return {"block": t.block, "cluster": t.cluster, "group": t.group, "stage": t.stage}
+        return {"block": t.block, "cluster": t.cluster, "group": t.group, "stage": t.stage, "resident": t.resident}
 
     def tuning(self) -> dict:
         t = Tuning()
         _check(load().xyl_get_tuning(self.handle, C.byref(t)))
         return {"block": t.block, "cluster": t.cluster, "group": t.group, "stage": t.stage,
-                "recompute_every": t.recompute_every}
+                "resident": t.resident, "recompute_every": t.recompute_every}
 
     # same method names as the oracle sampler, so tests drive both the same way
     def sweeps(self, n, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1):

@@ -62,6 +62,21 @@ def _rep_slice(plan, sample):
     return slice(off, off + plan.n_temps[sample])
 
 
+# engine name -> (engine constant, plan options); the FP32 batched engine runs in
+# its resident shape (spins in shared memory) and its global-memory shape
+VARIANTS = {
+    "FP32_RESIDENT": ("FP32_BATCHED", {"resident": 1}),
+    "FP32_GLOBAL": ("FP32_BATCHED", {"resident": -1}),
+    "FP32_PLAIN": ("FP32_PLAIN", {}),
+    "FP64_PLAIN": ("FP64_PLAIN", {}),
+}
+
+
+def _variant(xyl, name):
+    eng, opts = VARIANTS[name]
+    return getattr(xyl, eng), dict(opts)
+
+
 # --------------------------------------------------------------- FP64 engine
 @pytest.mark.parametrize("name", ["C1", "C2"])
 def test_fp64_trajectory_matches_oracle(env, orc, name):
@@ -132,12 +147,13 @@ def _fp32_per_sweep(plan, sims, samples, n_sweeps, ops, N_of):
     return compared, explained, worst
 
 
-@pytest.mark.parametrize("engine_name", ["FP32_BATCHED", "FP32_PLAIN"])
+@pytest.mark.parametrize("engine_name", ["FP32_RESIDENT", "FP32_GLOBAL", "FP32_PLAIN"])
 @pytest.mark.parametrize("name", ["C1", "C2"])
 def test_fp32_energy_matches_oracle(env, orc, name, engine_name):
     xyl, wl = env
     cfg = wl.config(name)
-    plan, _ = wl.make_plan(cfg, getattr(xyl, engine_name))
+    eng, opts = _variant(xyl, engine_name)
+    plan, _ = wl.make_plan(cfg, eng, **opts)
     plan.bind()
     plan.init_spins()
     sims = {0: _oracle_for(orc, wl, cfg, 0, u24=True)}
@@ -148,7 +164,7 @@ def test_fp32_energy_matches_oracle(env, orc, name, engine_name):
 
 
 # --------------------------------------------------------------- long runs
-@pytest.mark.parametrize("engine_name", ["FP32_BATCHED", "FP64_PLAIN"])
+@pytest.mark.parametrize("engine_name", ["FP32_RESIDENT", "FP32_GLOBAL", "FP64_PLAIN"])
 def test_long_run_statistics_c1(env, orc, engine_name):
     xyl, wl = env
     cfg = wl.config("C1")
@@ -164,7 +180,8 @@ def test_long_run_statistics_c1(env, orc, engine_name):
         sim.reset_acc()
     cfg.delta = list(delta)
     sim = _oracle_for(orc, wl, cfg, 0, u24=False)
-    plan, _ = wl.make_plan(cfg, getattr(xyl, engine_name))
+    eng, opts = _variant(xyl, engine_name)
+    plan, _ = wl.make_plan(cfg, eng, **opts)
     plan.bind()
     plan.init_spins()
     for s in (sim, plan):
@@ -191,21 +208,22 @@ def test_long_run_statistics_c1(env, orc, engine_name):
 
 
 # --------------------------------------------------------------- exact results through the kernels
-def _edge_plan(xyl, edges, n, betas, deltas, engine, xy=None, L=0, seed=5):
+def _edge_plan(xyl, edges, n, betas, deltas, variant, xy=None, L=0, seed=5):
     g = xyl.graph_from_edges(n, edges, xy=xy, L=L)
-    p = xyl.Plan([(g, 0, betas, deltas)], engine=engine, seed=seed)
+    eng, opts = _variant(xyl, variant)
+    p = xyl.Plan([(g, 0, betas, deltas)], engine=eng, seed=seed, **opts)
     p.bind()
     p.init_spins()
     return p
 
 
-ENGINES = ["FP32_BATCHED", "FP64_PLAIN", "FP32_PLAIN"]
+ENGINES = ["FP32_RESIDENT", "FP32_GLOBAL", "FP64_PLAIN", "FP32_PLAIN"]
 
 
 @pytest.mark.parametrize("engine_name", ENGINES)
 def test_chain_and_ring_closed_forms(env, engine_name):
     xyl, _ = env
-    eng = getattr(xyl, engine_name)
+    eng = engine_name
     n, beta = 12, 1.0
     p = _edge_plan(xyl, edges_chain(n), n, [beta], [2.0], eng)
     p.sweeps(200, NO_PT)
@@ -231,7 +249,7 @@ XY4 = [0, 0, 1, 0, 0, 1, 1, 1]
 @pytest.mark.parametrize("engine_name", ENGINES)
 def test_small_graphs_and_pt_against_quadrature(env, engine_name):
     xyl, _ = env
-    eng = getattr(xyl, engine_name)
+    eng = engine_name
     for n, edges in ((3, edges_ring(3)), (4, edges_complete(4))):
         beta = 1.3
         p = _edge_plan(xyl, edges, n, [beta], [2.5], eng, xy=XY4[: 2 * n], L=2)
@@ -265,7 +283,8 @@ def test_beta_zero_exact_moments(env, engine_name):
     L = 8
     N = L * L
     g = xyl.build_graph_csr(L, 6, 3.5, 1, 0)
-    p = xyl.Plan([(g, 0, [0.0], [np.pi])], engine=getattr(xyl, engine_name), seed=9)
+    eng, opts = _variant(xyl, engine_name)
+    p = xyl.Plan([(g, 0, [0.0], [np.pi])], engine=eng, seed=9, **opts)
     p.bind()
     p.init_spins()
     bins = bin_means(run_bins(p, 100, 200, NO_PT))[:, 0, :]
@@ -281,13 +300,15 @@ def test_beta_zero_exact_moments(env, engine_name):
 
 
 # --------------------------------------------------------------- full-size configurations
-@pytest.mark.parametrize("name,sampled", [("C3", [0, 400, 767]), ("C4", [0, 47]), ("C5", [70])])
-def test_full_size_batched_sampled_parity(env, orc, name, sampled):
+@pytest.mark.parametrize("name,sampled,resident", [("C3", [0, 400, 767], 1), ("C3", [1, 511], -1),
+                                                    ("C4", [0, 47], 0), ("C5", [70], 0)])
+def test_full_size_batched_sampled_parity(env, orc, name, sampled, resident):
     """Whole batch in the benchmark's launch configuration; sampled samples are
     re-run by the oracle from the same seeds; every sample obeys the invariants."""
     xyl, wl = env
     cfg = wl.config(name)
-    plan, graphs = wl.make_plan(cfg, xyl.FP32_BATCHED)
+    plan, graphs = wl.make_plan(cfg, xyl.FP32_BATCHED, resident=resident)
+    assert plan.tuning()["resident"] == (1 if resident == 1 else -1) or resident == 0
     plan.bind()
     plan.init_spins()
     sims = {k: _oracle_for(orc, wl, cfg, k, u24=True) for k in sampled}
@@ -312,12 +333,13 @@ def test_full_size_batched_sampled_parity(env, orc, name, sampled):
 
 
 # --------------------------------------------------------------- determinism, checkpoint, recovery
-def test_batched_runs_are_deterministic_and_resumable(env):
+@pytest.mark.parametrize("resident", [1, -1])
+def test_batched_runs_are_deterministic_and_resumable(env, resident):
     xyl, wl = env
     cfg = wl.config("C2")
     graphs = wl.build_graphs(cfg)
-    a, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs)
-    b, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs)
+    a, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, resident=resident)
+    b, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, resident=resident)
     for p in (a, b):
         p.bind()
         p.init_spins()
@@ -356,7 +378,7 @@ def test_split_sample_wait_times_out_and_recovers(env):
     the other groups give up: status ETIMEOUT, context still usable."""
     xyl, wl = env
     cfg = wl.config("C2")
-    plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, group=4)
+    plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, group=4, resident=-1)
     plan.bind()
     plan.init_spins()
     assert plan.unit_count() == 4
@@ -379,8 +401,10 @@ def test_launch_shape_does_not_change_the_trajectory(env):
     xyl, wl = env
     cfg = wl.config("C2")
     graphs = wl.build_graphs(cfg)
-    shapes = [dict(group=16, cluster=16, block=512), dict(group=1, cluster=8, block=256),
-              dict(group=4, cluster=4, block=128, stage=-1), dict(group=4, cluster=16, block=640)]
+    shapes = [dict(group=16, cluster=16, block=512, resident=-1), dict(group=1, cluster=8, block=256, resident=-1),
+              dict(group=4, cluster=4, block=128, stage=-1, resident=-1),
+              dict(group=4, cluster=16, block=640, resident=-1),
+              dict(group=1, block=640, resident=1), dict(group=1, block=256, stage=-1, resident=1)]
     ref = None
     for shp in shapes:
         p, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, **shp)
@@ -456,7 +480,7 @@ def test_long_run_statistics_reduced_c3(env, orc):
 def test_degenerate_inputs(env, engine_name):
     """No links, a single site, a zero Metropolis step, an odd number of slots."""
     xyl, _ = env
-    eng = getattr(xyl, engine_name)
+    eng = engine_name
     # isolated spins: zero field, zero energy; overrelaxation leaves them alone and
     # every Metropolis move is accepted (dE = 0)
     p = _edge_plan(xyl, [], 5, [1.0, 0.5, 2.0], [1.0, 1.0, 1.0], eng)
@@ -476,7 +500,8 @@ def test_degenerate_inputs(env, engine_name):
     assert st["acc"][0, ACC["n"]] == 4 and abs(st["acc"][0, ACC["m2"]] - 4.0) < 1e-5
     # Delta = 0: proposals equal the current spin, so Metropolis changes nothing
     g = xyl.build_graph_csr(8, 6, 3.5, 1, 0)
-    p = xyl.Plan([(g, 0, [1.0, 0.7, 0.4], [0.0, 0.0, 0.0])], engine=eng, seed=4)
+    e, opts = _variant(xyl, eng)
+    p = xyl.Plan([(g, 0, [1.0, 0.7, 0.4], [0.0, 0.0, 0.0])], engine=e, seed=4, **opts)
     p.bind()
     p.init_spins()
     s0 = np.stack([p.spins(0, r) for r in range(3)])

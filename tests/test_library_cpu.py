@@ -127,3 +127,32 @@ def test_plan_validation_without_gpu(xyl):
     with pytest.raises(xyl.XylError) as e:
         p.sweep(1, stream=0)
     assert e.value.code == xyl.ESTATE
+
+
+def test_resident_shape_selection_without_gpu(xyl):
+    """The batched engine's resident shape (spins in shared memory) is the
+    default where a CTA can hold whole replicas, with the largest group that
+    fits and at most 16 groups per sample; otherwise the global-memory shape."""
+    def tuning(L, R, **kw):
+        g = xyl.build_graph_csr(L, 6, 3.5, 1, 0)
+        return xyl.Plan([(g, 0, [1.0] * R, [1.0] * R)], engine=xyl.FP32_BATCHED, device="cpu", **kw).tuning()
+
+    t = tuning(128, 16)  # 16384 sites: one replica per CTA (128 KB), a cluster of 16
+    assert (t["resident"], t["group"], t["cluster"]) == (1, 1, 16)
+    t = tuning(64, 24)   # 4096 sites: four replicas per CTA, a cluster of 6, CSR staged
+    assert (t["resident"], t["group"], t["cluster"], t["stage"]) == (1, 4, 6, 1)
+    t = tuning(64, 24, stage=-1)
+    assert (t["resident"], t["stage"]) == (1, -1)
+    t = tuning(256, 8)   # 65536 sites: 512 KB per replica, does not fit
+    assert t["resident"] == -1
+    t = tuning(128, 32)  # would need 32 groups of one replica
+    assert t["resident"] == -1
+    assert tuning(64, 24, resident=-1)["resident"] == -1
+    with pytest.raises(xyl.XylError) as e:
+        tuning(256, 8, resident=1)
+    assert e.value.code == xyl.EINVAL
+    # samples with different slot counts cannot share a resident cluster shape
+    g1, g2 = xyl.build_graph_csr(16, 6, 3.5, 1, 0), xyl.build_graph_csr(16, 6, 3.5, 1, 1)
+    p = xyl.Plan([(g1, 0, [1.0] * 2, [1.0] * 2), (g2, 1, [1.0] * 4, [1.0] * 4)], engine=xyl.FP32_BATCHED,
+                 device="cpu")
+    assert p.tuning()["resident"] == -1

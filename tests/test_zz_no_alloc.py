@@ -25,12 +25,13 @@ def env():
     return xyl, workloads
 
 
-def test_noalloc_sweep_matches_sweep_twice(env):
+@pytest.mark.parametrize("resident", [1, -1])
+def test_noalloc_sweep_matches_sweep_twice(env, resident):
     xyl, wl = env
     cfg = wl.config("C2")
     graphs = wl.build_graphs(cfg)
-    ref, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs)
-    new, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs)
+    ref, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, resident=resident)
+    new, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, resident=resident)
     for p in (ref, new):
         p.bind()
         p.init_spins()
