@@ -61,6 +61,7 @@ struct DevPlan {
     int32_t *status;           // 0 or an XYL_E* code
     unsigned int *barrier;     // per sample arrival counters (batched engine)
     double *drift;             // largest |E_fused - E_fp64| seen by a recompute
+    const uint16_t *push;      // per site: CTAs of its group (bit = rank) that read it (site-split resident shape)
     uint64_t key;              // Philox key of the spin streams
     // Maclaurin coefficients (-1)^k / (2k+1)! and (-1)^k / (2k)! of the FP64 sin/cos
     double sin_coef[kSinTerms];

@@ -32,7 +32,8 @@ struct BatchedShape {
     // resident shape: one CTA per replica group holds the group's spins of
     // every site in shared memory; the groups of a sample form one cluster
     bool resident = false;
-    int cpc = 1;            // CTAs per cluster of the resident shape (groups per sample)
+    int gpc = 1;            // replica groups per cluster (resident shape)
+    int cpc = 1;            // CTAs per cluster of the resident shape, G x gpc
     int rs_csr_w = 0;       // staged CSR row width (16-bit ids), 0 = rows from global memory
     bool rs_ids = false;    // random-stream site ids staged (16-bit)
     size_t rs_off_ids = 0, rs_off_col = 0, rs_off_part = 0, rs_off_met = 0;
@@ -63,9 +64,9 @@ cudaError_t launch_batched(const DevPlan &P, const PlanShape &S, const BatchedSh
 cudaError_t batched_max_active_clusters(const PlanShape &S, const BatchedShape &B, int *clusters);
 size_t batched_static_smem_bytes();
 
-// Resident shape: one launch over samples [sample_begin, sample_begin + sample_count).
-cudaError_t launch_resident(const DevPlan &P, const BatchedShape &B, int sample_begin, int sample_count,
-                            int n_sweeps, uint32_t ops, int measure_every, cudaStream_t st);
+// Resident shape: one launch over units [unit_begin, unit_begin + unit_count), a multiple of gpc.
+cudaError_t launch_resident(const DevPlan &P, const BatchedShape &B, const int2 *d_units, int unit_begin,
+                            int unit_count, int n_sweeps, uint32_t ops, int measure_every, cudaStream_t st);
 cudaError_t resident_max_active_clusters(const BatchedShape &B, int *clusters);
 size_t resident_static_smem_bytes();
 

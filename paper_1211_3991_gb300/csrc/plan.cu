@@ -56,7 +56,7 @@ struct xyl_plan {
     DevPlan dev{};
     Region r_samples, r_row_ptr, r_col, r_perm, r_color_ptr, r_phase, r_spins, r_beta, r_delta, r_slot_of, r_rep_at,
         r_obs, r_last_E, r_acc, r_met_acc, r_met_try, r_pt_acc, r_pt_try, r_sweep, r_status, r_barrier, r_drift,
-        r_units;
+        r_units, r_push;
     cudaStream_t capture_stream = nullptr;
     std::map<std::tuple<int, uint32_t, int>, cudaGraphExec_t> graphs;
     int64_t last_launches = 0;
@@ -123,6 +123,7 @@ void layout(xyl_plan *p)
     take(p->r_barrier, S * sizeof(unsigned int));
     take(p->r_drift, sizeof(double));
     take(p->r_units, std::max<size_t>(p->total_R, 1) * sizeof(int2));  // the most units any shape makes
+    take(p->r_push, p->total_N * sizeof(uint16_t));
     p->ws_bytes = off;
 }
 
@@ -139,20 +140,26 @@ int check_bound(xyl_plan *p, const char *who)
     return XYL_OK;
 }
 
-// Shared-memory layout of the resident shape for groups of g replicas and
-// `block` threads: spins (with one zero row) | warp partial sums | accepted
-// counts | 16-bit site ids | 16-bit CSR rows, the last two when they fit.
-// Returns false when the shape does not apply to this batch.
-bool resident_fit(const xyl_plan *p, int g, int block, int stage, BatchedShape &B)
+// Shared-memory layout of the resident shape for groups of g replicas shared
+// by G CTAs with `block` threads each: spins of every site (with one zero
+// row) | warp partial sums | accepted counts | 16-bit site ids | 16-bit CSR
+// rows of the CTA's own sites, the last two when they fit.  A cluster holds
+// every group of a sample when G x groups <= 16, else one group.  Returns
+// false when the shape does not apply to this batch.
+bool resident_fit(const xyl_plan *p, int g, int G, int block, int stage, BatchedShape &B)
 {
     const int R0 = p->hs[0].R;
-    int max_N = 0, max_deg = 0;
+    int max_N = 0, max_deg = 0, owned = 0;
     for (auto &h : p->hs) {
         if (h.R != R0) return false;
         max_N = std::max(max_N, h.N);
         max_deg = std::max(max_deg, h.max_deg);
+        int o = 0;
+        for (int c = 0; c < h.Q; ++c) o += (h.color_ptr[c + 1] - h.color_ptr[c] + G - 1) / G;
+        owned = std::max(owned, o);
     }
-    if (R0 % g || R0 / g > 16 || max_deg > 8) return false;
+    if (R0 % g || max_deg > 8) return false;
+    const int n_groups = R0 / g;
     auto a16 = [](size_t v) { return (v + 15) / 16 * 16; };
     const size_t n_warps = (size_t)block / 32;
     const size_t spins = a16((size_t)(max_N + 1) * g * sizeof(float2));
@@ -166,14 +173,14 @@ bool resident_fit(const xyl_plan *p, int g, int block, int stage, BatchedShape &
     B.rs_csr_w = 0;
     B.rs_off_ids = B.rs_off_col = 0;
     if (max_N <= 65535) {  // ids and the padding id N fit 16 bits
-        const size_t ids = a16((size_t)max_N * sizeof(uint16_t));
+        const size_t ids = a16((size_t)owned * sizeof(uint16_t));
         if (off + ids <= kResidentDynLimitBytes) {
             B.rs_ids = true;
             B.rs_off_ids = off;
             off += ids;
         }
         const int W = B.fixed_deg == 6 ? 6 : 8;
-        const size_t col = a16((size_t)max_N * W * sizeof(uint16_t));
+        const size_t col = a16((size_t)owned * W * sizeof(uint16_t));
         if (stage >= 0 && off + col <= kResidentDynLimitBytes) {
             B.rs_csr_w = W;
             B.rs_off_col = off;
@@ -181,8 +188,10 @@ bool resident_fit(const xyl_plan *p, int g, int block, int stage, BatchedShape &
         }
     }
     B.resident = true;
-    B.cpc = R0 / g;
-    B.G = 1;
+    B.G = G;
+    B.gpc = n_groups * G <= 16 ? n_groups : 1;
+    B.cpc = G * B.gpc;
+    B.owned_max = owned;
     B.staged = B.rs_csr_w != 0;
     B.smem_bytes = off;
     return true;
@@ -218,9 +227,9 @@ int apply_shape(xyl_plan *p, int g, int G, int block, int stage, int resident)
     for (size_t s = 0; s < p->hs.size(); ++s)
         for (int k = 0; k < p->hs[s].R / g; ++k) p->units.push_back(make_int2((int)s, k));
     if (resident) {
-        if (!resident_fit(p, g, block, stage, B))
-            return fail(XYL_EINVAL, "resident shape with group=%d does not fit this batch (equal n_temps, n_temps/group "
-                        "<= 16, degree <= 8, spins within %zu B of shared memory)", g, kResidentDynLimitBytes);
+        if (!resident_fit(p, g, G, block, stage, B))
+            return fail(XYL_EINVAL, "resident shape with group=%d does not fit this batch (equal n_temps, degree <= 8, "
+                        "a group's spins within %zu B of shared memory)", g, kResidentDynLimitBytes);
         return XYL_OK;
     }
     int owned = 0;
@@ -243,18 +252,24 @@ int pick_batched_shape(xyl_plan *p, const xyl_tuning *tune)
     int block = 512;
     if (tune && tune->block > 0) block = tune->block;
     if (mode >= 0) {
-        // resident: the largest group that fits (pairs of replicas share a Philox block)
-        int pick = 0;
-        for (int g = 32; g >= 1 && !pick; g >>= 1) {
-            if (tune && tune->group > 0 && g != tune->group) continue;
-            bool divides = true;
-            for (auto &h : p->hs) divides &= (h.R % g == 0);
-            if (divides && apply_shape(p, g, 1, block, stage, 1) == XYL_OK) pick = g;
+        // resident: the largest group that fits with all groups of a sample in
+        // one cluster (pairs of replicas share a Philox block); a caller's
+        // group or cluster width is taken as given
+        const int G = (tune && tune->cluster > 0) ? tune->cluster : 1;
+        const bool given = mode == 1 || (tune && (tune->group > 0 || tune->cluster > 0));
+        for (int pass = 0; pass < (given ? 2 : 1); ++pass) {
+            for (int g = 32; g >= 1; g >>= 1) {
+                if (tune && tune->group > 0 && g != tune->group) continue;
+                bool divides = true;
+                for (auto &h : p->hs) divides &= (h.R % g == 0);
+                if (!divides || apply_shape(p, g, G, block, stage, 1) != XYL_OK) continue;
+                // first choice: every group of a sample in one cluster
+                if (pass == 1 || p->bshape.gpc * g == p->hs[0].R) return XYL_OK;
+            }
         }
-        if (pick) return XYL_OK;
         if (mode == 1)
-            return fail(XYL_EINVAL, "resident shape does not fit this batch (equal n_temps, n_temps/group <= 16, "
-                        "degree <= 8, spins within %zu B of shared memory)", kResidentDynLimitBytes);
+            return fail(XYL_EINVAL, "resident shape does not fit this batch (equal n_temps, degree <= 8, a group's "
+                        "spins within %zu B of shared memory)", kResidentDynLimitBytes);
         clear_error();
     }
     // replicas per cluster: largest power of two <= 16 dividing every sample's R
@@ -278,12 +293,48 @@ int configure_batched(xyl_plan *p, cudaStream_t st)
 {
     int clusters = 0;
     if (p->bshape.resident) {
-        // clusters never wait on one another: one launch, the hardware queues the rest
-        XYL_CUDA(resident_max_active_clusters(p->bshape, &clusters), "batched: occupancy");
+        const BatchedShape &B = p->bshape;
+        XYL_CUDA(resident_max_active_clusters(B, &clusters), "batched: occupancy");
         if (clusters < 1)
             return fail(XYL_EINVAL, "batched: a resident cluster of %d CTAs x %d threads (%zu B shared) cannot be resident",
-                        p->bshape.cpc, p->bshape.block, p->bshape.smem_bytes);
-        p->wave_units = (int)p->units.size();
+                        B.cpc, B.block, B.smem_bytes);
+        const int n_groups = p->hs[0].R / B.Rg;
+        if (B.gpc == n_groups) {
+            // a cluster is a whole sample and never waits on another: one
+            // launch, the hardware queues the clusters that do not fit yet
+            p->wave_units = (int)p->units.size();
+        } else {
+            // the clusters of a sample meet at a global barrier: a wave holds
+            // whole samples that are resident together
+            const int per_sample = n_groups / B.gpc;
+            const int samples_per_wave = clusters / per_sample;
+            if (samples_per_wave < 1)
+                return fail(XYL_EINVAL, "batched: %d resident clusters of %d CTAs cannot be co-resident (max %d)",
+                            per_sample, B.cpc, clusters);
+            p->wave_units = samples_per_wave * n_groups;
+        }
+        if (B.G > 1) {
+            // per site: the other CTAs of its group whose chunks link to it
+            std::vector<uint16_t> mask(p->total_N, 0);
+            size_t off = 0;
+            for (auto &h : p->hs) {
+                std::vector<int> owner(h.N);
+                for (int c = 0; c < h.Q; ++c) {
+                    const int cb = h.color_ptr[c], ce = h.color_ptr[c + 1];
+                    const int chunk = (ce - cb + B.G - 1) / B.G;
+                    for (int i = cb; i < ce; ++i) owner[i] = (i - cb) / chunk;
+                }
+                for (int i = 0; i < h.N; ++i) {
+                    uint32_t m = 0;
+                    for (int k = h.row_ptr[i]; k < h.row_ptr[i + 1]; ++k) m |= 1u << owner[h.col[k]];
+                    mask[off + i] = (uint16_t)(m & ~(1u << owner[i]));
+                }
+                off += h.N;
+            }
+            XYL_CUDA(cudaMemcpyAsync(p->ws + p->r_push.off, mask.data(), mask.size() * sizeof(uint16_t),
+                                     cudaMemcpyHostToDevice, st), "batched: peer masks");
+            XYL_CUDA(cudaStreamSynchronize(st), "batched: sync");
+        }
         XYL_CUDA(cudaMemcpyAsync(p->ws + p->r_units.off, p->units.data(), p->units.size() * sizeof(int2),
                                  cudaMemcpyHostToDevice, st), "batched: unit table");
         // the global-memory shape expects the buffer of its next sweep cleared
@@ -480,6 +531,7 @@ int xyl_bind(xyl_plan *p, void *d_workspace, size_t bytes, void *stream)
     P.status = at<int32_t>(p, p->r_status);
     P.barrier = at<unsigned int>(p, p->r_barrier);
     P.drift = at<double>(p, p->r_drift);
+    P.push = at<uint16_t>(p, p->r_push);
     P.key = p->seed;
     // Maclaurin coefficients by the factorial recurrence a_k = a_{k-1} / (n (n+1))
     {
@@ -521,19 +573,17 @@ int zero_region(xyl_plan *p, const Region &r, cudaStream_t st)
 // Enqueue the work of `n` sweeps (no graph).
 int issue_sweeps(xyl_plan *p, int n, uint32_t ops, int measure_every, cudaStream_t st, int64_t *launches)
 {
-    if (p->engine == XYL_FP32_BATCHED && p->bshape.resident) {
-        XYL_CUDA(launch_resident(p->dev, p->bshape, 0, (int)p->hs.size(), n, ops, measure_every, st),
-                 "sweep: resident launch");
-        ++*launches;
-        return XYL_OK;
-    }
     if (p->engine == XYL_FP32_BATCHED) {
         XYL_CUDA(cudaMemsetAsync(p->ws + p->r_barrier.off, 0, p->r_barrier.bytes, st), "sweep: barrier reset");
         const int total = (int)p->units.size();
         for (int u = 0; u < total; u += p->wave_units) {
             const int cnt = std::min(p->wave_units, total - u);
-            XYL_CUDA(launch_batched(p->dev, p->shape, p->bshape, at<int2>(p, p->r_units), u, cnt, n, ops, measure_every, st),
-                     "sweep: batched launch");
+            if (p->bshape.resident)
+                XYL_CUDA(launch_resident(p->dev, p->bshape, at<int2>(p, p->r_units), u, cnt, n, ops, measure_every, st),
+                         "sweep: resident launch");
+            else
+                XYL_CUDA(launch_batched(p->dev, p->shape, p->bshape, at<int2>(p, p->r_units), u, cnt, n, ops,
+                                        measure_every, st), "sweep: batched launch");
             ++*launches;
         }
         return XYL_OK;
@@ -571,7 +621,6 @@ int run_captured(xyl_plan *p, int n, uint32_t ops, int measure_every, cudaStream
 
 int64_t launches_of(xyl_plan *p, int n, uint32_t ops)
 {
-    if (p->engine == XYL_FP32_BATCHED && p->bshape.resident) return 1;
     if (p->engine == XYL_FP32_BATCHED)
         return ((int64_t)p->units.size() + p->wave_units - 1) / p->wave_units;
     const int64_t per_sweep = (int64_t)(((ops & XYL_OP_MET) ? p->shape.max_Q : 0) +
@@ -652,21 +701,17 @@ int xyl_sweep_units(xyl_plan *p, int32_t first_unit, int32_t n_units, int32_t n_
     if (!(ops & XYL_OP_MEASURE)) measure_every = 1;
     cudaStream_t st = as_stream(stream);
     p->last_launches = 0;
-    if (p->bshape.resident) {
-        // a resident cluster is a whole sample: whole samples only
-        const int ng = p->bshape.cpc;
-        if (first_unit % ng || n_units % ng)
-            return fail(XYL_EINVAL, "xyl_sweep_units: the resident shape runs whole samples (%d units each)", ng);
-        XYL_CUDA(launch_resident(p->dev, p->bshape, first_unit / ng, n_units / ng, n_sweeps, ops, measure_every, st),
-                 "xyl_sweep_units: launch");
-        p->last_launches = 1;
-        return XYL_OK;
-    }
+    if (p->bshape.resident && (first_unit % p->bshape.gpc || n_units % p->bshape.gpc))
+        return fail(XYL_EINVAL, "xyl_sweep_units: a resident cluster runs %d units together", p->bshape.gpc);
     XYL_CUDA(cudaMemsetAsync(p->ws + p->r_barrier.off, 0, p->r_barrier.bytes, st), "xyl_sweep_units: barrier reset");
     for (int u = first_unit; u < first_unit + n_units; u += p->wave_units) {
         const int cnt = std::min(p->wave_units, first_unit + n_units - u);
-        XYL_CUDA(launch_batched(p->dev, p->shape, p->bshape, at<int2>(p, p->r_units), u, cnt, n_sweeps, ops,
-                                measure_every, st), "xyl_sweep_units: launch");
+        if (p->bshape.resident)
+            XYL_CUDA(launch_resident(p->dev, p->bshape, at<int2>(p, p->r_units), u, cnt, n_sweeps, ops, measure_every,
+                                     st), "xyl_sweep_units: launch");
+        else
+            XYL_CUDA(launch_batched(p->dev, p->shape, p->bshape, at<int2>(p, p->r_units), u, cnt, n_sweeps, ops,
+                                    measure_every, st), "xyl_sweep_units: launch");
         ++p->last_launches;
     }
     return XYL_OK;
@@ -702,17 +747,15 @@ int xyl_sweep_noalloc(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measu
     P.obs = reinterpret_cast<double *>(base);
     P.barrier = reinterpret_cast<unsigned int *>(base + bar_off);
     p->last_launches = 0;
-    if (p->bshape.resident) {
-        XYL_CUDA(launch_resident(P, p->bshape, 0, (int)p->hs.size(), n_sweeps, ops, measure_every, st),
-                 "xyl_sweep_noalloc: launch");
-        p->last_launches = 1;
-        return XYL_OK;
-    }
     const int total = (int)p->units.size();
     for (int u = 0; u < total; u += p->wave_units) {
         const int cnt = std::min(p->wave_units, total - u);
-        XYL_CUDA(launch_batched(P, p->shape, p->bshape, at<int2>(p, p->r_units), u, cnt, n_sweeps, ops, measure_every,
-                                st), "xyl_sweep_noalloc: launch");
+        if (p->bshape.resident)
+            XYL_CUDA(launch_resident(P, p->bshape, at<int2>(p, p->r_units), u, cnt, n_sweeps, ops, measure_every, st),
+                     "xyl_sweep_noalloc: launch");
+        else
+            XYL_CUDA(launch_batched(P, p->shape, p->bshape, at<int2>(p, p->r_units), u, cnt, n_sweeps, ops,
+                                    measure_every, st), "xyl_sweep_noalloc: launch");
         ++p->last_launches;
     }
     return XYL_OK;
@@ -731,7 +774,8 @@ int xyl_pt_swap(xyl_plan *p, void *stream)
     cudaStream_t st = as_stream(stream);
     XYL_CUDA(launch_recompute(p->dev, p->shape, 0, buffer_mode(p), st), "xyl_pt_swap: recompute");
     XYL_CUDA(launch_finalize(p->dev, p->shape, XYL_OP_PT, 1, 0, buffer_mode(p), st), "xyl_pt_swap: finalize");
-    return XYL_OK;
+    // the batched kernels add the next sweep's sums into a cleared buffer
+    return buffer_mode(p) ? zero_region(p, p->r_obs, st) : XYL_OK;
 }
 
 int xyl_measure(xyl_plan *p, void *stream)
@@ -742,7 +786,7 @@ int xyl_measure(xyl_plan *p, void *stream)
     cudaStream_t st = as_stream(stream);
     XYL_CUDA(launch_recompute(p->dev, p->shape, 0, buffer_mode(p), st), "xyl_measure: recompute");
     XYL_CUDA(launch_finalize(p->dev, p->shape, XYL_OP_MEASURE, 1, 0, buffer_mode(p), st), "xyl_measure: finalize");
-    return XYL_OK;
+    return buffer_mode(p) ? zero_region(p, p->r_obs, st) : XYL_OK;
 }
 
 int xyl_recompute(xyl_plan *p, void *stream)
@@ -987,7 +1031,7 @@ int xyl_get_tuning(const xyl_plan *p, xyl_tuning *out)
     out->recompute_every = p->recompute_every;
     if (p->engine == XYL_FP32_BATCHED) {
         out->block = p->bshape.block;
-        out->cluster = p->bshape.resident ? p->bshape.cpc : p->bshape.G;
+        out->cluster = p->bshape.G;
         out->group = p->bshape.Rg;
         out->stage = p->bshape.staged ? 1 : -1;
         out->resident = p->bshape.resident ? 1 : -1;
@@ -1015,13 +1059,20 @@ int xyl_autotune(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_ev
     XYL_CUDA(cudaEventCreate(&e1), "xyl_autotune: event");
     float best_ms = -1.f;
     int best_g = keep.Rg, best_G = keep.G, best_block = keep.block, best_res = keep.resident ? 1 : 0;
+    int dev = 0, n_sm = 0;
+    XYL_CUDA(cudaGetDevice(&dev), "xyl_autotune: device");
+    XYL_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev), "xyl_autotune: SM count");
     for (int res = 0; res <= 1; ++res) {
         if ((p->resident_req < 0 && res) || (p->resident_req > 0 && !res)) continue;
         for (int g = 1; g <= 32; g *= 2) {
             bool divides = true;
             for (auto &h : p->hs) divides &= (h.R % g == 0);
             if (!divides) continue;
-            for (int G = 1; G <= (res ? 1 : 16); G *= 2) {
+            int64_t units = 0;
+            for (auto &h : p->hs) units += h.R / g;
+            for (int G = 1; G <= 16; G *= 2) {
+                // split a resident group across CTAs only while the batch leaves SMs idle
+                if (res && G > 1 && units * G > 2 * (int64_t)n_sm) continue;
                 for (int block : {128, 256, 384, 512, 640}) {
                     if (res ? block == 128 : block == 384) continue;
                     if (apply_shape(p, g, G, block, keep_stage, res) || configure_batched(p, st)) continue;

@@ -1,23 +1,30 @@
-// Resident FP32 engine: the batched sampler with each CTA's replicas held in
-// shared memory for the whole launch.
+// Resident FP32 engine: the batched sampler with the spins held in shared
+// memory for the whole launch.
 //
 // Work decomposition.  The replicas of a sample are split into groups of Rg
-// (a power of two); one CTA owns a group and keeps the group's spins of every
-// site, [site][replica] float2, in shared memory from the start of the launch
-// to its end, so a colour phase reads and writes nothing but shared memory and
-// phases are separated by __syncthreads alone.  The CTAs of all groups of a
-// sample form one thread-block cluster: once per sweep they publish their
-// replicas' energies (and, on measurement sweeps, the magnetisation and
-// Fourier sums) and meet at a cluster barrier, after which every CTA takes the
-// same parallel-tempering decisions and the first CTA records the
-// measurement.  Clusters never wait on one another.
+// (a power of two).  G CTAs (G >= 1) share a group: each keeps a full copy of
+// the group's spins of every site, [site][replica] float2, in its shared
+// memory from the start of the launch to its end, and updates its own chunk
+// of every colour class (chunk k of a class is its k-th contiguous 1/G).  A
+// colour phase therefore reads nothing but shared memory.  With G > 1 a CTA
+// writes each spin it changes into its own copy and into the copies of the
+// CTAs whose chunks have a link to that site (a per-site mask of peers, built
+// on the host), and the phases are separated by cluster barriers; with G = 1
+// __syncthreads separates them.
+//
+// A cluster holds gpc groups x G CTAs.  When all groups of a sample fit in one
+// cluster (gpc = R / Rg) the sample's CTAs meet once per sweep at a cluster
+// barrier; otherwise (gpc = 1) at a bounded global barrier like the
+// global-memory kernel's.  After the barrier every CTA reads all replica
+// energies, takes the same parallel-tempering decisions, and the first CTA of
+// the first group records the measurement.
 //
 // The per-spin arithmetic, the random streams and the order of every field
 // sum are those of the global-memory batched kernel, so both give bit-equal
-// spins from the same state; only the order of the energy sums differs.
-// The CSR rows (as 16-bit ids) and the random-stream site ids are staged in
-// shared memory when they fit beside the spins; otherwise they are read
-// through the read-only path, one item ahead.
+// spins from the same state; only the order of the energy sums differs.  The
+// CSR rows of a CTA's own sites (16-bit ids) and their random-stream site ids
+// are staged in shared memory when they fit beside the spins; otherwise they
+// are read through the read-only path, one item ahead.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -30,17 +37,20 @@ namespace xyl {
 namespace {
 
 constexpr int kSums = kObsCount;
+constexpr unsigned int kResidentBarrierPolls = 1u << 21;  // about a second of polling
 
 struct ResidentParams {
-    int sample_begin;
-    int cpc;             // CTAs per cluster = replica groups per sample
+    const int2 *units;   // (sample, group), sample-major
+    int unit_begin;
+    int G;               // CTAs that share one replica group
+    int gpc;             // replica groups per cluster
     int Rg;
     int log2lps;         // log2 of the lanes that share a site (Rg / RV)
     int n_sweeps;
     uint32_t ops;
     int measure_every;
     int n_warps;
-    // dynamic shared memory layout (byte offsets; 0 size = not staged)
+    // dynamic shared memory layout (byte offsets)
     int off_ids, off_col, off_part, off_met;
     int csr_w;           // staged CSR row width (6 or 8), 0 = rows read from global memory
     int ids;             // random-stream site ids staged as 16-bit values
@@ -53,29 +63,35 @@ struct ResidentShared {
     int slot_of[kMaxReplicas];
     int rep_at[kMaxReplicas];
     int cls_cb[kMaxColorsBatched + 1];
+    int cls_lo[kMaxColorsBatched];   // this CTA's chunk of each class: [lo, hi)
+    int cls_hi[kMaxColorsBatched];
+    int cls_base[kMaxColorsBatched]; // first staged row of the chunk
+    int abort_flag;
 };
 static_assert(sizeof(ResidentShared) + kResidentDynLimitBytes <= 232448, "resident shared memory above 227 KB");
 
-// Neighbour ids and random-stream key of one site.
+// Neighbour ids, random-stream key and peer mask of one site.
 template <int DEG>
 struct Row {
     int nb[DEG > 0 ? DEG : 8];  // missing entries of a shorter row point at the zero spin N
     uint32_t key;
+    uint32_t peers;
 };
 
 struct Stage {
-    const uint16_t *col;   // [N][csr_w] colour-sorted ids, padding -> N (a zero spin)
-    const uint16_t *ids;   // [N] original ids
+    const uint16_t *col;   // [owned][csr_w] colour-sorted ids, padding -> N (a zero spin)
+    const uint16_t *ids;   // [owned] original ids
 };
 
-template <int DEG, bool IS_MET>
-__device__ __forceinline__ void fetch_row(const DevPlan &P, const DevSample &d, const ResidentParams &rp,
-                                          const Stage &stg, int i, Row<DEG> &row)
+// i: colour-sorted site id; l: its staged row.
+template <int DEG, bool IS_MET, bool SPLIT>
+__device__ __forceinline__ void fetch_row(const DevPlan &P, const DevSample &d, const Stage &stg, int i, int l,
+                                          Row<DEG> &row)
 {
     constexpr int W = DEG > 0 ? DEG : 8;
     if (stg.col) {
         // rows of W 16-bit ids, 4-byte aligned (W even)
-        const uint32_t *c = reinterpret_cast<const uint32_t *>(stg.col + (size_t)i * W);
+        const uint32_t *c = reinterpret_cast<const uint32_t *>(stg.col + (size_t)l * W);
 #pragma unroll
         for (int k = 0; k < W / 2; ++k) {
             const uint32_t w = c[k];
@@ -95,7 +111,8 @@ __device__ __forceinline__ void fetch_row(const DevPlan &P, const DevSample &d, 
 #pragma unroll
         for (int k = 0; k < W; ++k) row.nb[k] = (DEG > 0 || k < deg) ? __ldg(cl + rb + k) : d.N;
     }
-    if (IS_MET) row.key = stg.ids ? (uint32_t)stg.ids[i] : (uint32_t)__ldg(P.perm + d.site_off + i);
+    if (IS_MET) row.key = stg.ids ? (uint32_t)stg.ids[l] : (uint32_t)__ldg(P.perm + d.site_off + i);
+    if (SPLIT) row.peers = __ldg(P.push + d.site_off + i);
 }
 
 template <int RV>
@@ -128,28 +145,50 @@ struct RLane {
     unsigned int acc[RV];
 };
 
-// One colour phase over every site of colour c for this CTA's replicas: one
+// Where this CTA sits: its group within the cluster and its chunk rank.
+struct Place {
+    int gi;              // group within the cluster
+    int sr;              // chunk rank within the group (0..G-1)
+};
+
+// The new spins of site i go to this CTA's copy and, with a site split, to
+// the copies of the peers that read the site.
+template <int RV, bool SPLIT>
+__device__ __forceinline__ void put_spins(cg::cluster_group &cluster, const ResidentParams &rp, const Place &pl,
+                                          float2 *p, uint32_t peers, const float2 (&n)[RV])
+{
+    sts_spins<RV>(p, n);
+    if (SPLIT) {
+        while (peers) {
+            const int r = __ffs(peers) - 1;
+            peers &= peers - 1u;
+            sts_spins<RV>(cluster.map_shared_rank(p, (unsigned)(pl.gi * rp.G + r)), n);
+        }
+    }
+}
+
+// One colour phase over this CTA's chunk of colour c for its replicas: one
 // thread per (site, block of RV consecutive replicas).  sp points at the
 // group's spins in shared memory.
-template <bool IS_MET, bool FUSE_E, int RV, int DEG>
+template <bool IS_MET, bool FUSE_E, int RV, int DEG, bool SPLIT>
 __device__ __forceinline__ void rphase(const DevPlan &P, const DevSample &d, const ResidentShared &sh,
-                                       const ResidentParams &rp, const Stage &stg, float2 *sp, int c, uint32_t t,
-                                       RLane<RV> &ln)
+                                       const ResidentParams &rp, const Stage &stg, cg::cluster_group &cluster,
+                                       const Place &pl, float2 *sp, int c, uint32_t t, RLane<RV> &ln)
 {
     constexpr int W = DEG > 0 ? DEG : 8;
-    const int cb = sh.cls_cb[c], ce = sh.cls_cb[c + 1];
-    const int items = (ce - cb) << rp.log2lps;
+    const int cb = sh.cls_cb[c], lo = sh.cls_lo[c], base = sh.cls_base[c];
+    const int items = (sh.cls_hi[c] - lo) << rp.log2lps;
     const int Rg = rp.Rg;
     float2 *spl = sp + ln.lane_rep;
     int q = threadIdx.x;
     if (q >= items) return;
     Row<DEG> cur;
-    fetch_row<DEG, IS_MET>(P, d, rp, stg, cb + (q >> rp.log2lps), cur);
+    fetch_row<DEG, IS_MET, SPLIT>(P, d, stg, lo + (q >> rp.log2lps), base + (q >> rp.log2lps), cur);
     for (; q < items; q += blockDim.x) {
-        const int i = cb + (q >> rp.log2lps);
+        const int i = lo + (q >> rp.log2lps);
         Row<DEG> nxt;
         const int qn = q + (int)blockDim.x;
-        if (qn < items) fetch_row<DEG, IS_MET>(P, d, rp, stg, cb + (qn >> rp.log2lps), nxt);
+        if (qn < items) fetch_row<DEG, IS_MET, SPLIT>(P, d, stg, lo + (qn >> rp.log2lps), base + (qn >> rp.log2lps), nxt);
         float2 s[RV];
         lds_spins<RV>(spl + i * Rg, s);
         float hx[RV], hy[RV], lx[RV], ly[RV];
@@ -185,11 +224,11 @@ __device__ __forceinline__ void rphase(const DevPlan &P, const DevSample &d, con
                 ln.acc[v] += ok ? 1u : 0u;
                 any |= ok;
             }
-            if (any) sts_spins<RV>(spl + i * Rg, n);
+            if (any) put_spins<RV, SPLIT>(cluster, rp, pl, spl + i * Rg, cur.peers, n);
         } else {
 #pragma unroll
             for (int v = 0; v < RV; ++v) overrelax_step(s[v].x, s[v].y, hx[v], hy[v], n[v].x, n[v].y);
-            sts_spins<RV>(spl + i * Rg, n);
+            put_spins<RV, SPLIT>(cluster, rp, pl, spl + i * Rg, cur.peers, n);
         }
         if (FUSE_E) {
 #pragma unroll
@@ -199,9 +238,20 @@ __device__ __forceinline__ void rphase(const DevPlan &P, const DevSample &d, con
     }
 }
 
-// Warp partial of a per-thread value of group replica rl (lanes l and l ^ o,
-// o >= lanes per site, hold the same replicas), one slot per warp so the CTA
-// sum is taken in a fixed order.
+// Phases end at a cluster barrier when peers read this CTA's writes.
+template <bool SPLIT>
+__device__ __forceinline__ void phase_barrier()
+{
+    if (SPLIT) {
+        cluster_arrive();
+        cluster_wait();
+    } else {
+        __syncthreads();
+    }
+}
+
+// Sum over the lanes of a warp that hold the same replicas (lanes l and
+// l ^ o, o >= lanes per site).
 __device__ __forceinline__ float warp_reduce_rep(const ResidentParams &rp, float x)
 {
     for (int o = 16; o >= (1 << rp.log2lps); o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -214,14 +264,17 @@ __device__ __forceinline__ unsigned warp_reduce_rep(const ResidentParams &rp, un
     return x;
 }
 
-template <int RV, int DEG>
+template <int RV, int DEG, bool SPLIT>
 __device__ __forceinline__ void resident_sweeps(const DevPlan &P, const ResidentParams &rp, ResidentShared &sh,
-                                                const Stage &stg, float2 *sp, float *part, unsigned *part_met,
-                                                int s, int group)
+                                                const Stage &stg, cg::cluster_group &cluster, const Place &pl,
+                                                float2 *sp, float *part, unsigned *part_met, int s, int group)
 {
     const DevSample d = P.samples[s];
     const int R = d.R, Rg = rp.Rg;
-    const bool leader = group == 0;
+    const int n_groups = R / Rg;
+    const bool global_barrier = rp.gpc < n_groups;
+    const int rank = (int)cluster.block_rank();
+    const bool leader = group == 0 && pl.sr == 0;
     const int warp = (int)(threadIdx.x >> 5);
     RLane<RV> ln;
     ln.lane_rep = (int)(threadIdx.x & ((1u << rp.log2lps) - 1u)) * RV;
@@ -242,39 +295,42 @@ __device__ __forceinline__ void resident_sweeps(const DevPlan &P, const Resident
         }
         if (met) {
             for (int c = 0; c < d.Q; ++c) {
-                if (orx) rphase<true, false, RV, DEG>(P, d, sh, rp, stg, sp, c, t, ln);
-                else rphase<true, true, RV, DEG>(P, d, sh, rp, stg, sp, c, t, ln);
-                __syncthreads();
+                if (orx) rphase<true, false, RV, DEG, SPLIT>(P, d, sh, rp, stg, cluster, pl, sp, c, t, ln);
+                else rphase<true, true, RV, DEG, SPLIT>(P, d, sh, rp, stg, cluster, pl, sp, c, t, ln);
+                phase_barrier<SPLIT>();
             }
         }
         if (orx) {
             for (int c = 0; c < d.Q; ++c) {
-                rphase<false, true, RV, DEG>(P, d, sh, rp, stg, sp, c, t, ln);
-                __syncthreads();
+                rphase<false, true, RV, DEG, SPLIT>(P, d, sh, rp, stg, cluster, pl, sp, c, t, ln);
+                phase_barrier<SPLIT>();
             }
         }
         // per-warp partials: fused energy, accepted moves and, on measurement
-        // sweeps, magnetisation and Fourier sums of the final spins
+        // sweeps, magnetisation and Fourier sums of this CTA's final sites
         float m[RV][kSums - 1];
 #pragma unroll
         for (int v = 0; v < RV; ++v)
 #pragma unroll
             for (int f = 0; f < kSums - 1; ++f) m[v][f] = 0.f;
         if (measure) {
-            const int items = d.N << rp.log2lps;
-            for (int q = threadIdx.x; q < items; q += blockDim.x) {
-                const int i = q >> rp.log2lps;
-                float2 sv[RV];
-                lds_spins<RV>(sp + ln.lane_rep + i * Rg, sv);
-                const float4 ph = __ldg(reinterpret_cast<const float4 *>(P.phase) + d.site_off + i);
+            for (int c = 0; c < d.Q; ++c) {
+                const int lo = sh.cls_lo[c];
+                const int items = (sh.cls_hi[c] - lo) << rp.log2lps;
+                for (int q = threadIdx.x; q < items; q += blockDim.x) {
+                    const int i = lo + (q >> rp.log2lps);
+                    float2 sv[RV];
+                    lds_spins<RV>(sp + ln.lane_rep + i * Rg, sv);
+                    const float4 ph = __ldg(reinterpret_cast<const float4 *>(P.phase) + d.site_off + i);
 #pragma unroll
-                for (int v = 0; v < RV; ++v) {
-                    m[v][kObsMx - 1] += sv[v].x;
-                    m[v][kObsMy - 1] += sv[v].y;
-                    m[v][kObsF1xRe - 1] += sv[v].x * ph.x; m[v][kObsF1xIm - 1] += sv[v].x * ph.y;
-                    m[v][kObsF1yRe - 1] += sv[v].y * ph.x; m[v][kObsF1yIm - 1] += sv[v].y * ph.y;
-                    m[v][kObsF2xRe - 1] += sv[v].x * ph.z; m[v][kObsF2xIm - 1] += sv[v].x * ph.w;
-                    m[v][kObsF2yRe - 1] += sv[v].y * ph.z; m[v][kObsF2yIm - 1] += sv[v].y * ph.w;
+                    for (int v = 0; v < RV; ++v) {
+                        m[v][kObsMx - 1] += sv[v].x;
+                        m[v][kObsMy - 1] += sv[v].y;
+                        m[v][kObsF1xRe - 1] += sv[v].x * ph.x; m[v][kObsF1xIm - 1] += sv[v].x * ph.y;
+                        m[v][kObsF1yRe - 1] += sv[v].y * ph.x; m[v][kObsF1yIm - 1] += sv[v].y * ph.y;
+                        m[v][kObsF2xRe - 1] += sv[v].x * ph.z; m[v][kObsF2xIm - 1] += sv[v].x * ph.w;
+                        m[v][kObsF2yRe - 1] += sv[v].y * ph.z; m[v][kObsF2yIm - 1] += sv[v].y * ph.w;
+                    }
                 }
             }
         }
@@ -297,14 +353,17 @@ __device__ __forceinline__ void resident_sweeps(const DevPlan &P, const Resident
             }
         }
         __syncthreads();
-        // CTA sums in warp order, in FP64; this CTA alone owns its replicas' slots
+        // CTA sums in warp order, in FP64: stored when this CTA alone covers
+        // its replicas' sites, else added across the G CTAs of the group
         const int buf = (int)(t & 1u);
         double *obs_s = P.obs + ((size_t)buf * P.total_R + d.rep_off) * kObsStride;
         for (int q = threadIdx.x; q < Rg * nf; q += blockDim.x) {
             const int rl = q / nf, f = q % nf;
             double v = 0.0;
             for (int w = 0; w < rp.n_warps; ++w) v += (double)part[((size_t)f * rp.n_warps + w) * Rg + rl];
-            __stcg(obs_s + (size_t)(group * Rg + rl) * kObsStride + f, v);
+            double *dst = obs_s + (size_t)(group * Rg + rl) * kObsStride + f;
+            if (SPLIT) atomicAdd(dst, v);
+            else __stcg(dst, v);
         }
         if (met && threadIdx.x < Rg) {
             const int r = group * Rg + threadIdx.x;
@@ -312,26 +371,56 @@ __device__ __forceinline__ void resident_sweeps(const DevPlan &P, const Resident
             for (int w = 0; w < rp.n_warps; ++w) n += part_met[w * Rg + threadIdx.x];
             if (n) atomicAdd(&P.met_acc[d.rep_off + sh.slot_of[r]], (unsigned long long)n);
         }
+        if (global_barrier) {
+            // every CTA of the sample signs in once its sums are out; the first
+            // CTA of each cluster waits for all of them (bounded) and tells the
+            // other CTAs of its cluster the outcome through their shared memory
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) atomicAdd(&P.barrier[s], 1u);
+            if (rank == 0 && threadIdx.x == 0) {
+                int failed = 0;
+                const unsigned int target = (unsigned int)(rp.G * n_groups * (it + 1));
+                if (!wait_counter_at_least(&P.barrier[s], target, kResidentBarrierPolls)) {
+                    atomicExch(P.status, XYL_ETIMEOUT);
+                    failed = 1;
+                }
+                __threadfence();
+                for (int k = 0; k < rp.G * rp.gpc; ++k) *cluster.map_shared_rank(&sh.abort_flag, k) = failed;
+            }
+        }
         // every group's sums are out before any CTA reads them
         cluster_arrive();
         cluster_wait();
+        if (global_barrier && *(volatile int *)&sh.abort_flag) break;
         for (int k = threadIdx.x; k < R; k += blockDim.x) sh.E[k] = __ldcg(obs_s + (size_t)k * kObsStride + kObsE);
         __syncthreads();
         pt_and_record(P, d, sh.E, sh.rep_at, sh.slot_of, t, rp.ops, leader, met, measure, obs_s);
+        if (SPLIT && pl.sr == 0) {
+            // clear this group's slots of the buffer the next sweep adds into:
+            // every reader of it finished before the barrier just passed
+            double *nxt = P.obs + ((size_t)(buf ^ 1) * P.total_R + d.rep_off + group * Rg) * kObsStride;
+            for (int q = threadIdx.x; q < Rg * kObsStride; q += blockDim.x) nxt[q] = 0.0;
+        }
         ++t;
         __syncthreads();
     }
     if (leader && threadIdx.x == 0) P.sweep[s] = t;
 }
 
-template <int RV, int DEG>
+template <int RV, int DEG, bool SPLIT>
 __global__ void __maxnreg__(96) resident_kernel(DevPlan P, ResidentParams rp)
 {
     __shared__ ResidentShared sh;
     extern __shared__ __align__(16) unsigned char dyn[];
     cg::cluster_group cluster = cg::this_cluster();
-    const int group = (int)cluster.block_rank();
-    const int s = rp.sample_begin + (int)(blockIdx.x / (unsigned)rp.cpc);
+    const int rank = (int)cluster.block_rank();
+    Place pl;
+    pl.gi = rank / rp.G;
+    pl.sr = rank - pl.gi * rp.G;
+    const int unit = rp.unit_begin + (int)(blockIdx.x / (unsigned)(rp.G * rp.gpc)) * rp.gpc + pl.gi;
+    const int2 ug = rp.units[unit];
+    const int s = ug.x, group = ug.y;
     const DevSample d = P.samples[s];
     const int R = d.R, Rg = rp.Rg, N = d.N;
 
@@ -341,7 +430,22 @@ __global__ void __maxnreg__(96) resident_kernel(DevPlan P, ResidentParams rp)
         sh.beta[k] = (float)P.beta[d.rep_off + k];
         sh.delta[k] = (float)P.delta[d.rep_off + k];
     }
-    for (int c = threadIdx.x; c <= d.Q; c += blockDim.x) sh.cls_cb[c] = P.color_ptr[d.color_off + c];
+    if (threadIdx.x == 0) {
+        sh.abort_flag = 0;
+        // this CTA's chunk of every colour class
+        int base = 0;
+        for (int c = 0; c < d.Q; ++c) {
+            const int cb = P.color_ptr[d.color_off + c], ce = P.color_ptr[d.color_off + c + 1];
+            const int chunk = (ce - cb + rp.G - 1) / rp.G;
+            const int lo = min(ce, cb + pl.sr * chunk), hi = min(ce, lo + chunk);
+            sh.cls_cb[c] = cb;
+            sh.cls_lo[c] = lo;
+            sh.cls_hi[c] = hi;
+            sh.cls_base[c] = base;
+            base += hi - lo;
+        }
+        sh.cls_cb[d.Q] = P.color_ptr[d.color_off + d.Q];
+    }
 
     // the group's spins of every site, then one zero row (target of padded CSR entries)
     float2 *sp = reinterpret_cast<float2 *>(dyn);
@@ -351,42 +455,55 @@ __global__ void __maxnreg__(96) resident_kernel(DevPlan P, ResidentParams rp)
         sp[k] = __ldcg(gsp + (size_t)i * R + rl);
     }
     for (int k = threadIdx.x; k < Rg; k += blockDim.x) sp[(size_t)N * Rg + k] = make_float2(0.f, 0.f);
+    __syncthreads();
+    // rows and site ids of this CTA's own sites
     Stage stg{nullptr, nullptr};
-    if (rp.ids) {
-        uint16_t *ids = reinterpret_cast<uint16_t *>(dyn + rp.off_ids);
-        for (int i = threadIdx.x; i < N; i += blockDim.x) ids[i] = (uint16_t)P.perm[d.site_off + i];
-        stg.ids = ids;
-    }
-    if (rp.csr_w) {
-        uint16_t *col = reinterpret_cast<uint16_t *>(dyn + rp.off_col);
+    uint16_t *ids = rp.ids ? reinterpret_cast<uint16_t *>(dyn + rp.off_ids) : nullptr;
+    uint16_t *col = rp.csr_w ? reinterpret_cast<uint16_t *>(dyn + rp.off_col) : nullptr;
+    if (ids || col) {
         const int W = rp.csr_w;
-        for (int q = threadIdx.x; q < N * W; q += blockDim.x) {
-            const int i = q / W, k = q - i * W;
-            const int rb = P.row_ptr[d.row_off + i], re = P.row_ptr[d.row_off + i + 1];
-            col[q] = (uint16_t)(k < re - rb ? P.col[d.col_off + rb + k] : N);
+        for (int c = 0; c < d.Q; ++c) {
+            const int lo = sh.cls_lo[c], n = sh.cls_hi[c] - lo, base = sh.cls_base[c];
+            for (int q = threadIdx.x; q < n; q += blockDim.x) {
+                const int i = lo + q, l = base + q;
+                if (ids) ids[l] = (uint16_t)P.perm[d.site_off + i];
+                if (col) {
+                    const int rb = P.row_ptr[d.row_off + i], re = P.row_ptr[d.row_off + i + 1];
+                    for (int k = 0; k < W; ++k) col[(size_t)l * W + k] = (uint16_t)(k < re - rb ? P.col[d.col_off + rb + k] : N);
+                }
+            }
         }
-        stg.col = col;
     }
+    stg.ids = ids;
+    stg.col = col;
     float *part = reinterpret_cast<float *>(dyn + rp.off_part);
     unsigned *part_met = reinterpret_cast<unsigned *>(dyn + rp.off_met);
-    __syncthreads();
-    resident_sweeps<RV, DEG>(P, rp, sh, stg, sp, part, part_met, s, group);
-    // write the spins back
+    // peers write into this CTA's copy only after it holds the starting spins
+    if (SPLIT) cluster.sync();
+    else __syncthreads();
+    resident_sweeps<RV, DEG, SPLIT>(P, rp, sh, stg, cluster, pl, sp, part, part_met, s, group);
+    // write this CTA's own sites back (every copy agrees after the last barrier)
     float2 *gspw = reinterpret_cast<float2 *>(P.spins) + d.spin_off + group * Rg;
-    for (int k = threadIdx.x; k < N * Rg; k += blockDim.x) {
-        const int i = k / Rg, rl = k - i * Rg;
-        __stcg(gspw + (size_t)i * R + rl, sp[k]);
+    for (int c = 0; c < d.Q; ++c) {
+        const int lo = sh.cls_lo[c], n = (sh.cls_hi[c] - lo) * Rg;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const int i = lo + k / Rg, rl = k % Rg;
+            __stcg(gspw + (size_t)i * R + rl, sp[(size_t)i * Rg + rl]);
+        }
     }
 }
 
 using KernelFn = void (*)(DevPlan, ResidentParams);
 
-KernelFn pick_resident(const BatchedShape &B)
+template <bool SPLIT>
+KernelFn pick_split(const BatchedShape &B)
 {
     const bool rv2 = B.Rg >= 2;
-    if (B.fixed_deg == 6) return rv2 ? resident_kernel<2, 6> : resident_kernel<1, 6>;
-    return rv2 ? resident_kernel<2, -8> : resident_kernel<1, -8>;
+    if (B.fixed_deg == 6) return rv2 ? resident_kernel<2, 6, SPLIT> : resident_kernel<1, 6, SPLIT>;
+    return rv2 ? resident_kernel<2, -8, SPLIT> : resident_kernel<1, -8, SPLIT>;
 }
+
+KernelFn pick_resident(const BatchedShape &B) { return B.G > 1 ? pick_split<true>(B) : pick_split<false>(B); }
 
 cudaError_t set_resident_attributes(KernelFn k)
 {
@@ -424,13 +541,15 @@ cudaError_t resident_max_active_clusters(const BatchedShape &B, int *clusters)
     return cudaOccupancyMaxActiveClusters(clusters, kernel, &cfg);
 }
 
-cudaError_t launch_resident(const DevPlan &P, const BatchedShape &B, int sample_begin, int sample_count,
-                            int n_sweeps, uint32_t ops, int measure_every, cudaStream_t st)
+cudaError_t launch_resident(const DevPlan &P, const BatchedShape &B, const int2 *d_units, int unit_begin,
+                            int unit_count, int n_sweeps, uint32_t ops, int measure_every, cudaStream_t st)
 {
-    if (sample_count <= 0) return cudaSuccess;
+    if (unit_count <= 0) return cudaSuccess;
     ResidentParams rp;
-    rp.sample_begin = sample_begin;
-    rp.cpc = B.cpc;
+    rp.units = d_units;
+    rp.unit_begin = unit_begin;
+    rp.G = B.G;
+    rp.gpc = B.gpc;
     rp.Rg = B.Rg;
     const int rv = B.Rg >= 2 ? 2 : 1;
     rp.log2lps = 0;
@@ -446,7 +565,7 @@ cudaError_t launch_resident(const DevPlan &P, const BatchedShape &B, int sample_
     rp.csr_w = B.rs_csr_w;
     rp.ids = B.rs_ids ? 1 : 0;
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = resident_config(B, (unsigned)(sample_count * B.cpc), attr);
+    cudaLaunchConfig_t cfg = resident_config(B, (unsigned)(unit_count / B.gpc * B.cpc), attr);
     cfg.stream = st;
     return cudaLaunchKernelEx(&cfg, pick_resident(B), P, rp);
 }

@@ -66,6 +66,7 @@ def _rep_slice(plan, sample):
 # its resident shape (spins in shared memory) and its global-memory shape
 VARIANTS = {
     "FP32_RESIDENT": ("FP32_BATCHED", {"resident": 1}),
+    "FP32_SPLIT": ("FP32_BATCHED", {"resident": 1, "cluster": 4}),
     "FP32_GLOBAL": ("FP32_BATCHED", {"resident": -1}),
     "FP32_PLAIN": ("FP32_PLAIN", {}),
     "FP64_PLAIN": ("FP64_PLAIN", {}),
@@ -147,7 +148,7 @@ def _fp32_per_sweep(plan, sims, samples, n_sweeps, ops, N_of):
     return compared, explained, worst
 
 
-@pytest.mark.parametrize("engine_name", ["FP32_RESIDENT", "FP32_GLOBAL", "FP32_PLAIN"])
+@pytest.mark.parametrize("engine_name", ["FP32_RESIDENT", "FP32_SPLIT", "FP32_GLOBAL", "FP32_PLAIN"])
 @pytest.mark.parametrize("name", ["C1", "C2"])
 def test_fp32_energy_matches_oracle(env, orc, name, engine_name):
     xyl, wl = env
@@ -217,7 +218,7 @@ def _edge_plan(xyl, edges, n, betas, deltas, variant, xy=None, L=0, seed=5):
     return p
 
 
-ENGINES = ["FP32_RESIDENT", "FP32_GLOBAL", "FP64_PLAIN", "FP32_PLAIN"]
+ENGINES = ["FP32_RESIDENT", "FP32_SPLIT", "FP32_GLOBAL", "FP64_PLAIN", "FP32_PLAIN"]
 
 
 @pytest.mark.parametrize("engine_name", ENGINES)
@@ -333,13 +334,13 @@ def test_full_size_batched_sampled_parity(env, orc, name, sampled, resident):
 
 
 # --------------------------------------------------------------- determinism, checkpoint, recovery
-@pytest.mark.parametrize("resident", [1, -1])
-def test_batched_runs_are_deterministic_and_resumable(env, resident):
+@pytest.mark.parametrize("shape", [dict(resident=1), dict(resident=1, cluster=4), dict(resident=-1)])
+def test_batched_runs_are_deterministic_and_resumable(env, shape):
     xyl, wl = env
     cfg = wl.config("C2")
     graphs = wl.build_graphs(cfg)
-    a, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, resident=resident)
-    b, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, resident=resident)
+    a, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, **shape)
+    b, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, **shape)
     for p in (a, b):
         p.bind()
         p.init_spins()
@@ -359,6 +360,25 @@ def test_batched_runs_are_deterministic_and_resumable(env, resident):
     assert a.status() == b.status() == (0, 25)
 
 
+@pytest.mark.parametrize("shape", [dict(resident=-1), dict(resident=1), dict(resident=1, cluster=4)])
+def test_standalone_pt_and_measure_between_sweeps(env, shape):
+    """xyl_pt_swap and xyl_measure between batched sweeps: the next sweep's
+    fused energies still equal a fresh FP64 recomputation."""
+    xyl, wl = env
+    cfg = wl.config("C2")
+    plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, **shape)
+    plan.bind()
+    plan.init_spins()
+    plan.sweep(3, ALL)
+    plan.measure()
+    plan.pt_swap()
+    plan.sweep(2, ALL)
+    E = plan.energies()
+    plan.recompute()
+    assert np.max(np.abs(plan.energies() - E)) / 16384 < 1e-5
+    assert np.all(plan.read_observables()["acc"][:, ACC["n"]] == 6)  # five sweeps and one xyl_measure
+
+
 def test_recompute_bounds_fp32_drift(env):
     xyl, wl = env
     cfg = wl.config("C2")
@@ -373,15 +393,16 @@ def test_recompute_bounds_fp32_drift(env):
     assert np.max(np.abs(np.hypot(s[:, 0], s[:, 1]) - 1)) < 1e-6
 
 
-def test_split_sample_wait_times_out_and_recovers(env):
+@pytest.mark.parametrize("shape", [dict(group=4, resident=-1), dict(group=1, cluster=4, resident=1)])
+def test_split_sample_wait_times_out_and_recovers(env, shape):
     """Running one of a sample's replica groups alone makes its bounded wait for
     the other groups give up: status ETIMEOUT, context still usable."""
     xyl, wl = env
     cfg = wl.config("C2")
-    plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, group=4, resident=-1)
+    plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, **shape)
     plan.bind()
     plan.init_spins()
-    assert plan.unit_count() == 4
+    assert plan.unit_count() == cfg.n_temps // shape["group"]
     plan.sweep_units(0, 1, 3, ALL)
     status, _ = plan.status()
     assert status == xyl.ETIMEOUT
@@ -404,7 +425,8 @@ def test_launch_shape_does_not_change_the_trajectory(env):
     shapes = [dict(group=16, cluster=16, block=512, resident=-1), dict(group=1, cluster=8, block=256, resident=-1),
               dict(group=4, cluster=4, block=128, stage=-1, resident=-1),
               dict(group=4, cluster=16, block=640, resident=-1),
-              dict(group=1, block=640, resident=1), dict(group=1, block=256, stage=-1, resident=1)]
+              dict(group=1, block=640, resident=1), dict(group=1, block=256, stage=-1, resident=1),
+              dict(group=1, cluster=4, block=640, resident=1), dict(group=1, cluster=2, block=384, stage=-1, resident=1)]
     ref = None
     for shp in shapes:
         p, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, **shp)

@@ -137,16 +137,19 @@ def test_resident_shape_selection_without_gpu(xyl):
         g = xyl.build_graph_csr(L, 6, 3.5, 1, 0)
         return xyl.Plan([(g, 0, [1.0] * R, [1.0] * R)], engine=xyl.FP32_BATCHED, device="cpu", **kw).tuning()
 
-    t = tuning(128, 16)  # 16384 sites: one replica per CTA (128 KB), a cluster of 16
-    assert (t["resident"], t["group"], t["cluster"]) == (1, 1, 16)
-    t = tuning(64, 24)   # 4096 sites: four replicas per CTA, a cluster of 6, CSR staged
-    assert (t["resident"], t["group"], t["cluster"], t["stage"]) == (1, 4, 6, 1)
+    t = tuning(128, 16)  # 16384 sites: one replica per CTA (128 KB), the 16 groups in one cluster
+    assert (t["resident"], t["group"], t["cluster"]) == (1, 1, 1)
+    t = tuning(64, 24)   # 4096 sites: four replicas per CTA, six groups per cluster, CSR staged
+    assert (t["resident"], t["group"], t["cluster"], t["stage"]) == (1, 4, 1, 1)
+    t = tuning(128, 16, cluster=8)  # each replica's sites split over 8 CTAs
+    assert (t["resident"], t["group"], t["cluster"], t["stage"]) == (1, 1, 8, 1)
     t = tuning(64, 24, stage=-1)
     assert (t["resident"], t["stage"]) == (1, -1)
     t = tuning(256, 8)   # 65536 sites: 512 KB per replica, does not fit
     assert t["resident"] == -1
-    t = tuning(128, 32)  # would need 32 groups of one replica
+    t = tuning(128, 32)  # 32 groups of one replica: no cluster holds them all
     assert t["resident"] == -1
+    assert tuning(128, 32, resident=1)["resident"] == 1  # asked for: groups meet at a global barrier
     assert tuning(64, 24, resident=-1)["resident"] == -1
     with pytest.raises(xyl.XylError) as e:
         tuning(256, 8, resident=1)

@@ -25,13 +25,13 @@ def env():
     return xyl, workloads
 
 
-@pytest.mark.parametrize("resident", [1, -1])
-def test_noalloc_sweep_matches_sweep_twice(env, resident):
+@pytest.mark.parametrize("shape", [dict(resident=1), dict(resident=1, cluster=4), dict(resident=-1)])
+def test_noalloc_sweep_matches_sweep_twice(env, shape):
     xyl, wl = env
     cfg = wl.config("C2")
     graphs = wl.build_graphs(cfg)
-    ref, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, resident=resident)
-    new, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, resident=resident)
+    ref, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, **shape)
+    new, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, **shape)
     for p in (ref, new):
         p.bind()
         p.init_spins()
