@@ -171,7 +171,14 @@ bool resident_fit(const xyl_plan *p, int g, int G, int block, int stage, Batched
     B.rs_off_met = spins + part;
     B.rs_ids = false;
     B.rs_csr_w = 0;
-    B.rs_off_ids = B.rs_off_col = 0;
+    B.rs_off_ids = B.rs_off_col = B.rs_off_peers = 0;
+    if (G > 1) {
+        const size_t peers = a16((size_t)owned * sizeof(uint16_t));
+        if (off + peers <= kResidentDynLimitBytes) {
+            B.rs_off_peers = off;
+            off += peers;
+        }
+    }
     if (max_N <= 65535) {  // ids and the padding id N fit 16 bits
         const size_t ids = a16((size_t)owned * sizeof(uint16_t));
         if (off + ids <= kResidentDynLimitBytes) {
@@ -1070,8 +1077,10 @@ int xyl_autotune(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_ev
             if (!divides) continue;
             int64_t units = 0;
             for (auto &h : p->hs) units += h.R / g;
-            for (int G = 1; G <= 16; G *= 2) {
-                // split a resident group across CTAs only while the batch leaves SMs idle
+            for (int G : {1, 2, 3, 4, 5, 6, 7, 8, 12, 16}) {
+                // global-memory shape: powers of two; split a resident group
+                // across CTAs only while the batch leaves SMs idle
+                if (!res && (G & (G - 1))) continue;
                 if (res && G > 1 && units * G > 2 * (int64_t)n_sm) continue;
                 for (int block : {128, 256, 384, 512, 640}) {
                     if (res ? block == 128 : block == 384) continue;

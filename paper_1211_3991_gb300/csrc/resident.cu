@@ -51,7 +51,7 @@ struct ResidentParams {
     int measure_every;
     int n_warps;
     // dynamic shared memory layout (byte offsets)
-    int off_ids, off_col, off_part, off_met;
+    int off_ids, off_col, off_part, off_met, off_peers;  // off_peers 0: masks read from global memory
     int csr_w;           // staged CSR row width (6 or 8), 0 = rows read from global memory
     int ids;             // random-stream site ids staged as 16-bit values
 };
@@ -79,8 +79,9 @@ struct Row {
 };
 
 struct Stage {
-    const uint16_t *col;   // [owned][csr_w] colour-sorted ids, padding -> N (a zero spin)
-    const uint16_t *ids;   // [owned] original ids
+    const uint16_t *col;    // [owned][csr_w] colour-sorted ids, padding -> N (a zero spin)
+    const uint16_t *ids;    // [owned] original ids
+    const uint16_t *peers;  // [owned] peer masks (site split)
 };
 
 // i: colour-sorted site id; l: its staged row.
@@ -112,7 +113,7 @@ __device__ __forceinline__ void fetch_row(const DevPlan &P, const DevSample &d, 
         for (int k = 0; k < W; ++k) row.nb[k] = (DEG > 0 || k < deg) ? __ldg(cl + rb + k) : d.N;
     }
     if (IS_MET) row.key = stg.ids ? (uint32_t)stg.ids[l] : (uint32_t)__ldg(P.perm + d.site_off + i);
-    if (SPLIT) row.peers = __ldg(P.push + d.site_off + i);
+    if (SPLIT) row.peers = stg.peers ? stg.peers[l] : __ldg(P.push + d.site_off + i);
 }
 
 template <int RV>
@@ -456,17 +457,19 @@ __global__ void __maxnreg__(96) resident_kernel(DevPlan P, ResidentParams rp)
     }
     for (int k = threadIdx.x; k < Rg; k += blockDim.x) sp[(size_t)N * Rg + k] = make_float2(0.f, 0.f);
     __syncthreads();
-    // rows and site ids of this CTA's own sites
-    Stage stg{nullptr, nullptr};
+    // rows, site ids and peer masks of this CTA's own sites
+    Stage stg{nullptr, nullptr, nullptr};
     uint16_t *ids = rp.ids ? reinterpret_cast<uint16_t *>(dyn + rp.off_ids) : nullptr;
     uint16_t *col = rp.csr_w ? reinterpret_cast<uint16_t *>(dyn + rp.off_col) : nullptr;
-    if (ids || col) {
+    uint16_t *peers = (SPLIT && rp.off_peers) ? reinterpret_cast<uint16_t *>(dyn + rp.off_peers) : nullptr;
+    if (ids || col || peers) {
         const int W = rp.csr_w;
         for (int c = 0; c < d.Q; ++c) {
             const int lo = sh.cls_lo[c], n = sh.cls_hi[c] - lo, base = sh.cls_base[c];
             for (int q = threadIdx.x; q < n; q += blockDim.x) {
                 const int i = lo + q, l = base + q;
                 if (ids) ids[l] = (uint16_t)P.perm[d.site_off + i];
+                if (peers) peers[l] = P.push[d.site_off + i];
                 if (col) {
                     const int rb = P.row_ptr[d.row_off + i], re = P.row_ptr[d.row_off + i + 1];
                     for (int k = 0; k < W; ++k) col[(size_t)l * W + k] = (uint16_t)(k < re - rb ? P.col[d.col_off + rb + k] : N);
@@ -476,6 +479,7 @@ __global__ void __maxnreg__(96) resident_kernel(DevPlan P, ResidentParams rp)
     }
     stg.ids = ids;
     stg.col = col;
+    stg.peers = peers;
     float *part = reinterpret_cast<float *>(dyn + rp.off_part);
     unsigned *part_met = reinterpret_cast<unsigned *>(dyn + rp.off_met);
     // peers write into this CTA's copy only after it holds the starting spins
@@ -562,6 +566,7 @@ cudaError_t launch_resident(const DevPlan &P, const BatchedShape &B, const int2 
     rp.off_col = (int)B.rs_off_col;
     rp.off_part = (int)B.rs_off_part;
     rp.off_met = (int)B.rs_off_met;
+    rp.off_peers = (int)B.rs_off_peers;
     rp.csr_w = B.rs_csr_w;
     rp.ids = B.rs_ids ? 1 : 0;
     cudaLaunchAttribute attr[1];
