@@ -141,7 +141,7 @@ typedef struct {
 } xyl_sample;
 
 typedef struct {
-    int32_t block;           /* threads per CTA of the batched engine, <= 672 (0 = default 512) */
+    int32_t block;           /* threads per CTA of the batched engine, <= 672, resident shape <= 1024 (0 = 512) */
     int32_t cluster;         /* CTAs per cluster of the batched engine (0 = tuned default) */
     int32_t group;           /* replicas per cluster, a power of two dividing every n_temps (0 = default) */
     int32_t recompute_every; /* FP64 energy recompute + renormalise every this many sweeps (0 = never) */

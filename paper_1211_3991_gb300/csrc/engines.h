@@ -43,6 +43,8 @@ struct BatchedShape {
 constexpr size_t kStageLimitBytes = 160 * 1024;
 // Dynamic shared memory of a resident-shape CTA (spins, staged tables, partial sums).
 constexpr size_t kResidentDynLimitBytes = 220 * 1024;
+// Resident CTAs above this many threads use the 64-register kernel (up to 1024 threads).
+constexpr int kResidentNarrowMaxThreads = 672;
 
 // Fixed scratch of xyl_sweep_noalloc (per GPU, for the life of the library).
 constexpr size_t kNoAllocScratchBytes = 1u << 20;

@@ -213,7 +213,9 @@ int apply_shape(xyl_plan *p, int g, int G, int block, int stage, int resident)
     for (auto &h : p->hs)
         if (h.R % g) return fail(XYL_EINVAL, "group=%d does not divide n_temps=%d", g, h.R);
     if (G < 1 || G > 16) return fail(XYL_EINVAL, "cluster=%d must be in [1, 16]", G);
-    if (block < 32 || block % 32 || block > 672) return fail(XYL_EINVAL, "block=%d must be a multiple of 32 <= 672", block);
+    const int max_block = resident ? 1024 : 672;
+    if (block < 32 || block % 32 || block > max_block)
+        return fail(XYL_EINVAL, "block=%d must be a multiple of 32 <= %d", block, max_block);
     BatchedShape &B = p->bshape;
     B = BatchedShape{};
     B.G = G;
@@ -1082,8 +1084,8 @@ int xyl_autotune(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_ev
                 // across CTAs only while the batch leaves SMs idle
                 if (!res && (G & (G - 1))) continue;
                 if (res && G > 1 && units * G > 2 * (int64_t)n_sm) continue;
-                for (int block : {128, 256, 384, 512, 640}) {
-                    if (res ? block == 128 : block == 384) continue;
+                for (int block : {128, 256, 384, 512, 640, 768, 1024}) {
+                    if (res ? block == 128 : (block == 384 || block > 672)) continue;
                     if (apply_shape(p, g, G, block, keep_stage, res) || configure_batched(p, st)) continue;
                     float ms = 0.f;
                     bool ok = true;

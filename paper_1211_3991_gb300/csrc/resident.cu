@@ -354,23 +354,28 @@ __device__ __forceinline__ void resident_sweeps(const DevPlan &P, const Resident
             }
         }
         __syncthreads();
-        // CTA sums in warp order, in FP64: stored when this CTA alone covers
-        // its replicas' sites, else added across the G CTAs of the group
+        // CTA sums: one warp per (replica, field) adds the warp partials in a
+        // fixed shuffle tree (lane w holds warp w's); stored when this CTA
+        // alone covers its replicas' sites, else added across the G CTAs
         const int buf = (int)(t & 1u);
         double *obs_s = P.obs + ((size_t)buf * P.total_R + d.rep_off) * kObsStride;
-        for (int q = threadIdx.x; q < Rg * nf; q += blockDim.x) {
+        const int lane = (int)(threadIdx.x & 31u);
+        for (int q = warp; q < Rg * nf; q += rp.n_warps) {
             const int rl = q / nf, f = q % nf;
-            double v = 0.0;
-            for (int w = 0; w < rp.n_warps; ++w) v += (double)part[((size_t)f * rp.n_warps + w) * Rg + rl];
+            float v = lane < rp.n_warps ? part[((size_t)f * rp.n_warps + lane) * Rg + rl] : 0.f;
+            v = warp_sum(v);
             double *dst = obs_s + (size_t)(group * Rg + rl) * kObsStride + f;
-            if (SPLIT) atomicAdd(dst, v);
-            else __stcg(dst, v);
+            if (lane == 0) {
+                if (SPLIT) atomicAdd(dst, (double)v);
+                else __stcg(dst, (double)v);
+            }
         }
-        if (met && threadIdx.x < Rg) {
-            const int r = group * Rg + threadIdx.x;
-            unsigned int n = 0;
-            for (int w = 0; w < rp.n_warps; ++w) n += part_met[w * Rg + threadIdx.x];
-            if (n) atomicAdd(&P.met_acc[d.rep_off + sh.slot_of[r]], (unsigned long long)n);
+        if (met) {
+            for (int rl = warp; rl < Rg; rl += rp.n_warps) {
+                unsigned n = lane < rp.n_warps ? part_met[lane * Rg + rl] : 0u;
+                n = warp_sum(n);
+                if (lane == 0 && n) atomicAdd(&P.met_acc[d.rep_off + sh.slot_of[group * Rg + rl]], (unsigned long long)n);
+            }
         }
         if (global_barrier) {
             // every CTA of the sample signs in once its sums are out; the first
@@ -410,7 +415,7 @@ __device__ __forceinline__ void resident_sweeps(const DevPlan &P, const Resident
 }
 
 template <int RV, int DEG, bool SPLIT>
-__global__ void __maxnreg__(96) resident_kernel(DevPlan P, ResidentParams rp)
+__device__ __forceinline__ void resident_body(const DevPlan &P, const ResidentParams &rp)
 {
     __shared__ ResidentShared sh;
     extern __shared__ __align__(16) unsigned char dyn[];
@@ -497,14 +502,33 @@ __global__ void __maxnreg__(96) resident_kernel(DevPlan P, ResidentParams rp)
     }
 }
 
+// Up to 672 threads with 96 registers each, or up to 1024 with 64.
+template <int RV, int DEG, bool SPLIT>
+__global__ void __maxnreg__(96) resident_kernel(DevPlan P, ResidentParams rp)
+{
+    resident_body<RV, DEG, SPLIT>(P, rp);
+}
+
+template <int RV, int DEG, bool SPLIT>
+__global__ void __launch_bounds__(1024, 1) resident_kernel_wide(DevPlan P, ResidentParams rp)
+{
+    resident_body<RV, DEG, SPLIT>(P, rp);
+}
+
 using KernelFn = void (*)(DevPlan, ResidentParams);
+
+template <int RV, int DEG, bool SPLIT>
+KernelFn pick_width(const BatchedShape &B)
+{
+    return B.block > kResidentNarrowMaxThreads ? resident_kernel_wide<RV, DEG, SPLIT> : resident_kernel<RV, DEG, SPLIT>;
+}
 
 template <bool SPLIT>
 KernelFn pick_split(const BatchedShape &B)
 {
     const bool rv2 = B.Rg >= 2;
-    if (B.fixed_deg == 6) return rv2 ? resident_kernel<2, 6, SPLIT> : resident_kernel<1, 6, SPLIT>;
-    return rv2 ? resident_kernel<2, -8, SPLIT> : resident_kernel<1, -8, SPLIT>;
+    if (B.fixed_deg == 6) return rv2 ? pick_width<2, 6, SPLIT>(B) : pick_width<1, 6, SPLIT>(B);
+    return rv2 ? pick_width<2, -8, SPLIT>(B) : pick_width<1, -8, SPLIT>(B);
 }
 
 KernelFn pick_resident(const BatchedShape &B) { return B.G > 1 ? pick_split<true>(B) : pick_split<false>(B); }

@@ -14,6 +14,22 @@ constexpr int kMaxReplicas = 256;
 __device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
+// The FP64 test u < exp(x), mostly decided without a double-precision exp:
+// exp(x) >= 1 > u for x >= 0; for x < -80, exp(x) < 2^-53, so only u = 0
+// passes; otherwise a single-precision estimate (relative error below 1e-5
+// for |x| <= 80: the rounding of x to float and of x log2(e), and the 2^-22
+// error of the hardware exponential) decides whenever u lies outside its
+// error band, and the double-precision exp decides the rest.
+__device__ __forceinline__ bool pt_accept(double u, double x)
+{
+    if (x >= 0.0) return true;
+    if (x < -80.0) return u == 0.0;
+    const double e = (double)__expf((float)x);
+    const double gap = u - e;
+    if (fabs(gap) > 2e-5 * e) return gap < 0.0;
+    return u < exp(x);
+}
+
 // App. B "Improved equilibrium dynamics": at sweep t, slots (k, k+1) with k of
 // the parity of t swap their replicas with probability min(1, exp((b_k -
 // b_k+1)(E_k - E_k+1))), one PT draw per pair (FP64 arithmetic and 53-bit
@@ -32,7 +48,7 @@ __device__ __forceinline__ void pt_and_record(const DevPlan &P, const DevSample 
             const int a = rep_at[k], b = rep_at[k + 1];
             const double x = (P.beta[d.rep_off + k] - P.beta[d.rep_off + k + 1]) * (E[a] - E[b]);
             const Words4 w = philox_draw((uint32_t)k, t, kPurposePt, 0u, d.sample_id, P.key);
-            const bool accept = uniform53(w.w0, w.w1) < exp(x);
+            const bool accept = pt_accept(uniform53(w.w0, w.w1), x);
             if (leader) P.pt_try[d.rep_off + k] += 1ull;
             if (accept) {
                 rep_at[k] = b;

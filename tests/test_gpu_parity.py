@@ -426,7 +426,8 @@ def test_launch_shape_does_not_change_the_trajectory(env):
               dict(group=4, cluster=4, block=128, stage=-1, resident=-1),
               dict(group=4, cluster=16, block=640, resident=-1),
               dict(group=1, block=640, resident=1), dict(group=1, block=256, stage=-1, resident=1),
-              dict(group=1, cluster=4, block=640, resident=1), dict(group=1, cluster=2, block=384, stage=-1, resident=1)]
+              dict(group=1, cluster=4, block=640, resident=1), dict(group=1, cluster=2, block=384, stage=-1, resident=1),
+              dict(group=1, block=1024, resident=1), dict(group=1, cluster=6, block=768, resident=1)]
     ref = None
     for shp in shapes:
         p, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, **shp)
@@ -445,6 +446,29 @@ def test_launch_shape_does_not_change_the_trajectory(env):
     p.init_spins()
     p.sweep(6, NO_PT)
     assert np.array_equal(np.stack([p.spins(0, r) for r in range(cfg.n_temps)]), ref[0])
+
+
+def test_replica_pairs_same_spins_in_every_shape(env):
+    """Four L=64 samples x 24 temperatures (replicas updated in pairs, RV = 2):
+    the resident shape at 512 and 1024 threads, split over three CTAs, and the
+    global-memory shape give bit-identical spins (Metropolis + overrelaxation)."""
+    xyl, wl = env
+    cfg = wl.config("C3")
+    cfg.graphs = cfg.graphs[:2] + cfg.graphs[256:257] + cfg.graphs[767:768]
+    cfg.stream_ids = [0, 1, 256, 767]
+    graphs = wl.build_graphs(cfg)
+    ref = None
+    for shp in (dict(group=4, block=512, resident=1), dict(group=4, block=1024, resident=1),
+                dict(group=2, cluster=3, block=768, resident=1), dict(group=8, cluster=2, block=640, resident=-1)):
+        p, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, **shp)
+        p.bind()
+        p.init_spins()
+        p.sweep(5, NO_PT)
+        got = np.stack([p.spins(s, r) for s in range(4) for r in range(cfg.n_temps)])
+        if ref is None:
+            ref = got
+        else:
+            assert np.array_equal(got, ref), shp
 
 
 def test_autotune_restores_state(env):
