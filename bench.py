@@ -143,8 +143,11 @@ def reduce_over_ranks(elapsed, units, world, device):
     return float(t.item()), float(u.item())
 
 
-def run_oracle_sample(cfg, sweeps, sample_index=0):
-    """The sequential FP64 oracle on one sample of the workload; returns (updates, seconds)."""
+def run_oracle_sample(cfg, sweeps=0, seconds=0.0, measure_every=32, chunk=25, max_seconds=30.0, sample_index=0):
+    """The sequential FP64 oracle on one sample of the workload, one host thread:
+    `sweeps` sweeps, or (sweeps = 0) chunks of `chunk` sweeps until at least
+    `seconds` (at most `max_seconds`) have passed.  Graph construction is not
+    timed.  Returns (site-updates, seconds, sweeps run)."""
     import oracle
     from paper_1211_3991_gb300 import workloads as wl
     L, rho, _ = cfg.graphs[sample_index]
@@ -153,11 +156,17 @@ def run_oracle_sample(cfg, sweeps, sample_index=0):
     sim = oracle.Sim(L * L, ei, ej, color, cfg.betas(), cfg.deltas(), wl.SPIN_SEED, sample=wl.graph_stream_id(cfg, sample_index),
                      xy=oracle.lattice_xy(L), L=L)
     sim.init()
-    t0 = time.perf_counter()
-    sim.sweeps(sweeps, OPS_ALL, 1)
-    dt = time.perf_counter() - t0
+    done, dt = 0, 0.0
+    while True:
+        n = sweeps - done if sweeps > 0 else chunk
+        t0 = time.perf_counter()
+        sim.sweeps(n, OPS_ALL, measure_every)
+        dt += time.perf_counter() - t0
+        done += n
+        if sweeps > 0 or dt >= seconds or dt >= max_seconds:
+            break
     sim.close()
-    return L * L * cfg.n_temps * 2 * sweeps, dt
+    return L * L * cfg.n_temps * 2 * done, dt, done
 
 
 def reference_arm(args, cfg):
@@ -168,10 +177,10 @@ def reference_arm(args, cfg):
     oracle.build()
     per_step = args.ref_sweeps
     for _ in range(args.warmup):
-        run_oracle_sample(cfg, per_step)
+        run_oracle_sample(cfg, per_step, measure_every=args.measure_every)
     ups, secs = 0, 0.0
     for _ in range(args.steps):
-        u, dt = run_oracle_sample(cfg, per_step)
+        u, dt, _ = run_oracle_sample(cfg, per_step, measure_every=args.measure_every)
         ups += u
         secs += dt
     value = ups / secs
@@ -199,8 +208,8 @@ def main():
     ap.add_argument("--group", type=int, default=0)
     ap.add_argument("--resident", type=int, default=0, choices=[-1, 0, 1],
                     help="1 = spins in shared memory for a launch, -1 = global-memory shape, 0 = library/autotuner")
-    ap.add_argument("--ref-sweeps", type=int, default=4)
-    ap.add_argument("--cpu-sweeps", type=int, default=20)
+    ap.add_argument("--ref-sweeps", type=int, default=50, help="oracle sweeps per step of --impl reference (about 1 s)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample: oracle time to run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
@@ -327,9 +336,9 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        ups, secs = run_oracle_sample(cfg, args.cpu_sweeps)
+        ups, secs, n_sw = run_oracle_sample(cfg, seconds=args.cpu_seconds, measure_every=args.measure_every)
         cpu = {"value": ups / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_sweeps} sweeps of sample 0 of {cfg.name} ({ups} site-updates, {secs:.1f} s)"}
+               "sample": f"{n_sw} sweeps of sample 0 of {cfg.name} ({ups} site-updates, {secs:.1f} s, one thread)"}
 
     if rank == 0:
         line = {
