@@ -52,6 +52,9 @@ def _load():
         lib.orc_disp_sample.argtypes = [C.c_int, C.c_double, C.c_uint64, C.c_uint32, C.c_int64, i32p]
         lib.orc_levy_graph.argtypes = [C.c_int, C.c_int, C.c_double, C.c_uint64, C.c_uint32, C.c_int,
                                        i32p, i32p, i32p, u64p]
+        lib.orc_fbc_table.argtypes = [C.c_int, C.c_double, i32p, i32p, u64p]
+        lib.orc_levy_bonds.argtypes = [C.c_int, C.c_double, C.c_int64, C.c_int, C.c_uint64, C.c_uint32, i32p, i32p,
+                                       u64p]
         lib.orc_pick_partner_counts.argtypes = [C.c_int, C.c_int, C.c_double, C.c_uint64, i32p, i32p, i32p,
                                                 C.c_int, C.c_int, C.c_int64, i64p]
         lib.orc_slo_color.argtypes = [C.c_int, C.c_int64, i32p, i32p, i32p]
@@ -153,6 +156,40 @@ def levy_graph(L: int, z: int, rho: float, seed: int, sample: int = 0, max_resta
     if rc == -3:
         raise RuntimeError("graph construction hit a dead end on every restart")
     return ei, ej, int(rs[0]), int(dr[0])
+
+
+def levy_bonds(L: int, rho: float, seed: int, sample: int = 0, n_bonds=None, fbc: bool = False):
+    """The paper's ensemble (Sec. II): exactly ``n_bonds`` bonds (default 2N,
+    mean degree 4), each pair drawn with probability proportional to r^-rho,
+    periodic (minimum image) or free boundaries.  Returns (ei, ej, attempts),
+    bonds in the order they were accepted.
+
+    Pinned by exact bond count / no self-loop / no repeated pair checks, the
+    law of the first bond over many streams (PBC and FBC, brute-force pair
+    counts), the exact hypergeometric degree law and pair-distance law of the
+    uniform graph at rho = 0, and the brute-force FBC displacement table."""
+    lib = _load()
+    n = L * L
+    m = 2 * n if n_bonds is None else int(n_bonds)
+    ei = np.zeros(max(m, 1), np.int32); ej = np.zeros(max(m, 1), np.int32)
+    at = np.zeros(1, np.uint64)
+    rc = lib.orc_levy_bonds(L, rho, m, 1 if fbc else 0, seed, sample, _ptr(ei, C.c_int32), _ptr(ej, C.c_int32),
+                            _ptr(at, C.c_uint64))
+    if rc == -1:
+        raise ValueError("bad graph arguments")
+    if rc == -3:
+        raise RuntimeError("too many rejected bond draws")
+    return ei[:m], ej[:m], int(at[0])
+
+
+def fbc_table(L: int, rho: float):
+    """Free-boundary link-law table: (dx, dy, B) in table order."""
+    lib = _load()
+    n = (2 * L - 1) ** 2 - 1
+    dx = np.zeros(n, np.int32); dy = np.zeros(n, np.int32); B = np.zeros(n, np.uint64)
+    if lib.orc_fbc_table(L, rho, _ptr(dx, C.c_int32), _ptr(dy, C.c_int32), _ptr(B, C.c_uint64)):
+        raise ValueError("bad lattice size")
+    return dx, dy, B
 
 
 def pick_partner_counts(L, z, rho, seed, deg, adj, unsat, i, n_trials):

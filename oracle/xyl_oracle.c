@@ -17,6 +17,9 @@
  *   orc_levy_graph()    Fixed-degree (every site exactly z links) sequential
  *                       pairing of unsaturated sites, each new link drawn with
  *                       the law above among the eligible partners.
+ *   orc_levy_bonds()    The paper's own ensemble: exactly M bonds (M = 2N, mean
+ *                       degree 4), each pair drawn with the same law, periodic
+ *                       or free boundaries (Sec. II).
  *   orc_slo_color()     Smallest-last-ordering colouring (App. B, "Graph
  *                       coloring").
  *   orc_csr()           Colour-sorted CSR (App. B, "Memory management": sites of
@@ -451,6 +454,136 @@ int orc_levy_graph(int L, int z, double rho, uint64_t seed, uint32_t sample, int
     }
     if (draws_out) *draws_out = total_draws;
     free(p.deg); free(p.adj); free(p.unsat); free(p.where);
+    disp_table_free(&t);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The paper's own ensemble (Sec. II, Eq. (Levyi)): exactly M bonds in all    */
+/* (M = 2N gives the mean degree 4 the paper uses), each a pair of sites      */
+/* drawn with probability proportional to |r_i - r_j|^-rho among all pairs of */
+/* the lattice; degrees are free (Poisson with mean 4 at rho = 0, the         */
+/* Erdos-Renyi limit).  Boundary conditions:                                  */
+/*   PBC  minimum-image displacements, the table above (r_max = (L/2) sqrt2); */
+/*   FBC  plain displacements |dx|, |dy| <= L-1 inside the L x L square       */
+/*        (r_max = L sqrt 2), table in raster order (dy outer, dx inner)      */
+/*        with the same integer boundaries.                                   */
+/* Reading of the draw (the paper gives no procedure):                        */
+/*   * attempt a uses Philox block a with counter                             */
+/*     (a_lo, a_hi, GRAPH<<24 | BONDS_SUB | fbc, sample):                     */
+/*     i = mulhi(w1:w0, N), displacement entry k = the one whose interval     */
+/*     holds w3:w2, j = i + d_k (wrapped for PBC);                            */
+/*   * an FBC partner outside the square, or a pair already bonded, is        */
+/*     rejected and the next attempt drawn;                                   */
+/*   * the first M accepted pairs are the bonds (ei = i, ej = j).             */
+/* Each ordered pair (i, j) has one table entry and one choice of i, so an    */
+/* accepted pair is drawn with probability proportional to r_ij^-rho among    */
+/* the pairs not yet bonded; at rho = 0 the graph is uniform among graphs     */
+/* with M edges.                                                              */
+/* ------------------------------------------------------------------------- */
+#define BONDS_SUB 0x400000u
+
+static int fbc_table_build(disp_table *t, int L, double rho)
+{
+    memset(t, 0, sizeof(*t));
+    t->L = L;
+    t->n = (2 * L - 1) * (2 * L - 1) - 1;
+    t->n_near = 0;
+    t->dx = (int *)malloc(sizeof(int) * (size_t)t->n);
+    t->dy = (int *)malloc(sizeof(int) * (size_t)t->n);
+    t->B = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)t->n);
+    double *S = (double *)malloc(sizeof(double) * (size_t)(t->n + 1));
+    if (!t->dx || !t->dy || !t->B || !S) { free(S); disp_table_free(t); return -1; }
+    int k = 0;
+    for (int dy = -(L - 1); dy <= L - 1; ++dy)
+        for (int dx = -(L - 1); dx <= L - 1; ++dx) {
+            if (dx == 0 && dy == 0) continue;
+            t->dx[k] = dx; t->dy[k] = dy; ++k;
+        }
+    S[0] = 0.0;
+    for (int m = 0; m < t->n; ++m) {
+        double r2 = (double)(t->dx[m] * t->dx[m] + t->dy[m] * t->dy[m]);
+        S[m + 1] = S[m] + pow(r2, -0.5 * rho);
+    }
+    const double two64 = 18446744073709551616.0;
+    t->B[0] = 0;
+    for (int m = 1; m < t->n; ++m) {
+        double q = (S[m] / S[t->n]) * two64;
+        t->B[m] = (q >= two64) ? UINT64_MAX : (uint64_t)q;
+    }
+    free(S);
+    return 0;
+}
+
+/* Exported for the FBC link-law tests: the table in table order. */
+int orc_fbc_table(int L, double rho, int32_t *dx, int32_t *dy, uint64_t *B)
+{
+    if (L < 2) return -1;
+    disp_table t;
+    if (fbc_table_build(&t, L, rho)) return -1;
+    for (int k = 0; k < t.n; ++k) { dx[k] = t.dx[k]; dy[k] = t.dy[k]; B[k] = t.B[k]; }
+    disp_table_free(&t);
+    return 0;
+}
+
+/*
+ * Build one graph of the M-bond ensemble.  Writes the M bonds in the order
+ * they were accepted.  Returns 0; -1 on bad arguments (PBC needs even L >= 4,
+ * FBC L >= 2, 0 <= M <= N(N-1)/2); -3 when 64 M + 10^6 attempts did not give M
+ * distinct bonds.  attempts_out (may be NULL) receives the attempts used.
+ */
+int orc_levy_bonds(int L, double rho, int64_t n_bonds, int fbc, uint64_t seed, uint32_t sample,
+                   int32_t *ei, int32_t *ej, uint64_t *attempts_out)
+{
+    if (fbc ? L < 2 : (L < 4 || (L & 1))) return -1;
+    const int64_t n = (int64_t)L * L;
+    if (n_bonds < 0 || n_bonds > n * (n - 1) / 2) return -1;
+    disp_table t;
+    if (fbc ? fbc_table_build(&t, L, rho) : disp_table_build(&t, L, rho)) return -1;
+    int *deg = (int *)calloc((size_t)n, sizeof(int));
+    int *cap = (int *)calloc((size_t)n, sizeof(int));
+    int **nbr = (int **)calloc((size_t)n, sizeof(int *));
+    int rc = (deg && cap && nbr) ? -3 : -1;
+    const uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    const uint64_t max_attempts = 64u * (uint64_t)n_bonds + 1000000u;
+    int64_t e = 0;
+    uint64_t a = 0;
+    while (rc == -3 && a < max_attempts) {
+        if (e == n_bonds) { rc = 0; break; }
+        uint32_t x[4];
+        draw_block((uint32_t)a, (uint32_t)(a >> 32), PURPOSE_GRAPH, BONDS_SUB | (fbc ? 1u : 0u), sample, key, x);
+        ++a;
+        int i = (int)mulhi64(((uint64_t)x[1] << 32) | x[0], (uint64_t)n);
+        int k = disp_locate(&t, ((uint64_t)x[3] << 32) | x[2], 0);
+        int j;
+        if (fbc) {
+            int xj = i % L + t.dx[k], yj = i / L + t.dy[k];
+            if (xj < 0 || xj >= L || yj < 0 || yj >= L) continue;
+            j = xj + L * yj;
+        } else {
+            j = site_shift(L, i, t.dx[k], t.dy[k]);
+        }
+        int bonded = 0;
+        for (int b = 0; b < deg[i] && !bonded; ++b) bonded = nbr[i][b] == j;
+        if (bonded) continue;
+        int ends[2] = { i, j };
+        for (int q = 0; q < 2 && rc == -3; ++q) {
+            int v = ends[q];
+            if (deg[v] == cap[v]) {
+                int *grown = (int *)realloc(nbr[v], sizeof(int) * (size_t)(cap[v] ? 2 * cap[v] : 8));
+                if (!grown) { rc = -1; break; }
+                cap[v] = cap[v] ? 2 * cap[v] : 8;
+                nbr[v] = grown;
+            }
+            nbr[v][deg[v]++] = ends[1 - q];
+        }
+        if (rc != -3) break;
+        ei[e] = i; ej[e] = j; ++e;
+    }
+    if (rc == -3 && e == n_bonds) rc = 0;
+    if (attempts_out) *attempts_out = a;
+    if (nbr) for (int64_t v = 0; v < n; ++v) free(nbr[v]);
+    free(nbr); free(cap); free(deg);
     disp_table_free(&t);
     return rc;
 }
