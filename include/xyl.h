@@ -4,9 +4,12 @@
  * model in complex topologies").
  *
  * Model, Eq. (HXY): H = -sum_{i<j} J_ij S_i . S_j with S_i a unit 2-vector and
- * J_ij in {0,1} the adjacency of the graph.  Graph, Eq. (Levyi): sites of a
- * periodic L x L square lattice; a link lands at distance r with probability
- * proportional to r^-rho; here every site carries exactly z links.
+ * J_ij in {0,1} the adjacency of the graph.  Graph, Eq. (Levyi): sites of an
+ * L x L square lattice; a link lands at distance r with probability
+ * proportional to r^-rho.  Two ensembles: every site carrying exactly z links
+ * on the periodic lattice (xyl_build_graph_csr), or a fixed total of links with
+ * free degrees on the periodic or free lattice, the paper's own (Sec. II,
+ * xyl_build_levy_bonds).
  *
  * Conventions for every entry point:
  *   * The return value is a status: XYL_OK (0) or a negative XYL_E* code; the
@@ -100,6 +103,36 @@ int xyl_version(void);
  * Errors: XYL_EINVAL for bad sizes, XYL_EGRAPH as above.
  */
 int xyl_build_graph_csr(int32_t L, int32_t z, double rho, uint64_t seed, uint32_t sample_id, xyl_graph **out);
+
+/* ---- boundary conditions of xyl_build_levy_bonds ---------------------- */
+#define XYL_PBC 0 /* periodic: minimum-image distances, r_max = (L/2) sqrt(2) */
+#define XYL_FBC 1 /* free: distances inside the L x L square, r_max = L sqrt(2) */
+
+/*
+ * xyl_build_levy_bonds -- one graph of the paper's own ensemble (Sec. II,
+ * Eq. (Levyi)): exactly n_bonds links (2N gives the mean degree 4 the paper
+ * uses), each a pair of sites drawn with probability proportional to
+ * |r_i - r_j|^-rho among all pairs of the lattice; degrees vary (Poisson with
+ * mean 4 at rho = 0, the Erdos-Renyi limit).  Coloured and packed like
+ * xyl_build_graph_csr.
+ *   L         lattice side; XYL_PBC needs an even L in [4, 4096], XYL_FBC any
+ *             L in [2, 4096]; N = L*L sites.
+ *   rho       decay exponent of the link law (finite).
+ *   n_bonds   number of links, 0 <= n_bonds <= N(N-1)/2.
+ *   boundary  XYL_PBC or XYL_FBC.
+ *   seed      64-bit key of the graph random stream; sample_id selects an
+ *             independent stream (disorder realisation).
+ *   out       receives a new handle (free with xyl_graph_free).
+ * Draws: attempt a takes Philox block a of the graph stream (its own stream
+ * id, apart from xyl_build_graph_csr's); the first site i from the first 64
+ * bits (uniform over the N sites), the displacement from the second 64 bits
+ * (the link-law table of the boundary condition); a partner outside the
+ * square (XYL_FBC) or an existing link rejects the attempt.
+ * Errors: XYL_EINVAL for bad arguments, XYL_EGRAPH when 64 n_bonds + 10^6
+ * attempts do not give n_bonds distinct links.
+ */
+int xyl_build_levy_bonds(int32_t L, double rho, int64_t n_bonds, int32_t boundary, uint64_t seed, uint32_t sample_id,
+                         xyl_graph **out);
 
 /*
  * xyl_graph_from_edges -- a graph from an explicit simple edge list (for the

@@ -1,5 +1,7 @@
-// Host-side graph construction of libxyl: dilute Levy graphs with a fixed
-// degree on the periodic L x L lattice (Eq. (Levyi)), smallest-last-ordering
+// Host-side graph construction of libxyl: dilute Levy graphs (Eq. (Levyi)) with
+// a fixed degree on the periodic L x L lattice, or with a fixed number of bonds
+// on the periodic or free lattice (the paper's own ensemble, Sec. II),
+// smallest-last-ordering
 // colouring and the colour-sorted CSR (App. B, "Graph coloring" and "Memory
 // management").  Compiled without FP contraction so that every decision taken
 // from the FP64 link-law table is reproducible bit for bit.
@@ -224,6 +226,79 @@ int draw_partner(const LinkLaw &law, const Pairing &pr, int i, DrawStream &ds)
 }
 
 // ---------------------------------------------------------------------------
+// Free boundaries: displacements |dx|, |dy| <= L-1 inside the L x L square
+// (r_max = L sqrt 2, Sec. II), raster order (dy outer, dx inner), weight
+// r^-rho per displacement, boundaries from the FP64 running sum as above.
+// ---------------------------------------------------------------------------
+LinkLaw make_free_law(int L, double rho)
+{
+    LinkLaw law;
+    law.L = L;
+    law.entries = (2 * L - 1) * (2 * L - 1) - 1;
+    law.near = 0;
+    law.ddx.reserve(law.entries);
+    law.ddy.reserve(law.entries);
+    for (int dy = 1 - L; dy <= L - 1; ++dy)
+        for (int dx = 1 - L; dx <= L - 1; ++dx) {
+            if (dx == 0 && dy == 0) continue;
+            law.ddx.push_back(dx);
+            law.ddy.push_back(dy);
+        }
+    std::vector<double> run(law.entries + 1, 0.0);
+    for (int k = 0; k < law.entries; ++k) {
+        const double r2 = (double)(law.ddx[k] * law.ddx[k] + law.ddy[k] * law.ddy[k]);
+        run[k + 1] = run[k] + std::pow(r2, -0.5 * rho);
+    }
+    const double two64 = 18446744073709551616.0;
+    law.lower.assign(law.entries, 0);
+    for (int k = 1; k < law.entries; ++k) {
+        const double q = (run[k] / run[law.entries]) * two64;
+        law.lower[k] = (q >= two64) ? ~0ull : (uint64_t)q;
+    }
+    return law;
+}
+
+// Stream id of the M-bond ensemble in counter word 2 (below the purpose byte),
+// apart from the pairing restarts of the fixed-degree ensemble.
+constexpr uint32_t kBondStream = 0x400000u;
+
+// M distinct bonds, each attempt one Philox block: the first site from
+// w1:w0, the displacement from w3:w2; a free-boundary partner outside the
+// square or an existing bond rejects the attempt.
+bool draw_bonds(const LinkLaw &law, bool free_bc, int64_t n_bonds, uint64_t seed, uint32_t sample, xyl_graph &g,
+                uint64_t *attempts)
+{
+    const int L = law.L;
+    const uint64_t n = (uint64_t)L * L;
+    std::vector<std::vector<int32_t>> nbr(n);
+    const uint64_t limit = 64u * (uint64_t)n_bonds + 1000000u;
+    int64_t e = 0;
+    uint64_t a = 0;
+    for (; e < n_bonds && a < limit; ++a) {
+        const Words4 w = philox_draw((uint32_t)a, (uint32_t)(a >> 32), kPurposeGraph, kBondStream | (free_bc ? 1u : 0u),
+                                     sample, seed);
+        const int i = (int)scale_u64(((uint64_t)w.w1 << 32) | w.w0, n);
+        const int k = law.find(((uint64_t)w.w3 << 32) | w.w2, 0);
+        int j;
+        if (free_bc) {
+            const int x = i % L + law.ddx[k], y = i / L + law.ddy[k];
+            if (x < 0 || x >= L || y < 0 || y >= L) continue;
+            j = x + L * y;
+        } else {
+            j = law.shift(i, k);
+        }
+        if (std::find(nbr[i].begin(), nbr[i].end(), j) != nbr[i].end()) continue;
+        nbr[i].push_back(j);
+        nbr[j].push_back(i);
+        g.ei[e] = i;
+        g.ej[e] = j;
+        ++e;
+    }
+    *attempts = a;
+    return e == n_bonds;
+}
+
+// ---------------------------------------------------------------------------
 // Smallest-last ordering: peel a vertex of least remaining degree (ties: least
 // id) until none is left, then colour in the reverse peeling order with the
 // least colour absent among already-coloured neighbours.
@@ -357,6 +432,43 @@ int xyl_build_graph_csr(int32_t L, int32_t z, double rho, uint64_t seed, uint32_
         return XYL_OK;
     } catch (const std::exception &ex) {
         return fail(XYL_EINVAL, "xyl_build_graph_csr: %s", ex.what());
+    }
+}
+
+int xyl_build_levy_bonds(int32_t L, double rho, int64_t n_bonds, int32_t boundary, uint64_t seed, uint32_t sample_id,
+                         xyl_graph **out)
+{
+    clear_error();
+    if (!out) return fail(XYL_EINVAL, "xyl_build_levy_bonds: out is NULL");
+    *out = nullptr;
+    if (boundary != XYL_PBC && boundary != XYL_FBC)
+        return fail(XYL_EINVAL, "xyl_build_levy_bonds: boundary=%d is neither XYL_PBC nor XYL_FBC", boundary);
+    const bool free_bc = boundary == XYL_FBC;
+    if (free_bc ? (L < 2 || L > 4096) : (L < 4 || (L & 1) || L > 4096))
+        return fail(XYL_EINVAL, "xyl_build_levy_bonds: L=%d must be %s", L,
+                    free_bc ? "in [2,4096]" : "even in [4,4096]");
+    const int64_t n = (int64_t)L * L;
+    if (n_bonds < 0 || n_bonds > n * (n - 1) / 2)
+        return fail(XYL_EINVAL, "xyl_build_levy_bonds: n_bonds=%lld outside [0, N(N-1)/2]", (long long)n_bonds);
+    if (!std::isfinite(rho)) return fail(XYL_EINVAL, "xyl_build_levy_bonds: rho must be finite");
+    try {
+        const LinkLaw law = free_bc ? make_free_law(L, rho) : make_law(L, rho);
+        auto *g = new xyl_graph();
+        g->n = (int32_t)n; g->L = L; g->z = 0; g->n_edges = n_bonds;
+        g->ei.resize(n_bonds); g->ej.resize(n_bonds);
+        uint64_t attempts = 0;
+        if (!draw_bonds(law, free_bc, n_bonds, seed, sample_id, *g, &attempts)) {
+            delete g;
+            return fail(XYL_EGRAPH, "xyl_build_levy_bonds: %llu attempts gave fewer than %lld distinct bonds",
+                        (unsigned long long)attempts, (long long)n_bonds);
+        }
+        g->xy.resize(2 * n);
+        for (int64_t v = 0; v < n; ++v) { g->xy[2 * v] = (int32_t)(v % L); g->xy[2 * v + 1] = (int32_t)(v / L); }
+        finish_graph(*g);
+        *out = g;
+        return XYL_OK;
+    } catch (const std::exception &ex) {
+        return fail(XYL_EINVAL, "xyl_build_levy_bonds: %s", ex.what());
     }
 }
 

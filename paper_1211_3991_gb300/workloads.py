@@ -10,6 +10,12 @@ configurations keep its structure at the sizes the benchmark names:
   C3  256 graphs per rho in {2.5, 3.5, 4.5}, L=64, 24 temperatures geometric in [1.5, 3.5]
   C4  8 graphs per L in {32, 48, 64, 96, 128, 192}, rho=3.0, 20 temperatures in [1.5, 3.5], FP64 recompute every 100 sweeps
   C5  64 graphs per rho in {2.5, 4.5}, L=512, 32 temperatures in [1.5, 3.5]
+
+The paper's own graph ensemble (Sec. II: 2N bonds, free degrees, periodic or
+free boundaries) at small sizes for parity checks:
+
+  E1  one graph, L=16, rho=0 (Erdos-Renyi limit), periodic, 4 temperatures geometric in [1.6, 2.4]
+  E2  one graph, L=16, rho=7/3, free boundaries, 4 temperatures geometric in [1.6, 2.4]
 """
 from __future__ import annotations
 
@@ -37,6 +43,8 @@ class Config:
     recompute_every: int = 0
     description: str = ""
     delta: list = field(default_factory=list)
+    ensemble: str = "fixed"   # "fixed": every site Z links; "bonds": 2N bonds in all (Sec. II)
+    boundary: str = "pbc"     # "bonds" ensemble: "pbc" or "fbc"
 
     @property
     def n_samples(self):
@@ -78,6 +86,12 @@ def config(name: str) -> Config:
         g = [(L, 3.0, s) for L in (32, 48, 64, 96, 128, 192) for s in range(8)]
         return Config("C4", g, geometric_temperatures(1.5, 3.5, 20), recompute_every=100,
                       description="8 graphs x L in {32,48,64,96,128,192}, rho=3.0, 20 T, FP64 recompute every 100")
+    if name == "E1":
+        return Config("E1", [(16, 0.0, 0)], geometric_temperatures(1.6, 2.4, 4), ensemble="bonds",
+                      description="L=16 2N bonds rho=0 periodic, 4 T geometric in [1.6,2.4]")
+    if name == "E2":
+        return Config("E2", [(16, 7.0 / 3.0, 0)], geometric_temperatures(1.6, 2.4, 4), ensemble="bonds",
+                      boundary="fbc", description="L=16 2N bonds rho=7/3 free boundaries, 4 T geometric in [1.6,2.4]")
     if name == "C5":
         g = [(512, rho, s) for rho in (2.5, 4.5) for s in range(64)]
         return Config("C5", g, geometric_temperatures(1.5, 3.5, 32),
@@ -112,6 +126,8 @@ def build_graphs(cfg: Config, threads: int = 0):
 
     def one(k):
         L, rho, s = cfg.graphs[k]
+        if cfg.ensemble == "bonds":
+            return xyl.build_levy_bonds(L, rho, GRAPH_SEED, graph_stream_id(cfg, k), fbc=cfg.boundary == "fbc")
         return xyl.build_graph_csr(L, Z, rho, GRAPH_SEED, graph_stream_id(cfg, k))
 
     with cf.ThreadPoolExecutor(max_workers=threads) as ex:

@@ -28,7 +28,7 @@ EXPORTED = (
     "xyl_read_observables", "xyl_reset_observables", "xyl_read_energies", "xyl_read_labels", "xyl_read_spins",
     "xyl_write_spins", "xyl_read_status", "xyl_state_bytes", "xyl_export_state", "xyl_import_state",
     "xyl_last_launch_count", "xyl_plan_free", "xyl_sweep_units", "xyl_unit_count", "xyl_autotune",
-    "xyl_get_tuning", "xyl_sweep_noalloc",
+    "xyl_get_tuning", "xyl_sweep_noalloc", "xyl_build_levy_bonds",
 )
 
 
@@ -99,6 +99,7 @@ def load():
             "xyl_autotune": ([P, i32, u32, i32, C.POINTER(Tuning), P], C.c_int),
             "xyl_get_tuning": ([P, C.POINTER(Tuning)], C.c_int),
             "xyl_sweep_noalloc": ([P, i32, u32, i32, P], C.c_int),
+            "xyl_build_levy_bonds": ([i32, f64, i64, i32, u64, u32, C.POINTER(P)], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -158,6 +159,14 @@ class Graph:
 def build_graph_csr(L: int, z: int, rho: float, seed: int, sample_id: int = 0) -> Graph:
     h = C.c_void_p()
     _check(load().xyl_build_graph_csr(L, z, rho, seed, sample_id, C.byref(h)))
+    return Graph(h.value)
+
+
+def build_levy_bonds(L: int, rho: float, seed: int, sample_id: int = 0, n_bonds=None, fbc: bool = False) -> Graph:
+    """The paper's ensemble: ``n_bonds`` links (default 2N), periodic or free boundaries."""
+    h = C.c_void_p()
+    m = 2 * L * L if n_bonds is None else int(n_bonds)
+    _check(load().xyl_build_levy_bonds(L, rho, m, 1 if fbc else 0, seed, sample_id, C.byref(h)))
     return Graph(h.value)
 
 

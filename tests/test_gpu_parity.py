@@ -38,9 +38,18 @@ def env():
     return xyl, workloads
 
 
+def _oracle_graph(orc, wl, cfg, k):
+    L, rho, _ = cfg.graphs[k]
+    if cfg.ensemble == "bonds":
+        ei, ej, _ = orc.levy_bonds(L, rho, wl.GRAPH_SEED, wl.graph_stream_id(cfg, k), fbc=cfg.boundary == "fbc")
+        return ei, ej
+    ei, ej, _, _ = orc.levy_graph(L, 6, rho, wl.GRAPH_SEED, wl.graph_stream_id(cfg, k))
+    return ei, ej
+
+
 def _oracle_for(orc, wl, cfg, k, u24):
     L, rho, _ = cfg.graphs[k]
-    ei, ej, _, _ = orc.levy_graph(L, 6, rho, wl.GRAPH_SEED, wl.graph_stream_id(cfg, k))
+    ei, ej = _oracle_graph(orc, wl, cfg, k)
     color, _ = orc.slo_color(L * L, ei, ej)
     sim = orc.Sim(L * L, ei, ej, color, cfg.betas(), cfg.deltas(), wl.SPIN_SEED, sample=wl.graph_stream_id(cfg, k),
                   xy=orc.lattice_xy(L), L=L, u24=u24)
@@ -79,7 +88,7 @@ def _variant(xyl, name):
 
 
 # --------------------------------------------------------------- FP64 engine
-@pytest.mark.parametrize("name", ["C1", "C2"])
+@pytest.mark.parametrize("name", ["C1", "C2", "E1", "E2"])
 def test_fp64_trajectory_matches_oracle(env, orc, name):
     xyl, wl = env
     cfg = wl.config(name)
@@ -164,7 +173,75 @@ def test_fp32_energy_matches_oracle(env, orc, name, engine_name):
     assert plan.status() == (0, 10)
 
 
+@pytest.mark.parametrize("engine_name", ["FP32_GLOBAL", "FP32_PLAIN"])
+@pytest.mark.parametrize("name", ["E1", "E2"])
+def test_fp32_energy_matches_oracle_bond_ensemble(env, orc, name, engine_name):
+    """The paper's 2N-bond graphs (Sec. II): free degrees up to 11 here, so
+    the batched engine runs its any-degree global-memory kernel; the shared-
+    memory shape, limited to degree 8, refuses them."""
+    xyl, wl = env
+    cfg = wl.config(name)
+    graphs = wl.build_graphs(cfg)
+    assert graphs[0].max_deg > 8
+    with pytest.raises(xyl.XylError) as e:
+        wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, resident=1)
+    assert e.value.code == xyl.EINVAL
+    eng, opts = _variant(xyl, engine_name)
+    plan, _ = wl.make_plan(cfg, eng, graphs=graphs, **opts)
+    plan.bind()
+    plan.init_spins()
+    sims = {0: _oracle_for(orc, wl, cfg, 0, u24=True)}
+    compared, explained, worst = _fp32_per_sweep(plan, sims, [0], 10, ALL, lambda s: cfg.graphs[s][0] ** 2)
+    print(f"{name} {engine_name}: {compared} replica-sweeps, {explained} near-tie misses, worst |dE|/N {worst:.2e}")
+    assert plan.status() == (0, 10)
+
+
 # --------------------------------------------------------------- long runs
+def _tuned_deltas(orc, wl, cfg, ops):
+    """Metropolis half-widths tuned on the oracle to about 50% acceptance, then frozen."""
+    sim = _oracle_for(orc, wl, cfg, 0, u24=False)
+    delta = np.array(cfg.deltas())
+    for _ in range(6):
+        sim.sweeps(200, ops)
+        st = sim.accumulators()
+        rate = st["met_acc"] / st["met_try"]
+        delta = np.clip(delta * rate / 0.5, 0.05, np.pi)
+        sim.set_delta(delta)
+        sim.reset_acc()
+    return list(delta)
+
+
+def test_long_run_statistics_bond_ensemble(env, orc):
+    """E1 (L=16, 2N bonds, rho=0, four temperatures around the critical point
+    with parallel tempering): per slot <e>, chi, U4 and <|m|> of the FP32
+    batched engine agree with the FP64 oracle within 3 sigma (binned jackknife)."""
+    xyl, wl = env
+    cfg = wl.config("E1")
+    cfg.delta = _tuned_deltas(orc, wl, cfg, ALL)
+    sim = _oracle_for(orc, wl, cfg, 0, u24=False)
+    plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED)
+    plan.bind()
+    plan.init_spins()
+    for s in (sim, plan):
+        s.sweeps(500, ALL)
+        s.reset_acc()
+    ob = bin_means(run_bins(sim, 100, 100, ALL))
+    gb = bin_means(run_bins(plan, 100, 100, ALL))
+    N = 256
+    fns = {
+        "e": lambda m: m[ACC["e"]],
+        "chi": lambda m: N * (m[ACC["m2"]] - m[ACC["mx"]] ** 2 - m[ACC["my"]] ** 2),
+        "U4": lambda m: m[ACC["m4"]] / m[ACC["m2"]] ** 2 - 1,
+        "absm": lambda m: m[ACC["absm"]],
+    }
+    for k in range(cfg.n_temps):
+        for key, fn in fns.items():
+            a, da = jackknife(ob[:, k, :], fn)
+            b, db = jackknife(gb[:, k, :], fn)
+            assert abs(a - b) < 3 * np.hypot(da, db), (k, key, a, da, b, db)
+    assert plan.status()[0] == 0
+
+
 @pytest.mark.parametrize("engine_name", ["FP32_RESIDENT", "FP32_GLOBAL", "FP64_PLAIN"])
 def test_long_run_statistics_c1(env, orc, engine_name):
     xyl, wl = env

@@ -61,6 +61,36 @@ def test_graph_and_csr_bit_exact_vs_oracle(xyl, orc, L, rho, seed, sid):
     assert g.max_deg == 6 and g.n_edges == L * L * 3
 
 
+BOND_CASES = [(L, rho, fbc, sid) for fbc in (False, True) for (L, rho, sid) in
+              [(16, 0.0, 0), (16, 3.5, 1), (64, 0.0, 2), (64, 7.0 / 3.0, 3), (64, 14.0 / 3.0, 4), (128, 10.0 / 3.0, 5),
+               (256, 0.5, 6)]] + [(7, 2.0, True, 7), (4, 1.0, False, 8)]
+
+
+@pytest.mark.parametrize("L,rho,fbc,sid", BOND_CASES)
+def test_levy_bonds_bit_exact_vs_oracle(xyl, orc, L, rho, fbc, sid):
+    """The paper's M-bond ensemble (Sec. II): the library's builder and the
+    oracle's give the same bonds in the same order and the same CSR."""
+    g = xyl.build_levy_bonds(L, rho, 3, sid, fbc=fbc)
+    oi, oj, _ = orc.levy_bonds(L, rho, 3, sid, fbc=fbc)
+    ei, ej = g.edges()
+    assert np.array_equal(ei, oi) and np.array_equal(ej, oj)
+    col, q = orc.slo_color(L * L, oi, oj)
+    for mine, theirs in zip(g.csr(), orc.csr(L * L, oi, oj, col, q)):
+        assert mine.dtype == theirs.dtype and np.array_equal(mine, theirs)
+
+
+def test_levy_bonds_rejects_bad_input(xyl):
+    for args in [(5, 1.0, 0, 0, False), (4, float("nan"), 0, 0, False), (1, 1.0, 0, 0, True)]:
+        with pytest.raises(xyl.XylError) as e:
+            xyl.build_levy_bonds(args[0], args[1], args[2], args[3], fbc=args[4])
+        assert e.value.code == xyl.EINVAL
+    with pytest.raises(xyl.XylError) as e:
+        xyl.build_levy_bonds(4, 1.0, 0, n_bonds=121)
+    assert e.value.code == xyl.EINVAL
+    g = xyl.build_levy_bonds(4, 1.0, 0, n_bonds=0)
+    assert g.n_edges == 0 and g.n_colors == 1
+
+
 def test_graph_from_edges_matches_oracle_colouring(xyl, orc):
     rng = np.random.default_rng(4)
     n = 40
