@@ -55,6 +55,7 @@ def _load():
         lib.orc_fbc_table.argtypes = [C.c_int, C.c_double, i32p, i32p, u64p]
         lib.orc_levy_bonds.argtypes = [C.c_int, C.c_double, C.c_int64, C.c_int, C.c_uint64, C.c_uint32, i32p, i32p,
                                        u64p]
+        lib.orc_walk_returns.argtypes = [C.c_int, i32p, i32p, C.c_int64, i32p, C.c_int32, C.c_uint64, u64p]
         lib.orc_pick_partner_counts.argtypes = [C.c_int, C.c_int, C.c_double, C.c_uint64, i32p, i32p, i32p,
                                                 C.c_int, C.c_int, C.c_int64, i64p]
         lib.orc_slo_color.argtypes = [C.c_int, C.c_int64, i32p, i32p, i32p]
@@ -180,6 +181,23 @@ def levy_bonds(L: int, rho: float, seed: int, sample: int = 0, n_bonds=None, fbc
     if rc == -3:
         raise RuntimeError("too many rejected bond draws")
     return ei[:m], ej[:m], int(at[0])
+
+
+def walk_returns(row_ptr, col, start, n_steps: int, seed: int):
+    """Self-return counts of simple random walks on a CSR graph (App. A):
+    returns[tau] = walkers on their starting node after tau steps.
+
+    Pinned by exact return probabilities (powers of the transition matrix) on
+    small graphs, the closed form [C(2n, n) / 4^n]^2 and the absence of odd
+    returns on the square lattice, and the isolated-node rule."""
+    lib = _load()
+    row_ptr = np.ascontiguousarray(row_ptr, np.int32); col = np.ascontiguousarray(col, np.int32)
+    start = np.ascontiguousarray(start, np.int32)
+    out = np.zeros(n_steps + 1, np.uint64)
+    if lib.orc_walk_returns(len(row_ptr) - 1, _ptr(row_ptr, C.c_int32), _ptr(col, C.c_int32), len(start),
+                            _ptr(start, C.c_int32), n_steps, seed, _ptr(out, C.c_uint64)):
+        raise ValueError("bad walk arguments")
+    return out
 
 
 def fbc_table(L: int, rho: float):

@@ -20,6 +20,8 @@
  *   orc_levy_bonds()    The paper's own ensemble: exactly M bonds (M = 2N, mean
  *                       degree 4), each pair drawn with the same law, periodic
  *                       or free boundaries (Sec. II).
+ *   orc_walk_returns()  Self-return counts of simple random walks, whose decay
+ *                       gives the spectral dimension (App. A).
  *   orc_slo_color()     Smallest-last-ordering colouring (App. B, "Graph
  *                       coloring").
  *   orc_csr()           Colour-sorted CSR (App. B, "Memory management": sites of
@@ -586,6 +588,42 @@ int orc_levy_bonds(int L, double rho, int64_t n_bonds, int fbc, uint64_t seed, u
     free(nbr); free(cap); free(deg);
     disp_table_free(&t);
     return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Random walks for the spectral dimension (Sec. "Spectral dimension",        */
+/* App. A): the probability P(tau) that a simple random walker is back on its */
+/* starting node after tau steps decays as tau^(-dbar/2).                     */
+/* Reading (the paper gives the observable, not the walk's details): at each  */
+/* step a walker on a node of degree k > 0 moves to one of its k neighbours   */
+/* chosen uniformly (CSR row order); on a node without neighbours it stays.   */
+/* Step tau (0-based) of walker w takes word tau mod 4 of Philox block        */
+/* floor(tau / 4) with counter (w, floor(tau / 4), WALK<<24, 0): neighbour    */
+/* index floor(word * k / 2^32).  returns[tau] counts the walkers on their    */
+/* starting node after tau steps (returns[0] = number of walkers).            */
+/* ------------------------------------------------------------------------- */
+#define PURPOSE_WALK 4
+
+int orc_walk_returns(int n, const int32_t *row_ptr, const int32_t *col, int64_t n_walkers, const int32_t *start,
+                     int32_t n_steps, uint64_t seed, uint64_t *returns)
+{
+    if (n < 1 || n_walkers < 0 || n_steps < 0 || n_walkers > 0xFFFFFFFFll) return -1;
+    for (int64_t w = 0; w < n_walkers; ++w)
+        if (start[w] < 0 || start[w] >= n) return -1;
+    const uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    for (int32_t t = 0; t <= n_steps; ++t) returns[t] = 0;
+    returns[0] = (uint64_t)n_walkers;
+    for (int64_t w = 0; w < n_walkers; ++w) {
+        int v = start[w];
+        uint32_t x[4] = { 0, 0, 0, 0 };
+        for (int32_t t = 0; t < n_steps; ++t) {
+            if (t % 4 == 0) draw_block((uint32_t)w, (uint32_t)(t / 4), PURPOSE_WALK, 0, 0, key, x);
+            const int k = row_ptr[v + 1] - row_ptr[v];
+            if (k > 0) v = col[row_ptr[v] + (int)(((uint64_t)x[t % 4] * (uint64_t)k) >> 32)];
+            if (v == start[w]) returns[t + 1]++;
+        }
+    }
+    return 0;
 }
 
 /* ------------------------------------------------------------------------- */
