@@ -351,6 +351,39 @@ size_t xyl_state_bytes(const xyl_plan *p);
 int xyl_export_state(xyl_plan *p, void *host, size_t bytes, void *stream);
 int xyl_import_state(xyl_plan *p, const void *host, size_t bytes, void *stream);
 
+/* ========================================================================= */
+/* Random walks: spectral dimension of a graph                               */
+/* ========================================================================= */
+
+/*
+ * xyl_walk_returns -- n_walkers independent simple random walks on a graph
+ * given as a CSR in device memory, counting the walkers back on their
+ * starting node after each step: P(tau) = returns[tau] / returns[0] decays as
+ * tau^(-dbar/2), dbar the spectral dimension (Sec. "Spectral dimension",
+ * Eq. (eqbard); App. A).  All pointers are device pointers owned by the
+ * caller; nothing is allocated.
+ *   row_ptr, col  CSR of n nodes and nnz neighbour entries (row_ptr[n] == nnz),
+ *                 e.g. xyl_graph_export_csr copied to the device; node ids are
+ *                 those of this CSR.
+ *   start         n_walkers starting nodes.
+ *   first_walker  id of walker 0: walker w draws from the stream of id
+ *                 first_walker + w, so a large ensemble can be run in pieces.
+ *   n_steps       steps per walker.
+ *   seed          64-bit key of the walk streams.
+ *   returns       n_steps + 1 counters, overwritten: returns[0] = walkers that
+ *                 ran, returns[tau] = walkers on their start after tau steps.
+ * Step tau of walker w takes word tau mod 4 of Philox block floor(tau/4) at
+ * counter (w, floor(tau/4), 4<<24, 0): a node of degree k > 0 sends the walker
+ * to neighbour floor(word * k / 2^32) of its CSR row; a node without
+ * neighbours keeps it.  A start outside [0, n) leaves that walker out; a row
+ * or neighbour outside the CSR stops that walker (no fault).  Asynchronous on
+ * `stream`.  Errors: XYL_EINVAL (sizes, NULL pointers, walker ids beyond
+ * 2^32), XYL_ECUDA.
+ */
+int xyl_walk_returns(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t nnz, const int32_t *start,
+                     int64_t n_walkers, uint32_t first_walker, int32_t n_steps, uint64_t seed, uint64_t *returns,
+                     void *stream);
+
 /* Number of kernel launches the last xyl_sweep call issued (graph nodes count). */
 int64_t xyl_last_launch_count(const xyl_plan *p);
 

@@ -18,7 +18,7 @@ struct Words4 {
 };
 
 // Stream purposes: top byte of counter word 2.
-enum : uint32_t { kPurposeGraph = 0u, kPurposeInit = 1u, kPurposeMet = 2u, kPurposePt = 3u };
+enum : uint32_t { kPurposeGraph = 0u, kPurposeInit = 1u, kPurposeMet = 2u, kPurposePt = 3u, kPurposeWalk = 4u };
 
 XYL_HD uint32_t mul_hi32(uint32_t a, uint32_t b)
 {

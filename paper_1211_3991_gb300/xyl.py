@@ -28,7 +28,7 @@ EXPORTED = (
     "xyl_read_observables", "xyl_reset_observables", "xyl_read_energies", "xyl_read_labels", "xyl_read_spins",
     "xyl_write_spins", "xyl_read_status", "xyl_state_bytes", "xyl_export_state", "xyl_import_state",
     "xyl_last_launch_count", "xyl_plan_free", "xyl_sweep_units", "xyl_unit_count", "xyl_autotune",
-    "xyl_get_tuning", "xyl_sweep_noalloc", "xyl_build_levy_bonds",
+    "xyl_get_tuning", "xyl_sweep_noalloc", "xyl_build_levy_bonds", "xyl_walk_returns",
 )
 
 
@@ -100,6 +100,7 @@ def load():
             "xyl_get_tuning": ([P, C.POINTER(Tuning)], C.c_int),
             "xyl_sweep_noalloc": ([P, i32, u32, i32, P], C.c_int),
             "xyl_build_levy_bonds": ([i32, f64, i64, i32, u64, u32, C.POINTER(P)], C.c_int),
+            "xyl_walk_returns": ([P, P, i32, i64, P, i64, u32, i32, u64, P, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -123,6 +124,17 @@ def _stream(stream):
         import torch
         stream = torch.cuda.current_stream()
     return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+# ----------------------------------------------------------------- random walks
+def walk_returns(row_ptr, col, start, n_steps: int, seed: int, returns, first_walker: int = 0, stream=None):
+    """Self-return counts of simple random walks (App. A) on a device CSR:
+    ``row_ptr``, ``col``, ``start`` int32 and ``returns`` (n_steps + 1) int64
+    CUDA tensors; argument marshalling only."""
+    _check(load().xyl_walk_returns(C.c_void_p(row_ptr.data_ptr()), C.c_void_p(col.data_ptr()), row_ptr.numel() - 1,
+                                   col.numel(), C.c_void_p(start.data_ptr()), start.numel(), first_walker, n_steps,
+                                   seed, C.c_void_p(returns.data_ptr()), _stream(stream)))
+    return returns
 
 
 # ----------------------------------------------------------------- graphs
