@@ -153,17 +153,27 @@ struct Place {
 };
 
 // The new spins of site i go to this CTA's copy and, with a site split, to
-// the copies of the peers that read the site.
+// the copies of the peers that read the site: the same shared-memory offset in
+// the peer, addressed through mapa and written with st.shared::cluster.
 template <int RV, bool SPLIT>
 __device__ __forceinline__ void put_spins(cg::cluster_group &cluster, const ResidentParams &rp, const Place &pl,
                                           float2 *p, uint32_t peers, const float2 (&n)[RV])
 {
+    (void)cluster;
     sts_spins<RV>(p, n);
     if (SPLIT) {
+        const uint32_t local = (uint32_t)__cvta_generic_to_shared(p);
+        const uint32_t first = (uint32_t)(pl.gi * rp.G);
         while (peers) {
-            const int r = __ffs(peers) - 1;
+            const uint32_t r = (uint32_t)__ffs(peers) - 1u;
             peers &= peers - 1u;
-            sts_spins<RV>(cluster.map_shared_rank(p, (unsigned)(pl.gi * rp.G + r)), n);
+            uint32_t remote;
+            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(first + r));
+            if constexpr (RV == 2)
+                asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(remote), "f"(n[0].x), "f"(n[0].y),
+                             "f"(n[RV - 1].x), "f"(n[RV - 1].y) : "memory");
+            else
+                asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(remote), "f"(n[0].x), "f"(n[0].y) : "memory");
         }
     }
 }
