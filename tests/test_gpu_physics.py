@@ -7,9 +7,9 @@ U4(T, N) with U4(T, N/4), in agreement with the analytic 1.9361.  For Poisson
 degrees of mean c the mean excess degree is also c, and the tree (cavity)
 instability of the XY model sits where c I1(beta)/I0(beta) = 1; that closed
 form is pinned here against the printed value, then the crossing of the
-disorder-averaged cumulant (Sec. III, U4 = [<m^4>]/[<m^2>]^2 - 1 as a ratio of
-disorder averages) between L = 32 and L = 64 from the FP32 batched engine is
-compared with it.
+disorder-averaged cumulant (Sec. III: U4 = [<m^4>] / [<m^2>^2] - 1, [.] the
+average over graphs of the thermal averages) between L = 32 and L = 64 from the
+FP32 batched engine is compared with it.
 """
 import numpy as np
 import pytest
@@ -44,7 +44,7 @@ def _u4_curves(xyl, wl, L, n_samples, temps, warm, meas):
     idx = np.arange(n_samples)
 
     def u4(keep):
-        return m4[keep].mean(0) / m2[keep].mean(0) ** 2 - 1.0
+        return m4[keep].mean(0) / (m2[keep] ** 2).mean(0) - 1.0
 
     return u4(idx), np.array([u4(np.delete(idx, k)) for k in idx])
 
