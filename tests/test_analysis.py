@@ -1,0 +1,87 @@
+"""Host analysis layer (paper_1211_3991_gb300.analysis) against exact cases.
+
+Sec. III observables from accumulator sums: a Gaussian two-component
+magnetisation has <m^4> = 2 <m^2>^2 (U4 = 1), an ordered one U4 = 0 and chi = 0;
+an Ornstein-Zernike chi(k) gives back its xi_2 exactly for any psi; the
+specific heat is N var(e) / T^2.  FSS tools: known crossings, the power laws of
+Eqs. Tfsscaling and scaling_lndotU4, jackknife = standard error for a mean,
+exponential windows.
+"""
+import numpy as np
+import pytest
+
+from paper_1211_3991_gb300 import analysis as an
+
+
+def _acc_from_samples(e, mx, my, chik):
+    m2 = mx ** 2 + my ** 2
+    rows = [len(e), e.sum(), (e ** 2).sum(), np.sqrt(m2).sum(), mx.sum(), my.sum(), m2.sum(), (m2 ** 2).sum(),
+            chik.sum()]
+    return np.array(rows, np.float64)
+
+
+def test_gaussian_and_ordered_cumulants():
+    rng = np.random.default_rng(0)
+    n = 1_000_000
+    N, T, L = 1024, 1.5, 32
+    e = rng.normal(-1.2, 0.03, n)
+    mx, my = rng.normal(0, 0.1, n), rng.normal(0, 0.1, n)
+    obs = an.observables(an.thermal_means(_acc_from_samples(e, mx, my, np.full(n, 2.0))), N, T, L)
+    assert abs(obs["u4_sample"] - 1.0) < 0.01
+    assert abs(obs["c"] - N * 0.03 ** 2 / T ** 2) / (N * 0.03 ** 2 / T ** 2) < 0.01
+    assert abs(obs["chi0"] - N * 0.02) / (N * 0.02) < 0.01
+    # ordered: |m| fixed, direction fixed -> U4 = 0, connected chi = 0
+    k = np.ones(1000)
+    obs = an.observables(an.thermal_means(_acc_from_samples(-2.0 * k, 0.6 * k, 0.8 * k, k)), N, T, L)
+    assert abs(obs["u4_sample"]) < 1e-12 and abs(obs["chi"]) < 1e-9 and abs(obs["chi0"] - N) < 1e-9
+    assert obs["c"] == pytest.approx(0.0, abs=1e-9)
+
+
+@pytest.mark.parametrize("rho,psi", [(None, 2.0), (3.5, 1.5), (5.0, 2.0)])
+def test_xi2_of_ornstein_zernike(rho, psi):
+    L, N, xi = 64, 4096, 7.3
+    kh = 2 * np.sin(np.pi / L)
+    chi0 = 250.0
+    chik = chi0 / (1.0 + (kh * xi) ** psi)
+    means = np.zeros(9)
+    means[0] = 1
+    means[6] = chi0 / N
+    means[8] = chik
+    assert an.observables(means, N, 1.0, L, rho=rho)["xi2"] == pytest.approx(xi, rel=1e-12)
+
+
+def test_disorder_u4_is_a_ratio_of_graph_averages():
+    means = np.zeros((2, 3, 9))
+    a, b = np.array([0.2, 0.3, 0.4]), np.array([0.1, 0.5, 0.2])
+    means[0, :, 6], means[1, :, 6] = a, b
+    means[0, :, 7], means[1, :, 7] = 2 * a ** 2, 2 * b ** 2
+    np.testing.assert_allclose(an.disorder_u4(means), 1.0, rtol=1e-14)
+    means[1, :, 7] = b ** 2
+    np.testing.assert_allclose(an.disorder_u4(means), (2 * a ** 2 + b ** 2) / (a ** 2 + b ** 2) - 1, rtol=1e-14)
+
+
+def test_jackknife_of_a_mean_is_the_standard_error():
+    x = np.random.default_rng(1).normal(size=(50, 3))
+    full, err, loo = an.jackknife(x, lambda d: d.mean(0))
+    np.testing.assert_allclose(full, x.mean(0))
+    np.testing.assert_allclose(err, x.std(0, ddof=1) / np.sqrt(50), rtol=1e-12)
+    assert loo.shape == (50, 3)
+
+
+def test_crossing_and_fss_fits():
+    T = np.linspace(1.0, 2.0, 11)
+    assert an.crossing(T, T - 1.55, 2 * (T - 1.55)) == pytest.approx(1.55, abs=1e-12)
+    assert np.isnan(an.crossing(T, T, T + 1))
+    N = np.array([16, 32, 64, 128, 256]) ** 2.0
+    tc, A, x = an.fit_tf(N, 1.9 + 0.5 * N ** -0.5)
+    assert tc == pytest.approx(1.9, abs=1e-4) and x == pytest.approx(0.5, abs=1e-3) and A == pytest.approx(0.5, rel=1e-2)
+    assert an.fit_nu_bar(N, 3.0 * N ** 0.5) == pytest.approx(2.0, rel=1e-12)
+
+
+def test_exponential_windows_and_equilibration_check():
+    assert an.exponential_windows(100) == [(1, 2), (2, 4), (4, 8), (8, 16), (16, 32), (32, 64)]
+    rng = np.random.default_rng(2)
+    _, ok = an.window_means(rng.normal(size=4096))
+    assert ok
+    _, ok = an.window_means(rng.normal(size=4096) + np.linspace(0, 5, 4096))
+    assert not ok
