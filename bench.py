@@ -151,7 +151,11 @@ def run_oracle_sample(cfg, sweeps=0, seconds=0.0, measure_every=32, chunk=25, ma
     import oracle
     from paper_1211_3991_gb300 import workloads as wl
     L, rho, _ = cfg.graphs[sample_index]
-    ei, ej, _, _ = oracle.levy_graph(L, wl.Z, rho, wl.GRAPH_SEED, wl.graph_stream_id(cfg, sample_index))
+    if cfg.ensemble == "bonds":
+        ei, ej, _ = oracle.levy_bonds(L, rho, wl.GRAPH_SEED, wl.graph_stream_id(cfg, sample_index),
+                                      fbc=cfg.boundary == "fbc")
+    else:
+        ei, ej, _, _ = oracle.levy_graph(L, wl.Z, rho, wl.GRAPH_SEED, wl.graph_stream_id(cfg, sample_index))
     color, _ = oracle.slo_color(L * L, ei, ej)
     sim = oracle.Sim(L * L, ei, ej, color, cfg.betas(), cfg.deltas(), wl.SPIN_SEED, sample=wl.graph_stream_id(cfg, sample_index),
                      xy=oracle.lattice_xy(L), L=L)
@@ -195,6 +199,95 @@ def reference_arm(args, cfg):
     }), flush=True)
 
 
+WALK_METRIC = "walker-steps/s of simple random walks (spectral dimension, App. A)"
+
+
+def walk_bench(args):
+    """Random walks on one 2N-bond Levy graph (L=512, rho=10/3, periodic): each
+    step of a walker reads its node's CSR row bounds and one neighbour id
+    (12 B of algorithmic gathers, two dependent loads).  Walkers start on random
+    nodes of degree > 2 (the paper's rule for rho <= 4)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1211_3991_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1211_3991_gb300 import xyl
+    rank, world, local = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    L, rho, W, T = 512, 10.0 / 3.0, args.walkers, args.walk_steps
+    g = xyl.build_levy_bonds(L, rho, 1, rank)
+    _, row_ptr, col, _ = g.csr()
+    start = np.random.default_rng(rank).choice(np.flatnonzero(np.diff(row_ptr) > 2), W).astype(np.int32)
+    rp, cl = torch.from_numpy(row_ptr).to(dev), torch.from_numpy(col).to(dev)
+    st = torch.from_numpy(start).to(dev)
+    out = torch.empty(T + 1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    for k in range(args.warmup):
+        xyl.walk_returns(rp, cl, st, T, 1000 + k, out, stream=stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for k in range(args.steps):
+        xyl.walk_returns(rp, cl, st, T, 2000 + k, out, first_walker=0, stream=stream)
+    b.record(stream)
+    b.synchronize()
+    clock_info = clocks.stop()
+    ms = a.elapsed_time(b)
+    max_ms, units = reduce_over_ranks(ms, float(W) * T * args.steps, world, dev)
+    value = units / (max_ms / 1e3)
+    # end to end: start nodes host -> device and the return histogram back, every step
+    host_start = torch.from_numpy(start).pin_memory()
+    host_out = torch.empty(T + 1, dtype=torch.int64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        st.copy_(host_start, non_blocking=True)
+        xyl.walk_returns(rp, cl, st, T, 3000 + k, out, stream=stream)
+        host_out.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_max, e2e_units = reduce_over_ranks(e2e_s, float(W) * T * args.steps, world, dev)
+    peak, peak_kind = _peaks()
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        # chunks of 20000 walkers until about 10 s of oracle time
+        n_cpu, dt, chunk = 0, 0.0, 20000
+        while dt < 10.0 and n_cpu + chunk <= W:
+            t1 = time.perf_counter()
+            oracle.walk_returns(row_ptr, col, start[n_cpu:n_cpu + chunk], T, 5)
+            dt += time.perf_counter() - t1
+            n_cpu += chunk
+        cpu = {"value": n_cpu * T / dt, "unit": "walker-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n_cpu} of the walkers, {T} steps ({dt:.1f} s, one thread)"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": WALK_METRIC, "value": value, "unit": "walker-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"one 2N-bond Levy graph per rank, L={L}, rho=10/3, periodic; {W} walkers x {T} "
+                       "steps per step, starts on nodes of degree > 2", "l2": "CSR (5 MB) L2-resident by design"},
+            "roofline": {"bound": "hbm", "achieved": 12.0 * value / world / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": 12.0 * value / world / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
+                         "bytes_per_update": 12.0, "kernel": "walk_kernel",
+                         "note": "two dependent L2 gathers per step: latency-bound, not HBM-bound"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_units / e2e_max, "unit": "walker-steps/s", "h2d_bytes_per_step": int(start.nbytes),
+                    "d2h_bytes_per_step": int(8 * (T + 1))},
+            "gpu_launches": args.steps,
+            "clocks": clock_info,
+        }), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -214,7 +307,16 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--measure-every", type=int, default=32, help="sweeps between measurements (the paper: 32)")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "walk"],
+                    help="sweep: the Monte Carlo sampler (default); walk: random walks for the spectral dimension")
+    ap.add_argument("--walkers", type=int, default=1 << 20)
+    ap.add_argument("--walk-steps", type=int, default=1000)
     args = ap.parse_args()
+    if args.workload == "walk":
+        if args.impl == "reference":
+            raise SystemExit("--impl reference times the sampler workload only")
+        walk_bench(args)
+        return
 
     from paper_1211_3991_gb300 import workloads as wl
     cfg = wl.config(args.config)

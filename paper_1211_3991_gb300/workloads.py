@@ -16,6 +16,7 @@ free boundaries) at small sizes for parity checks:
 
   E1  one graph, L=16, rho=0 (Erdos-Renyi limit), periodic, 4 temperatures geometric in [1.6, 2.4]
   E2  one graph, L=16, rho=7/3, free boundaries, 4 temperatures geometric in [1.6, 2.4]
+  B64 64 graphs, L=64, rho=10/3 (long-range regime), periodic, 12 temperatures geometric in [1.4, 2.0]
 """
 from __future__ import annotations
 
@@ -92,6 +93,9 @@ def config(name: str) -> Config:
     if name == "E2":
         return Config("E2", [(16, 7.0 / 3.0, 0)], geometric_temperatures(1.6, 2.4, 4), ensemble="bonds",
                       boundary="fbc", description="L=16 2N bonds rho=7/3 free boundaries, 4 T geometric in [1.6,2.4]")
+    if name == "B64":
+        return Config("B64", [(64, 10.0 / 3.0, s) for s in range(64)], geometric_temperatures(1.4, 2.0, 12),
+                      ensemble="bonds", description="64 graphs L=64 2N bonds rho=10/3 periodic, 12 T geometric in [1.4,2.0]")
     if name == "C5":
         g = [(512, rho, s) for rho in (2.5, 4.5) for s in range(64)]
         return Config("C5", g, geometric_temperatures(1.5, 3.5, 32),
