@@ -55,6 +55,7 @@ def _load():
         lib.orc_fbc_table.argtypes = [C.c_int, C.c_double, i32p, i32p, u64p]
         lib.orc_levy_bonds.argtypes = [C.c_int, C.c_double, C.c_int64, C.c_int, C.c_uint64, C.c_uint32, i32p, i32p,
                                        u64p]
+        lib.orc_sim_set_couplings.argtypes = [P, f64p]
         lib.orc_walk_returns.argtypes = [C.c_int, i32p, i32p, C.c_int64, i32p, C.c_int32, C.c_uint64, u64p]
         lib.orc_pick_partner_counts.argtypes = [C.c_int, C.c_int, C.c_double, C.c_uint64, i32p, i32p, i32p,
                                                 C.c_int, C.c_int, C.c_int64, i64p]
@@ -291,6 +292,18 @@ class Sim:
 
     def init(self, aligned=False):
         self._lib.orc_sim_init(self._h, 1 if aligned else 0)
+
+    def set_couplings(self, j_per_bond=None):
+        """Random bonds: one coupling per bond (edge order given to the
+        constructor); None restores J = 1.  Pinned by exact gauge invariance
+        and quadrature on frustrated small graphs."""
+        if j_per_bond is None:
+            self._jkeep = None
+            self._lib.orc_sim_set_couplings(self._h, None)
+            return
+        self._jkeep = np.ascontiguousarray(j_per_bond, np.float64)
+        if self._lib.orc_sim_set_couplings(self._h, _ptr(self._jkeep, C.c_double)):
+            raise MemoryError("oracle allocation failed")
 
     def sweeps(self, n, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1):
         self._lib.orc_sim_sweeps(self._h, int(n), int(ops), int(measure_every))

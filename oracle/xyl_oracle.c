@@ -870,6 +870,8 @@ typedef struct {
     int64_t *n_ties;          /* per replica: near-tie Metropolis tests since the last clear */
     int64_t first_pt_tie;
     double min_margin;        /* smallest Metropolis margin seen */
+    double *jb;               /* coupling of each bond, or NULL (all J = 1) */
+    double *jn;               /* coupling of each neighbour entry (aligned with nbr), or NULL */
 } orc_sim;
 
 void orc_sim_free(orc_sim *s)
@@ -879,6 +881,7 @@ void orc_sim_free(orc_sim *s)
     free(s->cx); free(s->sx); free(s->cy); free(s->sy); free(s->beta); free(s->delta);
     free(s->vx); free(s->vy); free(s->slot_of); free(s->rep_at); free(s->E); free(s->acc);
     free(s->met_acc); free(s->met_try); free(s->pt_acc); free(s->pt_try); free(s->first_tie); free(s->n_ties);
+    free(s->jb); free(s->jn);
     free(s);
 }
 
@@ -970,7 +973,8 @@ static double energy_of(const orc_sim *s, int r)
     double E = 0.0;
     for (int64_t e = 0; e < s->n_bonds; ++e) {
         int i = s->bi[e], j = s->bj[e];
-        E -= x[i] * x[j] + y[i] * y[j];
+        if (s->jb) E -= s->jb[e] * (x[i] * x[j] + y[i] * y[j]);
+        else E -= x[i] * x[j] + y[i] * y[j];
     }
     return E;
 }
@@ -1022,11 +1026,47 @@ static void note_tie(orc_sim *s, int r, double margin)
 static void local_field(const orc_sim *s, const double *x, const double *y, int v, double *hx, double *hy)
 {
     double ax = 0.0, ay = 0.0;
-    for (int a = s->ptr[v]; a < s->ptr[v + 1]; ++a) {
-        ax += x[s->nbr[a]];
-        ay += y[s->nbr[a]];
+    if (s->jn) {
+        for (int a = s->ptr[v]; a < s->ptr[v + 1]; ++a) {
+            ax += s->jn[a] * x[s->nbr[a]];
+            ay += s->jn[a] * y[s->nbr[a]];
+        }
+    } else {
+        for (int a = s->ptr[v]; a < s->ptr[v + 1]; ++a) {
+            ax += x[s->nbr[a]];
+            ay += y[s->nbr[a]];
+        }
     }
     *hx = ax; *hy = ay;
+}
+
+/*
+ * Random bonds (the paper's "other continuous models with random bonds",
+ * App. B): H = -sum_(ij) J_ij S_i . S_j with one coupling per bond (J = +1 or
+ * -1 for the XY spin glass; any value works), in the order of the bond list.
+ * The local field becomes h_i = sum_j J_ij S_j and the energy sums J_ij S_i.S_j;
+ * the sweep is otherwise unchanged.  NULL restores J = 1.  Recomputes the
+ * energies of the current spins.
+ */
+int orc_sim_set_couplings(orc_sim *s, const double *j_per_bond)
+{
+    free(s->jb); free(s->jn);
+    s->jb = s->jn = NULL;
+    if (!j_per_bond) { refresh_energies(s); return 0; }
+    s->jb = (double *)malloc(sizeof(double) * (size_t)(s->n_bonds + 1));
+    s->jn = (double *)malloc(sizeof(double) * (size_t)(s->ptr[s->n] + 1));
+    if (!s->jb || !s->jn) return -1;
+    for (int64_t e = 0; e < s->n_bonds; ++e) {
+        s->jb[e] = j_per_bond[e];
+        const int ends[2] = { s->bi[e], s->bj[e] };
+        for (int q = 0; q < 2; ++q) {
+            const int v = ends[q], u = ends[1 - q];
+            for (int a = s->ptr[v]; a < s->ptr[v + 1]; ++a)
+                if (s->nbr[a] == u) { s->jn[a] = j_per_bond[e]; break; }
+        }
+    }
+    refresh_energies(s);
+    return 0;
 }
 
 static void metropolis_site(orc_sim *s, int r, int v)

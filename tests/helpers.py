@@ -60,7 +60,7 @@ def run_bins(sim, n_bins: int, bin_sweeps: int, ops: int, measure_every: int = 1
     return np.array(out)
 
 
-def quadrature_moments(n, edges, beta, M=48, xy=None, L=None):
+def quadrature_moments(n, edges, beta, M=48, xy=None, L=None, couplings=None):
     """Exact <e>, <e^2>, <m^2>, <m^4>, <|m|>, <chi(k_min)> for n <= 4 spins.
 
     Fix theta_0 = 0 (all quantities are rotation invariant) and integrate the
@@ -69,8 +69,9 @@ def quadrature_moments(n, edges, beta, M=48, xy=None, L=None):
     mesh = np.meshgrid(*([grid] * (n - 1)), indexing="ij")
     th = [np.zeros_like(mesh[0])] + list(mesh)
     E = np.zeros_like(mesh[0])
-    for i, j in edges:
-        E -= np.cos(th[i] - th[j])
+    J = [1.0] * len(edges) if couplings is None else list(couplings)
+    for (i, j), c in zip(edges, J):
+        E -= c * np.cos(th[i] - th[j])
     w = np.exp(-beta * (E - E.min()))
     Z = w.sum()
     mx = sum(np.cos(t) for t in th) / n
