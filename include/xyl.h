@@ -144,6 +144,22 @@ int xyl_build_levy_bonds(int32_t L, double rho, int64_t n_bonds, int32_t boundar
 int xyl_graph_from_edges(int32_t n, int64_t n_edges, const int32_t *edges, const int32_t *xy, int32_t L,
                          xyl_graph **out);
 
+/*
+ * xyl_graph_set_couplings -- random bonds: H = -sum_(ij) J_ij S_i . S_j with
+ * J_ij = +1 or -1 per link (the paper's method applied to "random bonds", App.
+ * B; J = -1 everywhere on a bipartite graph is the antiferromagnet, random
+ * signs the XY spin glass).  j: one value per link in creation order (the
+ * order of xyl_graph_export_edges), each +1 or -1 (XYL_EINVAL otherwise), or
+ * NULL to restore J = 1.  Plans made from the graph afterwards use the
+ * couplings (a plan copies the graph when it is created).  Engines: every
+ * engine; the resident shape of the batched engine keeps J in bit 15 of its
+ * 16-bit staged rows, so with couplings it stages rows only when N <= 32767.
+ */
+int xyl_graph_set_couplings(xyl_graph *g, const int8_t *j);
+
+/* Couplings of the CSR entries (2*n_edges values aligned with xyl_graph_export_csr's col). */
+int xyl_graph_export_couplings(const xyl_graph *g, int8_t *j_csr);
+
 /* Sizes of a graph; any output pointer may be NULL.  restarts: pairing restarts used. */
 int xyl_graph_info(const xyl_graph *g, int32_t *n, int64_t *n_edges, int32_t *n_colors, int32_t *max_deg,
                    int32_t *restarts);

@@ -186,15 +186,20 @@ __global__ void recompute_kernel(DevPlan P, int layout, int fp64, int renormalis
         double lx = 0.0, ly = 0.0;
         const int rb = P.row_ptr[d.row_off + i], re = P.row_ptr[d.row_off + i + 1];
         for (int k = rb; k < re; ++k) {
-            const int j = P.col[d.col_off + k];
+            // a neighbour id with its top bit set is a link with J = -1 (random bonds)
+            const int raw = P.col[d.col_off + k];
+            const int j = raw & 0x7fffffff;
             if (j >= i) continue;
+            double vx, vy;
             if (fp64) {
                 const double2 v = reinterpret_cast<const double2 *>(P.spins)[spin_index(d, layout, j, r)];
-                lx += v.x; ly += v.y;
+                vx = v.x; vy = v.y;
             } else {
                 const float2 v = reinterpret_cast<const float2 *>(P.spins)[spin_index(d, layout, j, r)];
-                lx += v.x; ly += v.y;
+                vx = v.x; vy = v.y;
             }
+            if (raw < 0) { vx = -vx; vy = -vy; }
+            lx += vx; ly += vy;
         }
         acc[kObsE] -= sx * lx + sy * ly;
         acc[kObsMx] += sx;

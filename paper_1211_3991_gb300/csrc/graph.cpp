@@ -533,6 +533,43 @@ int xyl_graph_export_edges(const xyl_graph *g, int32_t *ei, int32_t *ej)
     return XYL_OK;
 }
 
+int xyl_graph_set_couplings(xyl_graph *g, const int8_t *j)
+{
+    clear_error();
+    if (!g) return fail(XYL_EINVAL, "xyl_graph_set_couplings: NULL graph");
+    if (!j) {
+        g->jlink.clear();
+        g->jcsr.clear();
+        return XYL_OK;
+    }
+    for (int64_t e = 0; e < g->n_edges; ++e)
+        if (j[e] != 1 && j[e] != -1) return fail(XYL_EINVAL, "xyl_graph_set_couplings: J[%lld] = %d is not +1 or -1",
+                                                 (long long)e, (int)j[e]);
+    // colour-sorted id of each original id, then the entry of each link in both rows
+    std::vector<int32_t> sorted(g->n);
+    for (int s = 0; s < g->n; ++s) sorted[g->perm[s]] = s;
+    std::vector<int8_t> csr(g->col.size(), 1);
+    for (int64_t e = 0; e < g->n_edges; ++e) {
+        const int a = sorted[g->ei[e]], b = sorted[g->ej[e]];
+        const int ends[2][2] = {{a, b}, {b, a}};
+        for (const auto &rb : ends) {
+            const int32_t *lo = g->col.data() + g->row_ptr[rb[0]], *hi = g->col.data() + g->row_ptr[rb[0] + 1];
+            const int32_t *at = std::lower_bound(lo, hi, rb[1]);
+            csr[at - g->col.data()] = j[e];
+        }
+    }
+    g->jlink.assign(j, j + g->n_edges);
+    g->jcsr.swap(csr);
+    return XYL_OK;
+}
+
+int xyl_graph_export_couplings(const xyl_graph *g, int8_t *j_csr)
+{
+    if (!g || !j_csr) return fail(XYL_EINVAL, "xyl_graph_export_couplings: NULL argument");
+    for (size_t k = 0; k < g->col.size(); ++k) j_csr[k] = g->jcsr.empty() ? (int8_t)1 : g->jcsr[k];
+    return XYL_OK;
+}
+
 void xyl_graph_free(xyl_graph *g) { delete g; }
 
 }  // extern "C"

@@ -33,4 +33,6 @@ struct xyl_graph {
     std::vector<int32_t> col;         // colour-sorted neighbour ids, ascending per row
     std::vector<int32_t> color_ptr;   // n_colors + 1
     std::vector<int32_t> color;       // colour of each original id
+    std::vector<int8_t> jlink;        // coupling of each link (creation order), empty = all +1
+    std::vector<int8_t> jcsr;         // coupling of each CSR entry (aligned with col), empty = all +1
 };

@@ -20,8 +20,10 @@ template <> __device__ __forceinline__ double2 make_vec2<double>(double x, doubl
 
 // One colour phase of the Metropolis (IS_MET) or overrelaxation pass.  With
 // FUSE the replica's energy (links to lower colours, counted at their upper
-// endpoint), magnetisation and Fourier sums are reduced into obs[0].
-template <typename Real, bool IS_MET, bool FUSE>
+// endpoint), magnetisation and Fourier sums are reduced into obs[0].  With
+// COUPLED a neighbour id with its top bit set is a link with J = -1: the
+// neighbour's spin enters the local field negated (exactly J * S_j).
+template <typename Real, bool IS_MET, bool FUSE, bool COUPLED>
 __global__ void __launch_bounds__(kPlainBlock) plain_phase_kernel(DevPlan P, int c)
 {
     using V = Vec2<Real>;
@@ -46,8 +48,13 @@ __global__ void __launch_bounds__(kPlainBlock) plain_phase_kernel(DevPlan P, int
         Real hx = 0, hy = 0;
         const int rb = rp[i], re = rp[i + 1];
         for (int k = rb; k < re; ++k) {
-            const int j = cl[k];
-            const V sj = sp[j];
+            const int raw = cl[k];
+            const int j = COUPLED ? (raw & 0x7fffffff) : raw;
+            V sj = sp[j];
+            if (COUPLED && raw < 0) {
+                sj.x = -sj.x;
+                sj.y = -sj.y;
+            }
             hx += sj.x;
             hy += sj.y;
             if (FUSE && j < cb) {
@@ -111,7 +118,7 @@ __global__ void __launch_bounds__(kPlainBlock) plain_phase_kernel(DevPlan P, int
     }
 }
 
-template <typename Real>
+template <typename Real, bool COUPLED>
 cudaError_t sweep_impl(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every, cudaStream_t st,
                        int64_t *launches)
 {
@@ -121,15 +128,15 @@ cudaError_t sweep_impl(const DevPlan &P, const PlanShape &S, uint32_t ops, int m
     if (met) {
         for (int c = 0; c < S.max_Q; ++c) {
             if (orx)
-                plain_phase_kernel<Real, true, false><<<grid, kPlainBlock, 0, st>>>(P, c);
+                plain_phase_kernel<Real, true, false, COUPLED><<<grid, kPlainBlock, 0, st>>>(P, c);
             else
-                plain_phase_kernel<Real, true, true><<<grid, kPlainBlock, 0, st>>>(P, c);
+                plain_phase_kernel<Real, true, true, COUPLED><<<grid, kPlainBlock, 0, st>>>(P, c);
             ++n;
         }
     }
     if (orx) {
         for (int c = 0; c < S.max_Q; ++c) {
-            plain_phase_kernel<Real, false, true><<<grid, kPlainBlock, 0, st>>>(P, c);
+            plain_phase_kernel<Real, false, true, COUPLED><<<grid, kPlainBlock, 0, st>>>(P, c);
             ++n;
         }
     }
@@ -146,8 +153,11 @@ cudaError_t sweep_impl(const DevPlan &P, const PlanShape &S, uint32_t ops, int m
 cudaError_t launch_plain_sweep(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every,
                                cudaStream_t st, int64_t *launches)
 {
-    return S.fp64 ? sweep_impl<double>(P, S, ops, measure_every, st, launches)
-                  : sweep_impl<float>(P, S, ops, measure_every, st, launches);
+    if (S.coupled)
+        return S.fp64 ? sweep_impl<double, true>(P, S, ops, measure_every, st, launches)
+                      : sweep_impl<float, true>(P, S, ops, measure_every, st, launches);
+    return S.fp64 ? sweep_impl<double, false>(P, S, ops, measure_every, st, launches)
+                  : sweep_impl<float, false>(P, S, ops, measure_every, st, launches);
 }
 
 }  // namespace xyl

@@ -21,6 +21,7 @@ struct HostSample {
     uint32_t sample_id = 0;
     std::vector<double> beta, delta;
     std::vector<int32_t> perm, row_ptr, col, color_ptr, xy;
+    std::vector<int8_t> jcsr;  // couplings of the CSR entries, empty = all +1
 };
 
 struct Region {
@@ -188,7 +189,8 @@ bool resident_fit(const xyl_plan *p, int g, int G, int block, int stage, Batched
         }
         const int W = B.fixed_deg == 6 ? 6 : 8;
         const size_t col = a16((size_t)owned * W * sizeof(uint16_t));
-        if (stage >= 0 && off + col <= kResidentDynLimitBytes) {
+        // with couplings bit 15 of a staged id holds J, so ids (and the padding id N) stay below 2^15
+        if (stage >= 0 && off + col <= kResidentDynLimitBytes && (!p->shape.coupled || max_N <= 32767)) {
             B.rs_csr_w = W;
             B.rs_off_col = off;
             off += col;
@@ -221,6 +223,7 @@ int apply_shape(xyl_plan *p, int g, int G, int block, int stage, int resident)
     B.G = G;
     B.Rg = g;
     B.block = block;
+    B.coupled = p->shape.coupled;
     int max_deg = 1;
     for (auto &h : p->hs) max_deg = std::max(max_deg, h.max_deg);
     B.max_deg = max_deg;
@@ -429,6 +432,8 @@ int xyl_plan_create(const xyl_sample *samples, int32_t n_samples, int32_t engine
             }
         }
         h.perm = g->perm; h.row_ptr = g->row_ptr; h.col = g->col; h.color_ptr = g->color_ptr; h.xy = g->xy;
+        h.jcsr = g->jcsr;
+        for (int8_t j : h.jcsr) p->shape.coupled |= (j < 0);
         p->total_R += h.R;
         p->total_N += h.N;
         p->total_nnz += (int64_t)h.col.size();
@@ -479,6 +484,10 @@ int xyl_bind(xyl_plan *p, void *d_workspace, size_t bytes, void *stream)
         d.col_off = col_off; d.spin_off = spin_off;
         row_ptr.insert(row_ptr.end(), h.row_ptr.begin(), h.row_ptr.end());
         col.insert(col.end(), h.col.begin(), h.col.end());
+        // random bonds: J = -1 in the top bit of the neighbour id
+        if (!h.jcsr.empty())
+            for (size_t k = 0; k < h.col.size(); ++k)
+                if (h.jcsr[k] < 0) col[col.size() - h.col.size() + k] |= (int32_t)0x80000000u;
         perm.insert(perm.end(), h.perm.begin(), h.perm.end());
         color_ptr.insert(color_ptr.end(), h.color_ptr.begin(), h.color_ptr.end());
         for (int i = 0; i < h.N; ++i) {

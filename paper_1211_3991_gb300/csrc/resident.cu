@@ -70,34 +70,44 @@ struct ResidentShared {
 };
 static_assert(sizeof(ResidentShared) + kResidentDynLimitBytes <= 232448, "resident shared memory above 227 KB");
 
-// Neighbour ids, random-stream key and peer mask of one site.
+// Neighbour ids, random-stream key and peer mask of one site; with random
+// bonds, bit k of neg marks a link with J = -1.
 template <int DEG>
 struct Row {
     int nb[DEG > 0 ? DEG : 8];  // missing entries of a shorter row point at the zero spin N
     uint32_t key;
     uint32_t peers;
+    uint32_t neg;
 };
 
 struct Stage {
-    const uint16_t *col;    // [owned][csr_w] colour-sorted ids, padding -> N (a zero spin)
+    const uint16_t *col;    // [owned][csr_w] colour-sorted ids, padding -> N (a zero spin); J = -1 in bit 15 (COUPLED)
     const uint16_t *ids;    // [owned] original ids
     const uint16_t *peers;  // [owned] peer masks (site split)
 };
 
-// i: colour-sorted site id; l: its staged row.
-template <int DEG, bool IS_MET, bool SPLIT>
+// i: colour-sorted site id; l: its staged row.  With COUPLED the sign of each
+// link comes from bit 15 of a staged id or bit 31 of a global one.
+template <int DEG, bool IS_MET, bool SPLIT, bool COUPLED>
 __device__ __forceinline__ void fetch_row(const DevPlan &P, const DevSample &d, const Stage &stg, int i, int l,
                                           Row<DEG> &row)
 {
     constexpr int W = DEG > 0 ? DEG : 8;
+    row.neg = 0u;
     if (stg.col) {
         // rows of W 16-bit ids, 4-byte aligned (W even)
         const uint32_t *c = reinterpret_cast<const uint32_t *>(stg.col + (size_t)l * W);
 #pragma unroll
         for (int k = 0; k < W / 2; ++k) {
             const uint32_t w = c[k];
-            row.nb[2 * k] = (int)(w & 0xffffu);
-            row.nb[2 * k + 1] = (int)(w >> 16);
+            if (COUPLED) {
+                row.nb[2 * k] = (int)(w & 0x7fffu);
+                row.nb[2 * k + 1] = (int)((w >> 16) & 0x7fffu);
+                row.neg |= ((w >> 15) & 1u) << (2 * k) | ((w >> 31) & 1u) << (2 * k + 1);
+            } else {
+                row.nb[2 * k] = (int)(w & 0xffffu);
+                row.nb[2 * k + 1] = (int)(w >> 16);
+            }
         }
     } else {
         const int32_t *cl = P.col + d.col_off;
@@ -111,6 +121,13 @@ __device__ __forceinline__ void fetch_row(const DevPlan &P, const DevSample &d, 
         }
 #pragma unroll
         for (int k = 0; k < W; ++k) row.nb[k] = (DEG > 0 || k < deg) ? __ldg(cl + rb + k) : d.N;
+        if (COUPLED) {
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                row.neg |= (row.nb[k] < 0 ? 1u : 0u) << k;
+                row.nb[k] &= 0x7fffffff;
+            }
+        }
     }
     if (IS_MET) row.key = stg.ids ? (uint32_t)stg.ids[l] : (uint32_t)__ldg(P.perm + d.site_off + i);
     if (SPLIT) row.peers = stg.peers ? stg.peers[l] : __ldg(P.push + d.site_off + i);
@@ -181,7 +198,7 @@ __device__ __forceinline__ void put_spins(cg::cluster_group &cluster, const Resi
 // One colour phase over this CTA's chunk of colour c for its replicas: one
 // thread per (site, block of RV consecutive replicas).  sp points at the
 // group's spins in shared memory.
-template <bool IS_MET, bool FUSE_E, int RV, int DEG, bool SPLIT>
+template <bool IS_MET, bool FUSE_E, int RV, int DEG, bool SPLIT, bool COUPLED>
 __device__ __forceinline__ void rphase(const DevPlan &P, const DevSample &d, const ResidentShared &sh,
                                        const ResidentParams &rp, const Stage &stg, cg::cluster_group &cluster,
                                        const Place &pl, float2 *sp, int c, uint32_t t, RLane<RV> &ln)
@@ -194,12 +211,13 @@ __device__ __forceinline__ void rphase(const DevPlan &P, const DevSample &d, con
     int q = threadIdx.x;
     if (q >= items) return;
     Row<DEG> cur;
-    fetch_row<DEG, IS_MET, SPLIT>(P, d, stg, lo + (q >> rp.log2lps), base + (q >> rp.log2lps), cur);
+    fetch_row<DEG, IS_MET, SPLIT, COUPLED>(P, d, stg, lo + (q >> rp.log2lps), base + (q >> rp.log2lps), cur);
     for (; q < items; q += blockDim.x) {
         const int i = lo + (q >> rp.log2lps);
         Row<DEG> nxt;
         const int qn = q + (int)blockDim.x;
-        if (qn < items) fetch_row<DEG, IS_MET, SPLIT>(P, d, stg, lo + (qn >> rp.log2lps), base + (qn >> rp.log2lps), nxt);
+        if (qn < items)
+            fetch_row<DEG, IS_MET, SPLIT, COUPLED>(P, d, stg, lo + (qn >> rp.log2lps), base + (qn >> rp.log2lps), nxt);
         float2 s[RV];
         lds_spins<RV>(spl + i * Rg, s);
         float hx[RV], hy[RV], lx[RV], ly[RV];
@@ -210,6 +228,10 @@ __device__ __forceinline__ void rphase(const DevPlan &P, const DevSample &d, con
             const int j = cur.nb[k];
             float2 sj[RV];
             lds_spins<RV>(spl + j * Rg, sj);
+            if (COUPLED && ((cur.neg >> k) & 1u)) {
+#pragma unroll
+                for (int v = 0; v < RV; ++v) sj[v] = make_float2(-sj[v].x, -sj[v].y);
+            }
             const bool lower = FUSE_E && j < cb;
 #pragma unroll
             for (int v = 0; v < RV; ++v) {
@@ -275,7 +297,7 @@ __device__ __forceinline__ unsigned warp_reduce_rep(const ResidentParams &rp, un
     return x;
 }
 
-template <int RV, int DEG, bool SPLIT>
+template <int RV, int DEG, bool SPLIT, bool COUPLED>
 __device__ __forceinline__ void resident_sweeps(const DevPlan &P, const ResidentParams &rp, ResidentShared &sh,
                                                 const Stage &stg, cg::cluster_group &cluster, const Place &pl,
                                                 float2 *sp, float *part, unsigned *part_met, int s, int group)
@@ -306,14 +328,14 @@ __device__ __forceinline__ void resident_sweeps(const DevPlan &P, const Resident
         }
         if (met) {
             for (int c = 0; c < d.Q; ++c) {
-                if (orx) rphase<true, false, RV, DEG, SPLIT>(P, d, sh, rp, stg, cluster, pl, sp, c, t, ln);
-                else rphase<true, true, RV, DEG, SPLIT>(P, d, sh, rp, stg, cluster, pl, sp, c, t, ln);
+                if (orx) rphase<true, false, RV, DEG, SPLIT, COUPLED>(P, d, sh, rp, stg, cluster, pl, sp, c, t, ln);
+                else rphase<true, true, RV, DEG, SPLIT, COUPLED>(P, d, sh, rp, stg, cluster, pl, sp, c, t, ln);
                 phase_barrier<SPLIT>();
             }
         }
         if (orx) {
             for (int c = 0; c < d.Q; ++c) {
-                rphase<false, true, RV, DEG, SPLIT>(P, d, sh, rp, stg, cluster, pl, sp, c, t, ln);
+                rphase<false, true, RV, DEG, SPLIT, COUPLED>(P, d, sh, rp, stg, cluster, pl, sp, c, t, ln);
                 phase_barrier<SPLIT>();
             }
         }
@@ -424,7 +446,7 @@ __device__ __forceinline__ void resident_sweeps(const DevPlan &P, const Resident
     if (leader && threadIdx.x == 0) P.sweep[s] = t;
 }
 
-template <int RV, int DEG, bool SPLIT>
+template <int RV, int DEG, bool SPLIT, bool COUPLED>
 __device__ __forceinline__ void resident_body(const DevPlan &P, const ResidentParams &rp)
 {
     __shared__ ResidentShared sh;
@@ -487,7 +509,12 @@ __device__ __forceinline__ void resident_body(const DevPlan &P, const ResidentPa
                 if (peers) peers[l] = P.push[d.site_off + i];
                 if (col) {
                     const int rb = P.row_ptr[d.row_off + i], re = P.row_ptr[d.row_off + i + 1];
-                    for (int k = 0; k < W; ++k) col[(size_t)l * W + k] = (uint16_t)(k < re - rb ? P.col[d.col_off + rb + k] : N);
+                    for (int k = 0; k < W; ++k) {
+                        const int raw = k < re - rb ? P.col[d.col_off + rb + k] : N;
+                        // with couplings the id keeps 15 bits and bit 15 holds J = -1
+                        col[(size_t)l * W + k] = COUPLED ? (uint16_t)((raw & 0x7fff) | (raw < 0 ? 0x8000 : 0))
+                                                         : (uint16_t)raw;
+                    }
                 }
             }
         }
@@ -500,7 +527,7 @@ __device__ __forceinline__ void resident_body(const DevPlan &P, const ResidentPa
     // peers write into this CTA's copy only after it holds the starting spins
     if (SPLIT) cluster.sync();
     else __syncthreads();
-    resident_sweeps<RV, DEG, SPLIT>(P, rp, sh, stg, cluster, pl, sp, part, part_met, s, group);
+    resident_sweeps<RV, DEG, SPLIT, COUPLED>(P, rp, sh, stg, cluster, pl, sp, part, part_met, s, group);
     // write this CTA's own sites back (every copy agrees after the last barrier)
     float2 *gspw = reinterpret_cast<float2 *>(P.spins) + d.spin_off + group * Rg;
     for (int c = 0; c < d.Q; ++c) {
@@ -513,35 +540,40 @@ __device__ __forceinline__ void resident_body(const DevPlan &P, const ResidentPa
 }
 
 // Up to 672 threads with 96 registers each, or up to 1024 with 64.
-template <int RV, int DEG, bool SPLIT>
+template <int RV, int DEG, bool SPLIT, bool COUPLED>
 __global__ void __maxnreg__(96) resident_kernel(DevPlan P, ResidentParams rp)
 {
-    resident_body<RV, DEG, SPLIT>(P, rp);
+    resident_body<RV, DEG, SPLIT, COUPLED>(P, rp);
 }
 
-template <int RV, int DEG, bool SPLIT>
+template <int RV, int DEG, bool SPLIT, bool COUPLED>
 __global__ void __launch_bounds__(1024, 1) resident_kernel_wide(DevPlan P, ResidentParams rp)
 {
-    resident_body<RV, DEG, SPLIT>(P, rp);
+    resident_body<RV, DEG, SPLIT, COUPLED>(P, rp);
 }
 
 using KernelFn = void (*)(DevPlan, ResidentParams);
 
-template <int RV, int DEG, bool SPLIT>
+template <int RV, int DEG, bool SPLIT, bool COUPLED>
 KernelFn pick_width(const BatchedShape &B)
 {
-    return B.block > kResidentNarrowMaxThreads ? resident_kernel_wide<RV, DEG, SPLIT> : resident_kernel<RV, DEG, SPLIT>;
+    return B.block > kResidentNarrowMaxThreads ? resident_kernel_wide<RV, DEG, SPLIT, COUPLED>
+                                               : resident_kernel<RV, DEG, SPLIT, COUPLED>;
 }
 
-template <bool SPLIT>
+template <bool SPLIT, bool COUPLED>
 KernelFn pick_split(const BatchedShape &B)
 {
     const bool rv2 = B.Rg >= 2;
-    if (B.fixed_deg == 6) return rv2 ? pick_width<2, 6, SPLIT>(B) : pick_width<1, 6, SPLIT>(B);
-    return rv2 ? pick_width<2, -8, SPLIT>(B) : pick_width<1, -8, SPLIT>(B);
+    if (B.fixed_deg == 6) return rv2 ? pick_width<2, 6, SPLIT, COUPLED>(B) : pick_width<1, 6, SPLIT, COUPLED>(B);
+    return rv2 ? pick_width<2, -8, SPLIT, COUPLED>(B) : pick_width<1, -8, SPLIT, COUPLED>(B);
 }
 
-KernelFn pick_resident(const BatchedShape &B) { return B.G > 1 ? pick_split<true>(B) : pick_split<false>(B); }
+KernelFn pick_resident(const BatchedShape &B)
+{
+    if (B.coupled) return B.G > 1 ? pick_split<true, true>(B) : pick_split<false, true>(B);
+    return B.G > 1 ? pick_split<true, false>(B) : pick_split<false, false>(B);
+}
 
 cudaError_t set_resident_attributes(KernelFn k)
 {

@@ -17,6 +17,12 @@ free boundaries) at small sizes for parity checks:
   E1  one graph, L=16, rho=0 (Erdos-Renyi limit), periodic, 4 temperatures geometric in [1.6, 2.4]
   E2  one graph, L=16, rho=7/3, free boundaries, 4 temperatures geometric in [1.6, 2.4]
   B64 64 graphs, L=64, rho=10/3 (long-range regime), periodic, 12 temperatures geometric in [1.4, 2.0]
+
+Random bonds (the method's random-bond variant, App. B): C1's and C2's graphs
+with J = +-1 at random (probability 1/2 each, the XY spin glass):
+
+  G1  L=16, rho=3.5, 4 temperatures geometric in [0.4, 1.0]
+  G2  L=128, rho=3.5, 16 temperatures geometric in [0.3, 1.2]
 """
 from __future__ import annotations
 
@@ -46,6 +52,7 @@ class Config:
     delta: list = field(default_factory=list)
     ensemble: str = "fixed"   # "fixed": every site Z links; "bonds": 2N bonds in all (Sec. II)
     boundary: str = "pbc"     # "bonds" ensemble: "pbc" or "fbc"
+    couplings: str = "ferro"  # "ferro": J = 1; "pm": random signs, J = -1 with probability 1/2 (spin glass)
 
     @property
     def n_samples(self):
@@ -93,6 +100,12 @@ def config(name: str) -> Config:
     if name == "E2":
         return Config("E2", [(16, 7.0 / 3.0, 0)], geometric_temperatures(1.6, 2.4, 4), ensemble="bonds",
                       boundary="fbc", description="L=16 2N bonds rho=7/3 free boundaries, 4 T geometric in [1.6,2.4]")
+    if name == "G2":
+        return Config("G2", [(128, 3.5, 0)], geometric_temperatures(0.3, 1.2, 16), couplings="pm",
+                      description="C2's graph with random +-1 couplings (XY spin glass), 16 T geometric in [0.3,1.2]")
+    if name == "G1":
+        return Config("G1", [(16, 3.5, 0)], geometric_temperatures(0.4, 1.0, 4), couplings="pm",
+                      description="C1's graph with random +-1 couplings, 4 T geometric in [0.4,1.0]")
     if name == "B64":
         return Config("B64", [(64, 10.0 / 3.0, s) for s in range(64)], geometric_temperatures(1.4, 2.0, 12),
                       ensemble="bonds", description="64 graphs L=64 2N bonds rho=10/3 periodic, 12 T geometric in [1.4,2.0]")
@@ -135,7 +148,25 @@ def build_graphs(cfg: Config, threads: int = 0):
         return xyl.build_graph_csr(L, Z, rho, GRAPH_SEED, graph_stream_id(cfg, k))
 
     with cf.ThreadPoolExecutor(max_workers=threads) as ex:
-        return list(ex.map(one, range(cfg.n_samples)))
+        graphs = list(ex.map(one, range(cfg.n_samples)))
+    for k, g in enumerate(graphs):
+        j = couplings_for(cfg, k, g.n_edges)
+        if j is not None:
+            g.set_couplings(j)
+    return graphs
+
+
+COUPLING_SEED = 3
+
+
+def couplings_for(cfg: Config, k: int, n_edges: int):
+    """Random +-1 couplings of sample k (one per link, creation order), or None
+    for the ferromagnet.  Seeded by the sample's stream id."""
+    if cfg.couplings == "ferro":
+        return None
+    import numpy as np
+    rng = np.random.default_rng([COUPLING_SEED, graph_stream_id(cfg, k)])
+    return np.where(rng.random(n_edges) < 0.5, -1, 1).astype(np.int8)
 
 
 def graph_stream_id(cfg: Config, k: int) -> int:

@@ -28,7 +28,8 @@ EXPORTED = (
     "xyl_read_observables", "xyl_reset_observables", "xyl_read_energies", "xyl_read_labels", "xyl_read_spins",
     "xyl_write_spins", "xyl_read_status", "xyl_state_bytes", "xyl_export_state", "xyl_import_state",
     "xyl_last_launch_count", "xyl_plan_free", "xyl_sweep_units", "xyl_unit_count", "xyl_autotune",
-    "xyl_get_tuning", "xyl_sweep_noalloc", "xyl_build_levy_bonds", "xyl_walk_returns",
+    "xyl_get_tuning", "xyl_sweep_noalloc", "xyl_build_levy_bonds", "xyl_walk_returns", "xyl_graph_set_couplings",
+    "xyl_graph_export_couplings",
 )
 
 
@@ -101,6 +102,8 @@ def load():
             "xyl_sweep_noalloc": ([P, i32, u32, i32, P], C.c_int),
             "xyl_build_levy_bonds": ([i32, f64, i64, i32, u64, u32, C.POINTER(P)], C.c_int),
             "xyl_walk_returns": ([P, P, i32, i64, P, i64, u32, i32, u64, P, P], C.c_int),
+            "xyl_graph_set_couplings": ([P, C.POINTER(C.c_int8)], C.c_int),
+            "xyl_graph_export_couplings": ([P, C.POINTER(C.c_int8)], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -161,6 +164,23 @@ class Graph:
         _check(load().xyl_graph_export_csr(self.handle, _p(perm, C.c_int32), _p(row_ptr, C.c_int32),
                                            _p(col, C.c_int32), _p(cptr, C.c_int32)))
         return perm, row_ptr, col, cptr
+
+    def set_couplings(self, j=None):
+        """Random bonds: +1/-1 per link (creation order); None restores J = 1."""
+        if j is None:
+            _check(load().xyl_graph_set_couplings(self.handle, None))
+            return self
+        j = np.ascontiguousarray(j, np.int8)
+        if len(j) != self.n_edges:
+            raise ValueError("one coupling per link")
+        _check(load().xyl_graph_set_couplings(self.handle, _p(j, C.c_int8)))
+        return self
+
+    def couplings(self):
+        """Couplings of the CSR entries (aligned with csr()'s col)."""
+        out = np.zeros(2 * self.n_edges, np.int8)
+        _check(load().xyl_graph_export_couplings(self.handle, _p(out, C.c_int8)))
+        return out
 
     def edges(self):
         ei = np.zeros(self.n_edges, np.int32); ej = np.zeros(self.n_edges, np.int32)

@@ -189,3 +189,27 @@ def test_resident_shape_selection_without_gpu(xyl):
     p = xyl.Plan([(g1, 0, [1.0] * 2, [1.0] * 2), (g2, 1, [1.0] * 4, [1.0] * 4)], engine=xyl.FP32_BATCHED,
                  device="cpu")
     assert p.tuning()["resident"] == -1
+
+
+def test_couplings_are_validated_and_aligned_with_the_csr(xyl):
+    g = xyl.build_graph_csr(16, 6, 3.5, 1, 0)
+    ei, ej = g.edges()
+    rng = np.random.default_rng(5)
+    J = rng.choice(np.array([-1, 1], np.int8), g.n_edges)
+    g.set_couplings(J)
+    perm, rp, col, _ = g.csr()
+    jc = g.couplings()
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(len(perm))
+    for e in range(g.n_edges):
+        for a, b in ((inv[ei[e]], inv[ej[e]]), (inv[ej[e]], inv[ei[e]])):
+            k = rp[a] + np.searchsorted(col[rp[a]:rp[a + 1]], b)
+            assert col[k] == b and jc[k] == J[e]
+    bad = J.copy()
+    bad[7] = 0
+    with pytest.raises(xyl.XylError) as e:
+        g.set_couplings(bad)
+    assert e.value.code == xyl.EINVAL
+    assert np.array_equal(g.couplings(), jc)     # a rejected call leaves the couplings as they were
+    g.set_couplings(None)
+    assert np.all(g.couplings() == 1)
