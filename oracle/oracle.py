@@ -56,6 +56,7 @@ def _load():
         lib.orc_levy_bonds.argtypes = [C.c_int, C.c_double, C.c_int64, C.c_int, C.c_uint64, C.c_uint32, i32p, i32p,
                                        u64p]
         lib.orc_sim_set_couplings.argtypes = [P, f64p]
+        lib.orc_sim_set_fields.argtypes = [P, f64p]
         lib.orc_walk_returns.argtypes = [C.c_int, i32p, i32p, C.c_int64, i32p, C.c_int32, C.c_uint64, u64p]
         lib.orc_pick_partner_counts.argtypes = [C.c_int, C.c_int, C.c_double, C.c_uint64, i32p, i32p, i32p,
                                                 C.c_int, C.c_int, C.c_int64, i64p]
@@ -303,6 +304,18 @@ class Sim:
             return
         self._jkeep = np.ascontiguousarray(j_per_bond, np.float64)
         if self._lib.orc_sim_set_couplings(self._h, _ptr(self._jkeep, C.c_double)):
+            raise MemoryError("oracle allocation failed")
+
+    def set_fields(self, hxy=None):
+        """Random fields: (n, 2) field vectors per site (original ids); None
+        removes them.  Pinned by the exact single-spin law I1(b|h|)/I0(b|h|)
+        and quadrature over all angles on 2-3-spin graphs."""
+        if hxy is None:
+            self._hkeep = None
+            self._lib.orc_sim_set_fields(self._h, None)
+            return
+        self._hkeep = np.ascontiguousarray(hxy, np.float64).reshape(-1)
+        if self._lib.orc_sim_set_fields(self._h, _ptr(self._hkeep, C.c_double)):
             raise MemoryError("oracle allocation failed")
 
     def sweeps(self, n, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1):

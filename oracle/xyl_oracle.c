@@ -872,6 +872,7 @@ typedef struct {
     double min_margin;        /* smallest Metropolis margin seen */
     double *jb;               /* coupling of each bond, or NULL (all J = 1) */
     double *jn;               /* coupling of each neighbour entry (aligned with nbr), or NULL */
+    double *hx, *hy;          /* field on each site, or NULL */
 } orc_sim;
 
 void orc_sim_free(orc_sim *s)
@@ -881,7 +882,7 @@ void orc_sim_free(orc_sim *s)
     free(s->cx); free(s->sx); free(s->cy); free(s->sy); free(s->beta); free(s->delta);
     free(s->vx); free(s->vy); free(s->slot_of); free(s->rep_at); free(s->E); free(s->acc);
     free(s->met_acc); free(s->met_try); free(s->pt_acc); free(s->pt_try); free(s->first_tie); free(s->n_ties);
-    free(s->jb); free(s->jn);
+    free(s->jb); free(s->jn); free(s->hx); free(s->hy);
     free(s);
 }
 
@@ -976,6 +977,8 @@ static double energy_of(const orc_sim *s, int r)
         if (s->jb) E -= s->jb[e] * (x[i] * x[j] + y[i] * y[j]);
         else E -= x[i] * x[j] + y[i] * y[j];
     }
+    if (s->hx)
+        for (int v = 0; v < s->n; ++v) E -= s->hx[v] * x[v] + s->hy[v] * y[v];
     return E;
 }
 
@@ -1037,7 +1040,32 @@ static void local_field(const orc_sim *s, const double *x, const double *y, int 
             ay += y[s->nbr[a]];
         }
     }
+    if (s->hx) {
+        /* the site's own field, added after the neighbours */
+        ax += s->hx[v];
+        ay += s->hy[v];
+    }
     *hx = ax; *hy = ay;
+}
+
+/*
+ * Random fields (the paper's "random fields" variant, App. B): H gains
+ * -sum_i h_i . S_i with one field vector per site (original ids, hxy[2i],
+ * hxy[2i+1]); the local field becomes sum_j J_ij S_j + h_i and the energy
+ * includes the field term.  NULL removes the fields.  Recomputes the energies.
+ */
+int orc_sim_set_fields(orc_sim *s, const double *hxy)
+{
+    free(s->hx); free(s->hy);
+    s->hx = s->hy = NULL;
+    if (hxy) {
+        s->hx = (double *)malloc(sizeof(double) * (size_t)s->n);
+        s->hy = (double *)malloc(sizeof(double) * (size_t)s->n);
+        if (!s->hx || !s->hy) return -1;
+        for (int v = 0; v < s->n; ++v) { s->hx[v] = hxy[2 * v]; s->hy[v] = hxy[2 * v + 1]; }
+    }
+    refresh_energies(s);
+    return 0;
 }
 
 /*

@@ -33,7 +33,9 @@ XYL_HD Words4 philox4x32_10(Words4 c, uint32_t k0, uint32_t k1)
 {
     const uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
     const uint32_t kWeylA = 0x9E3779B9u, kWeylB = 0xBB67AE85u;
+#if defined(__CUDACC__)
 #pragma unroll
+#endif
     for (int round = 0; round < 10; ++round) {
         const uint32_t hiA = mul_hi32(kMulA, c.w0), loA = kMulA * c.w0;
         const uint32_t hiB = mul_hi32(kMulB, c.w2), loB = kMulB * c.w2;

@@ -60,18 +60,25 @@ def run_bins(sim, n_bins: int, bin_sweeps: int, ops: int, measure_every: int = 1
     return np.array(out)
 
 
-def quadrature_moments(n, edges, beta, M=48, xy=None, L=None, couplings=None):
-    """Exact <e>, <e^2>, <m^2>, <m^4>, <|m|>, <chi(k_min)> for n <= 4 spins.
+def quadrature_moments(n, edges, beta, M=48, xy=None, L=None, couplings=None, fields=None):
+    """Exact <e>, <e^2>, <m^2>, <m^4>, <|m|>, <m_x>, <chi(k_min)> for n <= 4 spins.
 
-    Fix theta_0 = 0 (all quantities are rotation invariant) and integrate the
-    other n-1 angles on an M-point periodic grid."""
+    Without fields fix theta_0 = 0 (all quantities are rotation invariant) and
+    integrate the other n-1 angles on an M-point periodic grid; with fields
+    (n x 2 vectors, energy -sum h_i . S_i) integrate all n angles."""
     grid = 2 * np.pi * np.arange(M) / M - np.pi
-    mesh = np.meshgrid(*([grid] * (n - 1)), indexing="ij")
-    th = [np.zeros_like(mesh[0])] + list(mesh)
-    E = np.zeros_like(mesh[0])
+    if fields is None:
+        mesh = np.meshgrid(*([grid] * (n - 1)), indexing="ij")
+        th = [np.zeros_like(mesh[0])] + list(mesh)
+    else:
+        th = list(np.meshgrid(*([grid] * n), indexing="ij"))
+    E = np.zeros_like(th[0])
     J = [1.0] * len(edges) if couplings is None else list(couplings)
     for (i, j), c in zip(edges, J):
         E -= c * np.cos(th[i] - th[j])
+    if fields is not None:
+        for i in range(n):
+            E -= fields[i][0] * np.cos(th[i]) + fields[i][1] * np.sin(th[i])
     w = np.exp(-beta * (E - E.min()))
     Z = w.sum()
     mx = sum(np.cos(t) for t in th) / n
@@ -84,6 +91,7 @@ def quadrature_moments(n, edges, beta, M=48, xy=None, L=None, couplings=None):
         "m2": (w * m2).sum() / Z,
         "m4": (w * m2 * m2).sum() / Z,
         "absm": (w * np.sqrt(m2)).sum() / Z,
+        "mx": (w * mx).sum() / Z,
     }
     if xy is not None:
         xs = [xy[2 * v] for v in range(n)]
