@@ -160,6 +160,18 @@ int xyl_graph_set_couplings(xyl_graph *g, const int8_t *j);
 /* Couplings of the CSR entries (2*n_edges values aligned with xyl_graph_export_csr's col). */
 int xyl_graph_export_couplings(const xyl_graph *g, int8_t *j_csr);
 
+/*
+ * xyl_graph_set_fields -- random fields: H gains -sum_i h_i . S_i with one
+ * field vector per site (the paper's method applied to "random fields", App.
+ * B).  hxy: 2n values, (h_x, h_y) of each ORIGINAL site id, finite
+ * (XYL_EINVAL otherwise), or NULL to remove the fields.  The local field of a
+ * site becomes sum_j J_ij S_j + h_i (the neighbours summed first) and the
+ * energies include the field term.  Plans made afterwards use the fields; a
+ * plan with fields keeps one FP32 (FP64 for XYL_FP64_PLAIN) vector per site in
+ * its workspace.  Errors: XYL_EINVAL.
+ */
+int xyl_graph_set_fields(xyl_graph *g, const double *hxy);
+
 /* Sizes of a graph; any output pointer may be NULL.  restarts: pairing restarts used. */
 int xyl_graph_info(const xyl_graph *g, int32_t *n, int64_t *n_edges, int32_t *n_colors, int32_t *max_deg,
                    int32_t *restarts);

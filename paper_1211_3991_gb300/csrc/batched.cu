@@ -134,7 +134,7 @@ __device__ __forceinline__ Words4 first_draw(const DevPlan &P, const DevSample &
     return x;
 }
 
-template <bool IS_MET, bool FUSE_E, bool STAGED, int RV, int DEG, bool COUPLED>
+template <bool IS_MET, bool FUSE_E, bool STAGED, int RV, int DEG, bool DISORDER>
 __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, const SharedState &sh,
                                       const BatchedParams &bp, const Staged &stg, int c, uint32_t t, Lane<RV> &ln,
                                       const Words4 &first)
@@ -170,12 +170,12 @@ __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, cons
         float hx[RV], hy[RV], lx[RV], ly[RV];
 #pragma unroll
         for (int v = 0; v < RV; ++v) hx[v] = hy[v] = lx[v] = ly[v] = 0.f;
-        // with COUPLED, a neighbour id with its top bit set is a link with J = -1
+        // with DISORDER, a neighbour id with its top bit set is a link with J = -1
         auto gather = [&](int raw) {
-            const int j = COUPLED ? (raw & 0x7fffffff) : raw;
+            const int j = DISORDER ? (raw & 0x7fffffff) : raw;
             float2 sj[RV];
             load_spins<RV>(sp + j * R, sj);
-            if (COUPLED && raw < 0) {
+            if (DISORDER && raw < 0) {
 #pragma unroll
                 for (int v = 0; v < RV; ++v) sj[v] = make_float2(-sj[v].x, -sj[v].y);
             }
@@ -201,6 +201,19 @@ __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, cons
                 if (k < deg) gather(STAGED ? nb[k] : __ldg(nb + k));
         } else {
             for (int k = 0; k < deg; ++k) gather(STAGED ? nb[k] : __ldg(nb + k));
+        }
+        if (DISORDER && P.field) {
+            // the site's own field after its neighbours; the fused energy takes -h_i . S_i once
+            const float2 f = __ldg(reinterpret_cast<const float2 *>(P.field) + d.site_off + i);
+#pragma unroll
+            for (int v = 0; v < RV; ++v) {
+                hx[v] += f.x;
+                hy[v] += f.y;
+                if (FUSE_E) {
+                    lx[v] += f.x;
+                    ly[v] += f.y;
+                }
+            }
         }
         float2 n[RV];
         if (IS_MET) {
@@ -280,7 +293,7 @@ __device__ __forceinline__ void measure_own_sites(const DevPlan &P, const DevSam
         for (int f = 1; f < kSums; ++f) warp_part(sh, bp, lane_rep, v, f, m[v][f - 1]);
 }
 
-template <bool STAGED, int RV, int DEG, bool COUPLED>
+template <bool STAGED, int RV, int DEG, bool DISORDER>
 __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams &bp, SharedState &sh,
                                            const Staged &stg, cg::cluster_group &cluster, int s, int group,
                                            int rank)
@@ -310,8 +323,8 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
             // the next phase's first Philox block is drawn while the cluster
             // barrier of the previous phase completes
             for (int c = 0; c < d.Q; ++c) {
-                if (orx) phase<true, false, STAGED, RV, DEG, COUPLED>(P, d, sh, bp, stg, c, t, ln, first);
-                else phase<true, true, STAGED, RV, DEG, COUPLED>(P, d, sh, bp, stg, c, t, ln, first);
+                if (orx) phase<true, false, STAGED, RV, DEG, DISORDER>(P, d, sh, bp, stg, c, t, ln, first);
+                else phase<true, true, STAGED, RV, DEG, DISORDER>(P, d, sh, bp, stg, c, t, ln, first);
                 if (orx || c + 1 < d.Q) {
                     cluster_arrive();
                     if (c + 1 < d.Q) first = first_draw<STAGED>(P, d, sh, bp, stg, c + 1, t, ln.r0);
@@ -322,7 +335,7 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
         if (orx) {
             const Words4 none{0u, 0u, 0u, 0u};
             for (int c = 0; c < d.Q; ++c) {
-                phase<false, true, STAGED, RV, DEG, COUPLED>(P, d, sh, bp, stg, c, t, ln, none);
+                phase<false, true, STAGED, RV, DEG, DISORDER>(P, d, sh, bp, stg, c, t, ln, none);
                 if (c + 1 < d.Q) cluster.sync();
             }
         }
@@ -392,7 +405,7 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
     if (leader && threadIdx.x == 0) P.sweep[s] = t;
 }
 
-template <bool STAGED, int RV, int DEG, bool COUPLED>
+template <bool STAGED, int RV, int DEG, bool DISORDER>
 __global__ void __maxnreg__(96) batched_kernel(DevPlan P, BatchedParams bp)
 {
     __shared__ SharedState sh;
@@ -447,30 +460,30 @@ __global__ void __maxnreg__(96) batched_kernel(DevPlan P, BatchedParams bp)
         stg = Staged{col, deg, site};
         __syncthreads();
     }
-    run_sweeps<STAGED, RV, DEG, COUPLED>(P, bp, sh, stg, cluster, s, group, rank);
+    run_sweeps<STAGED, RV, DEG, DISORDER>(P, bp, sh, stg, cluster, s, group, rank);
 }
 
 using KernelFn = void (*)(DevPlan, BatchedParams);
 
 // The specialisation for a launch shape: CSR staged or not, one or two
-// replicas per thread, fixed degree 6 / at most 8 / any degree, couplings.
-template <bool STAGED, int RV, bool COUPLED>
+// replicas per thread, fixed degree 6 / at most 8 / any degree, random bonds or fields.
+template <bool STAGED, int RV, bool DISORDER>
 KernelFn pick_deg(const BatchedShape &B)
 {
-    if (B.fixed_deg == 6) return batched_kernel<STAGED, RV, 6, COUPLED>;
-    if (B.max_deg <= 8) return batched_kernel<STAGED, RV, -8, COUPLED>;
-    return batched_kernel<STAGED, RV, 0, COUPLED>;
+    if (B.fixed_deg == 6) return batched_kernel<STAGED, RV, 6, DISORDER>;
+    if (B.max_deg <= 8) return batched_kernel<STAGED, RV, -8, DISORDER>;
+    return batched_kernel<STAGED, RV, 0, DISORDER>;
 }
 
-template <bool COUPLED>
-KernelFn pick_kernel_c(const BatchedShape &B)
+template <bool DISORDER>
+KernelFn pick_kernel_d(const BatchedShape &B)
 {
     const bool rv2 = B.Rg >= 2;
-    if (B.staged) return rv2 ? pick_deg<true, 2, COUPLED>(B) : pick_deg<true, 1, COUPLED>(B);
-    return rv2 ? pick_deg<false, 2, COUPLED>(B) : pick_deg<false, 1, COUPLED>(B);
+    if (B.staged) return rv2 ? pick_deg<true, 2, DISORDER>(B) : pick_deg<true, 1, DISORDER>(B);
+    return rv2 ? pick_deg<false, 2, DISORDER>(B) : pick_deg<false, 1, DISORDER>(B);
 }
 
-KernelFn pick_kernel(const BatchedShape &B) { return B.coupled ? pick_kernel_c<true>(B) : pick_kernel_c<false>(B); }
+KernelFn pick_kernel(const BatchedShape &B) { return B.disorder ? pick_kernel_d<true>(B) : pick_kernel_d<false>(B); }
 
 // Function-wide attributes, the same for every plan: clusters up to 16 CTAs and
 // dynamic shared memory up to the staging ceiling (a launch asks for less).

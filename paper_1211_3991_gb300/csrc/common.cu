@@ -201,6 +201,16 @@ __global__ void recompute_kernel(DevPlan P, int layout, int fp64, int renormalis
             if (raw < 0) { vx = -vx; vy = -vy; }
             lx += vx; ly += vy;
         }
+        if (P.field) {
+            // random fields: -h_i . S_i once per site
+            if (fp64) {
+                const double2 f = reinterpret_cast<const double2 *>(P.field)[d.site_off + i];
+                lx += f.x; ly += f.y;
+            } else {
+                const float2 f = reinterpret_cast<const float2 *>(P.field)[d.site_off + i];
+                lx += f.x; ly += f.y;
+            }
+        }
         acc[kObsE] -= sx * lx + sy * ly;
         acc[kObsMx] += sx;
         acc[kObsMy] += sy;

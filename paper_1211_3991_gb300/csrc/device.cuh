@@ -62,6 +62,7 @@ struct DevPlan {
     unsigned int *barrier;     // per sample arrival counters (batched engine)
     double *drift;             // largest |E_fused - E_fp64| seen by a recompute
     const uint16_t *push;      // per site: CTAs of its group (bit = rank) that read it (site-split resident shape)
+    const void *field;         // per site (colour-sorted, site_off): field vector float2 / double2, or NULL
     uint64_t key;              // Philox key of the spin streams
     // Maclaurin coefficients (-1)^k / (2k+1)! and (-1)^k / (2k)! of the FP64 sin/cos
     double sin_coef[kSinTerms];

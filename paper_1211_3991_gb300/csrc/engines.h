@@ -17,7 +17,9 @@ struct PlanShape {
     int max_N = 0;
     int layout = kReplicaMajor;
     bool fp64 = false;
-    bool coupled = false;   // some link has J = -1: neighbour ids carry J in bit 31 (kernels' COUPLED variants)
+    bool coupled = false;   // some link has J = -1: neighbour ids carry J in bit 31
+    bool fields = false;    // sites carry a field vector (DevPlan::field)
+    bool disorder = false;  // coupled || fields: the kernels' DISORDER variants run
 };
 
 // Batched-engine launch shape chosen by the tuner.
@@ -29,7 +31,7 @@ struct BatchedShape {
     int owned_max = 0;      // largest number of sites one CTA owns
     int max_deg = 0;
     int fixed_deg = 0;      // degree shared by every site of every sample, 0 if degrees differ
-    bool coupled = false;   // random bonds (see PlanShape)
+    bool disorder = false;  // random bonds or fields (see PlanShape)
     size_t smem_bytes = 0;  // dynamic shared memory per CTA
     // resident shape: one CTA per replica group holds the group's spins of
     // every site in shared memory; the groups of a sample form one cluster

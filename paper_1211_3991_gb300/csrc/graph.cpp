@@ -563,6 +563,21 @@ int xyl_graph_set_couplings(xyl_graph *g, const int8_t *j)
     return XYL_OK;
 }
 
+int xyl_graph_set_fields(xyl_graph *g, const double *hxy)
+{
+    clear_error();
+    if (!g) return fail(XYL_EINVAL, "xyl_graph_set_fields: NULL graph");
+    if (!hxy) {
+        g->field.clear();
+        return XYL_OK;
+    }
+    for (int64_t k = 0; k < 2 * (int64_t)g->n; ++k)
+        if (!std::isfinite(hxy[k])) return fail(XYL_EINVAL, "xyl_graph_set_fields: component %lld is not finite",
+                                                (long long)k);
+    g->field.assign(hxy, hxy + 2 * (size_t)g->n);
+    return XYL_OK;
+}
+
 int xyl_graph_export_couplings(const xyl_graph *g, int8_t *j_csr)
 {
     if (!g || !j_csr) return fail(XYL_EINVAL, "xyl_graph_export_couplings: NULL argument");

@@ -35,4 +35,5 @@ struct xyl_graph {
     std::vector<int32_t> color;       // colour of each original id
     std::vector<int8_t> jlink;        // coupling of each link (creation order), empty = all +1
     std::vector<int8_t> jcsr;         // coupling of each CSR entry (aligned with col), empty = all +1
+    std::vector<double> field;        // 2n field components per original id, empty = no field
 };

@@ -21,9 +21,10 @@ template <> __device__ __forceinline__ double2 make_vec2<double>(double x, doubl
 // One colour phase of the Metropolis (IS_MET) or overrelaxation pass.  With
 // FUSE the replica's energy (links to lower colours, counted at their upper
 // endpoint), magnetisation and Fourier sums are reduced into obs[0].  With
-// COUPLED a neighbour id with its top bit set is a link with J = -1: the
-// neighbour's spin enters the local field negated (exactly J * S_j).
-template <typename Real, bool IS_MET, bool FUSE, bool COUPLED>
+// DISORDER a neighbour id with its top bit set is a link with J = -1 (the
+// neighbour's spin enters the local field negated, exactly J * S_j), and a
+// site field, when the plan has one, is added after the neighbours.
+template <typename Real, bool IS_MET, bool FUSE, bool DISORDER>
 __global__ void __launch_bounds__(kPlainBlock) plain_phase_kernel(DevPlan P, int c)
 {
     using V = Vec2<Real>;
@@ -49,9 +50,9 @@ __global__ void __launch_bounds__(kPlainBlock) plain_phase_kernel(DevPlan P, int
         const int rb = rp[i], re = rp[i + 1];
         for (int k = rb; k < re; ++k) {
             const int raw = cl[k];
-            const int j = COUPLED ? (raw & 0x7fffffff) : raw;
+            const int j = DISORDER ? (raw & 0x7fffffff) : raw;
             V sj = sp[j];
-            if (COUPLED && raw < 0) {
+            if (DISORDER && raw < 0) {
                 sj.x = -sj.x;
                 sj.y = -sj.y;
             }
@@ -60,6 +61,16 @@ __global__ void __launch_bounds__(kPlainBlock) plain_phase_kernel(DevPlan P, int
             if (FUSE && j < cb) {
                 lx += sj.x;
                 ly += sj.y;
+            }
+        }
+        if (DISORDER && P.field) {
+            // the site's own field after its neighbours; the fused energy takes -h_i . S_i once
+            const V f = reinterpret_cast<const V *>(P.field)[d.site_off + i];
+            hx += f.x;
+            hy += f.y;
+            if (FUSE) {
+                lx += f.x;
+                ly += f.y;
             }
         }
         if (IS_MET) {
@@ -118,7 +129,7 @@ __global__ void __launch_bounds__(kPlainBlock) plain_phase_kernel(DevPlan P, int
     }
 }
 
-template <typename Real, bool COUPLED>
+template <typename Real, bool DISORDER>
 cudaError_t sweep_impl(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every, cudaStream_t st,
                        int64_t *launches)
 {
@@ -128,15 +139,15 @@ cudaError_t sweep_impl(const DevPlan &P, const PlanShape &S, uint32_t ops, int m
     if (met) {
         for (int c = 0; c < S.max_Q; ++c) {
             if (orx)
-                plain_phase_kernel<Real, true, false, COUPLED><<<grid, kPlainBlock, 0, st>>>(P, c);
+                plain_phase_kernel<Real, true, false, DISORDER><<<grid, kPlainBlock, 0, st>>>(P, c);
             else
-                plain_phase_kernel<Real, true, true, COUPLED><<<grid, kPlainBlock, 0, st>>>(P, c);
+                plain_phase_kernel<Real, true, true, DISORDER><<<grid, kPlainBlock, 0, st>>>(P, c);
             ++n;
         }
     }
     if (orx) {
         for (int c = 0; c < S.max_Q; ++c) {
-            plain_phase_kernel<Real, false, true, COUPLED><<<grid, kPlainBlock, 0, st>>>(P, c);
+            plain_phase_kernel<Real, false, true, DISORDER><<<grid, kPlainBlock, 0, st>>>(P, c);
             ++n;
         }
     }
@@ -153,7 +164,7 @@ cudaError_t sweep_impl(const DevPlan &P, const PlanShape &S, uint32_t ops, int m
 cudaError_t launch_plain_sweep(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every,
                                cudaStream_t st, int64_t *launches)
 {
-    if (S.coupled)
+    if (S.disorder)
         return S.fp64 ? sweep_impl<double, true>(P, S, ops, measure_every, st, launches)
                       : sweep_impl<float, true>(P, S, ops, measure_every, st, launches);
     return S.fp64 ? sweep_impl<double, false>(P, S, ops, measure_every, st, launches)

@@ -22,6 +22,7 @@ struct HostSample {
     std::vector<double> beta, delta;
     std::vector<int32_t> perm, row_ptr, col, color_ptr, xy;
     std::vector<int8_t> jcsr;  // couplings of the CSR entries, empty = all +1
+    std::vector<double> field; // 2N field components per original id, empty = no field
 };
 
 struct Region {
@@ -57,7 +58,7 @@ struct xyl_plan {
     DevPlan dev{};
     Region r_samples, r_row_ptr, r_col, r_perm, r_color_ptr, r_phase, r_spins, r_beta, r_delta, r_slot_of, r_rep_at,
         r_obs, r_last_E, r_acc, r_met_acc, r_met_try, r_pt_acc, r_pt_try, r_sweep, r_status, r_barrier, r_drift,
-        r_units, r_push;
+        r_units, r_push, r_field;
     cudaStream_t capture_stream = nullptr;
     std::map<std::tuple<int, uint32_t, int>, cudaGraphExec_t> graphs;
     int64_t last_launches = 0;
@@ -125,6 +126,8 @@ void layout(xyl_plan *p)
     take(p->r_drift, sizeof(double));
     take(p->r_units, std::max<size_t>(p->total_R, 1) * sizeof(int2));  // the most units any shape makes
     take(p->r_push, p->total_N * sizeof(uint16_t));
+    // random fields: one vector per site, only when some sample has them
+    take(p->r_field, p->shape.fields ? p->total_N * (p->shape.fp64 ? sizeof(double2) : sizeof(float2)) : 0);
     p->ws_bytes = off;
 }
 
@@ -223,7 +226,7 @@ int apply_shape(xyl_plan *p, int g, int G, int block, int stage, int resident)
     B.G = G;
     B.Rg = g;
     B.block = block;
-    B.coupled = p->shape.coupled;
+    B.disorder = p->shape.disorder;
     int max_deg = 1;
     for (auto &h : p->hs) max_deg = std::max(max_deg, h.max_deg);
     B.max_deg = max_deg;
@@ -434,6 +437,8 @@ int xyl_plan_create(const xyl_sample *samples, int32_t n_samples, int32_t engine
         h.perm = g->perm; h.row_ptr = g->row_ptr; h.col = g->col; h.color_ptr = g->color_ptr; h.xy = g->xy;
         h.jcsr = g->jcsr;
         for (int8_t j : h.jcsr) p->shape.coupled |= (j < 0);
+        h.field = g->field;
+        p->shape.fields |= !h.field.empty();
         p->total_R += h.R;
         p->total_N += h.N;
         p->total_nnz += (int64_t)h.col.size();
@@ -447,6 +452,7 @@ int xyl_plan_create(const xyl_sample *samples, int32_t n_samples, int32_t engine
         p->hs.push_back(std::move(h));
     }
     p->shape.n_samples = n_samples;
+    p->shape.disorder = p->shape.coupled || p->shape.fields;
     if (engine == XYL_FP32_BATCHED) {
         const int rc = pick_batched_shape(p, tune);
         if (rc) { delete p; return rc; }
@@ -518,6 +524,21 @@ int xyl_bind(xyl_plan *p, void *d_workspace, size_t bytes, void *stream)
     else
         XYL_CUDA(up(p->r_phase, ph32.data(), ph32.size() * sizeof(float4)), "xyl_bind: upload");
     XYL_CUDA(up(p->r_beta, beta.data(), beta.size() * 8), "xyl_bind: upload");
+    if (p->shape.fields) {
+        // field of each site in colour-sorted order (zero for samples without fields)
+        std::vector<double> f64;
+        std::vector<float> f32;
+        for (const HostSample &h : p->hs)
+            for (int i = 0; i < h.N; ++i) {
+                const int v = h.perm[i];
+                const double fx = h.field.empty() ? 0.0 : h.field[2 * (size_t)v];
+                const double fy = h.field.empty() ? 0.0 : h.field[2 * (size_t)v + 1];
+                if (p->shape.fp64) { f64.push_back(fx); f64.push_back(fy); }
+                else { f32.push_back((float)fx); f32.push_back((float)fy); }
+            }
+        if (p->shape.fp64) XYL_CUDA(up(p->r_field, f64.data(), f64.size() * 8), "xyl_bind: upload");
+        else XYL_CUDA(up(p->r_field, f32.data(), f32.size() * 4), "xyl_bind: upload");
+    }
     XYL_CUDA(up(p->r_delta, delta.data(), delta.size() * 8), "xyl_bind: upload");
     // everything mutable starts zeroed
     const Region *zero[] = {&p->r_spins, &p->r_slot_of, &p->r_rep_at, &p->r_obs, &p->r_last_E, &p->r_acc,
@@ -533,6 +554,7 @@ int xyl_bind(xyl_plan *p, void *d_workspace, size_t bytes, void *stream)
     P.perm = at<int32_t>(p, p->r_perm);
     P.color_ptr = at<int32_t>(p, p->r_color_ptr);
     P.phase = p->ws + p->r_phase.off;
+    P.field = p->shape.fields ? p->ws + p->r_field.off : nullptr;
     P.spins = p->ws + p->r_spins.off;
     P.beta = at<double>(p, p->r_beta);
     P.delta = at<double>(p, p->r_delta);

@@ -81,14 +81,14 @@ struct Row {
 };
 
 struct Stage {
-    const uint16_t *col;    // [owned][csr_w] colour-sorted ids, padding -> N (a zero spin); J = -1 in bit 15 (COUPLED)
+    const uint16_t *col;    // [owned][csr_w] colour-sorted ids, padding -> N (a zero spin); J = -1 in bit 15 (DISORDER)
     const uint16_t *ids;    // [owned] original ids
     const uint16_t *peers;  // [owned] peer masks (site split)
 };
 
-// i: colour-sorted site id; l: its staged row.  With COUPLED the sign of each
+// i: colour-sorted site id; l: its staged row.  With DISORDER the sign of each
 // link comes from bit 15 of a staged id or bit 31 of a global one.
-template <int DEG, bool IS_MET, bool SPLIT, bool COUPLED>
+template <int DEG, bool IS_MET, bool SPLIT, bool DISORDER>
 __device__ __forceinline__ void fetch_row(const DevPlan &P, const DevSample &d, const Stage &stg, int i, int l,
                                           Row<DEG> &row)
 {
@@ -100,7 +100,7 @@ __device__ __forceinline__ void fetch_row(const DevPlan &P, const DevSample &d, 
 #pragma unroll
         for (int k = 0; k < W / 2; ++k) {
             const uint32_t w = c[k];
-            if (COUPLED) {
+            if (DISORDER) {
                 row.nb[2 * k] = (int)(w & 0x7fffu);
                 row.nb[2 * k + 1] = (int)((w >> 16) & 0x7fffu);
                 row.neg |= ((w >> 15) & 1u) << (2 * k) | ((w >> 31) & 1u) << (2 * k + 1);
@@ -121,7 +121,7 @@ __device__ __forceinline__ void fetch_row(const DevPlan &P, const DevSample &d, 
         }
 #pragma unroll
         for (int k = 0; k < W; ++k) row.nb[k] = (DEG > 0 || k < deg) ? __ldg(cl + rb + k) : d.N;
-        if (COUPLED) {
+        if (DISORDER) {
 #pragma unroll
             for (int k = 0; k < W; ++k) {
                 row.neg |= (row.nb[k] < 0 ? 1u : 0u) << k;
@@ -198,7 +198,7 @@ __device__ __forceinline__ void put_spins(cg::cluster_group &cluster, const Resi
 // One colour phase over this CTA's chunk of colour c for its replicas: one
 // thread per (site, block of RV consecutive replicas).  sp points at the
 // group's spins in shared memory.
-template <bool IS_MET, bool FUSE_E, int RV, int DEG, bool SPLIT, bool COUPLED>
+template <bool IS_MET, bool FUSE_E, int RV, int DEG, bool SPLIT, bool DISORDER>
 __device__ __forceinline__ void rphase(const DevPlan &P, const DevSample &d, const ResidentShared &sh,
                                        const ResidentParams &rp, const Stage &stg, cg::cluster_group &cluster,
                                        const Place &pl, float2 *sp, int c, uint32_t t, RLane<RV> &ln)
@@ -211,13 +211,13 @@ __device__ __forceinline__ void rphase(const DevPlan &P, const DevSample &d, con
     int q = threadIdx.x;
     if (q >= items) return;
     Row<DEG> cur;
-    fetch_row<DEG, IS_MET, SPLIT, COUPLED>(P, d, stg, lo + (q >> rp.log2lps), base + (q >> rp.log2lps), cur);
+    fetch_row<DEG, IS_MET, SPLIT, DISORDER>(P, d, stg, lo + (q >> rp.log2lps), base + (q >> rp.log2lps), cur);
     for (; q < items; q += blockDim.x) {
         const int i = lo + (q >> rp.log2lps);
         Row<DEG> nxt;
         const int qn = q + (int)blockDim.x;
         if (qn < items)
-            fetch_row<DEG, IS_MET, SPLIT, COUPLED>(P, d, stg, lo + (qn >> rp.log2lps), base + (qn >> rp.log2lps), nxt);
+            fetch_row<DEG, IS_MET, SPLIT, DISORDER>(P, d, stg, lo + (qn >> rp.log2lps), base + (qn >> rp.log2lps), nxt);
         float2 s[RV];
         lds_spins<RV>(spl + i * Rg, s);
         float hx[RV], hy[RV], lx[RV], ly[RV];
@@ -228,7 +228,7 @@ __device__ __forceinline__ void rphase(const DevPlan &P, const DevSample &d, con
             const int j = cur.nb[k];
             float2 sj[RV];
             lds_spins<RV>(spl + j * Rg, sj);
-            if (COUPLED && ((cur.neg >> k) & 1u)) {
+            if (DISORDER && ((cur.neg >> k) & 1u)) {
 #pragma unroll
                 for (int v = 0; v < RV; ++v) sj[v] = make_float2(-sj[v].x, -sj[v].y);
             }
@@ -240,6 +240,19 @@ __device__ __forceinline__ void rphase(const DevPlan &P, const DevSample &d, con
                 if (lower) {
                     lx[v] += sj[v].x;
                     ly[v] += sj[v].y;
+                }
+            }
+        }
+        if (DISORDER && P.field) {
+            // the site's own field after its neighbours; the fused energy takes -h_i . S_i once
+            const float2 f = __ldg(reinterpret_cast<const float2 *>(P.field) + d.site_off + i);
+#pragma unroll
+            for (int v = 0; v < RV; ++v) {
+                hx[v] += f.x;
+                hy[v] += f.y;
+                if (FUSE_E) {
+                    lx[v] += f.x;
+                    ly[v] += f.y;
                 }
             }
         }
@@ -297,7 +310,7 @@ __device__ __forceinline__ unsigned warp_reduce_rep(const ResidentParams &rp, un
     return x;
 }
 
-template <int RV, int DEG, bool SPLIT, bool COUPLED>
+template <int RV, int DEG, bool SPLIT, bool DISORDER>
 __device__ __forceinline__ void resident_sweeps(const DevPlan &P, const ResidentParams &rp, ResidentShared &sh,
                                                 const Stage &stg, cg::cluster_group &cluster, const Place &pl,
                                                 float2 *sp, float *part, unsigned *part_met, int s, int group)
@@ -328,14 +341,14 @@ __device__ __forceinline__ void resident_sweeps(const DevPlan &P, const Resident
         }
         if (met) {
             for (int c = 0; c < d.Q; ++c) {
-                if (orx) rphase<true, false, RV, DEG, SPLIT, COUPLED>(P, d, sh, rp, stg, cluster, pl, sp, c, t, ln);
-                else rphase<true, true, RV, DEG, SPLIT, COUPLED>(P, d, sh, rp, stg, cluster, pl, sp, c, t, ln);
+                if (orx) rphase<true, false, RV, DEG, SPLIT, DISORDER>(P, d, sh, rp, stg, cluster, pl, sp, c, t, ln);
+                else rphase<true, true, RV, DEG, SPLIT, DISORDER>(P, d, sh, rp, stg, cluster, pl, sp, c, t, ln);
                 phase_barrier<SPLIT>();
             }
         }
         if (orx) {
             for (int c = 0; c < d.Q; ++c) {
-                rphase<false, true, RV, DEG, SPLIT, COUPLED>(P, d, sh, rp, stg, cluster, pl, sp, c, t, ln);
+                rphase<false, true, RV, DEG, SPLIT, DISORDER>(P, d, sh, rp, stg, cluster, pl, sp, c, t, ln);
                 phase_barrier<SPLIT>();
             }
         }
@@ -446,7 +459,7 @@ __device__ __forceinline__ void resident_sweeps(const DevPlan &P, const Resident
     if (leader && threadIdx.x == 0) P.sweep[s] = t;
 }
 
-template <int RV, int DEG, bool SPLIT, bool COUPLED>
+template <int RV, int DEG, bool SPLIT, bool DISORDER>
 __device__ __forceinline__ void resident_body(const DevPlan &P, const ResidentParams &rp)
 {
     __shared__ ResidentShared sh;
@@ -511,8 +524,8 @@ __device__ __forceinline__ void resident_body(const DevPlan &P, const ResidentPa
                     const int rb = P.row_ptr[d.row_off + i], re = P.row_ptr[d.row_off + i + 1];
                     for (int k = 0; k < W; ++k) {
                         const int raw = k < re - rb ? P.col[d.col_off + rb + k] : N;
-                        // with couplings the id keeps 15 bits and bit 15 holds J = -1
-                        col[(size_t)l * W + k] = COUPLED ? (uint16_t)((raw & 0x7fff) | (raw < 0 ? 0x8000 : 0))
+                        // with random bonds the id keeps 15 bits and bit 15 holds J = -1
+                        col[(size_t)l * W + k] = DISORDER ? (uint16_t)((raw & 0x7fff) | (raw < 0 ? 0x8000 : 0))
                                                          : (uint16_t)raw;
                     }
                 }
@@ -527,7 +540,7 @@ __device__ __forceinline__ void resident_body(const DevPlan &P, const ResidentPa
     // peers write into this CTA's copy only after it holds the starting spins
     if (SPLIT) cluster.sync();
     else __syncthreads();
-    resident_sweeps<RV, DEG, SPLIT, COUPLED>(P, rp, sh, stg, cluster, pl, sp, part, part_met, s, group);
+    resident_sweeps<RV, DEG, SPLIT, DISORDER>(P, rp, sh, stg, cluster, pl, sp, part, part_met, s, group);
     // write this CTA's own sites back (every copy agrees after the last barrier)
     float2 *gspw = reinterpret_cast<float2 *>(P.spins) + d.spin_off + group * Rg;
     for (int c = 0; c < d.Q; ++c) {
@@ -540,38 +553,38 @@ __device__ __forceinline__ void resident_body(const DevPlan &P, const ResidentPa
 }
 
 // Up to 672 threads with 96 registers each, or up to 1024 with 64.
-template <int RV, int DEG, bool SPLIT, bool COUPLED>
+template <int RV, int DEG, bool SPLIT, bool DISORDER>
 __global__ void __maxnreg__(96) resident_kernel(DevPlan P, ResidentParams rp)
 {
-    resident_body<RV, DEG, SPLIT, COUPLED>(P, rp);
+    resident_body<RV, DEG, SPLIT, DISORDER>(P, rp);
 }
 
-template <int RV, int DEG, bool SPLIT, bool COUPLED>
+template <int RV, int DEG, bool SPLIT, bool DISORDER>
 __global__ void __launch_bounds__(1024, 1) resident_kernel_wide(DevPlan P, ResidentParams rp)
 {
-    resident_body<RV, DEG, SPLIT, COUPLED>(P, rp);
+    resident_body<RV, DEG, SPLIT, DISORDER>(P, rp);
 }
 
 using KernelFn = void (*)(DevPlan, ResidentParams);
 
-template <int RV, int DEG, bool SPLIT, bool COUPLED>
+template <int RV, int DEG, bool SPLIT, bool DISORDER>
 KernelFn pick_width(const BatchedShape &B)
 {
-    return B.block > kResidentNarrowMaxThreads ? resident_kernel_wide<RV, DEG, SPLIT, COUPLED>
-                                               : resident_kernel<RV, DEG, SPLIT, COUPLED>;
+    return B.block > kResidentNarrowMaxThreads ? resident_kernel_wide<RV, DEG, SPLIT, DISORDER>
+                                               : resident_kernel<RV, DEG, SPLIT, DISORDER>;
 }
 
-template <bool SPLIT, bool COUPLED>
+template <bool SPLIT, bool DISORDER>
 KernelFn pick_split(const BatchedShape &B)
 {
     const bool rv2 = B.Rg >= 2;
-    if (B.fixed_deg == 6) return rv2 ? pick_width<2, 6, SPLIT, COUPLED>(B) : pick_width<1, 6, SPLIT, COUPLED>(B);
-    return rv2 ? pick_width<2, -8, SPLIT, COUPLED>(B) : pick_width<1, -8, SPLIT, COUPLED>(B);
+    if (B.fixed_deg == 6) return rv2 ? pick_width<2, 6, SPLIT, DISORDER>(B) : pick_width<1, 6, SPLIT, DISORDER>(B);
+    return rv2 ? pick_width<2, -8, SPLIT, DISORDER>(B) : pick_width<1, -8, SPLIT, DISORDER>(B);
 }
 
 KernelFn pick_resident(const BatchedShape &B)
 {
-    if (B.coupled) return B.G > 1 ? pick_split<true, true>(B) : pick_split<false, true>(B);
+    if (B.disorder) return B.G > 1 ? pick_split<true, true>(B) : pick_split<false, true>(B);
     return B.G > 1 ? pick_split<true, false>(B) : pick_split<false, false>(B);
 }
 

@@ -23,6 +23,8 @@ with J = +-1 at random (probability 1/2 each, the XY spin glass):
 
   G1  L=16, rho=3.5, 4 temperatures geometric in [0.4, 1.0]
   G2  L=128, rho=3.5, 16 temperatures geometric in [0.3, 1.2]
+  H1  G1 with random fields of magnitude 0.5 (uniform random directions)
+  H2  G2 with random fields of magnitude 0.5
 """
 from __future__ import annotations
 
@@ -53,6 +55,7 @@ class Config:
     ensemble: str = "fixed"   # "fixed": every site Z links; "bonds": 2N bonds in all (Sec. II)
     boundary: str = "pbc"     # "bonds" ensemble: "pbc" or "fbc"
     couplings: str = "ferro"  # "ferro": J = 1; "pm": random signs, J = -1 with probability 1/2 (spin glass)
+    field: float = 0.0        # magnitude of a random field on every site (uniform random direction), 0 = none
 
     @property
     def n_samples(self):
@@ -106,6 +109,12 @@ def config(name: str) -> Config:
     if name == "G1":
         return Config("G1", [(16, 3.5, 0)], geometric_temperatures(0.4, 1.0, 4), couplings="pm",
                       description="C1's graph with random +-1 couplings, 4 T geometric in [0.4,1.0]")
+    if name == "H1":
+        return Config("H1", [(16, 3.5, 0)], geometric_temperatures(0.4, 1.0, 4), couplings="pm", field=0.5,
+                      description="C1's graph, random +-1 couplings and random fields of magnitude 0.5, 4 T")
+    if name == "H2":
+        return Config("H2", [(128, 3.5, 0)], geometric_temperatures(0.3, 1.2, 16), couplings="pm", field=0.5,
+                      description="C2's graph, random +-1 couplings and random fields of magnitude 0.5, 16 T")
     if name == "B64":
         return Config("B64", [(64, 10.0 / 3.0, s) for s in range(64)], geometric_temperatures(1.4, 2.0, 12),
                       ensemble="bonds", description="64 graphs L=64 2N bonds rho=10/3 periodic, 12 T geometric in [1.4,2.0]")
@@ -153,6 +162,9 @@ def build_graphs(cfg: Config, threads: int = 0):
         j = couplings_for(cfg, k, g.n_edges)
         if j is not None:
             g.set_couplings(j)
+        h = fields_for(cfg, k, g.n)
+        if h is not None:
+            g.set_fields(h)
     return graphs
 
 
@@ -167,6 +179,16 @@ def couplings_for(cfg: Config, k: int, n_edges: int):
     import numpy as np
     rng = np.random.default_rng([COUPLING_SEED, graph_stream_id(cfg, k)])
     return np.where(rng.random(n_edges) < 0.5, -1, 1).astype(np.int8)
+
+
+def fields_for(cfg: Config, k: int, n: int):
+    """Random fields of sample k ((n, 2) vectors of magnitude cfg.field in
+    uniformly random directions), or None.  Seeded by the sample's stream id."""
+    if cfg.field == 0.0:
+        return None
+    import numpy as np
+    phi = np.random.default_rng([COUPLING_SEED + 1, graph_stream_id(cfg, k)]).random(n) * 2.0 * np.pi
+    return cfg.field * np.stack([np.cos(phi), np.sin(phi)], 1)
 
 
 def graph_stream_id(cfg: Config, k: int) -> int:

@@ -29,7 +29,7 @@ EXPORTED = (
     "xyl_write_spins", "xyl_read_status", "xyl_state_bytes", "xyl_export_state", "xyl_import_state",
     "xyl_last_launch_count", "xyl_plan_free", "xyl_sweep_units", "xyl_unit_count", "xyl_autotune",
     "xyl_get_tuning", "xyl_sweep_noalloc", "xyl_build_levy_bonds", "xyl_walk_returns", "xyl_graph_set_couplings",
-    "xyl_graph_export_couplings",
+    "xyl_graph_export_couplings", "xyl_graph_set_fields",
 )
 
 
@@ -104,6 +104,7 @@ def load():
             "xyl_walk_returns": ([P, P, i32, i64, P, i64, u32, i32, u64, P, P], C.c_int),
             "xyl_graph_set_couplings": ([P, C.POINTER(C.c_int8)], C.c_int),
             "xyl_graph_export_couplings": ([P, C.POINTER(C.c_int8)], C.c_int),
+            "xyl_graph_set_fields": ([P, pf64], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -174,6 +175,17 @@ class Graph:
         if len(j) != self.n_edges:
             raise ValueError("one coupling per link")
         _check(load().xyl_graph_set_couplings(self.handle, _p(j, C.c_int8)))
+        return self
+
+    def set_fields(self, hxy=None):
+        """Random fields: (n, 2) field vectors per original site id; None removes them."""
+        if hxy is None:
+            _check(load().xyl_graph_set_fields(self.handle, None))
+            return self
+        h = np.ascontiguousarray(hxy, np.float64).reshape(-1)
+        if len(h) != 2 * self.n:
+            raise ValueError("one field vector per site")
+        _check(load().xyl_graph_set_fields(self.handle, _p(h, C.c_double)))
         return self
 
     def couplings(self):

@@ -1,10 +1,12 @@
-"""Random bonds on the GPU (H = -sum J_ij S_i.S_j, J = +-1; App. B's random-bond
-variant) against the oracle, and exact gauge invariance of every engine.
+"""Random bonds and fields on the GPU (H = -sum J_ij S_i.S_j - sum h_i.S_i,
+J = +-1; App. B's random-bond and random-field variants) against the oracle,
+and exact gauge invariance of every engine.
 
 * FP64 engine vs oracle: angles within 1e-9 rad over 10 sweeps (G1, G2).
 * FP32 engines vs oracle: energy per spin within 1e-5 per sweep from a shared
   state (near-tie decisions excepted, as for the ferromagnet).
-* Gauge invariance: couplings tau_i tau_j J_ij with spins tau_i S_i describe the
+* Gauge invariance: couplings tau_i tau_j J_ij and fields tau_i h_i with spins
+  tau_i S_i describe the
   same system; the kernels' update arithmetic maps term by term under S -> -S,
   so the gauged run is the negated run bit for bit, labels equal and energies
   equal up to the order of FP64 atomic additions.
@@ -36,12 +38,15 @@ def _oracle(orc, wl, cfg, k, u24, tie_eps=0.0):
     sim = orc.Sim(L * L, ei, ej, color, cfg.betas(), cfg.deltas(), wl.SPIN_SEED, sample=wl.graph_stream_id(cfg, k),
                   xy=orc.lattice_xy(L), L=L, u24=u24)
     sim.set_couplings(wl.couplings_for(cfg, k, len(ei)).astype(np.float64))
+    h = wl.fields_for(cfg, k, L * L)
+    if h is not None:
+        sim.set_fields(h)
     sim.set_tie_eps(tie_eps)
     sim.init()
     return sim
 
 
-@pytest.mark.parametrize("name", ["G1", "G2"])
+@pytest.mark.parametrize("name", ["G1", "G2", "H1", "H2"])
 def test_fp64_trajectory_with_random_bonds(env, orc, name):
     xyl, wl = env
     cfg = wl.config(name)
@@ -61,7 +66,7 @@ def test_fp64_trajectory_with_random_bonds(env, orc, name):
 
 
 @pytest.mark.parametrize("engine_name", ["FP32_RESIDENT", "FP32_SPLIT", "FP32_GLOBAL", "FP32_PLAIN"])
-@pytest.mark.parametrize("name", ["G1", "G2"])
+@pytest.mark.parametrize("name", ["G1", "G2", "H1", "H2"])
 def test_fp32_energy_with_random_bonds(env, orc, name, engine_name):
     xyl, wl = env
     cfg = wl.config(name)
@@ -76,9 +81,10 @@ def test_fp32_energy_with_random_bonds(env, orc, name, engine_name):
 
 
 @pytest.mark.parametrize("engine_name", ["FP32_RESIDENT", "FP32_SPLIT", "FP32_GLOBAL", "FP32_PLAIN", "FP64_PLAIN"])
-def test_gauge_invariance_is_exact_on_the_gpu(env, engine_name):
+@pytest.mark.parametrize("name", ["G2", "H2"])
+def test_gauge_invariance_is_exact_on_the_gpu(env, name, engine_name):
     xyl, wl = env
-    cfg = wl.config("G2")
+    cfg = wl.config(name)
     eng, opts = _variant(xyl, engine_name)
     graphs = wl.build_graphs(cfg)
     g = graphs[0]
@@ -87,6 +93,9 @@ def test_gauge_invariance_is_exact_on_the_gpu(env, engine_name):
     tau = np.random.default_rng(8).choice(np.array([-1, 1], np.int8), g.n)
     gauged = xyl.build_graph_csr(128, 6, 3.5, wl.GRAPH_SEED, wl.graph_stream_id(cfg, 0))
     gauged.set_couplings((tau[ei] * tau[ej] * J).astype(np.int8))
+    h = wl.fields_for(cfg, 0, g.n)
+    if h is not None:
+        gauged.set_fields(h * tau[:, None])
     a, _ = wl.make_plan(cfg, eng, graphs=[g], **opts)
     b, _ = wl.make_plan(cfg, eng, graphs=[gauged], **opts)
     for p in (a, b):

@@ -213,3 +213,17 @@ def test_couplings_are_validated_and_aligned_with_the_csr(xyl):
     assert np.array_equal(g.couplings(), jc)     # a rejected call leaves the couplings as they were
     g.set_couplings(None)
     assert np.all(g.couplings() == 1)
+
+
+def test_fields_are_validated(xyl):
+    g = xyl.build_graph_csr(8, 6, 3.5, 1, 0)
+    h = np.zeros((64, 2))
+    h[5, 1] = np.nan
+    with pytest.raises(xyl.XylError) as e:
+        g.set_fields(h)
+    assert e.value.code == xyl.EINVAL
+    g.set_fields(np.ones((64, 2)))
+    p = xyl.Plan([(g, 0, [1.0, 0.5], [1.0, 1.0])], engine=xyl.FP32_BATCHED, device="cpu")
+    q = xyl.Plan([(g.set_fields(None), 0, [1.0, 0.5], [1.0, 1.0])], engine=xyl.FP32_BATCHED, device="cpu")
+    # one float2 per site for the fields (an empty region still takes one 256-byte slot)
+    assert p.workspace_bytes == q.workspace_bytes + 64 * 8 - 256
