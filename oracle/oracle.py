@@ -22,7 +22,7 @@ _lock = threading.Lock()
 _lib = None
 
 OP_MET, OP_OR, OP_PT, OP_MEASURE = 1, 2, 4, 8
-ACC_FIELDS = ("n", "e", "e2", "absm", "mx", "my", "m2", "m4", "chik")
+ACC_FIELDS = ("n", "e", "e2", "absm", "mx", "my", "m2", "m4", "chik", "mz")
 
 
 def build(force: bool = False) -> str:
@@ -57,6 +57,9 @@ def _load():
                                        u64p]
         lib.orc_sim_set_couplings.argtypes = [P, f64p]
         lib.orc_sim_set_fields.argtypes = [P, f64p]
+        lib.orc_sim_set_dim.argtypes = [P, C.c_int]
+        lib.orc_o3_propose.argtypes = [C.c_double] * 6 + [f64p, f64p, f64p]
+        lib.orc_o3_propose.restype = None
         lib.orc_walk_returns.argtypes = [C.c_int, i32p, i32p, C.c_int64, i32p, C.c_int32, C.c_uint64, u64p]
         lib.orc_pick_partner_counts.argtypes = [C.c_int, C.c_int, C.c_double, C.c_uint64, i32p, i32p, i32p,
                                                 C.c_int, C.c_int, C.c_int64, i64p]
@@ -265,9 +268,10 @@ class Sim:
     moments, the low-temperature limit, the high-temperature series and exact
     energy conservation of overrelaxation."""
 
-    def __init__(self, n, ei, ej, color, beta, delta, seed, sample=0, xy=None, L=None, u24=False):
+    def __init__(self, n, ei, ej, color, beta, delta, seed, sample=0, xy=None, L=None, u24=False, dim=2):
         self._lib = _load()
         self.n = int(n)
+        self.dim = int(dim)
         self.R = len(beta)
         self._keep = [np.ascontiguousarray(ei, np.int32), np.ascontiguousarray(ej, np.int32),
                       np.ascontiguousarray(color, np.int32)]
@@ -279,6 +283,8 @@ class Sim:
             int(L or 0), self.R, _ptr(b, C.c_double), _ptr(d, C.c_double), seed, sample, 1 if u24 else 0)
         if not self._h:
             raise MemoryError("oracle allocation failed")
+        if self.dim != 2 and self._lib.orc_sim_set_dim(self._h, self.dim):
+            raise ValueError("spin dimension must be 2 (XY) or 3 (O(3))")
 
     def close(self):
         if self._h:
@@ -315,7 +321,10 @@ class Sim:
             self._lib.orc_sim_set_fields(self._h, None)
             return
         self._hkeep = np.ascontiguousarray(hxy, np.float64).reshape(-1)
-        if self._lib.orc_sim_set_fields(self._h, _ptr(self._hkeep, C.c_double)):
+        rc = self._lib.orc_sim_set_fields(self._h, _ptr(self._hkeep, C.c_double))
+        if rc == -2:
+            raise ValueError("random fields are two-component (XY only)")
+        if rc:
             raise MemoryError("oracle allocation failed")
 
     def sweeps(self, n, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1):
@@ -331,12 +340,12 @@ class Sim:
         self._lib.orc_sim_set_angles(self._h, _ptr(a, C.c_double))
 
     def vectors(self) -> np.ndarray:
-        out = np.zeros((self.R, self.n, 2), np.float64)
+        out = np.zeros((self.R, self.n, self.dim), np.float64)
         self._lib.orc_sim_get_vectors(self._h, _ptr(out, C.c_double))
         return out
 
     def set_vectors(self, v):
-        v = np.ascontiguousarray(v, np.float64).reshape(self.R, self.n, 2)
+        v = np.ascontiguousarray(v, np.float64).reshape(self.R, self.n, self.dim)
         self._lib.orc_sim_set_vectors(self._h, _ptr(v, C.c_double))
 
     def set_labels(self, rep_at, sweep_index):
@@ -389,7 +398,18 @@ class Sim:
         return int(self._lib.orc_sim_sweep_index(self._h))
 
 
-def graph_sim(ei, ej, n, beta, delta, seed, sample=0, xy=None, L=None, u24=False):
+def graph_sim(ei, ej, n, beta, delta, seed, sample=0, xy=None, L=None, u24=False, dim=2):
     """Sampler on an explicit edge list, coloured by ``slo_color``."""
     color, _ = slo_color(n, ei, ej)
-    return Sim(n, ei, ej, color, beta, delta, seed, sample=sample, xy=xy, L=L, u24=u24)
+    return Sim(n, ei, ej, color, beta, delta, seed, sample=sample, xy=xy, L=L, u24=u24, dim=dim)
+
+
+def o3_propose(s, half_width: float, u: float, uphi: float) -> np.ndarray:
+    """The O(3) Metropolis proposal: a point of the spherical cap of angular
+    radius ``half_width`` around the unit vector ``s``, from the cap uniform
+    ``u`` and the azimuth uniform ``uphi``."""
+    lib = _load()
+    out = [C.c_double(), C.c_double(), C.c_double()]
+    lib.orc_o3_propose(float(s[0]), float(s[1]), float(s[2]), float(half_width), float(u), float(uphi),
+                       *[C.byref(o) for o in out])
+    return np.array([o.value for o in out])

@@ -27,6 +27,8 @@
  *   orc_csr()           Colour-sorted CSR (App. B, "Memory management": sites of
  *                       one colour stored consecutively).
  *   orc_sincos_series() sin/cos of the Metropolis step by their Maclaurin series.
+ *   orc_sim_set_dim()   O(3) spins (three components), the first of the "other
+ *                       continuous models" the method carries over to (App. B).
  *   orc_sim_*()         Monte Carlo sweeps of H = -sum_{i<j} J_ij S_i.S_j,
  *                       Eq. (HXY): single-spin Metropolis over the colour classes
  *                       in sequence (App. B), overrelaxation (App. B, "Improved
@@ -847,7 +849,7 @@ void orc_sincos_series(double x, double *sn, double *cs)
 /* sweep t: counter (k, t, PT<<24, sample), u53(w0,w1).                       */
 /* ------------------------------------------------------------------------- */
 enum { OP_MET = 1u, OP_OR = 2u, OP_PT = 4u, OP_MEASURE = 8u };
-enum { ACC_N, ACC_E, ACC_E2, ACC_ABSM, ACC_MX, ACC_MY, ACC_M2, ACC_M4, ACC_CHIK, ACC_COUNT };
+enum { ACC_N, ACC_E, ACC_E2, ACC_ABSM, ACC_MX, ACC_MY, ACC_M2, ACC_M4, ACC_CHIK, ACC_MZ, ACC_COUNT };
 
 typedef struct {
     int n, R, L, Q;
@@ -873,6 +875,8 @@ typedef struct {
     double *jb;               /* coupling of each bond, or NULL (all J = 1) */
     double *jn;               /* coupling of each neighbour entry (aligned with nbr), or NULL */
     double *hx, *hy;          /* field on each site, or NULL */
+    int dim;                  /* spin components: 2 (XY) or 3 (O(3)) */
+    double *vz;               /* third spin component [R][n] (zero for XY) */
 } orc_sim;
 
 void orc_sim_free(orc_sim *s)
@@ -882,7 +886,7 @@ void orc_sim_free(orc_sim *s)
     free(s->cx); free(s->sx); free(s->cy); free(s->sy); free(s->beta); free(s->delta);
     free(s->vx); free(s->vy); free(s->slot_of); free(s->rep_at); free(s->E); free(s->acc);
     free(s->met_acc); free(s->met_try); free(s->pt_acc); free(s->pt_try); free(s->first_tie); free(s->n_ties);
-    free(s->jb); free(s->jn); free(s->hx); free(s->hy);
+    free(s->jb); free(s->jn); free(s->hx); free(s->hy); free(s->vz);
     free(s);
 }
 
@@ -944,6 +948,8 @@ orc_sim *orc_sim_new(int n, int64_t ne, const int32_t *ei, const int32_t *ej, co
     for (int r = 0; r < R; ++r) { s->beta[r] = beta[r]; s->delta[r] = delta[r]; }
     s->vx = (double *)calloc((size_t)R * (size_t)n, sizeof(double));
     s->vy = (double *)calloc((size_t)R * (size_t)n, sizeof(double));
+    s->vz = (double *)calloc((size_t)R * (size_t)n, sizeof(double));
+    s->dim = 2;
     s->slot_of = (int *)malloc(sizeof(int) * (size_t)R);
     s->rep_at = (int *)malloc(sizeof(int) * (size_t)R);
     s->E = (double *)calloc((size_t)R, sizeof(double));
@@ -972,6 +978,15 @@ static double energy_of(const orc_sim *s, int r)
 {
     const double *x = s->vx + (size_t)r * s->n, *y = s->vy + (size_t)r * s->n;
     double E = 0.0;
+    if (s->dim == 3) {
+        const double *z = s->vz + (size_t)r * s->n;
+        for (int64_t e = 0; e < s->n_bonds; ++e) {
+            int i = s->bi[e], j = s->bj[e];
+            double d = x[i] * x[j] + y[i] * y[j] + z[i] * z[j];
+            E -= s->jb ? s->jb[e] * d : d;
+        }
+        return E;
+    }
     for (int64_t e = 0; e < s->n_bonds; ++e) {
         int i = s->bi[e], j = s->bj[e];
         if (s->jb) E -= s->jb[e] * (x[i] * x[j] + y[i] * y[j]);
@@ -989,9 +1004,12 @@ static void refresh_energies(orc_sim *s)
 
 /* aligned != 0: every spin (1, 0); else the INIT draws.  Resets the sweep count,
  * the slot labels and every accumulator. */
+static void init_o3(orc_sim *s, int aligned);
+
 void orc_sim_init(orc_sim *s, int aligned)
 {
-    for (int r = 0; r < s->R; ++r) {
+    if (s->dim == 3) init_o3(s, aligned);
+    for (int r = 0; r < s->R && s->dim == 2; ++r) {
         for (int v = 0; v < s->n; ++v) {
             double sn = 0.0, cs = 1.0;
             if (!aligned) {
@@ -1004,6 +1022,8 @@ void orc_sim_init(orc_sim *s, int aligned)
             s->vx[(size_t)r * s->n + v] = cs;
             s->vy[(size_t)r * s->n + v] = sn;
         }
+    }
+    for (int r = 0; r < s->R; ++r) {
         s->slot_of[r] = r; s->rep_at[r] = r; s->first_tie[r] = -1; s->n_ties[r] = 0;
     }
     s->t = 0;
@@ -1056,6 +1076,7 @@ static void local_field(const orc_sim *s, const double *x, const double *y, int 
  */
 int orc_sim_set_fields(orc_sim *s, const double *hxy)
 {
+    if (hxy && s->dim != 2) return -2;  /* fields are 2-vectors: XY only */
     free(s->hx); free(s->hy);
     s->hx = s->hy = NULL;
     if (hxy) {
@@ -1097,8 +1118,12 @@ int orc_sim_set_couplings(orc_sim *s, const double *j_per_bond)
     return 0;
 }
 
+static void metropolis_site_o3(orc_sim *s, int r, int v);
+static void overrelax_site_o3(orc_sim *s, int r, int v);
+
 static void metropolis_site(orc_sim *s, int r, int v)
 {
+    if (s->dim == 3) { metropolis_site_o3(s, r, v); return; }
     double *x = s->vx + (size_t)r * s->n, *y = s->vy + (size_t)r * s->n;
     int slot = s->slot_of[r];
     uint32_t w[4];
@@ -1142,6 +1167,7 @@ static void metropolis_site(orc_sim *s, int r, int v)
 
 static void overrelax_site(orc_sim *s, int r, int v)
 {
+    if (s->dim == 3) { overrelax_site_o3(s, r, v); return; }
     double *x = s->vx + (size_t)r * s->n, *y = s->vy + (size_t)r * s->n;
     double hx, hy;
     local_field(s, x, y, v, &hx, &hy);
@@ -1178,10 +1204,11 @@ static void parallel_tempering(orc_sim *s)
 /* Observables of Sec. III for replica r: e, m, |F(k_min)|^2 (two directions). */
 static void observe(const orc_sim *s, int r, double out[ACC_COUNT])
 {
-    const double *x = s->vx + (size_t)r * s->n, *y = s->vy + (size_t)r * s->n;
-    double mx = 0, my = 0;
+    const double *x = s->vx + (size_t)r * s->n, *y = s->vy + (size_t)r * s->n, *z = s->vz + (size_t)r * s->n;
+    double mx = 0, my = 0, mz = 0;
     double fxr_a = 0, fxi_a = 0, fyr_a = 0, fyi_a = 0; /* k along x: spin x / y comps */
     double fxr_b = 0, fxi_b = 0, fyr_b = 0, fyi_b = 0; /* k along y */
+    double fzr_a = 0, fzi_a = 0, fzr_b = 0, fzi_b = 0; /* spin z component (O(3)) */
     for (int v = 0; v < s->n; ++v) {
         double c = x[v], sn = y[v];
         mx += c; my += sn;
@@ -1189,13 +1216,23 @@ static void observe(const orc_sim *s, int r, double out[ACC_COUNT])
         fyr_a += sn * s->cx[v]; fyi_a += sn * s->sx[v];
         fxr_b += c * s->cy[v]; fxi_b += c * s->sy[v];
         fyr_b += sn * s->cy[v]; fyi_b += sn * s->sy[v];
+        if (s->dim == 3) {
+            mz += z[v];
+            fzr_a += z[v] * s->cx[v]; fzi_a += z[v] * s->sx[v];
+            fzr_b += z[v] * s->cy[v]; fzi_b += z[v] * s->sy[v];
+        }
     }
     double N = (double)s->n;
     double e = s->E[r] / N;
-    mx /= N; my /= N;
+    mx /= N; my /= N; mz /= N;
     double m2 = mx * mx + my * my;
     double fa = fxr_a * fxr_a + fxi_a * fxi_a + fyr_a * fyr_a + fyi_a * fyi_a;
     double fb = fxr_b * fxr_b + fxi_b * fxi_b + fyr_b * fyr_b + fyi_b * fyi_b;
+    if (s->dim == 3) {
+        m2 += mz * mz;
+        fa += fzr_a * fzr_a + fzi_a * fzi_a;
+        fb += fzr_b * fzr_b + fzi_b * fzi_b;
+    }
     out[ACC_N] = 1.0;
     out[ACC_E] = e;
     out[ACC_E2] = e * e;
@@ -1205,6 +1242,7 @@ static void observe(const orc_sim *s, int r, double out[ACC_COUNT])
     out[ACC_M2] = m2;
     out[ACC_M4] = m2 * m2;
     out[ACC_CHIK] = (fa + fb) / (2.0 * N);
+    out[ACC_MZ] = mz;
 }
 
 void orc_sim_sweeps(orc_sim *s, int n_sweeps, unsigned ops, int measure_every)
@@ -1249,15 +1287,25 @@ void orc_sim_set_angles(orc_sim *s, const double *in)
     refresh_energies(s);
 }
 
-/* spin vectors as (x, y) pairs, [R][n][2] */
+/* spin vectors, [R][n][dim] */
 void orc_sim_get_vectors(const orc_sim *s, double *out)
 {
-    for (size_t q = 0; q < (size_t)s->R * (size_t)s->n; ++q) { out[2 * q] = s->vx[q]; out[2 * q + 1] = s->vy[q]; }
+    const size_t d = (size_t)s->dim;
+    for (size_t q = 0; q < (size_t)s->R * (size_t)s->n; ++q) {
+        out[d * q] = s->vx[q];
+        out[d * q + 1] = s->vy[q];
+        if (d == 3) out[d * q + 2] = s->vz[q];
+    }
 }
 
 void orc_sim_set_vectors(orc_sim *s, const double *in)
 {
-    for (size_t q = 0; q < (size_t)s->R * (size_t)s->n; ++q) { s->vx[q] = in[2 * q]; s->vy[q] = in[2 * q + 1]; }
+    const size_t d = (size_t)s->dim;
+    for (size_t q = 0; q < (size_t)s->R * (size_t)s->n; ++q) {
+        s->vx[q] = in[d * q];
+        s->vy[q] = in[d * q + 1];
+        if (d == 3) s->vz[q] = in[d * q + 2];
+    }
     refresh_energies(s);
 }
 
@@ -1317,3 +1365,169 @@ void orc_sim_clear_ties(orc_sim *s)
 }
 
 uint64_t orc_sim_sweep_index(const orc_sim *s) { return s->t; }
+
+/* ------------------------------------------------------------------------- */
+/* O(3) spins (App. B: the method carries over to other continuous models;    */
+/* O(3) is the paper's example).  S_i = (x, y, z) unit vectors, the same      */
+/* Hamiltonian with the three-component dot product, the same sweep, PT and   */
+/* measurement; m^2 and chi(k) take all three components, ACC_MZ sums m_z.    */
+/* Readings where the paper fixes nothing:                                    */
+/*   init: uniform on the sphere (Archimedes): z = 2u - 1, phi = 2 pi u' - pi,*/
+/*     rho = sqrt((1 - z)(1 + z)), S = (rho cos phi, rho sin phi, z).          */
+/*     53-bit: u = u53(w0,w1), u' = u53(w2,w3) of the INIT block of (i, r);   */
+/*     24-bit: u24(w0), u24(w1).  aligned: S = (1, 0, 0).                      */
+/*   Metropolis: S' uniform on the spherical cap of angular radius Delta      */
+/*     around S (Delta <= pi; Delta = pi is the whole sphere): with            */
+/*     w = u (1 - cos Delta) = u * 2 sin^2(Delta / 2), cos theta = 1 - w and  */
+/*     sin theta = sqrt(w (2 - w)); azimuth phi = 2 pi u'' - pi in the frame  */
+/*     (e1, e2) orthogonal to S of Duff et al. (JCGT 6(1), 2017), its first   */
+/*     vector times g:                                                        */
+/*       g = +1 if z >= 0 else -1, a = -1 / (g + z), b = x y a,               */
+/*       e1 = (g + x^2 a, b, -x),  e2 = (b, g + y^2 a, -y);                    */
+/*     S' = cos theta S + sin theta (cos phi e1 + sin phi e2).  The proposal   */
+/*     density depends on the angle between S and S' only, so it is          */
+/*     symmetric; and the frame of -S is minus the frame of S, bit for bit,   */
+/*     so the proposal from -S is minus the proposal from S (the gauge        */
+/*     symmetry S -> -S, J -> -J then holds step by step, as for XY).         */
+/*     dE = -(S' - S) . h; the test as for XY.                                */
+/*     53-bit draws: block (i, t, MET<<24 | r): u = u53(w0,w1), test u53(w2,w3);*/
+/*     block (i, t, MET<<24 | 0x800000 | r): u'' = u53(w0,w1).                */
+/*     24-bit draws: one block (i, t, MET<<24 | r) per replica: u24(w0) for   */
+/*     the cap, u24(w1) for phi, u24(w2) for the test.                        */
+/*   Overrelaxation: S' = 2 (S.h) h / |h|^2 - S (rotation by pi about h).     */
+/* Random fields are 2-vectors and stay XY-only.                              */
+/* ------------------------------------------------------------------------- */
+#define MET_SECOND_BLOCK 0x800000u
+
+int orc_sim_set_dim(orc_sim *s, int dim)
+{
+    if (dim != 2 && dim != 3) return -1;
+    if (dim == 3 && s->hx) return -2;
+    s->dim = dim;
+    memset(s->vz, 0, sizeof(double) * (size_t)s->R * (size_t)s->n);
+    refresh_energies(s);
+    return 0;
+}
+
+int orc_sim_dim(const orc_sim *s) { return s->dim; }
+
+static void init_o3(orc_sim *s, int aligned)
+{
+    for (int r = 0; r < s->R; ++r) {
+        for (int v = 0; v < s->n; ++v) {
+            const size_t q = (size_t)r * s->n + v;
+            if (aligned) { s->vx[q] = 1.0; s->vy[q] = 0.0; s->vz[q] = 0.0; continue; }
+            uint32_t w[4];
+            draw_block((uint32_t)v, 0, PURPOSE_INIT, (uint32_t)r, s->sample, s->key, w);
+            double u = s->u24_mode ? u24(w[0]) : u53(w[0], w[1]);
+            double up = s->u24_mode ? u24(w[1]) : u53(w[2], w[3]);
+            double z = 2.0 * u - 1.0;
+            double phi = 2.0 * ORC_PI * up - ORC_PI;
+            double rho = sqrt((1.0 - z) * (1.0 + z));
+            double sn, cs;
+            orc_sincos_series(phi, &sn, &cs);
+            s->vx[q] = rho * cs;
+            s->vy[q] = rho * sn;
+            s->vz[q] = z;
+        }
+    }
+}
+
+static void local_field3(const orc_sim *s, int r, int v, double *hx, double *hy, double *hz)
+{
+    const double *x = s->vx + (size_t)r * s->n, *y = s->vy + (size_t)r * s->n, *z = s->vz + (size_t)r * s->n;
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    for (int a = s->ptr[v]; a < s->ptr[v + 1]; ++a) {
+        const int j = s->nbr[a];
+        if (s->jn) {
+            ax += s->jn[a] * x[j];
+            ay += s->jn[a] * y[j];
+            az += s->jn[a] * z[j];
+        } else {
+            ax += x[j];
+            ay += y[j];
+            az += z[j];
+        }
+    }
+    *hx = ax; *hy = ay; *hz = az;
+}
+
+/* the cap proposal of the header above, every step as written there */
+void orc_o3_propose(double x, double y, double z, double half_width, double u, double uphi,
+                    double *nx, double *ny, double *nz)
+{
+    double sh, ch;
+    orc_sincos_series(0.5 * half_width, &sh, &ch);
+    const double w = u * (2.0 * (sh * sh));
+    const double ct = 1.0 - w;
+    const double st = sqrt(w * (2.0 - w));
+    double sp, cp;
+    orc_sincos_series(2.0 * ORC_PI * uphi - ORC_PI, &sp, &cp);
+    const double g = z >= 0.0 ? 1.0 : -1.0;
+    const double a = -1.0 / (g + z);
+    const double b = x * y * a;
+    const double e1x = g + (x * x) * a, e1y = b, e1z = -x;
+    const double e2x = b, e2y = g + (y * y) * a, e2z = -y;
+    const double tx = cp * e1x + sp * e2x, ty = cp * e1y + sp * e2y, tz = cp * e1z + sp * e2z;
+    *nx = ct * x + st * tx;
+    *ny = ct * y + st * ty;
+    *nz = ct * z + st * tz;
+}
+
+static void metropolis_site_o3(orc_sim *s, int r, int v)
+{
+    const size_t q = (size_t)r * s->n + v;
+    const int slot = s->slot_of[r];
+    uint32_t w[4];
+    double ud, up, ua;
+    draw_block((uint32_t)v, (uint32_t)s->t, PURPOSE_MET, (uint32_t)r, s->sample, s->key, w);
+    if (s->u24_mode) {
+        ud = u24(w[0]);
+        up = u24(w[1]);
+        ua = u24(w[2]);
+    } else {
+        ud = u53(w[0], w[1]);
+        ua = u53(w[2], w[3]);
+        draw_block((uint32_t)v, (uint32_t)s->t, PURPOSE_MET, MET_SECOND_BLOCK | (uint32_t)r, s->sample, s->key, w);
+        up = u53(w[0], w[1]);
+    }
+    double hx, hy, hz;
+    local_field3(s, r, v, &hx, &hy, &hz);
+    const double x = s->vx[q], y = s->vy[q], z = s->vz[q];
+    double nx, ny, nz;
+    orc_o3_propose(x, y, z, s->delta[slot], ud, up, &nx, &ny, &nz);
+    const double dE = -((nx - x) * hx + (ny - y) * hy + (nz - z) * hz);
+    int accept;
+    if (dE <= 0.0) {
+        accept = 1;
+        note_tie(s, r, -dE);
+    } else {
+        double p = exp(-s->beta[slot] * dE);
+        accept = ua < p;
+        double margin = fabs(ua - p);
+        if (dE < margin) margin = dE;
+        note_tie(s, r, margin);
+    }
+    s->met_try[slot]++;
+    if (accept) {
+        s->vx[q] = nx;
+        s->vy[q] = ny;
+        s->vz[q] = nz;
+        s->met_acc[slot]++;
+    }
+}
+
+static void overrelax_site_o3(orc_sim *s, int r, int v)
+{
+    const size_t q = (size_t)r * s->n + v;
+    double hx, hy, hz;
+    local_field3(s, r, v, &hx, &hy, &hz);
+    const double h2 = hx * hx + hy * hy + hz * hz;
+    if (h2 > 0.0) {
+        const double x = s->vx[q], y = s->vy[q], z = s->vz[q];
+        const double k = 2.0 * (x * hx + y * hy + z * hz) / h2;
+        s->vx[q] = k * hx - x;
+        s->vy[q] = k * hy - y;
+        s->vz[q] = k * hz - z;
+    }
+}

@@ -13,7 +13,7 @@ import itertools
 import numpy as np
 from scipy import special
 
-ACC = {k: i for i, k in enumerate(("n", "e", "e2", "absm", "mx", "my", "m2", "m4", "chik"))}
+ACC = {k: i for i, k in enumerate(("n", "e", "e2", "absm", "mx", "my", "m2", "m4", "chik", "mz"))}
 
 
 def jackknife(bins: np.ndarray, fn):
