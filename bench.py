@@ -31,12 +31,15 @@ L2_FLUSH_BYTES = 256 << 20
 # algorithmic bytes per site-update (FP32 float2 spins, z = 6, R replicas sharing one CSR):
 # compulsory HBM model = own spin read 8 B + write 8 B + 6 x 4 B of indices / R
 # L2-level gather model = (z + 1) spin reads + 1 write (8 B each) + 6 x 4 B of indices / R
-def hbm_bytes_per_update(R):
-    return 16.0 + 24.0 / R
+def hbm_bytes_per_update(R, dim=2):
+    """Compulsory bytes of one site-update: the spin read and written once
+    (8 B FP32 XY, 16 B for an O(3) spin padded to a 4-vector), the site's
+    tables (24 B) once per sweep shared by the R replicas."""
+    return 2.0 * (8.0 if dim == 2 else 16.0) + 24.0 / R
 
 
-def l2_bytes_per_update(R):
-    return 64.0 + 24.0 / R
+def l2_bytes_per_update(R, dim=2):
+    return 64.0 * (1.0 if dim == 2 else 2.0) + 24.0 / R
 
 
 def _env_rank():
@@ -158,7 +161,13 @@ def run_oracle_sample(cfg, sweeps=0, seconds=0.0, measure_every=32, chunk=25, ma
         ei, ej, _, _ = oracle.levy_graph(L, wl.Z, rho, wl.GRAPH_SEED, wl.graph_stream_id(cfg, sample_index))
     color, _ = oracle.slo_color(L * L, ei, ej)
     sim = oracle.Sim(L * L, ei, ej, color, cfg.betas(), cfg.deltas(), wl.SPIN_SEED, sample=wl.graph_stream_id(cfg, sample_index),
-                     xy=oracle.lattice_xy(L), L=L)
+                     xy=oracle.lattice_xy(L), L=L, dim=cfg.spin_dim)
+    J = wl.couplings_for(cfg, sample_index, len(ei))
+    if J is not None:
+        sim.set_couplings(J.astype(float))
+    h = wl.fields_for(cfg, sample_index, L * L)
+    if h is not None:
+        sim.set_fields(h)
     sim.init()
     done, dt = 0, 0.0
     while True:
@@ -340,11 +349,15 @@ def main():
     cfg = wl.shard(cfg, rank, world)
     graphs = wl.build_graphs(cfg)
     stream = torch.cuda.current_stream()
+    # O(3) spins run on the plain engine; XY on the batched engine
+    engine_name = "FP32_PLAIN" if cfg.spin_dim == 3 else "FP32_BATCHED"
     tune = dict(block=args.block, cluster=args.cluster, group=args.group, resident=args.resident)
-    plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, **tune)
+    if cfg.spin_dim == 3:
+        tune = {}
+    plan, _ = wl.make_plan(cfg, getattr(xyl, engine_name), graphs=graphs, **tune)
     plan.bind(stream)
     plan.init_spins(stream=stream)
-    if not (args.block or args.cluster or args.group) and not args.no_autotune:
+    if engine_name == "FP32_BATCHED" and not (args.block or args.cluster or args.group) and not args.no_autotune:
         plan.autotune(32, OPS_ALL, args.measure_every, stream=stream)
     updates_per_sweep = cfg.spins_per_sweep() * 2
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -425,16 +438,17 @@ def main():
     R = cfg.n_temps
     avg_launch_s = (total_ms / 1e3) / max(1, launches)
     per_launch_updates = updates_per_sweep * sweeps * args.steps / max(1, launches)
-    achieved = hbm_bytes_per_update(R) * per_launch_updates / avg_launch_s / 1e9
+    dim = cfg.spin_dim
+    achieved = hbm_bytes_per_update(R, dim) * per_launch_updates / avg_launch_s / 1e9
     prof = _profile_traffic(kernel_name(plan), args.config)
     traffic = None
     if prof is not None:
         per_launch_sweeps = sweeps * args.steps / max(1, launches)
         traffic = prof["bytes_per_launch"] * (per_launch_sweeps / prof["sweeps_per_launch"] if prof["scales"] else 1.0)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_kind": peak_kind, "bytes_per_update": hbm_bytes_per_update(R),
+                "traffic": traffic, "peak_kind": peak_kind, "bytes_per_update": hbm_bytes_per_update(R, dim),
                 "kernel": kernel_name(plan)}
-    l2_achieved = l2_bytes_per_update(R) * per_launch_updates / avg_launch_s / 1e9
+    l2_achieved = l2_bytes_per_update(R, dim) * per_launch_updates / avg_launch_s / 1e9
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -447,7 +461,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{cfg.name}: {cfg.description}", "engine": "FP32_BATCHED",
+            "config": {"workload": f"{cfg.name}: {cfg.description}", "engine": engine_name,
                        "sweeps_per_step": sweeps, "samples_on_rank0": cfg.n_samples, "temperatures": R,
                        "l2": "flushed (256 MiB write) between timed steps",
                        "measure_every": args.measure_every,
@@ -455,7 +469,7 @@ def main():
             "fp64_plain": {"value": fp64, "unit": UNIT, "ratio_fp32_batched_over_fp64_plain":
                            (value / world / fp64) if fp64 else None},
             "roofline": roofline,
-            "roofline_l2_model": {"bytes_per_update": l2_bytes_per_update(R), "achieved_GBps": l2_achieved},
+            "roofline_l2_model": {"bytes_per_update": l2_bytes_per_update(R, dim), "achieved_GBps": l2_achieved},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches),
@@ -467,12 +481,18 @@ def main():
 
 
 def plan_shape(plan):
+    from paper_1211_3991_gb300 import xyl
+    if plan.engine != xyl.FP32_BATCHED:  # plain engines: one launch per colour phase, 256 threads per CTA
+        return {"plain": True, "threads_per_cta": 256}
     t = plan.tuning()
     return {"spins_in_shared_memory": t["resident"] > 0, "units": plan.unit_count(), "replicas_per_group": t["group"],
             "ctas_per_cluster": t["cluster"], "threads_per_cta": t["block"], "csr_in_shared_memory": t["stage"] > 0}
 
 
 def kernel_name(plan):
+    from paper_1211_3991_gb300 import xyl
+    if plan.engine != xyl.FP32_BATCHED:
+        return "o3_phase_kernel" if plan.dim == 3 else "plain_phase_kernel"
     return "resident_kernel" if plan.tuning()["resident"] > 0 else "batched_kernel"
 
 

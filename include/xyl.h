@@ -4,9 +4,11 @@
  * model in complex topologies").
  *
  * Model, Eq. (HXY): H = -sum_{i<j} J_ij S_i . S_j with S_i a unit 2-vector and
- * J_ij in {0,1} the adjacency of the graph.  Graph, Eq. (Levyi): sites of an
- * L x L square lattice; a link lands at distance r with probability
- * proportional to r^-rho.  Two ensembles: every site carrying exactly z links
+ * J_ij in {0,1} the adjacency of the graph.  Variants the method carries over
+ * to (App. B): random couplings J = +-1 per link, random fields -sum h_i . S_i,
+ * and O(3) spins (unit 3-vectors; xyl_tuning.spin_dim = 3, plain engines).
+ * Graph, Eq. (Levyi): sites of an L x L square lattice; a link lands at
+ * distance r with probability proportional to r^-rho.  Two ensembles: every site carrying exactly z links
  * on the periodic lattice (xyl_build_graph_csr), or a fixed total of links with
  * free degrees on the periodic or free lattice, the paper's own (Sec. II,
  * xyl_build_levy_bonds).
@@ -70,7 +72,8 @@ extern "C" {
 #define XYL_ACC_M2 6    /* sum of m^2 */
 #define XYL_ACC_M4 7    /* sum of m^4 */
 #define XYL_ACC_CHIK 8  /* sum of (|F(k1)|^2 + |F(k2)|^2) / (2N), k = 2 pi / L */
-#define XYL_ACC_COUNT 9
+#define XYL_ACC_MZ 9    /* sum of m_z (O(3) spins; 0 for XY) */
+#define XYL_ACC_COUNT 10
 
 typedef struct xyl_graph xyl_graph;
 typedef struct xyl_plan xyl_plan;
@@ -208,8 +211,30 @@ typedef struct {
     int32_t recompute_every; /* FP64 energy recompute + renormalise every this many sweeps (0 = never) */
     int32_t stage;           /* batched engine: 0 = stage CSR rows in shared memory when they fit, -1 = never */
     int32_t resident;        /* batched engine: 1 = resident shape, -1 = never, 0 = library's choice (below) */
-    int32_t reserved[2];
+    int32_t spin_dim;        /* spin components: 0 or 2 = XY; 3 = O(3) (plain engines, no fields; see below) */
+    int32_t reserved[1];
 } xyl_tuning;
+
+/*
+ * O(3) spins (spin_dim = 3; App. B names O(3) among the continuous models the
+ * method carries over to).  Same Hamiltonian with three-component unit
+ * vectors, same sweep, parallel tempering and measurements; m^2, m^4 and
+ * chi(k) take all three components and XYL_ACC_MZ sums m_z.  Initial spins
+ * are uniform on the sphere: z = 2u - 1, phi = 2 pi u' - pi from the INIT
+ * block of (site, replica) (u53(w0,w1), u53(w2,w3) in FP64; u24(w0), u24(w1)
+ * in FP32), aligned = (1, 0, 0).  Metropolis proposes a point uniform on the
+ * spherical cap of angular radius Delta around S: 1 - cos theta =
+ * u * 2 sin^2(Delta/2), azimuth phi = 2 pi u'' - pi in the orthonormal frame
+ * e1 = (g + x^2 a, b, -x), e2 = (b, g + y^2 a, -y), g = sign(z) (+1 at z = 0),
+ * a = -1/(g + z), b = x y a (Duff et al., JCGT 2017, first vector times g),
+ * S' = cos theta S + sin theta (cos phi e1 + sin phi e2); accept as for XY.
+ * FP64 draws: block (site, t, MET<<24 | r): u = u53(w0,w1), test u53(w2,w3);
+ * block (site, t, MET<<24 | 0x800000 | r): u'' = u53(w0,w1).  FP32: one block
+ * (site, t, MET<<24 | r) per replica, u24(w0), u24(w1), u24(w2), and the
+ * proposal renormalised.  Overrelaxation: S' = 2 (S.h) h / |h|^2 - S.  Spins
+ * are stored as padded 4-vectors (16 B FP32, 32 B FP64).  The batched engine
+ * and random fields are XY-only (XYL_EINVAL).
+ */
 
 /*
  * Resident shape of the batched engine.  One CTA owns a group of `group`
@@ -231,7 +256,8 @@ typedef struct {
  * graph and temperature slots) for one engine.  Replica r of a sample starts at
  * slot r.  seed keys every spin/Metropolis/PT random stream.  tune may be NULL.
  * *workspace_bytes receives the device bytes xyl_bind needs.
- * Errors: XYL_EINVAL (empty batch, bad slot count, unknown engine).
+ * Errors: XYL_EINVAL (empty batch, bad slot count, unknown engine, spin_dim
+ * other than 0, 2 or 3, O(3) spins on the batched engine or with fields).
  */
 int xyl_plan_create(const xyl_sample *samples, int32_t n_samples, int32_t engine, uint64_t seed,
                     const xyl_tuning *tune, xyl_plan **out, size_t *workspace_bytes);
@@ -247,7 +273,7 @@ int xyl_bind(xyl_plan *p, void *d_workspace, size_t bytes, void *stream);
 /*
  * xyl_init_spins -- theta = 2 pi u - pi from the INIT stream of each (site,
  * replica, sample), stored as unit vectors; aligned != 0 sets every spin to
- * (1, 0) instead.  Resets the sweep counter, the slot labels, the per-slot
+ * (1, 0) instead (O(3) spins: uniform on the sphere, see above).  Resets the sweep counter, the slot labels, the per-slot
  * accumulators and the status word.
  */
 int xyl_init_spins(xyl_plan *p, int32_t aligned, void *stream);
@@ -363,7 +389,7 @@ int xyl_read_energies(xyl_plan *p, double *E, void *stream);
 /* replica_at_slot[k] for every slot of the batch (slot-major). */
 int xyl_read_labels(xyl_plan *p, int32_t *replica_at_slot, void *stream);
 
-/* Spin vectors of one replica, original site order: sxy[2*i], sxy[2*i+1] (FP64). */
+/* Spin vectors of one replica, original site order: sxy[d*i + k], k < d, d = 2 (XY) or 3 (O(3)), FP64. */
 int xyl_read_spins(xyl_plan *p, int32_t sample, int32_t replica, double *sxy, void *stream);
 
 /* Overwrite the spin vectors of one replica (original site order). */

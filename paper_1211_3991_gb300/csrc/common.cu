@@ -56,7 +56,7 @@ __global__ void reset_labels_kernel(DevPlan P)
 // obs[buffer], attempts the PT swaps of pairs (k, k+1), k = t mod 2 (App. B:
 // accept iff u < exp((beta_k - beta_k+1)(E_k - E_k+1)), FP64), adds one
 // measurement per slot when due, updates the counters and clears the buffer.
-__global__ void finalize_kernel(DevPlan P, uint32_t ops, int measure_every, int advance, int buffer_mode)
+__global__ void finalize_kernel(DevPlan P, uint32_t ops, int measure_every, int advance, int buffer_mode, int dim)
 {
     extern __shared__ double sh[];
     const int s = blockIdx.x;
@@ -99,11 +99,18 @@ __global__ void finalize_kernel(DevPlan P, uint32_t ops, int measure_every, int 
             const double *o = obs + (size_t)r * kObsStride;
             const double e = o[kObsE] * invN;
             const double mx = o[kObsMx] * invN, my = o[kObsMy] * invN;
-            const double m2 = mx * mx + my * my;
-            const double f1 = o[kObsF1xRe] * o[kObsF1xRe] + o[kObsF1xIm] * o[kObsF1xIm] +
-                              o[kObsF1yRe] * o[kObsF1yRe] + o[kObsF1yIm] * o[kObsF1yIm];
-            const double f2 = o[kObsF2xRe] * o[kObsF2xRe] + o[kObsF2xIm] * o[kObsF2xIm] +
-                              o[kObsF2yRe] * o[kObsF2yRe] + o[kObsF2yIm] * o[kObsF2yIm];
+            double m2 = mx * mx + my * my;
+            double f1 = o[kObsF1xRe] * o[kObsF1xRe] + o[kObsF1xIm] * o[kObsF1xIm] +
+                        o[kObsF1yRe] * o[kObsF1yRe] + o[kObsF1yIm] * o[kObsF1yIm];
+            double f2 = o[kObsF2xRe] * o[kObsF2xRe] + o[kObsF2xIm] * o[kObsF2xIm] +
+                        o[kObsF2yRe] * o[kObsF2yRe] + o[kObsF2yIm] * o[kObsF2yIm];
+            const double mz = dim == 3 ? o[kObsMz] * invN : 0.0;
+            if (dim == 3) {
+                // O(3) spins: the third component joins m^2 and |F(k)|^2
+                m2 += mz * mz;
+                f1 += o[kObsF1zRe] * o[kObsF1zRe] + o[kObsF1zIm] * o[kObsF1zIm];
+                f2 += o[kObsF2zRe] * o[kObsF2zRe] + o[kObsF2zIm] * o[kObsF2zIm];
+            }
             double *a = P.acc + (size_t)(d.rep_off + k) * kAccCount;
             a[XYL_ACC_N] += 1.0;
             a[XYL_ACC_E] += e;
@@ -114,6 +121,7 @@ __global__ void finalize_kernel(DevPlan P, uint32_t ops, int measure_every, int 
             a[XYL_ACC_M2] += m2;
             a[XYL_ACC_M4] += m2 * m2;
             a[XYL_ACC_CHIK] += (f1 + f2) * 0.5 * invN;
+            a[XYL_ACC_MZ] += mz;
         }
     }
     __syncthreads();
@@ -239,7 +247,12 @@ __global__ void recompute_kernel(DevPlan P, int layout, int fp64, int renormalis
 cudaError_t launch_init(const DevPlan &P, const PlanShape &S, int aligned, cudaStream_t st)
 {
     dim3 grid((S.max_N + 255) / 256, S.max_R, S.n_samples);
-    init_kernel<<<grid, 256, 0, st>>>(P, S.layout, S.fp64 ? 1 : 0, aligned);
+    if (S.dim == 3) {
+        const cudaError_t e = launch_o3_init(P, S, aligned, st);
+        if (e != cudaSuccess) return e;
+    } else {
+        init_kernel<<<grid, 256, 0, st>>>(P, S.layout, S.fp64 ? 1 : 0, aligned);
+    }
     reset_labels_kernel<<<S.n_samples, 128, 0, st>>>(P);
     return cudaGetLastError();
 }
@@ -248,12 +261,13 @@ cudaError_t launch_finalize(const DevPlan &P, const PlanShape &S, uint32_t ops, 
                             int buffer_mode, cudaStream_t st)
 {
     const size_t smem = (size_t)S.max_R * (sizeof(double) + sizeof(int));
-    finalize_kernel<<<S.n_samples, 128, smem, st>>>(P, ops, measure_every, advance, buffer_mode);
+    finalize_kernel<<<S.n_samples, 128, smem, st>>>(P, ops, measure_every, advance, buffer_mode, S.dim);
     return cudaGetLastError();
 }
 
 cudaError_t launch_recompute(const DevPlan &P, const PlanShape &S, int renormalise, int buffer_mode, cudaStream_t st)
 {
+    if (S.dim == 3) return launch_o3_recompute(P, S, renormalise, buffer_mode, st);
     dim3 grid(S.max_R, S.n_samples);
     recompute_kernel<<<grid, 256, 0, st>>>(P, S.layout, S.fp64 ? 1 : 0, renormalise, buffer_mode);
     return cudaGetLastError();

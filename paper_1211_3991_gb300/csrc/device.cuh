@@ -1,6 +1,7 @@
 // Device-side descriptors and the per-spin update arithmetic shared by the
-// engines of libxyl.  Spins are unit 2-vectors; the Hamiltonian is
-// H = -sum_{i<j} J_ij S_i . S_j, Eq. (HXY).
+// engines of libxyl.  Spins are unit 2-vectors (XY; O(3) spins, unit
+// 3-vectors stored as padded 4-vectors, run on the plain engines); the
+// Hamiltonian is H = -sum_{i<j} J_ij S_i . S_j, Eq. (HXY).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -19,9 +20,12 @@ enum ObsField : int {
     kObsMx, kObsMy,
     kObsF1xRe, kObsF1xIm, kObsF1yRe, kObsF1yIm,   // k1: spin x / spin y components
     kObsF2xRe, kObsF2xIm, kObsF2yRe, kObsF2yIm,   // k2
-    kObsCount
+    kObsCount,                                    // fields of two-component spins
+    kObsMz = kObsCount,                           // O(3): third component
+    kObsF1zRe, kObsF1zIm, kObsF2zRe, kObsF2zIm,
+    kObsCount3                                    // fields of three-component spins
 };
-constexpr int kObsStride = 12;  // padded
+constexpr int kObsStride = 16;
 constexpr int kMaxColorsBatched = 32;  // colour classes per graph the batched engine accepts
 constexpr int kSinTerms = 15;
 constexpr int kCosTerms = 16;
@@ -48,7 +52,7 @@ struct DevPlan {
     const int32_t *perm;       // colour-sorted id -> original id
     const int32_t *color_ptr;
     const void *phase;         // per site (cos kx, sin kx, cos ky, sin ky): float4 or double4_32a
-    void *spins;               // float2 / double2
+    void *spins;               // float2 / double2 (O(3): float4 / double4_32a)
     const double *beta;        // per slot
     const double *delta;       // per slot
     int32_t *slot_of;          // per replica: slot it sits at

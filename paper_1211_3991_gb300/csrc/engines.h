@@ -20,6 +20,7 @@ struct PlanShape {
     bool coupled = false;   // some link has J = -1: neighbour ids carry J in bit 31
     bool fields = false;    // sites carry a field vector (DevPlan::field)
     bool disorder = false;  // coupled || fields: the kernels' DISORDER variants run
+    int dim = 2;            // spin components: 2 (XY) or 3 (O(3), plain engines)
 };
 
 // Batched-engine launch shape chosen by the tuner.
@@ -62,6 +63,13 @@ cudaError_t launch_recompute(const DevPlan &P, const PlanShape &S, int renormali
                              cudaStream_t st);
 cudaError_t launch_plain_sweep(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every,
                                cudaStream_t st, int64_t *launches);
+
+// O(3) spins (plain engines): initialisation, one sweep, FP64 recompute.
+cudaError_t launch_o3_init(const DevPlan &P, const PlanShape &S, int aligned, cudaStream_t st);
+cudaError_t launch_o3_sweep(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every,
+                            cudaStream_t st, int64_t *launches);
+cudaError_t launch_o3_recompute(const DevPlan &P, const PlanShape &S, int renormalise, int buffer_mode,
+                                cudaStream_t st);
 
 // Batched engine: one launch per wave of samples; `units` lists (sample, group) per cluster.
 cudaError_t launch_batched(const DevPlan &P, const PlanShape &S, const BatchedShape &B, const int2 *d_units,

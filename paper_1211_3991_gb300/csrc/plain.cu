@@ -164,6 +164,7 @@ cudaError_t sweep_impl(const DevPlan &P, const PlanShape &S, uint32_t ops, int m
 cudaError_t launch_plain_sweep(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every,
                                cudaStream_t st, int64_t *launches)
 {
+    if (S.dim == 3) return launch_o3_sweep(P, S, ops, measure_every, st, launches);
     if (S.disorder)
         return S.fp64 ? sweep_impl<double, true>(P, S, ops, measure_every, st, launches)
                       : sweep_impl<float, true>(P, S, ops, measure_every, st, launches);

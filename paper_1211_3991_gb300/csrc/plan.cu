@@ -64,7 +64,11 @@ struct xyl_plan {
     int64_t last_launches = 0;
     int64_t launches_per_graph_plain = 0;
 
-    size_t spin_elem() const { return shape.fp64 ? sizeof(double2) : sizeof(float2); }
+    size_t spin_elem() const
+    {
+        if (shape.dim == 3) return shape.fp64 ? sizeof(double4_32a) : sizeof(float4);
+        return shape.fp64 ? sizeof(double2) : sizeof(float2);
+    }
 
     void drop_graphs()
     {
@@ -407,6 +411,16 @@ int xyl_plan_create(const xyl_sample *samples, int32_t n_samples, int32_t engine
     p->shape.layout = (engine == XYL_FP32_BATCHED) ? kInterleaved : kReplicaMajor;
     p->recompute_every = tune ? std::max(0, tune->recompute_every) : 0;
     p->resident_req = tune ? tune->resident : 0;
+    const int dim = (tune && tune->spin_dim) ? tune->spin_dim : 2;
+    if (dim != 2 && dim != 3) {
+        delete p;
+        return fail(XYL_EINVAL, "xyl_plan_create: spin_dim %d (2 = XY, 3 = O(3))", dim);
+    }
+    if (dim == 3 && engine == XYL_FP32_BATCHED) {
+        delete p;
+        return fail(XYL_EINVAL, "xyl_plan_create: O(3) spins run on the plain engines");
+    }
+    p->shape.dim = dim;
     for (int s = 0; s < n_samples; ++s) {
         const xyl_sample &in = samples[s];
         const xyl_graph *g = in.graph;
@@ -453,6 +467,10 @@ int xyl_plan_create(const xyl_sample *samples, int32_t n_samples, int32_t engine
     }
     p->shape.n_samples = n_samples;
     p->shape.disorder = p->shape.coupled || p->shape.fields;
+    if (dim == 3 && p->shape.fields) {
+        delete p;
+        return fail(XYL_EINVAL, "xyl_plan_create: random fields are two-component (XY only)");
+    }
     if (engine == XYL_FP32_BATCHED) {
         const int rc = pick_batched_shape(p, tune);
         if (rc) { delete p; return rc; }
@@ -934,12 +952,19 @@ static int spin_copy(xyl_plan *p, int32_t sample, int32_t replica, double *out, 
     const bool inter = p->shape.layout == kInterleaved;
     char *dev = inter ? base + (size_t)replica * elem : base + (size_t)replica * h.N * elem;
     const size_t pitch = inter ? (size_t)h.R * elem : elem;
+    const int dim = p->shape.dim;
     if (out) {
         XYL_CUDA(cudaMemcpy2DAsync(buf.data(), elem, dev, pitch, elem, h.N, cudaMemcpyDeviceToHost, st), "spins: copy");
         XYL_CUDA(cudaStreamSynchronize(st), "spins: sync");
         for (int i = 0; i < h.N; ++i) {
             const int v = h.perm[i];
-            if (p->shape.fp64) {
+            if (dim == 3 && p->shape.fp64) {
+                const double4_32a s = reinterpret_cast<const double4_32a *>(buf.data())[i];
+                out[3 * v] = s.x; out[3 * v + 1] = s.y; out[3 * v + 2] = s.z;
+            } else if (dim == 3) {
+                const float4 s = reinterpret_cast<const float4 *>(buf.data())[i];
+                out[3 * v] = s.x; out[3 * v + 1] = s.y; out[3 * v + 2] = s.z;
+            } else if (p->shape.fp64) {
                 const double2 s = reinterpret_cast<const double2 *>(buf.data())[i];
                 out[2 * v] = s.x; out[2 * v + 1] = s.y;
             } else {
@@ -951,7 +976,14 @@ static int spin_copy(xyl_plan *p, int32_t sample, int32_t replica, double *out, 
     }
     for (int i = 0; i < h.N; ++i) {
         const int v = h.perm[i];
-        if (p->shape.fp64)
+        if (dim == 3 && p->shape.fp64) {
+            double4_32a s;
+            s.x = in[3 * v]; s.y = in[3 * v + 1]; s.z = in[3 * v + 2]; s.w = 0.0;
+            reinterpret_cast<double4_32a *>(buf.data())[i] = s;
+        } else if (dim == 3) {
+            reinterpret_cast<float4 *>(buf.data())[i] =
+                make_float4((float)in[3 * v], (float)in[3 * v + 1], (float)in[3 * v + 2], 0.0f);
+        } else if (p->shape.fp64)
             reinterpret_cast<double2 *>(buf.data())[i] = make_double2(in[2 * v], in[2 * v + 1]);
         else
             reinterpret_cast<float2 *>(buf.data())[i] = make_float2((float)in[2 * v], (float)in[2 * v + 1]);
@@ -1069,6 +1101,7 @@ int xyl_get_tuning(const xyl_plan *p, xyl_tuning *out)
     if (!p || !out) return fail(XYL_EINVAL, "xyl_get_tuning: NULL argument");
     std::memset(out, 0, sizeof(*out));
     out->recompute_every = p->recompute_every;
+    out->spin_dim = p->shape.dim;
     if (p->engine == XYL_FP32_BATCHED) {
         out->block = p->bshape.block;
         out->cluster = p->bshape.G;

@@ -25,6 +25,9 @@ with J = +-1 at random (probability 1/2 each, the XY spin glass):
   G2  L=128, rho=3.5, 16 temperatures geometric in [0.3, 1.2]
   H1  G1 with random fields of magnitude 0.5 (uniform random directions)
   H2  G2 with random fields of magnitude 0.5
+  O1  C1's graph with O(3) spins, 4 temperatures geometric in [0.9, 1.8]
+  O2  C2's graph with O(3) spins, 16 temperatures geometric in [0.9, 1.8]
+  O2G O2 with random +-1 couplings, 16 temperatures geometric in [0.4, 1.2]
 """
 from __future__ import annotations
 
@@ -56,6 +59,7 @@ class Config:
     boundary: str = "pbc"     # "bonds" ensemble: "pbc" or "fbc"
     couplings: str = "ferro"  # "ferro": J = 1; "pm": random signs, J = -1 with probability 1/2 (spin glass)
     field: float = 0.0        # magnitude of a random field on every site (uniform random direction), 0 = none
+    spin_dim: int = 2         # 2: XY spins; 3: O(3) spins (plain engines)
 
     @property
     def n_samples(self):
@@ -115,6 +119,15 @@ def config(name: str) -> Config:
     if name == "H2":
         return Config("H2", [(128, 3.5, 0)], geometric_temperatures(0.3, 1.2, 16), couplings="pm", field=0.5,
                       description="C2's graph, random +-1 couplings and random fields of magnitude 0.5, 16 T")
+    if name == "O1":
+        return Config("O1", [(16, 3.5, 0)], geometric_temperatures(0.9, 1.8, 4), spin_dim=3,
+                      description="C1's graph with O(3) spins, 4 T geometric in [0.9,1.8]")
+    if name == "O2":
+        return Config("O2", [(128, 3.5, 0)], geometric_temperatures(0.9, 1.8, 16), spin_dim=3,
+                      description="C2's graph with O(3) spins, 16 T geometric in [0.9,1.8]")
+    if name == "O2G":
+        return Config("O2G", [(128, 3.5, 0)], geometric_temperatures(0.4, 1.2, 16), spin_dim=3, couplings="pm",
+                      description="C2's graph with O(3) spins and random +-1 couplings, 16 T geometric in [0.4,1.2]")
     if name == "B64":
         return Config("B64", [(64, 10.0 / 3.0, s) for s in range(64)], geometric_temperatures(1.4, 2.0, 12),
                       ensemble="bonds", description="64 graphs L=64 2N bonds rho=10/3 periodic, 12 T geometric in [1.4,2.0]")
@@ -205,4 +218,5 @@ def make_plan(cfg: Config, engine, graphs=None, seed=SPIN_SEED, **tuning):
     samples = [(g, graph_stream_id(cfg, k), cfg.betas(), cfg.deltas()) for k, g in enumerate(graphs)]
     if "recompute_every" not in tuning:
         tuning["recompute_every"] = cfg.recompute_every
+    tuning.setdefault("spin_dim", cfg.spin_dim)
     return xyl.Plan(samples, engine=engine, seed=seed, **tuning), graphs

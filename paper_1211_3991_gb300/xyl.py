@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libxyl.so")
 OK, EINVAL, ENOSPC, EGRAPH, ECUDA, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
 OP_MET, OP_OR, OP_PT, OP_MEASURE = 1, 2, 4, 8
 FP64_PLAIN, FP32_BATCHED, FP32_PLAIN = 0, 1, 2
-ACC_FIELDS = ("n", "e", "e2", "absm", "mx", "my", "m2", "m4", "chik")
+ACC_FIELDS = ("n", "e", "e2", "absm", "mx", "my", "m2", "m4", "chik", "mz")
 
 EXPORTED = (
     "xyl_last_error", "xyl_version", "xyl_build_graph_csr", "xyl_graph_from_edges", "xyl_graph_info",
@@ -47,7 +47,7 @@ class Sample(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("block", C.c_int32), ("cluster", C.c_int32), ("group", C.c_int32),
                 ("recompute_every", C.c_int32), ("stage", C.c_int32), ("resident", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("spin_dim", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 _lib = None
@@ -230,7 +230,7 @@ class Plan:
     ``samples``: list of (Graph, sample_id, beta[list], delta[list])."""
 
     def __init__(self, samples, engine=FP32_BATCHED, seed=0, block=0, cluster=0, group=0, recompute_every=0,
-                 stage=0, resident=0, device=None):
+                 stage=0, resident=0, device=None, spin_dim=2):
         import torch
         lib = load()
         self._keep = []
@@ -245,7 +245,8 @@ class Plan:
             arr[k] = Sample(g.handle, sid, len(b), _p(b, C.c_double), _p(d, C.c_double))
             self.n_temps.append(len(b))
             self.sizes.append(g.n)
-        tune = Tuning(block, cluster, group, recompute_every, stage, resident)
+        tune = Tuning(block, cluster, group, recompute_every, stage, resident, spin_dim)
+        self.dim = int(spin_dim)
         h = C.c_void_p(); nbytes = C.c_size_t()
         _check(lib.xyl_plan_create(arr, len(samples), engine, seed, C.byref(tune), C.byref(h), C.byref(nbytes)))
         self.handle = h
@@ -340,12 +341,14 @@ class Plan:
         return out
 
     def spins(self, sample, replica, stream=None):
-        out = np.zeros(2 * self.sizes[sample], np.float64)
+        out = np.zeros(self.dim * self.sizes[sample], np.float64)
         _check(load().xyl_read_spins(self.handle, sample, replica, _p(out, C.c_double), _stream(stream)))
-        return out.reshape(-1, 2)
+        return out.reshape(-1, self.dim)
 
     def write_spins(self, sample, replica, sxy, stream=None):
         a = np.ascontiguousarray(np.asarray(sxy, np.float64).reshape(-1))
+        if len(a) != self.dim * self.sizes[sample]:
+            raise XylError(EINVAL, f"write_spins: need {self.dim} components per site")
         _check(load().xyl_write_spins(self.handle, sample, replica, _p(a, C.c_double), _stream(stream)))
 
     def status(self, stream=None):

@@ -1,0 +1,167 @@
+"""O(3) spins on the GPU plain engines (App. B's other continuous models)
+against the oracle.
+
+* FP64: initial spins identical to the oracle's, then 10 sweeps of Metropolis,
+  overrelaxation, PT and measurement with every spin within 1e-12, identical
+  slot labels and FP64 accumulators (including m_z and chi(k)) to 1e-9; with
+  and without random +-1 couplings.
+* FP32: every sweep starts the oracle (24-bit draws) from the GPU's spins and
+  labels; energies per spin within 1e-5 and directions within 1e-4 rad, a
+  miss allowed only where the oracle flags a near-tie decision.
+* Gauge invariance: couplings tau_i tau_j J_ij with spins tau_i S_i give the
+  negated run bit for bit on both plain engines.
+* A random tree measured by the FP32 engine against the exact tree energy
+  -(n-1) L(beta) / n, L the Langevin function.
+"""
+import numpy as np
+import pytest
+
+from test_gpu_parity import FP32_TIE_EPS
+
+pytestmark = pytest.mark.gpu
+
+ALL = 1 | 2 | 4 | 8
+NO_PT = 1 | 2 | 8
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    from paper_1211_3991_gb300 import build
+    build.build()
+    from paper_1211_3991_gb300 import workloads, xyl
+    xyl.load()
+    return xyl, workloads
+
+
+def _oracle(orc, wl, cfg, k, u24):
+    L, rho, _ = cfg.graphs[k]
+    ei, ej, _, _ = orc.levy_graph(L, 6, rho, wl.GRAPH_SEED, wl.graph_stream_id(cfg, k))
+    color, _ = orc.slo_color(L * L, ei, ej)
+    sim = orc.Sim(L * L, ei, ej, color, cfg.betas(), cfg.deltas(), wl.SPIN_SEED, sample=wl.graph_stream_id(cfg, k),
+                  xy=orc.lattice_xy(L), L=L, u24=u24, dim=3)
+    J = wl.couplings_for(cfg, k, len(ei))
+    if J is not None:
+        sim.set_couplings(J.astype(np.float64))
+    sim.init()
+    return sim
+
+
+def _gpu_vectors(plan, sample, R):
+    return np.stack([plan.spins(sample, r) for r in range(R)])
+
+
+@pytest.mark.parametrize("name", ["O1", "O2", "O2G"])
+def test_fp64_trajectory_matches_oracle(env, orc, name):
+    xyl, wl = env
+    cfg = wl.config(name)
+    plan, _ = wl.make_plan(cfg, xyl.FP64_PLAIN)
+    plan.bind()
+    plan.init_spins()
+    sim = _oracle(orc, wl, cfg, 0, u24=False)
+    R = cfg.n_temps
+    assert np.array_equal(_gpu_vectors(plan, 0, R), sim.vectors())
+    for t in range(10):
+        plan.sweep(1, ALL)
+        sim.sweeps(1, ALL)
+        gap = np.abs(_gpu_vectors(plan, 0, R) - sim.vectors()).max()
+        assert gap < 1e-12, (t, gap)
+        assert np.array_equal(plan.labels(), sim.labels())
+        np.testing.assert_allclose(plan.energies(), sim.energies(), rtol=1e-10, atol=1e-9)
+    g, o = plan.read_observables(), sim.accumulators()
+    np.testing.assert_allclose(g["acc"], o["acc"], rtol=1e-9, atol=1e-12)
+    assert np.array_equal(g["met_acc"], o["met_acc"]) and np.array_equal(g["pt_acc"], o["pt_acc"])
+    assert np.abs(o["acc"][:, 9]).max() > 0  # m_z is measured
+    assert plan.status() == (0, 10)
+
+
+def _direction_gap(a, b):
+    cos = np.clip((a * b).sum(-1) / (np.linalg.norm(a, axis=-1) * np.linalg.norm(b, axis=-1)), -1.0, 1.0)
+    return np.arccos(cos)
+
+
+@pytest.mark.parametrize("name", ["O1", "O2", "O2G"])
+def test_fp32_energy_matches_oracle(env, orc, name):
+    xyl, wl = env
+    cfg = wl.config(name)
+    plan, _ = wl.make_plan(cfg, xyl.FP32_PLAIN)
+    plan.bind()
+    plan.init_spins()
+    sim = _oracle(orc, wl, cfg, 0, u24=True)
+    R, N = cfg.n_temps, cfg.graphs[0][0] ** 2
+    assert np.abs(_gpu_vectors(plan, 0, R) - sim.vectors()).max() < 1e-7
+    compared = explained = 0
+    for t in range(10):
+        sim.set_vectors(_gpu_vectors(plan, 0, R))
+        sim.set_labels(plan.labels(), plan.status()[1])
+        sim.set_tie_eps(FP32_TIE_EPS)
+        sim.clear_ties()
+        plan.sweep(1, ALL)
+        sim.sweeps(1, ALL)
+        ties = sim.tie_counts()
+        _, pt_tie, _ = sim.ties()
+        gap = np.percentile(_direction_gap(_gpu_vectors(plan, 0, R), sim.vectors()), 99, axis=1)
+        dE = np.abs(plan.energies() - sim.energies()) / N
+        for r in range(R):
+            compared += 1
+            if dE[r] < 1e-5 and gap[r] < 1e-4:
+                continue
+            assert ties[r] > 0, (t, r, dE[r], gap[r])
+            explained += 1
+        if not np.array_equal(plan.labels(), sim.labels()):
+            assert pt_tie >= 0 or ties.sum() > 0, t
+    print(f"{name}: {compared} replica-sweeps, {explained} near-tie misses")
+    assert explained <= 0.2 * compared
+    assert plan.status() == (0, 10)
+
+
+@pytest.mark.parametrize("engine_name", ["FP32_PLAIN", "FP64_PLAIN"])
+def test_gauge_invariance_is_exact(env, engine_name):
+    xyl, wl = env
+    cfg = wl.config("O2G")
+    eng = getattr(xyl, engine_name)
+    g = wl.build_graphs(cfg)[0]
+    ei, ej = g.edges()
+    J = wl.couplings_for(cfg, 0, g.n_edges)
+    tau = np.random.default_rng(8).choice(np.array([-1, 1], np.int8), g.n)
+    gauged = xyl.build_graph_csr(128, 6, 3.5, wl.GRAPH_SEED, wl.graph_stream_id(cfg, 0))
+    gauged.set_couplings((tau[ei] * tau[ej] * J).astype(np.int8))
+    a, _ = wl.make_plan(cfg, eng, graphs=[g])
+    b, _ = wl.make_plan(cfg, eng, graphs=[gauged])
+    for p in (a, b):
+        p.bind()
+        p.init_spins()
+    for r in range(cfg.n_temps):
+        b.write_spins(0, r, a.spins(0, r) * tau[:, None].astype(np.float64))
+    a.recompute()
+    for _ in range(3):
+        a.sweep(4, ALL)
+        b.sweep(4, ALL)
+        for r in range(cfg.n_temps):
+            assert np.array_equal(b.spins(0, r), a.spins(0, r) * tau[:, None]), r
+        assert np.array_equal(a.labels(), b.labels())
+        np.testing.assert_allclose(a.energies(), b.energies(), rtol=1e-12, atol=0)
+    assert a.status() == b.status() == (0, 12)
+
+
+def test_random_tree_energy_is_the_langevin_law(env):
+    xyl, _ = env
+    rng = np.random.default_rng(21)
+    n, beta = 4096, 1.3
+    edges = np.array([(int(rng.integers(0, i)), i) for i in range(1, n)], np.int32)
+    g = xyl.graph_from_edges(n, edges)
+    plan = xyl.Plan([(g, 0, [beta] * 8, [2.0] * 8)], engine=xyl.FP32_PLAIN, seed=3, spin_dim=3)
+    plan.bind()
+    plan.init_spins()
+    plan.sweep(200, NO_PT)
+    plan.reset_observables()
+    plan.sweep(2000, NO_PT, 4)
+    acc = plan.read_observables()["acc"]
+    e = acc[:, 1] / acc[:, 0]
+    want = -(n - 1) * (1.0 / np.tanh(beta) - 1.0 / beta) / n
+    # 8 independent replicas: their spread bounds the statistical error
+    err = e.std(ddof=1) / np.sqrt(len(e))
+    assert abs(e.mean() - want) < 5 * err + 2e-5, (e.mean(), want, err)
+    assert plan.status() == (0, 2200)

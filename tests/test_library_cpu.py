@@ -227,3 +227,19 @@ def test_fields_are_validated(xyl):
     q = xyl.Plan([(g.set_fields(None), 0, [1.0, 0.5], [1.0, 1.0])], engine=xyl.FP32_BATCHED, device="cpu")
     # one float2 per site for the fields (an empty region still takes one 256-byte slot)
     assert p.workspace_bytes == q.workspace_bytes + 64 * 8 - 256
+
+
+def test_o3_plans_are_validated(xyl):
+    g = xyl.build_graph_csr(8, 6, 3.5, 1, 0)
+    for engine, kw in ((xyl.FP32_BATCHED, {"spin_dim": 3}), (xyl.FP32_PLAIN, {"spin_dim": 4})):
+        with pytest.raises(xyl.XylError) as e:
+            xyl.Plan([(g, 0, [1.0, 0.5], [1.0, 1.0])], engine=engine, device="cpu", **kw)
+        assert e.value.code == xyl.EINVAL
+    q = xyl.Plan([(g, 0, [1.0, 0.5], [1.0, 1.0])], engine=xyl.FP32_PLAIN, device="cpu")
+    p = xyl.Plan([(g, 0, [1.0, 0.5], [1.0, 1.0])], engine=xyl.FP32_PLAIN, device="cpu", spin_dim=3)
+    # spins are padded 4-vectors: 16 B instead of 8 B per (site, replica)
+    assert p.workspace_bytes == q.workspace_bytes + 2 * 64 * 8
+    g.set_fields(np.ones((64, 2)))
+    with pytest.raises(xyl.XylError) as e:
+        xyl.Plan([(g, 0, [1.0, 0.5], [1.0, 1.0])], engine=xyl.FP64_PLAIN, device="cpu", spin_dim=3)
+    assert e.value.code == xyl.EINVAL
