@@ -14,7 +14,9 @@ observables of Sec. III and the finite-size tools of Sec. IV and App. C:
 * ``fit_tf``: T_f(N) = T_c + A N^-x through crossing temperatures (Eq. Tfsscaling);
 * ``fit_nu_bar``: ln dU4/dT = c + (1/nu_bar) ln N at fixed U4 (Eq. scaling_lndotU4);
 * ``exponential_windows`` / ``window_means``: time averages over windows
-  [2^k, 2^(k+1)) of the measurement series, the paper's equilibration check.
+  [2^k, 2^(k+1)) of the measurement series, the paper's equilibration check;
+* ``heat_capacity_check``: the specific heat from fluctuations against the
+  temperature derivative of the energy, the paper's second equilibration check.
 """
 from __future__ import annotations
 
@@ -129,3 +131,14 @@ def window_means(series: np.ndarray, windows=None):
                      for a, b in windows])
     ok = bool(np.all(np.abs(means[-1] - means[-2]) < 3 * np.hypot(sems[-1], sems[-2]))) if len(windows) >= 2 else False
     return means, ok
+
+
+def heat_capacity_check(T, e, c):
+    """Specific heat per spin from fluctuations, c = N var(e) / T^2, against
+    d<e>/dT from the energy curve (second-order finite differences on the
+    possibly non-uniform temperature grid).  In equilibrium the two agree, as
+    d<E>/dT = var(E) / T^2.  Returns (d<e>/dT, relative difference)."""
+    T = np.asarray(T, np.float64)
+    dedT = np.gradient(np.asarray(e, np.float64), T)
+    c = np.asarray(c, np.float64)
+    return dedT, np.abs(dedT - c) / np.maximum(np.abs(c), 1e-300)

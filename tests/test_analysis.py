@@ -85,3 +85,21 @@ def test_exponential_windows_and_equilibration_check():
     assert ok
     _, ok = an.window_means(rng.normal(size=4096) + np.linspace(0, 5, 4096))
     assert not ok
+
+
+def test_heat_capacity_check_on_the_xy_dimer():
+    """Two XY spins, one bond: e = -I1(b)/I0(b) / 2 per spin, and
+    var(E) = <cos^2> - <cos>^2 with <cos^2> = (1 + I2/I0) / 2 (Bessel), so
+    c = N var(e) / T^2 = var(E) / (2 T^2) must equal de/dT."""
+    from scipy.special import iv
+    T = np.geomspace(0.5, 3.0, 400)
+    b = 1.0 / T
+    m1 = iv(1, b) / iv(0, b)
+    m2 = 0.5 * (1.0 + iv(2, b) / iv(0, b))
+    e = -0.5 * m1
+    c = (m2 - m1 ** 2) / (2.0 * T ** 2)
+    dedT, rel = an.heat_capacity_check(T, e, c)
+    assert rel[2:-2].max() < 1e-3
+    # an energy curve off by a temperature-dependent factor fails it
+    _, rel_bad = an.heat_capacity_check(T, e * (1 + 0.2 * T), c)
+    assert rel_bad[2:-2].max() > 0.05
