@@ -135,6 +135,8 @@ def test_gauge_invariance_is_exact(env, engine_name):
         p.init_spins()
     for r in range(cfg.n_temps):
         b.write_spins(0, r, a.spins(0, r) * tau[:, None].astype(np.float64))
+    # both renormalised the same way (xyl_recompute rescales every spin to |S| = 1)
+    b.recompute()
     a.recompute()
     for _ in range(3):
         a.sweep(4, ALL)
