@@ -100,6 +100,7 @@ class ClockSampler:
 KERNEL_SOURCES = {
     "batched_kernel": ["batched.cu"],
     "resident_kernel": ["resident.cu"],
+    "o3_phase_kernel": ["o3.cu"],
 }
 SHARED_SOURCES = ["engines.h", "device.cuh", "philox.cuh", "sweep_tail.cuh"]
 
