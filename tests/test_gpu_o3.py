@@ -167,3 +167,40 @@ def test_random_tree_energy_is_the_langevin_law(env):
     err = e.std(ddof=1) / np.sqrt(len(e))
     assert abs(e.mean() - want) < 5 * err + 2e-5, (e.mean(), want, err)
     assert plan.status() == (0, 2200)
+
+
+@pytest.mark.parametrize("engine_name", ["FP32_PLAIN", "FP64_PLAIN"])
+def test_degenerate_inputs(env, engine_name):
+    """No links, a single site, a zero Metropolis step, an odd number of slots."""
+    xyl, _ = env
+    eng = getattr(xyl, engine_name)
+
+    def plan_of(g, betas, deltas):
+        p = xyl.Plan([(g, 0, betas, deltas)], engine=eng, seed=4, spin_dim=3)
+        p.bind()
+        p.init_spins()
+        return p
+
+    # isolated spins: overrelaxation leaves them alone, every Metropolis move is accepted
+    p = plan_of(xyl.graph_from_edges(5, []), [1.0, 0.5, 2.0], [1.0, 1.0, 1.0])
+    s0 = np.stack([p.spins(0, r) for r in range(3)])
+    p.sweep(3, 2 | 4 | 8)
+    assert np.array_equal(np.stack([p.spins(0, r) for r in range(3)]), s0)
+    assert np.all(p.energies() == 0.0)
+    p.sweep(3, ALL)
+    st = p.read_observables()
+    assert np.array_equal(st["met_acc"], st["met_try"])
+    assert np.all(st["pt_acc"][:2] == st["pt_try"][:2])
+    v = np.stack([p.spins(0, r) for r in range(3)]).reshape(-1, 3)
+    assert np.allclose(np.linalg.norm(v, axis=1), 1, atol=1e-6) and np.abs(v[:, 2]).max() > 0
+    # one site, one slot: m^2 = 1 exactly at every measurement
+    p = plan_of(xyl.graph_from_edges(1, []), [1.0], [0.5])
+    p.sweep(4, ALL)
+    st = p.read_observables()
+    assert st["acc"][0, 0] == 4 and abs(st["acc"][0, 6] - 4.0) < 1e-5
+    # Delta = 0: the cap is the spin itself, Metropolis changes nothing
+    p = plan_of(xyl.build_graph_csr(8, 6, 3.5, 1, 0), [1.0, 0.7, 0.4], [0.0, 0.0, 0.0])
+    s0 = np.stack([p.spins(0, r) for r in range(3)])
+    p.sweep(5, 1 | 4 | 8)
+    assert np.max(np.abs(np.stack([p.spins(0, r) for r in range(3)]) - s0)) < 1e-6
+    assert p.status() == (0, 5)

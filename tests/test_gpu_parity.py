@@ -78,6 +78,8 @@ VARIANTS = {
     "FP32_SPLIT": ("FP32_BATCHED", {"resident": 1, "cluster": 4}),
     "FP32_GLOBAL": ("FP32_BATCHED", {"resident": -1}),
     "FP32_PLAIN": ("FP32_PLAIN", {}),
+    # the launch shape the benchmark's autotuner picks at C2
+    "FP32_BENCH": ("FP32_BATCHED", {"resident": 1, "group": 1, "cluster": 6, "block": 512}),
     "FP64_PLAIN": ("FP64_PLAIN", {}),
 }
 
@@ -170,6 +172,23 @@ def test_fp32_energy_matches_oracle(env, orc, name, engine_name):
     assert _angle_gap(_gpu_angles(plan, 0, cfg.n_temps), sims[0].angles()).max() < 1e-6
     compared, explained, worst = _fp32_per_sweep(plan, sims, [0], 10, ALL, lambda s: cfg.graphs[s][0] ** 2)
     print(f"{name} {engine_name}: {compared} replica-sweeps, {explained} near-tie misses, worst |dE|/N {worst:.2e}")
+    assert plan.status() == (0, 10)
+
+
+def test_fp32_energy_matches_oracle_in_the_benchmark_shape(env, orc):
+    """C2 in the launch shape the benchmark times (spins in shared memory, one
+    replica per group, six CTAs per replica, 512 threads)."""
+    xyl, wl = env
+    cfg = wl.config("C2")
+    eng, opts = _variant(xyl, "FP32_BENCH")
+    plan, _ = wl.make_plan(cfg, eng, **opts)
+    t = plan.tuning()
+    assert (t["resident"], t["group"], t["cluster"], t["block"]) == (1, 1, 6, 512)
+    plan.bind()
+    plan.init_spins()
+    sims = {0: _oracle_for(orc, wl, cfg, 0, u24=True)}
+    compared, explained, worst = _fp32_per_sweep(plan, sims, [0], 10, ALL, lambda s: cfg.graphs[s][0] ** 2)
+    print(f"C2 bench shape: {compared} replica-sweeps, {explained} near-tie misses, worst |dE|/N {worst:.2e}")
     assert plan.status() == (0, 10)
 
 
