@@ -438,6 +438,18 @@ int xyl_walk_returns(const int32_t *row_ptr, const int32_t *col, int32_t n, int6
                      int64_t n_walkers, uint32_t first_walker, int32_t n_steps, uint64_t seed, uint64_t *returns,
                      void *stream);
 
+/*
+ * xyl_philox -- the library's random generator, Philox4x32-10 (Salmon, Moraes,
+ * Dror & Shaw, SC'11: ten rounds, multipliers 0xD2511F53 / 0xCD9E8D57, key
+ * increments 0x9E3779B9 / 0xBB67AE85), one block per (counter, key) pair, so
+ * that the generator every stream draws from can be checked against other
+ * implementations.  Device pointers owned by the caller: ctr 4n words
+ * (16-byte aligned), key 2n words (8-byte aligned), out 4n words (16-byte
+ * aligned).  Asynchronous on `stream`.  Errors: XYL_EINVAL (n < 0, NULL or
+ * misaligned pointers), XYL_ECUDA.
+ */
+int xyl_philox(const uint32_t *ctr, const uint32_t *key, int64_t n, uint32_t *out, void *stream);
+
 /* Number of kernel launches the last xyl_sweep call issued (graph nodes count). */
 int64_t xyl_last_launch_count(const xyl_plan *p);
 

@@ -4,7 +4,7 @@ Every routine here only marshals numpy arrays into the C functions; the
 arithmetic lives in the C file, which cites the passages it follows.  Parity
 status of each function is recorded in its docstring; all of them are pinned by
 ``tests/test_oracle_*.py`` against closed forms, exact special cases, brute force
-or published known-answer values.
+or an independent implementation (cuRAND's Philox4x32-10).
 """
 from __future__ import annotations
 
@@ -100,7 +100,7 @@ def _ptr(a, ctype):
 def philox(ctr, key) -> np.ndarray:
     """Philox4x32-10 block for counter ``ctr`` (4 words) and key (2 words).
 
-    Pinned by the Random123 known-answer vectors (tests/golden/philox_kat.txt)."""
+    Pinned against cuRAND's host Philox4x32-10 generator (tests/test_oracle_philox.py)."""
     lib = _load()
     c = np.ascontiguousarray(ctr, dtype=np.uint32)
     k = np.ascontiguousarray(key, dtype=np.uint32)

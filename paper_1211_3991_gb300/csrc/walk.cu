@@ -9,6 +9,8 @@
 // dependent loads (row bounds, then the neighbour id), so the kernel is bound
 // by memory latency; every walker of a warp steps together, and a warp adds
 // its returns of a step with one atomic (ballot + popcount).
+//
+// Also here: xyl_philox, the raw generator of every random stream.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -51,10 +53,41 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const int32_t *__res
     }
 }
 
+// One Philox4x32-10 block per thread: the generator every stream of the
+// library draws from, exposed so that it can be checked against other
+// implementations.
+__global__ void philox_kernel(const uint32_t *__restrict__ ctr, const uint32_t *__restrict__ key, int64_t n,
+                              uint32_t *__restrict__ out)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const uint4 c = __ldg(reinterpret_cast<const uint4 *>(ctr) + q);
+    const uint2 k = __ldg(reinterpret_cast<const uint2 *>(key) + q);
+    const Words4 w = philox4x32_10(Words4{c.x, c.y, c.z, c.w}, k.x, k.y);
+    reinterpret_cast<uint4 *>(out)[q] = make_uint4(w.w0, w.w1, w.w2, w.w3);
+}
+
 }  // namespace
 }  // namespace xyl
 
 using namespace xyl;
+
+extern "C" int xyl_philox(const uint32_t *ctr, const uint32_t *key, int64_t n, uint32_t *out, void *stream)
+{
+    clear_error();
+    if (n < 0) return fail(XYL_EINVAL, "xyl_philox: n < 0");
+    if (n == 0) return XYL_OK;
+    if (!ctr || !key || !out) return fail(XYL_EINVAL, "xyl_philox: NULL pointer");
+    if ((reinterpret_cast<uintptr_t>(ctr) | reinterpret_cast<uintptr_t>(out)) % 16 ||
+        reinterpret_cast<uintptr_t>(key) % 8)
+        return fail(XYL_EINVAL, "xyl_philox: counters and outputs need 16-byte, keys 8-byte alignment");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t blocks = (n + 255) / 256;
+    if (blocks > 0x7fffffff) return fail(XYL_EINVAL, "xyl_philox: too many blocks");
+    philox_kernel<<<(unsigned)blocks, 256, 0, st>>>(ctr, key, n, out);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? XYL_OK : fail(XYL_ECUDA, "xyl_philox: %s", cudaGetErrorString(e));
+}
 
 extern "C" int xyl_walk_returns(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t nnz,
                                 const int32_t *start, int64_t n_walkers, uint32_t first_walker, int32_t n_steps,

@@ -29,7 +29,7 @@ EXPORTED = (
     "xyl_write_spins", "xyl_read_status", "xyl_state_bytes", "xyl_export_state", "xyl_import_state",
     "xyl_last_launch_count", "xyl_plan_free", "xyl_sweep_units", "xyl_unit_count", "xyl_autotune",
     "xyl_get_tuning", "xyl_sweep_noalloc", "xyl_build_levy_bonds", "xyl_walk_returns", "xyl_graph_set_couplings",
-    "xyl_graph_export_couplings", "xyl_graph_set_fields",
+    "xyl_graph_export_couplings", "xyl_graph_set_fields", "xyl_philox",
 )
 
 
@@ -105,6 +105,7 @@ def load():
             "xyl_graph_set_couplings": ([P, C.POINTER(C.c_int8)], C.c_int),
             "xyl_graph_export_couplings": ([P, C.POINTER(C.c_int8)], C.c_int),
             "xyl_graph_set_fields": ([P, pf64], C.c_int),
+            "xyl_philox": ([P, P, i64, P, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -139,6 +140,14 @@ def walk_returns(row_ptr, col, start, n_steps: int, seed: int, returns, first_wa
                                    col.numel(), C.c_void_p(start.data_ptr()), start.numel(), first_walker, n_steps,
                                    seed, C.c_void_p(returns.data_ptr()), _stream(stream)))
     return returns
+
+
+def philox(ctr, key, out, stream=None):
+    """Philox4x32-10 blocks on the device: ``ctr`` (n, 4) and ``key`` (n, 2)
+    uint32-valued int32 CUDA tensors, ``out`` (n, 4); argument marshalling only."""
+    _check(load().xyl_philox(C.c_void_p(ctr.data_ptr()), C.c_void_p(key.data_ptr()), ctr.shape[0],
+                             C.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
 
 
 # ----------------------------------------------------------------- graphs

@@ -5,6 +5,7 @@
   periodic trapezoid rule over relative angles (spectrally convergent for the
   smooth periodic Boltzmann weight), used to pin both samplers.
 * ``bessel_*``: closed forms of the open chain and the periodic ring.
+* ``paper_critical_temperatures``: the paper's printed T_c table (tests/golden).
 """
 from __future__ import annotations
 
@@ -161,3 +162,22 @@ def edges_chain(n):
 
 def edges_complete(n):
     return list(itertools.combinations(range(n), 2))
+
+
+def paper_critical_temperatures():
+    """The paper's Table criticalexponents (T_c from T_f and from U crosses, by
+    rho) and the analytic Erdos-Renyi T_c of Sec. IV, from
+    tests/golden/critical_temperatures.txt."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "critical_temperatures.txt")
+    rows, analytic = {}, None
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if not line:
+            continue
+        w = line.split()
+        if w[0] == "analytic_er":
+            analytic = float(w[1])
+            continue
+        rows[float(w[0])] = tuple(float(x) for x in w[1:5])
+    return rows, analytic

@@ -16,6 +16,8 @@ import pytest
 from scipy.optimize import brentq
 from scipy.special import iv
 
+from helpers import paper_critical_temperatures
+
 
 def cavity_tc(c=4.0):
     beta = brentq(lambda b: c * iv(1, b) / iv(0, b) - 1.0, 1e-3, 10.0)
@@ -23,7 +25,11 @@ def cavity_tc(c=4.0):
 
 
 def test_cavity_temperature_is_the_papers_analytic_value():
-    assert abs(cavity_tc(4.0) - 1.9361) < 5e-5
+    table, analytic = paper_critical_temperatures()
+    assert abs(cavity_tc(4.0) - analytic) < 5e-5
+    # and the paper's own crossing estimate at rho = 0 agrees with it
+    tc_u, err_u = table[0.0][2], table[0.0][3]
+    assert abs(tc_u - analytic) < err_u
     # large c: I1/I0 ~ beta/2, so T_c -> c/2 (the Gaussian mean-field value 2 at c = 4 is above it)
     assert abs(cavity_tc(400.0) - 200.0) / 200.0 < 1e-2
 
@@ -75,7 +81,9 @@ def test_u4_crossing_at_rho_zero_matches_analytic_tc():
     loo = np.array([_crossing(temps, a - b) for a, b in zip(loo_a, loo_b)])
     err = np.sqrt((S - 1) / S * np.nansum((loo - np.nanmean(loo)) ** 2))
     tc = cavity_tc(4.0)
-    print(f"U4 crossing L=32/64: {t_x:.4f} +- {err:.4f} (analytic {tc:.4f})")
+    table, _ = paper_critical_temperatures()
+    print(f"U4 crossing L=32/64: {t_x:.4f} +- {err:.4f} (analytic {tc:.4f}, paper {table[0.0][2]}({table[0.0][3]}))")
     assert np.isfinite(t_x) and err < 0.02
     # 3 sigma plus 0.01 for the finite-size shift of the crossing (O(N^-1/2) with nu_bar = 2)
     assert abs(t_x - tc) < 3 * err + 0.01, (t_x, err, tc)
+    assert abs(t_x - table[0.0][2]) < 3 * err + table[0.0][3] + 0.01

@@ -243,3 +243,12 @@ def test_o3_plans_are_validated(xyl):
     with pytest.raises(xyl.XylError) as e:
         xyl.Plan([(g, 0, [1.0, 0.5], [1.0, 1.0])], engine=xyl.FP64_PLAIN, device="cpu", spin_dim=3)
     assert e.value.code == xyl.EINVAL
+
+
+def test_philox_entry_rejects_bad_arguments(xyl):
+    import ctypes as C
+    lib = xyl.load()
+    assert lib.xyl_philox(None, None, -1, None, None) == xyl.EINVAL
+    assert lib.xyl_philox(None, None, 4, None, None) == xyl.EINVAL
+    assert lib.xyl_philox(None, None, 0, None, None) == 0
+    assert lib.xyl_philox(C.c_void_p(16), C.c_void_p(12), 1, C.c_void_p(32), None) == xyl.EINVAL  # key misaligned
