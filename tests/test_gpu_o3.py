@@ -204,3 +204,53 @@ def test_degenerate_inputs(env, engine_name):
     p.sweep(5, 1 | 4 | 8)
     assert np.max(np.abs(np.stack([p.spins(0, r) for r in range(3)]) - s0)) < 1e-6
     assert p.status() == (0, 5)
+
+
+def test_uneven_batch_each_sample_matches_its_oracle(env, orc):
+    """Two samples of different sizes (L = 16 and 24) and slot counts in one FP64
+    plan: each follows its own oracle run (streams keyed by its sample id)."""
+    xyl, wl = env
+    sizes, temps = [16, 24], [[0.9, 1.3, 1.8], [1.0, 1.5]]
+    graphs = [xyl.build_graph_csr(L, 6, 3.5, wl.GRAPH_SEED, k) for k, L in enumerate(sizes)]
+    samples = [(g, 10 + k, [1 / T for T in ts], [1.5] * len(ts)) for k, (g, ts) in enumerate(zip(graphs, temps))]
+    plan = xyl.Plan(samples, engine=xyl.FP64_PLAIN, seed=wl.SPIN_SEED, spin_dim=3)
+    plan.bind()
+    plan.init_spins()
+    sims = []
+    for k, (L, ts) in enumerate(zip(sizes, temps)):
+        ei, ej, _, _ = orc.levy_graph(L, 6, 3.5, wl.GRAPH_SEED, k)
+        color, _ = orc.slo_color(L * L, ei, ej)
+        sim = orc.Sim(L * L, ei, ej, color, [1 / T for T in ts], [1.5] * len(ts), wl.SPIN_SEED, sample=10 + k,
+                      xy=orc.lattice_xy(L), L=L, dim=3)
+        sim.init()
+        sims.append(sim)
+    plan.sweep(6, ALL)
+    for sim in sims:
+        sim.sweeps(6, ALL)
+    labels = plan.labels()
+    off = 0
+    for k, sim in enumerate(sims):
+        R = len(temps[k])
+        assert np.abs(_gpu_vectors(plan, k, R) - sim.vectors()).max() < 1e-12, k
+        assert np.array_equal(labels[off:off + R], sim.labels()), k
+        off += R
+
+
+def test_checkpoint_resumes_bit_for_bit(env):
+    xyl, wl = env
+    cfg = wl.config("O1")
+    a, _ = wl.make_plan(cfg, xyl.FP32_PLAIN)
+    a.bind()
+    a.init_spins()
+    a.sweep(5, ALL)
+    blob = a.export_state()
+    a.sweep(7, ALL)
+    want = (_gpu_vectors(a, 0, cfg.n_temps), a.labels(), a.read_observables()["acc"])
+    b, _ = wl.make_plan(cfg, xyl.FP32_PLAIN)
+    b.bind()
+    b.import_state(blob)
+    b.sweep(7, ALL)
+    got = (_gpu_vectors(b, 0, cfg.n_temps), b.labels(), b.read_observables()["acc"])
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+    np.testing.assert_allclose(got[2], want[2], rtol=1e-12)
+    assert b.status() == (0, 12)
