@@ -28,6 +28,7 @@ with J = +-1 at random (probability 1/2 each, the XY spin glass):
   O1  C1's graph with O(3) spins, 4 temperatures geometric in [0.9, 1.8]
   O2  C2's graph with O(3) spins, 16 temperatures geometric in [0.9, 1.8]
   O2G O2 with random +-1 couplings, 16 temperatures geometric in [0.4, 1.2]
+  O3  256 graphs L=64 (rho=3.5) with O(3) spins, 24 temperatures geometric in [0.9, 1.8]
 """
 from __future__ import annotations
 
@@ -125,6 +126,9 @@ def config(name: str) -> Config:
     if name == "O2":
         return Config("O2", [(128, 3.5, 0)], geometric_temperatures(0.9, 1.8, 16), spin_dim=3,
                       description="C2's graph with O(3) spins, 16 T geometric in [0.9,1.8]")
+    if name == "O3":
+        return Config("O3", [(64, 3.5, s) for s in range(256)], geometric_temperatures(0.9, 1.8, 24), spin_dim=3,
+                      description="256 graphs L=64 z=6 rho=3.5 with O(3) spins, 24 T geometric in [0.9,1.8]")
     if name == "O2G":
         return Config("O2G", [(128, 3.5, 0)], geometric_temperatures(0.4, 1.2, 16), spin_dim=3, couplings="pm",
                       description="C2's graph with O(3) spins and random +-1 couplings, 16 T geometric in [0.4,1.2]")
