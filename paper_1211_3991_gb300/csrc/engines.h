@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "device.cuh"
 
 namespace xyl {
@@ -14,6 +16,7 @@ struct PlanShape {
     int max_R = 0;
     int max_Q = 0;
     int max_class = 0;
+    std::vector<int> class_max;  // per colour index: largest class of that colour over the samples
     int max_N = 0;
     int layout = kReplicaMajor;
     bool fp64 = false;

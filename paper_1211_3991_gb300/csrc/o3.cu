@@ -13,6 +13,8 @@
 // the same as the oracle's.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "engines.h"
 
 namespace xyl {
@@ -334,21 +336,25 @@ template <typename Real, bool DISORDER>
 cudaError_t o3_sweep_impl(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every, cudaStream_t st,
                           int64_t *launches)
 {
-    dim3 grid((S.max_class + kO3Block - 1) / kO3Block, S.max_R, S.n_samples);
+    // each colour phase gets blocks for the largest class of that colour only
+    auto grid = [&](int c) {
+        const int sites = c < (int)S.class_max.size() ? S.class_max[c] : S.max_class;
+        return dim3((unsigned)std::max(1, (sites + kO3Block - 1) / kO3Block), S.max_R, S.n_samples);
+    };
     const bool met = ops & XYL_OP_MET, orx = ops & XYL_OP_OR;
     int64_t n = 0;
     if (met) {
         for (int c = 0; c < S.max_Q; ++c) {
             if (orx)
-                o3_phase_kernel<Real, true, false, DISORDER><<<grid, kO3Block, 0, st>>>(P, c);
+                o3_phase_kernel<Real, true, false, DISORDER><<<grid(c), kO3Block, 0, st>>>(P, c);
             else
-                o3_phase_kernel<Real, true, true, DISORDER><<<grid, kO3Block, 0, st>>>(P, c);
+                o3_phase_kernel<Real, true, true, DISORDER><<<grid(c), kO3Block, 0, st>>>(P, c);
             ++n;
         }
     }
     if (orx) {
         for (int c = 0; c < S.max_Q; ++c) {
-            o3_phase_kernel<Real, false, true, DISORDER><<<grid, kO3Block, 0, st>>>(P, c);
+            o3_phase_kernel<Real, false, true, DISORDER><<<grid(c), kO3Block, 0, st>>>(P, c);
             ++n;
         }
     }

@@ -6,6 +6,8 @@
 // reference GPU kernel) and FP32.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "engines.h"
 
 namespace xyl {
@@ -133,21 +135,25 @@ template <typename Real, bool DISORDER>
 cudaError_t sweep_impl(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every, cudaStream_t st,
                        int64_t *launches)
 {
-    dim3 grid((S.max_class + kPlainBlock - 1) / kPlainBlock, S.max_R, S.n_samples);
+    // each colour phase gets blocks for the largest class of that colour only
+    auto grid = [&](int c) {
+        const int sites = c < (int)S.class_max.size() ? S.class_max[c] : S.max_class;
+        return dim3((unsigned)std::max(1, (sites + kPlainBlock - 1) / kPlainBlock), S.max_R, S.n_samples);
+    };
     const bool met = ops & XYL_OP_MET, orx = ops & XYL_OP_OR;
     int64_t n = 0;
     if (met) {
         for (int c = 0; c < S.max_Q; ++c) {
             if (orx)
-                plain_phase_kernel<Real, true, false, DISORDER><<<grid, kPlainBlock, 0, st>>>(P, c);
+                plain_phase_kernel<Real, true, false, DISORDER><<<grid(c), kPlainBlock, 0, st>>>(P, c);
             else
-                plain_phase_kernel<Real, true, true, DISORDER><<<grid, kPlainBlock, 0, st>>>(P, c);
+                plain_phase_kernel<Real, true, true, DISORDER><<<grid(c), kPlainBlock, 0, st>>>(P, c);
             ++n;
         }
     }
     if (orx) {
         for (int c = 0; c < S.max_Q; ++c) {
-            plain_phase_kernel<Real, false, true, DISORDER><<<grid, kPlainBlock, 0, st>>>(P, c);
+            plain_phase_kernel<Real, false, true, DISORDER><<<grid(c), kPlainBlock, 0, st>>>(P, c);
             ++n;
         }
     }

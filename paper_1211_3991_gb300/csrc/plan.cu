@@ -461,8 +461,11 @@ int xyl_plan_create(const xyl_sample *samples, int32_t n_samples, int32_t engine
         p->shape.max_R = std::max(p->shape.max_R, h.R);
         p->shape.max_Q = std::max(p->shape.max_Q, h.Q);
         p->shape.max_N = std::max(p->shape.max_N, h.N);
-        for (int c = 0; c < h.Q; ++c)
+        if ((int)p->shape.class_max.size() < h.Q) p->shape.class_max.resize(h.Q, 0);
+        for (int c = 0; c < h.Q; ++c) {
             p->shape.max_class = std::max(p->shape.max_class, h.color_ptr[c + 1] - h.color_ptr[c]);
+            p->shape.class_max[c] = std::max(p->shape.class_max[c], h.color_ptr[c + 1] - h.color_ptr[c]);
+        }
         p->hs.push_back(std::move(h));
     }
     p->shape.n_samples = n_samples;
