@@ -21,6 +21,7 @@ namespace xyl {
 namespace {
 
 constexpr int kO3Block = 256;
+constexpr int kGather = 4;  // neighbour loads in flight per thread
 constexpr uint32_t kMetSecondBlock = 0x800000u;
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTwoPi = 6.283185307179586476925286766559;
@@ -140,22 +141,34 @@ __global__ void __launch_bounds__(kO3Block) o3_phase_kernel(DevPlan P, int c)
         const V si = sp[i];
         Real hx = 0, hy = 0, hz = 0;
         const int rb = rp[i], re = rp[i + 1];
-        for (int k = rb; k < re; ++k) {
-            const int raw = cl[k];
-            const int j = DISORDER ? (raw & 0x7fffffff) : raw;
-            V sj = sp[j];
-            if (DISORDER && raw < 0) {
-                sj.x = -sj.x;
-                sj.y = -sj.y;
-                sj.z = -sj.z;
-            }
-            hx += sj.x;
-            hy += sj.y;
-            hz += sj.z;
-            if (FUSE && j < cb) {
-                lx += sj.x;
-                ly += sj.y;
-                lz += sj.z;
+        // neighbours in groups of kGather: every id of a group, then every spin,
+        // are in flight together; the sums still run in row order
+        for (int k0 = rb; k0 < re; k0 += kGather) {
+            int raw[kGather];
+            V sv[kGather];
+#pragma unroll
+            for (int q = 0; q < kGather; ++q) raw[q] = k0 + q < re ? cl[k0 + q] : 0;
+#pragma unroll
+            for (int q = 0; q < kGather; ++q)
+                if (k0 + q < re) sv[q] = sp[DISORDER ? (raw[q] & 0x7fffffff) : raw[q]];
+#pragma unroll
+            for (int q = 0; q < kGather; ++q) {
+                if (k0 + q >= re) break;
+                const int j = DISORDER ? (raw[q] & 0x7fffffff) : raw[q];
+                V sj = sv[q];
+                if (DISORDER && raw[q] < 0) {
+                    sj.x = -sj.x;
+                    sj.y = -sj.y;
+                    sj.z = -sj.z;
+                }
+                hx += sj.x;
+                hy += sj.y;
+                hz += sj.z;
+                if (FUSE && j < cb) {
+                    lx += sj.x;
+                    ly += sj.y;
+                    lz += sj.z;
+                }
             }
         }
         if (IS_MET) {

@@ -14,6 +14,7 @@ namespace xyl {
 namespace {
 
 constexpr int kPlainBlock = 256;
+constexpr int kGather = 4;  // neighbour loads in flight per thread
 
 template <typename Real>
 __device__ __forceinline__ Vec2<Real> make_vec2(Real x, Real y);
@@ -50,19 +51,31 @@ __global__ void __launch_bounds__(kPlainBlock) plain_phase_kernel(DevPlan P, int
         const V si = sp[i];
         Real hx = 0, hy = 0;
         const int rb = rp[i], re = rp[i + 1];
-        for (int k = rb; k < re; ++k) {
-            const int raw = cl[k];
-            const int j = DISORDER ? (raw & 0x7fffffff) : raw;
-            V sj = sp[j];
-            if (DISORDER && raw < 0) {
-                sj.x = -sj.x;
-                sj.y = -sj.y;
-            }
-            hx += sj.x;
-            hy += sj.y;
-            if (FUSE && j < cb) {
-                lx += sj.x;
-                ly += sj.y;
+        // neighbours in groups of kGather: every id of a group, then every spin,
+        // are in flight together; the sums still run in row order
+        for (int k0 = rb; k0 < re; k0 += kGather) {
+            int raw[kGather];
+            V sv[kGather];
+#pragma unroll
+            for (int q = 0; q < kGather; ++q) raw[q] = k0 + q < re ? cl[k0 + q] : 0;
+#pragma unroll
+            for (int q = 0; q < kGather; ++q)
+                if (k0 + q < re) sv[q] = sp[DISORDER ? (raw[q] & 0x7fffffff) : raw[q]];
+#pragma unroll
+            for (int q = 0; q < kGather; ++q) {
+                if (k0 + q >= re) break;
+                const int j = DISORDER ? (raw[q] & 0x7fffffff) : raw[q];
+                V sj = sv[q];
+                if (DISORDER && raw[q] < 0) {
+                    sj.x = -sj.x;
+                    sj.y = -sj.y;
+                }
+                hx += sj.x;
+                hy += sj.y;
+                if (FUSE && j < cb) {
+                    lx += sj.x;
+                    ly += sj.y;
+                }
             }
         }
         if (DISORDER && P.field) {
