@@ -56,11 +56,10 @@ __global__ void reset_labels_kernel(DevPlan P)
 // obs[buffer], attempts the PT swaps of pairs (k, k+1), k = t mod 2 (App. B:
 // accept iff u < exp((beta_k - beta_k+1)(E_k - E_k+1)), FP64), adds one
 // measurement per slot when due, updates the counters and clears the buffer.
-__global__ void finalize_kernel(DevPlan P, uint32_t ops, int measure_every, int advance, int buffer_mode, int dim,
-                                int s0)
+__global__ void finalize_kernel(DevPlan P, uint32_t ops, int measure_every, int advance, int buffer_mode, int dim)
 {
     extern __shared__ double sh[];
-    const int s = s0 + (int)blockIdx.x;
+    const int s = blockIdx.x;
     const DevSample d = P.samples[s];
     const int R = d.R;
     double *E = sh;
@@ -259,12 +258,10 @@ cudaError_t launch_init(const DevPlan &P, const PlanShape &S, int aligned, cudaS
 }
 
 cudaError_t launch_finalize(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every, int advance,
-                            int buffer_mode, cudaStream_t st, int s0, int ns)
+                            int buffer_mode, cudaStream_t st)
 {
-    if (ns < 0) ns = S.n_samples - s0;
-    if (ns <= 0) return cudaSuccess;
     const size_t smem = (size_t)S.max_R * (sizeof(double) + sizeof(int));
-    finalize_kernel<<<ns, 128, smem, st>>>(P, ops, measure_every, advance, buffer_mode, S.dim, s0);
+    finalize_kernel<<<S.n_samples, 128, smem, st>>>(P, ops, measure_every, advance, buffer_mode, S.dim);
     return cudaGetLastError();
 }
 

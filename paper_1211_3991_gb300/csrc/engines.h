@@ -60,19 +60,17 @@ constexpr int kMaxDevicesNoAlloc = 64;
 cudaError_t batched_noalloc_scratch(void **ptr);
 
 cudaError_t launch_init(const DevPlan &P, const PlanShape &S, int aligned, cudaStream_t st);
-// Samples [s0, s0 + ns) (ns < 0: every sample from s0 on).
 cudaError_t launch_finalize(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every, int advance,
-                            int obs_buf_from_sweep, cudaStream_t st, int s0 = 0, int ns = -1);
+                            int obs_buf_from_sweep, cudaStream_t st);
 cudaError_t launch_recompute(const DevPlan &P, const PlanShape &S, int renormalise, int obs_buf_from_sweep,
                              cudaStream_t st);
-// One sweep of samples [s0, s0 + ns) on the plain engines (every phase, then finalize).
 cudaError_t launch_plain_sweep(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every,
-                               cudaStream_t st, int64_t *launches, int s0, int ns);
+                               cudaStream_t st, int64_t *launches);
 
 // O(3) spins (plain engines): initialisation, one sweep, FP64 recompute.
 cudaError_t launch_o3_init(const DevPlan &P, const PlanShape &S, int aligned, cudaStream_t st);
 cudaError_t launch_o3_sweep(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every,
-                            cudaStream_t st, int64_t *launches, int s0, int ns);
+                            cudaStream_t st, int64_t *launches);
 cudaError_t launch_o3_recompute(const DevPlan &P, const PlanShape &S, int renormalise, int buffer_mode,
                                 cudaStream_t st);
 

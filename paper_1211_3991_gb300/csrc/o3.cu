@@ -118,11 +118,11 @@ __global__ void o3_init_kernel(DevPlan P, int fp64, int aligned)
 // spins; FUSE, DISORDER and the per-block reduction as in the XY plain kernel,
 // with the z component's magnetisation and Fourier sums added.
 template <typename Real, bool IS_MET, bool FUSE, bool DISORDER>
-__global__ void __launch_bounds__(kO3Block) o3_phase_kernel(DevPlan P, int c, int s0)
+__global__ void __launch_bounds__(kO3Block) o3_phase_kernel(DevPlan P, int c)
 {
     using V = Vec3<Real>;
     using V4 = Vec4<Real>;
-    const int s = s0 + (int)blockIdx.z, r = blockIdx.y;
+    const int s = blockIdx.z, r = blockIdx.y;
     const DevSample d = P.samples[s];
     if (r >= d.R || c >= d.Q) return;
     const int cb = P.color_ptr[d.color_off + c], ce = P.color_ptr[d.color_off + c + 1];
@@ -347,33 +347,33 @@ __global__ void o3_recompute_kernel(DevPlan P, int fp64, int renormalise, int bu
 
 template <typename Real, bool DISORDER>
 cudaError_t o3_sweep_impl(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every, cudaStream_t st,
-                          int64_t *launches, int s0, int ns)
+                          int64_t *launches)
 {
     // each colour phase gets blocks for the largest class of that colour only
     auto grid = [&](int c) {
         const int sites = c < (int)S.class_max.size() ? S.class_max[c] : S.max_class;
-        return dim3((unsigned)std::max(1, (sites + kO3Block - 1) / kO3Block), S.max_R, (unsigned)ns);
+        return dim3((unsigned)std::max(1, (sites + kO3Block - 1) / kO3Block), S.max_R, S.n_samples);
     };
     const bool met = ops & XYL_OP_MET, orx = ops & XYL_OP_OR;
     int64_t n = 0;
     if (met) {
         for (int c = 0; c < S.max_Q; ++c) {
             if (orx)
-                o3_phase_kernel<Real, true, false, DISORDER><<<grid(c), kO3Block, 0, st>>>(P, c, s0);
+                o3_phase_kernel<Real, true, false, DISORDER><<<grid(c), kO3Block, 0, st>>>(P, c);
             else
-                o3_phase_kernel<Real, true, true, DISORDER><<<grid(c), kO3Block, 0, st>>>(P, c, s0);
+                o3_phase_kernel<Real, true, true, DISORDER><<<grid(c), kO3Block, 0, st>>>(P, c);
             ++n;
         }
     }
     if (orx) {
         for (int c = 0; c < S.max_Q; ++c) {
-            o3_phase_kernel<Real, false, true, DISORDER><<<grid(c), kO3Block, 0, st>>>(P, c, s0);
+            o3_phase_kernel<Real, false, true, DISORDER><<<grid(c), kO3Block, 0, st>>>(P, c);
             ++n;
         }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = launch_finalize(P, S, ops, measure_every, 1, 0, st, s0, ns);
+    e = launch_finalize(P, S, ops, measure_every, 1, 0, st);
     ++n;
     if (launches) *launches += n;
     return e;
@@ -389,13 +389,13 @@ cudaError_t launch_o3_init(const DevPlan &P, const PlanShape &S, int aligned, cu
 }
 
 cudaError_t launch_o3_sweep(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every, cudaStream_t st,
-                            int64_t *launches, int s0, int ns)
+                            int64_t *launches)
 {
     if (S.coupled)
-        return S.fp64 ? o3_sweep_impl<double, true>(P, S, ops, measure_every, st, launches, s0, ns)
-                      : o3_sweep_impl<float, true>(P, S, ops, measure_every, st, launches, s0, ns);
-    return S.fp64 ? o3_sweep_impl<double, false>(P, S, ops, measure_every, st, launches, s0, ns)
-                  : o3_sweep_impl<float, false>(P, S, ops, measure_every, st, launches, s0, ns);
+        return S.fp64 ? o3_sweep_impl<double, true>(P, S, ops, measure_every, st, launches)
+                      : o3_sweep_impl<float, true>(P, S, ops, measure_every, st, launches);
+    return S.fp64 ? o3_sweep_impl<double, false>(P, S, ops, measure_every, st, launches)
+                  : o3_sweep_impl<float, false>(P, S, ops, measure_every, st, launches);
 }
 
 cudaError_t launch_o3_recompute(const DevPlan &P, const PlanShape &S, int renormalise, int buffer_mode,

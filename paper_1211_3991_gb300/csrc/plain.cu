@@ -28,11 +28,11 @@ template <> __device__ __forceinline__ double2 make_vec2<double>(double x, doubl
 // neighbour's spin enters the local field negated, exactly J * S_j), and a
 // site field, when the plan has one, is added after the neighbours.
 template <typename Real, bool IS_MET, bool FUSE, bool DISORDER>
-__global__ void __launch_bounds__(kPlainBlock) plain_phase_kernel(DevPlan P, int c, int s0)
+__global__ void __launch_bounds__(kPlainBlock) plain_phase_kernel(DevPlan P, int c)
 {
     using V = Vec2<Real>;
     using V4 = Vec4<Real>;
-    const int s = s0 + (int)blockIdx.z, r = blockIdx.y;
+    const int s = blockIdx.z, r = blockIdx.y;
     const DevSample d = P.samples[s];
     if (r >= d.R || c >= d.Q) return;
     const int cb = P.color_ptr[d.color_off + c], ce = P.color_ptr[d.color_off + c + 1];
@@ -146,33 +146,33 @@ __global__ void __launch_bounds__(kPlainBlock) plain_phase_kernel(DevPlan P, int
 
 template <typename Real, bool DISORDER>
 cudaError_t sweep_impl(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every, cudaStream_t st,
-                       int64_t *launches, int s0, int ns)
+                       int64_t *launches)
 {
     // each colour phase gets blocks for the largest class of that colour only
     auto grid = [&](int c) {
         const int sites = c < (int)S.class_max.size() ? S.class_max[c] : S.max_class;
-        return dim3((unsigned)std::max(1, (sites + kPlainBlock - 1) / kPlainBlock), S.max_R, (unsigned)ns);
+        return dim3((unsigned)std::max(1, (sites + kPlainBlock - 1) / kPlainBlock), S.max_R, S.n_samples);
     };
     const bool met = ops & XYL_OP_MET, orx = ops & XYL_OP_OR;
     int64_t n = 0;
     if (met) {
         for (int c = 0; c < S.max_Q; ++c) {
             if (orx)
-                plain_phase_kernel<Real, true, false, DISORDER><<<grid(c), kPlainBlock, 0, st>>>(P, c, s0);
+                plain_phase_kernel<Real, true, false, DISORDER><<<grid(c), kPlainBlock, 0, st>>>(P, c);
             else
-                plain_phase_kernel<Real, true, true, DISORDER><<<grid(c), kPlainBlock, 0, st>>>(P, c, s0);
+                plain_phase_kernel<Real, true, true, DISORDER><<<grid(c), kPlainBlock, 0, st>>>(P, c);
             ++n;
         }
     }
     if (orx) {
         for (int c = 0; c < S.max_Q; ++c) {
-            plain_phase_kernel<Real, false, true, DISORDER><<<grid(c), kPlainBlock, 0, st>>>(P, c, s0);
+            plain_phase_kernel<Real, false, true, DISORDER><<<grid(c), kPlainBlock, 0, st>>>(P, c);
             ++n;
         }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = launch_finalize(P, S, ops, measure_every, 1, 0, st, s0, ns);
+    e = launch_finalize(P, S, ops, measure_every, 1, 0, st);
     ++n;
     if (launches) *launches += n;
     return e;
@@ -181,15 +181,14 @@ cudaError_t sweep_impl(const DevPlan &P, const PlanShape &S, uint32_t ops, int m
 }  // namespace
 
 cudaError_t launch_plain_sweep(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every,
-                               cudaStream_t st, int64_t *launches, int s0, int ns)
+                               cudaStream_t st, int64_t *launches)
 {
-    if (ns <= 0) return cudaSuccess;
-    if (S.dim == 3) return launch_o3_sweep(P, S, ops, measure_every, st, launches, s0, ns);
+    if (S.dim == 3) return launch_o3_sweep(P, S, ops, measure_every, st, launches);
     if (S.disorder)
-        return S.fp64 ? sweep_impl<double, true>(P, S, ops, measure_every, st, launches, s0, ns)
-                      : sweep_impl<float, true>(P, S, ops, measure_every, st, launches, s0, ns);
-    return S.fp64 ? sweep_impl<double, false>(P, S, ops, measure_every, st, launches, s0, ns)
-                  : sweep_impl<float, false>(P, S, ops, measure_every, st, launches, s0, ns);
+        return S.fp64 ? sweep_impl<double, true>(P, S, ops, measure_every, st, launches)
+                      : sweep_impl<float, true>(P, S, ops, measure_every, st, launches);
+    return S.fp64 ? sweep_impl<double, false>(P, S, ops, measure_every, st, launches)
+                  : sweep_impl<float, false>(P, S, ops, measure_every, st, launches);
 }
 
 }  // namespace xyl

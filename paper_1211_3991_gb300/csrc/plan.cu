@@ -52,7 +52,6 @@ struct xyl_plan {
     int total_Q1 = 0;
     std::vector<int2> units;
     int wave_units = 0;
-    std::vector<int2> plain_waves;  // plain engines: (first sample, count) of each wave
     size_t ws_bytes = 0;
     char *ws = nullptr;
     bool bound = false;
@@ -134,22 +133,6 @@ void layout(xyl_plan *p)
     // random fields: one vector per site, only when some sample has them
     take(p->r_field, p->shape.fields ? p->total_N * (p->shape.fp64 ? sizeof(double2) : sizeof(float2)) : 0);
     p->ws_bytes = off;
-    // plain engines: consecutive samples whose spins and tables fit in a third
-    // of the L2 form a wave; a wave runs its sweeps before the next one starts
-    constexpr size_t kPlainWaveBytes = 40u << 20;
-    p->plain_waves.clear();
-    size_t wave_bytes = 0;
-    for (int s = 0; s < (int)S; ++s) {
-        const HostSample &h = p->hs[s];
-        const size_t bytes = (size_t)h.N * h.R * p->spin_elem() + (size_t)h.N * (3 * sizeof(int32_t) + 32) +
-                             h.col.size() * sizeof(int32_t);
-        if (p->plain_waves.empty() || wave_bytes + bytes > kPlainWaveBytes) {
-            p->plain_waves.push_back(make_int2(s, 0));
-            wave_bytes = 0;
-        }
-        p->plain_waves.back().y++;
-        wave_bytes += bytes;
-    }
 }
 
 template <typename T>
@@ -666,11 +649,8 @@ int issue_sweeps(xyl_plan *p, int n, uint32_t ops, int measure_every, cudaStream
         }
         return XYL_OK;
     }
-    // samples are independent: each wave runs all n sweeps while its spins stay in L2
-    for (const int2 &w : p->plain_waves)
-        for (int k = 0; k < n; ++k)
-            XYL_CUDA(launch_plain_sweep(p->dev, p->shape, ops, measure_every, st, launches, w.x, w.y),
-                     "sweep: plain launch");
+    for (int k = 0; k < n; ++k)
+        XYL_CUDA(launch_plain_sweep(p->dev, p->shape, ops, measure_every, st, launches), "sweep: plain launch");
     return XYL_OK;
 }
 
@@ -706,7 +686,7 @@ int64_t launches_of(xyl_plan *p, int n, uint32_t ops)
         return ((int64_t)p->units.size() + p->wave_units - 1) / p->wave_units;
     const int64_t per_sweep = (int64_t)(((ops & XYL_OP_MET) ? p->shape.max_Q : 0) +
                                         ((ops & XYL_OP_OR) ? p->shape.max_Q : 0) + 1);
-    return per_sweep * n * (int64_t)p->plain_waves.size();
+    return per_sweep * n;
 }
 
 int do_recompute(xyl_plan *p, int renormalise, cudaStream_t st)

@@ -650,35 +650,3 @@ def test_degenerate_inputs(env, engine_name):
     p.sweep(5, 1 | 4 | 8)
     assert np.max(np.abs(np.stack([p.spins(0, r) for r in range(3)]) - s0)) < 1e-6
     assert p.status() == (0, 5)
-
-
-def test_plain_engine_sample_waves(env, orc):
-    """The plain engines run large batches in waves of consecutive samples (a
-    wave's spins stay in L2 for all its sweeps).  30 samples of L = 64 x 24
-    slots in FP64 make two waves: the last sample of each follows its own oracle
-    run bit for bit; and in FP32 the waves give the batched engine's spins."""
-    xyl, wl = env
-    base = wl.config("C3")
-    cfg = wl.Config("W30", base.graphs[:30], base.temperatures)
-    plan, graphs = wl.make_plan(cfg, xyl.FP64_PLAIN)
-    plan.bind()
-    plan.init_spins()
-    plan.sweep(3, ALL)
-    assert plan.last_launch_count() >= 2 * 3 * (2 * 5 + 1)  # at least two waves of 3 sweeps
-    for k in (0, 29):
-        sim = _oracle_for(orc, wl, cfg, k, u24=False)
-        sim.sweeps(3, ALL)
-        got = _gpu_angles(plan, k, cfg.n_temps)
-        assert _angle_gap(got, sim.angles()).max() < 1e-9, k
-        assert np.array_equal(plan.labels()[_rep_slice(plan, k)], sim.labels()), k
-    assert plan.status() == (0, 3)
-    cfg = wl.Config("W60", base.graphs[:60], base.temperatures)
-    graphs = wl.build_graphs(cfg)
-    spins = []
-    for eng, opts in ((xyl.FP32_PLAIN, {}), (xyl.FP32_BATCHED, {"resident": -1})):
-        p, _ = wl.make_plan(cfg, eng, graphs=graphs, **opts)
-        p.bind()
-        p.init_spins()
-        p.sweep(4, NO_PT)
-        spins.append(np.stack([p.spins(k, r) for k in (0, 37, 59) for r in range(cfg.n_temps)]))
-    assert np.array_equal(spins[0], spins[1])
