@@ -241,10 +241,11 @@ typedef struct {
  * replicas of one sample and keeps their spins of every site in shared memory
  * for the whole launch ((n + 1) x group x 8 bytes, with the per-warp partial
  * sums, within 220 KB); the n_temps / group CTAs of a sample form one cluster
- * (at most 16), so every sample must have the same n_temps and degree <= 8.
- * Colour phases then touch no global memory; the CSR rows (16-bit ids) and
- * the site ids are staged beside the spins when they fit (stage >= 0), else
- * read from global memory.  Spins are bit-equal to the global-memory shape's
+ * (at most 16), so every sample must have the same n_temps.  Colour phases
+ * then touch no global memory but the CSR: rows of up to eight neighbours
+ * (16-bit ids) and the site ids are staged beside the spins when they fit
+ * (stage >= 0), else read from global memory, and longer rows (the 2N-bond
+ * graphs) are read from the global CSR entry by entry.  Spins are bit-equal to the global-memory shape's
  * from the same state.  On input `cluster` is ignored for this shape; on output
  * (xyl_get_tuning, xyl_autotune) it holds the cluster size.  The library's
  * choice (resident = 0) is the resident shape when it fits with group >= 1,

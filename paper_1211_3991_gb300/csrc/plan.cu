@@ -166,7 +166,7 @@ bool resident_fit(const xyl_plan *p, int g, int G, int block, int stage, Batched
         for (int c = 0; c < h.Q; ++c) o += (h.color_ptr[c + 1] - h.color_ptr[c] + G - 1) / G;
         owned = std::max(owned, o);
     }
-    if (R0 % g || max_deg > 8) return false;
+    if (R0 % g) return false;
     const int n_groups = R0 / g;
     auto a16 = [](size_t v) { return (v + 15) / 16 * 16; };
     const size_t n_warps = (size_t)block / 32;
@@ -196,8 +196,10 @@ bool resident_fit(const xyl_plan *p, int g, int G, int block, int stage, Batched
         }
         const int W = B.fixed_deg == 6 ? 6 : 8;
         const size_t col = a16((size_t)owned * W * sizeof(uint16_t));
-        // with couplings bit 15 of a staged id holds J, so ids (and the padding id N) stay below 2^15
-        if (stage >= 0 && off + col <= kResidentDynLimitBytes && (!p->shape.coupled || max_N <= 32767)) {
+        // with couplings bit 15 of a staged id holds J, so ids (and the padding id N) stay below 2^15;
+        // rows longer than eight are read from the global CSR
+        if (stage >= 0 && max_deg <= 8 && off + col <= kResidentDynLimitBytes &&
+            (!p->shape.coupled || max_N <= 32767)) {
             B.rs_csr_w = W;
             B.rs_off_col = off;
             off += col;
@@ -247,7 +249,7 @@ int apply_shape(xyl_plan *p, int g, int G, int block, int stage, int resident)
         for (int k = 0; k < p->hs[s].R / g; ++k) p->units.push_back(make_int2((int)s, k));
     if (resident) {
         if (!resident_fit(p, g, G, block, stage, B))
-            return fail(XYL_EINVAL, "resident shape with group=%d does not fit this batch (equal n_temps, degree <= 8, "
+            return fail(XYL_EINVAL, "resident shape with group=%d does not fit this batch (equal n_temps, "
                         "a group's spins within %zu B of shared memory)", g, kResidentDynLimitBytes);
         return XYL_OK;
     }
@@ -287,7 +289,7 @@ int pick_batched_shape(xyl_plan *p, const xyl_tuning *tune)
             }
         }
         if (mode == 1)
-            return fail(XYL_EINVAL, "resident shape does not fit this batch (equal n_temps, degree <= 8, a group's "
+            return fail(XYL_EINVAL, "resident shape does not fit this batch (equal n_temps, a group's "
                         "spins within %zu B of shared memory)", kResidentDynLimitBytes);
         clear_error();
     }

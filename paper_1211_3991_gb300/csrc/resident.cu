@@ -24,7 +24,8 @@
 // spins from the same state; only the order of the energy sums differs.  The
 // CSR rows of a CTA's own sites (16-bit ids) and their random-stream site ids
 // are staged in shared memory when they fit beside the spins; otherwise they
-// are read through the read-only path, one item ahead.
+// are read through the read-only path, one item ahead.  Rows longer than eight
+// (the paper's 2N-bond graphs) are read from the global CSR entry by entry.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -80,6 +81,15 @@ struct Row {
     uint32_t neg;
 };
 
+// DEG = 0 (any degree): the row's place in the global CSR, read entry by entry.
+template <>
+struct Row<0> {
+    int rb, deg;
+    uint32_t key;
+    uint32_t peers;
+    uint32_t neg;
+};
+
 struct Stage {
     const uint16_t *col;    // [owned][csr_w] colour-sorted ids, padding -> N (a zero spin); J = -1 in bit 15 (DISORDER)
     const uint16_t *ids;    // [owned] original ids
@@ -94,7 +104,10 @@ __device__ __forceinline__ void fetch_row(const DevPlan &P, const DevSample &d, 
 {
     constexpr int W = DEG > 0 ? DEG : 8;
     row.neg = 0u;
-    if (stg.col) {
+    if constexpr (DEG == 0) {
+        row.rb = __ldg(P.row_ptr + d.row_off + i);
+        row.deg = __ldg(P.row_ptr + d.row_off + i + 1) - row.rb;
+    } else if (stg.col) {
         // rows of W 16-bit ids, 4-byte aligned (W even)
         const uint32_t *c = reinterpret_cast<const uint32_t *>(stg.col + (size_t)l * W);
 #pragma unroll
@@ -223,23 +236,54 @@ __device__ __forceinline__ void rphase(const DevPlan &P, const DevSample &d, con
         float hx[RV], hy[RV], lx[RV], ly[RV];
 #pragma unroll
         for (int v = 0; v < RV; ++v) hx[v] = hy[v] = lx[v] = ly[v] = 0.f;
+        if constexpr (DEG == 0) {
+            // any degree: ids from the global CSR in groups of four, sums in row order
+            const int32_t *cl = P.col + d.col_off + cur.rb;
+            for (int k0 = 0; k0 < cur.deg; k0 += 4) {
+                int raw[4];
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-            const int j = cur.nb[k];
-            float2 sj[RV];
-            lds_spins<RV>(spl + j * Rg, sj);
-            if (DISORDER && ((cur.neg >> k) & 1u)) {
+                for (int q = 0; q < 4; ++q) raw[q] = k0 + q < cur.deg ? __ldg(cl + k0 + q) : 0;
 #pragma unroll
-                for (int v = 0; v < RV; ++v) sj[v] = make_float2(-sj[v].x, -sj[v].y);
+                for (int q = 0; q < 4; ++q) {
+                    if (k0 + q >= cur.deg) break;
+                    const int j = DISORDER ? (raw[q] & 0x7fffffff) : raw[q];
+                    float2 sj[RV];
+                    lds_spins<RV>(spl + j * Rg, sj);
+                    if (DISORDER && raw[q] < 0) {
+#pragma unroll
+                        for (int v = 0; v < RV; ++v) sj[v] = make_float2(-sj[v].x, -sj[v].y);
+                    }
+                    const bool lower = FUSE_E && j < cb;
+#pragma unroll
+                    for (int v = 0; v < RV; ++v) {
+                        hx[v] += sj[v].x;
+                        hy[v] += sj[v].y;
+                        if (lower) {
+                            lx[v] += sj[v].x;
+                            ly[v] += sj[v].y;
+                        }
+                    }
+                }
             }
-            const bool lower = FUSE_E && j < cb;
+        } else {
 #pragma unroll
-            for (int v = 0; v < RV; ++v) {
-                hx[v] += sj[v].x;
-                hy[v] += sj[v].y;
-                if (lower) {
-                    lx[v] += sj[v].x;
-                    ly[v] += sj[v].y;
+            for (int k = 0; k < W; ++k) {
+                const int j = cur.nb[k];
+                float2 sj[RV];
+                lds_spins<RV>(spl + j * Rg, sj);
+                if (DISORDER && ((cur.neg >> k) & 1u)) {
+#pragma unroll
+                    for (int v = 0; v < RV; ++v) sj[v] = make_float2(-sj[v].x, -sj[v].y);
+                }
+                const bool lower = FUSE_E && j < cb;
+#pragma unroll
+                for (int v = 0; v < RV; ++v) {
+                    hx[v] += sj[v].x;
+                    hy[v] += sj[v].y;
+                    if (lower) {
+                        lx[v] += sj[v].x;
+                        ly[v] += sj[v].y;
+                    }
                 }
             }
         }
@@ -579,6 +623,7 @@ KernelFn pick_split(const BatchedShape &B)
 {
     const bool rv2 = B.Rg >= 2;
     if (B.fixed_deg == 6) return rv2 ? pick_width<2, 6, SPLIT, DISORDER>(B) : pick_width<1, 6, SPLIT, DISORDER>(B);
+    if (B.max_deg > 8) return rv2 ? pick_width<2, 0, SPLIT, DISORDER>(B) : pick_width<1, 0, SPLIT, DISORDER>(B);
     return rv2 ? pick_width<2, -8, SPLIT, DISORDER>(B) : pick_width<1, -8, SPLIT, DISORDER>(B);
 }
 

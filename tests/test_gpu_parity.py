@@ -192,19 +192,16 @@ def test_fp32_energy_matches_oracle_in_the_benchmark_shape(env, orc):
     assert plan.status() == (0, 10)
 
 
-@pytest.mark.parametrize("engine_name", ["FP32_GLOBAL", "FP32_PLAIN"])
+@pytest.mark.parametrize("engine_name", ["FP32_RESIDENT", "FP32_SPLIT", "FP32_GLOBAL", "FP32_PLAIN"])
 @pytest.mark.parametrize("name", ["E1", "E2"])
 def test_fp32_energy_matches_oracle_bond_ensemble(env, orc, name, engine_name):
     """The paper's 2N-bond graphs (Sec. II): free degrees up to 11 here, so
-    the batched engine runs its any-degree global-memory kernel; the shared-
-    memory shape, limited to degree 8, refuses them."""
+    both batched shapes run their any-degree kernels (rows read from the
+    global CSR entry by entry)."""
     xyl, wl = env
     cfg = wl.config(name)
     graphs = wl.build_graphs(cfg)
     assert graphs[0].max_deg > 8
-    with pytest.raises(xyl.XylError) as e:
-        wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, resident=1)
-    assert e.value.code == xyl.EINVAL
     eng, opts = _variant(xyl, engine_name)
     plan, _ = wl.make_plan(cfg, eng, graphs=graphs, **opts)
     plan.bind()
@@ -542,6 +539,34 @@ def test_launch_shape_does_not_change_the_trajectory(env):
     p.init_spins()
     p.sweep(6, NO_PT)
     assert np.array_equal(np.stack([p.spins(0, r) for r in range(cfg.n_temps)]), ref[0])
+
+
+def test_any_degree_shapes_give_the_same_spins(env):
+    """On the paper's 2N-bond graphs (degrees above 8): the resident shape (one
+    CTA, two, or four per group), the global-memory shape and the FP32 plain
+    engine perform the same per-site arithmetic, bit for bit."""
+    xyl, wl = env
+    cfg = wl.Config("B8", [(64, 10.0 / 3.0, s) for s in range(8)], wl.geometric_temperatures(1.4, 2.0, 12),
+                    ensemble="bonds")
+    graphs = wl.build_graphs(cfg)
+    assert max(g.max_deg for g in graphs) > 8
+    ref = None
+    for eng, shp in ((xyl.FP32_BATCHED, dict(group=4, resident=1)), (xyl.FP32_BATCHED, dict(group=2, resident=1)),
+                     (xyl.FP32_BATCHED, dict(group=1, cluster=4, resident=1)),
+                     (xyl.FP32_BATCHED, dict(group=4, cluster=2, block=1024, resident=1)),
+                     (xyl.FP32_BATCHED, dict(group=4, cluster=2, resident=-1)), (xyl.FP32_PLAIN, {})):
+        p, _ = wl.make_plan(cfg, eng, graphs=graphs, **shp)
+        if eng == xyl.FP32_BATCHED:
+            assert p.tuning()["resident"] == shp["resident"], shp
+        p.bind()
+        p.init_spins()
+        p.sweep(5, NO_PT)
+        got = np.stack([p.spins(k, r) for k in range(cfg.n_samples) for r in range(cfg.n_temps)])
+        if ref is None:
+            ref = got
+        else:
+            assert np.array_equal(got, ref), shp
+        assert p.status() == (0, 5)
 
 
 def test_replica_pairs_same_spins_in_every_shape(env):
