@@ -45,6 +45,7 @@ struct BatchedShape {
     int rs_csr_w = 0;       // staged CSR row width (16-bit ids), 0 = rows from global memory
     bool rs_ids = false;    // random-stream site ids staged (16-bit)
     size_t rs_off_ids = 0, rs_off_col = 0, rs_off_part = 0, rs_off_met = 0, rs_off_peers = 0;
+    size_t rs_off_beta = 0; // FP64 slot inverse temperatures of the sample
 };
 
 // Shared memory a CTA may use for staged CSR rows.

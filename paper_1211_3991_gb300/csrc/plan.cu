@@ -173,10 +173,12 @@ bool resident_fit(const xyl_plan *p, int g, int G, int block, int stage, Batched
     const size_t spins = a16((size_t)(max_N + 1) * g * sizeof(float2));
     const size_t part = a16((size_t)kObsCount * n_warps * g * sizeof(float));
     const size_t met = a16(n_warps * g * sizeof(unsigned));
-    size_t off = spins + part + met;
+    const size_t beta = a16((size_t)R0 * sizeof(double));
+    size_t off = spins + part + met + beta;
     if (off > kResidentDynLimitBytes) return false;
     B.rs_off_part = spins;
     B.rs_off_met = spins + part;
+    B.rs_off_beta = spins + part + met;
     B.rs_ids = false;
     B.rs_csr_w = 0;
     B.rs_off_ids = B.rs_off_col = B.rs_off_peers = 0;

@@ -53,6 +53,7 @@ struct ResidentParams {
     int n_warps;
     // dynamic shared memory layout (byte offsets)
     int off_ids, off_col, off_part, off_met, off_peers;  // off_peers 0: masks read from global memory
+    int off_beta;        // FP64 slot inverse temperatures (parallel tempering)
     int csr_w;           // staged CSR row width (6 or 8), 0 = rows read from global memory
     int ids;             // random-stream site ids staged as 16-bit values
 };
@@ -357,7 +358,8 @@ __device__ __forceinline__ unsigned warp_reduce_rep(const ResidentParams &rp, un
 template <int RV, int DEG, bool SPLIT, bool DISORDER>
 __device__ __forceinline__ void resident_sweeps(const DevPlan &P, const ResidentParams &rp, ResidentShared &sh,
                                                 const Stage &stg, cg::cluster_group &cluster, const Place &pl,
-                                                float2 *sp, float *part, unsigned *part_met, int s, int group)
+                                                float2 *sp, float *part, unsigned *part_met, const double *beta64,
+                                                int s, int group)
 {
     const DevSample d = P.samples[s];
     const int R = d.R, Rg = rp.Rg;
@@ -490,7 +492,7 @@ __device__ __forceinline__ void resident_sweeps(const DevPlan &P, const Resident
         if (global_barrier && *(volatile int *)&sh.abort_flag) break;
         for (int k = threadIdx.x; k < R; k += blockDim.x) sh.E[k] = __ldcg(obs_s + (size_t)k * kObsStride + kObsE);
         __syncthreads();
-        pt_and_record(P, d, sh.E, sh.rep_at, sh.slot_of, t, rp.ops, leader, met, measure, obs_s);
+        pt_and_record(P, d, sh.E, sh.rep_at, sh.slot_of, t, rp.ops, leader, met, measure, obs_s, beta64);
         if (SPLIT && pl.sr == 0) {
             // clear this group's slots of the buffer the next sweep adds into:
             // every reader of it finished before the barrier just passed
@@ -519,11 +521,13 @@ __device__ __forceinline__ void resident_body(const DevPlan &P, const ResidentPa
     const DevSample d = P.samples[s];
     const int R = d.R, Rg = rp.Rg, N = d.N;
 
+    double *beta64 = reinterpret_cast<double *>(dyn + rp.off_beta);
     for (int k = threadIdx.x; k < R; k += blockDim.x) {
         sh.slot_of[k] = P.slot_of[d.rep_off + k];
         sh.rep_at[k] = P.rep_at[d.rep_off + k];
         sh.beta[k] = (float)P.beta[d.rep_off + k];
         sh.delta[k] = (float)P.delta[d.rep_off + k];
+        beta64[k] = P.beta[d.rep_off + k];
     }
     if (threadIdx.x == 0) {
         sh.abort_flag = 0;
@@ -584,7 +588,7 @@ __device__ __forceinline__ void resident_body(const DevPlan &P, const ResidentPa
     // peers write into this CTA's copy only after it holds the starting spins
     if (SPLIT) cluster.sync();
     else __syncthreads();
-    resident_sweeps<RV, DEG, SPLIT, DISORDER>(P, rp, sh, stg, cluster, pl, sp, part, part_met, s, group);
+    resident_sweeps<RV, DEG, SPLIT, DISORDER>(P, rp, sh, stg, cluster, pl, sp, part, part_met, beta64, s, group);
     // write this CTA's own sites back (every copy agrees after the last barrier)
     float2 *gspw = reinterpret_cast<float2 *>(P.spins) + d.spin_off + group * Rg;
     for (int c = 0; c < d.Q; ++c) {
@@ -690,6 +694,7 @@ cudaError_t launch_resident(const DevPlan &P, const BatchedShape &B, const int2 
     rp.off_col = (int)B.rs_off_col;
     rp.off_part = (int)B.rs_off_part;
     rp.off_met = (int)B.rs_off_met;
+    rp.off_beta = (int)B.rs_off_beta;
     rp.off_peers = (int)B.rs_off_peers;
     rp.csr_w = B.rs_csr_w;
     rp.ids = B.rs_ids ? 1 : 0;

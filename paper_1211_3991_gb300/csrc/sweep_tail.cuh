@@ -34,28 +34,32 @@ __device__ __forceinline__ bool pt_accept(double u, double x)
 // the parity of t swap their replicas with probability min(1, exp((b_k -
 // b_k+1)(E_k - E_k+1))), one PT draw per pair (FP64 arithmetic and 53-bit
 // uniforms).  E is indexed by replica, rep_at / slot_of are this CTA's copies
-// of the labels.  The leader then writes the labels and energies back and, on
+// of the labels, beta_s the slots' FP64 inverse temperatures in shared memory
+// (NULL: read from the plan).  The leader's counters are fire-and-forget
+// atomics, so no read of global memory sits on its path.  The leader then writes the labels and energies back and, on
 // measurement sweeps, adds e, e^2, |m|, m_x, m_y, m^2, m^4 and chi(k_min) of
 // each slot (Sec. III) from the per-replica sums obs_s.
 __device__ __forceinline__ void pt_and_record(const DevPlan &P, const DevSample &d, const double *E, int *rep_at,
                                               int *slot_of, uint32_t t, uint32_t ops, bool leader, bool met,
-                                              bool measure, const double *obs_s)
+                                              bool measure, const double *obs_s, const double *beta_s = nullptr)
 {
     const int R = d.R;
     if (ops & XYL_OP_PT) {
         for (int p = threadIdx.x; 2 * p + (int)(t & 1u) + 1 < R; p += blockDim.x) {
             const int k = 2 * p + (int)(t & 1u);
             const int a = rep_at[k], b = rep_at[k + 1];
-            const double x = (P.beta[d.rep_off + k] - P.beta[d.rep_off + k + 1]) * (E[a] - E[b]);
+            const double bk = beta_s ? beta_s[k] : P.beta[d.rep_off + k];
+            const double bk1 = beta_s ? beta_s[k + 1] : P.beta[d.rep_off + k + 1];
+            const double x = (bk - bk1) * (E[a] - E[b]);
             const Words4 w = philox_draw((uint32_t)k, t, kPurposePt, 0u, d.sample_id, P.key);
             const bool accept = pt_accept(uniform53(w.w0, w.w1), x);
-            if (leader) P.pt_try[d.rep_off + k] += 1ull;
+            if (leader) atomicAdd(&P.pt_try[d.rep_off + k], 1ull);
             if (accept) {
                 rep_at[k] = b;
                 rep_at[k + 1] = a;
                 slot_of[b] = k;
                 slot_of[a] = k + 1;
-                if (leader) P.pt_acc[d.rep_off + k] += 1ull;
+                if (leader) atomicAdd(&P.pt_acc[d.rep_off + k], 1ull);
             }
         }
         __syncthreads();
@@ -67,7 +71,7 @@ __device__ __forceinline__ void pt_and_record(const DevPlan &P, const DevSample 
         P.rep_at[d.rep_off + k] = r;
         P.slot_of[d.rep_off + r] = k;
         P.last_E[d.rep_off + k] = E[k];
-        if (met) P.met_try[d.rep_off + k] += (unsigned long long)d.N;
+        if (met) atomicAdd(&P.met_try[d.rep_off + k], (unsigned long long)d.N);
         if (measure) {
             const double *o = obs_s + (size_t)r * kObsStride;
             const double e = E[r] * invN;
