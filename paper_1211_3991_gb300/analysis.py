@@ -15,6 +15,8 @@ observables of Sec. III and the finite-size tools of Sec. IV and App. C:
 * ``fit_nu_bar``: ln dU4/dT = c + (1/nu_bar) ln N at fixed U4 (Eq. scaling_lndotU4);
 * ``exponential_windows`` / ``window_means``: time averages over windows
   [2^k, 2^(k+1)) of the measurement series, the paper's equilibration check;
+* ``window_histogram_check``: the distributions of an observable over the last
+  two exponential windows against each other (two-sample Kolmogorov-Smirnov);
 * ``heat_capacity_check``: the specific heat from fluctuations against the
   temperature derivative of the energy, the paper's second equilibration check.
 """
@@ -131,6 +133,21 @@ def window_means(series: np.ndarray, windows=None):
                      for a, b in windows])
     ok = bool(np.all(np.abs(means[-1] - means[-2]) < 3 * np.hypot(sems[-1], sems[-2]))) if len(windows) >= 2 else False
     return means, ok
+
+
+def window_histogram_check(series, windows=None):
+    """The equilibration check on distributions: the values of one observable
+    in the last two exponential windows are compared by a two-sample
+    Kolmogorov-Smirnov test (measurements far enough apart to be nearly
+    independent, e.g. every 32 sweeps).  Returns (statistic, p-value)."""
+    from scipy import stats
+    s = np.asarray(series, np.float64)
+    windows = windows or exponential_windows(len(s))
+    if len(windows) < 2:
+        raise ValueError("need at least two exponential windows")
+    (a0, a1), (b0, b1) = windows[-2], windows[-1]
+    res = stats.ks_2samp(s[a0:a1], s[b0:b1])
+    return float(res.statistic), float(res.pvalue)
 
 
 def heat_capacity_check(T, e, c):

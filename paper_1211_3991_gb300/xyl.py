@@ -305,7 +305,7 @@ class Plan:
         t = Tuning()
         _check(load().xyl_get_tuning(self.handle, C.byref(t)))
         return {"block": t.block, "cluster": t.cluster, "group": t.group, "stage": t.stage,
-                "resident": t.resident, "recompute_every": t.recompute_every}
+                "resident": t.resident, "recompute_every": t.recompute_every, "spin_dim": t.spin_dim}
 
     # same method names as the oracle sampler, so tests drive both the same way
     def sweeps(self, n, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1):

@@ -103,3 +103,17 @@ def test_heat_capacity_check_on_the_xy_dimer():
     # an energy curve off by a temperature-dependent factor fails it
     _, rel_bad = an.heat_capacity_check(T, e * (1 + 0.2 * T), c)
     assert rel_bad[2:-2].max() > 0.05
+
+
+def test_window_histograms_of_a_stationary_and_a_drifting_series():
+    rng = np.random.default_rng(5)
+    x = rng.standard_cauchy(4096)  # heavy tails: a distribution check, not a moment check
+    _, p = an.window_histogram_check(x)
+    assert p > 1e-3
+    # same mean, wider spread in the last window: the means agree, the histograms do not
+    y = x.copy()
+    y[2048:] *= 3.0
+    _, p = an.window_histogram_check(y)
+    assert p < 1e-6
+    with pytest.raises(ValueError):
+        an.window_histogram_check(np.ones(3))

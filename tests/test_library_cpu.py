@@ -252,3 +252,22 @@ def test_philox_entry_rejects_bad_arguments(xyl):
     assert lib.xyl_philox(None, None, 4, None, None) == xyl.EINVAL
     assert lib.xyl_philox(None, None, 0, None, None) == 0
     assert lib.xyl_philox(C.c_void_p(16), C.c_void_p(12), 1, C.c_void_p(32), None) == xyl.EINVAL  # key misaligned
+
+
+def test_launch_shape_choice_on_the_host(xyl):
+    """Shape selection is host logic: the resident shape takes graphs of any
+    degree (the 2N-bond ensemble reaches 11 and more) with rows read from the
+    global CSR, stages 16-bit rows only up to degree 8, and O(3) plans report
+    their spin dimension."""
+    bonds = xyl.build_levy_bonds(32, 0.0, 1, 0)
+    assert bonds.max_deg > 8
+    p = xyl.Plan([(bonds, 0, [1.0] * 8, [1.0] * 8)], engine=xyl.FP32_BATCHED, device="cpu")
+    t = p.tuning()
+    assert t["resident"] == 1 and t["stage"] == -1 and t["group"] == 8
+    fixed = xyl.build_graph_csr(32, 6, 3.5, 1, 0)
+    t = xyl.Plan([(fixed, 0, [1.0] * 8, [1.0] * 8)], engine=xyl.FP32_BATCHED, device="cpu").tuning()
+    assert t["resident"] == 1 and t["stage"] == 1
+    t = xyl.Plan([(bonds, 0, [1.0] * 8, [1.0] * 8)], engine=xyl.FP32_BATCHED, device="cpu", resident=-1).tuning()
+    assert t["resident"] == -1
+    t = xyl.Plan([(fixed, 0, [1.0] * 2, [1.0] * 2)], engine=xyl.FP32_PLAIN, device="cpu", spin_dim=3).tuning()
+    assert t["spin_dim"] == 3
