@@ -58,6 +58,8 @@ def _load():
         lib.orc_sim_set_couplings.argtypes = [P, f64p]
         lib.orc_sim_set_fields.argtypes = [P, f64p]
         lib.orc_sim_set_dim.argtypes = [P, C.c_int]
+        lib.orc_reflect.argtypes = [C.c_int, f64p, f64p, f64p]
+        lib.orc_reflect.restype = None
         lib.orc_o3_propose.argtypes = [C.c_double] * 6 + [f64p, f64p, f64p]
         lib.orc_o3_propose.restype = None
         lib.orc_walk_returns.argtypes = [C.c_int, i32p, i32p, C.c_int64, i32p, C.c_int32, C.c_uint64, u64p]
@@ -402,6 +404,17 @@ def graph_sim(ei, ej, n, beta, delta, seed, sample=0, xy=None, L=None, u24=False
     """Sampler on an explicit edge list, coloured by ``slo_color``."""
     color, _ = slo_color(n, ei, ej)
     return Sim(n, ei, ej, color, beta, delta, seed, sample=sample, xy=xy, L=L, u24=u24, dim=dim)
+
+
+def reflect(s, h) -> np.ndarray:
+    """The overrelaxation map: the reflection of spin ``s`` (2 or 3
+    components) about the local field ``h``."""
+    lib = _load()
+    sv = np.ascontiguousarray(s, np.float64)
+    hv = np.ascontiguousarray(h, np.float64)
+    out = np.zeros_like(sv)
+    lib.orc_reflect(len(sv), _ptr(sv, C.c_double), _ptr(hv, C.c_double), _ptr(out, C.c_double))
+    return out
 
 
 def o3_propose(s, half_width: float, u: float, uphi: float) -> np.ndarray:

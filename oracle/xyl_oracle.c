@@ -1120,6 +1120,7 @@ int orc_sim_set_couplings(orc_sim *s, const double *j_per_bond)
 
 static void metropolis_site_o3(orc_sim *s, int r, int v);
 static void overrelax_site_o3(orc_sim *s, int r, int v);
+void orc_reflect(int dim, const double *sv, const double *h, double *out);
 
 static void metropolis_site(orc_sim *s, int r, int v)
 {
@@ -1165,20 +1166,38 @@ static void metropolis_site(orc_sim *s, int r, int v)
     }
 }
 
+/*
+ * Overrelaxation map (App. B, "Improved equilibrium dynamics", Creutz): the
+ * reflection of a spin about its local field, s' = 2 (s.h) h / |h|^2 - s, for
+ * dim = 2 or 3 components (sums left to right); s is returned unchanged when
+ * h = 0.  It conserves s.h (hence the energy) and |s|, and applying it twice
+ * gives s back.
+ */
+void orc_reflect(int dim, const double *sv, const double *h, double *out)
+{
+    double h2 = h[0] * h[0] + h[1] * h[1];
+    double sh = sv[0] * h[0] + sv[1] * h[1];
+    if (dim == 3) {
+        h2 += h[2] * h[2];
+        sh += sv[2] * h[2];
+    }
+    if (!(h2 > 0.0)) {
+        for (int a = 0; a < dim; ++a) out[a] = sv[a];
+        return;
+    }
+    const double k = 2.0 * sh / h2;
+    for (int a = 0; a < dim; ++a) out[a] = k * h[a] - sv[a];
+}
+
 static void overrelax_site(orc_sim *s, int r, int v)
 {
     if (s->dim == 3) { overrelax_site_o3(s, r, v); return; }
     double *x = s->vx + (size_t)r * s->n, *y = s->vy + (size_t)r * s->n;
-    double hx, hy;
-    local_field(s, x, y, v, &hx, &hy);
-    double h2 = hx * hx + hy * hy;
-    if (h2 > 0.0) {
-        double k = 2.0 * (x[v] * hx + y[v] * hy) / h2;
-        double nx = k * hx - x[v];
-        double ny = k * hy - y[v];
-        x[v] = nx;
-        y[v] = ny;
-    }
+    double h[2], sv[2] = { x[v], y[v] }, out[2];
+    local_field(s, x, y, v, &h[0], &h[1]);
+    orc_reflect(2, sv, h, out);
+    x[v] = out[0];
+    y[v] = out[1];
 }
 
 static void parallel_tempering(orc_sim *s)
@@ -1520,14 +1539,10 @@ static void metropolis_site_o3(orc_sim *s, int r, int v)
 static void overrelax_site_o3(orc_sim *s, int r, int v)
 {
     const size_t q = (size_t)r * s->n + v;
-    double hx, hy, hz;
-    local_field3(s, r, v, &hx, &hy, &hz);
-    const double h2 = hx * hx + hy * hy + hz * hz;
-    if (h2 > 0.0) {
-        const double x = s->vx[q], y = s->vy[q], z = s->vz[q];
-        const double k = 2.0 * (x * hx + y * hy + z * hz) / h2;
-        s->vx[q] = k * hx - x;
-        s->vy[q] = k * hy - y;
-        s->vz[q] = k * hz - z;
-    }
+    double h[3], sv[3] = { s->vx[q], s->vy[q], s->vz[q] }, out[3];
+    local_field3(s, r, v, &h[0], &h[1], &h[2]);
+    orc_reflect(3, sv, h, out);
+    s->vx[q] = out[0];
+    s->vy[q] = out[1];
+    s->vz[q] = out[2];
 }

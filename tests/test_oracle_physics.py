@@ -209,3 +209,24 @@ def test_sampler_is_deterministic(orc):
         s.sweeps(20, ALL)
     assert np.array_equal(sims[0].angles(), sims[1].angles())
     assert np.array_equal(sims[0].labels(), sims[1].labels())
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_overrelaxation_map_is_an_energy_conserving_involution(orc, dim):
+    """The reflection about the local field keeps |s| and s.h (so the energy),
+    turns s about h by pi (s' + s is parallel to h), and applied twice gives s
+    back; with h = 0 the spin is left as it is."""
+    rng = np.random.default_rng(dim)
+    for _ in range(500):
+        s = rng.normal(size=dim)
+        s /= np.linalg.norm(s)
+        h = rng.normal(size=dim) * rng.uniform(0.01, 6.0)
+        r = orc.reflect(s, h)
+        assert abs(np.linalg.norm(r) - 1.0) < 1e-14
+        assert abs(r @ h - s @ h) < 1e-13 * (1 + np.abs(h).sum())
+        par = (r + s) - ((r + s) @ h) / (h @ h) * h
+        assert np.abs(par).max() < 1e-13
+        np.testing.assert_allclose(orc.reflect(r, h), s, atol=1e-14)
+        assert np.abs(r - s).max() > 0 or abs(abs(s @ h) - np.linalg.norm(h)) < 1e-12
+    s = rng.normal(size=dim)
+    assert np.array_equal(orc.reflect(s, np.zeros(dim)), s)
