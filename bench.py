@@ -101,6 +101,7 @@ KERNEL_SOURCES = {
     "batched_kernel": ["batched.cu"],
     "resident_kernel": ["resident.cu"],
     "o3_phase_kernel": ["o3.cu"],
+    "walk_kernel": ["walk.cu"],
 }
 SHARED_SOURCES = ["engines.h", "device.cuh", "philox.cuh", "sweep_tail.cuh"]
 
@@ -295,6 +296,9 @@ def walk_bench(args):
             n_cpu += chunk
         cpu = {"value": n_cpu * T / dt, "unit": "walker-steps/s", "cores": 1, "kind": "oracle",
                "sample": f"{n_cpu} of the walkers, {T} steps ({dt:.1f} s, one thread)"}
+    # DRAM bytes of one launch from the committed ncu summary (one launch = one step of W walkers)
+    prof = _profile_traffic("walk_kernel", "walk")
+    walk_traffic = prof["bytes_per_launch"] if prof and W == 1 << 20 and T == 1000 else None
     if rank == 0:
         print(json.dumps({
             "metric": WALK_METRIC, "value": value, "unit": "walker-steps/s", "n_gpus": world, "steps": args.steps,
@@ -303,7 +307,7 @@ def walk_bench(args):
             "config": {"workload": f"one 2N-bond Levy graph per rank, L={L}, rho=10/3, periodic; {W} walkers x {T} "
                        "steps per step, starts on nodes of degree > 2", "l2": "CSR (5 MB) L2-resident by design"},
             "roofline": {"bound": "hbm", "achieved": 12.0 * value / world / 1e9, "peak": peak, "unit": "GB/s",
-                         "frac": 12.0 * value / world / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
+                         "frac": 12.0 * value / world / 1e9 / peak, "traffic": walk_traffic, "peak_kind": peak_kind,
                          "bytes_per_update": 12.0, "kernel": "walk_kernel",
                          "note": "two dependent L2 gathers per step: latency-bound, not HBM-bound"},
             "cpu_baseline": cpu,
