@@ -27,6 +27,7 @@
  *   orc_csr()           Colour-sorted CSR (App. B, "Memory management": sites of
  *                       one colour stored consecutively).
  *   orc_sincos_series() sin/cos of the Metropolis step by their Maclaurin series.
+ *   orc_reflect()       The overrelaxation map (App. B, Creutz reflection).
  *   orc_sim_set_dim()   O(3) spins (three components), the first of the "other
  *                       continuous models" the method carries over to (App. B).
  *   orc_sim_*()         Monte Carlo sweeps of H = -sum_{i<j} J_ij S_i.S_j,
