@@ -185,21 +185,23 @@ def run_oracle_sample(cfg, sweeps=0, seconds=0.0, measure_every=32, chunk=25, ma
 
 
 def _oracle_worker(job):
-    name, k, seconds, measure_every = job
+    name, k, sweeps, seconds, measure_every = job
     from paper_1211_3991_gb300 import workloads as wl
-    ups, dt, done = run_oracle_sample(wl.config(name), seconds=seconds, measure_every=measure_every, sample_index=k)
-    return ups, dt, done
+    return run_oracle_sample(wl.config(name), sweeps=sweeps, seconds=seconds, measure_every=measure_every,
+                             sample_index=k)
 
 
-def run_oracle_parallel(cfg, seconds, measure_every, procs):
+def run_oracle_parallel(cfg, seconds, measure_every, procs, sweeps=0):
     """The oracle on samples 0..procs-1 of a multi-sample workload, one process
     per sample on the host cores (spawned, so safe after GPU work), all running
-    at once.  Returns (site-updates/s summed over processes, sweeps per process)."""
+    at once: `sweeps` sweeps each, or (sweeps = 0) about `seconds` each.
+    Returns (site-updates/s summed over processes, [(site-updates, seconds,
+    sweeps)] per process)."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     with ctx.Pool(procs) as pool:
-        res = pool.map(_oracle_worker, [(cfg.name, k, seconds, measure_every) for k in range(procs)])
-    return sum(u / dt for u, dt, _ in res), [n for _, _, n in res]
+        res = pool.map(_oracle_worker, [(cfg.name, k, sweeps, seconds, measure_every) for k in range(procs)])
+    return sum(u / dt for u, dt, _ in res), res
 
 
 def reference_arm(args, cfg):
@@ -209,21 +211,29 @@ def reference_arm(args, cfg):
     import oracle
     oracle.build()
     per_step = args.ref_sweeps
+    # one sample: one host core; several independent samples: one process per core
+    procs = min(cfg.n_samples, os.cpu_count() or 1)
     for _ in range(args.warmup):
         run_oracle_sample(cfg, per_step, measure_every=args.measure_every)
-    ups, secs = 0, 0.0
+    rates, secs = [], 0.0
     for _ in range(args.steps):
-        u, dt, _ = run_oracle_sample(cfg, per_step, measure_every=args.measure_every)
-        ups += u
+        if procs > 1:
+            rate, res = run_oracle_parallel(cfg, 0.0, args.measure_every, procs, sweeps=per_step)
+            dt = max(t for _, t, _ in res)
+        else:
+            u, dt, _ = run_oracle_sample(cfg, per_step, measure_every=args.measure_every)
+            rate = u / dt
+        rates.append(rate)
         secs += dt
-    value = ups / secs
-    sample = f"{per_step} sweeps of sample 0 of {cfg.name} ({cfg.description}) per step"
+    value = sum(rates) / len(rates)
+    sample = (f"{per_step} sweeps of sample 0 of {cfg.name} ({cfg.description}) per step" if procs == 1 else
+              f"{per_step} sweeps of each of samples 0..{procs - 1} of {cfg.name}, one process each, per step")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{cfg.name}: {cfg.description}", "engine": "sequential FP64 CPU oracle"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -478,7 +488,8 @@ def main():
         if cfg.n_samples > 1:
             # independent samples: one oracle process per host core
             procs = min(cfg.n_samples, os.cpu_count() or 1)
-            rate, n_sw = run_oracle_parallel(cfg, args.cpu_seconds, args.measure_every, procs)
+            rate, res = run_oracle_parallel(cfg, args.cpu_seconds, args.measure_every, procs)
+            n_sw = [n for _, _, n in res]
             cpu = {"value": rate, "unit": UNIT, "cores": procs, "kind": "oracle",
                    "sample": f"samples 0..{procs - 1} of {cfg.name}, one process each, about {args.cpu_seconds:.0f} s "
                              f"each ({min(n_sw)}-{max(n_sw)} sweeps), rates summed"}
