@@ -1,8 +1,8 @@
 """Host analysis of the sampler's accumulators (numpy, no GPU).
 
 The library returns, per (sample, temperature slot), FP64 sums over the
-measurements of e = E/N, e^2, |m|, m_x, m_y, m^2, m^4 and chi(k_min)
-(xyl_read_observables, field order ``FIELDS``).  This module turns them into the
+measurements of e = E/N, e^2, |m|, m_x, m_y, m^2, m^4, chi(k_min) and m_z
+(O(3) spins; zero for XY) (xyl_read_observables, field order ``FIELDS``).  This module turns them into the
 observables of Sec. III and the finite-size tools of Sec. IV and App. C:
 
 * ``observables``: specific heat (Eq. specificheat), susceptibility (Eq. chi,
@@ -24,12 +24,12 @@ from __future__ import annotations
 
 import numpy as np
 
-FIELDS = ("n", "e", "e2", "absm", "mx", "my", "m2", "m4", "chik")
+FIELDS = ("n", "e", "e2", "absm", "mx", "my", "m2", "m4", "chik", "mz")
 _IX = {f: k for k, f in enumerate(FIELDS)}
 
 
 def thermal_means(acc: np.ndarray) -> np.ndarray:
-    """Accumulator sums (..., 9) -> thermal averages (..., 9); field 0 keeps the count."""
+    """Accumulator sums (..., F) -> thermal averages (..., F); field 0 keeps the count."""
     acc = np.asarray(acc, np.float64)
     out = acc.copy()
     out[..., 1:] = acc[..., 1:] / acc[..., :1]
@@ -37,7 +37,8 @@ def thermal_means(acc: np.ndarray) -> np.ndarray:
 
 
 def observables(means: np.ndarray, N: int, T, L: int, rho: float | None = None, d: int = 2) -> dict:
-    """Sec. III observables from thermal averages (..., 9) of one graph size.
+    """Sec. III observables from thermal averages (..., F) of one graph size
+    (F = 10 as the library returns them, or 9 without the m_z field).
 
     T broadcasts against the leading axes (e.g. one value per slot).  xi_2 takes
     psi = rho - d in the long-range regime and 2 in the short-range one, read as
@@ -46,6 +47,7 @@ def observables(means: np.ndarray, N: int, T, L: int, rho: float | None = None, 
     g = lambda f: m[..., _IX[f]]
     T = np.asarray(T, np.float64)
     chi0 = N * g("m2")
+    mz = g("mz") if m.shape[-1] > _IX["mz"] else 0.0
     chik = g("chik")
     psi = 2.0 if rho is None else min(rho - d, 2.0)
     ratio = np.maximum(chi0 / chik - 1.0, 0.0)
@@ -53,7 +55,7 @@ def observables(means: np.ndarray, N: int, T, L: int, rho: float | None = None, 
         "e": g("e"),
         "c": N * (g("e2") - g("e") ** 2) / T ** 2,
         "absm": g("absm"),
-        "chi": N * (g("m2") - g("mx") ** 2 - g("my") ** 2),
+        "chi": N * (g("m2") - g("mx") ** 2 - g("my") ** 2 - mz ** 2),
         "chi0": chi0,
         "chik": chik,
         "u4_sample": g("m4") / g("m2") ** 2 - 1.0,

@@ -117,3 +117,14 @@ def test_window_histograms_of_a_stationary_and_a_drifting_series():
     assert p < 1e-6
     with pytest.raises(ValueError):
         an.window_histogram_check(np.ones(3))
+
+
+def test_connected_susceptibility_takes_m_z_for_o3():
+    # an ordered O(3) state along z: m = (0, 0, 1), so chi = N(<m^2> - |<m>|^2) = 0
+    means = np.zeros(10)
+    means[0] = 1
+    means[6] = 1.0   # m^2
+    means[9] = 1.0   # m_z
+    assert an.observables(means, 64, 1.0, 8)["chi"] == pytest.approx(0.0, abs=1e-12)
+    # without the m_z field (XY accumulators) the same m^2 is all fluctuation
+    assert an.observables(means[:9], 64, 1.0, 8)["chi"] == pytest.approx(64.0)
