@@ -125,6 +125,7 @@ def test_connected_susceptibility_takes_m_z_for_o3():
     means[0] = 1
     means[6] = 1.0   # m^2
     means[9] = 1.0   # m_z
+    means[8] = 1.0   # chi(k_min)
     assert an.observables(means, 64, 1.0, 8)["chi"] == pytest.approx(0.0, abs=1e-12)
     # without the m_z field (XY accumulators) the same m^2 is all fluctuation
     assert an.observables(means[:9], 64, 1.0, 8)["chi"] == pytest.approx(64.0)
