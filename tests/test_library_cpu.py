@@ -271,3 +271,30 @@ def test_launch_shape_choice_on_the_host(xyl):
     assert t["resident"] == -1
     t = xyl.Plan([(fixed, 0, [1.0] * 2, [1.0] * 2)], engine=xyl.FP32_PLAIN, device="cpu", spin_dim=3).tuning()
     assert t["spin_dim"] == 3
+
+
+def test_calls_before_bind_report_the_call_order(xyl):
+    """Every device-side entry point checks its plan first: a NULL plan is
+    XYL_EINVAL, a plan without a workspace XYL_ESTATE; nothing reaches CUDA."""
+    import ctypes as C
+    lib = xyl.load()
+    g = xyl.build_graph_csr(8, 6, 3.5, 1, 0)
+    p = xyl.Plan([(g, 0, [1.0, 0.5], [1.0, 1.0])], engine=xyl.FP32_BATCHED, device="cpu")
+    h = p.handle
+    buf = (C.c_double * 64)()
+    calls = {
+        "xyl_init_spins": lambda q: lib.xyl_init_spins(q, 0, None),
+        "xyl_sweep": lambda q: lib.xyl_sweep(q, 1, 15, 1, None),
+        "xyl_sweep_units": lambda q: lib.xyl_sweep_units(q, 0, 1, 1, 15, 1, None),
+        "xyl_sweep_noalloc": lambda q: lib.xyl_sweep_noalloc(q, 1, 15, 1, None),
+        "xyl_pt_swap": lambda q: lib.xyl_pt_swap(q, None),
+        "xyl_measure": lambda q: lib.xyl_measure(q, None),
+        "xyl_recompute": lambda q: lib.xyl_recompute(q, None),
+        "xyl_set_delta": lambda q: lib.xyl_set_delta(q, 0, buf, None),
+        "xyl_read_energies": lambda q: lib.xyl_read_energies(q, buf, None),
+        "xyl_read_spins": lambda q: lib.xyl_read_spins(q, 0, 0, buf, None),
+        "xyl_export_state": lambda q: lib.xyl_export_state(q, buf, 64 * 8, None),
+    }
+    for name, call in calls.items():
+        assert call(h) == xyl.ESTATE, name
+        assert call(None) == xyl.EINVAL, name
