@@ -16,8 +16,10 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "xyl_oracle.c")
-_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+# XYL_ORACLE_SRC / XYL_ORACLE_LIB point the pins at another copy of the oracle
+# (the mutation tests build copies with planted mistakes)
+_SRC = os.environ.get("XYL_ORACLE_SRC") or os.path.join(_HERE, "xyl_oracle.c")
+_LIB_PATH = os.environ.get("XYL_ORACLE_LIB") or os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
