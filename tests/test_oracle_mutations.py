@@ -53,6 +53,15 @@ MUTATIONS = [
     ("walk neighbour index", "v = col[row_ptr[v] + (int)(((uint64_t)x[t % 4] * (uint64_t)k) >> 32)];",
      "v = col[row_ptr[v] + (int)(((uint64_t)x[t % 4] * (uint64_t)(k - 1)) >> 32)];",
      "tests/test_oracle_walk.py::test_return_counts_match_transition_matrix_powers"),
+    ("initial angles on half the circle", "double th = 2.0 * ORC_PI * u - ORC_PI;", "double th = ORC_PI * u - ORC_PI;",
+     "tests/test_oracle_physics.py::test_initial_angles_are_uniform"),
+    ("SLO tie-break", "return a.deg < b.deg || (a.deg == b.deg && a.id < b.id);",
+     "return a.deg < b.deg || (a.deg == b.deg && a.id > b.id);",
+     "tests/test_oracle_graph.py::test_slo_hand_derived_colourings"),
+    ("bond duplicates kept", "        if (bonded) continue;\n        int ends[2] = { i, j };",
+     "        (void)bonded;\n        int ends[2] = { i, j };", "tests/test_oracle_bonds.py::test_bonds_simple_counted_seeded"),
+    ("CSR rows unsorted", "        qsort(col + row_ptr[a], (size_t)d, sizeof(int32_t), cmp_int);", "",
+     "tests/test_oracle_graph.py::test_csr_layout"),
     ("O(3) cap factor", "const double w = u * (2.0 * (sh * sh));", "const double w = u * (sh * sh);",
      "tests/test_oracle_o3.py::test_cap_proposal_is_uniform_on_the_cap"),
     ("O(3) z dropped from the energy", "double d = x[i] * x[j] + y[i] * y[j] + z[i] * z[j];",

@@ -230,3 +230,18 @@ def test_overrelaxation_map_is_an_energy_conserving_involution(orc, dim):
         assert np.abs(r - s).max() > 0 or abs(abs(s @ h) - np.linalg.norm(h)) < 1e-12
     s = rng.normal(size=dim)
     assert np.array_equal(orc.reflect(s, np.zeros(dim)), s)
+
+
+@pytest.mark.parametrize("u24", [False, True])
+def test_initial_angles_are_uniform(orc, u24):
+    """theta = 2 pi u - pi: uniform on the circle (Kolmogorov-Smirnov), unit
+    vectors; the aligned start is (1, 0) everywhere."""
+    from scipy import stats
+    n = 20000
+    sim = orc.graph_sim(np.zeros(0, np.int32), np.zeros(0, np.int32), n, [1.0, 1.0], [1.0, 1.0], 5, u24=u24)
+    sim.init()
+    th = sim.angles().ravel()
+    assert stats.kstest(th, stats.uniform(-np.pi, 2 * np.pi).cdf).pvalue > 1e-3
+    assert np.abs(np.hypot(*sim.vectors().reshape(-1, 2).T) - 1.0).max() < 1e-15
+    sim.init(aligned=True)
+    assert np.array_equal(sim.vectors().reshape(-1, 2), np.tile([1.0, 0.0], (2 * n, 1)))
