@@ -31,6 +31,10 @@
  *   * Sites have two numberings: the ORIGINAL id (x + L*y on the lattice, or the
  *     caller's id for xyl_graph_from_edges) and the colour-sorted id of the CSR.
  *     Random streams and every host-visible per-site array use original ids.
+ *   * Threads: a plan (and the CUDA graphs it caches) serves one caller at a
+ *     time; different plans may be used from different threads.  A graph is
+ *     only read by xyl_plan_create (which copies what it needs), so it may be
+ *     freed or changed afterwards.
  */
 #ifndef XYL_H
 #define XYL_H
