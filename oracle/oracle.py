@@ -89,6 +89,11 @@ def _load():
         lib.orc_sim_set_labels.argtypes = [P, i32p, C.c_uint64]
         lib.orc_sim_get_tie_counts.argtypes = [P, i64p]
         lib.orc_sim_clear_ties.argtypes = [P]
+        lib.orc_sim_get_tie_log.argtypes = [P, C.c_int, C.c_int64, i32p, i32p, i64p, i32p]
+        lib.orc_sim_get_tie_log.restype = C.c_int64
+        lib.orc_sim_force.argtypes = [P, C.c_int64, i32p, i32p, i32p]
+        lib.orc_sim_force_pt.argtypes = [P, C.c_int64, i32p, i32p]
+        lib.orc_sim_set_active.argtypes = [P, C.POINTER(C.c_uint8)]
         lib.orc_sincos_series.argtypes = [C.c_double, f64p, f64p]
         lib.orc_sincos_series.restype = None
         lib.orc_sim_sweep_index.argtypes = [P]
@@ -363,6 +368,46 @@ class Sim:
 
     def clear_ties(self):
         self._lib.orc_sim_clear_ties(self._h)
+
+    def tie_log(self, pt=False):
+        """Near-tie tests since the last clear: (replica, original site id,
+        sweep, outcome) rows for Metropolis; for PT the site column is the
+        pair k and the replica column is -1."""
+        n = self._lib.orc_sim_get_tie_log(self._h, 1 if pt else 0, 0, None, None, None, None)
+        rep = np.zeros(n, np.int32); site = np.zeros(n, np.int32)
+        sweep = np.zeros(n, np.int64); acc = np.zeros(n, np.int32)
+        if n:
+            self._lib.orc_sim_get_tie_log(self._h, 1 if pt else 0, n, _ptr(rep, C.c_int32), _ptr(site, C.c_int32),
+                                          _ptr(sweep, C.c_int64), _ptr(acc, C.c_int32))
+        return [(int(a), int(b), int(c), int(d)) for a, b, c, d in zip(rep, site, sweep, acc)]
+
+    def force(self, decisions=()):
+        """Metropolis outcomes to take instead of the test's: an iterable of
+        (replica, original site id, accept); empty removes them."""
+        d = list(decisions)
+        rep = np.array([x[0] for x in d], np.int32); site = np.array([x[1] for x in d], np.int32)
+        acc = np.array([1 if x[2] else 0 for x in d], np.int32)
+        if self._lib.orc_sim_force(self._h, len(d), _ptr(rep, C.c_int32), _ptr(site, C.c_int32),
+                                   _ptr(acc, C.c_int32)):
+            raise ValueError("bad forced decision")
+
+    def force_pt(self, decisions=()):
+        """PT outcomes to take instead of the test's: (pair k, accept) pairs; empty removes them."""
+        d = list(decisions)
+        pair = np.array([x[0] for x in d], np.int32); acc = np.array([1 if x[1] else 0 for x in d], np.int32)
+        if self._lib.orc_sim_force_pt(self._h, len(d), _ptr(pair, C.c_int32), _ptr(acc, C.c_int32)):
+            raise ValueError("bad forced PT decision")
+
+    def set_active(self, replicas=None):
+        """Sweeps update only these replicas (None: all).  For spins and
+        energies only: PT then compares stale energies of the others."""
+        if replicas is None:
+            self._lib.orc_sim_set_active(self._h, None)
+            return
+        mask = np.zeros(self.R, np.uint8)
+        mask[list(replicas)] = 1
+        if self._lib.orc_sim_set_active(self._h, _ptr(mask, C.c_uint8)):
+            raise MemoryError("oracle allocation failed")
 
     def energies(self) -> np.ndarray:
         out = np.zeros(self.R, np.float64)

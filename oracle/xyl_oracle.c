@@ -850,6 +850,10 @@ void orc_sincos_series(double x, double *sn, double *cs)
 /* sweep t: counter (k, t, PT<<24, sample), u53(w0,w1).                       */
 /* ------------------------------------------------------------------------- */
 enum { OP_MET = 1u, OP_OR = 2u, OP_PT = 4u, OP_MEASURE = 8u };
+
+/* One near-tie decision: replica (or -1 for PT), original site id (PT: pair k),
+ * sweep index and the outcome the test took. */
+typedef struct { int32_t rep, site; int64_t sweep; int32_t accepted; } orc_tie;
 enum { ACC_N, ACC_E, ACC_E2, ACC_ABSM, ACC_MX, ACC_MY, ACC_M2, ACC_M4, ACC_CHIK, ACC_MZ, ACC_COUNT };
 
 typedef struct {
@@ -878,6 +882,14 @@ typedef struct {
     double *hx, *hy;          /* field on each site, or NULL */
     int dim;                  /* spin components: 2 (XY) or 3 (O(3)) */
     double *vz;               /* third spin component [R][n] (zero for XY) */
+    /* checking aids (none changes a decision unless a test sets it):          */
+    orc_tie *tie_log;         /* near-tie Metropolis tests since the last clear */
+    int64_t tie_len, tie_cap;
+    orc_tie *pt_log;          /* near-tie PT tests since the last clear (site = pair k) */
+    int64_t pt_len, pt_cap;
+    int8_t *forced;           /* [R][n] Metropolis outcome to take instead of the test's (-1: none), or NULL */
+    int8_t *pt_forced;        /* [R] PT outcome of pair k to take instead of the test's (-1: none), or NULL */
+    uint8_t *active;          /* [R] replicas the sweeps update, or NULL (all) */
 } orc_sim;
 
 void orc_sim_free(orc_sim *s)
@@ -888,6 +900,7 @@ void orc_sim_free(orc_sim *s)
     free(s->vx); free(s->vy); free(s->slot_of); free(s->rep_at); free(s->E); free(s->acc);
     free(s->met_acc); free(s->met_try); free(s->pt_acc); free(s->pt_try); free(s->first_tie); free(s->n_ties);
     free(s->jb); free(s->jn); free(s->hx); free(s->hy); free(s->vz);
+    free(s->tie_log); free(s->pt_log); free(s->forced); free(s->pt_forced); free(s->active);
     free(s);
 }
 
@@ -1029,6 +1042,8 @@ void orc_sim_init(orc_sim *s, int aligned)
     }
     s->t = 0;
     s->first_pt_tie = -1;
+    s->tie_len = 0;
+    s->pt_len = 0;
     s->min_margin = INFINITY;
     memset(s->acc, 0, sizeof(double) * (size_t)s->R * ACC_COUNT);
     memset(s->met_acc, 0, sizeof(uint64_t) * (size_t)s->R);
@@ -1038,13 +1053,40 @@ void orc_sim_init(orc_sim *s, int aligned)
     refresh_energies(s);
 }
 
-static void note_tie(orc_sim *s, int r, double margin)
+static void log_tie(orc_tie **log, int64_t *len, int64_t *cap, int r, int site, int64_t t, int accepted)
+{
+    if (*len == *cap) {
+        int64_t nc = *cap ? 2 * *cap : 64;
+        orc_tie *grown = (orc_tie *)realloc(*log, sizeof(orc_tie) * (size_t)nc);
+        if (!grown) return;  /* the count of n_ties still records it */
+        *log = grown;
+        *cap = nc;
+    }
+    orc_tie e = { r, site, t, accepted };
+    (*log)[(*len)++] = e;
+}
+
+/* margin: distance of the test from flipping (|u - exp(-beta dE)|, or |dE|
+ * near dE = 0); a test closer than tie_eps is counted and logged with the
+ * outcome the test took. */
+static void note_tie(orc_sim *s, int r, int v, double margin, int accepted)
 {
     if (margin < s->min_margin) s->min_margin = margin;
     if (margin < s->tie_eps) {
         s->n_ties[r]++;
         if (s->first_tie[r] < 0) s->first_tie[r] = (int64_t)s->t;
+        log_tie(&s->tie_log, &s->tie_len, &s->tie_cap, r, v, (int64_t)s->t, accepted);
     }
+}
+
+/* the outcome a test set for (r, v), else the test's own */
+static int forced_outcome(const orc_sim *s, int r, int v, int accept)
+{
+    if (s->forced) {
+        const int8_t f = s->forced[(size_t)r * s->n + v];
+        if (f >= 0) return f;
+    }
+    return accept;
 }
 
 static void local_field(const orc_sim *s, const double *x, const double *y, int v, double *hx, double *hy)
@@ -1151,14 +1193,15 @@ static void metropolis_site(orc_sim *s, int r, int v)
     int accept;
     if (dE <= 0.0) {
         accept = 1;
-        note_tie(s, r, -dE);
+        note_tie(s, r, v, -dE, accept);
     } else {
         double a = exp(-s->beta[slot] * dE);
         accept = ua < a;
         double margin = fabs(ua - a);
         if (dE < margin) margin = dE;
-        note_tie(s, r, margin);
+        note_tie(s, r, v, margin, accept);
     }
+    accept = forced_outcome(s, r, v, accept);
     s->met_try[slot]++;
     if (accept) {
         x[v] = nx;
@@ -1211,7 +1254,11 @@ static void parallel_tempering(orc_sim *s)
         double u = u53(w[0], w[1]);
         double p = exp(x);
         int accept = u < p;
-        if (x < 0.0 && fabs(u - p) < s->tie_eps && s->first_pt_tie < 0) s->first_pt_tie = (int64_t)s->t;
+        if (x < 0.0 && fabs(u - p) < s->tie_eps) {
+            if (s->first_pt_tie < 0) s->first_pt_tie = (int64_t)s->t;
+            log_tie(&s->pt_log, &s->pt_len, &s->pt_cap, -1, k, (int64_t)s->t, accept);
+        }
+        if (s->pt_forced && s->pt_forced[k] >= 0) accept = s->pt_forced[k];
         s->pt_try[k]++;
         if (accept) {
             s->rep_at[k] = b; s->rep_at[k + 1] = a;
@@ -1269,6 +1316,7 @@ void orc_sim_sweeps(orc_sim *s, int n_sweeps, unsigned ops, int measure_every)
 {
     for (int it = 0; it < n_sweeps; ++it) {
         for (int r = 0; r < s->R; ++r) {
+            if (s->active && !s->active[r]) continue;
             if (ops & OP_MET)
                 for (int c = 0; c < s->Q; ++c)
                     for (int a = s->cls_ptr[c]; a < s->cls_ptr[c + 1]; ++a) metropolis_site(s, r, s->cls[a]);
@@ -1380,11 +1428,84 @@ void orc_sim_get_tie_counts(const orc_sim *s, int64_t *n_ties)
 void orc_sim_clear_ties(orc_sim *s)
 {
     for (int r = 0; r < s->R; ++r) { s->first_tie[r] = -1; s->n_ties[r] = 0; }
+    s->tie_len = 0;
+    s->pt_len = 0;
     s->first_pt_tie = -1;
     s->min_margin = INFINITY;
 }
 
 uint64_t orc_sim_sweep_index(const orc_sim *s) { return s->t; }
+
+/* ------------------------------------------------------------------------- */
+/* Checking aids for the single-precision parity tests.  A single-precision   */
+/* kernel evaluates exp(-beta dE) and the PT energies with rounding errors    */
+/* far below 1e-5, so it can only take a different outcome where the test is  */
+/* that close to flipping.  The log lists every such near-tie test (replica,  */
+/* original site id, sweep, outcome); a test then re-runs a sweep with chosen */
+/* near-tie outcomes forced the other way, to show that a mismatch comes from */
+/* exactly those decisions.  The replica mask lets it re-run one replica      */
+/* alone (the others keep their spins and energies; PT then compares stale    */
+/* energies, so a masked run is for spins and energies only).                */
+/* ------------------------------------------------------------------------- */
+
+/* copy up to max entries of the Metropolis (pt = 0) or PT (pt = 1) near-tie
+ * log; returns the number of entries logged since the last clear */
+int64_t orc_sim_get_tie_log(const orc_sim *s, int pt, int64_t max, int32_t *rep, int32_t *site, int64_t *sweep,
+                            int32_t *accepted)
+{
+    const orc_tie *log = pt ? s->pt_log : s->tie_log;
+    const int64_t len = pt ? s->pt_len : s->tie_len;
+    for (int64_t q = 0; q < len && q < max; ++q) {
+        rep[q] = log[q].rep; site[q] = log[q].site; sweep[q] = log[q].sweep; accepted[q] = log[q].accepted;
+    }
+    return len;
+}
+
+/* Metropolis outcomes to take at (replica, original site) in the sweeps that
+ * follow, instead of the test's; n = 0 removes them all.  Returns -1 on bad
+ * input or allocation failure. */
+int orc_sim_force(orc_sim *s, int64_t n, const int32_t *rep, const int32_t *site, const int32_t *accept)
+{
+    if (n <= 0) { free(s->forced); s->forced = NULL; return 0; }
+    if (!s->forced) {
+        s->forced = (int8_t *)malloc((size_t)s->R * (size_t)s->n);
+        if (!s->forced) return -1;
+    }
+    memset(s->forced, -1, (size_t)s->R * (size_t)s->n);
+    for (int64_t q = 0; q < n; ++q) {
+        if (rep[q] < 0 || rep[q] >= s->R || site[q] < 0 || site[q] >= s->n) return -1;
+        s->forced[(size_t)rep[q] * s->n + site[q]] = accept[q] ? 1 : 0;
+    }
+    return 0;
+}
+
+/* PT outcomes to take for pair k (slots k, k+1) instead of the test's; n = 0 removes them. */
+int orc_sim_force_pt(orc_sim *s, int64_t n, const int32_t *pair, const int32_t *accept)
+{
+    if (n <= 0) { free(s->pt_forced); s->pt_forced = NULL; return 0; }
+    if (!s->pt_forced) {
+        s->pt_forced = (int8_t *)malloc((size_t)s->R);
+        if (!s->pt_forced) return -1;
+    }
+    memset(s->pt_forced, -1, (size_t)s->R);
+    for (int64_t q = 0; q < n; ++q) {
+        if (pair[q] < 0 || pair[q] + 1 >= s->R) return -1;
+        s->pt_forced[pair[q]] = accept[q] ? 1 : 0;
+    }
+    return 0;
+}
+
+/* mask[r] != 0: the sweeps update replica r; NULL: every replica */
+int orc_sim_set_active(orc_sim *s, const uint8_t *mask)
+{
+    if (!mask) { free(s->active); s->active = NULL; return 0; }
+    if (!s->active) {
+        s->active = (uint8_t *)malloc((size_t)s->R);
+        if (!s->active) return -1;
+    }
+    memcpy(s->active, mask, (size_t)s->R);
+    return 0;
+}
 
 /* ------------------------------------------------------------------------- */
 /* O(3) spins (App. B: the method carries over to other continuous models;    */
@@ -1520,14 +1641,15 @@ static void metropolis_site_o3(orc_sim *s, int r, int v)
     int accept;
     if (dE <= 0.0) {
         accept = 1;
-        note_tie(s, r, -dE);
+        note_tie(s, r, v, -dE, accept);
     } else {
         double p = exp(-s->beta[slot] * dE);
         accept = ua < p;
         double margin = fabs(ua - p);
         if (dE < margin) margin = dE;
-        note_tie(s, r, margin);
+        note_tie(s, r, v, margin, accept);
     }
+    accept = forced_outcome(s, r, v, accept);
     s->met_try[slot]++;
     if (accept) {
         s->vx[q] = nx;

@@ -181,3 +181,134 @@ def paper_critical_temperatures():
             continue
         rows[float(w[0])] = tuple(float(x) for x in w[1:5])
     return rows, analytic
+
+
+# ----------------------------------------------------------------- FP32 parity from a shared state
+FP32_TIE_EPS = 3e-5      # > 5x the worst FP32 error of exp(-beta dE) or of a PT exponent per decision
+FP32_E_TOL = 1e-5        # energy per spin
+FP32_DIR_TOL = 1e-4      # 99th percentile of the spin direction gaps (rad)
+MAX_FLIPS = 3            # near-tie decisions forced together when tracing one replica-sweep
+
+
+def direction_gap(a, b):
+    """Angle between spin vectors a and b (..., d), d = 2 or 3, by atan2(|a x b|, a . b)."""
+    dot = (a * b).sum(-1)
+    if a.shape[-1] == 2:
+        cross = np.abs(a[..., 0] * b[..., 1] - a[..., 1] * b[..., 0])
+    else:
+        cross = np.linalg.norm(np.cross(a, b), axis=-1)
+    return np.arctan2(cross, dot)
+
+
+def _replica_ok(gpu_vec, sim_vec, gpu_E, sim_E, N):
+    gap = np.percentile(direction_gap(gpu_vec, sim_vec), 99)
+    return abs(gpu_E - sim_E) / N < FP32_E_TOL and gap < FP32_DIR_TOL, abs(gpu_E - sim_E) / N
+
+
+def fp32_parity_sweeps(plan, sims, samples, n_sweeps, ops, N_of, rep_slice):
+    """FP32 kernel against the oracle in its 24-bit mode, one sweep at a time.
+
+    Overrelaxation is chaotic (FP32 and FP64 trajectories decorrelate within
+    about eight sweeps), so every sweep starts the oracle from the GPU's own
+    spins, labels and sweep index, then both run one sweep.  Each replica must
+    then agree: energy per spin within 1e-5 and 99% of spin directions within
+    1e-4 rad (a site whose local field nearly cancels has an ill-conditioned
+    reflection).  A replica that misses must be traced to decisions FP32
+    rounding can flip: the oracle logs every Metropolis test within 3e-5 of
+    flipping, and some set of at most three of that replica-sweep's logged
+    decisions, forced the other way, must make the re-run oracle agree.  The
+    slot labels must then agree too, with logged PT near-ties forced the same
+    way where needed.  No other miss is allowed.
+
+    Returns (replica-sweeps compared, misses traced, decisions flipped, worst
+    |dE|/N among the agreeing ones)."""
+    import itertools
+    MET_OR = ops & 3
+    compared = traced = flipped = 0
+    worst = 0.0
+    for _ in range(n_sweeps):
+        t_gpu = plan.status()[1]
+        labels = plan.labels()
+        start = {}
+        for s in samples:
+            sim = sims[s]
+            vec = np.stack([plan.spins(s, r) for r in range(sim.R)])
+            start[s] = (vec, labels[rep_slice(s)].copy())
+            sim.set_vectors(vec)
+            sim.set_labels(start[s][1], t_gpu)
+            sim.set_tie_eps(FP32_TIE_EPS)
+            sim.clear_ties()
+            sim.force([])
+            sim.force_pt([])
+            sim.set_active(None)
+        plan.sweep(1, ops)
+        E = plan.energies()
+        labels_after = plan.labels()
+
+        def restart(sim, s):
+            sim.set_vectors(start[s][0])
+            sim.set_labels(start[s][1], t_gpu)
+
+        for s in samples:
+            sim = sims[s]
+            N = N_of(s)
+            gvec = np.stack([plan.spins(s, r) for r in range(sim.R)])
+            gE = E[rep_slice(s)]
+            glab = labels_after[rep_slice(s)]
+            sim.sweeps(1, ops)
+            svec, sE = sim.vectors(), sim.energies()
+            misses = []
+            for r in range(sim.R):
+                compared += 1
+                ok, dE = _replica_ok(gvec[r], svec[r], gE[r], sE[r], N)
+                if ok:
+                    worst = max(worst, dE)
+                else:
+                    misses.append(r)
+            if not misses and np.array_equal(glab, sim.labels()):
+                continue
+            log = sim.tie_log()
+            pt_log = sim.tie_log(pt=True)
+            forced = []
+            for r in misses:
+                cands = [(v, a) for rr, v, _, a in log if rr == r]
+                found = None
+                for size in range(1, min(len(cands), MAX_FLIPS) + 1):
+                    for combo in itertools.combinations(cands, size):
+                        restart(sim, s)
+                        sim.set_active([r])
+                        sim.force([(r, v, 1 - a) for v, a in combo])
+                        sim.sweeps(1, MET_OR)
+                        if _replica_ok(gvec[r], sim.vectors()[r], gE[r], sim.energies()[r], N)[0]:
+                            found = combo
+                            break
+                    if found:
+                        break
+                assert found, f"sample {s} replica {r} sweep {t_gpu}: a miss not traced to near-tie decisions " \
+                              f"({len(cands)} logged)"
+                forced += [(r, v, 1 - a) for v, a in found]
+                traced += 1
+                flipped += len(found)
+            # the whole sweep again with the traced decisions forced: every
+            # replica agrees, and so do the labels (PT near-ties forced if needed)
+            sim.set_active(None)
+            pt_cands = [(k, a) for _, k, _, a in pt_log]
+            ok_all = False
+            for size in range(0, min(len(pt_cands), MAX_FLIPS) + 1):
+                for combo in itertools.combinations(pt_cands, size):
+                    restart(sim, s)
+                    sim.force(forced)
+                    sim.force_pt([(k, 1 - a) for k, a in combo])
+                    sim.sweeps(1, ops)
+                    same = all(_replica_ok(gvec[r], sim.vectors()[r], gE[r], sim.energies()[r], N)[0]
+                               for r in range(sim.R))
+                    if same and np.array_equal(glab, sim.labels()):
+                        ok_all = True
+                        flipped += size
+                        break
+                if ok_all:
+                    break
+            assert ok_all, f"sample {s} sweep {t_gpu}: labels or energies not traced to near-tie decisions"
+            sim.force([])
+            sim.force_pt([])
+    return compared, traced, flipped, worst

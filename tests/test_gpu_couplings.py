@@ -4,7 +4,7 @@ and exact gauge invariance of every engine.
 
 * FP64 engine vs oracle: angles within 1e-9 rad over 10 sweeps (G1, G2).
 * FP32 engines vs oracle: energy per spin within 1e-5 per sweep from a shared
-  state (near-tie decisions excepted, as for the ferromagnet).
+  state, every miss traced to flipped near-tie decisions as for the ferromagnet.
 * Gauge invariance: couplings tau_i tau_j J_ij and fields tau_i h_i with spins
   tau_i S_i describe the
   same system; the kernels' update arithmetic maps term by term under S -> -S,
@@ -14,7 +14,7 @@ and exact gauge invariance of every engine.
 import numpy as np
 import pytest
 
-from test_gpu_parity import ALL, _angle_gap, _fp32_per_sweep, _gpu_angles, _variant
+from test_gpu_parity import ALL, _angle_gap, _fp32_per_sweep, _gpu_angles, _report, _variant
 
 pytestmark = pytest.mark.gpu
 
@@ -75,8 +75,7 @@ def test_fp32_energy_with_random_bonds(env, orc, name, engine_name):
     plan.bind()
     plan.init_spins()
     sims = {0: _oracle(orc, wl, cfg, 0, u24=True)}
-    compared, explained, worst = _fp32_per_sweep(plan, sims, [0], 10, ALL, lambda s: cfg.graphs[s][0] ** 2)
-    print(f"{name} {engine_name}: {compared} replica-sweeps, {explained} near-tie misses, worst |dE|/N {worst:.2e}")
+    _report(f"{name} {engine_name}", _fp32_per_sweep(plan, sims, [0], 10, ALL, lambda s: cfg.graphs[s][0] ** 2))
     assert plan.status() == (0, 10)
 
 

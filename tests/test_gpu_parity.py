@@ -7,8 +7,10 @@ All calls go through the C ABI (ctypes binding).  Bars:
   FP64 trajectories decorrelate within about eight sweeps), so every sweep
   starts the oracle from the GPU's own spins and labels; energy per spin then
   agrees within 1e-5 and 99% of angles within 1e-4 rad for every (replica,
-  sweep), except where the oracle flags a near-tie decision
-  (|u - exp(-beta dE)| < 3e-5) that FP32 rounding may flip (at most 20%).
+  sweep).  A replica-sweep that misses must be traced to decisions FP32
+  rounding can flip: forcing at most three of the oracle's logged near-tie
+  decisions of that replica-sweep (|u - exp(-beta dE)| < 3e-5) the other way
+  must reproduce the GPU's result; no untraced miss is allowed.
 * long runs: <e>, chi, U4, <|m|>, chi(k_min) within 3 sigma (binned jackknife)
   of the oracle.
 * kernels alone against the chain / ring / quadrature / beta = 0 exact results.
@@ -16,14 +18,13 @@ All calls go through the C ABI (ctypes binding).  Bars:
 import numpy as np
 import pytest
 
-from helpers import (ACC, bin_means, chain_closed_form, edges_chain, edges_complete, edges_ring, jackknife,
-                     quadrature_moments, ring_mean_energy, run_bins)
+from helpers import (ACC, bin_means, chain_closed_form, edges_chain, edges_complete, edges_ring, fp32_parity_sweeps,
+                     jackknife, quadrature_moments, ring_mean_energy, run_bins)
 
 pytestmark = pytest.mark.gpu
 
 ALL = 1 | 2 | 4 | 8
 NO_PT = 1 | 2 | 8
-TIE_EPS = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -53,7 +54,6 @@ def _oracle_for(orc, wl, cfg, k, u24):
     color, _ = orc.slo_color(L * L, ei, ej)
     sim = orc.Sim(L * L, ei, ej, color, cfg.betas(), cfg.deltas(), wl.SPIN_SEED, sample=wl.graph_stream_id(cfg, k),
                   xy=orc.lattice_xy(L), L=L, u24=u24)
-    sim.set_tie_eps(TIE_EPS)
     sim.init()
     return sim
 
@@ -115,48 +115,16 @@ def test_fp64_trajectory_matches_oracle(env, orc, name):
 
 
 # --------------------------------------------------------------- FP32 engines
-FP32_TIE_EPS = 3e-5  # > 5x the worst FP32 error of exp(-beta dE) per decision
-
-
 def _fp32_per_sweep(plan, sims, samples, n_sweeps, ops, N_of):
-    """Every sweep starts the oracle from the GPU's own spins and labels, runs
-    one sweep on both, and compares energy per spin (1e-5) and angles (1e-4).
-    A miss is allowed only where the oracle flags a near-tie decision in that
-    sweep (FP32 rounding can flip such a decision); misses stay rare."""
-    compared = explained = 0
-    worst = 0.0
-    for t in range(n_sweeps):
-        t_gpu = plan.status()[1]
-        labels = plan.labels()
-        for s in samples:
-            sim = sims[s]
-            sim.set_vectors(np.stack([plan.spins(s, r) for r in range(sim.R)]))
-            sim.set_labels(labels[_rep_slice(plan, s)], t_gpu)
-            sim.set_tie_eps(FP32_TIE_EPS)
-            sim.clear_ties()
-        plan.sweep(1, ops)
-        E = plan.energies()
-        labels_after = plan.labels()
-        for s in samples:
-            sim = sims[s]
-            sim.sweeps(1, ops)
-            ties = sim.tie_counts()
-            _, pt_tie, _ = sim.ties()
-            # spins whose local field nearly cancels have an ill-conditioned
-            # reflection: judge angles by their 99th percentile, energies exactly
-            gap = np.percentile(_angle_gap(_gpu_angles(plan, s, sim.R), sim.angles()), 99, axis=1)
-            dE = np.abs(E[_rep_slice(plan, s)] - sim.energies()) / N_of(s)
-            for r in range(sim.R):
-                compared += 1
-                if dE[r] < 1e-5 and gap[r] < 1e-4:
-                    worst = max(worst, dE[r])
-                    continue
-                assert ties[r] > 0, (s, r, t, dE[r], gap[r])
-                explained += 1
-            if not np.array_equal(labels_after[_rep_slice(plan, s)], sim.labels()):
-                assert pt_tie >= 0 or ties.sum() > 0, (s, t)
-    assert explained <= 0.2 * compared, (explained, compared)
-    return compared, explained, worst
+    """Per-sweep FP32 parity from a shared state; every miss traced to flipped
+    near-tie decisions (helpers.fp32_parity_sweeps)."""
+    return fp32_parity_sweeps(plan, sims, samples, n_sweeps, ops, N_of, lambda s: _rep_slice(plan, s))
+
+
+def _report(label, stats):
+    compared, traced, flipped, worst = stats
+    print(f"{label}: {compared} replica-sweeps, {traced} misses traced to {flipped} flipped near-tie decisions, "
+          f"0 unexplained, worst |dE|/N {worst:.2e}")
 
 
 @pytest.mark.parametrize("engine_name", ["FP32_RESIDENT", "FP32_SPLIT", "FP32_GLOBAL", "FP32_PLAIN"])
@@ -170,8 +138,7 @@ def test_fp32_energy_matches_oracle(env, orc, name, engine_name):
     plan.init_spins()
     sims = {0: _oracle_for(orc, wl, cfg, 0, u24=True)}
     assert _angle_gap(_gpu_angles(plan, 0, cfg.n_temps), sims[0].angles()).max() < 1e-6
-    compared, explained, worst = _fp32_per_sweep(plan, sims, [0], 10, ALL, lambda s: cfg.graphs[s][0] ** 2)
-    print(f"{name} {engine_name}: {compared} replica-sweeps, {explained} near-tie misses, worst |dE|/N {worst:.2e}")
+    _report(f"{name} {engine_name}", _fp32_per_sweep(plan, sims, [0], 10, ALL, lambda s: cfg.graphs[s][0] ** 2))
     assert plan.status() == (0, 10)
 
 
@@ -187,8 +154,7 @@ def test_fp32_energy_matches_oracle_in_the_benchmark_shape(env, orc):
     plan.bind()
     plan.init_spins()
     sims = {0: _oracle_for(orc, wl, cfg, 0, u24=True)}
-    compared, explained, worst = _fp32_per_sweep(plan, sims, [0], 10, ALL, lambda s: cfg.graphs[s][0] ** 2)
-    print(f"C2 bench shape: {compared} replica-sweeps, {explained} near-tie misses, worst |dE|/N {worst:.2e}")
+    _report("C2 bench shape", _fp32_per_sweep(plan, sims, [0], 10, ALL, lambda s: cfg.graphs[s][0] ** 2))
     assert plan.status() == (0, 10)
 
 
@@ -207,8 +173,7 @@ def test_fp32_energy_matches_oracle_bond_ensemble(env, orc, name, engine_name):
     plan.bind()
     plan.init_spins()
     sims = {0: _oracle_for(orc, wl, cfg, 0, u24=True)}
-    compared, explained, worst = _fp32_per_sweep(plan, sims, [0], 10, ALL, lambda s: cfg.graphs[s][0] ** 2)
-    print(f"{name} {engine_name}: {compared} replica-sweeps, {explained} near-tie misses, worst |dE|/N {worst:.2e}")
+    _report(f"{name} {engine_name}", _fp32_per_sweep(plan, sims, [0], 10, ALL, lambda s: cfg.graphs[s][0] ** 2))
     assert plan.status() == (0, 10)
 
 
@@ -407,9 +372,7 @@ def test_full_size_batched_sampled_parity(env, orc, name, sampled, resident):
     plan.init_spins()
     sims = {k: _oracle_for(orc, wl, cfg, k, u24=True) for k in sampled}
     n_sweeps = 2 if name == "C5" else 3
-    compared, explained, worst = _fp32_per_sweep(plan, sims, sampled, n_sweeps, ALL,
-                                                 lambda s: cfg.graphs[s][0] ** 2)
-    print(f"{name}: {compared} replica-sweeps, {explained} near-tie misses, worst |dE|/N {worst:.2e}")
+    _report(name, _fp32_per_sweep(plan, sims, sampled, n_sweeps, ALL, lambda s: cfg.graphs[s][0] ** 2))
     status, t = plan.status()
     assert status == 0 and t == n_sweeps
     # invariants over the whole batch
@@ -478,12 +441,22 @@ def test_recompute_bounds_fp32_drift(env):
     plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, recompute_every=50)
     plan.bind()
     plan.init_spins()
+    assert plan.drift() == 0.0
     plan.sweep(200, ALL)
+    # four periodic recomputes ran: their largest |E_fused - E_fp64| is recorded
+    d200 = plan.drift()
+    assert 0.0 < d200 / 16384 < 1e-5
     E = plan.energies()
     plan.recompute()
-    assert np.max(np.abs(plan.energies() - E)) / 16384 < 1e-5
+    gap = np.max(np.abs(plan.energies() - E))
+    assert gap / 16384 < 1e-5
+    assert plan.drift() == max(d200, gap)
     s = plan.spins(0, 3)
     assert np.max(np.abs(np.hypot(s[:, 0], s[:, 1]) - 1)) < 1e-6
+    # writing spins changes the energies but is not a drift; a reset clears it
+    plan.write_spins(0, 3, -s)
+    assert plan.drift(reset=True) == max(d200, gap)
+    assert plan.drift() == 0.0
 
 
 @pytest.mark.parametrize("shape", [dict(group=4, resident=-1), dict(group=1, cluster=4, resident=1)])
