@@ -324,19 +324,27 @@ int xyl_sweep_units(xyl_plan *p, int32_t first_unit, int32_t n_units, int32_t n_
  * scratch (per-replica sums of the sweep and the per-sample barrier counters)
  * lives in one fixed array of 1 MiB that every GPU using the library holds
  * until the process exits.  Inputs and outputs stay in the plan's workspace.
- * The batch must fit that array: 192 B per temperature slot plus 4 B per
- * sample (about 5400 slots); larger batches get XYL_EINVAL.  The first call
- * on a device looks up the array's device address (with that device current),
- * so make it before any stream capture.  All calls share the one array and
- * each call clears it first: calls that overlap on the GPU (different streams,
- * plans or threads) race and must be serialised by the caller.  No graph is
- * used.  Errors: XYL_EINVAL, XYL_ESTATE, XYL_ECUDA.  The paper has no
- * counterpart of this entry point.
+ * The batch must fit that array: 256 B per temperature slot (rounded up to
+ * a multiple of 256 B) plus 4 B per sample, i.e. 256 * slots + 4 * samples
+ * <= 1048576 (at most 4095 slots; 31 samples x 128 slots fit, 32 x 128 do
+ * not); larger batches get XYL_EINVAL.  The first call on a device looks up
+ * the array's device address (with that device current), so make it before
+ * any stream capture.  All calls share the one array, which keeps the last
+ * call's contents; every launch clears what it needs first, so calls that
+ * overlap on the GPU (different streams, plans or threads) race and must be
+ * serialised by the caller.  Like xyl_sweep, the sweeps are cut into launches
+ * at the FP64 recompute points (xyl_tuning.recompute_every), n_sweeps = 0
+ * does nothing, and xyl_sweep and xyl_sweep_noalloc may be mixed freely on one
+ * plan.  No graph is used.  Errors: XYL_EINVAL, XYL_ESTATE, XYL_ECUDA.  The
+ * paper has no counterpart of this entry point.
  */
 int xyl_sweep_noalloc(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_every, void *stream);
 
 /* Number of work units of a batched plan (0 for other engines). */
 int32_t xyl_unit_count(const xyl_plan *p);
+
+/* Work units one launch of a bound batched plan runs together (its wave; 0 for other engines or before bind). */
+int32_t xyl_wave_units(const xyl_plan *p);
 
 /*
  * xyl_autotune -- XYL_FP32_BATCHED only: time n_sweeps sweeps (ops,
@@ -375,6 +383,27 @@ int xyl_recompute(xyl_plan *p, void *stream);
 /* Replace the Metropolis half-widths of one sample's slots (n_temps values). */
 int xyl_set_delta(xyl_plan *p, int32_t sample, const double *delta, void *stream);
 
+/* The current Metropolis half-widths of one sample's slots (n_temps values; host call). */
+int xyl_get_delta(const xyl_plan *p, int32_t sample, double *delta);
+
+/*
+ * xyl_tune_delta -- warm-up that sets each slot's Metropolis half-width
+ * Delta so that about `target` of its proposals are accepted, then freezes it
+ * (the paper fixes no proposal, App. B; the half-width is tuned before any
+ * measurement and stays fixed while measuring).  Runs rounds + 1 blocks of
+ * n_sweeps sweeps with `ops` (XYL_OP_MET required; XYL_OP_MEASURE ignored).
+ * After each of the first `rounds` blocks, Delta_k becomes Delta_k * f with
+ * f = a_k / target clamped to [1/2, 2], a_k the block's acceptance at slot k,
+ * and Delta_k kept in [1e-3, pi]; the last block only measures.  A slot
+ * whose acceptance stays above target at Delta = pi (hot slots) keeps pi.
+ * rate (may be NULL) receives each slot's acceptance in the last block,
+ * slot-major over the batch.  The sweep counter advances; the accumulators
+ * and counters are zeroed at the end.  Synchronises `stream`.
+ * Errors: XYL_EINVAL, XYL_ESTATE, XYL_ECUDA.
+ */
+int xyl_tune_delta(xyl_plan *p, int32_t rounds, int32_t n_sweeps, uint32_t ops, double target, double *rate,
+                   void *stream);
+
 /*
  * xyl_read_observables -- per-slot accumulators, slot-major over the batch
  * (sample 0 slots, sample 1 slots, ...).  acc: [slots][XYL_ACC_COUNT];
@@ -399,6 +428,20 @@ int xyl_read_spins(xyl_plan *p, int32_t sample, int32_t replica, double *sxy, vo
 
 /* Overwrite the spin vectors of one replica (original site order). */
 int xyl_write_spins(xyl_plan *p, int32_t sample, int32_t replica, const double *sxy, void *stream);
+
+/*
+ * xyl_read_drift -- the largest |E_fused - E_fp64| over every replica seen
+ * since xyl_init_spins (or the last reset): E_fused is the energy a sweep
+ * summed in FP32 alongside its last pass, E_fp64 the energy recomputed in FP64
+ * from the stored spins by the next FP64 recompute (xyl_recompute, the
+ * periodic recompute of xyl_tuning.recompute_every, xyl_pt_swap,
+ * xyl_measure).  It is the health signal of the FP32-update / FP64-observable
+ * split (App. B "Memory management": single-precision spins, double-precision
+ * observables); the paper reports no such figure.  xyl_write_spins does not
+ * change it.  reset != 0 clears it after the read.  Synchronises `stream`.
+ * Errors: XYL_EINVAL (NULL output), XYL_ESTATE, XYL_ECUDA.
+ */
+int xyl_read_drift(xyl_plan *p, double *max_drift, int32_t reset, void *stream);
 
 /* Status word (0 = fine, else an XYL_E* code recorded on the device) and the sweep index of sample 0. */
 int xyl_read_status(xyl_plan *p, int32_t *status, uint64_t *sweep_index, void *stream);

@@ -127,7 +127,7 @@ void layout(xyl_plan *p)
     take(p->r_sweep, S * sizeof(uint32_t));
     take(p->r_status, sizeof(int32_t));
     take(p->r_barrier, S * sizeof(unsigned int));
-    take(p->r_drift, sizeof(double));
+    take(p->r_drift, 2 * sizeof(double));  // the recorded drift, and a save slot for xyl_write_spins
     take(p->r_units, std::max<size_t>(p->total_R, 1) * sizeof(int2));  // the most units any shape makes
     take(p->r_push, p->total_N * sizeof(uint16_t));
     // random fields: one vector per site, only when some sample has them
@@ -802,33 +802,56 @@ int xyl_sweep_noalloc(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measu
     if (need > kNoAllocScratchBytes)
         return fail(XYL_EINVAL, "xyl_sweep_noalloc: batch needs %zu B of scratch, the fixed array holds %zu B "
                     "(%d slots and %zu samples; use xyl_sweep)", need, kNoAllocScratchBytes, p->total_R, p->hs.size());
+    p->last_launches = 0;
+    if (n_sweeps == 0) return XYL_OK;  // like xyl_sweep: nothing runs, the shared array is not touched
     void *scratch = nullptr;
     XYL_CUDA(batched_noalloc_scratch(&scratch), "xyl_sweep_noalloc: scratch address");
     cudaStream_t st = as_stream(stream);
     char *base = static_cast<char *>(scratch);
-    // both sum buffers and the barrier counters must start at zero
-    XYL_CUDA(cudaMemsetAsync(base, 0, need, st), "xyl_sweep_noalloc: clear scratch");
     DevPlan P = p->dev;
     P.obs = reinterpret_cast<double *>(base);
     P.barrier = reinterpret_cast<unsigned int *>(base + bar_off);
-    p->last_launches = 0;
-    const int total = (int)p->units.size();
-    for (int u = 0; u < total; u += p->wave_units) {
-        const int cnt = std::min(p->wave_units, total - u);
-        if (p->bshape.resident)
-            XYL_CUDA(launch_resident(P, p->bshape, at<int2>(p, p->r_units), u, cnt, n_sweeps, ops, measure_every, st),
-                     "xyl_sweep_noalloc: launch");
-        else
-            XYL_CUDA(launch_batched(P, p->shape, p->bshape, at<int2>(p, p->r_units), u, cnt, n_sweeps, ops,
-                                    measure_every, st), "xyl_sweep_noalloc: launch");
-        ++p->last_launches;
+    // the sweeps are cut at the FP64 recompute points exactly as xyl_sweep cuts them
+    int left = n_sweeps;
+    while (left > 0) {
+        int n = left;
+        if (p->recompute_every > 0) n = (int)std::min<int64_t>(n, p->recompute_every - p->sweeps_since_recompute);
+        // every launch finds the sum buffer of its first sweep and the barrier counters at zero
+        XYL_CUDA(cudaMemsetAsync(base, 0, need, st), "xyl_sweep_noalloc: clear scratch");
+        const int total = (int)p->units.size();
+        for (int u = 0; u < total; u += p->wave_units) {
+            const int cnt = std::min(p->wave_units, total - u);
+            if (p->bshape.resident)
+                XYL_CUDA(launch_resident(P, p->bshape, at<int2>(p, p->r_units), u, cnt, n, ops, measure_every, st),
+                         "xyl_sweep_noalloc: launch");
+            else
+                XYL_CUDA(launch_batched(P, p->shape, p->bshape, at<int2>(p, p->r_units), u, cnt, n, ops,
+                                        measure_every, st), "xyl_sweep_noalloc: launch");
+            ++p->last_launches;
+        }
+        left -= n;
+        p->sweeps_since_recompute += n;
+        if (p->recompute_every > 0 && p->sweeps_since_recompute >= p->recompute_every) {
+            if ((rc = do_recompute(p, 1, st))) return rc;
+            p->last_launches += 1;
+            p->sweeps_since_recompute = 0;
+        }
     }
-    return XYL_OK;
+    // xyl_sweep's kernels add into the plan's own sum buffer of their first
+    // sweep and expect it cleared; these sweeps moved the sweep parity without
+    // touching that buffer, so clear it here (a memset of the caller's
+    // workspace: nothing is allocated)
+    return zero_region(p, p->r_obs, st);
 }
 
 int32_t xyl_unit_count(const xyl_plan *p)
 {
     return (p && p->engine == XYL_FP32_BATCHED) ? (int32_t)p->units.size() : 0;
+}
+
+int32_t xyl_wave_units(const xyl_plan *p)
+{
+    return (p && p->engine == XYL_FP32_BATCHED && p->bound) ? (int32_t)p->wave_units : 0;
 }
 
 int xyl_pt_swap(xyl_plan *p, void *stream)
@@ -881,6 +904,53 @@ int xyl_set_delta(xyl_plan *p, int32_t sample, const double *delta, void *stream
     XYL_CUDA(cudaStreamSynchronize(st), "xyl_set_delta: sync");
     // graphs hold kernel arguments only (pointers), so they stay valid
     return XYL_OK;
+}
+
+int xyl_get_delta(const xyl_plan *p, int32_t sample, double *delta)
+{
+    clear_error();
+    if (!p || !delta) return fail(XYL_EINVAL, "xyl_get_delta: NULL argument");
+    if (sample < 0 || sample >= (int)p->hs.size()) return fail(XYL_EINVAL, "xyl_get_delta: bad sample");
+    const HostSample &h = p->hs[sample];
+    std::copy(h.delta.begin(), h.delta.end(), delta);
+    return XYL_OK;
+}
+
+int xyl_tune_delta(xyl_plan *p, int32_t rounds, int32_t n_sweeps, uint32_t ops, double target, double *rate,
+                   void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_tune_delta");
+    if (rc) return rc;
+    if (rounds < 0 || n_sweeps < 1 || !(ops & XYL_OP_MET) || !(target > 0.0 && target < 1.0))
+        return fail(XYL_EINVAL, "xyl_tune_delta: need rounds >= 0, n_sweeps >= 1, XYL_OP_MET and 0 < target < 1");
+    ops &= (XYL_OP_MET | XYL_OP_OR | XYL_OP_PT);
+    cudaStream_t st = as_stream(stream);
+    const size_t slots = (size_t)p->total_R;
+    std::vector<uint64_t> acc(slots), tries(slots);
+    std::vector<double> last(slots, 0.0);
+    for (int round = 0; round <= rounds; ++round) {
+        if ((rc = xyl_reset_observables(p, stream))) return rc;
+        if ((rc = xyl_sweep(p, n_sweeps, ops, 1, stream))) return rc;
+        if ((rc = xyl_read_observables(p, nullptr, acc.data(), tries.data(), nullptr, nullptr, stream))) return rc;
+        size_t k = 0;
+        for (size_t s = 0; s < p->hs.size(); ++s) {
+            HostSample &h = p->hs[s];
+            std::vector<double> d(h.delta);
+            for (int j = 0; j < h.R; ++j, ++k) {
+                last[k] = tries[k] ? (double)acc[k] / (double)tries[k] : 0.0;
+                // acceptance falls as the step grows: scale the step by the ratio
+                // of the measured to the wanted acceptance, at most x2 or /2 per
+                // round, within [1e-3, pi]
+                const double f = std::min(2.0, std::max(0.5, last[k] / target));
+                d[j] = std::min(M_PI, std::max(1e-3, d[j] * f));
+            }
+            // the last round only measures the frozen widths
+            if (round < rounds && (rc = xyl_set_delta(p, (int32_t)s, d.data(), stream))) return rc;
+        }
+    }
+    if (rate) std::copy(last.begin(), last.end(), rate);
+    return xyl_reset_observables(p, stream);
 }
 
 static int read_region(xyl_plan *p, const Region &r, void *dst, cudaStream_t st)
@@ -1017,7 +1087,28 @@ int xyl_write_spins(xyl_plan *p, int32_t sample, int32_t replica, const double *
     if (!sxy) return fail(XYL_EINVAL, "xyl_write_spins: NULL input");
     cudaStream_t st = as_stream(stream);
     if ((rc = spin_copy(p, sample, replica, nullptr, sxy, st))) return rc;
-    return do_recompute(p, 0, st);
+    // the energies of the new spins are not a drift of the FP32 update: keep
+    // the recorded maximum as it was
+    char *drift = p->ws + p->r_drift.off;
+    XYL_CUDA(cudaMemcpyAsync(drift + sizeof(double), drift, sizeof(double), cudaMemcpyDeviceToDevice, st),
+             "xyl_write_spins: save drift");
+    if ((rc = do_recompute(p, 0, st))) return rc;
+    XYL_CUDA(cudaMemcpyAsync(drift, drift + sizeof(double), sizeof(double), cudaMemcpyDeviceToDevice, st),
+             "xyl_write_spins: restore drift");
+    return XYL_OK;
+}
+
+int xyl_read_drift(xyl_plan *p, double *max_drift, int32_t reset, void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_read_drift");
+    if (rc) return rc;
+    if (!max_drift) return fail(XYL_EINVAL, "xyl_read_drift: NULL output");
+    cudaStream_t st = as_stream(stream);
+    XYL_CUDA(cudaMemcpyAsync(max_drift, p->ws + p->r_drift.off, sizeof(double), cudaMemcpyDeviceToHost, st),
+             "xyl_read_drift: copy");
+    if (reset) XYL_CUDA(cudaMemsetAsync(p->ws + p->r_drift.off, 0, sizeof(double), st), "xyl_read_drift: reset");
+    return finish_read(p, st);
 }
 
 int xyl_read_status(xyl_plan *p, int32_t *status, uint64_t *sweep_index, void *stream)

@@ -29,7 +29,8 @@ EXPORTED = (
     "xyl_write_spins", "xyl_read_status", "xyl_state_bytes", "xyl_export_state", "xyl_import_state",
     "xyl_last_launch_count", "xyl_plan_free", "xyl_sweep_units", "xyl_unit_count", "xyl_autotune",
     "xyl_get_tuning", "xyl_sweep_noalloc", "xyl_build_levy_bonds", "xyl_walk_returns", "xyl_graph_set_couplings",
-    "xyl_graph_export_couplings", "xyl_graph_set_fields", "xyl_philox",
+    "xyl_graph_export_couplings", "xyl_graph_set_fields", "xyl_philox", "xyl_read_drift",
+    "xyl_get_delta", "xyl_tune_delta", "xyl_wave_units",
 )
 
 
@@ -106,6 +107,10 @@ def load():
             "xyl_graph_export_couplings": ([P, C.POINTER(C.c_int8)], C.c_int),
             "xyl_graph_set_fields": ([P, pf64], C.c_int),
             "xyl_philox": ([P, P, i64, P, P], C.c_int),
+            "xyl_read_drift": ([P, pf64, i32, P], C.c_int),
+            "xyl_get_delta": ([P, i32, pf64], C.c_int),
+            "xyl_tune_delta": ([P, i32, i32, u32, f64, pf64, P], C.c_int),
+            "xyl_wave_units": ([P], C.c_int32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -295,6 +300,9 @@ class Plan:
     def unit_count(self) -> int:
         return int(load().xyl_unit_count(self.handle))
 
+    def wave_units(self) -> int:
+        return int(load().xyl_wave_units(self.handle))
+
     def autotune(self, n_sweeps, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1, stream=None) -> dict:
         t = Tuning()
         _check(load().xyl_autotune(self.handle, int(n_sweeps), int(ops), int(measure_every), C.byref(t),
@@ -323,6 +331,18 @@ class Plan:
     def set_delta(self, sample, delta, stream=None):
         d = np.ascontiguousarray(delta, np.float64)
         _check(load().xyl_set_delta(self.handle, sample, _p(d, C.c_double), _stream(stream)))
+
+    def get_delta(self, sample):
+        out = np.zeros(self.n_temps[sample], np.float64)
+        _check(load().xyl_get_delta(self.handle, sample, _p(out, C.c_double)))
+        return out
+
+    def tune_delta(self, rounds=8, n_sweeps=50, ops=OP_MET | OP_OR | OP_PT, target=0.5, stream=None):
+        """xyl_tune_delta: per-slot acceptance of the frozen half-widths, slot-major."""
+        rate = np.zeros(self.total_slots, np.float64)
+        _check(load().xyl_tune_delta(self.handle, int(rounds), int(n_sweeps), int(ops), float(target),
+                                     _p(rate, C.c_double), _stream(stream)))
+        return rate
 
     def read_observables(self, stream=None):
         n = self.total_slots
@@ -359,6 +379,12 @@ class Plan:
         if len(a) != self.dim * self.sizes[sample]:
             raise XylError(EINVAL, f"write_spins: need {self.dim} components per site")
         _check(load().xyl_write_spins(self.handle, sample, replica, _p(a, C.c_double), _stream(stream)))
+
+    def drift(self, reset=False, stream=None) -> float:
+        """Largest |E_fused - E_fp64| recorded by the FP64 recomputes (xyl_read_drift)."""
+        out = np.zeros(1, np.float64)
+        _check(load().xyl_read_drift(self.handle, _p(out, C.c_double), 1 if reset else 0, _stream(stream)))
+        return float(out[0])
 
     def status(self, stream=None):
         s = C.c_int32(); t = C.c_uint64()

@@ -459,6 +459,31 @@ def test_recompute_bounds_fp32_drift(env):
     assert plan.drift() == 0.0
 
 
+@pytest.mark.parametrize("shape", [dict(resident=1), dict(resident=-1)])
+def test_delta_tuning_reaches_half_acceptance(env, shape):
+    """xyl_tune_delta: after the warm-up every C2 slot (T in [0.8, 1.6], where
+    Delta < pi suffices) accepts 40-60% of its proposals with the frozen
+    half-widths, and the accumulators start from zero."""
+    xyl, wl = env
+    cfg = wl.config("C2")
+    plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, **shape)
+    plan.bind()
+    plan.init_spins()
+    d0 = plan.get_delta(0)
+    rate = plan.tune_delta(rounds=8, n_sweeps=50)
+    d = plan.get_delta(0)
+    assert np.all((rate > 0.4) & (rate < 0.6)), rate
+    assert np.all((d > 0) & (d <= np.pi)) and not np.allclose(d, d0)
+    assert np.all(np.diff(d) > 0)  # hotter slots take wider steps
+    st = plan.read_observables()
+    assert not st["acc"].any() and not st["met_try"].any()
+    # the frozen widths hold: a further block accepts about half as well
+    plan.sweep(100, 1 | 2 | 4)
+    st = plan.read_observables()
+    r = st["met_acc"] / st["met_try"]
+    assert np.all((r > 0.35) & (r < 0.65)), r
+
+
 @pytest.mark.parametrize("shape", [dict(group=4, resident=-1), dict(group=1, cluster=4, resident=1)])
 def test_split_sample_wait_times_out_and_recovers(env, shape):
     """Running one of a sample's replica groups alone makes its bounded wait for

@@ -294,6 +294,8 @@ def test_calls_before_bind_report_the_call_order(xyl):
         "xyl_read_energies": lambda q: lib.xyl_read_energies(q, buf, None),
         "xyl_read_spins": lambda q: lib.xyl_read_spins(q, 0, 0, buf, None),
         "xyl_export_state": lambda q: lib.xyl_export_state(q, buf, 64 * 8, None),
+        "xyl_read_drift": lambda q: lib.xyl_read_drift(q, buf, 0, None),
+        "xyl_tune_delta": lambda q: lib.xyl_tune_delta(q, 2, 10, 3, 0.5, buf, None),
     }
     for name, call in calls.items():
         assert call(h) == xyl.ESTATE, name
