@@ -128,9 +128,12 @@ def _profile_traffic(kernel, config):
     if vals.get("source_sha256") != kernel_source_digest(kernel):
         return None
     try:
-        return {"bytes_per_launch": float(vals["dram_bytes_per_launch"]),
-                "scales": not vals.get("traffic_scales_with_sweeps", "yes").startswith("no"),
-                "sweeps_per_launch": float(vals["sweeps_per_launch"])}
+        out = {"bytes_per_launch": float(vals["dram_bytes_per_launch"]),
+               "scales": not vals.get("traffic_scales_with_sweeps", "yes").startswith("no"),
+               "sweeps_per_launch": float(vals["sweeps_per_launch"])}
+        if "site_updates_per_launch" in vals:
+            out["updates_per_launch"] = float(vals["site_updates_per_launch"])
+        return out
     except (KeyError, ValueError):
         return None
 
@@ -204,33 +207,65 @@ def run_oracle_parallel(cfg, seconds, measure_every, procs, sweeps=0):
     return sum(u / dt for u, dt, _ in res), res
 
 
+def _oracle_steps_worker(job):
+    """One oracle process: build sample k once, then warm-up and timed chunks
+    of `sweeps` sweeps; returns (site-updates per chunk, [seconds per timed chunk])."""
+    name, max_samples, k, sweeps, warmup, steps, measure_every = job
+    import oracle
+    from paper_1211_3991_gb300 import workloads as wl
+    cfg = wl.config(name)
+    if max_samples > 0:
+        cfg = wl.first_samples(cfg, max_samples)
+    L, rho, _ = cfg.graphs[k]
+    if cfg.ensemble == "bonds":
+        ei, ej, _ = oracle.levy_bonds(L, rho, wl.GRAPH_SEED, wl.graph_stream_id(cfg, k), fbc=cfg.boundary == "fbc")
+    else:
+        ei, ej, _, _ = oracle.levy_graph(L, wl.Z, rho, wl.GRAPH_SEED, wl.graph_stream_id(cfg, k))
+    color, _ = oracle.slo_color(L * L, ei, ej)
+    sim = oracle.Sim(L * L, ei, ej, color, cfg.betas(), cfg.deltas(), wl.SPIN_SEED, sample=wl.graph_stream_id(cfg, k),
+                     xy=oracle.lattice_xy(L), L=L, dim=cfg.spin_dim)
+    J = wl.couplings_for(cfg, k, len(ei))
+    if J is not None:
+        sim.set_couplings(J.astype(float))
+    h = wl.fields_for(cfg, k, L * L)
+    if h is not None:
+        sim.set_fields(h)
+    sim.init()
+    for _ in range(warmup):
+        sim.sweeps(sweeps, OPS_ALL, measure_every)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        sim.sweeps(sweeps, OPS_ALL, measure_every)
+        times.append(time.perf_counter() - t0)
+    sim.close()
+    return L * L * cfg.n_temps * 2 * sweeps, times
+
+
 def reference_arm(args, cfg):
+    """The oracle as it stands on the host cores: one process per independent
+    sample (one sample: one core), each building its sample once, then
+    `warmup` + `steps` chunks of sweeps (about a second each); the rate is the
+    sum of the processes' rates."""
     rank, world, _ = _env_rank()
     if rank != 0:
         return
+    import multiprocessing as mp
     import oracle
     oracle.build()
-    per_step = args.ref_sweeps
-    # one sample: one host core; several independent samples: one process per core
     procs = min(cfg.n_samples, os.cpu_count() or 1)
-    for _ in range(args.warmup):
-        run_oracle_sample(cfg, per_step, measure_every=args.measure_every)
-    rates, secs = [], 0.0
-    for _ in range(args.steps):
-        if procs > 1:
-            rate, res = run_oracle_parallel(cfg, 0.0, args.measure_every, procs, sweeps=per_step)
-            dt = max(t for _, t, _ in res)
-        else:
-            u, dt, _ = run_oracle_sample(cfg, per_step, measure_every=args.measure_every)
-            rate = u / dt
-        rates.append(rate)
-        secs += dt
-    value = sum(rates) / len(rates)
+    per_sweep = 2 * cfg.spins_per_sweep() / cfg.n_samples
+    per_step = args.ref_sweeps or int(max(1, round(2.5e7 / per_sweep)))
+    jobs = [(cfg.name, args.max_samples, k, per_step, args.warmup, args.steps, args.measure_every) for k in range(procs)]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(_oracle_steps_worker, jobs)
+    value = sum(u * len(t) / sum(t) for u, t in res)
+    ms_step = 1e3 * max(sum(t) for _, t in res) / args.steps
     sample = (f"{per_step} sweeps of sample 0 of {cfg.name} ({cfg.description}) per step" if procs == 1 else
               f"{per_step} sweeps of each of samples 0..{procs - 1} of {cfg.name}, one process each, per step")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{cfg.name}: {cfg.description}", "engine": "sequential FP64 CPU oracle"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample},
@@ -330,70 +365,89 @@ def walk_bench(args):
         dist.destroy_process_group()
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="C2")
-    ap.add_argument("--sweeps-per-step", type=int, default=0, help="0 = calibrate to about 50 ms per step")
-    ap.add_argument("--block", type=int, default=0)
-    ap.add_argument("--cluster", type=int, default=0)
-    ap.add_argument("--group", type=int, default=0)
-    ap.add_argument("--resident", type=int, default=0, choices=[-1, 0, 1],
-                    help="1 = spins in shared memory for a launch, -1 = global-memory shape, 0 = library/autotuner")
-    ap.add_argument("--ref-sweeps", type=int, default=50, help="oracle sweeps per step of --impl reference (about 1 s)")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample: oracle time to run")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--measure-every", type=int, default=32, help="sweeps between measurements (the paper: 32)")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "walk"],
-                    help="sweep: the Monte Carlo sampler (default); walk: random walks for the spectral dimension")
-    ap.add_argument("--walkers", type=int, default=1 << 20)
-    ap.add_argument("--walk-steps", type=int, default=1000)
-    args = ap.parse_args()
-    if args.workload == "walk":
-        if args.impl == "reference":
-            raise SystemExit("--impl reference times the sampler workload only")
-        walk_bench(args)
-        return
+# Secondary ceilings measured on this GB300 by the project's own probes (CUDA
+# events, 2.07 GHz): MEASURED_PEAKS.json holds only the HBM copy and BF16 GEMM.
+SMEM_GATHER_PROBE_GBS = 15000.0  # random 8-byte gathers from shared memory, 128 KB per CTA, every SM
+L2_STREAM_PROBE_GBS = 19300.0    # streaming reads of a 64 MiB L2-resident buffer
+L2_BYTES = 126 << 20             # L2 capacity usable for a resident working set
 
-    from paper_1211_3991_gb300 import workloads as wl
-    cfg = wl.config(args.config)
-    if args.impl == "reference":
-        reference_arm(args, cfg)
-        return
 
+def roofline_for(plan, cfg, per_launch_updates, avg_launch_s, name, spins_live_bytes):
+    """Roofline of the kernel a plan runs, against the ceiling its schedule
+    meets: spins held in shared memory for a whole launch -> on-chip gather
+    model vs the shared-memory gather probe; spins in global memory with a
+    launch wave's spins within L2 -> L2 gather model vs the L2 probe; else the
+    compulsory HBM model vs the measured HBM copy bandwidth."""
+    R, dim = cfg.n_temps, cfg.spin_dim
+    kernel = kernel_name(plan)
+    hbm_peak, hbm_kind = _peaks()
+    models = {"hbm_compulsory": hbm_bytes_per_update(R, dim), "gather": l2_bytes_per_update(R, dim)}
+    achieved = {k: b * per_launch_updates / avg_launch_s / 1e9 for k, b in models.items()}
+    if kernel == "resident_kernel":
+        bound, b, peak, kind = "smem", models["gather"], SMEM_GATHER_PROBE_GBS, \
+            "own probe: shared-memory random 8-byte gathers"
+        basis = "spins held in shared memory for the whole launch: (z+1) 8-B spin reads + one 8-B write per update"
+    elif spins_live_bytes <= L2_BYTES:
+        bound, b, peak, kind = "l2", models["gather"], L2_STREAM_PROBE_GBS, "own probe: L2-resident stream read"
+        basis = f"a launch wave's spins ({spins_live_bytes / 2**20:.0f} MiB) stay in L2: gather model"
+    else:
+        bound, b, peak, kind = "hbm", models["hbm_compulsory"], hbm_peak, hbm_kind
+        basis = (f"a launch wave's spins ({spins_live_bytes / 2**30:.2f} GiB) exceed L2: compulsory model, each spin "
+                 "read and written once per pass")
+    a = b * per_launch_updates / avg_launch_s / 1e9
+    prof = _profile_traffic(kernel, name)
+    traffic = None
+    if prof is not None:
+        # DRAM bytes of the captured launch, scaled to this launch by its site-updates
+        # (a capture of a subset of the workload) unless they do not grow with it
+        if not prof["scales"]:
+            traffic = prof["bytes_per_launch"]
+        elif "updates_per_launch" in prof:
+            traffic = prof["bytes_per_launch"] * per_launch_updates / prof["updates_per_launch"]
+        else:
+            traffic = prof["bytes_per_launch"] * per_launch_updates / (cfg.spins_per_sweep() * 2) / \
+                prof["sweeps_per_launch"]
+    return {"bound": bound, "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak, "traffic": traffic,
+            "peak_kind": kind, "bytes_per_update": b, "kernel": kernel, "basis": basis,
+            "other_models_GBps": {k: v for k, v in achieved.items()}}
+
+
+def spins_live_bytes(plan, cfg):
+    """Bytes of spins the units of one launch wave keep live (all of them when
+    one wave runs the whole batch; the plain engines run it all at once)."""
+    units = plan.unit_count()
+    frac = min(1.0, plan.wave_units() / units) if units else 1.0
+    return frac * cfg.spins_per_sweep() * (8 if cfg.spin_dim == 2 else 16)
+
+
+def measure_workload(args, name, xyl, wl, dev, stream, flush, rank, world, steps, warmup, full):
+    """Time one workload: FP32 sampler (Delta tuned in the library, launch shape
+    autotuned), the FP64 plain engine on the same batch, and, for the headline
+    workload (full=True), the end-to-end loop and the clock record."""
+    import numpy as np
     import torch
-    import torch.distributed as dist
-    from paper_1211_3991_gb300 import build as libbuild
-    libbuild.build()
-    from paper_1211_3991_gb300 import xyl
-
-    rank, world, local = _env_rank()
-    if world > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-
+    cfg = wl.config(name)
+    if args.max_samples > 0:
+        cfg = wl.first_samples(cfg, args.max_samples)
     # every rank runs its own disorder realisations; no data-path collective
     cfg = wl.shard(cfg, rank, world)
     graphs = wl.build_graphs(cfg)
-    stream = torch.cuda.current_stream()
     # O(3) spins run on the plain engine; XY on the batched engine
     engine_name = "FP32_PLAIN" if cfg.spin_dim == 3 else "FP32_BATCHED"
     tune = dict(block=args.block, cluster=args.cluster, group=args.group, resident=args.resident)
-    if cfg.spin_dim == 3:
+    if cfg.spin_dim == 3 or not full:
         tune = {}
     plan, _ = wl.make_plan(cfg, getattr(xyl, engine_name), graphs=graphs, **tune)
     plan.bind(stream)
     plan.init_spins(stream=stream)
-    if engine_name == "FP32_BATCHED" and not (args.block or args.cluster or args.group) and not args.no_autotune:
-        plan.autotune(32, OPS_ALL, args.measure_every, stream=stream)
+    # Metropolis half-widths: warm-up to about 50% acceptance, then frozen
+    rates = None
+    if not args.no_tune_delta:
+        rates = plan.tune_delta(rounds=args.tune_rounds, n_sweeps=args.tune_sweeps, ops=1 | 2 | 4, stream=stream)
+    explicit = full and (args.block or args.cluster or args.group)
+    if engine_name == "FP32_BATCHED" and not explicit and not args.no_autotune:
+        plan.autotune(args.autotune_sweeps, OPS_ALL, args.measure_every, stream=stream)
     updates_per_sweep = cfg.spins_per_sweep() * 2
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def timed_steps(p, n_steps, sweeps):
         total_ms, launches = 0.0, 0
@@ -408,80 +462,160 @@ def main():
             launches += p.last_launch_count()
         return total_ms, launches
 
-    # calibrate the step length
-    sweeps = args.sweeps_per_step
+    # calibrate the step length (about 50 ms, at least min_sweeps sweeps)
+    sweeps = args.sweeps_per_step if full else 0
     if sweeps <= 0:
-        ms, _ = timed_steps(plan, 1, 50)
-        sweeps = int(min(20000, max(50, round(50.0 / max(ms / 50, 1e-6) / 10) * 10)))
-    for _ in range(args.warmup):
+        probe = max(2, args.min_sweeps)
+        ms, _ = timed_steps(plan, 1, probe)
+        sweeps = int(min(20000, max(args.min_sweeps, round(50.0 / max(ms / probe, 1e-6)))))
+    for _ in range(warmup):
         timed_steps(plan, 1, sweeps)
 
     def barrier():
         if world > 1:
+            import torch.distributed as dist
             dist.barrier()
         torch.cuda.synchronize()
 
     barrier()
-    clocks = ClockSampler(local)
-    total_ms, launches = timed_steps(plan, args.steps, sweeps)
-    clock_info = clocks.stop()
+    clocks = ClockSampler(torch.cuda.current_device()) if full else None
+    total_ms, launches = timed_steps(plan, steps, sweeps)
+    clock_info = clocks.stop() if clocks else None
     barrier()
-    max_ms, units = reduce_over_ranks(total_ms, updates_per_sweep * sweeps * args.steps, world, dev)
+    max_ms, units = reduce_over_ranks(total_ms, updates_per_sweep * sweeps * steps, world, dev)
     value = units / (max_ms / 1e3)
 
-    # end to end through the public API with host buffers: per step the slot
-    # half-widths go host->device, the step's measurements come back device->host
-    import numpy as np
-    deltas = np.array(cfg.deltas(), np.float64)
-    h2d = d2h = 0
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        for s in range(cfg.n_samples):
-            plan.set_delta(s, deltas, stream=stream)
-        h2d = deltas.nbytes * cfg.n_samples
-        plan.sweep(sweeps, OPS_ALL, args.measure_every, stream=stream)
-        obs = plan.read_observables(stream=stream)
-        d2h = sum(v.nbytes for v in obs.values())
-        plan.reset_observables(stream=stream)
-    barrier()
-    e2e_s = time.perf_counter() - t0
-    e2e_max_s, e2e_units = reduce_over_ranks(e2e_s, updates_per_sweep * sweeps * args.steps, world, dev)
-    e2e = {"value": e2e_units / e2e_max_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    e2e = None
+    if full:
+        # end to end through the public API with host buffers: per step the slot
+        # half-widths go host->device, the step's measurements come back device->host
+        deltas = [plan.get_delta(s) for s in range(cfg.n_samples)]
+        h2d = d2h = 0
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            for s in range(cfg.n_samples):
+                plan.set_delta(s, deltas[s], stream=stream)
+            h2d = sum(d.nbytes for d in deltas)
+            plan.sweep(sweeps, OPS_ALL, args.measure_every, stream=stream)
+            obs = plan.read_observables(stream=stream)
+            d2h = sum(v.nbytes for v in obs.values())
+            plan.reset_observables(stream=stream)
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        e2e_max_s, e2e_units = reduce_over_ranks(e2e_s, updates_per_sweep * sweeps * steps, world, dev)
+        e2e = {"value": e2e_units / e2e_max_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     status, _ = plan.status(stream=stream)
     if status != 0:
         raise SystemExit(f"device status {status}")
 
-    # FP64 plain kernel on the same workload, same GPU
+    # FP64 plain kernel on the same workload and GPU, same half-widths
     fp64 = None
     if not args.no_fp64:
         p64, _ = wl.make_plan(cfg, xyl.FP64_PLAIN, graphs=graphs)
         p64.bind(stream)
+        for s in range(cfg.n_samples):
+            p64.set_delta(s, plan.get_delta(s), stream=stream)
         p64.init_spins(stream=stream)
-        s64 = max(10, sweeps // 20)
-        timed_steps(p64, 1, s64)
-        n64 = max(3, min(args.steps, 5))
+        ms1, _ = timed_steps(p64, 1, 2)
+        s64 = int(max(2, min(sweeps, round(100.0 / max(ms1 / 2, 1e-6)))))
+        n64 = max(3, min(steps, 5))
         ms64, _ = timed_steps(p64, n64, s64)
         fp64 = updates_per_sweep * s64 * n64 / (ms64 / 1e3)
         del p64
 
-    peak, peak_kind = _peaks()
-    R = cfg.n_temps
     avg_launch_s = (total_ms / 1e3) / max(1, launches)
-    per_launch_updates = updates_per_sweep * sweeps * args.steps / max(1, launches)
-    dim = cfg.spin_dim
-    achieved = hbm_bytes_per_update(R, dim) * per_launch_updates / avg_launch_s / 1e9
-    prof = _profile_traffic(kernel_name(plan), args.config)
-    traffic = None
-    if prof is not None:
-        per_launch_sweeps = sweeps * args.steps / max(1, launches)
-        traffic = prof["bytes_per_launch"] * (per_launch_sweeps / prof["sweeps_per_launch"] if prof["scales"] else 1.0)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_kind": peak_kind, "bytes_per_update": hbm_bytes_per_update(R, dim),
-                "kernel": kernel_name(plan)}
-    l2_achieved = l2_bytes_per_update(R, dim) * per_launch_updates / avg_launch_s / 1e9
+    per_launch_updates = updates_per_sweep * sweeps * steps / max(1, launches)
+    roof = roofline_for(plan, cfg, per_launch_updates, avg_launch_s, name, spins_live_bytes(plan, cfg))
+    out = {
+        "value": value, "ms_per_step": max_ms / steps, "sweeps_per_step": sweeps, "launches": int(launches),
+        "workload": f"{cfg.name}: {cfg.description}", "engine": engine_name, "cluster": plan_shape(plan),
+        "samples": cfg.n_samples, "temperatures": cfg.n_temps,
+        "fp64_plain": {"value": fp64, "unit": UNIT,
+                       "ratio_fp32_batched_over_fp64_plain": (value / world / fp64) if fp64 else None},
+        "roofline": roof, "e2e": e2e, "clocks": clock_info,
+    }
+    if rates is not None:
+        out["metropolis_acceptance"] = {"tuned_to": 0.5, "min": float(np.min(rates)), "max": float(np.max(rates)),
+                                        "per_slot_sample0": [round(float(x), 3) for x in rates[:cfg.n_temps]],
+                                        "delta_sample0": [round(float(x), 4) for x in plan.get_delta(0)]}
+    del plan
+    return out, cfg
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="C5")
+    ap.add_argument("--extra-configs", default="C2,C3",
+                    help="comma-separated workloads also measured (shorter) and reported in the same line; '' = none")
+    ap.add_argument("--extra-steps", type=int, default=5)
+    ap.add_argument("--sweeps-per-step", type=int, default=0, help="0 = calibrate to about 50 ms per step")
+    ap.add_argument("--min-sweeps", type=int, default=8, help="least sweeps per step when calibrating")
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--cluster", type=int, default=0)
+    ap.add_argument("--group", type=int, default=0)
+    ap.add_argument("--resident", type=int, default=0, choices=[-1, 0, 1],
+                    help="1 = spins in shared memory for a launch, -1 = global-memory shape, 0 = library/autotuner")
+    ap.add_argument("--ref-sweeps", type=int, default=0,
+                    help="oracle sweeps per step of --impl reference (0 = about 1 s of the workload's sample)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample: oracle time to run")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--autotune-sweeps", type=int, default=8)
+    ap.add_argument("--no-tune-delta", action="store_true")
+    ap.add_argument("--tune-rounds", type=int, default=6)
+    ap.add_argument("--tune-sweeps", type=int, default=40)
+    ap.add_argument("--measure-every", type=int, default=32, help="sweeps between measurements (the paper: 32)")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "walk"],
+                    help="sweep: the Monte Carlo sampler (default); walk: random walks for the spectral dimension")
+    ap.add_argument("--max-samples", type=int, default=0,
+                    help="run only the first N samples of the workload (0 = all), e.g. for a profiler capture")
+    ap.add_argument("--walkers", type=int, default=1 << 20)
+    ap.add_argument("--walk-steps", type=int, default=1000)
+    args = ap.parse_args()
+    if args.workload == "walk":
+        if args.impl == "reference":
+            raise SystemExit("--impl reference times the sampler workload only")
+        walk_bench(args)
+        return
+
+    from paper_1211_3991_gb300 import workloads as wl
+    if args.impl == "reference":
+        cfg = wl.config(args.config)
+        if args.max_samples > 0:
+            cfg = wl.first_samples(cfg, args.max_samples)
+        reference_arm(args, cfg)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1211_3991_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1211_3991_gb300 import xyl
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    head, cfg = measure_workload(args, args.config, xyl, wl, dev, stream, flush, rank, world, args.steps,
+                                 args.warmup, True)
+    extras = {}
+    for name in [n for n in args.extra_configs.split(",") if n and n != args.config]:
+        res, _ = measure_workload(args, name, xyl, wl, dev, stream, flush, rank, world, args.extra_steps,
+                                  min(args.warmup, 3), False)
+        extras[name] = {k: res[k] for k in ("value", "ms_per_step", "sweeps_per_step", "workload", "cluster",
+                                            "fp64_plain", "roofline", "metropolis_acceptance") if k in res}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -500,22 +634,23 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{cfg.name}: {cfg.description}", "engine": engine_name,
-                       "sweeps_per_step": sweeps, "samples_on_rank0": cfg.n_samples, "temperatures": R,
+            "config": {"workload": head["workload"], "engine": head["engine"],
+                       "sweeps_per_step": head["sweeps_per_step"], "samples_on_rank0": head["samples"],
+                       "temperatures": head["temperatures"],
                        "l2": "flushed (256 MiB write) between timed steps",
                        "measure_every": args.measure_every,
-                       "cluster": plan_shape(plan), "parallelism": f"dp{world} (independent samples per rank)"},
-            "fp64_plain": {"value": fp64, "unit": UNIT, "ratio_fp32_batched_over_fp64_plain":
-                           (value / world / fp64) if fp64 else None},
-            "roofline": roofline,
-            "roofline_l2_model": {"bytes_per_update": l2_bytes_per_update(R, dim), "achieved_GBps": l2_achieved},
+                       "cluster": head["cluster"], "parallelism": f"dp{world} (independent samples per rank)"},
+            "fp64_plain": head["fp64_plain"],
+            "roofline": head["roofline"],
+            "metropolis_acceptance": head.get("metropolis_acceptance"),
             "cpu_baseline": cpu,
-            "e2e": e2e,
-            "gpu_launches": int(launches),
-            "clocks": clock_info,
+            "e2e": head["e2e"],
+            "gpu_launches": head["launches"],
+            "clocks": head["clocks"],
+            "extra_configs": extras,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -142,6 +142,18 @@ def config(name: str) -> Config:
     raise KeyError(name)
 
 
+def first_samples(cfg: Config, n: int) -> Config:
+    """The first n samples of a configuration (same stream ids), e.g. a subset
+    small enough for a profiler capture."""
+    import copy
+    out = copy.copy(cfg)
+    n = max(1, min(n, cfg.n_samples))
+    out.stream_ids = [graph_stream_id(cfg, k) for k in range(n)]
+    out.graphs = cfg.graphs[:n]
+    out.description = f"{cfg.description}; first {n} of its {cfg.n_samples} samples"
+    return out
+
+
 def shard(cfg: Config, rank: int, world: int) -> Config:
     """Rank `rank` of `world`: its own disorder realisations.
 
