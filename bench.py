@@ -434,7 +434,7 @@ def measure_workload(args, name, xyl, wl, dev, stream, flush, rank, world, steps
     graphs = wl.build_graphs(cfg)
     # O(3) spins run on the plain engine; XY on the batched engine
     engine_name = "FP32_PLAIN" if cfg.spin_dim == 3 else "FP32_BATCHED"
-    tune = dict(block=args.block, cluster=args.cluster, group=args.group, resident=args.resident)
+    tune = dict(block=args.block, cluster=args.cluster, group=args.group, resident=args.resident, waves=args.waves)
     if cfg.spin_dim == 3 or not full:
         tune = {}
     plan, _ = wl.make_plan(cfg, getattr(xyl, engine_name), graphs=graphs, **tune)
@@ -445,8 +445,11 @@ def measure_workload(args, name, xyl, wl, dev, stream, flush, rank, world, steps
     if not args.no_tune_delta:
         rates = plan.tune_delta(rounds=args.tune_rounds, n_sweeps=args.tune_sweeps, ops=1 | 2 | 4, stream=stream)
     explicit = full and (args.block or args.cluster or args.group)
+    autotune_s = None
     if engine_name == "FP32_BATCHED" and not explicit and not args.no_autotune:
+        t0 = time.perf_counter()
         plan.autotune(args.autotune_sweeps, OPS_ALL, args.measure_every, stream=stream)
+        autotune_s = time.perf_counter() - t0
     updates_per_sweep = cfg.spins_per_sweep() * 2
 
     def timed_steps(p, n_steps, sweeps):
@@ -535,7 +538,7 @@ def measure_workload(args, name, xyl, wl, dev, stream, flush, rank, world, steps
         "samples": cfg.n_samples, "temperatures": cfg.n_temps,
         "fp64_plain": {"value": fp64, "unit": UNIT,
                        "ratio_fp32_batched_over_fp64_plain": (value / world / fp64) if fp64 else None},
-        "roofline": roof, "e2e": e2e, "clocks": clock_info,
+        "roofline": roof, "e2e": e2e, "clocks": clock_info, "autotune_s": autotune_s,
     }
     if rates is not None:
         out["metropolis_acceptance"] = {"tuned_to": 0.5, "min": float(np.min(rates)), "max": float(np.max(rates)),
@@ -562,13 +565,15 @@ def main():
     ap.add_argument("--group", type=int, default=0)
     ap.add_argument("--resident", type=int, default=0, choices=[-1, 0, 1],
                     help="1 = spins in shared memory for a launch, -1 = global-memory shape, 0 = library/autotuner")
+    ap.add_argument("--waves", type=int, default=0, choices=[-1, 0, 1],
+                    help="global-memory shape: 1 = launch waves sized to L2, -1 = never, 0 = library/autotuner")
     ap.add_argument("--ref-sweeps", type=int, default=0,
                     help="oracle sweeps per step of --impl reference (0 = about 1 s of the workload's sample)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample: oracle time to run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--autotune-sweeps", type=int, default=8)
+    ap.add_argument("--autotune-sweeps", type=int, default=4)
     ap.add_argument("--no-tune-delta", action="store_true")
     ap.add_argument("--tune-rounds", type=int, default=6)
     ap.add_argument("--tune-sweeps", type=int, default=40)
@@ -650,6 +655,7 @@ def main():
             "e2e": head["e2e"],
             "gpu_launches": head["launches"],
             "clocks": head["clocks"],
+            "autotune_s": head["autotune_s"],
             "extra_configs": extras,
         }
         print(json.dumps(line), flush=True)
@@ -663,7 +669,8 @@ def plan_shape(plan):
         return {"plain": True, "threads_per_cta": 256}
     t = plan.tuning()
     return {"spins_in_shared_memory": t["resident"] > 0, "units": plan.unit_count(), "replicas_per_group": t["group"],
-            "ctas_per_cluster": t["cluster"], "threads_per_cta": t["block"], "csr_in_shared_memory": t["stage"] > 0}
+            "ctas_per_cluster": t["cluster"], "threads_per_cta": t["block"], "csr_in_shared_memory": t["stage"] > 0,
+            "l2_sized_waves": t["waves"] > 0, "units_per_launch": plan.wave_units()}
 
 
 def kernel_name(plan):

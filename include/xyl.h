@@ -216,7 +216,8 @@ typedef struct {
     int32_t stage;           /* batched engine: 0 = stage CSR rows in shared memory when they fit, -1 = never */
     int32_t resident;        /* batched engine: 1 = resident shape, -1 = never, 0 = library's choice (below) */
     int32_t spin_dim;        /* spin components: 0 or 2 = XY; 3 = O(3) (plain engines, no fields; see below) */
-    int32_t reserved[1];
+    int32_t waves;           /* batched engine, global-memory shape: 1 = cap each launch wave to the samples whose
+                                spins and tables fit in L2, -1 = never, 0 = library's choice (never) */
 } xyl_tuning;
 
 /*

@@ -134,6 +134,43 @@ __device__ __forceinline__ Words4 first_draw(const DevPlan &P, const DevSample &
     return x;
 }
 
+// Where the neighbour ids of one item come from, and its random-stream key;
+// fetched one item ahead of its use so that an update waits on one memory
+// round trip (its neighbours' spins), not three.
+template <int DEG>
+struct GRow {
+    int nb[DEG > 0 ? DEG : 1];  // fixed degree, rows in global memory: the ids themselves
+    int rb, deg;                 // otherwise: the row's start (staged rows or global CSR) and length
+    uint32_t key;
+};
+
+template <bool IS_MET, bool STAGED, int DEG>
+__device__ __forceinline__ void fetch_grow(const DevPlan &P, const DevSample &d, const BatchedParams &bp,
+                                           const Staged &stg, int i, int l, GRow<DEG> &row)
+{
+    if (STAGED) {
+        row.rb = l * bp.max_deg;
+        row.deg = DEG > 0 ? DEG : stg.deg[l];
+        if (IS_MET) row.key = (uint32_t)stg.site_id[l];
+    } else if (DEG > 0) {
+        // every row holds DEG ids and starts at DEG * i: no row_ptr read; the
+        // rows of a sample start at an even offset, so ids come in pairs
+        const int2 *c = reinterpret_cast<const int2 *>(P.col + d.col_off + (int64_t)DEG * i);
+#pragma unroll
+        for (int k = 0; k < DEG / 2; ++k) {
+            const int2 w = __ldg(c + k);
+            row.nb[2 * k] = w.x;
+            row.nb[2 * k + 1] = w.y;
+        }
+        row.deg = DEG;
+        if (IS_MET) row.key = (uint32_t)__ldg(P.perm + d.site_off + i);
+    } else {
+        row.rb = __ldg(P.row_ptr + d.row_off + i);
+        row.deg = __ldg(P.row_ptr + d.row_off + i + 1) - row.rb;
+        if (IS_MET) row.key = (uint32_t)__ldg(P.perm + d.site_off + i);
+    }
+}
+
 template <bool IS_MET, bool FUSE_E, bool STAGED, int RV, int DEG, bool DISORDER>
 __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, const SharedState &sh,
                                       const BatchedParams &bp, const Staged &stg, int c, uint32_t t, Lane<RV> &ln,
@@ -145,26 +182,22 @@ __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, cons
     const int R = d.R;
     const float2 *sp = reinterpret_cast<const float2 *>(P.spins) + d.spin_off + ln.r0;
     float2 *spw = reinterpret_cast<float2 *>(P.spins) + d.spin_off + ln.r0;
-    const int32_t *rp = P.row_ptr + d.row_off;
     const int32_t *cl = P.col + d.col_off;
 
-    for (int q = threadIdx.x; q < items; q += blockDim.x) {
-        const int off = q >> bp.log2lps;
-        const int i = lo + off;
-        const int *nb;
-        int deg;
-        uint32_t site_key = 0;
-        if (STAGED) {
-            const int l = base + off;
-            nb = stg.col + (size_t)l * bp.max_deg;
-            deg = DEG > 0 ? DEG : stg.deg[l];
-            if (IS_MET) site_key = (uint32_t)stg.site_id[l];
-        } else {
-            const int rb = __ldg(rp + i);
-            nb = cl + rb;
-            deg = __ldg(rp + i + 1) - rb;
-            if (IS_MET) site_key = (uint32_t)__ldg(P.perm + d.site_off + i);
-        }
+    int q = threadIdx.x;
+    if (q >= items) return;
+    // rows staged in shared memory are read where they are used; rows in
+    // global memory one item ahead
+    GRow<DEG> cur;
+    if (!STAGED) fetch_grow<IS_MET, STAGED, DEG>(P, d, bp, stg, lo + (q >> bp.log2lps), 0, cur);
+    for (; q < items; q += blockDim.x) {
+        const int i = lo + (q >> bp.log2lps);
+        GRow<DEG> nxt;
+        const int qn = q + (int)blockDim.x;
+        if (STAGED)
+            fetch_grow<IS_MET, STAGED, DEG>(P, d, bp, stg, i, base + (q >> bp.log2lps), cur);
+        else if (qn < items)
+            fetch_grow<IS_MET, STAGED, DEG>(P, d, bp, stg, lo + (qn >> bp.log2lps), 0, nxt);
         float2 s[RV];
         load_spins<RV>(sp + i * R, s);
         float hx[RV], hy[RV], lx[RV], ly[RV];
@@ -193,14 +226,14 @@ __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, cons
         if (DEG > 0) {
             // every site has exactly DEG links
 #pragma unroll
-            for (int k = 0; k < DEG; ++k) gather(STAGED ? nb[k] : __ldg(nb + k));
+            for (int k = 0; k < DEG; ++k) gather(STAGED ? stg.col[cur.rb + k] : cur.nb[k]);
         } else if (DEG < 0) {
             // at most -DEG links
 #pragma unroll
             for (int k = 0; k < -DEG; ++k)
-                if (k < deg) gather(STAGED ? nb[k] : __ldg(nb + k));
+                if (k < cur.deg) gather(STAGED ? stg.col[cur.rb + k] : __ldg(cl + cur.rb + k));
         } else {
-            for (int k = 0; k < deg; ++k) gather(STAGED ? nb[k] : __ldg(nb + k));
+            for (int k = 0; k < cur.deg; ++k) gather(STAGED ? stg.col[cur.rb + k] : __ldg(cl + cur.rb + k));
         }
         if (DISORDER && P.field) {
             // the site's own field after its neighbours; the fused energy takes -h_i . S_i once
@@ -217,7 +250,7 @@ __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, cons
         }
         float2 n[RV];
         if (IS_MET) {
-            const Words4 x = (q == (int)threadIdx.x) ? first : met_block_f32(site_key, t, ln.r0, d.sample_id, P.key);
+            const Words4 x = (q == (int)threadIdx.x) ? first : met_block_f32(cur.key, t, ln.r0, d.sample_id, P.key);
             bool any = false;
 #pragma unroll
             for (int v = 0; v < RV; ++v) {
@@ -239,6 +272,7 @@ __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, cons
 #pragma unroll
             for (int v = 0; v < RV; ++v) ln.e[v] -= n[v].x * lx[v] + n[v].y * ly[v];
         }
+        if (!STAGED) cur = nxt;
     }
 }
 

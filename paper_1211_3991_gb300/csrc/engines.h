@@ -40,6 +40,7 @@ struct BatchedShape {
     // resident shape: one CTA per replica group holds the group's spins of
     // every site in shared memory; the groups of a sample form one cluster
     bool resident = false;
+    bool l2_waves = false;  // global-memory shape: launch waves hold as many samples as fit in L2
     int gpc = 1;            // replica groups per cluster (resident shape)
     int cpc = 1;            // CTAs per cluster of the resident shape, G x gpc
     int rs_csr_w = 0;       // staged CSR row width (16-bit ids), 0 = rows from global memory

@@ -46,6 +46,7 @@ struct xyl_plan {
     int recompute_every = 0;
     int stage_mode = 0;
     int resident_req = 0;   // the caller's resident setting: 1 only, -1 never, 0 either
+    int waves_req = 0;      // the caller's waves setting: 1 L2-sized, -1 never, 0 either (autotuner)
     int64_t sweeps_since_recompute = 0;
     int total_R = 0;
     int64_t total_N = 0, total_nnz = 0, total_spins = 0;
@@ -220,7 +221,7 @@ bool resident_fit(const xyl_plan *p, int g, int G, int block, int stage, Batched
 // Launch shape of the batched engine: R_g replicas per group, G CTAs per
 // cluster, `block` threads per CTA; stage < 0 disables shared-memory staging;
 // resident != 0 asks for the resident shape (G is then ignored).
-int apply_shape(xyl_plan *p, int g, int G, int block, int stage, int resident)
+int apply_shape(xyl_plan *p, int g, int G, int block, int stage, int resident, int waves = 0)
 {
     if (g < 1 || g > 32 || (g & (g - 1))) return fail(XYL_EINVAL, "group=%d must be a power of two <= 32", g);
     for (auto &h : p->hs)
@@ -265,7 +266,29 @@ int apply_shape(xyl_plan *p, int g, int G, int block, int stage, int resident)
     const size_t bytes = (size_t)owned * (size_t)(max_deg + 2) * sizeof(int32_t);
     B.staged = stage >= 0 && bytes <= kStageLimitBytes;
     B.smem_bytes = B.staged ? bytes : 0;
+    B.l2_waves = waves > 0;
     return XYL_OK;
+}
+
+// Device bytes one sample keeps live during a sweep of the global-memory
+// shape: its spins, CSR, site ids and Fourier phases.
+size_t sample_live_bytes(const HostSample &h)
+{
+    return (size_t)h.N * h.R * sizeof(float2) + h.col.size() * sizeof(int32_t) +
+           (size_t)(2 * h.N + 1) * sizeof(int32_t) + (size_t)h.N * sizeof(float4);
+}
+
+// Samples a launch wave of the global-memory shape may hold so that their
+// working set stays in L2 (three quarters of it, the rest for the sums and
+// the other traffic); at least one.
+int l2_wave_samples(const xyl_plan *p)
+{
+    int dev = 0, l2 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+        return 1;
+    size_t per = 1;
+    for (auto &h : p->hs) per = std::max(per, sample_live_bytes(h));
+    return (int)std::max<size_t>(1, (size_t)l2 * 3 / 4 / per);
 }
 
 int pick_batched_shape(xyl_plan *p, const xyl_tuning *tune)
@@ -307,7 +330,7 @@ int pick_batched_shape(xyl_plan *p, const xyl_tuning *tune)
     const double items_per_phase = (double)max_N * g / std::max(1, p->shape.max_Q);
     while (G < 16 && items_per_phase / (G * 2) >= 1024.0) G *= 2;
     if (tune && tune->cluster > 0) G = tune->cluster;
-    return apply_shape(p, g, G, block, stage, 0);
+    return apply_shape(p, g, G, block, stage, 0, tune ? tune->waves : 0);
 }
 
 // Upload the unit table of the current shape, set the kernel attributes and
@@ -379,13 +402,18 @@ int configure_batched(xyl_plan *p, cudaStream_t st)
     }
     if (groups_max > 1) {
         if (!uniform_groups) return fail(XYL_EINVAL, "batched: several groups per sample need equal n_temps");
-        const int samples_per_wave = clusters / n_groups;
+        int samples_per_wave = clusters / n_groups;
         if (samples_per_wave < 1)
             return fail(XYL_EINVAL, "batched: %d clusters of %d CTAs cannot be co-resident (max %d)", n_groups,
                         p->bshape.G, clusters);
+        if (p->bshape.l2_waves) samples_per_wave = std::min(samples_per_wave, l2_wave_samples(p));
         p->wave_units = samples_per_wave * n_groups;
     } else {
-        p->wave_units = (int)p->units.size();
+        // one group per sample: clusters never wait on one another, so a launch
+        // may hold more than fit at once (the hardware queues them), unless
+        // its waves are sized to L2
+        p->wave_units = p->bshape.l2_waves ? std::min((int)p->units.size(), l2_wave_samples(p))
+                                           : (int)p->units.size();
     }
     XYL_CUDA(cudaMemcpyAsync(p->ws + p->r_units.off, p->units.data(), p->units.size() * sizeof(int2),
                              cudaMemcpyHostToDevice, st), "batched: unit table");
@@ -415,6 +443,7 @@ int xyl_plan_create(const xyl_sample *samples, int32_t n_samples, int32_t engine
     p->shape.layout = (engine == XYL_FP32_BATCHED) ? kInterleaved : kReplicaMajor;
     p->recompute_every = tune ? std::max(0, tune->recompute_every) : 0;
     p->resident_req = tune ? tune->resident : 0;
+    p->waves_req = tune ? tune->waves : 0;
     const int dim = (tune && tune->spin_dim) ? tune->spin_dim : 2;
     if (dim != 2 && dim != 3) {
         delete p;
@@ -1206,6 +1235,7 @@ int xyl_get_tuning(const xyl_plan *p, xyl_tuning *out)
         out->group = p->bshape.Rg;
         out->stage = p->bshape.staged ? 1 : -1;
         out->resident = p->bshape.resident ? 1 : -1;
+        out->waves = p->bshape.l2_waves ? 1 : -1;
     }
     return XYL_OK;
 }
@@ -1221,6 +1251,8 @@ int xyl_autotune(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_ev
     if ((ops & XYL_OP_MEASURE) && measure_every < 1) return fail(XYL_EINVAL, "xyl_autotune: measure_every must be >= 1");
     if (!(ops & XYL_OP_MEASURE)) measure_every = 1;
     cudaStream_t st = as_stream(stream);
+    // the state is saved once and restored once: the timed tries advance the
+    // chain, which does not change how long a sweep takes
     std::vector<char> snap(xyl_state_bytes(p));
     if ((rc = xyl_export_state(p, snap.data(), snap.size(), stream))) return rc;
     const BatchedShape keep = p->bshape;
@@ -1230,48 +1262,65 @@ int xyl_autotune(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_ev
     XYL_CUDA(cudaEventCreate(&e1), "xyl_autotune: event");
     float best_ms = -1.f;
     int best_g = keep.Rg, best_G = keep.G, best_block = keep.block, best_res = keep.resident ? 1 : 0;
-    int dev = 0, n_sm = 0;
+    int best_waves = keep.l2_waves ? 1 : 0;
+    int dev = 0, n_sm = 0, l2 = 0;
     XYL_CUDA(cudaGetDevice(&dev), "xyl_autotune: device");
     XYL_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev), "xyl_autotune: SM count");
+    XYL_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev), "xyl_autotune: L2 size");
+    size_t live = 0;
+    for (auto &h : p->hs) live += sample_live_bytes(h);
+    // L2-sized waves change nothing when the whole batch fits in L2
+    const bool try_waves = live > (size_t)l2 * 3 / 4 && p->waves_req >= 0;
+    const bool large = p->total_spins >= ((int64_t)1 << 26);
     for (int res = 0; res <= 1; ++res) {
         if ((p->resident_req < 0 && res) || (p->resident_req > 0 && !res)) continue;
-        for (int g = 1; g <= 32; g *= 2) {
-            bool divides = true;
-            for (auto &h : p->hs) divides &= (h.R % g == 0);
-            if (!divides) continue;
-            int64_t units = 0;
-            for (auto &h : p->hs) units += h.R / g;
-            for (int G : {1, 2, 3, 4, 5, 6, 7, 8, 12, 16}) {
-                // global-memory shape: powers of two; split a resident group
-                // across CTAs only while the batch leaves SMs idle
-                if (!res && (G & (G - 1))) continue;
-                if (res && G > 1 && units * G > 2 * (int64_t)n_sm) continue;
-                for (int block : {128, 256, 384, 512, 640, 768, 1024}) {
-                    if (res ? block == 128 : (block == 384 || block > 672)) continue;
-                    if (apply_shape(p, g, G, block, keep_stage, res) || configure_batched(p, st)) continue;
-                    float ms = 0.f;
-                    bool ok = true;
-                    for (int rep = 0; rep < 2 && ok; ++rep) {
-                        if (xyl_import_state(p, snap.data(), snap.size(), stream)) { ok = false; break; }
-                        int64_t launches = 0;
-                        XYL_CUDA(cudaMemsetAsync(p->ws + p->r_barrier.off, 0, p->r_barrier.bytes, st), "xyl_autotune");
-                        XYL_CUDA(cudaEventRecord(e0, st), "xyl_autotune: record");
-                        if (issue_sweeps(p, n_sweeps, ops, measure_every, st, &launches)) { ok = false; break; }
-                        XYL_CUDA(cudaEventRecord(e1, st), "xyl_autotune: record");
-                        XYL_CUDA(cudaEventSynchronize(e1), "xyl_autotune: sync");
-                        XYL_CUDA(cudaEventElapsedTime(&ms, e0, e1), "xyl_autotune: time");
-                        int32_t status = 0;
-                        XYL_CUDA(cudaMemcpy(&status, p->ws + p->r_status.off, sizeof(status), cudaMemcpyDeviceToHost),
-                                 "xyl_autotune: status");
-                        if (status) ok = false;
-                    }
-                    clear_error();
-                    if (ok && (best_ms < 0.f || ms < best_ms)) {
-                        best_ms = ms;
-                        best_g = g;
-                        best_G = G;
-                        best_block = block;
-                        best_res = res;
+        for (int waves = 0; waves <= (res ? 0 : 1); ++waves) {
+            if (waves ? !try_waves : p->waves_req > 0) continue;
+            for (int g = 1; g <= 32; g *= 2) {
+                bool divides = true;
+                for (auto &h : p->hs) divides &= (h.R % g == 0);
+                if (!divides) continue;
+                int64_t units = 0;
+                for (auto &h : p->hs) units += h.R / g;
+                for (int G : {1, 2, 3, 4, 5, 6, 7, 8, 12, 16}) {
+                    // global-memory shape: powers of two and 6, 12 (a GPC holds two
+                    // clusters of 6 or 8 but one of 12 or 16); split a resident
+                    // group across CTAs only while the batch leaves SMs idle
+                    if (!res && (G & (G - 1)) && G != 6 && G != 12) continue;
+                    if (res && G > 1 && units * G > 2 * (int64_t)n_sm) continue;
+                    for (int block : {128, 256, 384, 512, 640, 768, 1024}) {
+                        if (res ? block == 128 : (block == 384 || block > 672)) continue;
+                        if (!res && large && block < 512) continue;  // large samples: many items per CTA
+                        if (apply_shape(p, g, G, block, keep_stage, res, waves) || configure_batched(p, st)) continue;
+                        float ms = 0.f;
+                        bool ok = true;
+                        for (int rep = 0; rep < 2 && ok; ++rep) {
+                            // a shape already 1.5x slower than the best on its first timing cannot win
+                            if (rep == 1 && best_ms > 0.f && ms > 1.5f * best_ms) break;
+                            int64_t launches = 0;
+                            XYL_CUDA(cudaMemsetAsync(p->ws + p->r_barrier.off, 0, p->r_barrier.bytes, st), "xyl_autotune");
+                            XYL_CUDA(cudaEventRecord(e0, st), "xyl_autotune: record");
+                            if (issue_sweeps(p, n_sweeps, ops, measure_every, st, &launches)) { ok = false; break; }
+                            XYL_CUDA(cudaEventRecord(e1, st), "xyl_autotune: record");
+                            XYL_CUDA(cudaEventSynchronize(e1), "xyl_autotune: sync");
+                            XYL_CUDA(cudaEventElapsedTime(&ms, e0, e1), "xyl_autotune: time");
+                            int32_t status = 0;
+                            XYL_CUDA(cudaMemcpy(&status, p->ws + p->r_status.off, sizeof(status), cudaMemcpyDeviceToHost),
+                                     "xyl_autotune: status");
+                            if (status) {
+                                ok = false;
+                                XYL_CUDA(cudaMemset(p->ws + p->r_status.off, 0, sizeof(int32_t)), "xyl_autotune: status");
+                            }
+                        }
+                        clear_error();
+                        if (ok && (best_ms < 0.f || ms < best_ms)) {
+                            best_ms = ms;
+                            best_g = g;
+                            best_G = G;
+                            best_block = block;
+                            best_res = res;
+                            best_waves = waves;
+                        }
                     }
                 }
             }
@@ -1279,7 +1328,7 @@ int xyl_autotune(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_ev
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if ((rc = apply_shape(p, best_g, best_G, best_block, keep_stage, best_res))) return rc;
+    if ((rc = apply_shape(p, best_g, best_G, best_block, keep_stage, best_res, best_waves))) return rc;
     if ((rc = configure_batched(p, st))) return rc;
     if ((rc = xyl_import_state(p, snap.data(), snap.size(), stream))) return rc;
     if (best) xyl_get_tuning(p, best);

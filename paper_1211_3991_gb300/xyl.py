@@ -48,7 +48,7 @@ class Sample(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("block", C.c_int32), ("cluster", C.c_int32), ("group", C.c_int32),
                 ("recompute_every", C.c_int32), ("stage", C.c_int32), ("resident", C.c_int32),
-                ("spin_dim", C.c_int32), ("reserved", C.c_int32 * 1)]
+                ("spin_dim", C.c_int32), ("waves", C.c_int32)]
 
 
 _lib = None
@@ -244,7 +244,7 @@ class Plan:
     ``samples``: list of (Graph, sample_id, beta[list], delta[list])."""
 
     def __init__(self, samples, engine=FP32_BATCHED, seed=0, block=0, cluster=0, group=0, recompute_every=0,
-                 stage=0, resident=0, device=None, spin_dim=2):
+                 stage=0, resident=0, device=None, spin_dim=2, waves=0):
         import torch
         lib = load()
         self._keep = []
@@ -259,7 +259,7 @@ class Plan:
             arr[k] = Sample(g.handle, sid, len(b), _p(b, C.c_double), _p(d, C.c_double))
             self.n_temps.append(len(b))
             self.sizes.append(g.n)
-        tune = Tuning(block, cluster, group, recompute_every, stage, resident, spin_dim)
+        tune = Tuning(block, cluster, group, recompute_every, stage, resident, spin_dim, waves)
         self.dim = int(spin_dim)
         h = C.c_void_p(); nbytes = C.c_size_t()
         _check(lib.xyl_plan_create(arr, len(samples), engine, seed, C.byref(tune), C.byref(h), C.byref(nbytes)))
@@ -307,13 +307,15 @@ class Plan:
         t = Tuning()
         _check(load().xyl_autotune(self.handle, int(n_sweeps), int(ops), int(measure_every), C.byref(t),
                                    _stream(stream)))
-        return {"block": t.block, "cluster": t.cluster, "group": t.group, "stage": t.stage, "resident": t.resident}
+        return {"block": t.block, "cluster": t.cluster, "group": t.group, "stage": t.stage, "resident": t.resident,
+                "waves": t.waves}
 
     def tuning(self) -> dict:
         t = Tuning()
         _check(load().xyl_get_tuning(self.handle, C.byref(t)))
         return {"block": t.block, "cluster": t.cluster, "group": t.group, "stage": t.stage,
-                "resident": t.resident, "recompute_every": t.recompute_every, "spin_dim": t.spin_dim}
+                "resident": t.resident, "recompute_every": t.recompute_every, "spin_dim": t.spin_dim,
+                "waves": t.waves}
 
     # same method names as the oracle sampler, so tests drive both the same way
     def sweeps(self, n, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1):
