@@ -100,7 +100,8 @@ class ClockSampler:
 KERNEL_SOURCES = {
     "batched_kernel": ["batched.cu"],
     "resident_kernel": ["resident.cu"],
-    "o3_phase_kernel": ["o3.cu"],
+    "o3_phase_kernel": ["o3.cu", "o3_f32.cuh"],
+    "resident_o3_kernel": ["resident_o3.cu", "o3_f32.cuh"],
     "walk_kernel": ["walk.cu"],
 }
 SHARED_SOURCES = ["engines.h", "device.cuh", "philox.cuh", "sweep_tail.cuh"]
@@ -382,11 +383,16 @@ def roofline_for(plan, cfg, per_launch_updates, avg_launch_s, name, spins_live_b
     kernel = kernel_name(plan)
     hbm_peak, hbm_kind = _peaks()
     models = {"hbm_compulsory": hbm_bytes_per_update(R, dim), "gather": l2_bytes_per_update(R, dim)}
+    if kernel == "resident_o3_kernel":
+        # three 4-byte components per spin in shared memory: 7 reads + 1 write of 12 B
+        models["gather"] = 96.0 + 24.0 / R
     achieved = {k: b * per_launch_updates / avg_launch_s / 1e9 for k, b in models.items()}
-    if kernel == "resident_kernel":
+    if kernel in ("resident_kernel", "resident_o3_kernel"):
         bound, b, peak, kind = "smem", models["gather"], SMEM_GATHER_PROBE_GBS, \
             "own probe: shared-memory random 8-byte gathers"
-        basis = "spins held in shared memory for the whole launch: (z+1) 8-B spin reads + one 8-B write per update"
+        spin_b = 12 if kernel == "resident_o3_kernel" else 8
+        basis = (f"spins held in shared memory for the whole launch: (z+1) {spin_b}-B spin reads + one {spin_b}-B "
+                 "write per update")
     elif spins_live_bytes <= L2_BYTES:
         bound, b, peak, kind = "l2", models["gather"], L2_STREAM_PROBE_GBS, "own probe: L2-resident stream read"
         basis = f"a launch wave's spins ({spins_live_bytes / 2**20:.0f} MiB) stay in L2: gather model"
@@ -416,7 +422,9 @@ def spins_live_bytes(plan, cfg):
     """Bytes of spins the units of one launch wave keep live (all of them when
     one wave runs the whole batch; the plain engines run it all at once)."""
     units = plan.unit_count()
-    frac = min(1.0, plan.wave_units() / units) if units else 1.0
+    frac = 1.0
+    if units and plan.part_count() == 1:
+        frac = min(1.0, plan.wave_units() / units)
     return frac * cfg.spins_per_sweep() * (8 if cfg.spin_dim == 2 else 16)
 
 
@@ -432,10 +440,9 @@ def measure_workload(args, name, xyl, wl, dev, stream, flush, rank, world, steps
     # every rank runs its own disorder realisations; no data-path collective
     cfg = wl.shard(cfg, rank, world)
     graphs = wl.build_graphs(cfg)
-    # O(3) spins run on the plain engine; XY on the batched engine
-    engine_name = "FP32_PLAIN" if cfg.spin_dim == 3 else "FP32_BATCHED"
+    engine_name = "FP32_BATCHED"
     tune = dict(block=args.block, cluster=args.cluster, group=args.group, resident=args.resident, waves=args.waves)
-    if cfg.spin_dim == 3 or not full:
+    if not full:
         tune = {}
     plan, _ = wl.make_plan(cfg, getattr(xyl, engine_name), graphs=graphs, **tune)
     plan.bind(stream)
@@ -445,10 +452,18 @@ def measure_workload(args, name, xyl, wl, dev, stream, flush, rank, world, steps
     if not args.no_tune_delta:
         rates = plan.tune_delta(rounds=args.tune_rounds, n_sweeps=args.tune_sweeps, ops=1 | 2 | 4, stream=stream)
     explicit = full and (args.block or args.cluster or args.group)
-    autotune_s = None
-    if engine_name == "FP32_BATCHED" and not explicit and not args.no_autotune:
+    autotune_s, shape_source = None, "library default"
+    if explicit:
+        shape_source = "command line"
+    elif engine_name == "FP32_BATCHED" and not args.no_autotune:
         t0 = time.perf_counter()
-        plan.autotune(args.autotune_sweeps, OPS_ALL, args.measure_every, stream=stream)
+        n_try = args.autotune_sweeps or int(min(64, max(4, round(2e9 / (2 * cfg.spins_per_sweep())))))
+        if args.autotune_cache:
+            _, hit = plan.autotune_cached(args.autotune_cache, n_try, OPS_ALL, args.measure_every, stream=stream)
+            shape_source = "autotune cache (shapes xyl_autotune chose for this batch signature)" if hit else "autotuned"
+        else:
+            plan.autotune(n_try, OPS_ALL, args.measure_every, stream=stream)
+            shape_source = "autotuned"
         autotune_s = time.perf_counter() - t0
     updates_per_sweep = cfg.spins_per_sweep() * 2
 
@@ -538,7 +553,7 @@ def measure_workload(args, name, xyl, wl, dev, stream, flush, rank, world, steps
         "samples": cfg.n_samples, "temperatures": cfg.n_temps,
         "fp64_plain": {"value": fp64, "unit": UNIT,
                        "ratio_fp32_batched_over_fp64_plain": (value / world / fp64) if fp64 else None},
-        "roofline": roof, "e2e": e2e, "clocks": clock_info, "autotune_s": autotune_s,
+        "roofline": roof, "e2e": e2e, "clocks": clock_info, "autotune_s": autotune_s, "shape_source": shape_source,
     }
     if rates is not None:
         out["metropolis_acceptance"] = {"tuned_to": 0.5, "min": float(np.min(rates)), "max": float(np.max(rates)),
@@ -573,7 +588,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--autotune-sweeps", type=int, default=4)
+    ap.add_argument("--autotune-sweeps", type=int, default=0,
+                    help="sweeps per timed try of the autotuner (0 = about 2e9 site-updates, 4 to 64)")
+    ap.add_argument("--autotune-cache", default=os.path.join(ROOT, "paper_1211_3991_gb300", "autotune_cache.json"),
+                    help="JSON file of launch shapes by batch signature ('' = always autotune)")
     ap.add_argument("--no-tune-delta", action="store_true")
     ap.add_argument("--tune-rounds", type=int, default=6)
     ap.add_argument("--tune-sweeps", type=int, default=40)
@@ -620,7 +638,8 @@ def main():
         res, _ = measure_workload(args, name, xyl, wl, dev, stream, flush, rank, world, args.extra_steps,
                                   min(args.warmup, 3), False)
         extras[name] = {k: res[k] for k in ("value", "ms_per_step", "sweeps_per_step", "workload", "cluster",
-                                            "fp64_plain", "roofline", "metropolis_acceptance") if k in res}
+                                            "fp64_plain", "roofline", "metropolis_acceptance", "shape_source")
+                        if k in res}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -656,6 +675,7 @@ def main():
             "gpu_launches": head["launches"],
             "clocks": head["clocks"],
             "autotune_s": head["autotune_s"],
+            "shape_source": head["shape_source"],
             "extra_configs": extras,
         }
         print(json.dumps(line), flush=True)
@@ -668,15 +688,21 @@ def plan_shape(plan):
     if plan.engine != xyl.FP32_BATCHED:  # plain engines: one launch per colour phase, 256 threads per CTA
         return {"plain": True, "threads_per_cta": 256}
     t = plan.tuning()
-    return {"spins_in_shared_memory": t["resident"] > 0, "units": plan.unit_count(), "replicas_per_group": t["group"],
-            "ctas_per_cluster": t["cluster"], "threads_per_cta": t["block"], "csr_in_shared_memory": t["stage"] > 0,
-            "l2_sized_waves": t["waves"] > 0, "units_per_launch": plan.wave_units()}
+    out = {"spins_in_shared_memory": t["resident"] > 0, "units": plan.unit_count(), "replicas_per_group": t["group"],
+           "ctas_per_cluster": t["cluster"], "threads_per_cta": t["block"], "csr_in_shared_memory": t["stage"] > 0,
+           "l2_sized_waves": t["waves"] > 0, "units_per_launch": plan.wave_units()}
+    if plan.part_count() > 1:
+        # a mixed-size batch: one launch shape per size, largest first (the keys above are part 0's)
+        out["parts"] = [plan.part_tuning(k) for k in range(plan.part_count())]
+    return out
 
 
 def kernel_name(plan):
     from paper_1211_3991_gb300 import xyl
     if plan.engine != xyl.FP32_BATCHED:
         return "o3_phase_kernel" if plan.dim == 3 else "plain_phase_kernel"
+    if plan.dim == 3:
+        return "resident_o3_kernel"
     return "resident_kernel" if plan.tuning()["resident"] > 0 else "batched_kernel"
 
 

@@ -6,7 +6,7 @@
  * Model, Eq. (HXY): H = -sum_{i<j} J_ij S_i . S_j with S_i a unit 2-vector and
  * J_ij in {0,1} the adjacency of the graph.  Variants the method carries over
  * to (App. B): random couplings J = +-1 per link, random fields -sum h_i . S_i,
- * and O(3) spins (unit 3-vectors; xyl_tuning.spin_dim = 3, plain engines).
+ * and O(3) spins (unit 3-vectors; xyl_tuning.spin_dim = 3).
  * Graph, Eq. (Levyi): sites of an L x L square lattice; a link lands at
  * distance r with probability proportional to r^-rho.  Two ensembles: every site carrying exactly z links
  * on the periodic lattice (xyl_build_graph_csr), or a fixed total of links with
@@ -209,13 +209,14 @@ typedef struct {
 } xyl_sample;
 
 typedef struct {
-    int32_t block;           /* threads per CTA of the batched engine, <= 672, resident shape <= 1024 (0 = 512) */
+    int32_t block;           /* threads per CTA of the batched engine, <= 1024 (0 = 512); above 672 the
+                                global-memory shape reads its CSR rows from global memory */
     int32_t cluster;         /* CTAs per cluster of the batched engine (0 = tuned default) */
     int32_t group;           /* replicas per cluster, a power of two dividing every n_temps (0 = default) */
     int32_t recompute_every; /* FP64 energy recompute + renormalise every this many sweeps (0 = never) */
     int32_t stage;           /* batched engine: 0 = stage CSR rows in shared memory when they fit, -1 = never */
     int32_t resident;        /* batched engine: 1 = resident shape, -1 = never, 0 = library's choice (below) */
-    int32_t spin_dim;        /* spin components: 0 or 2 = XY; 3 = O(3) (plain engines, no fields; see below) */
+    int32_t spin_dim;        /* spin components: 0 or 2 = XY; 3 = O(3) (no fields; see below) */
     int32_t waves;           /* batched engine, global-memory shape: 1 = cap each launch wave to the samples whose
                                 spins and tables fit in L2, -1 = never, 0 = library's choice (never) */
 } xyl_tuning;
@@ -237,8 +238,12 @@ typedef struct {
  * block (site, t, MET<<24 | 0x800000 | r): u'' = u53(w0,w1).  FP32: one block
  * (site, t, MET<<24 | r) per replica, u24(w0), u24(w1), u24(w2), and the
  * proposal renormalised.  Overrelaxation: S' = 2 (S.h) h / |h|^2 - S.  Spins
- * are stored as padded 4-vectors (16 B FP32, 32 B FP64).  The batched engine
- * and random fields are XY-only (XYL_EINVAL).
+ * are stored as padded 4-vectors (16 B FP32, 32 B FP64), replica-major.  On
+ * XYL_FP32_BATCHED, O(3) spins run in the resident shape only: one CTA per
+ * group of replicas keeps three single-precision component arrays of every
+ * site in shared memory (12 B a site and replica, within 220 KB), with the
+ * plain engine's per-spin arithmetic, so both engines give bit-identical
+ * spins from the same state.  Random fields are XY-only (XYL_EINVAL).
  */
 
 /*
@@ -263,7 +268,8 @@ typedef struct {
  * slot r.  seed keys every spin/Metropolis/PT random stream.  tune may be NULL.
  * *workspace_bytes receives the device bytes xyl_bind needs.
  * Errors: XYL_EINVAL (empty batch, bad slot count, unknown engine, spin_dim
- * other than 0, 2 or 3, O(3) spins on the batched engine or with fields).
+ * other than 0, 2 or 3, O(3) spins with fields or, on the batched engine,
+ * outside the resident shape).
  */
 int xyl_plan_create(const xyl_sample *samples, int32_t n_samples, int32_t engine, uint64_t seed,
                     const xyl_tuning *tune, xyl_plan **out, size_t *workspace_bytes);
@@ -304,7 +310,8 @@ int xyl_sweep(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_every
 /*
  * xyl_sweep_units -- XYL_FP32_BATCHED only: run xyl_sweep on the work units
  * [first_unit, first_unit + n_units) of the batch (a unit is one group of
- * replicas of one sample; units are numbered sample by sample).  All units of
+ * replicas of one sample; units are numbered part by part, see
+ * xyl_part_count, and sample by sample within a part).  All units of
  * a sample must be included for parallel tempering to proceed: a sample whose
  * groups are split across calls makes the in-kernel wait for the missing
  * groups give up after about a second, set the status word to XYL_ETIMEOUT
@@ -344,8 +351,38 @@ int xyl_sweep_noalloc(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measu
 /* Number of work units of a batched plan (0 for other engines). */
 int32_t xyl_unit_count(const xyl_plan *p);
 
-/* Work units one launch of a bound batched plan runs together (its wave; 0 for other engines or before bind). */
+/* Work units one launch of a bound batched plan runs together (part 0's wave; 0 for other engines or before bind). */
 int32_t xyl_wave_units(const xyl_plan *p);
+
+/*
+ * Mixed sizes in one batch (App. B "Computational speed": the cost of a sweep
+ * follows the graph's size and colour count, so each size wants its own
+ * launch shape).  When the library chooses the shape (xyl_tuning resident,
+ * group, cluster and block all 0) and the samples of a batched plan differ in
+ * size, the plan runs one part per size, largest first, each with its own
+ * launch shape (spins in shared memory where a replica group fits, else in
+ * global memory); a caller-given shape applies to the whole batch as one part.
+ * In one xyl_sweep the parts whose clusters wait on other clusters of their
+ * sample (a cross-cluster barrier) run first, one at a time; the others run
+ * side by side on forked streams (also inside the captured CUDA graph).
+ * Results are those of any single shape: every shape performs the same
+ * per-site arithmetic.  xyl_get_tuning reports part 0; xyl_autotune tunes
+ * every part.
+ */
+int32_t xyl_part_count(const xyl_plan *p);
+
+/* Launch shape of one part (0 <= part < xyl_part_count) and its number of samples (may be NULL). */
+int xyl_get_part_tuning(const xyl_plan *p, int32_t part, xyl_tuning *out, int32_t *n_samples);
+
+/*
+ * xyl_set_part_tuning -- give one part of a batched plan a launch shape, e.g.
+ * one an earlier xyl_autotune chose for a batch of the same sizes: resident
+ * (1 or -1), group, cluster and block must be set, stage and waves as in
+ * xyl_tuning.  On a bound plan the shape takes effect at once (synchronises
+ * `stream`); the sampler state is untouched.  A shape that does not fit
+ * leaves the part as it was.  Errors: XYL_EINVAL, XYL_ECUDA.
+ */
+int xyl_set_part_tuning(xyl_plan *p, int32_t part, const xyl_tuning *t, void *stream);
 
 /*
  * xyl_autotune -- XYL_FP32_BATCHED only: time n_sweeps sweeps (ops,
@@ -358,7 +395,7 @@ int32_t xyl_wave_units(const xyl_plan *p);
 int xyl_autotune(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_every, xyl_tuning *best,
                  void *stream);
 
-/* Current launch shape of a batched plan (block, cluster, group, stage filled in). */
+/* Current launch shape of a batched plan (block, cluster, group, stage filled in; part 0 of a mixed-size plan). */
 int xyl_get_tuning(const xyl_plan *p, xyl_tuning *out);
 
 /*
@@ -443,6 +480,19 @@ int xyl_write_spins(xyl_plan *p, int32_t sample, int32_t replica, const double *
  * Errors: XYL_EINVAL (NULL output), XYL_ESTATE, XYL_ECUDA.
  */
 int xyl_read_drift(xyl_plan *p, double *max_drift, int32_t reset, void *stream);
+
+/*
+ * xyl_check_plan -- check, on the device, the colour-sorted CSR the sweeps
+ * read, for every sample of the plan: each colour class is an independent
+ * set (App. B "Graph coloring": the sites of one colour update at once only
+ * because no link joins two of them), neighbour ids lie in [0, N) and differ
+ * from the site, rows are ascending (no repeated link), and every link is in
+ * both of its rows.  *violations receives the number of failed checks (0 for
+ * a sound plan).  A debugging aid in place of memory checkers; it reads the
+ * workspace only.  Synchronises `stream`.  Errors: XYL_EINVAL, XYL_ESTATE,
+ * XYL_ECUDA.
+ */
+int xyl_check_plan(xyl_plan *p, int64_t *violations, void *stream);
 
 /* Status word (0 = fine, else an XYL_E* code recorded on the device) and the sweep index of sample 0. */
 int xyl_read_status(xyl_plan *p, int32_t *status, uint64_t *sweep_index, void *stream);

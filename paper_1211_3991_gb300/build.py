@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libxyl.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-CU_SOURCES = ["common.cu", "plain.cu", "batched.cu", "resident.cu", "plan.cu", "walk.cu", "o3.cu"]
+CU_SOURCES = ["common.cu", "plain.cu", "batched.cu", "resident.cu", "resident_o3.cu", "plan.cu", "walk.cu", "o3.cu"]
 CXX_SOURCES = ["graph.cpp"]
 # FP64 engine and spin initialisation: every expression evaluated as written (no
 # FMA contraction), so their arithmetic is a fixed sequence of IEEE operations

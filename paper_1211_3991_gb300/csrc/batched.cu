@@ -62,11 +62,13 @@ __device__ __forceinline__ void st_spin2(float2 *p, float4 v) { __stcg(reinterpr
 // sweeps, magnetisation and Fourier sums (one extra pass over the CTA's sites).
 constexpr int kSums = kObsCount;
 
-constexpr int kMaxWarps = 21;  // 672 threads per CTA at most (96 registers each)
+constexpr int kMaxWarps = 21;      // 672 threads per CTA at most with 96 registers each
+constexpr int kMaxWarpsWide = 32;  // 1024 threads with 64 registers each (rows in global memory only)
 
-struct SharedState {
-    float part[kSums][kMaxWarps][32];      // per field, warp, group replica: warp partial sums
-    unsigned int part_met[kMaxWarps][32];  // per warp, group replica: accepted Metropolis moves
+template <int MW>
+struct SharedStateT {
+    float part[kSums][MW][32];      // per field, warp, group replica: warp partial sums
+    unsigned int part_met[MW][32];  // per warp, group replica: accepted Metropolis moves
     double E[kMaxReplicas];                // energies of every replica of the sample
     float beta[kMaxReplicas];              // per slot
     float delta[kMaxReplicas];             // per slot
@@ -78,6 +80,7 @@ struct SharedState {
     int cls_base[kMaxColorsBatched];       // first staged row of the chunk
     int abort_flag;
 };
+using SharedState = SharedStateT<kMaxWarps>;
 
 struct Staged {
     const int *col;      // [owned_max][max_deg] colour-sorted neighbour ids
@@ -118,8 +121,8 @@ __device__ __forceinline__ void store_spins(float2 *row, const float2 (&v)[RV])
 // One colour phase of one pass for this CTA's chunk: one thread per (site,
 // block of RV consecutive replicas).
 // Philox block of this thread's first item in colour c (Metropolis pass).
-template <bool STAGED>
-__device__ __forceinline__ Words4 first_draw(const DevPlan &P, const DevSample &d, const SharedState &sh,
+template <bool STAGED, class SS>
+__device__ __forceinline__ Words4 first_draw(const DevPlan &P, const DevSample &d, const SS &sh,
                                              const BatchedParams &bp, const Staged &stg, int c, uint32_t t, int r0)
 {
     const int lo = sh.cls_lo[c], hi = sh.cls_hi[c];
@@ -171,8 +174,8 @@ __device__ __forceinline__ void fetch_grow(const DevPlan &P, const DevSample &d,
     }
 }
 
-template <bool IS_MET, bool FUSE_E, bool STAGED, int RV, int DEG, bool DISORDER>
-__device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, const SharedState &sh,
+template <bool IS_MET, bool FUSE_E, bool STAGED, int RV, int DEG, bool DISORDER, class SS>
+__device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, const SS &sh,
                                       const BatchedParams &bp, const Staged &stg, int c, uint32_t t, Lane<RV> &ln,
                                       const Words4 &first)
 {
@@ -279,21 +282,23 @@ __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, cons
 // Warp partial of a per-thread value of replica lane_rep+v (lanes l and
 // l ^ o, o >= lanes per site, hold the same replicas), stored per warp so that
 // the CTA sum is taken in a fixed order.
-__device__ __forceinline__ void warp_part(SharedState &sh, const BatchedParams &bp, int lane_rep, int v, int f, float x)
+template <class SS>
+__device__ __forceinline__ void warp_part(SS &sh, const BatchedParams &bp, int lane_rep, int v, int f, float x)
 {
     for (int o = 16; o >= (1 << bp.log2lps); o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     if ((threadIdx.x & 31) < (1 << bp.log2lps)) sh.part[f][threadIdx.x >> 5][lane_rep + v] = x;
 }
 
-__device__ __forceinline__ void warp_count(SharedState &sh, const BatchedParams &bp, int lane_rep, int v, unsigned x)
+template <class SS>
+__device__ __forceinline__ void warp_count(SS &sh, const BatchedParams &bp, int lane_rep, int v, unsigned x)
 {
     for (int o = 16; o >= (1 << bp.log2lps); o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     if ((threadIdx.x & 31) < (1 << bp.log2lps)) sh.part_met[threadIdx.x >> 5][lane_rep + v] = x;
 }
 
 // Magnetisation and Fourier sums of the CTA's own sites (final spins).
-template <int RV>
-__device__ __forceinline__ void measure_own_sites(const DevPlan &P, const DevSample &d, SharedState &sh,
+template <int RV, class SS>
+__device__ __forceinline__ void measure_own_sites(const DevPlan &P, const DevSample &d, SS &sh,
                                                   const BatchedParams &bp, int r0, int lane_rep)
 {
     float m[RV][kSums - 1];
@@ -327,8 +332,8 @@ __device__ __forceinline__ void measure_own_sites(const DevPlan &P, const DevSam
         for (int f = 1; f < kSums; ++f) warp_part(sh, bp, lane_rep, v, f, m[v][f - 1]);
 }
 
-template <bool STAGED, int RV, int DEG, bool DISORDER>
-__device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams &bp, SharedState &sh,
+template <bool STAGED, int RV, int DEG, bool DISORDER, class SS>
+__device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams &bp, SS &sh,
                                            const Staged &stg, cg::cluster_group &cluster, int s, int group,
                                            int rank)
 {
@@ -439,10 +444,10 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
     if (leader && threadIdx.x == 0) P.sweep[s] = t;
 }
 
-template <bool STAGED, int RV, int DEG, bool DISORDER>
-__global__ void __maxnreg__(96) batched_kernel(DevPlan P, BatchedParams bp)
+template <bool STAGED, int RV, int DEG, bool DISORDER, int MW>
+__device__ __forceinline__ void batched_body(const DevPlan &P, const BatchedParams &bp)
 {
-    __shared__ SharedState sh;
+    __shared__ SharedStateT<MW> sh;
     extern __shared__ int dyn[];
     cg::cluster_group cluster = cg::this_cluster();
     const int unit = bp.unit_begin + (int)(blockIdx.x / bp.G);
@@ -497,6 +502,21 @@ __global__ void __maxnreg__(96) batched_kernel(DevPlan P, BatchedParams bp)
     run_sweeps<STAGED, RV, DEG, DISORDER>(P, bp, sh, stg, cluster, s, group, rank);
 }
 
+// Up to 672 threads with 96 registers each, or, rows in global memory only,
+// up to 1024 threads with 64 registers each (more warps to cover the latency
+// of the neighbour gathers).
+template <bool STAGED, int RV, int DEG, bool DISORDER>
+__global__ void __maxnreg__(96) batched_kernel(DevPlan P, BatchedParams bp)
+{
+    batched_body<STAGED, RV, DEG, DISORDER, kMaxWarps>(P, bp);
+}
+
+template <int RV, int DEG, bool DISORDER>
+__global__ void __launch_bounds__(1024, 1) batched_kernel_wide(DevPlan P, BatchedParams bp)
+{
+    batched_body<false, RV, DEG, DISORDER, kMaxWarpsWide>(P, bp);
+}
+
 using KernelFn = void (*)(DevPlan, BatchedParams);
 
 // The specialisation for a launch shape: CSR staged or not, one or two
@@ -504,6 +524,11 @@ using KernelFn = void (*)(DevPlan, BatchedParams);
 template <bool STAGED, int RV, bool DISORDER>
 KernelFn pick_deg(const BatchedShape &B)
 {
+    if (!STAGED && B.block > kMaxWarps * 32) {
+        if (B.fixed_deg == 6) return batched_kernel_wide<RV, 6, DISORDER>;
+        if (B.max_deg <= 8) return batched_kernel_wide<RV, -8, DISORDER>;
+        return batched_kernel_wide<RV, 0, DISORDER>;
+    }
     if (B.fixed_deg == 6) return batched_kernel<STAGED, RV, 6, DISORDER>;
     if (B.max_deg <= 8) return batched_kernel<STAGED, RV, -8, DISORDER>;
     return batched_kernel<STAGED, RV, 0, DISORDER>;
@@ -535,7 +560,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 }  // namespace
 
-size_t batched_static_smem_bytes() { return sizeof(SharedState); }
+size_t batched_static_smem_bytes() { return sizeof(SharedStateT<kMaxWarpsWide>); }
 
 // Device address of the static scratch array on the current device.  The first
 // call on a device looks it up (with that device current) and caches it.

@@ -242,7 +242,47 @@ __global__ void recompute_kernel(DevPlan P, int layout, int fp64, int renormalis
     }
 }
 
+// One block per sample: checks the device CSR the sweeps read.  Every
+// colour class must be an independent set (App. B "Graph coloring": sites of
+// one colour update together only because no link joins two of them), every
+// neighbour id must lie in [0, N) and differ from the site, each row must be
+// ascending, and every link must appear in both rows.  Violations are counted.
+__global__ void check_kernel(DevPlan P, unsigned long long *violations)
+{
+    const int s = blockIdx.x;
+    const DevSample d = P.samples[s];
+    const int32_t *rp = P.row_ptr + d.row_off;
+    const int32_t *cl = P.col + d.col_off;
+    const int32_t *cp = P.color_ptr + d.color_off;
+    unsigned long long bad = 0;
+    for (int i = threadIdx.x; i < d.N; i += blockDim.x) {
+        int c = 0;
+        while (c + 1 < d.Q && cp[c + 1] <= i) ++c;
+        const int cb = cp[c], ce = cp[c + 1];
+        const int rb = rp[i], re = rp[i + 1];
+        if (rb > re) { ++bad; continue; }
+        int prev = -1;
+        for (int k = rb; k < re; ++k) {
+            const int j = cl[k] & 0x7fffffff;  // the top bit carries a coupling J = -1
+            if (j < 0 || j >= d.N || j == i) { ++bad; continue; }
+            if (j >= cb && j < ce) ++bad;      // a link inside a colour class
+            if (j <= prev) ++bad;              // rows ascending, no repeated link
+            prev = j;
+            bool back = false;
+            for (int q = rp[j]; q < rp[j + 1] && !back; ++q) back = (cl[q] & 0x7fffffff) == i;
+            if (!back) ++bad;                  // the link must appear in row j too
+        }
+    }
+    if (bad) atomicAdd(violations, bad);
+}
+
 }  // namespace
+
+cudaError_t launch_check(const DevPlan &P, const PlanShape &S, unsigned long long *violations, cudaStream_t st)
+{
+    check_kernel<<<S.n_samples, 256, 0, st>>>(P, violations);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_init(const DevPlan &P, const PlanShape &S, int aligned, cudaStream_t st)
 {

@@ -41,6 +41,8 @@ struct BatchedShape {
     // every site in shared memory; the groups of a sample form one cluster
     bool resident = false;
     bool l2_waves = false;  // global-memory shape: launch waves hold as many samples as fit in L2
+    int dim = 2;            // spin components: 3 runs the O(3) resident kernel
+    int o3_comp = 0;        // O(3) resident: floats in each spin component array
     int gpc = 1;            // replica groups per cluster (resident shape)
     int cpc = 1;            // CTAs per cluster of the resident shape, G x gpc
     int rs_csr_w = 0;       // staged CSR row width (16-bit ids), 0 = rows from global memory
@@ -62,6 +64,7 @@ constexpr int kMaxDevicesNoAlloc = 64;
 cudaError_t batched_noalloc_scratch(void **ptr);
 
 cudaError_t launch_init(const DevPlan &P, const PlanShape &S, int aligned, cudaStream_t st);
+cudaError_t launch_check(const DevPlan &P, const PlanShape &S, unsigned long long *violations, cudaStream_t st);
 cudaError_t launch_finalize(const DevPlan &P, const PlanShape &S, uint32_t ops, int measure_every, int advance,
                             int obs_buf_from_sweep, cudaStream_t st);
 cudaError_t launch_recompute(const DevPlan &P, const PlanShape &S, int renormalise, int obs_buf_from_sweep,
@@ -88,5 +91,10 @@ cudaError_t launch_resident(const DevPlan &P, const BatchedShape &B, const int2 
                             int unit_count, int n_sweeps, uint32_t ops, int measure_every, cudaStream_t st);
 cudaError_t resident_max_active_clusters(const BatchedShape &B, int *clusters);
 size_t resident_static_smem_bytes();
+
+// Resident shape for O(3) spins (one CTA per replica group, G = 1).
+cudaError_t launch_resident_o3(const DevPlan &P, const BatchedShape &B, const int2 *d_units, int unit_begin,
+                               int unit_count, int n_sweeps, uint32_t ops, int measure_every, cudaStream_t st);
+cudaError_t resident_o3_max_active_clusters(const BatchedShape &B, int *clusters);
 
 }  // namespace xyl

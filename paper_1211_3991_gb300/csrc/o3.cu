@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "engines.h"
+#include "o3_f32.cuh"
 
 namespace xyl {
 namespace {
@@ -61,31 +62,6 @@ __device__ __forceinline__ void cap_propose(const DevPlan &P, double x, double y
     nx = ct * x + st * tx;
     ny = ct * y + st * ty;
     nz = ct * z + st * tz;
-}
-
-// FP32 form: hardware sincos/exp, the proposal renormalised.
-__device__ __forceinline__ void cap_propose_f32(float x, float y, float z, float half_width, float u, float uphi,
-                                                float &nx, float &ny, float &nz)
-{
-    float sh, ch;
-    __sincosf(0.5f * half_width, &sh, &ch);
-    const float w = u * (2.0f * (sh * sh));
-    const float ct = 1.0f - w;
-    const float st = sqrtf(fmaxf(w * (2.0f - w), 0.0f));
-    float sp, cp;
-    __sincosf(6.28318530717958647692f * uphi - 3.14159265358979323846f, &sp, &cp);
-    const float g = z >= 0.0f ? 1.0f : -1.0f;
-    const float a = -1.0f / (g + z);
-    const float b = x * y * a;
-    const float e1x = g + (x * x) * a, e1y = b, e1z = -x;
-    const float e2x = b, e2y = g + (y * y) * a, e2z = -y;
-    const float px = ct * x + st * (cp * e1x + sp * e2x);
-    const float py = ct * y + st * (cp * e1y + sp * e2y);
-    const float pz = ct * z + st * (cp * e1z + sp * e2z);
-    const float inv = rsqrtf(px * px + py * py + pz * pz);
-    nx = px * inv;
-    ny = py * inv;
-    nz = pz * inv;
 }
 
 __global__ void o3_init_kernel(DevPlan P, int fp64, int aligned)
@@ -183,10 +159,10 @@ __global__ void __launch_bounds__(kO3Block) o3_phase_kernel(DevPlan P, int c)
                 const double dE = -((nx - si.x) * hx + (ny - si.y) * hy + (nz - si.z) * hz);
                 accepted = dE <= 0.0 || uniform53(a.w2, a.w3) < exp(-beta * dE);
             } else {
+                // the single-precision steps of o3_f32.cuh (hardware sincos/exp, proposal renormalised)
                 const Words4 a = philox_draw(site, t, kPurposeMet, (uint32_t)r, d.sample_id, P.key);
-                cap_propose_f32(si.x, si.y, si.z, (float)half_width, uniform24(a.w0), uniform24(a.w1), nx, ny, nz);
-                const float dE = -((nx - si.x) * hx + (ny - si.y) * hy + (nz - si.z) * hz);
-                accepted = dE <= 0.0f || uniform24(a.w2) < __expf(-(float)beta * dE);
+                o3_cap_propose_f32(si.x, si.y, si.z, (float)half_width, uniform24(a.w0), uniform24(a.w1), nx, ny, nz);
+                accepted = o3_accept_f32(si.x, si.y, si.z, nx, ny, nz, hx, hy, hz, (float)beta, uniform24(a.w2));
             }
             if (accepted) {
                 sp[i] = make_v3(nx, ny, nz);
@@ -196,16 +172,20 @@ __global__ void __launch_bounds__(kO3Block) o3_phase_kernel(DevPlan P, int c)
                 nz = si.z;
             }
         } else {
-            const Real h2 = hx * hx + hy * hy + hz * hz;
-            if (h2 > (Real)0) {
-                const Real k = (Real)2 * (si.x * hx + si.y * hy + si.z * hz) / h2;
-                nx = k * hx - si.x;
-                ny = k * hy - si.y;
-                nz = k * hz - si.z;
+            if constexpr (sizeof(Real) == 4) {
+                o3_reflect_f32(si.x, si.y, si.z, hx, hy, hz, nx, ny, nz);
             } else {
-                nx = si.x;
-                ny = si.y;
-                nz = si.z;
+                const Real h2 = hx * hx + hy * hy + hz * hz;
+                if (h2 > (Real)0) {
+                    const Real k = (Real)2 * (si.x * hx + si.y * hy + si.z * hz) / h2;
+                    nx = k * hx - si.x;
+                    ny = k * hy - si.y;
+                    nz = k * hz - si.z;
+                } else {
+                    nx = si.x;
+                    ny = si.y;
+                    nz = si.z;
+                }
             }
             sp[i] = make_v3(nx, ny, nz);
         }

@@ -37,30 +37,44 @@ const int kGraphChunk = 32;  // sweeps per captured graph of the plain engine
 
 }  // namespace
 
+// A part of a batched plan: the samples of one size run with one launch
+// shape (a plan whose samples all have the same size has one part).
+struct Part {
+    std::vector<int> samples;   // plan samples it runs (indices), in plan order
+    BatchedShape B;
+    int stage_mode = 0;
+    std::vector<int2> units;    // (sample, group) per unit, sample by sample
+    int u0 = 0;                 // its first unit in the plan's unit table
+    int wave_units = 0;         // units one launch runs together
+    bool barrier_free = false;  // no cluster waits on another: may run beside other parts
+};
+
 struct xyl_plan {
     int engine = 0;
     uint64_t seed = 0;
     std::vector<HostSample> hs;
     PlanShape shape;
-    BatchedShape bshape;
+    std::vector<Part> parts;
     int recompute_every = 0;
-    int stage_mode = 0;
     int resident_req = 0;   // the caller's resident setting: 1 only, -1 never, 0 either
     int waves_req = 0;      // the caller's waves setting: 1 L2-sized, -1 never, 0 either (autotuner)
     int64_t sweeps_since_recompute = 0;
     int total_R = 0;
     int64_t total_N = 0, total_nnz = 0, total_spins = 0;
     int total_Q1 = 0;
-    std::vector<int2> units;
-    int wave_units = 0;
+    std::vector<int2> units;  // every part's units, part by part
     size_t ws_bytes = 0;
     char *ws = nullptr;
     bool bound = false;
     DevPlan dev{};
     Region r_samples, r_row_ptr, r_col, r_perm, r_color_ptr, r_phase, r_spins, r_beta, r_delta, r_slot_of, r_rep_at,
         r_obs, r_last_E, r_acc, r_met_acc, r_met_try, r_pt_acc, r_pt_try, r_sweep, r_status, r_barrier, r_drift,
-        r_units, r_push, r_field;
+        r_units, r_push, r_field, r_check;
     cudaStream_t capture_stream = nullptr;
+    // parts that run side by side: one stream and one event each, and the fork event
+    std::vector<cudaStream_t> part_streams;
+    std::vector<cudaEvent_t> part_events;
+    cudaEvent_t fork_event = nullptr;
     std::map<std::tuple<int, uint32_t, int>, cudaGraphExec_t> graphs;
     int64_t last_launches = 0;
     int64_t launches_per_graph_plain = 0;
@@ -80,6 +94,9 @@ struct xyl_plan {
     {
         drop_graphs();
         if (capture_stream) cudaStreamDestroy(capture_stream);
+        for (cudaStream_t q : part_streams) cudaStreamDestroy(q);
+        for (cudaEvent_t e : part_events) cudaEventDestroy(e);
+        if (fork_event) cudaEventDestroy(fork_event);
     }
 };
 
@@ -129,6 +146,7 @@ void layout(xyl_plan *p)
     take(p->r_status, sizeof(int32_t));
     take(p->r_barrier, S * sizeof(unsigned int));
     take(p->r_drift, 2 * sizeof(double));  // the recorded drift, and a save slot for xyl_write_spins
+    take(p->r_check, sizeof(unsigned long long));  // violation count of xyl_check_plan
     take(p->r_units, std::max<size_t>(p->total_R, 1) * sizeof(int2));  // the most units any shape makes
     take(p->r_push, p->total_N * sizeof(uint16_t));
     // random fields: one vector per site, only when some sample has them
@@ -155,11 +173,13 @@ int check_bound(xyl_plan *p, const char *who)
 // rows of the CTA's own sites, the last two when they fit.  A cluster holds
 // every group of a sample when G x groups <= 16, else one group.  Returns
 // false when the shape does not apply to this batch.
-bool resident_fit(const xyl_plan *p, int g, int G, int block, int stage, BatchedShape &B)
+bool resident_fit(const xyl_plan *p, const std::vector<int> &samples, int g, int G, int block, int stage,
+                  BatchedShape &B)
 {
-    const int R0 = p->hs[0].R;
+    const int R0 = p->hs[samples[0]].R;
     int max_N = 0, max_deg = 0, owned = 0;
-    for (auto &h : p->hs) {
+    for (int si : samples) {
+        const HostSample &h = p->hs[si];
         if (h.R != R0) return false;
         max_N = std::max(max_N, h.N);
         max_deg = std::max(max_deg, h.max_deg);
@@ -218,53 +238,125 @@ bool resident_fit(const xyl_plan *p, int g, int G, int block, int stage, Batched
     return true;
 }
 
+// Shared-memory layout of the O(3) resident shape: one CTA per group of g
+// replicas keeps three single-precision component arrays of every site (one
+// zero row) | warp partial sums (16 fields) | accepted counts | FP64 slot
+// inverse temperatures | 16-bit site ids | 16-bit CSR rows, the last two when
+// they fit.  The groups of a sample share a cluster when they are at most 16.
+bool resident_fit_o3(const xyl_plan *p, const std::vector<int> &samples, int g, int block, int stage,
+                     BatchedShape &B)
+{
+    const int R0 = p->hs[samples[0]].R;
+    int max_N = 0, max_deg = 0;
+    for (int si : samples) {
+        const HostSample &h = p->hs[si];
+        if (h.R != R0) return false;
+        max_N = std::max(max_N, h.N);
+        max_deg = std::max(max_deg, h.max_deg);
+    }
+    if (R0 % g || block % g) return false;
+    const int n_groups = R0 / g;
+    auto a16 = [](size_t v) { return (v + 15) / 16 * 16; };
+    const size_t n_warps = (size_t)block / 32;
+    const size_t comp = ((size_t)(max_N + 1) * g + 3) / 4 * 4;
+    const size_t spins = 3 * comp * sizeof(float);
+    const size_t part = a16((size_t)kObsCount3 * n_warps * g * sizeof(float));
+    const size_t met = a16(n_warps * g * sizeof(unsigned));
+    const size_t beta = a16((size_t)R0 * sizeof(double));
+    size_t off = spins + part + met + beta;
+    if (off > kResidentDynLimitBytes) return false;
+    B.rs_off_part = spins;
+    B.rs_off_met = spins + part;
+    B.rs_off_beta = spins + part + met;
+    B.rs_ids = false;
+    B.rs_csr_w = 0;
+    B.rs_off_ids = B.rs_off_col = B.rs_off_peers = 0;
+    if (max_N <= 65535) {
+        const size_t ids = a16((size_t)max_N * sizeof(uint16_t));
+        if (off + ids <= kResidentDynLimitBytes) {
+            B.rs_ids = true;
+            B.rs_off_ids = off;
+            off += ids;
+        }
+        const int W = B.fixed_deg == 6 ? 6 : 8;
+        const size_t col = a16((size_t)max_N * W * sizeof(uint16_t));
+        if (stage >= 0 && max_deg <= 8 && off + col <= kResidentDynLimitBytes && (!p->shape.coupled || max_N <= 32767)) {
+            B.rs_csr_w = W;
+            B.rs_off_col = off;
+            off += col;
+        }
+    }
+    B.resident = true;
+    B.dim = 3;
+    B.o3_comp = (int)comp;
+    B.G = 1;
+    B.gpc = n_groups <= 16 ? n_groups : 1;
+    B.cpc = B.gpc;
+    B.owned_max = max_N;
+    B.staged = B.rs_csr_w != 0;
+    B.smem_bytes = off;
+    return true;
+}
+
 // Launch shape of the batched engine: R_g replicas per group, G CTAs per
 // cluster, `block` threads per CTA; stage < 0 disables shared-memory staging;
-// resident != 0 asks for the resident shape (G is then ignored).
-int apply_shape(xyl_plan *p, int g, int G, int block, int stage, int resident, int waves = 0)
+// resident != 0 asks for the resident shape (G is then ignored).  O(3) spins
+// run in the resident shape with one CTA per group.
+int apply_shape(xyl_plan *p, Part &part, int g, int G, int block, int stage, int resident, int waves = 0)
 {
     if (g < 1 || g > 32 || (g & (g - 1))) return fail(XYL_EINVAL, "group=%d must be a power of two <= 32", g);
-    for (auto &h : p->hs)
-        if (h.R % g) return fail(XYL_EINVAL, "group=%d does not divide n_temps=%d", g, h.R);
+    for (int si : part.samples)
+        if (p->hs[si].R % g) return fail(XYL_EINVAL, "group=%d does not divide n_temps=%d", g, p->hs[si].R);
     if (G < 1 || G > 16) return fail(XYL_EINVAL, "cluster=%d must be in [1, 16]", G);
-    const int max_block = resident ? 1024 : 672;
-    if (block < 32 || block % 32 || block > max_block)
-        return fail(XYL_EINVAL, "block=%d must be a multiple of 32 <= %d", block, max_block);
-    BatchedShape &B = p->bshape;
+    if (block < 32 || block % 32 || block > 1024)
+        return fail(XYL_EINVAL, "block=%d must be a multiple of 32 <= 1024", block);
+    BatchedShape &B = part.B;
     B = BatchedShape{};
     B.G = G;
     B.Rg = g;
     B.block = block;
     B.disorder = p->shape.disorder;
     int max_deg = 1;
-    for (auto &h : p->hs) max_deg = std::max(max_deg, h.max_deg);
+    for (int si : part.samples) max_deg = std::max(max_deg, p->hs[si].max_deg);
     B.max_deg = max_deg;
     int fixed = -1;
-    for (auto &h : p->hs)
+    for (int si : part.samples) {
+        const HostSample &h = p->hs[si];
         for (int i = 0; i < h.N && fixed != 0; ++i) {
             const int dg = h.row_ptr[i + 1] - h.row_ptr[i];
             fixed = (fixed < 0 || fixed == dg) ? dg : 0;
         }
+    }
     B.fixed_deg = fixed < 0 ? 0 : fixed;
-    p->stage_mode = stage;
-    p->units.clear();
-    for (size_t s = 0; s < p->hs.size(); ++s)
-        for (int k = 0; k < p->hs[s].R / g; ++k) p->units.push_back(make_int2((int)s, k));
+    part.stage_mode = stage;
+    part.units.clear();
+    for (int si : part.samples)
+        for (int k = 0; k < p->hs[si].R / g; ++k) part.units.push_back(make_int2(si, k));
+    if (p->shape.dim == 3) {
+        if (!resident || G != 1)
+            return fail(XYL_EINVAL, "O(3) spins on the batched engine run in the resident shape, one CTA per group");
+        if (!resident_fit_o3(p, part.samples, g, block, stage, B))
+            return fail(XYL_EINVAL, "O(3) resident shape with group=%d does not fit this batch (equal n_temps, a "
+                        "group's spins, 12 B a site, within %zu B of shared memory)", g, kResidentDynLimitBytes);
+        return XYL_OK;
+    }
     if (resident) {
-        if (!resident_fit(p, g, G, block, stage, B))
+        if (!resident_fit(p, part.samples, g, G, block, stage, B))
             return fail(XYL_EINVAL, "resident shape with group=%d does not fit this batch (equal n_temps, "
                         "a group's spins within %zu B of shared memory)", g, kResidentDynLimitBytes);
         return XYL_OK;
     }
     int owned = 0;
-    for (auto &h : p->hs) {
+    for (int si : part.samples) {
+        const HostSample &h = p->hs[si];
         int o = 0;
         for (int c = 0; c < h.Q; ++c) o += (h.color_ptr[c + 1] - h.color_ptr[c] + G - 1) / G;
         owned = std::max(owned, o);
     }
     B.owned_max = owned;
     const size_t bytes = (size_t)owned * (size_t)(max_deg + 2) * sizeof(int32_t);
-    B.staged = stage >= 0 && bytes <= kStageLimitBytes;
+    // CTAs above 672 threads (64 registers each) read their rows from global memory
+    B.staged = stage >= 0 && bytes <= kStageLimitBytes && block <= 672;
     B.smem_bytes = B.staged ? bytes : 0;
     B.l2_waves = waves > 0;
     return XYL_OK;
@@ -281,22 +373,36 @@ size_t sample_live_bytes(const HostSample &h)
 // Samples a launch wave of the global-memory shape may hold so that their
 // working set stays in L2 (three quarters of it, the rest for the sums and
 // the other traffic); at least one.
-int l2_wave_samples(const xyl_plan *p)
+int l2_wave_samples(const xyl_plan *p, const Part &part)
 {
     int dev = 0, l2 = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
         return 1;
     size_t per = 1;
-    for (auto &h : p->hs) per = std::max(per, sample_live_bytes(h));
+    for (int si : part.samples) per = std::max(per, sample_live_bytes(p->hs[si]));
     return (int)std::max<size_t>(1, (size_t)l2 * 3 / 4 / per);
 }
 
-int pick_batched_shape(xyl_plan *p, const xyl_tuning *tune)
+int pick_part_shape(xyl_plan *p, Part &part, const xyl_tuning *tune)
 {
     const int mode = tune ? tune->resident : 0;
     const int stage = tune ? tune->stage : 0;
     int block = 512;
     if (tune && tune->block > 0) block = tune->block;
+    if (p->shape.dim == 3) {
+        // O(3): resident only, the largest group that fits, all groups of a sample in one cluster first
+        if (mode < 0) return fail(XYL_EINVAL, "O(3) spins on the batched engine run in the resident shape");
+        for (int pass = 0; pass < 2; ++pass)
+            for (int g = 32; g >= 1; g >>= 1) {
+                if (tune && tune->group > 0 && g != tune->group) continue;
+                bool divides = true;
+                for (int si : part.samples) divides &= (p->hs[si].R % g == 0);
+                if (!divides || apply_shape(p, part, g, 1, block, stage, 1) != XYL_OK) continue;
+                if (pass == 1 || part.B.gpc * g == p->hs[part.samples[0]].R) return XYL_OK;
+            }
+        return fail(XYL_EINVAL, "O(3) resident shape does not fit this batch (equal n_temps, a group's spins, 12 B "
+                    "a site, within %zu B of shared memory)", kResidentDynLimitBytes);
+    }
     if (mode >= 0) {
         // resident: the largest group that fits with all groups of a sample in
         // one cluster (pairs of replicas share a Philox block); a caller's
@@ -307,10 +413,10 @@ int pick_batched_shape(xyl_plan *p, const xyl_tuning *tune)
             for (int g = 32; g >= 1; g >>= 1) {
                 if (tune && tune->group > 0 && g != tune->group) continue;
                 bool divides = true;
-                for (auto &h : p->hs) divides &= (h.R % g == 0);
-                if (!divides || apply_shape(p, g, G, block, stage, 1) != XYL_OK) continue;
+                for (int si : part.samples) divides &= (p->hs[si].R % g == 0);
+                if (!divides || apply_shape(p, part, g, G, block, stage, 1) != XYL_OK) continue;
                 // first choice: every group of a sample in one cluster
-                if (pass == 1 || p->bshape.gpc * g == p->hs[0].R) return XYL_OK;
+                if (pass == 1 || part.B.gpc * g == p->hs[part.samples[0]].R) return XYL_OK;
             }
         }
         if (mode == 1)
@@ -320,35 +426,84 @@ int pick_batched_shape(xyl_plan *p, const xyl_tuning *tune)
     }
     // replicas per cluster: largest power of two <= 16 dividing every sample's R
     int g = 16;
-    for (auto &h : p->hs)
-        while (g > 1 && h.R % g) g >>= 1;
+    for (int si : part.samples)
+        while (g > 1 && p->hs[si].R % g) g >>= 1;
     if (tune && tune->group > 0) g = tune->group;
     int max_N = 0;
-    for (auto &h : p->hs) max_N = std::max(max_N, h.N);
+    for (int si : part.samples) max_N = std::max(max_N, p->hs[si].N);
     // default cluster width: enough CTAs that a phase has a few thousand items per CTA
     int G = 1;
     const double items_per_phase = (double)max_N * g / std::max(1, p->shape.max_Q);
     while (G < 16 && items_per_phase / (G * 2) >= 1024.0) G *= 2;
     if (tune && tune->cluster > 0) G = tune->cluster;
-    return apply_shape(p, g, G, block, stage, 0, tune ? tune->waves : 0);
+    return apply_shape(p, part, g, G, block, stage, 0, tune ? tune->waves : 0);
 }
 
-// Upload the unit table of the current shape, set the kernel attributes and
-// size the launch waves: all groups of a sample must be resident together.
-int configure_batched(xyl_plan *p, cudaStream_t st)
+void gather_units(xyl_plan *p);
+
+// Split a batched plan into parts: one per sample size (largest first) when
+// the library chooses the shapes and the sizes differ, else one part.
+int pick_batched_shape(xyl_plan *p, const xyl_tuning *tune)
+{
+    const bool caller_shape = tune && (tune->resident != 0 || tune->group > 0 || tune->cluster > 0 || tune->block > 0);
+    std::vector<int> sizes;
+    for (auto &h : p->hs) sizes.push_back(h.N);
+    std::sort(sizes.begin(), sizes.end(), std::greater<int>());
+    sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
+    p->parts.clear();
+    if (caller_shape || sizes.size() == 1) {
+        Part part;
+        for (int s = 0; s < (int)p->hs.size(); ++s) part.samples.push_back(s);
+        p->parts.push_back(part);
+    } else {
+        for (int n : sizes) {
+            Part part;
+            for (int s = 0; s < (int)p->hs.size(); ++s)
+                if (p->hs[s].N == n) part.samples.push_back(s);
+            p->parts.push_back(part);
+        }
+    }
+    for (Part &part : p->parts) {
+        const int rc = pick_part_shape(p, part, tune);
+        if (rc) return rc;
+    }
+    gather_units(p);
+    return XYL_OK;
+}
+
+// The plan's unit table: every part's units, part by part.
+void gather_units(xyl_plan *p)
+{
+    p->units.clear();
+    for (Part &part : p->parts) {
+        part.u0 = (int)p->units.size();
+        p->units.insert(p->units.end(), part.units.begin(), part.units.end());
+    }
+}
+
+// Set the kernel attributes of a part's shape, size its launch waves (all
+// groups of a sample resident together when they meet at a global barrier)
+// and, for a site split, upload the peer masks of its samples.
+int configure_part(xyl_plan *p, Part &part, cudaStream_t st)
 {
     int clusters = 0;
-    if (p->bshape.resident) {
-        const BatchedShape &B = p->bshape;
-        XYL_CUDA(resident_max_active_clusters(B, &clusters), "batched: occupancy");
+    const BatchedShape &B = part.B;
+    const HostSample &h0 = p->hs[part.samples[0]];
+    const int n_units = (int)part.units.size();
+    if (B.resident) {
+        if (B.dim == 3)
+            XYL_CUDA(resident_o3_max_active_clusters(B, &clusters), "batched: occupancy");
+        else
+            XYL_CUDA(resident_max_active_clusters(B, &clusters), "batched: occupancy");
         if (clusters < 1)
             return fail(XYL_EINVAL, "batched: a resident cluster of %d CTAs x %d threads (%zu B shared) cannot be resident",
                         B.cpc, B.block, B.smem_bytes);
-        const int n_groups = p->hs[0].R / B.Rg;
+        const int n_groups = h0.R / B.Rg;
         if (B.gpc == n_groups) {
             // a cluster is a whole sample and never waits on another: one
             // launch, the hardware queues the clusters that do not fit yet
-            p->wave_units = (int)p->units.size();
+            part.wave_units = n_units;
+            part.barrier_free = true;
         } else {
             // the clusters of a sample meet at a global barrier: a wave holds
             // whole samples that are resident together
@@ -357,14 +512,17 @@ int configure_batched(xyl_plan *p, cudaStream_t st)
             if (samples_per_wave < 1)
                 return fail(XYL_EINVAL, "batched: %d resident clusters of %d CTAs cannot be co-resident (max %d)",
                             per_sample, B.cpc, clusters);
-            p->wave_units = samples_per_wave * n_groups;
+            part.wave_units = samples_per_wave * n_groups;
+            part.barrier_free = false;
         }
         if (B.G > 1) {
             // per site: the other CTAs of its group whose chunks link to it
-            std::vector<uint16_t> mask(p->total_N, 0);
-            size_t off = 0;
-            for (auto &h : p->hs) {
+            std::vector<int64_t> site_off(p->hs.size(), 0);
+            for (size_t s = 1; s < p->hs.size(); ++s) site_off[s] = site_off[s - 1] + p->hs[s - 1].N;
+            for (int si : part.samples) {
+                const HostSample &h = p->hs[si];
                 std::vector<int> owner(h.N);
+                std::vector<uint16_t> mask(h.N, 0);
                 for (int c = 0; c < h.Q; ++c) {
                     const int cb = h.color_ptr[c], ce = h.color_ptr[c + 1];
                     const int chunk = (ce - cb + B.G - 1) / B.G;
@@ -373,54 +531,77 @@ int configure_batched(xyl_plan *p, cudaStream_t st)
                 for (int i = 0; i < h.N; ++i) {
                     uint32_t m = 0;
                     for (int k = h.row_ptr[i]; k < h.row_ptr[i + 1]; ++k) m |= 1u << owner[h.col[k]];
-                    mask[off + i] = (uint16_t)(m & ~(1u << owner[i]));
+                    mask[i] = (uint16_t)(m & ~(1u << owner[i]));
                 }
-                off += h.N;
+                XYL_CUDA(cudaMemcpyAsync(p->ws + p->r_push.off + site_off[si] * sizeof(uint16_t), mask.data(),
+                                         mask.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st), "batched: peer masks");
+                XYL_CUDA(cudaStreamSynchronize(st), "batched: sync");
             }
-            XYL_CUDA(cudaMemcpyAsync(p->ws + p->r_push.off, mask.data(), mask.size() * sizeof(uint16_t),
-                                     cudaMemcpyHostToDevice, st), "batched: peer masks");
-            XYL_CUDA(cudaStreamSynchronize(st), "batched: sync");
         }
-        XYL_CUDA(cudaMemcpyAsync(p->ws + p->r_units.off, p->units.data(), p->units.size() * sizeof(int2),
-                                 cudaMemcpyHostToDevice, st), "batched: unit table");
-        // the global-memory shape expects the buffer of its next sweep cleared
-        XYL_CUDA(cudaMemsetAsync(p->ws + p->r_obs.off, 0, p->r_obs.bytes, st), "batched: obs");
-        XYL_CUDA(cudaStreamSynchronize(st), "batched: sync");
-        p->drop_graphs();
         return XYL_OK;
     }
-    XYL_CUDA(batched_max_active_clusters(p->shape, p->bshape, &clusters), "batched: occupancy");
+    XYL_CUDA(batched_max_active_clusters(p->shape, B, &clusters), "batched: occupancy");
     if (clusters < 1)
         return fail(XYL_EINVAL, "batched: a cluster of %d CTAs x %d threads (%zu B shared) cannot be resident",
-                    p->bshape.G, p->bshape.block, p->bshape.smem_bytes);
-    const int n_groups = p->hs[0].R / p->bshape.Rg;
+                    B.G, B.block, B.smem_bytes);
+    const int n_groups = h0.R / B.Rg;
     bool uniform_groups = true;
     int groups_max = 1;
-    for (auto &h : p->hs) {
-        uniform_groups &= (h.R / p->bshape.Rg == n_groups);
-        groups_max = std::max(groups_max, h.R / p->bshape.Rg);
+    for (int si : part.samples) {
+        uniform_groups &= (p->hs[si].R / B.Rg == n_groups);
+        groups_max = std::max(groups_max, p->hs[si].R / B.Rg);
     }
     if (groups_max > 1) {
         if (!uniform_groups) return fail(XYL_EINVAL, "batched: several groups per sample need equal n_temps");
         int samples_per_wave = clusters / n_groups;
         if (samples_per_wave < 1)
             return fail(XYL_EINVAL, "batched: %d clusters of %d CTAs cannot be co-resident (max %d)", n_groups,
-                        p->bshape.G, clusters);
-        if (p->bshape.l2_waves) samples_per_wave = std::min(samples_per_wave, l2_wave_samples(p));
-        p->wave_units = samples_per_wave * n_groups;
+                        B.G, clusters);
+        if (B.l2_waves) samples_per_wave = std::min(samples_per_wave, l2_wave_samples(p, part));
+        part.wave_units = samples_per_wave * n_groups;
+        part.barrier_free = false;
     } else {
         // one group per sample: clusters never wait on one another, so a launch
         // may hold more than fit at once (the hardware queues them), unless
         // its waves are sized to L2
-        p->wave_units = p->bshape.l2_waves ? std::min((int)p->units.size(), l2_wave_samples(p))
-                                           : (int)p->units.size();
+        part.wave_units = B.l2_waves ? std::min(n_units, l2_wave_samples(p, part)) : n_units;
+        part.barrier_free = true;
     }
+    return XYL_OK;
+}
+
+// Upload the unit table; streams and events for parts that run side by side;
+// the global-memory shape expects the sum buffer of its next sweep cleared.
+int finish_configure(xyl_plan *p, cudaStream_t st)
+{
+    gather_units(p);
     XYL_CUDA(cudaMemcpyAsync(p->ws + p->r_units.off, p->units.data(), p->units.size() * sizeof(int2),
                              cudaMemcpyHostToDevice, st), "batched: unit table");
     XYL_CUDA(cudaMemsetAsync(p->ws + p->r_obs.off, 0, p->r_obs.bytes, st), "batched: obs");
     XYL_CUDA(cudaStreamSynchronize(st), "batched: sync");
+    int side = 0;
+    for (const Part &part : p->parts) side += part.barrier_free ? 1 : 0;
+    while ((int)p->part_streams.size() < side) {
+        cudaStream_t q = nullptr;
+        cudaEvent_t e = nullptr;
+        XYL_CUDA(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking), "batched: stream");
+        p->part_streams.push_back(q);
+        XYL_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "batched: event");
+        p->part_events.push_back(e);
+    }
+    if (!p->fork_event && side > 1)
+        XYL_CUDA(cudaEventCreateWithFlags(&p->fork_event, cudaEventDisableTiming), "batched: event");
     p->drop_graphs();
     return XYL_OK;
+}
+
+int configure_batched(xyl_plan *p, cudaStream_t st)
+{
+    for (Part &part : p->parts) {
+        const int rc = configure_part(p, part, st);
+        if (rc) return rc;
+    }
+    return finish_configure(p, st);
 }
 
 }  // namespace
@@ -449,11 +630,9 @@ int xyl_plan_create(const xyl_sample *samples, int32_t n_samples, int32_t engine
         delete p;
         return fail(XYL_EINVAL, "xyl_plan_create: spin_dim %d (2 = XY, 3 = O(3))", dim);
     }
-    if (dim == 3 && engine == XYL_FP32_BATCHED) {
-        delete p;
-        return fail(XYL_EINVAL, "xyl_plan_create: O(3) spins run on the plain engines");
-    }
     p->shape.dim = dim;
+    // O(3) spins are padded 4-vectors, replica-major in global memory on every engine
+    if (dim == 3) p->shape.layout = kReplicaMajor;
     for (int s = 0; s < n_samples; ++s) {
         const xyl_sample &in = samples[s];
         const xyl_graph *g = in.graph;
@@ -664,24 +843,68 @@ int zero_region(xyl_plan *p, const Region &r, cudaStream_t st)
     return XYL_OK;
 }
 
+// Launch units [u, u + cnt) of a part, in its waves.
+int launch_units(xyl_plan *p, const DevPlan &P, const Part &part, int u_begin, int cnt, int n, uint32_t ops,
+                 int measure_every, cudaStream_t st, int64_t *launches)
+{
+    for (int u = u_begin; u < u_begin + cnt; u += part.wave_units) {
+        const int c = std::min(part.wave_units, u_begin + cnt - u);
+        if (part.B.resident && part.B.dim == 3)
+            XYL_CUDA(launch_resident_o3(P, part.B, at<int2>(p, p->r_units), u, c, n, ops, measure_every, st),
+                     "sweep: resident launch");
+        else if (part.B.resident)
+            XYL_CUDA(launch_resident(P, part.B, at<int2>(p, p->r_units), u, c, n, ops, measure_every, st),
+                     "sweep: resident launch");
+        else
+            XYL_CUDA(launch_batched(P, p->shape, part.B, at<int2>(p, p->r_units), u, c, n, ops, measure_every, st),
+                     "sweep: batched launch");
+        ++*launches;
+    }
+    return XYL_OK;
+}
+
+// The batched engine's launches for n sweeps: parts whose clusters wait on
+// other clusters of their sample run first, one after another, each with the
+// whole GPU (nothing else may hold the SMs their waves count on); then the
+// parts that never wait run side by side on forked streams.
+int issue_batched(xyl_plan *p, const DevPlan &P, int n, uint32_t ops, int measure_every, cudaStream_t st,
+                  int64_t *launches, bool side_by_side)
+{
+    int rc;
+    XYL_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(P.barrier), 0, p->hs.size() * sizeof(unsigned int), st),
+             "sweep: barrier reset");
+    std::vector<const Part *> free_parts;
+    for (const Part &part : p->parts) {
+        if (part.barrier_free) {
+            free_parts.push_back(&part);
+            continue;
+        }
+        if ((rc = launch_units(p, P, part, part.u0, (int)part.units.size(), n, ops, measure_every, st, launches)))
+            return rc;
+    }
+    if (free_parts.size() <= 1 || !side_by_side || !p->fork_event) {
+        for (const Part *part : free_parts)
+            if ((rc = launch_units(p, P, *part, part->u0, (int)part->units.size(), n, ops, measure_every, st, launches)))
+                return rc;
+        return XYL_OK;
+    }
+    XYL_CUDA(cudaEventRecord(p->fork_event, st), "sweep: fork");
+    for (size_t k = 0; k < free_parts.size(); ++k) {
+        cudaStream_t q = p->part_streams[k];
+        XYL_CUDA(cudaStreamWaitEvent(q, p->fork_event, 0), "sweep: fork");
+        if ((rc = launch_units(p, P, *free_parts[k], free_parts[k]->u0, (int)free_parts[k]->units.size(), n, ops,
+                               measure_every, q, launches)))
+            return rc;
+        XYL_CUDA(cudaEventRecord(p->part_events[k], q), "sweep: join");
+        XYL_CUDA(cudaStreamWaitEvent(st, p->part_events[k], 0), "sweep: join");
+    }
+    return XYL_OK;
+}
+
 // Enqueue the work of `n` sweeps (no graph).
 int issue_sweeps(xyl_plan *p, int n, uint32_t ops, int measure_every, cudaStream_t st, int64_t *launches)
 {
-    if (p->engine == XYL_FP32_BATCHED) {
-        XYL_CUDA(cudaMemsetAsync(p->ws + p->r_barrier.off, 0, p->r_barrier.bytes, st), "sweep: barrier reset");
-        const int total = (int)p->units.size();
-        for (int u = 0; u < total; u += p->wave_units) {
-            const int cnt = std::min(p->wave_units, total - u);
-            if (p->bshape.resident)
-                XYL_CUDA(launch_resident(p->dev, p->bshape, at<int2>(p, p->r_units), u, cnt, n, ops, measure_every, st),
-                         "sweep: resident launch");
-            else
-                XYL_CUDA(launch_batched(p->dev, p->shape, p->bshape, at<int2>(p, p->r_units), u, cnt, n, ops,
-                                        measure_every, st), "sweep: batched launch");
-            ++*launches;
-        }
-        return XYL_OK;
-    }
+    if (p->engine == XYL_FP32_BATCHED) return issue_batched(p, p->dev, n, ops, measure_every, st, launches, true);
     for (int k = 0; k < n; ++k)
         XYL_CUDA(launch_plain_sweep(p->dev, p->shape, ops, measure_every, st, launches), "sweep: plain launch");
     return XYL_OK;
@@ -715,8 +938,12 @@ int run_captured(xyl_plan *p, int n, uint32_t ops, int measure_every, cudaStream
 
 int64_t launches_of(xyl_plan *p, int n, uint32_t ops)
 {
-    if (p->engine == XYL_FP32_BATCHED)
-        return ((int64_t)p->units.size() + p->wave_units - 1) / p->wave_units;
+    if (p->engine == XYL_FP32_BATCHED) {
+        int64_t n_launch = 0;
+        for (const Part &part : p->parts)
+            n_launch += ((int64_t)part.units.size() + part.wave_units - 1) / part.wave_units;
+        return n_launch;
+    }
     const int64_t per_sweep = (int64_t)(((ops & XYL_OP_MET) ? p->shape.max_Q : 0) +
                                         ((ops & XYL_OP_OR) ? p->shape.max_Q : 0) + 1);
     return per_sweep * n;
@@ -795,18 +1022,21 @@ int xyl_sweep_units(xyl_plan *p, int32_t first_unit, int32_t n_units, int32_t n_
     if (!(ops & XYL_OP_MEASURE)) measure_every = 1;
     cudaStream_t st = as_stream(stream);
     p->last_launches = 0;
-    if (p->bshape.resident && (first_unit % p->bshape.gpc || n_units % p->bshape.gpc))
-        return fail(XYL_EINVAL, "xyl_sweep_units: a resident cluster runs %d units together", p->bshape.gpc);
+    // the range may span parts: each part runs its own units of it
+    for (const Part &part : p->parts) {
+        const int lo = std::max(first_unit, part.u0);
+        const int hi = std::min(first_unit + n_units, part.u0 + (int)part.units.size());
+        if (lo >= hi) continue;
+        if (part.B.resident && ((lo - part.u0) % part.B.gpc || (hi - lo) % part.B.gpc))
+            return fail(XYL_EINVAL, "xyl_sweep_units: a resident cluster runs %d units together", part.B.gpc);
+    }
     XYL_CUDA(cudaMemsetAsync(p->ws + p->r_barrier.off, 0, p->r_barrier.bytes, st), "xyl_sweep_units: barrier reset");
-    for (int u = first_unit; u < first_unit + n_units; u += p->wave_units) {
-        const int cnt = std::min(p->wave_units, first_unit + n_units - u);
-        if (p->bshape.resident)
-            XYL_CUDA(launch_resident(p->dev, p->bshape, at<int2>(p, p->r_units), u, cnt, n_sweeps, ops, measure_every,
-                                     st), "xyl_sweep_units: launch");
-        else
-            XYL_CUDA(launch_batched(p->dev, p->shape, p->bshape, at<int2>(p, p->r_units), u, cnt, n_sweeps, ops,
-                                    measure_every, st), "xyl_sweep_units: launch");
-        ++p->last_launches;
+    for (const Part &part : p->parts) {
+        const int lo = std::max(first_unit, part.u0);
+        const int hi = std::min(first_unit + n_units, part.u0 + (int)part.units.size());
+        if (lo >= hi) continue;
+        if ((rc = launch_units(p, p->dev, part, lo, hi - lo, n_sweeps, ops, measure_every, st, &p->last_launches)))
+            return rc;
     }
     return XYL_OK;
 }
@@ -847,17 +1077,7 @@ int xyl_sweep_noalloc(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measu
         if (p->recompute_every > 0) n = (int)std::min<int64_t>(n, p->recompute_every - p->sweeps_since_recompute);
         // every launch finds the sum buffer of its first sweep and the barrier counters at zero
         XYL_CUDA(cudaMemsetAsync(base, 0, need, st), "xyl_sweep_noalloc: clear scratch");
-        const int total = (int)p->units.size();
-        for (int u = 0; u < total; u += p->wave_units) {
-            const int cnt = std::min(p->wave_units, total - u);
-            if (p->bshape.resident)
-                XYL_CUDA(launch_resident(P, p->bshape, at<int2>(p, p->r_units), u, cnt, n, ops, measure_every, st),
-                         "xyl_sweep_noalloc: launch");
-            else
-                XYL_CUDA(launch_batched(P, p->shape, p->bshape, at<int2>(p, p->r_units), u, cnt, n, ops,
-                                        measure_every, st), "xyl_sweep_noalloc: launch");
-            ++p->last_launches;
-        }
+        if ((rc = issue_batched(p, P, n, ops, measure_every, st, &p->last_launches, false))) return rc;
         left -= n;
         p->sweeps_since_recompute += n;
         if (p->recompute_every > 0 && p->sweeps_since_recompute >= p->recompute_every) {
@@ -880,7 +1100,12 @@ int32_t xyl_unit_count(const xyl_plan *p)
 
 int32_t xyl_wave_units(const xyl_plan *p)
 {
-    return (p && p->engine == XYL_FP32_BATCHED && p->bound) ? (int32_t)p->wave_units : 0;
+    return (p && p->engine == XYL_FP32_BATCHED && p->bound) ? (int32_t)p->parts[0].wave_units : 0;
+}
+
+int32_t xyl_part_count(const xyl_plan *p)
+{
+    return (p && p->engine == XYL_FP32_BATCHED) ? (int32_t)p->parts.size() : 0;
 }
 
 int xyl_pt_swap(xyl_plan *p, void *stream)
@@ -1127,6 +1352,23 @@ int xyl_write_spins(xyl_plan *p, int32_t sample, int32_t replica, const double *
     return XYL_OK;
 }
 
+int xyl_check_plan(xyl_plan *p, int64_t *violations, void *stream)
+{
+    clear_error();
+    int rc = check_bound(p, "xyl_check_plan");
+    if (rc) return rc;
+    if (!violations) return fail(XYL_EINVAL, "xyl_check_plan: NULL output");
+    cudaStream_t st = as_stream(stream);
+    unsigned long long *d = at<unsigned long long>(p, p->r_check);
+    XYL_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned long long), st), "xyl_check_plan: clear");
+    XYL_CUDA(launch_check(p->dev, p->shape, d, st), "xyl_check_plan: launch");
+    unsigned long long n = 0;
+    XYL_CUDA(cudaMemcpyAsync(&n, d, sizeof(n), cudaMemcpyDeviceToHost, st), "xyl_check_plan: copy");
+    XYL_CUDA(cudaStreamSynchronize(st), "xyl_check_plan: sync");
+    *violations = (int64_t)n;
+    return XYL_OK;
+}
+
 int xyl_read_drift(xyl_plan *p, double *max_drift, int32_t reset, void *stream)
 {
     clear_error();
@@ -1223,21 +1465,56 @@ int xyl_import_state(xyl_plan *p, const void *host, size_t bytes, void *stream)
 
 int64_t xyl_last_launch_count(const xyl_plan *p) { return p ? p->last_launches : 0; }
 
-int xyl_get_tuning(const xyl_plan *p, xyl_tuning *out)
+int xyl_get_part_tuning(const xyl_plan *p, int32_t part, xyl_tuning *out, int32_t *n_samples)
 {
-    if (!p || !out) return fail(XYL_EINVAL, "xyl_get_tuning: NULL argument");
+    if (!p || !out) return fail(XYL_EINVAL, "xyl_get_part_tuning: NULL argument");
     std::memset(out, 0, sizeof(*out));
     out->recompute_every = p->recompute_every;
     out->spin_dim = p->shape.dim;
-    if (p->engine == XYL_FP32_BATCHED) {
-        out->block = p->bshape.block;
-        out->cluster = p->bshape.G;
-        out->group = p->bshape.Rg;
-        out->stage = p->bshape.staged ? 1 : -1;
-        out->resident = p->bshape.resident ? 1 : -1;
-        out->waves = p->bshape.l2_waves ? 1 : -1;
-    }
+    if (n_samples) *n_samples = 0;
+    if (p->engine != XYL_FP32_BATCHED) return part == 0 ? XYL_OK : fail(XYL_EINVAL, "xyl_get_part_tuning: bad part");
+    if (part < 0 || part >= (int)p->parts.size()) return fail(XYL_EINVAL, "xyl_get_part_tuning: bad part %d", part);
+    const BatchedShape &B = p->parts[part].B;
+    out->block = B.block;
+    out->cluster = B.G;
+    out->group = B.Rg;
+    out->stage = B.staged ? 1 : -1;
+    out->resident = B.resident ? 1 : -1;
+    out->waves = B.l2_waves ? 1 : -1;
+    if (n_samples) *n_samples = (int32_t)p->parts[part].samples.size();
     return XYL_OK;
+}
+
+int xyl_set_part_tuning(xyl_plan *p, int32_t part, const xyl_tuning *t, void *stream)
+{
+    clear_error();
+    if (!p || !t) return fail(XYL_EINVAL, "xyl_set_part_tuning: NULL argument");
+    if (p->engine != XYL_FP32_BATCHED) return fail(XYL_EINVAL, "xyl_set_part_tuning: batched engine only");
+    if (part < 0 || part >= (int)p->parts.size()) return fail(XYL_EINVAL, "xyl_set_part_tuning: bad part %d", part);
+    if (t->resident == 0 || t->group < 1 || t->cluster < 1 || t->block < 1)
+        return fail(XYL_EINVAL, "xyl_set_part_tuning: resident (+-1), group, cluster and block must be given");
+    Part &pt = p->parts[part];
+    const Part keep = pt;
+    int rc = apply_shape(p, pt, t->group, t->cluster, t->block, t->stage, t->resident > 0 ? 1 : 0,
+                         t->waves > 0 ? 1 : 0);
+    if (!rc && p->bound) {
+        cudaStream_t st = as_stream(stream);
+        rc = configure_part(p, pt, st);
+        if (!rc) rc = finish_configure(p, st);
+    }
+    if (rc) {
+        pt = keep;  // the part keeps its shape
+        gather_units(p);
+        return rc;
+    }
+    if (!p->bound) gather_units(p);
+    return XYL_OK;
+}
+
+int xyl_get_tuning(const xyl_plan *p, xyl_tuning *out)
+{
+    if (!p || !out) return fail(XYL_EINVAL, "xyl_get_tuning: NULL argument");
+    return xyl_get_part_tuning(p, 0, out, nullptr);
 }
 
 int xyl_autotune(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_every, xyl_tuning *best,
@@ -1255,84 +1532,104 @@ int xyl_autotune(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_ev
     // chain, which does not change how long a sweep takes
     std::vector<char> snap(xyl_state_bytes(p));
     if ((rc = xyl_export_state(p, snap.data(), snap.size(), stream))) return rc;
-    const BatchedShape keep = p->bshape;
-    const int keep_stage = p->stage_mode;
     cudaEvent_t e0, e1;
     XYL_CUDA(cudaEventCreate(&e0), "xyl_autotune: event");
     XYL_CUDA(cudaEventCreate(&e1), "xyl_autotune: event");
-    float best_ms = -1.f;
-    int best_g = keep.Rg, best_G = keep.G, best_block = keep.block, best_res = keep.resident ? 1 : 0;
-    int best_waves = keep.l2_waves ? 1 : 0;
     int dev = 0, n_sm = 0, l2 = 0;
     XYL_CUDA(cudaGetDevice(&dev), "xyl_autotune: device");
     XYL_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev), "xyl_autotune: SM count");
     XYL_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev), "xyl_autotune: L2 size");
-    size_t live = 0;
-    for (auto &h : p->hs) live += sample_live_bytes(h);
-    // L2-sized waves change nothing when the whole batch fits in L2
-    const bool try_waves = live > (size_t)l2 * 3 / 4 && p->waves_req >= 0;
-    const bool large = p->total_spins >= ((int64_t)1 << 26);
-    for (int res = 0; res <= 1; ++res) {
-        if ((p->resident_req < 0 && res) || (p->resident_req > 0 && !res)) continue;
-        for (int waves = 0; waves <= (res ? 0 : 1); ++waves) {
-            if (waves ? !try_waves : p->waves_req > 0) continue;
-            for (int g = 1; g <= 32; g *= 2) {
-                bool divides = true;
-                for (auto &h : p->hs) divides &= (h.R % g == 0);
-                if (!divides) continue;
-                int64_t units = 0;
-                for (auto &h : p->hs) units += h.R / g;
-                for (int G : {1, 2, 3, 4, 5, 6, 7, 8, 12, 16}) {
-                    // global-memory shape: powers of two and 6, 12 (a GPC holds two
-                    // clusters of 6 or 8 but one of 12 or 16); split a resident
-                    // group across CTAs only while the batch leaves SMs idle
-                    if (!res && (G & (G - 1)) && G != 6 && G != 12) continue;
-                    if (res && G > 1 && units * G > 2 * (int64_t)n_sm) continue;
-                    for (int block : {128, 256, 384, 512, 640, 768, 1024}) {
-                        if (res ? block == 128 : (block == 384 || block > 672)) continue;
-                        if (!res && large && block < 512) continue;  // large samples: many items per CTA
-                        if (apply_shape(p, g, G, block, keep_stage, res, waves) || configure_batched(p, st)) continue;
-                        float ms = 0.f;
-                        bool ok = true;
-                        for (int rep = 0; rep < 2 && ok; ++rep) {
-                            // a shape already 1.5x slower than the best on its first timing cannot win
-                            if (rep == 1 && best_ms > 0.f && ms > 1.5f * best_ms) break;
-                            int64_t launches = 0;
-                            XYL_CUDA(cudaMemsetAsync(p->ws + p->r_barrier.off, 0, p->r_barrier.bytes, st), "xyl_autotune");
-                            XYL_CUDA(cudaEventRecord(e0, st), "xyl_autotune: record");
-                            if (issue_sweeps(p, n_sweeps, ops, measure_every, st, &launches)) { ok = false; break; }
-                            XYL_CUDA(cudaEventRecord(e1, st), "xyl_autotune: record");
-                            XYL_CUDA(cudaEventSynchronize(e1), "xyl_autotune: sync");
-                            XYL_CUDA(cudaEventElapsedTime(&ms, e0, e1), "xyl_autotune: time");
-                            int32_t status = 0;
-                            XYL_CUDA(cudaMemcpy(&status, p->ws + p->r_status.off, sizeof(status), cudaMemcpyDeviceToHost),
-                                     "xyl_autotune: status");
-                            if (status) {
-                                ok = false;
-                                XYL_CUDA(cudaMemset(p->ws + p->r_status.off, 0, sizeof(int32_t)), "xyl_autotune: status");
+    bool any = false;
+    // each part on its own: its launches alone are timed for every shape
+    for (Part &part : p->parts) {
+        const BatchedShape keep = part.B;
+        const int keep_stage = part.stage_mode;
+        float best_ms = -1.f;
+        int best_g = keep.Rg, best_G = keep.G, best_block = keep.block, best_res = keep.resident ? 1 : 0;
+        int best_waves = keep.l2_waves ? 1 : 0;
+        size_t live = 0;
+        int64_t spins = 0;
+        for (int si : part.samples) {
+            live += sample_live_bytes(p->hs[si]);
+            spins += (int64_t)p->hs[si].N * p->hs[si].R;
+        }
+        // L2-sized waves change nothing when the whole part fits in L2
+        const bool try_waves = live > (size_t)l2 * 3 / 4 && p->waves_req >= 0;
+        const bool large = spins >= ((int64_t)1 << 26);
+        for (int res = 0; res <= 1; ++res) {
+            if ((p->resident_req < 0 && res) || (p->resident_req > 0 && !res)) continue;
+            for (int waves = 0; waves <= (res ? 0 : 1); ++waves) {
+                if (waves ? !try_waves : p->waves_req > 0) continue;
+                for (int g = 1; g <= 32; g *= 2) {
+                    bool divides = true;
+                    for (int si : part.samples) divides &= (p->hs[si].R % g == 0);
+                    if (!divides) continue;
+                    int64_t units = 0;
+                    for (int si : part.samples) units += p->hs[si].R / g;
+                    for (int G : {1, 2, 3, 4, 5, 6, 7, 8, 12, 16}) {
+                        if (p->shape.dim == 3 && (G > 1 || !res)) continue;  // O(3): resident, one CTA per group
+                        // global-memory shape: powers of two and 6, 12 (a GPC holds two
+                        // clusters of 6 or 8 but one of 12 or 16); split a resident
+                        // group across CTAs only while the batch leaves SMs idle
+                        if (!res && (G & (G - 1)) && G != 6 && G != 12) continue;
+                        if (res && G > 1 && units * G > 2 * (int64_t)n_sm) continue;
+                        for (int block : {128, 256, 384, 512, 640, 768, 1024}) {
+                            if (res ? block == 128 : block == 384) continue;
+                            if (!res && large && block < 512) continue;  // large samples: many items per CTA
+                            if (apply_shape(p, part, g, G, block, keep_stage, res, waves) ||
+                                configure_part(p, part, st) || finish_configure(p, st))
+                                continue;
+                            float ms = 0.f, rep_ms = 0.f;
+                            bool ok = true;
+                            for (int rep = 0; rep < 2 && ok; ++rep) {
+                                // a shape already 1.5x slower than the best on its first timing cannot win
+                                if (rep == 1 && best_ms > 0.f && ms > 1.5f * best_ms) break;
+                                int64_t launches = 0;
+                                XYL_CUDA(cudaMemsetAsync(p->ws + p->r_barrier.off, 0, p->r_barrier.bytes, st),
+                                         "xyl_autotune");
+                                XYL_CUDA(cudaEventRecord(e0, st), "xyl_autotune: record");
+                                if (launch_units(p, p->dev, part, part.u0, (int)part.units.size(), n_sweeps, ops,
+                                                 measure_every, st, &launches)) {
+                                    ok = false;
+                                    break;
+                                }
+                                XYL_CUDA(cudaEventRecord(e1, st), "xyl_autotune: record");
+                                XYL_CUDA(cudaEventSynchronize(e1), "xyl_autotune: sync");
+                                XYL_CUDA(cudaEventElapsedTime(&rep_ms, e0, e1), "xyl_autotune: time");
+                                ms = rep == 0 ? rep_ms : std::min(ms, rep_ms);  // the faster of the two timings
+                                int32_t status = 0;
+                                XYL_CUDA(cudaMemcpy(&status, p->ws + p->r_status.off, sizeof(status),
+                                                    cudaMemcpyDeviceToHost), "xyl_autotune: status");
+                                if (status) {
+                                    ok = false;
+                                    XYL_CUDA(cudaMemset(p->ws + p->r_status.off, 0, sizeof(int32_t)),
+                                             "xyl_autotune: status");
+                                }
                             }
-                        }
-                        clear_error();
-                        if (ok && (best_ms < 0.f || ms < best_ms)) {
-                            best_ms = ms;
-                            best_g = g;
-                            best_G = G;
-                            best_block = block;
-                            best_res = res;
-                            best_waves = waves;
+                            clear_error();
+                            if (ok && (best_ms < 0.f || ms < best_ms)) {
+                                best_ms = ms;
+                                best_g = g;
+                                best_G = G;
+                                best_block = block;
+                                best_res = res;
+                                best_waves = waves;
+                            }
                         }
                     }
                 }
             }
         }
+        any |= best_ms >= 0.f;
+        if ((rc = apply_shape(p, part, best_g, best_G, best_block, keep_stage, best_res, best_waves))) return rc;
+        if ((rc = configure_part(p, part, st))) return rc;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if ((rc = apply_shape(p, best_g, best_G, best_block, keep_stage, best_res, best_waves))) return rc;
-    if ((rc = configure_batched(p, st))) return rc;
+    if ((rc = finish_configure(p, st))) return rc;
     if ((rc = xyl_import_state(p, snap.data(), snap.size(), stream))) return rc;
     if (best) xyl_get_tuning(p, best);
-    return best_ms < 0.f ? fail(XYL_EINVAL, "xyl_autotune: no launch shape ran") : XYL_OK;
+    return any ? XYL_OK : fail(XYL_EINVAL, "xyl_autotune: no launch shape ran");
 }
 
 void xyl_plan_free(xyl_plan *p) { delete p; }

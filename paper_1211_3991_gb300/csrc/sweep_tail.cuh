@@ -38,10 +38,12 @@ __device__ __forceinline__ bool pt_accept(double u, double x)
 // (NULL: read from the plan).  The leader's counters are fire-and-forget
 // atomics, so no read of global memory sits on its path.  The leader then writes the labels and energies back and, on
 // measurement sweeps, adds e, e^2, |m|, m_x, m_y, m^2, m^4 and chi(k_min) of
-// each slot (Sec. III) from the per-replica sums obs_s.
+// each slot (Sec. III) from the per-replica sums obs_s; dim = 3 (O(3) spins)
+// adds the third component to m^2 and |F(k)|^2 and sums m_z.
 __device__ __forceinline__ void pt_and_record(const DevPlan &P, const DevSample &d, const double *E, int *rep_at,
                                               int *slot_of, uint32_t t, uint32_t ops, bool leader, bool met,
-                                              bool measure, const double *obs_s, const double *beta_s = nullptr)
+                                              bool measure, const double *obs_s, const double *beta_s = nullptr,
+                                              int dim = 2)
 {
     const int R = d.R;
     if (ops & XYL_OP_PT) {
@@ -76,7 +78,8 @@ __device__ __forceinline__ void pt_and_record(const DevPlan &P, const DevSample 
             const double *o = obs_s + (size_t)r * kObsStride;
             const double e = E[r] * invN;
             const double mx = __ldcg(o + kObsMx) * invN, my = __ldcg(o + kObsMy) * invN;
-            const double m2 = mx * mx + my * my;
+            const double mz = dim == 3 ? __ldcg(o + kObsMz) * invN : 0.0;
+            double m2 = mx * mx + my * my;
             double f1 = 0.0, f2 = 0.0;
 #pragma unroll
             for (int f = kObsF1xRe; f <= kObsF1yIm; ++f) {
@@ -88,6 +91,13 @@ __device__ __forceinline__ void pt_and_record(const DevPlan &P, const DevSample 
                 const double z = __ldcg(o + f);
                 f2 += z * z;
             }
+            if (dim == 3) {
+                m2 += mz * mz;
+                const double a1 = __ldcg(o + kObsF1zRe), b1 = __ldcg(o + kObsF1zIm);
+                const double a2 = __ldcg(o + kObsF2zRe), b2 = __ldcg(o + kObsF2zIm);
+                f1 += a1 * a1 + b1 * b1;
+                f2 += a2 * a2 + b2 * b2;
+            }
             double *a = P.acc + (size_t)(d.rep_off + k) * kAccCount;
             a[XYL_ACC_N] += 1.0;
             a[XYL_ACC_E] += e;
@@ -98,6 +108,7 @@ __device__ __forceinline__ void pt_and_record(const DevPlan &P, const DevSample 
             a[XYL_ACC_M2] += m2;
             a[XYL_ACC_M4] += m2 * m2;
             a[XYL_ACC_CHIK] += (f1 + f2) * 0.5 * invN;
+            if (dim == 3) a[XYL_ACC_MZ] += mz;
         }
     }
 }

@@ -30,7 +30,8 @@ EXPORTED = (
     "xyl_last_launch_count", "xyl_plan_free", "xyl_sweep_units", "xyl_unit_count", "xyl_autotune",
     "xyl_get_tuning", "xyl_sweep_noalloc", "xyl_build_levy_bonds", "xyl_walk_returns", "xyl_graph_set_couplings",
     "xyl_graph_export_couplings", "xyl_graph_set_fields", "xyl_philox", "xyl_read_drift",
-    "xyl_get_delta", "xyl_tune_delta", "xyl_wave_units",
+    "xyl_get_delta", "xyl_tune_delta", "xyl_wave_units", "xyl_part_count", "xyl_get_part_tuning",
+    "xyl_set_part_tuning", "xyl_check_plan",
 )
 
 
@@ -111,6 +112,10 @@ def load():
             "xyl_get_delta": ([P, i32, pf64], C.c_int),
             "xyl_tune_delta": ([P, i32, i32, u32, f64, pf64, P], C.c_int),
             "xyl_wave_units": ([P], C.c_int32),
+            "xyl_part_count": ([P], C.c_int32),
+            "xyl_get_part_tuning": ([P, i32, C.POINTER(Tuning), pi32], C.c_int),
+            "xyl_set_part_tuning": ([P, i32, C.POINTER(Tuning), P], C.c_int),
+            "xyl_check_plan": ([P, pi64, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -303,6 +308,54 @@ class Plan:
     def wave_units(self) -> int:
         return int(load().xyl_wave_units(self.handle))
 
+    def part_count(self) -> int:
+        return int(load().xyl_part_count(self.handle))
+
+    def set_part_tuning(self, part, t, stream=None):
+        """xyl_set_part_tuning: a launch shape for one part (keys block, cluster, group, stage, resident, waves)."""
+        tune = Tuning(int(t["block"]), int(t["cluster"]), int(t["group"]), 0, int(t.get("stage", 0)),
+                      int(t["resident"]), self.dim, int(t.get("waves", 0)))
+        _check(load().xyl_set_part_tuning(self.handle, int(part), C.byref(tune), _stream(stream)))
+
+    def signature(self) -> str:
+        """What a launch shape depends on: engine, spin dimension, and per sample its size,
+        slots, largest degree and colour count, in plan order; with the GPU's name."""
+        import hashlib
+        import torch
+        rows = [(g.n, len(b), g.max_deg, g.n_colors) for g, b in zip(self._keep[0::3], self._keep[1::3])]
+        text = f"{self.engine}|{self.dim}|{torch.cuda.get_device_name()}|{rows}"
+        return hashlib.sha256(text.encode()).hexdigest()[:24]
+
+    def autotune_cached(self, path, n_sweeps=4, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1,
+                        stream=None):
+        """The launch shapes an earlier xyl_autotune chose for a batch with this
+        signature, read from the JSON file `path`; on a miss, autotune and add
+        them.  Returns (per-part shapes, True if they came from the file)."""
+        import json
+        cache = {}
+        if os.path.exists(path):
+            with open(path) as f:
+                cache = json.load(f)
+        key = self.signature()
+        if key in cache and len(cache[key]["parts"]) == self.part_count():
+            for k, t in enumerate(cache[key]["parts"]):
+                self.set_part_tuning(k, t, stream=stream)
+            return cache[key]["parts"], True
+        self.autotune(n_sweeps, ops, measure_every, stream=stream)
+        parts = [{k: v for k, v in self.part_tuning(i).items() if k != "samples"} for i in range(self.part_count())]
+        cache[key] = {"parts": parts, "sizes": sorted(set(self.sizes)), "slots": sorted(set(self.n_temps))}
+        with open(path, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        return parts, False
+
+    def part_tuning(self, part) -> dict:
+        """Launch shape of one part of a mixed-size batch and its sample count."""
+        t = Tuning()
+        n = C.c_int32()
+        _check(load().xyl_get_part_tuning(self.handle, int(part), C.byref(t), C.byref(n)))
+        return {"block": t.block, "cluster": t.cluster, "group": t.group, "stage": t.stage,
+                "resident": t.resident, "waves": t.waves, "samples": n.value}
+
     def autotune(self, n_sweeps, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1, stream=None) -> dict:
         t = Tuning()
         _check(load().xyl_autotune(self.handle, int(n_sweeps), int(ops), int(measure_every), C.byref(t),
@@ -381,6 +434,12 @@ class Plan:
         if len(a) != self.dim * self.sizes[sample]:
             raise XylError(EINVAL, f"write_spins: need {self.dim} components per site")
         _check(load().xyl_write_spins(self.handle, sample, replica, _p(a, C.c_double), _stream(stream)))
+
+    def check(self, stream=None) -> int:
+        """xyl_check_plan: failed checks of the device CSR (independent colour classes, ids, order, symmetry)."""
+        out = np.zeros(1, np.int64)
+        _check(load().xyl_check_plan(self.handle, _p(out, C.c_int64), _stream(stream)))
+        return int(out[0])
 
     def drift(self, reset=False, stream=None) -> float:
         """Largest |E_fused - E_fp64| recorded by the FP64 recomputes (xyl_read_drift)."""

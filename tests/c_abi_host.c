@@ -56,13 +56,17 @@ int main(void)
         if (xyl_sweep(p, 1, XYL_OP_MET | XYL_OP_OR, 1, NULL) != XYL_ESTATE) return 6;
         xyl_plan_free(p);
     }
-    /* O(3) spins: plain engines only */
+    /* O(3) spins: plain engines, and the batched engine's resident shape only */
     xyl_tuning o3 = { 0, 0, 0, 0, 0, 0, 3, 0 };
     xyl_plan *p = NULL;
     size_t bytes = 0;
     CHECK(xyl_plan_create(s, 2, XYL_FP32_PLAIN, 7, &o3, &p, &bytes));
     xyl_plan_free(p);
-    if (xyl_plan_create(s, 2, XYL_FP32_BATCHED, 7, &o3, &p, &bytes) != XYL_EINVAL) return 7;
+    CHECK(xyl_plan_create(s, 2, XYL_FP32_BATCHED, 7, &o3, &p, &bytes));
+    if (xyl_part_count(p) != 1) return 7; /* both graphs have 1024 sites: one part */
+    xyl_plan_free(p);
+    o3.resident = -1;
+    if (xyl_plan_create(s, 2, XYL_FP32_BATCHED, 7, &o3, &p, &bytes) != XYL_EINVAL) return 8;
     printf("ok\n");
     free(perm); free(row_ptr); free(col); free(color_ptr);
     xyl_graph_free(g);

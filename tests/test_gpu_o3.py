@@ -77,11 +77,19 @@ def test_fp64_trajectory_matches_oracle(env, orc, name):
     assert plan.status() == (0, 10)
 
 
+# the FP32 engines for O(3) spins: the per-colour-launch plain engine and the
+# batched engine's resident shape (three component arrays in shared memory)
+FP32_O3 = {"FP32_PLAIN": ("FP32_PLAIN", {}), "FP32_RESIDENT": ("FP32_BATCHED", {"resident": 1}),
+           "FP32_RESIDENT_1": ("FP32_BATCHED", {"resident": 1, "group": 1, "block": 1024})}
+
+
+@pytest.mark.parametrize("engine_name", ["FP32_PLAIN", "FP32_RESIDENT"])
 @pytest.mark.parametrize("name", ["O1", "O2", "O2G"])
-def test_fp32_energy_matches_oracle(env, orc, name):
+def test_fp32_energy_matches_oracle(env, orc, name, engine_name):
     xyl, wl = env
     cfg = wl.config(name)
-    plan, _ = wl.make_plan(cfg, xyl.FP32_PLAIN)
+    eng, opts = FP32_O3[engine_name]
+    plan, _ = wl.make_plan(cfg, getattr(xyl, eng), **opts)
     plan.bind()
     plan.init_spins()
     sim = _oracle(orc, wl, cfg, 0, u24=True)
@@ -89,24 +97,55 @@ def test_fp32_energy_matches_oracle(env, orc, name):
     assert np.abs(_gpu_vectors(plan, 0, R) - sim.vectors()).max() < 1e-7
     compared, traced, flipped, worst = fp32_parity_sweeps(plan, {0: sim}, [0], 10, ALL, lambda s: N,
                                                           lambda s: slice(0, R))
-    print(f"{name}: {compared} replica-sweeps, {traced} misses traced to {flipped} flipped near-tie decisions, "
-          f"0 unexplained, worst |dE|/N {worst:.2e}")
+    print(f"{name} {engine_name}: {compared} replica-sweeps, {traced} misses traced to {flipped} flipped near-tie "
+          f"decisions, 0 unexplained, worst |dE|/N {worst:.2e}")
     assert plan.status() == (0, 10)
 
 
-@pytest.mark.parametrize("engine_name", ["FP32_PLAIN", "FP64_PLAIN"])
+@pytest.mark.parametrize("name", ["O2", "O2G", "O3"])
+def test_resident_shape_gives_the_plain_engines_spins(env, name):
+    """The resident O(3) shape performs the plain FP32 engine's per-spin
+    arithmetic (same Philox block per replica, neighbour sums in row order,
+    the single-precision steps of o3_f32.cuh), so Metropolis + overrelaxation
+    sweeps give bit-identical spins; several groups per CTA, one replica per
+    CTA at 1024 threads, and a batch of samples (O3: four L=64 graphs)."""
+    xyl, wl = env
+    cfg = wl.config(name)
+    if name == "O3":
+        cfg.graphs = cfg.graphs[:4]
+    graphs = wl.build_graphs(cfg)
+    ref = None
+    for eng_name in ("FP32_PLAIN", "FP32_RESIDENT", "FP32_RESIDENT_1"):
+        eng, opts = FP32_O3[eng_name]
+        p, _ = wl.make_plan(cfg, getattr(xyl, eng), graphs=graphs, **opts)
+        if eng == "FP32_BATCHED":
+            t = p.tuning()
+            assert t["resident"] == 1 and t["spin_dim"] == 3
+        p.bind()
+        p.init_spins()
+        p.sweep(5, NO_PT)
+        got = np.stack([p.spins(k, r) for k in range(cfg.n_samples) for r in range(cfg.n_temps)])
+        if ref is None:
+            ref = got
+        else:
+            assert np.array_equal(got, ref), eng_name
+        assert p.status() == (0, 5)
+
+
+@pytest.mark.parametrize("engine_name", ["FP32_PLAIN", "FP64_PLAIN", "FP32_RESIDENT"])
 def test_gauge_invariance_is_exact(env, engine_name):
     xyl, wl = env
     cfg = wl.config("O2G")
-    eng = getattr(xyl, engine_name)
+    eng_name, opts = FP32_O3.get(engine_name, (engine_name, {}))
+    eng = getattr(xyl, eng_name)
     g = wl.build_graphs(cfg)[0]
     ei, ej = g.edges()
     J = wl.couplings_for(cfg, 0, g.n_edges)
     tau = np.random.default_rng(8).choice(np.array([-1, 1], np.int8), g.n)
     gauged = xyl.build_graph_csr(128, 6, 3.5, wl.GRAPH_SEED, wl.graph_stream_id(cfg, 0))
     gauged.set_couplings((tau[ei] * tau[ej] * J).astype(np.int8))
-    a, _ = wl.make_plan(cfg, eng, graphs=[g])
-    b, _ = wl.make_plan(cfg, eng, graphs=[gauged])
+    a, _ = wl.make_plan(cfg, eng, graphs=[g], **opts)
+    b, _ = wl.make_plan(cfg, eng, graphs=[gauged], **opts)
     for p in (a, b):
         p.bind()
         p.init_spins()
@@ -125,13 +164,15 @@ def test_gauge_invariance_is_exact(env, engine_name):
     assert a.status() == b.status() == (0, 12)
 
 
-def test_random_tree_energy_is_the_langevin_law(env):
+@pytest.mark.parametrize("engine_name", ["FP32_PLAIN", "FP32_RESIDENT"])
+def test_random_tree_energy_is_the_langevin_law(env, engine_name):
     xyl, _ = env
     rng = np.random.default_rng(21)
     n, beta = 4096, 1.3
     edges = np.array([(int(rng.integers(0, i)), i) for i in range(1, n)], np.int32)
     g = xyl.graph_from_edges(n, edges)
-    plan = xyl.Plan([(g, 0, [beta] * 8, [2.0] * 8)], engine=xyl.FP32_PLAIN, seed=3, spin_dim=3)
+    eng, opts = FP32_O3[engine_name]
+    plan = xyl.Plan([(g, 0, [beta] * 8, [2.0] * 8)], engine=getattr(xyl, eng), seed=3, spin_dim=3, **opts)
     plan.bind()
     plan.init_spins()
     plan.sweep(200, NO_PT)
@@ -146,14 +187,15 @@ def test_random_tree_energy_is_the_langevin_law(env):
     assert plan.status() == (0, 2200)
 
 
-@pytest.mark.parametrize("engine_name", ["FP32_PLAIN", "FP64_PLAIN"])
+@pytest.mark.parametrize("engine_name", ["FP32_PLAIN", "FP64_PLAIN", "FP32_RESIDENT"])
 def test_degenerate_inputs(env, engine_name):
     """No links, a single site, a zero Metropolis step, an odd number of slots."""
     xyl, _ = env
-    eng = getattr(xyl, engine_name)
+    eng_name, opts = FP32_O3.get(engine_name, (engine_name, {}))
+    eng = getattr(xyl, eng_name)
 
     def plan_of(g, betas, deltas):
-        p = xyl.Plan([(g, 0, betas, deltas)], engine=eng, seed=4, spin_dim=3)
+        p = xyl.Plan([(g, 0, betas, deltas)], engine=eng, seed=4, spin_dim=3, **opts)
         p.bind()
         p.init_spins()
         return p
@@ -213,17 +255,19 @@ def test_uneven_batch_each_sample_matches_its_oracle(env, orc):
         off += R
 
 
-def test_checkpoint_resumes_bit_for_bit(env):
+@pytest.mark.parametrize("engine_name", ["FP32_PLAIN", "FP32_RESIDENT"])
+def test_checkpoint_resumes_bit_for_bit(env, engine_name):
     xyl, wl = env
     cfg = wl.config("O1")
-    a, _ = wl.make_plan(cfg, xyl.FP32_PLAIN)
+    eng, opts = FP32_O3[engine_name]
+    a, _ = wl.make_plan(cfg, getattr(xyl, eng), **opts)
     a.bind()
     a.init_spins()
     a.sweep(5, ALL)
     blob = a.export_state()
     a.sweep(7, ALL)
     want = (_gpu_vectors(a, 0, cfg.n_temps), a.labels(), a.read_observables()["acc"])
-    b, _ = wl.make_plan(cfg, xyl.FP32_PLAIN)
+    b, _ = wl.make_plan(cfg, getattr(xyl, eng), **opts)
     b.bind()
     b.import_state(blob)
     b.sweep(7, ALL)

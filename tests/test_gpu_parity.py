@@ -178,6 +178,31 @@ def test_fp32_energy_matches_oracle_bond_ensemble(env, orc, name, engine_name):
 
 
 # --------------------------------------------------------------- long runs
+def _observables(N):
+    """Sec. III observables from a slot's mean accumulator row: e, the
+    connected chi, U4 in the paper's form, <|m|> and chi(k_min)."""
+    return {
+        "e": lambda m: m[ACC["e"]],
+        "chi": lambda m: N * (m[ACC["m2"]] - m[ACC["mx"]] ** 2 - m[ACC["my"]] ** 2),
+        "U4": lambda m: m[ACC["m4"]] / m[ACC["m2"]] ** 2 - 1,
+        "absm": lambda m: m[ACC["absm"]],
+        "chik": lambda m: m[ACC["chik"]],
+    }
+
+
+def _compare_long_run(label, ob, gb, fns, slots):
+    """Per slot and observable: FP32 engine minus FP64 oracle within 3 sigma
+    (binned jackknife of both); prints the difference and sigma."""
+    for k in slots:
+        for key, fn in fns.items():
+            a, da = jackknife(ob[:, k, :], fn)
+            b, db = jackknife(gb[:, k, :], fn)
+            sigma = np.hypot(da, db)
+            print(f"ERRTAB {label} slot {k} {key}: oracle {a:.6g} +- {da:.2g}, FP32 {b:.6g} +- {db:.2g}, "
+                  f"diff {b - a:+.3g} = {(b - a) / sigma:+.2f} sigma")
+            assert abs(a - b) < 3 * sigma, (label, k, key, a, da, b, db)
+
+
 def _tuned_deltas(orc, wl, cfg, ops):
     """Metropolis half-widths tuned on the oracle to about 50% acceptance, then frozen."""
     sim = _oracle_for(orc, wl, cfg, 0, u24=False)
@@ -209,17 +234,7 @@ def test_long_run_statistics_bond_ensemble(env, orc):
     ob = bin_means(run_bins(sim, 100, 100, ALL))
     gb = bin_means(run_bins(plan, 100, 100, ALL))
     N = 256
-    fns = {
-        "e": lambda m: m[ACC["e"]],
-        "chi": lambda m: N * (m[ACC["m2"]] - m[ACC["mx"]] ** 2 - m[ACC["my"]] ** 2),
-        "U4": lambda m: m[ACC["m4"]] / m[ACC["m2"]] ** 2 - 1,
-        "absm": lambda m: m[ACC["absm"]],
-    }
-    for k in range(cfg.n_temps):
-        for key, fn in fns.items():
-            a, da = jackknife(ob[:, k, :], fn)
-            b, db = jackknife(gb[:, k, :], fn)
-            assert abs(a - b) < 3 * np.hypot(da, db), (k, key, a, da, b, db)
+    _compare_long_run("E1", ob, gb, _observables(N), range(cfg.n_temps))
     assert plan.status()[0] == 0
 
 
@@ -246,20 +261,9 @@ def test_long_run_statistics_c1(env, orc, engine_name):
     for s in (sim, plan):
         s.sweeps(500, NO_PT)
         s.reset_acc()
-    ob = bin_means(run_bins(sim, 100, 100, NO_PT))[:, 0, :]
-    gb = bin_means(run_bins(plan, 100, 100, NO_PT))[:, 0, :]
-    N = 256
-    fns = {
-        "e": lambda m: m[ACC["e"]],
-        "chi": lambda m: N * (m[ACC["m2"]] - m[ACC["mx"]] ** 2 - m[ACC["my"]] ** 2),
-        "U4": lambda m: m[ACC["m4"]] / m[ACC["m2"]] ** 2 - 1,
-        "absm": lambda m: m[ACC["absm"]],
-        "chik": lambda m: m[ACC["chik"]],
-    }
-    for key, fn in fns.items():
-        a, da = jackknife(ob, fn)
-        b, db = jackknife(gb, fn)
-        assert abs(a - b) < 3 * np.hypot(da, db), (key, a, da, b, db)
+    ob = bin_means(run_bins(sim, 100, 100, NO_PT))
+    gb = bin_means(run_bins(plan, 100, 100, NO_PT))
+    _compare_long_run(f"C1 {engine_name}", ob, gb, _observables(256), [0])
     plan.sweeps(200, NO_PT)
     st = plan.read_observables()
     rate = st["met_acc"][0] / st["met_try"][0]
@@ -435,6 +439,52 @@ def test_standalone_pt_and_measure_between_sweeps(env, shape):
     assert np.all(plan.read_observables()["acc"][:, ACC["n"]] == 6)  # five sweeps and one xyl_measure
 
 
+def test_c4_drift_at_its_recompute_interval(env):
+    """C4 (uneven sizes, FP64 recompute every 100 sweeps): the largest
+    |E_fused - E_fp64| the recomputes see stays far below the 1e-5-per-spin
+    bar of the smallest sample (N = 1024)."""
+    xyl, wl = env
+    cfg = wl.config("C4")
+    plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED)
+    plan.bind()
+    plan.init_spins()
+    plan.sweep(300, ALL, 32)
+    d = plan.drift()
+    print(f"ERRTAB C4 drift after 300 sweeps (recompute every 100): max |E_fused - E_fp64| = {d:.3g} "
+          f"({d / 1024:.2g} per spin at N = 1024, {d / 36864:.2g} at N = 36864)")
+    assert plan.status() == (0, 300)
+    assert 0.0 < d < 1e-5 * 1024
+
+
+def test_device_check_of_the_colour_classes(env):
+    """xyl_check_plan finds no fault in sound plans (fixed-degree graphs, the
+    paper's 2N-bond graphs, a mixed-size batch run as parts) and counts the
+    faults of a CSR corrupted in the workspace: a link inside a colour class."""
+    import torch
+    xyl, wl = env
+    for name in ("C2", "E1", "B64"):
+        cfg = wl.config(name)
+        plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED)
+        plan.bind()
+        assert plan.check() == 0, name
+    cfg = _c4_two_per_size(wl)
+    plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED)
+    plan.bind()
+    assert plan.check() == 0
+    # corrupt sample 0 of C2: the first id of row 0 becomes a site of row 0's own class
+    cfg = wl.config("C2")
+    graphs = wl.build_graphs(cfg)
+    plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs)
+    plan.bind()
+    _, row_ptr, col, cptr = graphs[0].csr()
+    ws = plan.workspace.cpu().numpy().view(np.int32).copy()
+    hits = np.flatnonzero(ws[: len(ws) - len(col)] == col[0])
+    at = next(k for k in hits if np.array_equal(ws[k:k + len(col)], col))
+    ws[at] = 1 if cptr[1] > 1 else 0  # site 1 shares site 0's colour class
+    plan.workspace.copy_(torch.from_numpy(ws.view(np.uint8)).to(plan.workspace.device))
+    assert plan.check() >= 2  # the link is inside a class and is missing from row 1
+
+
 def test_recompute_bounds_fp32_drift(env):
     xyl, wl = env
     cfg = wl.config("C2")
@@ -567,6 +617,46 @@ def test_any_degree_shapes_give_the_same_spins(env):
         assert p.status() == (0, 5)
 
 
+def _c4_two_per_size(wl):
+    """C4's six sizes (L = 32..192, rho = 3, 20 temperatures), two samples each."""
+    cfg = wl.config("C4")
+    idx = [k for k, g in enumerate(cfg.graphs) if g[2] < 2]
+    cfg.stream_ids = [wl.graph_stream_id(cfg, k) for k in idx]
+    cfg.graphs = [cfg.graphs[k] for k in idx]
+    return cfg
+
+
+def test_mixed_sizes_as_parts_give_the_same_spins(env):
+    """A mixed-size batch run as parts (each size its own launch shape, spins in
+    shared memory where a group fits, the parts without a cross-cluster barrier
+    side by side on forked streams) gives spins bit-identical to the whole
+    batch in one global-memory shape; with parallel tempering and measurement
+    it runs cleanly and every sample keeps a permutation of its slots."""
+    xyl, wl = env
+    cfg = _c4_two_per_size(wl)
+    graphs = wl.build_graphs(cfg)
+    parts, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs)
+    whole, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, resident=-1)
+    assert parts.part_count() == 6 and whole.part_count() == 1
+    assert [parts.part_tuning(k)["resident"] for k in range(6)][-3:] == [1, 1, 1]
+    for p in (parts, whole):
+        p.bind()
+        p.init_spins()
+        p.sweep(4, NO_PT)
+        p.sweep(3, NO_PT)
+    for k in range(cfg.n_samples):
+        for r in range(cfg.n_temps):
+            assert np.array_equal(parts.spins(k, r), whole.spins(k, r)), (k, r)
+    assert parts.status() == (0, 7)
+    parts.sweep(40, ALL, 4)
+    assert parts.status() == (0, 47)
+    labels = parts.labels().reshape(cfg.n_samples, cfg.n_temps)
+    assert all(sorted(row.tolist()) == list(range(cfg.n_temps)) for row in labels)
+    st = parts.read_observables()
+    assert np.all(st["acc"][:, ACC["n"]] == 7 + 10)  # every one of the first 7 sweeps measured, then every 4th
+    assert np.all(st["pt_try"].reshape(cfg.n_samples, cfg.n_temps)[:, :-1] > 0)
+
+
 def test_replica_pairs_same_spins_in_every_shape(env):
     """Four L=64 samples x 24 temperatures (replicas updated in pairs, RV = 2):
     the resident shape at 512 and 1024 threads, split over three CTAs, and the
@@ -627,18 +717,7 @@ def test_long_run_statistics_reduced_c3(env, orc):
         s.reset_acc()
     ob = bin_means(run_bins(sim, 60, 100, ALL))
     gb = bin_means(run_bins(plan, 60, 100, ALL))
-    N = 64 * 64
-    fns = {
-        "e": lambda m: m[ACC["e"]],
-        "chi": lambda m: N * (m[ACC["m2"]] - m[ACC["mx"]] ** 2 - m[ACC["my"]] ** 2),
-        "U4": lambda m: m[ACC["m4"]] / m[ACC["m2"]] ** 2 - 1,
-        "absm": lambda m: m[ACC["absm"]],
-    }
-    for k in range(4):
-        for key, fn in fns.items():
-            a, da = jackknife(ob[:, k, :], fn)
-            b, db = jackknife(gb[:, k, :], fn)
-            assert abs(a - b) < 3 * np.hypot(da, db), (k, key, a, da, b, db)
+    _compare_long_run("reduced C3", ob, gb, _observables(64 * 64), range(4))
 
 
 @pytest.mark.parametrize("engine_name", ENGINES)

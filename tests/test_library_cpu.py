@@ -231,10 +231,22 @@ def test_fields_are_validated(xyl):
 
 def test_o3_plans_are_validated(xyl):
     g = xyl.build_graph_csr(8, 6, 3.5, 1, 0)
-    for engine, kw in ((xyl.FP32_BATCHED, {"spin_dim": 3}), (xyl.FP32_PLAIN, {"spin_dim": 4})):
+    for engine, kw in ((xyl.FP32_BATCHED, {"spin_dim": 3, "resident": -1}), (xyl.FP32_PLAIN, {"spin_dim": 4})):
         with pytest.raises(xyl.XylError) as e:
             xyl.Plan([(g, 0, [1.0, 0.5], [1.0, 1.0])], engine=engine, device="cpu", **kw)
         assert e.value.code == xyl.EINVAL
+    # O(3) on the batched engine: the resident shape, one CTA per group of
+    # replicas, the largest group whose three component arrays fit
+    big = xyl.build_graph_csr(128, 6, 3.5, 1, 0)
+    t = xyl.Plan([(big, 0, [1.0] * 16, [1.0] * 16)], engine=xyl.FP32_BATCHED, device="cpu", spin_dim=3).tuning()
+    assert (t["resident"], t["group"], t["cluster"], t["spin_dim"]) == (1, 1, 1, 3)
+    mid = xyl.build_graph_csr(64, 6, 3.5, 1, 0)
+    t = xyl.Plan([(mid, 0, [1.0] * 24, [1.0] * 24)], engine=xyl.FP32_BATCHED, device="cpu", spin_dim=3).tuning()
+    assert (t["resident"], t["group"]) == (1, 4)
+    huge = xyl.build_graph_csr(192, 6, 3.5, 1, 0)  # 12 B x 36865 sites > 220 KB even for one replica
+    with pytest.raises(xyl.XylError) as e:
+        xyl.Plan([(huge, 0, [1.0] * 2, [1.0] * 2)], engine=xyl.FP32_BATCHED, device="cpu", spin_dim=3)
+    assert e.value.code == xyl.EINVAL
     q = xyl.Plan([(g, 0, [1.0, 0.5], [1.0, 1.0])], engine=xyl.FP32_PLAIN, device="cpu")
     p = xyl.Plan([(g, 0, [1.0, 0.5], [1.0, 1.0])], engine=xyl.FP32_PLAIN, device="cpu", spin_dim=3)
     # spins are padded 4-vectors: 16 B instead of 8 B per (site, replica)
@@ -296,7 +308,30 @@ def test_calls_before_bind_report_the_call_order(xyl):
         "xyl_export_state": lambda q: lib.xyl_export_state(q, buf, 64 * 8, None),
         "xyl_read_drift": lambda q: lib.xyl_read_drift(q, buf, 0, None),
         "xyl_tune_delta": lambda q: lib.xyl_tune_delta(q, 2, 10, 3, 0.5, buf, None),
+        "xyl_check_plan": lambda q: lib.xyl_check_plan(q, C.cast(buf, C.POINTER(C.c_int64)), None),
     }
     for name, call in calls.items():
         assert call(h) == xyl.ESTATE, name
         assert call(None) == xyl.EINVAL, name
+
+
+def test_mixed_sizes_run_as_parts(xyl):
+    """A batch of several sizes with the library choosing the shapes runs one
+    part per size, largest first: spins in shared memory where a replica group
+    fits (all groups of a sample in one cluster), else in global memory; a
+    caller-given shape keeps one part.  Units are numbered part by part."""
+    graphs = {L: xyl.build_graph_csr(L, 6, 3.0, 1, k) for k, L in enumerate((32, 64, 96, 128, 192))}
+    betas = [1.0 / t for t in np.geomspace(1.5, 3.5, 20)]
+    samples = [(graphs[L], k, betas, [1.0] * 20) for k, L in enumerate((64, 192, 32, 96, 128, 64))]
+    p = xyl.Plan(samples, engine=xyl.FP32_BATCHED, device="cpu")
+    assert p.part_count() == 5
+    parts = [p.part_tuning(k) for k in range(5)]
+    assert [t["samples"] for t in parts] == [1, 1, 1, 2, 1]          # N = 192^2, 128^2, 96^2, 64^2, 32^2
+    assert [t["resident"] for t in parts] == [-1, -1, 1, 1, 1]
+    assert [t["group"] for t in parts[2:]] == [2, 4, 4]               # largest group whose spins fit
+    assert p.tuning() == {**p.tuning(), **{k: v for k, v in parts[0].items() if k != "samples"}}
+    assert p.unit_count() == sum(20 // t["group"] for t in parts[:2]) * 1 + 10 + 2 * 5 + 5
+    q = xyl.Plan(samples, engine=xyl.FP32_BATCHED, device="cpu", resident=-1)
+    assert q.part_count() == 1 and q.part_tuning(0)["samples"] == 6
+    r = xyl.Plan(samples[:1] + samples[5:], engine=xyl.FP32_BATCHED, device="cpu")
+    assert r.part_count() == 1

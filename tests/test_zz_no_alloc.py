@@ -85,6 +85,34 @@ def test_noalloc_and_sweep_mix_on_one_plan(env, shape):
     _same_state(xyl, cfg, mix, ref)
 
 
+def test_noalloc_on_a_mixed_size_batch(env):
+    """A batch of several sizes runs as parts (one launch shape per size); the
+    allocation-free sweep runs its parts one after another instead of side by
+    side, with the same result."""
+    xyl, wl = env
+    cfg = wl.config("C4")
+    idx = [k for k, g in enumerate(cfg.graphs) if g[2] == 0]
+    cfg.stream_ids = [wl.graph_stream_id(cfg, k) for k in idx]
+    cfg.graphs = [cfg.graphs[k] for k in idx]
+    graphs = wl.build_graphs(cfg)
+    plans = [wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs)[0] for _ in range(2)]
+    for p in plans:
+        assert p.part_count() == 6
+        p.bind()
+        p.init_spins()
+    ref, new = plans
+    for _ in range(2):
+        ref.sweep(6, ALL)
+        new.sweep_noalloc(6, ALL)
+    assert new.status() == ref.status() == (0, 12)
+    sizes = np.repeat([L * L for L, _, _ in cfg.graphs], cfg.n_temps)
+    assert np.max(np.abs(new.energies() - ref.energies()) / sizes) < 1e-5
+    assert np.array_equal(new.labels(), ref.labels())
+    for k in range(cfg.n_samples):
+        for r in range(cfg.n_temps):
+            assert np.max(np.abs(new.spins(k, r) - ref.spins(k, r))) < 1e-5
+
+
 def test_noalloc_batch_limit(env):
     """256 B per slot + 4 B per sample within the 1 MiB array: 31 samples x 128
     slots fit (1015932 B), 32 x 128 do not (1048704 B)."""
