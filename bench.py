@@ -413,9 +413,15 @@ def roofline_for(plan, cfg, per_launch_updates, avg_launch_s, name, spins_live_b
         else:
             traffic = prof["bytes_per_launch"] * per_launch_updates / (cfg.spins_per_sweep() * 2) / \
                 prof["sweeps_per_launch"]
-    return {"bound": bound, "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak, "traffic": traffic,
-            "peak_kind": kind, "bytes_per_update": b, "kernel": kernel, "basis": basis,
-            "other_models_GBps": {k: v for k, v in achieved.items()}}
+    out = {"bound": bound, "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak, "traffic": traffic,
+           "peak_kind": kind, "bytes_per_update": b, "kernel": kernel, "basis": basis,
+           "other_models_GBps": {k: v for k, v in achieved.items()}}
+    if traffic is not None:
+        # the DRAM rate the measured traffic implies at this launch's duration
+        out["dram_GBps_from_traffic"] = traffic / avg_launch_s / 1e9
+        out["dram_frac_of_measured_hbm"] = out["dram_GBps_from_traffic"] / hbm_peak
+        out["dram_bytes_per_update"] = traffic / per_launch_updates
+    return out
 
 
 def spins_live_bytes(plan, cfg):
@@ -447,10 +453,6 @@ def measure_workload(args, name, xyl, wl, dev, stream, flush, rank, world, steps
     plan, _ = wl.make_plan(cfg, getattr(xyl, engine_name), graphs=graphs, **tune)
     plan.bind(stream)
     plan.init_spins(stream=stream)
-    # Metropolis half-widths: warm-up to about 50% acceptance, then frozen
-    rates = None
-    if not args.no_tune_delta:
-        rates = plan.tune_delta(rounds=args.tune_rounds, n_sweeps=args.tune_sweeps, ops=1 | 2 | 4, stream=stream)
     explicit = full and (args.block or args.cluster or args.group)
     autotune_s, shape_source = None, "library default"
     if explicit:
@@ -465,6 +467,10 @@ def measure_workload(args, name, xyl, wl, dev, stream, flush, rank, world, steps
             plan.autotune(n_try, OPS_ALL, args.measure_every, stream=stream)
             shape_source = "autotuned"
         autotune_s = time.perf_counter() - t0
+    # Metropolis half-widths: warm-up to about 50% acceptance in the chosen shape, then frozen
+    rates = None
+    if not args.no_tune_delta:
+        rates = plan.tune_delta(rounds=args.tune_rounds, n_sweeps=args.tune_sweeps, ops=1 | 2 | 4, stream=stream)
     updates_per_sweep = cfg.spins_per_sweep() * 2
 
     def timed_steps(p, n_steps, sweeps):
