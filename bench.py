@@ -1,11 +1,13 @@
 """Benchmark: site-updates/s of the FP32 batched sampler vs the FP64 plain kernel.
 
 One step = `sweeps_per_step` whole sweeps (Metropolis pass + overrelaxation pass
-over every colour class, parallel-tempering swap attempt and FP64 measurement
-after every sweep) of the workload's full batch.  Default workload: one Levy
-graph, L=128 (16384 sites), z=6, rho=3.5, 16 temperatures geometric in
-[0.8, 1.6], swap attempt every sweep.  A site-update is one Metropolis or one
-overrelaxation update of one spin of one replica.
+over every colour class, parallel-tempering swap attempt after every sweep, an
+FP64 measurement every `measure_every` sweeps) of the workload's full batch.
+Default workload C5: 128 Levy graphs, L=512 (262144 sites each), z=6, rho in
+{2.5, 4.5}, 32 temperatures geometric in [1.5, 3.5]; C2 (one graph, L=128, 16
+temperatures) and C3 (768 graphs, L=64, 24 temperatures) are measured in the
+same run.  A site-update is one Metropolis or one overrelaxation update of one
+spin of one replica.
 
 Prints ONE JSON line (rank 0).  `--impl reference` times the sequential CPU
 oracle on the same workload instead.
@@ -103,6 +105,7 @@ KERNEL_SOURCES = {
     "o3_phase_kernel": ["o3.cu", "o3_f32.cuh"],
     "resident_o3_kernel": ["resident_o3.cu", "o3_f32.cuh"],
     "walk_kernel": ["walk.cu"],
+    "plain_phase_kernel": ["plain.cu"],
 }
 SHARED_SOURCES = ["engines.h", "device.cuh", "philox.cuh", "sweep_tail.cuh"]
 
@@ -115,9 +118,10 @@ def kernel_source_digest(kernel):
     return h.hexdigest()
 
 
-def _profile_traffic(kernel, config):
-    """DRAM bytes per launch of `kernel` on `config` from the committed ncu
-    summary, valid only while the kernel's sources are unchanged since the capture."""
+def _profile_values(kernel, config):
+    """The machine-read lines ("- key: value") of the committed ncu summary of
+    `kernel` on `config`, or None once the kernel's sources have changed since
+    the capture."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{config}.md")
     if not os.path.exists(path) or kernel not in KERNEL_SOURCES:
         return None
@@ -127,6 +131,15 @@ def _profile_traffic(kernel, config):
             k, v = line[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("source_sha256") != kernel_source_digest(kernel):
+        return None
+    return vals
+
+
+def _profile_traffic(kernel, config):
+    """DRAM bytes per launch of `kernel` on `config` from the committed ncu
+    summary, valid only while the kernel's sources are unchanged since the capture."""
+    vals = _profile_values(kernel, config)
+    if vals is None:
         return None
     try:
         out = {"bytes_per_launch": float(vals["dram_bytes_per_launch"]),
@@ -424,6 +437,18 @@ def roofline_for(plan, cfg, per_launch_updates, avg_launch_s, name, spins_live_b
     return out
 
 
+def fp64_bound(name):
+    """What bounds the FP64 plain engine on this workload, from the committed
+    ncu summary of its phase kernel (while its sources are unchanged): the FP64
+    pipe's active fraction, time-weighted over the launches of one sweep."""
+    vals = _profile_values("plain_phase_kernel", name)
+    if vals is None or "fp64_pipe_active_pct" not in vals:
+        return {"fp64_pipe_active": None}
+    return {"fp64_pipe_active": float(vals["fp64_pipe_active_pct"]) / 100.0,
+            "bound": "FP64 pipe (ncu sm__pipe_fp64_cycles_active, time-weighted over one sweep)",
+            "profile": f"profiles/plain_phase_kernel_{name}.md"}
+
+
 def spins_live_bytes(plan, cfg):
     """Bytes of spins the units of one launch wave keep live (all of them when
     one wave runs the whole batch; the plain engines run it all at once)."""
@@ -558,7 +583,8 @@ def measure_workload(args, name, xyl, wl, dev, stream, flush, rank, world, steps
         "workload": f"{cfg.name}: {cfg.description}", "engine": engine_name, "cluster": plan_shape(plan),
         "samples": cfg.n_samples, "temperatures": cfg.n_temps,
         "fp64_plain": {"value": fp64, "unit": UNIT,
-                       "ratio_fp32_batched_over_fp64_plain": (value / world / fp64) if fp64 else None},
+                       "ratio_fp32_batched_over_fp64_plain": (value / world / fp64) if fp64 else None,
+                       **fp64_bound(name)},
         "roofline": roof, "e2e": e2e, "clocks": clock_info, "autotune_s": autotune_s, "shape_source": shape_source,
     }
     if rates is not None:

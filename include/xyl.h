@@ -54,6 +54,7 @@ extern "C" {
 #define XYL_ECUDA (-4)    /* a CUDA runtime call failed */
 #define XYL_ETIMEOUT (-5) /* a bounded device-side wait gave up */
 #define XYL_ESTATE (-6)   /* wrong call order (e.g. sweep before bind) */
+#define XYL_EBOUNDS (-7)  /* debug builds (XYL_DEBUG) only: a kernel met an id outside its array and skipped it */
 
 /* ---- sweep operations (bit mask) --------------------------------------- */
 #define XYL_OP_MET 1u     /* Metropolis pass over the colour classes (App. B) */
@@ -175,9 +176,21 @@ int xyl_graph_export_couplings(const xyl_graph *g, int8_t *j_csr);
  * site becomes sum_j J_ij S_j + h_i (the neighbours summed first) and the
  * energies include the field term.  Plans made afterwards use the fields; a
  * plan with fields keeps one FP32 (FP64 for XYL_FP64_PLAIN) vector per site in
- * its workspace.  Errors: XYL_EINVAL.
+ * its workspace.  These are XY fields: a plan with O(3) spins refuses them
+ * (XYL_EINVAL at xyl_plan_create).  Errors: XYL_EINVAL.
  */
 int xyl_graph_set_fields(xyl_graph *g, const double *hxy);
+
+/*
+ * xyl_graph_set_fields3 -- random fields for O(3) spins: hxyz holds 3n values,
+ * (h_x, h_y, h_z) of each ORIGINAL site id, finite (XYL_EINVAL otherwise), or
+ * NULL to remove the fields.  As xyl_graph_set_fields otherwise: H gains
+ * -sum_i h_i . S_i, the local field is sum_j J_ij S_j + h_i (the neighbours
+ * summed first), the energies include the field term; a plan keeps one padded
+ * 4-vector per site.  Only plans with spin_dim = 3 take them (XYL_EINVAL at
+ * xyl_plan_create otherwise).  Errors: XYL_EINVAL.
+ */
+int xyl_graph_set_fields3(xyl_graph *g, const double *hxyz);
 
 /* Sizes of a graph; any output pointer may be NULL.  restarts: pairing restarts used. */
 int xyl_graph_info(const xyl_graph *g, int32_t *n, int64_t *n_edges, int32_t *n_colors, int32_t *max_deg,
@@ -216,7 +229,7 @@ typedef struct {
     int32_t recompute_every; /* FP64 energy recompute + renormalise every this many sweeps (0 = never) */
     int32_t stage;           /* batched engine: 0 = stage CSR rows in shared memory when they fit, -1 = never */
     int32_t resident;        /* batched engine: 1 = resident shape, -1 = never, 0 = library's choice (below) */
-    int32_t spin_dim;        /* spin components: 0 or 2 = XY; 3 = O(3) (no fields; see below) */
+    int32_t spin_dim;        /* spin components: 0 or 2 = XY; 3 = O(3) (see below) */
     int32_t waves;           /* batched engine, global-memory shape: 1 = cap each launch wave to the samples whose
                                 spins and tables fit in L2, -1 = never, 0 = library's choice (never) */
 } xyl_tuning;
@@ -243,7 +256,8 @@ typedef struct {
  * group of replicas keeps three single-precision component arrays of every
  * site in shared memory (12 B a site and replica, within 220 KB), with the
  * plain engine's per-spin arithmetic, so both engines give bit-identical
- * spins from the same state.  Random fields are XY-only (XYL_EINVAL).
+ * spins from the same state.  Random fields on O(3) spins are 3-vectors
+ * (xyl_graph_set_fields3), on every engine.
  */
 
 /*
@@ -268,8 +282,8 @@ typedef struct {
  * slot r.  seed keys every spin/Metropolis/PT random stream.  tune may be NULL.
  * *workspace_bytes receives the device bytes xyl_bind needs.
  * Errors: XYL_EINVAL (empty batch, bad slot count, unknown engine, spin_dim
- * other than 0, 2 or 3, O(3) spins with fields or, on the batched engine,
- * outside the resident shape).
+ * other than 0, 2 or 3, fields whose component count differs from the spins'
+ * or, for O(3) spins on the batched engine, outside the resident shape).
  */
 int xyl_plan_create(const xyl_sample *samples, int32_t n_samples, int32_t engine, uint64_t seed,
                     const xyl_tuning *tune, xyl_plan **out, size_t *workspace_bytes);
@@ -494,7 +508,9 @@ int xyl_read_drift(xyl_plan *p, double *max_drift, int32_t reset, void *stream);
  */
 int xyl_check_plan(xyl_plan *p, int64_t *violations, void *stream);
 
-/* Status word (0 = fine, else an XYL_E* code recorded on the device) and the sweep index of sample 0. */
+/* Status word (0 = fine, else the first XYL_E* code recorded on the device: XYL_ETIMEOUT from a bounded
+ * wait; in a debug build, XYL_EBOUNDS from a neighbour id, row length or colour-class bound out of range,
+ * which the kernel skipped) and the sweep index of sample 0. */
 int xyl_read_status(xyl_plan *p, int32_t *status, uint64_t *sweep_index, void *stream);
 
 /* Bytes of a checkpoint: spins, labels, sweep counters, accumulators, counters. */

@@ -59,6 +59,7 @@ def _load():
                                        u64p]
         lib.orc_sim_set_couplings.argtypes = [P, f64p]
         lib.orc_sim_set_fields.argtypes = [P, f64p]
+        lib.orc_sim_set_fields3.argtypes = [P, f64p]
         lib.orc_sim_set_dim.argtypes = [P, C.c_int]
         lib.orc_reflect.argtypes = [C.c_int, f64p, f64p, f64p]
         lib.orc_reflect.restype = None
@@ -322,17 +323,21 @@ class Sim:
             raise MemoryError("oracle allocation failed")
 
     def set_fields(self, hxy=None):
-        """Random fields: (n, 2) field vectors per site (original ids); None
-        removes them.  Pinned by the exact single-spin law I1(b|h|)/I0(b|h|)
-        and quadrature over all angles on 2-3-spin graphs."""
+        """Random fields: (n, 2) field vectors per site for XY spins, (n, 3)
+        for O(3) spins (original ids); None removes them.  Pinned by the exact
+        single-spin laws (XY: I1(b|h|)/I0(b|h|); O(3): the Langevin function
+        coth(b|h|) - 1/(b|h|)) and by quadrature on 2-3-spin graphs."""
         if hxy is None:
             self._hkeep = None
             self._lib.orc_sim_set_fields(self._h, None)
             return
-        self._hkeep = np.ascontiguousarray(hxy, np.float64).reshape(-1)
-        rc = self._lib.orc_sim_set_fields(self._h, _ptr(self._hkeep, C.c_double))
+        h = np.ascontiguousarray(hxy, np.float64)
+        comps = h.shape[-1] if h.ndim == 2 else 2
+        self._hkeep = h.reshape(-1)
+        setter = self._lib.orc_sim_set_fields3 if comps == 3 else self._lib.orc_sim_set_fields
+        rc = setter(self._h, _ptr(self._hkeep, C.c_double))
         if rc == -2:
-            raise ValueError("random fields are two-component (XY only)")
+            raise ValueError("field vectors need as many components as the spins (2: XY, 3: O(3))")
         if rc:
             raise MemoryError("oracle allocation failed")
 

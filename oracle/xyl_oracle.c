@@ -880,6 +880,7 @@ typedef struct {
     double *jb;               /* coupling of each bond, or NULL (all J = 1) */
     double *jn;               /* coupling of each neighbour entry (aligned with nbr), or NULL */
     double *hx, *hy;          /* field on each site, or NULL */
+    double *hz;               /* third field component (O(3) fields), or NULL */
     int dim;                  /* spin components: 2 (XY) or 3 (O(3)) */
     double *vz;               /* third spin component [R][n] (zero for XY) */
     /* checking aids (none changes a decision unless a test sets it):          */
@@ -899,7 +900,7 @@ void orc_sim_free(orc_sim *s)
     free(s->cx); free(s->sx); free(s->cy); free(s->sy); free(s->beta); free(s->delta);
     free(s->vx); free(s->vy); free(s->slot_of); free(s->rep_at); free(s->E); free(s->acc);
     free(s->met_acc); free(s->met_try); free(s->pt_acc); free(s->pt_try); free(s->first_tie); free(s->n_ties);
-    free(s->jb); free(s->jn); free(s->hx); free(s->hy); free(s->vz);
+    free(s->jb); free(s->jn); free(s->hx); free(s->hy); free(s->hz); free(s->vz);
     free(s->tie_log); free(s->pt_log); free(s->forced); free(s->pt_forced); free(s->active);
     free(s);
 }
@@ -999,6 +1000,8 @@ static double energy_of(const orc_sim *s, int r)
             double d = x[i] * x[j] + y[i] * y[j] + z[i] * z[j];
             E -= s->jb ? s->jb[e] * d : d;
         }
+        if (s->hz)
+            for (int v = 0; v < s->n; ++v) E -= s->hx[v] * x[v] + s->hy[v] * y[v] + s->hz[v] * z[v];
         return E;
     }
     for (int64_t e = 0; e < s->n_bonds; ++e) {
@@ -1119,14 +1122,41 @@ static void local_field(const orc_sim *s, const double *x, const double *y, int 
  */
 int orc_sim_set_fields(orc_sim *s, const double *hxy)
 {
-    if (hxy && s->dim != 2) return -2;  /* fields are 2-vectors: XY only */
-    free(s->hx); free(s->hy);
-    s->hx = s->hy = NULL;
+    if (hxy && s->dim != 2) return -2;  /* 2-vectors: XY spins (orc_sim_set_fields3 for O(3)) */
+    free(s->hx); free(s->hy); free(s->hz);
+    s->hx = s->hy = s->hz = NULL;
     if (hxy) {
         s->hx = (double *)malloc(sizeof(double) * (size_t)s->n);
         s->hy = (double *)malloc(sizeof(double) * (size_t)s->n);
         if (!s->hx || !s->hy) return -1;
         for (int v = 0; v < s->n; ++v) { s->hx[v] = hxy[2 * v]; s->hy[v] = hxy[2 * v + 1]; }
+    }
+    refresh_energies(s);
+    return 0;
+}
+
+/*
+ * Random fields on O(3) spins: one 3-vector per site (original ids, hxyz[3i],
+ * hxyz[3i+1], hxyz[3i+2]); H gains -sum_i h_i . S_i as for XY, the local
+ * field becomes sum_j J_ij S_j + h_i (the field added after the neighbours)
+ * and the energy includes the field term.  Needs dim 3; NULL removes the
+ * fields.  Recomputes the energies.
+ */
+int orc_sim_set_fields3(orc_sim *s, const double *hxyz)
+{
+    if (hxyz && s->dim != 3) return -2;
+    free(s->hx); free(s->hy); free(s->hz);
+    s->hx = s->hy = s->hz = NULL;
+    if (hxyz) {
+        s->hx = (double *)malloc(sizeof(double) * (size_t)s->n);
+        s->hy = (double *)malloc(sizeof(double) * (size_t)s->n);
+        s->hz = (double *)malloc(sizeof(double) * (size_t)s->n);
+        if (!s->hx || !s->hy || !s->hz) return -1;
+        for (int v = 0; v < s->n; ++v) {
+            s->hx[v] = hxyz[3 * v];
+            s->hy[v] = hxyz[3 * v + 1];
+            s->hz[v] = hxyz[3 * v + 2];
+        }
     }
     refresh_energies(s);
     return 0;
@@ -1536,14 +1566,15 @@ int orc_sim_set_active(orc_sim *s, const uint8_t *mask)
 /*     24-bit draws: one block (i, t, MET<<24 | r) per replica: u24(w0) for   */
 /*     the cap, u24(w1) for phi, u24(w2) for the test.                        */
 /*   Overrelaxation: S' = 2 (S.h) h / |h|^2 - S (rotation by pi about h).     */
-/* Random fields are 2-vectors and stay XY-only.                              */
+/* Random fields: 3-vectors per site (orc_sim_set_fields3), added to the     */
+/* local field after the neighbours, -h.S in the energy, as for XY.          */
 /* ------------------------------------------------------------------------- */
 #define MET_SECOND_BLOCK 0x800000u
 
 int orc_sim_set_dim(orc_sim *s, int dim)
 {
     if (dim != 2 && dim != 3) return -1;
-    if (dim == 3 && s->hx) return -2;
+    if (s->hx && (s->hz != NULL) != (dim == 3)) return -2;  /* fields keep their component count */
     s->dim = dim;
     memset(s->vz, 0, sizeof(double) * (size_t)s->R * (size_t)s->n);
     refresh_energies(s);
@@ -1589,6 +1620,13 @@ static void local_field3(const orc_sim *s, int r, int v, double *hx, double *hy,
             ay += y[j];
             az += z[j];
         }
+    }
+    if (s->hz) {
+        /* the site's own field, added after the neighbours */
+        const double f[3] = { s->hx[v], s->hy[v], s->hz[v] };
+        ax += f[0];
+        ay += f[1];
+        az += f[2];
     }
     *hx = ax; *hy = ay; *hz = az;
 }

@@ -169,7 +169,7 @@ __device__ __forceinline__ void fetch_grow(const DevPlan &P, const DevSample &d,
         if (IS_MET) row.key = (uint32_t)__ldg(P.perm + d.site_off + i);
     } else {
         row.rb = __ldg(P.row_ptr + d.row_off + i);
-        row.deg = __ldg(P.row_ptr + d.row_off + i + 1) - row.rb;
+        row.deg = checked_id(P, __ldg(P.row_ptr + d.row_off + i + 1) - row.rb, bp.max_deg + 1, 0);
         if (IS_MET) row.key = (uint32_t)__ldg(P.perm + d.site_off + i);
     }
 }
@@ -208,7 +208,7 @@ __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, cons
         for (int v = 0; v < RV; ++v) hx[v] = hy[v] = lx[v] = ly[v] = 0.f;
         // with DISORDER, a neighbour id with its top bit set is a link with J = -1
         auto gather = [&](int raw) {
-            const int j = DISORDER ? (raw & 0x7fffffff) : raw;
+            const int j = checked_id(P, DISORDER ? (raw & 0x7fffffff) : raw, d.N, 0);
             float2 sj[RV];
             load_spins<RV>(sp + j * R, sj);
             if (DISORDER && raw < 0) {
@@ -468,7 +468,8 @@ __device__ __forceinline__ void batched_body(const DevPlan &P, const BatchedPara
         // this CTA's chunk of every colour class
         int base = 0;
         for (int c = 0; c < d.Q; ++c) {
-            const int cb = P.color_ptr[d.color_off + c], ce = P.color_ptr[d.color_off + c + 1];
+            int cb = P.color_ptr[d.color_off + c], ce = P.color_ptr[d.color_off + c + 1];
+            checked_class(P, cb, ce, d.N);
             const int chunk = (ce - cb + bp.G - 1) / bp.G;
             const int lo = min(ce, cb + rank * chunk), hi = min(ce, lo + chunk);
             sh.cls_cb[c] = cb;
@@ -490,10 +491,11 @@ __device__ __forceinline__ void batched_body(const DevPlan &P, const BatchedPara
             const int lo = sh.cls_lo[c], n = sh.cls_hi[c] - lo, base = sh.cls_base[c];
             for (int q = threadIdx.x; q < n; q += blockDim.x) {
                 const int i = lo + q, l = base + q;
-                const int rb = P.row_ptr[d.row_off + i], re = P.row_ptr[d.row_off + i + 1];
-                deg[l] = re - rb;
+                const int rb = P.row_ptr[d.row_off + i];
+                const int n_k = checked_id(P, P.row_ptr[d.row_off + i + 1] - rb, bp.max_deg + 1, 0);
+                deg[l] = n_k;
                 site[l] = P.perm[d.site_off + i];
-                for (int k = 0; k < re - rb; ++k) col[(size_t)l * bp.max_deg + k] = P.col[d.col_off + rb + k];
+                for (int k = 0; k < n_k; ++k) col[(size_t)l * bp.max_deg + k] = P.col[d.col_off + rb + k];
             }
         }
         stg = Staged{col, deg, site};

@@ -192,11 +192,12 @@ __global__ void recompute_kernel(DevPlan P, int layout, int fp64, int renormalis
             ph = make_double4_32a(p.x, p.y, p.z, p.w);
         }
         double lx = 0.0, ly = 0.0;
-        const int rb = P.row_ptr[d.row_off + i], re = P.row_ptr[d.row_off + i + 1];
+        const int rb = P.row_ptr[d.row_off + i];
+        const int re = rb + checked_id(P, P.row_ptr[d.row_off + i + 1] - rb, d.max_deg + 1, 0);
         for (int k = rb; k < re; ++k) {
             // a neighbour id with its top bit set is a link with J = -1 (random bonds)
             const int raw = P.col[d.col_off + k];
-            const int j = raw & 0x7fffffff;
+            const int j = checked_id(P, raw & 0x7fffffff, d.N, 0);
             if (j >= i) continue;
             double vx, vy;
             if (fp64) {

@@ -73,6 +73,40 @@ struct DevPlan {
     double cos_coef[kCosTerms];
 };
 
+// Debug builds (compiled with XYL_DEBUG): every neighbour id a kernel is about
+// to follow is checked against its array before the access.  A bad id sets the
+// status word to XYL_EBOUNDS (the first error code recorded stays) and is
+// replaced by `safe`, so that the access stays inside the array; the run goes
+// on and the caller reads the status.  Release builds compile the check out.
+__device__ __forceinline__ int checked_id(const DevPlan &P, int j, int limit, int safe)
+{
+#ifdef XYL_DEBUG
+    if ((unsigned)j >= (unsigned)limit) {
+        atomicCAS(P.status, 0, XYL_EBOUNDS);
+        return safe;
+    }
+#endif
+    return j;
+}
+
+// Whether sweep t (its index before the increment at its end) ends with a
+// measurement: every measure_every-th sweep (0: never).
+__device__ __forceinline__ bool measurement_sweep(uint32_t t, int measure_every)
+{
+    return measure_every > 0 && ((t + 1u) % (uint32_t)measure_every) == 0u;
+}
+
+// The colour class [cb, ce) of a sample, checked in debug builds to lie in [0, n].
+__device__ __forceinline__ void checked_class(const DevPlan &P, int &cb, int &ce, int n)
+{
+#ifdef XYL_DEBUG
+    if (cb < 0 || cb > ce || ce > n) {
+        atomicCAS(P.status, 0, XYL_EBOUNDS);
+        cb = ce = 0;
+    }
+#endif
+}
+
 // sin and cos of |x| <= pi by their Maclaurin series (Horner in x^2 with IEEE
 // fused multiply-add; truncation below 3e-17).  Every rounding step is fixed,
 // so the FP64 engine's trajectory does not depend on a math library.

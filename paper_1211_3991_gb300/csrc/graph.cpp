@@ -563,19 +563,27 @@ int xyl_graph_set_couplings(xyl_graph *g, const int8_t *j)
     return XYL_OK;
 }
 
-int xyl_graph_set_fields(xyl_graph *g, const double *hxy)
+static int set_fields(xyl_graph *g, const double *h, int dim, const char *who)
 {
     clear_error();
-    if (!g) return fail(XYL_EINVAL, "xyl_graph_set_fields: NULL graph");
-    if (!hxy) {
+    if (!g) return fail(XYL_EINVAL, "%s: NULL graph", who);
+    if (!h) {
         g->field.clear();
+        g->field_dim = 0;
         return XYL_OK;
     }
-    for (int64_t k = 0; k < 2 * (int64_t)g->n; ++k)
-        if (!std::isfinite(hxy[k])) return fail(XYL_EINVAL, "xyl_graph_set_fields: component %lld is not finite",
-                                                (long long)k);
-    g->field.assign(hxy, hxy + 2 * (size_t)g->n);
+    for (int64_t k = 0; k < dim * (int64_t)g->n; ++k)
+        if (!std::isfinite(h[k])) return fail(XYL_EINVAL, "%s: component %lld is not finite", who, (long long)k);
+    g->field.assign(h, h + dim * (size_t)g->n);
+    g->field_dim = dim;
     return XYL_OK;
+}
+
+int xyl_graph_set_fields(xyl_graph *g, const double *hxy) { return set_fields(g, hxy, 2, "xyl_graph_set_fields"); }
+
+int xyl_graph_set_fields3(xyl_graph *g, const double *hxyz)
+{
+    return set_fields(g, hxyz, 3, "xyl_graph_set_fields3");
 }
 
 int xyl_graph_export_couplings(const xyl_graph *g, int8_t *j_csr)

@@ -35,5 +35,6 @@ struct xyl_graph {
     std::vector<int32_t> color;       // colour of each original id
     std::vector<int8_t> jlink;        // coupling of each link (creation order), empty = all +1
     std::vector<int8_t> jcsr;         // coupling of each CSR entry (aligned with col), empty = all +1
-    std::vector<double> field;        // 2n field components per original id, empty = no field
+    std::vector<double> field;        // field_dim x n field components per original id, empty = no field
+    int32_t field_dim = 0;            // 2: XY fields (xyl_graph_set_fields), 3: O(3) fields (xyl_graph_set_fields3)
 };

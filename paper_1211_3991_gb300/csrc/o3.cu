@@ -94,14 +94,15 @@ __global__ void o3_init_kernel(DevPlan P, int fp64, int aligned)
 // spins; FUSE, DISORDER and the per-block reduction as in the XY plain kernel,
 // with the z component's magnetisation and Fourier sums added.
 template <typename Real, bool IS_MET, bool FUSE, bool DISORDER>
-__global__ void __launch_bounds__(kO3Block) o3_phase_kernel(DevPlan P, int c)
+__global__ void __launch_bounds__(kO3Block) o3_phase_kernel(DevPlan P, int c, int meas_every)
 {
     using V = Vec3<Real>;
     using V4 = Vec4<Real>;
     const int s = blockIdx.z, r = blockIdx.y;
     const DevSample d = P.samples[s];
     if (r >= d.R || c >= d.Q) return;
-    const int cb = P.color_ptr[d.color_off + c], ce = P.color_ptr[d.color_off + c + 1];
+    int cb = P.color_ptr[d.color_off + c], ce = P.color_ptr[d.color_off + c + 1];
+    checked_class(P, cb, ce, d.N);
     const int base = cb + (int)blockIdx.x * kO3Block;
     if (base >= ce) return;
     const int i = base + (int)threadIdx.x;
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(kO3Block) o3_phase_kernel(DevPlan P, int c)
     if (active) {
         const V si = sp[i];
         Real hx = 0, hy = 0, hz = 0;
-        const int rb = rp[i], re = rp[i + 1];
+        const int rb = rp[i], re = rb + checked_id(P, rp[i + 1] - rp[i], d.max_deg + 1, 0);
         // neighbours in groups of kGather: every id of a group, then every spin,
         // are in flight together; the sums still run in row order
         for (int k0 = rb; k0 < re; k0 += kGather) {
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(kO3Block) o3_phase_kernel(DevPlan P, int c)
             for (int q = 0; q < kGather; ++q) raw[q] = k0 + q < re ? cl[k0 + q] : 0;
 #pragma unroll
             for (int q = 0; q < kGather; ++q)
-                if (k0 + q < re) sv[q] = sp[DISORDER ? (raw[q] & 0x7fffffff) : raw[q]];
+                if (k0 + q < re) sv[q] = sp[checked_id(P, DISORDER ? (raw[q] & 0x7fffffff) : raw[q], d.N, 0)];
 #pragma unroll
             for (int q = 0; q < kGather; ++q) {
                 if (k0 + q >= re) break;
@@ -145,6 +146,18 @@ __global__ void __launch_bounds__(kO3Block) o3_phase_kernel(DevPlan P, int c)
                     ly += sj.y;
                     lz += sj.z;
                 }
+            }
+        }
+        if (DISORDER && P.field) {
+            // the site's own field after its neighbours; the fused energy takes -h_i . S_i once
+            const V4 f = reinterpret_cast<const V4 *>(P.field)[d.site_off + i];
+            hx += f.x;
+            hy += f.y;
+            hz += f.z;
+            if (FUSE) {
+                lx += f.x;
+                ly += f.y;
+                lz += f.z;
             }
         }
         if (IS_MET) {
@@ -197,27 +210,32 @@ __global__ void __launch_bounds__(kO3Block) o3_phase_kernel(DevPlan P, int c)
     }
     if (FUSE) {
         __shared__ double part[kO3Block / 32][kObsCount3];
-        V4 ph = {0, 0, 0, 0};
-        if (active) ph = reinterpret_cast<const V4 *>(P.phase)[d.site_off + i];
+        const bool full = measurement_sweep(P.sweep[s], meas_every);
+        const int nf = full ? kObsCount3 : 1;
         Real v[kObsCount3];
         v[kObsE] = active ? -(nx * lx + ny * ly + nz * lz) : (Real)0;
-        v[kObsMx] = nx;
-        v[kObsMy] = ny;
-        v[kObsMz] = nz;
-        v[kObsF1xRe] = nx * ph.x; v[kObsF1xIm] = nx * ph.y;
-        v[kObsF1yRe] = ny * ph.x; v[kObsF1yIm] = ny * ph.y;
-        v[kObsF1zRe] = nz * ph.x; v[kObsF1zIm] = nz * ph.y;
-        v[kObsF2xRe] = nx * ph.z; v[kObsF2xIm] = nx * ph.w;
-        v[kObsF2yRe] = ny * ph.z; v[kObsF2yIm] = ny * ph.w;
-        v[kObsF2zRe] = nz * ph.z; v[kObsF2zIm] = nz * ph.w;
+        if (full) {
+            V4 ph = {0, 0, 0, 0};
+            if (active) ph = reinterpret_cast<const V4 *>(P.phase)[d.site_off + i];
+            v[kObsMx] = nx;
+            v[kObsMy] = ny;
+            v[kObsMz] = nz;
+            v[kObsF1xRe] = nx * ph.x; v[kObsF1xIm] = nx * ph.y;
+            v[kObsF1yRe] = ny * ph.x; v[kObsF1yIm] = ny * ph.y;
+            v[kObsF1zRe] = nz * ph.x; v[kObsF1zIm] = nz * ph.y;
+            v[kObsF2xRe] = nx * ph.z; v[kObsF2xIm] = nx * ph.w;
+            v[kObsF2yRe] = ny * ph.z; v[kObsF2yIm] = ny * ph.w;
+            v[kObsF2zRe] = nz * ph.z; v[kObsF2zIm] = nz * ph.w;
+        }
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
         for (int f = 0; f < kObsCount3; ++f) {
+            if (f >= nf) break;
             const Real w = warp_sum(v[f]);
             if (lane == 0) part[warp][f] = (double)w;
         }
         __syncthreads();
-        if (threadIdx.x < kObsCount3) {
+        if ((int)threadIdx.x < nf) {
             double total = 0.0;
 #pragma unroll
             for (int w = 0; w < kO3Block / 32; ++w) total += part[w][threadIdx.x];
@@ -288,16 +306,27 @@ __global__ void o3_recompute_kernel(DevPlan P, int fp64, int renormalise, int bu
             ph.x = p.x; ph.y = p.y; ph.z = p.z; ph.w = p.w;
         }
         double lx = 0.0, ly = 0.0, lz = 0.0;
-        const int rb = P.row_ptr[d.row_off + i], re = P.row_ptr[d.row_off + i + 1];
+        const int rb = P.row_ptr[d.row_off + i];
+        const int re = rb + checked_id(P, P.row_ptr[d.row_off + i + 1] - rb, d.max_deg + 1, 0);
         for (int k = rb; k < re; ++k) {
             // a neighbour id with its top bit set is a link with J = -1
             const int raw = P.col[d.col_off + k];
-            const int j = raw & 0x7fffffff;
+            const int j = checked_id(P, raw & 0x7fffffff, d.N, 0);
             if (j >= i) continue;
             double vx, vy, vz;
             load(j, vx, vy, vz);
             if (raw < 0) { vx = -vx; vy = -vy; vz = -vz; }
             lx += vx; ly += vy; lz += vz;
+        }
+        if (P.field) {
+            // random fields: -h_i . S_i once per site
+            if (fp64) {
+                const double4_32a f = reinterpret_cast<const double4_32a *>(P.field)[d.site_off + i];
+                lx += f.x; ly += f.y; lz += f.z;
+            } else {
+                const float4 f = reinterpret_cast<const float4 *>(P.field)[d.site_off + i];
+                lx += f.x; ly += f.y; lz += f.z;
+            }
         }
         acc[kObsE] -= sx * lx + sy * ly + sz * lz;
         acc[kObsMx] += sx;
@@ -335,19 +364,20 @@ cudaError_t o3_sweep_impl(const DevPlan &P, const PlanShape &S, uint32_t ops, in
         return dim3((unsigned)std::max(1, (sites + kO3Block - 1) / kO3Block), S.max_R, S.n_samples);
     };
     const bool met = ops & XYL_OP_MET, orx = ops & XYL_OP_OR;
+    const int me = (ops & XYL_OP_MEASURE) ? measure_every : 0;
     int64_t n = 0;
     if (met) {
         for (int c = 0; c < S.max_Q; ++c) {
             if (orx)
-                o3_phase_kernel<Real, true, false, DISORDER><<<grid(c), kO3Block, 0, st>>>(P, c);
+                o3_phase_kernel<Real, true, false, DISORDER><<<grid(c), kO3Block, 0, st>>>(P, c, me);
             else
-                o3_phase_kernel<Real, true, true, DISORDER><<<grid(c), kO3Block, 0, st>>>(P, c);
+                o3_phase_kernel<Real, true, true, DISORDER><<<grid(c), kO3Block, 0, st>>>(P, c, me);
             ++n;
         }
     }
     if (orx) {
         for (int c = 0; c < S.max_Q; ++c) {
-            o3_phase_kernel<Real, false, true, DISORDER><<<grid(c), kO3Block, 0, st>>>(P, c);
+            o3_phase_kernel<Real, false, true, DISORDER><<<grid(c), kO3Block, 0, st>>>(P, c, me);
             ++n;
         }
     }

@@ -23,19 +23,22 @@ template <> __device__ __forceinline__ double2 make_vec2<double>(double x, doubl
 
 // One colour phase of the Metropolis (IS_MET) or overrelaxation pass.  With
 // FUSE the replica's energy (links to lower colours, counted at their upper
-// endpoint), magnetisation and Fourier sums are reduced into obs[0].  With
+// endpoint) is reduced into obs[0] on every sweep, and its magnetisation and
+// Fourier sums on the sweeps that end with a measurement (every meas_every-th;
+// meas_every = 0: none).  With
 // DISORDER a neighbour id with its top bit set is a link with J = -1 (the
 // neighbour's spin enters the local field negated, exactly J * S_j), and a
 // site field, when the plan has one, is added after the neighbours.
 template <typename Real, bool IS_MET, bool FUSE, bool DISORDER>
-__global__ void __launch_bounds__(kPlainBlock) plain_phase_kernel(DevPlan P, int c)
+__global__ void __launch_bounds__(kPlainBlock) plain_phase_kernel(DevPlan P, int c, int meas_every)
 {
     using V = Vec2<Real>;
     using V4 = Vec4<Real>;
     const int s = blockIdx.z, r = blockIdx.y;
     const DevSample d = P.samples[s];
     if (r >= d.R || c >= d.Q) return;
-    const int cb = P.color_ptr[d.color_off + c], ce = P.color_ptr[d.color_off + c + 1];
+    int cb = P.color_ptr[d.color_off + c], ce = P.color_ptr[d.color_off + c + 1];
+    checked_class(P, cb, ce, d.N);
     const int base = cb + (int)blockIdx.x * kPlainBlock;
     if (base >= ce) return;
     const int i = base + (int)threadIdx.x;
@@ -50,7 +53,7 @@ __global__ void __launch_bounds__(kPlainBlock) plain_phase_kernel(DevPlan P, int
     if (active) {
         const V si = sp[i];
         Real hx = 0, hy = 0;
-        const int rb = rp[i], re = rp[i + 1];
+        const int rb = rp[i], re = rb + checked_id(P, rp[i + 1] - rp[i], d.max_deg + 1, 0);
         // neighbours in groups of kGather: every id of a group, then every spin,
         // are in flight together; the sums still run in row order
         for (int k0 = rb; k0 < re; k0 += kGather) {
@@ -60,7 +63,7 @@ __global__ void __launch_bounds__(kPlainBlock) plain_phase_kernel(DevPlan P, int
             for (int q = 0; q < kGather; ++q) raw[q] = k0 + q < re ? cl[k0 + q] : 0;
 #pragma unroll
             for (int q = 0; q < kGather; ++q)
-                if (k0 + q < re) sv[q] = sp[DISORDER ? (raw[q] & 0x7fffffff) : raw[q]];
+                if (k0 + q < re) sv[q] = sp[checked_id(P, DISORDER ? (raw[q] & 0x7fffffff) : raw[q], d.N, 0)];
 #pragma unroll
             for (int q = 0; q < kGather; ++q) {
                 if (k0 + q >= re) break;
@@ -118,24 +121,29 @@ __global__ void __launch_bounds__(kPlainBlock) plain_phase_kernel(DevPlan P, int
     }
     if (FUSE) {
         __shared__ double part[kPlainBlock / 32][kObsCount];
-        V4 ph = {0, 0, 0, 0};
-        if (active) ph = reinterpret_cast<const V4 *>(P.phase)[d.site_off + i];
+        const bool full = measurement_sweep(P.sweep[s], meas_every);
+        const int nf = full ? kObsCount : 1;
         Real v[kObsCount];
         v[kObsE] = active ? -(nx * lx + ny * ly) : (Real)0;
-        v[kObsMx] = nx;
-        v[kObsMy] = ny;
-        v[kObsF1xRe] = nx * ph.x; v[kObsF1xIm] = nx * ph.y;
-        v[kObsF1yRe] = ny * ph.x; v[kObsF1yIm] = ny * ph.y;
-        v[kObsF2xRe] = nx * ph.z; v[kObsF2xIm] = nx * ph.w;
-        v[kObsF2yRe] = ny * ph.z; v[kObsF2yIm] = ny * ph.w;
+        if (full) {
+            V4 ph = {0, 0, 0, 0};
+            if (active) ph = reinterpret_cast<const V4 *>(P.phase)[d.site_off + i];
+            v[kObsMx] = nx;
+            v[kObsMy] = ny;
+            v[kObsF1xRe] = nx * ph.x; v[kObsF1xIm] = nx * ph.y;
+            v[kObsF1yRe] = ny * ph.x; v[kObsF1yIm] = ny * ph.y;
+            v[kObsF2xRe] = nx * ph.z; v[kObsF2xIm] = nx * ph.w;
+            v[kObsF2yRe] = ny * ph.z; v[kObsF2yIm] = ny * ph.w;
+        }
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
         for (int f = 0; f < kObsCount; ++f) {
+            if (f >= nf) break;
             const Real w = warp_sum(v[f]);
             if (lane == 0) part[warp][f] = (double)w;
         }
         __syncthreads();
-        if (threadIdx.x < kObsCount) {
+        if ((int)threadIdx.x < nf) {
             double total = 0.0;
 #pragma unroll
             for (int w = 0; w < kPlainBlock / 32; ++w) total += part[w][threadIdx.x];
@@ -154,19 +162,20 @@ cudaError_t sweep_impl(const DevPlan &P, const PlanShape &S, uint32_t ops, int m
         return dim3((unsigned)std::max(1, (sites + kPlainBlock - 1) / kPlainBlock), S.max_R, S.n_samples);
     };
     const bool met = ops & XYL_OP_MET, orx = ops & XYL_OP_OR;
+    const int me = (ops & XYL_OP_MEASURE) ? measure_every : 0;
     int64_t n = 0;
     if (met) {
         for (int c = 0; c < S.max_Q; ++c) {
             if (orx)
-                plain_phase_kernel<Real, true, false, DISORDER><<<grid(c), kPlainBlock, 0, st>>>(P, c);
+                plain_phase_kernel<Real, true, false, DISORDER><<<grid(c), kPlainBlock, 0, st>>>(P, c, me);
             else
-                plain_phase_kernel<Real, true, true, DISORDER><<<grid(c), kPlainBlock, 0, st>>>(P, c);
+                plain_phase_kernel<Real, true, true, DISORDER><<<grid(c), kPlainBlock, 0, st>>>(P, c, me);
             ++n;
         }
     }
     if (orx) {
         for (int c = 0; c < S.max_Q; ++c) {
-            plain_phase_kernel<Real, false, true, DISORDER><<<grid(c), kPlainBlock, 0, st>>>(P, c);
+            plain_phase_kernel<Real, false, true, DISORDER><<<grid(c), kPlainBlock, 0, st>>>(P, c, me);
             ++n;
         }
     }

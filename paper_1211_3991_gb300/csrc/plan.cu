@@ -9,8 +9,20 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "engines.h"
 #include "internal.h"
+
+// A named NVTX range over one library call: profilers that read NVTX (ncu
+// --nvtx) see each call's launches under its name; without a tool attached
+// the push and pop cost next to nothing.
+struct CallRange {
+    explicit CallRange(const char *name) { nvtxRangePushA(name); }
+    ~CallRange() { nvtxRangePop(); }
+    CallRange(const CallRange &) = delete;
+    CallRange &operator=(const CallRange &) = delete;
+};
 
 using namespace xyl;
 
@@ -22,7 +34,8 @@ struct HostSample {
     std::vector<double> beta, delta;
     std::vector<int32_t> perm, row_ptr, col, color_ptr, xy;
     std::vector<int8_t> jcsr;  // couplings of the CSR entries, empty = all +1
-    std::vector<double> field; // 2N field components per original id, empty = no field
+    std::vector<double> field; // field_dim x N field components per original id, empty = no field
+    int32_t field_dim = 0;
 };
 
 struct Region {
@@ -150,7 +163,10 @@ void layout(xyl_plan *p)
     take(p->r_units, std::max<size_t>(p->total_R, 1) * sizeof(int2));  // the most units any shape makes
     take(p->r_push, p->total_N * sizeof(uint16_t));
     // random fields: one vector per site, only when some sample has them
-    take(p->r_field, p->shape.fields ? p->total_N * (p->shape.fp64 ? sizeof(double2) : sizeof(float2)) : 0);
+    // (O(3): padded 4-vectors, like the spins)
+    const size_t field_elem = p->shape.dim == 3 ? (p->shape.fp64 ? sizeof(double4_32a) : sizeof(float4))
+                                                : (p->shape.fp64 ? sizeof(double2) : sizeof(float2));
+    take(p->r_field, p->shape.fields ? p->total_N * field_elem : 0);
     p->ws_bytes = off;
 }
 
@@ -664,6 +680,12 @@ int xyl_plan_create(const xyl_sample *samples, int32_t n_samples, int32_t engine
         h.jcsr = g->jcsr;
         for (int8_t j : h.jcsr) p->shape.coupled |= (j < 0);
         h.field = g->field;
+        h.field_dim = g->field_dim;
+        if (!h.field.empty() && h.field_dim != dim) {
+            delete p;
+            return fail(XYL_EINVAL, "xyl_plan_create: sample %d has %d-component fields for %d-component spins "
+                        "(xyl_graph_set_fields for XY, xyl_graph_set_fields3 for O(3))", s, h.field_dim, dim);
+        }
         p->shape.fields |= !h.field.empty();
         p->total_R += h.R;
         p->total_N += h.N;
@@ -682,10 +704,6 @@ int xyl_plan_create(const xyl_sample *samples, int32_t n_samples, int32_t engine
     }
     p->shape.n_samples = n_samples;
     p->shape.disorder = p->shape.coupled || p->shape.fields;
-    if (dim == 3 && p->shape.fields) {
-        delete p;
-        return fail(XYL_EINVAL, "xyl_plan_create: random fields are two-component (XY only)");
-    }
     if (engine == XYL_FP32_BATCHED) {
         const int rc = pick_batched_shape(p, tune);
         if (rc) { delete p; return rc; }
@@ -698,6 +716,7 @@ int xyl_plan_create(const xyl_sample *samples, int32_t n_samples, int32_t engine
 
 int xyl_bind(xyl_plan *p, void *d_workspace, size_t bytes, void *stream)
 {
+    CallRange range_("xyl_bind");
     clear_error();
     if (!p || !d_workspace) return fail(XYL_EINVAL, "xyl_bind: NULL plan or workspace");
     if (bytes < p->ws_bytes) return fail(XYL_ENOSPC, "xyl_bind: workspace %zu B < required %zu B", bytes, p->ws_bytes);
@@ -761,13 +780,16 @@ int xyl_bind(xyl_plan *p, void *d_workspace, size_t bytes, void *stream)
         // field of each site in colour-sorted order (zero for samples without fields)
         std::vector<double> f64;
         std::vector<float> f32;
+        // (O(3): (h_x, h_y, h_z, 0) per site)
+        const int dim = p->shape.dim, slots = dim == 3 ? 4 : 2;
         for (const HostSample &h : p->hs)
             for (int i = 0; i < h.N; ++i) {
                 const int v = h.perm[i];
-                const double fx = h.field.empty() ? 0.0 : h.field[2 * (size_t)v];
-                const double fy = h.field.empty() ? 0.0 : h.field[2 * (size_t)v + 1];
-                if (p->shape.fp64) { f64.push_back(fx); f64.push_back(fy); }
-                else { f32.push_back((float)fx); f32.push_back((float)fy); }
+                for (int a = 0; a < slots; ++a) {
+                    const double f = (h.field.empty() || a >= dim) ? 0.0 : h.field[dim * (size_t)v + a];
+                    if (p->shape.fp64) f64.push_back(f);
+                    else f32.push_back((float)f);
+                }
             }
         if (p->shape.fp64) XYL_CUDA(up(p->r_field, f64.data(), f64.size() * 8), "xyl_bind: upload");
         else XYL_CUDA(up(p->r_field, f32.data(), f32.size() * 4), "xyl_bind: upload");
@@ -961,6 +983,7 @@ extern "C" {
 
 int xyl_init_spins(xyl_plan *p, int32_t aligned, void *stream)
 {
+    CallRange range_("xyl_init_spins");
     clear_error();
     int rc = check_bound(p, "xyl_init_spins");
     if (rc) return rc;
@@ -978,6 +1001,7 @@ int xyl_init_spins(xyl_plan *p, int32_t aligned, void *stream)
 
 int xyl_sweep(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_every, void *stream)
 {
+    CallRange range_("xyl_sweep");
     clear_error();
     int rc = check_bound(p, "xyl_sweep");
     if (rc) return rc;
@@ -1010,6 +1034,7 @@ int xyl_sweep(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_every
 int xyl_sweep_units(xyl_plan *p, int32_t first_unit, int32_t n_units, int32_t n_sweeps, uint32_t ops,
                     int32_t measure_every, void *stream)
 {
+    CallRange range_("xyl_sweep_units");
     clear_error();
     int rc = check_bound(p, "xyl_sweep_units");
     if (rc) return rc;
@@ -1110,6 +1135,7 @@ int32_t xyl_part_count(const xyl_plan *p)
 
 int xyl_pt_swap(xyl_plan *p, void *stream)
 {
+    CallRange range_("xyl_pt_swap");
     clear_error();
     int rc = check_bound(p, "xyl_pt_swap");
     if (rc) return rc;
@@ -1122,6 +1148,7 @@ int xyl_pt_swap(xyl_plan *p, void *stream)
 
 int xyl_measure(xyl_plan *p, void *stream)
 {
+    CallRange range_("xyl_measure");
     clear_error();
     int rc = check_bound(p, "xyl_measure");
     if (rc) return rc;
@@ -1133,6 +1160,7 @@ int xyl_measure(xyl_plan *p, void *stream)
 
 int xyl_recompute(xyl_plan *p, void *stream)
 {
+    CallRange range_("xyl_recompute");
     clear_error();
     int rc = check_bound(p, "xyl_recompute");
     if (rc) return rc;
@@ -1173,6 +1201,7 @@ int xyl_get_delta(const xyl_plan *p, int32_t sample, double *delta)
 int xyl_tune_delta(xyl_plan *p, int32_t rounds, int32_t n_sweeps, uint32_t ops, double target, double *rate,
                    void *stream)
 {
+    CallRange range_("xyl_tune_delta");
     clear_error();
     int rc = check_bound(p, "xyl_tune_delta");
     if (rc) return rc;
@@ -1354,6 +1383,7 @@ int xyl_write_spins(xyl_plan *p, int32_t sample, int32_t replica, const double *
 
 int xyl_check_plan(xyl_plan *p, int64_t *violations, void *stream)
 {
+    CallRange range_("xyl_check_plan");
     clear_error();
     int rc = check_bound(p, "xyl_check_plan");
     if (rc) return rc;
@@ -1520,6 +1550,7 @@ int xyl_get_tuning(const xyl_plan *p, xyl_tuning *out)
 int xyl_autotune(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_every, xyl_tuning *best,
                  void *stream)
 {
+    CallRange range_("xyl_autotune");
     clear_error();
     int rc = check_bound(p, "xyl_autotune");
     if (rc) return rc;

@@ -107,7 +107,7 @@ __device__ __forceinline__ void fetch_row(const DevPlan &P, const DevSample &d, 
     row.neg = 0u;
     if constexpr (DEG == 0) {
         row.rb = __ldg(P.row_ptr + d.row_off + i);
-        row.deg = __ldg(P.row_ptr + d.row_off + i + 1) - row.rb;
+        row.deg = checked_id(P, __ldg(P.row_ptr + d.row_off + i + 1) - row.rb, d.max_deg + 1, 0);
     } else if (stg.col) {
         // rows of W 16-bit ids, 4-byte aligned (W even)
         const uint32_t *c = reinterpret_cast<const uint32_t *>(stg.col + (size_t)l * W);
@@ -247,7 +247,7 @@ __device__ __forceinline__ void rphase(const DevPlan &P, const DevSample &d, con
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     if (k0 + q >= cur.deg) break;
-                    const int j = DISORDER ? (raw[q] & 0x7fffffff) : raw[q];
+                    const int j = checked_id(P, DISORDER ? (raw[q] & 0x7fffffff) : raw[q], d.N + 1, d.N);
                     float2 sj[RV];
                     lds_spins<RV>(spl + j * Rg, sj);
                     if (DISORDER && raw[q] < 0) {
@@ -269,7 +269,7 @@ __device__ __forceinline__ void rphase(const DevPlan &P, const DevSample &d, con
         } else {
 #pragma unroll
             for (int k = 0; k < W; ++k) {
-                const int j = cur.nb[k];
+                const int j = checked_id(P, cur.nb[k], d.N + 1, d.N);  // N: the zero row
                 float2 sj[RV];
                 lds_spins<RV>(spl + j * Rg, sj);
                 if (DISORDER && ((cur.neg >> k) & 1u)) {
@@ -534,7 +534,8 @@ __device__ __forceinline__ void resident_body(const DevPlan &P, const ResidentPa
         // this CTA's chunk of every colour class
         int base = 0;
         for (int c = 0; c < d.Q; ++c) {
-            const int cb = P.color_ptr[d.color_off + c], ce = P.color_ptr[d.color_off + c + 1];
+            int cb = P.color_ptr[d.color_off + c], ce = P.color_ptr[d.color_off + c + 1];
+            checked_class(P, cb, ce, d.N);
             const int chunk = (ce - cb + rp.G - 1) / rp.G;
             const int lo = min(ce, cb + pl.sr * chunk), hi = min(ce, lo + chunk);
             sh.cls_cb[c] = cb;

@@ -78,7 +78,7 @@ __device__ __forceinline__ void o3_fetch_row(const DevPlan &P, const DevSample &
     row.neg = 0u;
     if constexpr (DEG == 0) {
         row.rb = __ldg(P.row_ptr + d.row_off + i);
-        row.deg = __ldg(P.row_ptr + d.row_off + i + 1) - row.rb;
+        row.deg = checked_id(P, __ldg(P.row_ptr + d.row_off + i + 1) - row.rb, d.max_deg + 1, 0);
     } else if (col) {
         const uint32_t *c = reinterpret_cast<const uint32_t *>(col + (size_t)i * W);
 #pragma unroll
@@ -139,7 +139,8 @@ __device__ __forceinline__ void o3_phase(const DevPlan &P, const DevSample &d, c
         if (qn < items) o3_fetch_row<DEG, IS_MET, DISORDER>(P, d, op, col, ids, cb + (qn >> op.log2rg), nxt);
         const float x = sx[i * Rg], y = sy[i * Rg], z = sz[i * Rg];
         float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
-        auto add = [&](int j, bool neg) {
+        auto add = [&](int j_raw, bool neg) {
+            const int j = checked_id(P, j_raw, d.N + 1, d.N);  // N: the zero row
             float vx = sx[j * Rg], vy = sy[j * Rg], vz = sz[j * Rg];
             if (DISORDER && neg) {
                 vx = -vx;
@@ -164,6 +165,18 @@ __device__ __forceinline__ void o3_phase(const DevPlan &P, const DevSample &d, c
         } else {
 #pragma unroll
             for (int k = 0; k < W; ++k) add(cur.nb[k], DISORDER && ((cur.neg >> k) & 1u));
+        }
+        if (DISORDER && P.field) {
+            // the site's own field after its neighbours; the fused energy takes -h_i . S_i once
+            const float4 f = __ldg(reinterpret_cast<const float4 *>(P.field) + d.site_off + i);
+            hx = __fadd_rn(hx, f.x);
+            hy = __fadd_rn(hy, f.y);
+            hz = __fadd_rn(hz, f.z);
+            if (FUSE_E) {
+                lx += f.x;
+                ly += f.y;
+                lz += f.z;
+            }
         }
         float nx, ny, nz;
         if (IS_MET) {
@@ -232,7 +245,8 @@ __device__ __forceinline__ void o3_body(const DevPlan &P, const O3Params &op)
         sh.delta[k] = (float)P.delta[d.rep_off + k];
         beta64[k] = P.beta[d.rep_off + k];
     }
-    for (int c = threadIdx.x; c <= d.Q; c += blockDim.x) sh.cls_cb[c] = P.color_ptr[d.color_off + c];
+    for (int c = threadIdx.x; c <= d.Q; c += blockDim.x)
+        sh.cls_cb[c] = checked_id(P, P.color_ptr[d.color_off + c], d.N + 1, 0);
     if (threadIdx.x == 0) sh.abort_flag = 0;
     // spins of the group (replica-major float4 in global memory), then the zero row
     float *xs = reinterpret_cast<float *>(dyn);

@@ -28,6 +28,8 @@ with J = +-1 at random (probability 1/2 each, the XY spin glass):
   O1  C1's graph with O(3) spins, 4 temperatures geometric in [0.9, 1.8]
   O2  C2's graph with O(3) spins, 16 temperatures geometric in [0.9, 1.8]
   O2G O2 with random +-1 couplings, 16 temperatures geometric in [0.4, 1.2]
+  OH1 O1's graph with random +-1 couplings and random 3-vector fields of magnitude 0.5, 4 temperatures in [0.4, 1.2]
+  OH2 O2G with random 3-vector fields of magnitude 0.5
   O3  256 graphs L=64 (rho=3.5) with O(3) spins, 24 temperatures geometric in [0.9, 1.8]
 """
 from __future__ import annotations
@@ -132,6 +134,13 @@ def config(name: str) -> Config:
     if name == "O2G":
         return Config("O2G", [(128, 3.5, 0)], geometric_temperatures(0.4, 1.2, 16), spin_dim=3, couplings="pm",
                       description="C2's graph with O(3) spins and random +-1 couplings, 16 T geometric in [0.4,1.2]")
+    if name == "OH1":
+        return Config("OH1", [(16, 3.5, 0)], geometric_temperatures(0.4, 1.2, 4), spin_dim=3, couplings="pm",
+                      field=0.5, description="O1's graph with random +-1 couplings and random 3-vector fields of "
+                      "magnitude 0.5, 4 T geometric in [0.4,1.2]")
+    if name == "OH2":
+        return Config("OH2", [(128, 3.5, 0)], geometric_temperatures(0.4, 1.2, 16), spin_dim=3, couplings="pm",
+                      field=0.5, description="O2G with random 3-vector fields of magnitude 0.5, 16 T")
     if name == "B64":
         return Config("B64", [(64, 10.0 / 3.0, s) for s in range(64)], geometric_temperatures(1.4, 2.0, 12),
                       ensemble="bonds", description="64 graphs L=64 2N bonds rho=10/3 periodic, 12 T geometric in [1.4,2.0]")
@@ -211,12 +220,18 @@ def couplings_for(cfg: Config, k: int, n_edges: int):
 
 
 def fields_for(cfg: Config, k: int, n: int):
-    """Random fields of sample k ((n, 2) vectors of magnitude cfg.field in
-    uniformly random directions), or None.  Seeded by the sample's stream id."""
+    """Random fields of sample k, or None: (n, 2) vectors of magnitude
+    cfg.field in uniformly random directions for XY spins, (n, 3) vectors
+    uniform on the sphere of that radius for O(3) spins.  Seeded by the
+    sample's stream id."""
     if cfg.field == 0.0:
         return None
     import numpy as np
-    phi = np.random.default_rng([COUPLING_SEED + 1, graph_stream_id(cfg, k)]).random(n) * 2.0 * np.pi
+    rng = np.random.default_rng([COUPLING_SEED + 1, graph_stream_id(cfg, k)])
+    if cfg.spin_dim == 3:
+        v = rng.normal(size=(n, 3))
+        return cfg.field * v / np.linalg.norm(v, axis=1, keepdims=True)
+    phi = rng.random(n) * 2.0 * np.pi
     return cfg.field * np.stack([np.cos(phi), np.sin(phi)], 1)
 
 

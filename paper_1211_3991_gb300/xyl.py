@@ -14,9 +14,11 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libxyl.so")
+# XYL_DEBUG=1 in the environment selects the debug build (kernels check every
+# neighbour id before following it; see build.build(debug=True))
+LIB_PATH = os.path.join(_HERE, "libxyl_debug.so" if os.environ.get("XYL_DEBUG") == "1" else "libxyl.so")
 
-OK, EINVAL, ENOSPC, EGRAPH, ECUDA, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOSPC, EGRAPH, ECUDA, ETIMEOUT, ESTATE, EBOUNDS = 0, -1, -2, -3, -4, -5, -6, -7
 OP_MET, OP_OR, OP_PT, OP_MEASURE = 1, 2, 4, 8
 FP64_PLAIN, FP32_BATCHED, FP32_PLAIN = 0, 1, 2
 ACC_FIELDS = ("n", "e", "e2", "absm", "mx", "my", "m2", "m4", "chik", "mz")
@@ -29,7 +31,7 @@ EXPORTED = (
     "xyl_write_spins", "xyl_read_status", "xyl_state_bytes", "xyl_export_state", "xyl_import_state",
     "xyl_last_launch_count", "xyl_plan_free", "xyl_sweep_units", "xyl_unit_count", "xyl_autotune",
     "xyl_get_tuning", "xyl_sweep_noalloc", "xyl_build_levy_bonds", "xyl_walk_returns", "xyl_graph_set_couplings",
-    "xyl_graph_export_couplings", "xyl_graph_set_fields", "xyl_philox", "xyl_read_drift",
+    "xyl_graph_export_couplings", "xyl_graph_set_fields", "xyl_graph_set_fields3", "xyl_philox", "xyl_read_drift",
     "xyl_get_delta", "xyl_tune_delta", "xyl_wave_units", "xyl_part_count", "xyl_get_part_tuning",
     "xyl_set_part_tuning", "xyl_check_plan",
 )
@@ -107,6 +109,7 @@ def load():
             "xyl_graph_set_couplings": ([P, C.POINTER(C.c_int8)], C.c_int),
             "xyl_graph_export_couplings": ([P, C.POINTER(C.c_int8)], C.c_int),
             "xyl_graph_set_fields": ([P, pf64], C.c_int),
+            "xyl_graph_set_fields3": ([P, pf64], C.c_int),
             "xyl_philox": ([P, P, i64, P, P], C.c_int),
             "xyl_read_drift": ([P, pf64, i32, P], C.c_int),
             "xyl_get_delta": ([P, i32, pf64], C.c_int),
@@ -197,14 +200,17 @@ class Graph:
         return self
 
     def set_fields(self, hxy=None):
-        """Random fields: (n, 2) field vectors per original site id; None removes them."""
+        """Random fields per original site id: (n, 2) vectors for XY spins
+        (xyl_graph_set_fields), (n, 3) for O(3) spins (xyl_graph_set_fields3);
+        None removes them."""
         if hxy is None:
             _check(load().xyl_graph_set_fields(self.handle, None))
             return self
-        h = np.ascontiguousarray(hxy, np.float64).reshape(-1)
-        if len(h) != 2 * self.n:
-            raise ValueError("one field vector per site")
-        _check(load().xyl_graph_set_fields(self.handle, _p(h, C.c_double)))
+        h = np.ascontiguousarray(hxy, np.float64)
+        if h.ndim != 2 or h.shape[0] != self.n or h.shape[1] not in (2, 3):
+            raise ValueError("one field vector (2 or 3 components) per site")
+        fn = load().xyl_graph_set_fields3 if h.shape[1] == 3 else load().xyl_graph_set_fields
+        _check(fn(self.handle, _p(h.reshape(-1), C.c_double)))
         return self
 
     def couplings(self):

@@ -8,8 +8,9 @@ against the oracle.
 * FP32: every sweep starts the oracle (24-bit draws) from the GPU's spins and
   labels; energies per spin within 1e-5 and directions within 1e-4 rad, every
   miss traced to near-tie decisions that, forced the other way, reproduce it.
-* Gauge invariance: couplings tau_i tau_j J_ij with spins tau_i S_i give the
-  negated run bit for bit on both plain engines.
+* Gauge invariance: couplings tau_i tau_j J_ij (and fields tau_i h_i) with
+  spins tau_i S_i give the negated run bit for bit on every engine.
+* Random 3-vector fields (OH1, OH2): the same FP64, FP32 and shape checks.
 * A random tree measured by the FP32 engine against the exact tree energy
   -(n-1) L(beta) / n, L the Langevin function.
 """
@@ -45,6 +46,9 @@ def _oracle(orc, wl, cfg, k, u24):
     J = wl.couplings_for(cfg, k, len(ei))
     if J is not None:
         sim.set_couplings(J.astype(np.float64))
+    h = wl.fields_for(cfg, k, L * L)
+    if h is not None:
+        sim.set_fields(h)
     sim.init()
     return sim
 
@@ -53,7 +57,7 @@ def _gpu_vectors(plan, sample, R):
     return np.stack([plan.spins(sample, r) for r in range(R)])
 
 
-@pytest.mark.parametrize("name", ["O1", "O2", "O2G"])
+@pytest.mark.parametrize("name", ["O1", "O2", "O2G", "OH1", "OH2"])
 def test_fp64_trajectory_matches_oracle(env, orc, name):
     xyl, wl = env
     cfg = wl.config(name)
@@ -84,7 +88,7 @@ FP32_O3 = {"FP32_PLAIN": ("FP32_PLAIN", {}), "FP32_RESIDENT": ("FP32_BATCHED", {
 
 
 @pytest.mark.parametrize("engine_name", ["FP32_PLAIN", "FP32_RESIDENT"])
-@pytest.mark.parametrize("name", ["O1", "O2", "O2G"])
+@pytest.mark.parametrize("name", ["O1", "O2", "O2G", "OH1", "OH2"])
 def test_fp32_energy_matches_oracle(env, orc, name, engine_name):
     xyl, wl = env
     cfg = wl.config(name)
@@ -102,7 +106,7 @@ def test_fp32_energy_matches_oracle(env, orc, name, engine_name):
     assert plan.status() == (0, 10)
 
 
-@pytest.mark.parametrize("name", ["O2", "O2G", "O3"])
+@pytest.mark.parametrize("name", ["O2", "O2G", "OH2", "O3"])
 def test_resident_shape_gives_the_plain_engines_spins(env, name):
     """The resident O(3) shape performs the plain FP32 engine's per-spin
     arithmetic (same Philox block per replica, neighbour sums in row order,
@@ -133,9 +137,12 @@ def test_resident_shape_gives_the_plain_engines_spins(env, name):
 
 
 @pytest.mark.parametrize("engine_name", ["FP32_PLAIN", "FP64_PLAIN", "FP32_RESIDENT"])
-def test_gauge_invariance_is_exact(env, engine_name):
+@pytest.mark.parametrize("name", ["O2G", "OH2"])
+def test_gauge_invariance_is_exact(env, engine_name, name):
+    """tau_i S_i with couplings tau_i tau_j J_ij and fields tau_i h_i is the same
+    physics: the run follows the original one sign for sign, bit for bit."""
     xyl, wl = env
-    cfg = wl.config("O2G")
+    cfg = wl.config(name)
     eng_name, opts = FP32_O3.get(engine_name, (engine_name, {}))
     eng = getattr(xyl, eng_name)
     g = wl.build_graphs(cfg)[0]
@@ -144,6 +151,9 @@ def test_gauge_invariance_is_exact(env, engine_name):
     tau = np.random.default_rng(8).choice(np.array([-1, 1], np.int8), g.n)
     gauged = xyl.build_graph_csr(128, 6, 3.5, wl.GRAPH_SEED, wl.graph_stream_id(cfg, 0))
     gauged.set_couplings((tau[ei] * tau[ej] * J).astype(np.int8))
+    h = wl.fields_for(cfg, 0, g.n)
+    if h is not None:
+        gauged.set_fields(h * tau[:, None])
     a, _ = wl.make_plan(cfg, eng, graphs=[g], **opts)
     b, _ = wl.make_plan(cfg, eng, graphs=[gauged], **opts)
     for p in (a, b):

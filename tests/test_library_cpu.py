@@ -251,9 +251,26 @@ def test_o3_plans_are_validated(xyl):
     p = xyl.Plan([(g, 0, [1.0, 0.5], [1.0, 1.0])], engine=xyl.FP32_PLAIN, device="cpu", spin_dim=3)
     # spins are padded 4-vectors: 16 B instead of 8 B per (site, replica)
     assert p.workspace_bytes == q.workspace_bytes + 2 * 64 * 8
+    # fields keep the spins' component count: XY fields refuse O(3) spins and the reverse
     g.set_fields(np.ones((64, 2)))
     with pytest.raises(xyl.XylError) as e:
         xyl.Plan([(g, 0, [1.0, 0.5], [1.0, 1.0])], engine=xyl.FP64_PLAIN, device="cpu", spin_dim=3)
+    assert e.value.code == xyl.EINVAL
+    g.set_fields(np.ones((64, 3)))
+    with pytest.raises(xyl.XylError) as e:
+        xyl.Plan([(g, 0, [1.0, 0.5], [1.0, 1.0])], engine=xyl.FP64_PLAIN, device="cpu")
+    assert e.value.code == xyl.EINVAL
+    # O(3) fields: one padded 4-vector per site (16 B FP32, 32 B FP64), every engine
+    for engine, kw, b in ((xyl.FP32_PLAIN, {}, 16), (xyl.FP64_PLAIN, {}, 32), (xyl.FP32_BATCHED, {"resident": 1}, 16)):
+        with_f = xyl.Plan([(g, 0, [1.0, 0.5], [1.0, 1.0])], engine=engine, device="cpu", spin_dim=3, **kw)
+        g.set_fields(None)
+        no_f = xyl.Plan([(g, 0, [1.0, 0.5], [1.0, 1.0])], engine=engine, device="cpu", spin_dim=3, **kw)
+        g.set_fields(np.ones((64, 3)))
+        assert with_f.workspace_bytes == no_f.workspace_bytes + 64 * b - 256
+    h = np.ones((64, 3))
+    h[7, 2] = np.inf
+    with pytest.raises(xyl.XylError) as e:
+        g.set_fields(h)
     assert e.value.code == xyl.EINVAL
 
 

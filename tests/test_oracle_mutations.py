@@ -66,6 +66,11 @@ MUTATIONS = [
      "tests/test_oracle_o3.py::test_cap_proposal_is_uniform_on_the_cap"),
     ("O(3) z dropped from the energy", "double d = x[i] * x[j] + y[i] * y[j] + z[i] * z[j];",
      "double d = x[i] * x[j] + y[i] * y[j];", "tests/test_oracle_o3.py::test_tree_moments_are_exact"),
+    ("O(3) field z dropped from the local field", "        az += f[2];\n", "",
+     "tests/test_oracle_o3.py::test_free_spins_in_fields_follow_the_langevin_law"),
+    ("O(3) field term dropped from the energy",
+     "E -= s->hx[v] * x[v] + s->hy[v] * y[v] + s->hz[v] * z[v];", "E -= 0.0;",
+     "tests/test_oracle_o3.py::test_bond_with_fields_against_quadrature"),
 ]
 
 

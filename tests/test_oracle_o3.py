@@ -19,6 +19,10 @@ oracle's own formulas:
 * beta = 0: <m^2> = 1/N and <m^4> = (N^2 + 2N(N-1)/3) / N^4 for independent
   uniform unit 3-vectors (the XY value would be 2N(N-1)/2 in the second term).
 * Overrelaxation alone conserves the energy; gauge invariance is exact.
+* Random fields (3-vectors): a spin without links follows the Langevin law
+  <S> = L(beta|h|) h/|h|; a bond with fields against quadrature over one spin
+  with the other integrated out exactly (itself checked by brute-force
+  sampling); overrelaxation still conserves the energy.
 """
 import numpy as np
 import pytest
@@ -227,9 +231,108 @@ def test_gauge_invariance_is_exact(orc):
         np.testing.assert_array_equal(a.labels(), b.labels())
 
 
-def test_fields_stay_two_component(orc):
+def test_fields_keep_the_spins_component_count(orc):
     sim = orc.graph_sim([0], [1], 2, [1.0], [1.0], 1, dim=3)
     with pytest.raises(ValueError):
         sim.set_fields(np.ones((2, 2)))
+    xy = orc.graph_sim([0], [1], 2, [1.0], [1.0], 1)
+    with pytest.raises(ValueError):
+        xy.set_fields(np.ones((2, 3)))
     with pytest.raises(ValueError):
         orc.graph_sim([0], [1], 2, [1.0], [1.0], 1, dim=4)
+
+
+def _unit(v):
+    v = np.asarray(v, np.float64)
+    return v / np.linalg.norm(v, axis=-1, keepdims=True)
+
+
+def test_free_spins_in_fields_follow_the_langevin_law(orc):
+    """A spin with no links in a field h: <S> = L(beta|h|) h/|h| and its energy
+    -|h| L(beta|h|), L(x) = coth x - 1/x (one-spin partition function
+    4 pi sinh(beta|h|) / (beta|h|)); field directions with all three components."""
+    n, beta = 6, 1.3
+    mags = np.array([0.2, 0.5, 1.0, 1.5, 2.5, 4.0])
+    dirs = _unit(np.random.default_rng(4).normal(size=(n, 3)))
+    h = mags[:, None] * dirs
+    sim = orc.graph_sim(np.zeros(0, np.int32), np.zeros(0, np.int32), n, [beta], [np.pi], 5, dim=3)
+    sim.set_fields(h)
+    sim.init()
+    sim.sweeps(200, NO_PT)
+    sim.reset_acc()
+    bins = bin_means(run_bins(sim, 100, 400, NO_PT))
+    Lh = _langevin(beta * mags)
+    want = {"e": -(mags * Lh).sum() / n}
+    for a, key in enumerate(("mx", "my", "mz")):
+        want[key] = (Lh * dirs[:, a]).sum() / n
+    for key, w in want.items():
+        got, err = jackknife(bins[:, 0, :], lambda m: m[ACC[key]])
+        assert abs(got - w) < 4.5 * err + 1e-9, (key, got, w, err)
+
+
+def _bond_with_fields(J, h1, h2, beta, M=64):
+    """<e>, <e^2>, <m_x>, <m_z> of two O(3) spins, H = -J S1.S2 - h1.S1 - h2.S2.
+    S2 is integrated out exactly: given S1 it has density ~ exp(beta a.S2),
+    a = J S1 + h2, so <a.S2> = |a| L(beta|a|) and <(a.S2)^2> = |a|^2 y2(beta|a|);
+    S1 runs over a Gauss-Legendre (cos theta) x periodic (phi) grid."""
+    x, wx = np.polynomial.legendre.leggauss(M)
+    phi = 2 * np.pi * np.arange(2 * M) / (2 * M)
+    ct, ph = np.meshgrid(x, phi, indexing="ij")
+    st = np.sqrt(1 - ct ** 2)
+    S1 = np.stack([st * np.cos(ph), st * np.sin(ph), ct], -1)
+    wq = wx[:, None] * np.ones_like(ph)
+    b = S1 @ np.asarray(h1)
+    a = J * S1 + np.asarray(h2)
+    A = np.linalg.norm(a, axis=-1)
+    # log of exp(beta b) sinh(beta A) / (beta A), kept finite
+    logw = beta * b + beta * A + np.log1p(-np.exp(-2 * beta * A)) - np.log(2 * beta * A)
+    w = wq * np.exp(logw - logw.max())
+    LA, y2 = _langevin(beta * A), _second(beta * A)
+    E = -(b + A * LA)
+    E2 = b ** 2 + 2 * b * A * LA + A ** 2 * y2
+    S2 = LA[..., None] * a / A[..., None]
+    m = 0.5 * (S1 + S2)
+    Z = w.sum()
+    return {"e": (w * E).sum() / Z / 2, "e2": (w * E2).sum() / Z / 4, "mx": (w * m[..., 0]).sum() / Z,
+            "mz": (w * m[..., 2]).sum() / Z}
+
+
+def test_bond_integration_against_brute_force_sampling():
+    """The bond quadrature itself against plain importance sampling."""
+    rng = np.random.default_rng(1)
+    J, h1, h2, beta = -1.0, [0.3, -0.8, 0.5], [0.9, 0.2, -0.4], 1.1
+    v = _unit(rng.normal(size=(1000000, 2, 3)))
+    E = -(J * (v[:, 0] * v[:, 1]).sum(1) + v[:, 0] @ np.array(h1) + v[:, 1] @ np.array(h2))
+    w = np.exp(-beta * E)
+    q = _bond_with_fields(J, h1, h2, beta)
+    assert abs((w * E).sum() / w.sum() / 2 - q["e"]) < 0.003
+    assert abs((w * E * E).sum() / w.sum() / 4 - q["e2"]) < 0.006
+    assert abs((w * (v[:, 0, 2] + v[:, 1, 2]) / 2).sum() / w.sum() - q["mz"]) < 0.003
+
+
+@pytest.mark.parametrize("J", [1.0, -1.0])
+def test_bond_with_fields_against_quadrature(orc, J):
+    h1, h2, beta = [0.3, -0.8, 0.5], [0.9, 0.2, -0.4], 1.1
+    sim = orc.graph_sim([0], [1], 2, [beta], [2.5], 8, dim=3)
+    sim.set_couplings([J])
+    sim.set_fields(np.array([h1, h2]))
+    sim.init()
+    sim.sweeps(100, NO_PT)
+    sim.reset_acc()
+    bins = bin_means(run_bins(sim, 100, 400, NO_PT))
+    q = _bond_with_fields(J, h1, h2, beta)
+    for key in ("e", "e2", "mx", "mz"):
+        got, err = jackknife(bins[:, 0, :], lambda m: m[ACC[key]])
+        assert abs(got - q[key]) < 4.5 * err + 1e-9, (key, got, q[key], err)
+
+
+def test_overrelaxation_with_fields_conserves_energy(orc):
+    L = 16
+    ei, ej, _, _ = orc.levy_graph(L, 6, 3.5, 1, 0)
+    sim = orc.graph_sim(ei, ej, L * L, [0.7, 1.3], [1.0, 1.0], 6, dim=3)
+    sim.set_fields(0.5 * _unit(np.random.default_rng(3).normal(size=(L * L, 3))))
+    sim.init()
+    sim.sweeps(5, 1)
+    E0 = sim.energies().copy()
+    sim.sweeps(20, 2)
+    np.testing.assert_allclose(sim.energies(), E0, rtol=1e-12)
