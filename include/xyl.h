@@ -225,7 +225,8 @@ typedef struct {
     int32_t block;           /* threads per CTA of the batched engine, <= 1024 (0 = 512); above 672 the
                                 global-memory shape reads its CSR rows from global memory */
     int32_t cluster;         /* CTAs per cluster of the batched engine (0 = tuned default) */
-    int32_t group;           /* replicas per cluster, a power of two dividing every n_temps (0 = default) */
+    int32_t group;           /* replicas per cluster, dividing every n_temps, <= 32: a power of two, or
+                                even in the global-memory shape (0 = default) */
     int32_t recompute_every; /* FP64 energy recompute + renormalise every this many sweeps (0 = never) */
     int32_t stage;           /* batched engine: 0 = stage CSR rows in shared memory when they fit, -1 = never */
     int32_t resident;        /* batched engine: 1 = resident shape, -1 = never, 0 = library's choice (below) */

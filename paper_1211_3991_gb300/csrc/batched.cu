@@ -2,11 +2,15 @@
 // cycles for a batch of samples.
 //
 // Work decomposition.  The replicas of a sample are split into groups of Rg
-// (a power of two).  Each (sample, group) unit is owned by one thread-block
-// cluster of G CTAs.  Inside a unit, every colour class is cut into G
-// contiguous chunks; CTA k updates chunk k for all Rg replicas, one thread per
-// (site, replica) with the replica index fastest, so the lanes that share a
-// site read one contiguous Rg x 8-byte segment of each neighbour's row.
+// (any divisor of the sample's replica count up to 32).  Each (sample, group)
+// unit is owned by one thread-block cluster of G CTAs.  Inside a unit, every
+// colour class is cut into G contiguous chunks; CTA k updates chunk k for all
+// Rg replicas.  A thread updates RV replicas (2 when Rg is even, else 1) of
+// one site per item; the lps = Rg / RV lanes of a site are consecutive
+// threads, so they read one contiguous Rg x 8-byte segment of each
+// neighbour's row.  Thread t serves lane t % lps of sites t / lps, t / lps +
+// spr, ... (spr = block / lps sites per round; with lps not a power of two the
+// last block % lps threads idle).
 // Spins are interleaved [sample][site][replica] float2 in global memory and
 // stay L2-resident for the batch sizes this engine serves; they are read and
 // written through L2 (ld/st .cg), and colour phases are separated by cluster
@@ -42,7 +46,11 @@ struct BatchedParams {
     int unit_begin;
     int G, Rg;
     int rv;              // replicas one thread updates (1 or 2)
-    int log2lps;         // log2 of the lanes that share a site (Rg / rv)
+    int lps;             // lanes that share a site (Rg / rv)
+    int log2lps;         // log2(lps) when lps is a power of two
+    int spr;             // sites per round: block / lps
+    int act;             // threads with a lane: spr * lps
+    int pow2;            // lps is a power of two: a site's lanes tile every warp (warp-shuffle sums)
     int n_sweeps;
     uint32_t ops;
     int measure_every;
@@ -89,6 +97,45 @@ struct Staged {
 };
 
 // What one thread needs about its replicas during a sweep.
+// This thread's first site within a chunk (a large value: no lane); it is
+// recomputed where needed rather than kept live through the sweep.
+__device__ __forceinline__ int first_site(const BatchedParams &bp)
+{
+    if ((int)threadIdx.x >= bp.act) return 0x3fffffff;
+    return bp.pow2 ? (int)threadIdx.x >> bp.log2lps : (int)threadIdx.x / bp.lps;
+}
+
+// A thread's items of one colour chunk of n sites.  NP2 = false (lps a power
+// of two): item q = site offset x lps + lane, q = thread, thread + block, ...;
+// NP2 = true: site offsets first_site, first_site + spr, ...
+template <bool NP2>
+struct ItemIter;
+
+template <>
+struct ItemIter<false> {
+    int q, items;
+    __device__ __forceinline__ ItemIter(const BatchedParams &bp, int n)
+        : q((int)threadIdx.x), items(n > 0 ? n << bp.log2lps : 0) {}
+    __device__ __forceinline__ bool ok() const { return q < items; }
+    __device__ __forceinline__ int off(const BatchedParams &bp) const { return q >> bp.log2lps; }
+    __device__ __forceinline__ bool first() const { return q == (int)threadIdx.x; }
+    __device__ __forceinline__ bool next_ok() const { return q + (int)blockDim.x < items; }
+    __device__ __forceinline__ int next_off(const BatchedParams &bp) const { return (q + (int)blockDim.x) >> bp.log2lps; }
+    __device__ __forceinline__ void step(const BatchedParams &) { q += (int)blockDim.x; }
+};
+
+template <>
+struct ItemIter<true> {
+    int o, n, spr;
+    __device__ __forceinline__ ItemIter(const BatchedParams &bp, int n_) : o(first_site(bp)), n(n_), spr(bp.spr) {}
+    __device__ __forceinline__ bool ok() const { return o < n; }
+    __device__ __forceinline__ int off(const BatchedParams &) const { return o; }
+    __device__ __forceinline__ bool first() const { return o < spr; }
+    __device__ __forceinline__ bool next_ok() const { return o + spr < n; }
+    __device__ __forceinline__ int next_off(const BatchedParams &) const { return o + spr; }
+    __device__ __forceinline__ void step(const BatchedParams &) { o += spr; }
+};
+
 template <int RV>
 struct Lane {
     int r0;              // first replica this thread updates (absolute within the sample)
@@ -121,17 +168,17 @@ __device__ __forceinline__ void store_spins(float2 *row, const float2 (&v)[RV])
 // One colour phase of one pass for this CTA's chunk: one thread per (site,
 // block of RV consecutive replicas).
 // Philox block of this thread's first item in colour c (Metropolis pass).
-template <bool STAGED, class SS>
+template <bool STAGED, bool NP2, class SS>
 __device__ __forceinline__ Words4 first_draw(const DevPlan &P, const DevSample &d, const SS &sh,
                                              const BatchedParams &bp, const Staged &stg, int c, uint32_t t, int r0)
 {
     const int lo = sh.cls_lo[c], hi = sh.cls_hi[c];
-    const int items = hi > lo ? (hi - lo) << bp.log2lps : 0;
+    const ItemIter<NP2> it(bp, hi - lo);
     Words4 x{0u, 0u, 0u, 0u};
-    if ((int)threadIdx.x < items) {
-        const int off = (int)threadIdx.x >> bp.log2lps;
-        const uint32_t site = STAGED ? (uint32_t)stg.site_id[sh.cls_base[c] + off]
-                                     : (uint32_t)__ldg(P.perm + d.site_off + lo + off);
+    if (it.ok()) {
+        const int o0 = it.off(bp);
+        const uint32_t site = STAGED ? (uint32_t)stg.site_id[sh.cls_base[c] + o0]
+                                     : (uint32_t)__ldg(P.perm + d.site_off + lo + o0);
         x = met_block_f32(site, t, r0, d.sample_id, P.key);
     }
     return x;
@@ -174,33 +221,33 @@ __device__ __forceinline__ void fetch_grow(const DevPlan &P, const DevSample &d,
     }
 }
 
-template <bool IS_MET, bool FUSE_E, bool STAGED, int RV, int DEG, bool DISORDER, class SS>
+template <bool IS_MET, bool FUSE_E, bool STAGED, int RV, int DEG, bool DISORDER, bool NP2, class SS>
 __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, const SS &sh,
                                       const BatchedParams &bp, const Staged &stg, int c, uint32_t t, Lane<RV> &ln,
                                       const Words4 &first)
 {
     const int cb = sh.cls_cb[c];
     const int lo = sh.cls_lo[c], hi = sh.cls_hi[c], base = sh.cls_base[c];
-    const int items = hi > lo ? (hi - lo) << bp.log2lps : 0;
+    const int n = hi - lo;
     const int R = d.R;
     const float2 *sp = reinterpret_cast<const float2 *>(P.spins) + d.spin_off + ln.r0;
     float2 *spw = reinterpret_cast<float2 *>(P.spins) + d.spin_off + ln.r0;
     const int32_t *cl = P.col + d.col_off;
 
-    int q = threadIdx.x;
-    if (q >= items) return;
+    ItemIter<NP2> it(bp, n);
+    if (!it.ok()) return;
     // rows staged in shared memory are read where they are used; rows in
     // global memory one item ahead
     GRow<DEG> cur;
-    if (!STAGED) fetch_grow<IS_MET, STAGED, DEG>(P, d, bp, stg, lo + (q >> bp.log2lps), 0, cur);
-    for (; q < items; q += blockDim.x) {
-        const int i = lo + (q >> bp.log2lps);
+    if (!STAGED) fetch_grow<IS_MET, STAGED, DEG>(P, d, bp, stg, lo + it.off(bp), 0, cur);
+    for (; it.ok(); it.step(bp)) {
+        const int o = it.off(bp);
+        const int i = lo + o;
         GRow<DEG> nxt;
-        const int qn = q + (int)blockDim.x;
         if (STAGED)
-            fetch_grow<IS_MET, STAGED, DEG>(P, d, bp, stg, i, base + (q >> bp.log2lps), cur);
-        else if (qn < items)
-            fetch_grow<IS_MET, STAGED, DEG>(P, d, bp, stg, lo + (qn >> bp.log2lps), 0, nxt);
+            fetch_grow<IS_MET, STAGED, DEG>(P, d, bp, stg, i, base + o, cur);
+        else if (it.next_ok())
+            fetch_grow<IS_MET, STAGED, DEG>(P, d, bp, stg, lo + it.next_off(bp), 0, nxt);
         float2 s[RV];
         load_spins<RV>(sp + i * R, s);
         float hx[RV], hy[RV], lx[RV], ly[RV];
@@ -253,7 +300,7 @@ __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, cons
         }
         float2 n[RV];
         if (IS_MET) {
-            const Words4 x = (q == (int)threadIdx.x) ? first : met_block_f32(cur.key, t, ln.r0, d.sample_id, P.key);
+            const Words4 x = it.first() ? first : met_block_f32(cur.key, t, ln.r0, d.sample_id, P.key);
             bool any = false;
 #pragma unroll
             for (int v = 0; v < RV; ++v) {
@@ -279,9 +326,9 @@ __device__ __forceinline__ void phase(const DevPlan &P, const DevSample &d, cons
     }
 }
 
-// Warp partial of a per-thread value of replica lane_rep+v (lanes l and
-// l ^ o, o >= lanes per site, hold the same replicas), stored per warp so that
-// the CTA sum is taken in a fixed order.
+// Warp partial of a per-thread value of replica lane_rep+v (lps a power of
+// two: lanes l and l ^ o, o >= lps, hold the same replicas), stored per warp
+// so that the CTA sum is taken in a fixed order.
 template <class SS>
 __device__ __forceinline__ void warp_part(SS &sh, const BatchedParams &bp, int lane_rep, int v, int f, float x)
 {
@@ -296,10 +343,51 @@ __device__ __forceinline__ void warp_count(SS &sh, const BatchedParams &bp, int 
     if ((threadIdx.x & 31) < (1 << bp.log2lps)) sh.part_met[threadIdx.x >> 5][lane_rep + v] = x;
 }
 
-// Magnetisation and Fourier sums of the CTA's own sites (final spins).
+// lps not a power of two: the CTA sum of one per-thread value per replica of
+// the group, in thread order (so it is the same on every run), added to field
+// f of the group's slots.  The warp partial array serves as scratch (it holds
+// kSums x 32 floats per warp, at least RV per thread).  Called by every thread.
 template <int RV, class SS>
+__device__ __forceinline__ void cta_sum_np2(SS &sh, const BatchedParams &bp, const float (&x)[RV], double *obs_g,
+                                            int f)
+{
+    float *tp = &sh.part[0][0][0];
+    const int n = (int)blockDim.x;
+#pragma unroll
+    for (int v = 0; v < RV; ++v) tp[v * n + threadIdx.x] = (int)threadIdx.x < bp.act ? x[v] : 0.f;
+    __syncthreads();
+    if ((int)threadIdx.x < bp.Rg) {
+        const int v = (int)threadIdx.x % RV, lane = (int)threadIdx.x / RV;
+        float s = 0.f;
+        for (int k = lane; k < bp.act; k += bp.lps) s += tp[v * n + k];
+        atomicAdd(obs_g + (size_t)threadIdx.x * kObsStride + f, (double)s);
+    }
+    __syncthreads();
+}
+
+template <int RV, class SS>
+__device__ __forceinline__ void cta_count_np2(SS &sh, const BatchedParams &bp, const unsigned (&x)[RV],
+                                              unsigned long long *met_acc, int r_base)
+{
+    unsigned *tp = reinterpret_cast<unsigned *>(&sh.part[0][0][0]);
+    const int n = (int)blockDim.x;
+#pragma unroll
+    for (int v = 0; v < RV; ++v) tp[v * n + threadIdx.x] = (int)threadIdx.x < bp.act ? x[v] : 0u;
+    __syncthreads();
+    if ((int)threadIdx.x < bp.Rg) {
+        const int v = (int)threadIdx.x % RV, lane = (int)threadIdx.x / RV;
+        unsigned s = 0;
+        for (int k = lane; k < bp.act; k += bp.lps) s += tp[v * n + k];
+        if (s) atomicAdd(&met_acc[sh.slot_of[r_base + threadIdx.x]], (unsigned long long)s);
+    }
+    __syncthreads();
+}
+
+// Magnetisation and Fourier sums of the CTA's own sites (final spins), as warp
+// partials (lps a power of two) or added to the group's slots of obs_g.
+template <int RV, bool NP2, class SS>
 __device__ __forceinline__ void measure_own_sites(const DevPlan &P, const DevSample &d, SS &sh,
-                                                  const BatchedParams &bp, int r0, int lane_rep)
+                                                  const BatchedParams &bp, int r0, int lane_rep, double *obs_g)
 {
     float m[RV][kSums - 1];
 #pragma unroll
@@ -309,9 +397,8 @@ __device__ __forceinline__ void measure_own_sites(const DevPlan &P, const DevSam
     const float2 *sp = reinterpret_cast<const float2 *>(P.spins) + d.spin_off + r0;
     for (int c = 0; c < d.Q; ++c) {
         const int lo = sh.cls_lo[c], hi = sh.cls_hi[c];
-        const int items = hi > lo ? (hi - lo) << bp.log2lps : 0;
-        for (int q = threadIdx.x; q < items; q += blockDim.x) {
-            const int i = lo + (q >> bp.log2lps);
+        for (ItemIter<NP2> it(bp, hi - lo); it.ok(); it.step(bp)) {
+            const int i = lo + it.off(bp);
             float2 s[RV];
             load_spins<RV>(sp + i * d.R, s);
             const float4 ph = __ldg(reinterpret_cast<const float4 *>(P.phase) + d.site_off + i);
@@ -326,13 +413,23 @@ __device__ __forceinline__ void measure_own_sites(const DevPlan &P, const DevSam
             }
         }
     }
+    if constexpr (!NP2) {
 #pragma unroll
-    for (int v = 0; v < RV; ++v)
+        for (int v = 0; v < RV; ++v)
 #pragma unroll
-        for (int f = 1; f < kSums; ++f) warp_part(sh, bp, lane_rep, v, f, m[v][f - 1]);
+            for (int f = 1; f < kSums; ++f) warp_part(sh, bp, lane_rep, v, f, m[v][f - 1]);
+    } else {
+#pragma unroll
+        for (int f = 1; f < kSums; ++f) {
+            float x[RV];
+#pragma unroll
+            for (int v = 0; v < RV; ++v) x[v] = m[v][f - 1];
+            cta_sum_np2<RV>(sh, bp, x, obs_g, f);
+        }
+    }
 }
 
-template <bool STAGED, int RV, int DEG, bool DISORDER, class SS>
+template <bool STAGED, int RV, int DEG, bool DISORDER, bool NP2, class SS>
 __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams &bp, SS &sh,
                                            const Staged &stg, cg::cluster_group &cluster, int s, int group,
                                            int rank)
@@ -341,12 +438,15 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
     const int R = d.R;
     const int n_groups = R / bp.Rg;
     const bool leader = (group == 0 && rank == 0);
-    const int lane_rep = (threadIdx.x & ((1 << bp.log2lps) - 1)) * RV;  // replica offset within the group
+    // replica offset within the group of this thread's lane (threads past
+    // spr * lps have no lane and update nothing)
+    const int lane_rep = NP2 ? ((int)threadIdx.x < bp.act ? ((int)threadIdx.x % bp.lps) * RV : 0)
+                             : (int)(threadIdx.x & ((1 << bp.log2lps) - 1)) * RV;
     Lane<RV> ln;
     ln.r0 = group * bp.Rg + lane_rep;
     uint32_t t = P.sweep[s];
     const bool met = bp.ops & XYL_OP_MET, orx = bp.ops & XYL_OP_OR;
-    Words4 first = first_draw<STAGED>(P, d, sh, bp, stg, 0, t, ln.r0);
+    Words4 first = first_draw<STAGED, NP2>(P, d, sh, bp, stg, 0, t, ln.r0);
     for (int it = 0; it < bp.n_sweeps; ++it) {
         const bool measure = (bp.ops & XYL_OP_MEASURE) && bp.measure_every > 0 &&
                              ((t + 1u) % (uint32_t)bp.measure_every) == 0u;
@@ -362,11 +462,11 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
             // the next phase's first Philox block is drawn while the cluster
             // barrier of the previous phase completes
             for (int c = 0; c < d.Q; ++c) {
-                if (orx) phase<true, false, STAGED, RV, DEG, DISORDER>(P, d, sh, bp, stg, c, t, ln, first);
-                else phase<true, true, STAGED, RV, DEG, DISORDER>(P, d, sh, bp, stg, c, t, ln, first);
+                if (orx) phase<true, false, STAGED, RV, DEG, DISORDER, NP2>(P, d, sh, bp, stg, c, t, ln, first);
+                else phase<true, true, STAGED, RV, DEG, DISORDER, NP2>(P, d, sh, bp, stg, c, t, ln, first);
                 if (orx || c + 1 < d.Q) {
                     cluster_arrive();
-                    if (c + 1 < d.Q) first = first_draw<STAGED>(P, d, sh, bp, stg, c + 1, t, ln.r0);
+                    if (c + 1 < d.Q) first = first_draw<STAGED, NP2>(P, d, sh, bp, stg, c + 1, t, ln.r0);
                     cluster_wait();
                 }
             }
@@ -374,39 +474,49 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
         if (orx) {
             const Words4 none{0u, 0u, 0u, 0u};
             for (int c = 0; c < d.Q; ++c) {
-                phase<false, true, STAGED, RV, DEG, DISORDER>(P, d, sh, bp, stg, c, t, ln, none);
+                phase<false, true, STAGED, RV, DEG, DISORDER, NP2>(P, d, sh, bp, stg, c, t, ln, none);
                 if (c + 1 < d.Q) cluster.sync();
             }
         }
         // this CTA's sums: fused energies, Metropolis counts, and on measurement
-        // sweeps the magnetisation and Fourier sums of its own (final) sites
-#pragma unroll
-        for (int v = 0; v < RV; ++v) {
-            warp_part(sh, bp, lane_rep, v, kObsE, ln.e[v]);
-            if (met) warp_count(sh, bp, lane_rep, v, ln.acc[v]);
-        }
-        if (measure) {
-            __syncthreads();  // own sites written by other threads of this CTA
-            measure_own_sites<RV>(P, d, sh, bp, ln.r0, lane_rep);
-        }
-        __syncthreads();
-        // CTA sums in warp order (FP32 over at most a few thousand sites), then
-        // FP64 across the CTAs of the sample
+        // sweeps the magnetisation and Fourier sums of its own (final) sites;
+        // CTA sums in a fixed order (FP32 over at most a few thousand sites),
+        // then FP64 across the CTAs of the sample
         const int buf = (int)(t & 1u);
         double *obs_s = P.obs + ((size_t)buf * P.total_R + d.rep_off) * kObsStride;
-        const int nf = measure ? kSums : 1;
-        const int n_warps = (int)(blockDim.x >> 5);
-        for (int q = threadIdx.x; q < bp.Rg * nf; q += blockDim.x) {
-            const int rl = q / nf, f = q % nf;
-            float v = 0.f;
-            for (int w = 0; w < n_warps; ++w) v += sh.part[f][w][rl];
-            atomicAdd(obs_s + (size_t)(group * bp.Rg + rl) * kObsStride + f, (double)v);
-        }
-        if (met && threadIdx.x < bp.Rg) {
-            const int r = group * bp.Rg + threadIdx.x;
-            unsigned int n = 0;
-            for (int w = 0; w < n_warps; ++w) n += sh.part_met[w][threadIdx.x];
-            if (n) atomicAdd(&P.met_acc[d.rep_off + sh.slot_of[r]], (unsigned long long)n);
+        double *obs_g = obs_s + (size_t)group * bp.Rg * kObsStride;
+        if constexpr (!NP2) {
+#pragma unroll
+            for (int v = 0; v < RV; ++v) {
+                warp_part(sh, bp, lane_rep, v, kObsE, ln.e[v]);
+                if (met) warp_count(sh, bp, lane_rep, v, ln.acc[v]);
+            }
+            if (measure) {
+                __syncthreads();  // own sites written by other threads of this CTA
+                measure_own_sites<RV, NP2>(P, d, sh, bp, ln.r0, lane_rep, obs_g);
+            }
+            __syncthreads();
+            // per replica: the warp partials in warp order
+            const int nf = measure ? kSums : 1;
+            const int n_warps = (int)(blockDim.x >> 5);
+            for (int q = threadIdx.x; q < bp.Rg * nf; q += blockDim.x) {
+                const int rl = q / nf, f = q % nf;
+                float v = 0.f;
+                for (int w = 0; w < n_warps; ++w) v += sh.part[f][w][rl];
+                atomicAdd(obs_g + (size_t)rl * kObsStride + f, (double)v);
+            }
+            if (met && threadIdx.x < bp.Rg) {
+                const int r = group * bp.Rg + threadIdx.x;
+                unsigned int n = 0;
+                for (int w = 0; w < n_warps; ++w) n += sh.part_met[w][threadIdx.x];
+                if (n) atomicAdd(&P.met_acc[d.rep_off + sh.slot_of[r]], (unsigned long long)n);
+            }
+        } else {
+            // per replica: the thread values in thread order
+            __syncthreads();  // every thread is past its last phase before the scratch is written
+            cta_sum_np2<RV>(sh, bp, ln.e, obs_g, kObsE);
+            if (met) cta_count_np2<RV>(sh, bp, ln.acc, P.met_acc + d.rep_off, group * bp.Rg);
+            if (measure) measure_own_sites<RV, NP2>(P, d, sh, bp, ln.r0, lane_rep, obs_g);
         }
         if (n_groups > 1) {
             // every CTA of the sample signs in once its sums are out; the first
@@ -426,7 +536,7 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
             }
         }
         cluster_arrive();
-        if (met) first = first_draw<STAGED>(P, d, sh, bp, stg, 0, t + 1u, ln.r0);  // next sweep's first draw
+        if (met) first = first_draw<STAGED, NP2>(P, d, sh, bp, stg, 0, t + 1u, ln.r0);  // next sweep's first draw
         cluster_wait();
         if (n_groups > 1 && *(volatile int *)&sh.abort_flag) break;
         for (int k = threadIdx.x; k < R; k += blockDim.x) sh.E[k] = __ldcg(obs_s + (size_t)k * kObsStride + kObsE);
@@ -444,7 +554,7 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
     if (leader && threadIdx.x == 0) P.sweep[s] = t;
 }
 
-template <bool STAGED, int RV, int DEG, bool DISORDER, int MW>
+template <bool STAGED, int RV, int DEG, bool DISORDER, bool NP2, int MW>
 __device__ __forceinline__ void batched_body(const DevPlan &P, const BatchedParams &bp)
 {
     __shared__ SharedStateT<MW> sh;
@@ -501,47 +611,53 @@ __device__ __forceinline__ void batched_body(const DevPlan &P, const BatchedPara
         stg = Staged{col, deg, site};
         __syncthreads();
     }
-    run_sweeps<STAGED, RV, DEG, DISORDER>(P, bp, sh, stg, cluster, s, group, rank);
+    run_sweeps<STAGED, RV, DEG, DISORDER, NP2>(P, bp, sh, stg, cluster, s, group, rank);
 }
 
 // Up to 672 threads with 96 registers each, or, rows in global memory only,
 // up to 1024 threads with 64 registers each (more warps to cover the latency
 // of the neighbour gathers).
-template <bool STAGED, int RV, int DEG, bool DISORDER>
+// NP2: lanes per site not a power of two (even groups of 6, 10, 12, ... replicas).
+template <bool STAGED, int RV, int DEG, bool DISORDER, bool NP2>
 __global__ void __maxnreg__(96) batched_kernel(DevPlan P, BatchedParams bp)
 {
-    batched_body<STAGED, RV, DEG, DISORDER, kMaxWarps>(P, bp);
+    batched_body<STAGED, RV, DEG, DISORDER, NP2, kMaxWarps>(P, bp);
 }
 
-template <int RV, int DEG, bool DISORDER>
+template <int RV, int DEG, bool DISORDER, bool NP2>
 __global__ void __launch_bounds__(1024, 1) batched_kernel_wide(DevPlan P, BatchedParams bp)
 {
-    batched_body<false, RV, DEG, DISORDER, kMaxWarpsWide>(P, bp);
+    batched_body<false, RV, DEG, DISORDER, NP2, kMaxWarpsWide>(P, bp);
 }
 
 using KernelFn = void (*)(DevPlan, BatchedParams);
 
 // The specialisation for a launch shape: CSR staged or not, one or two
-// replicas per thread, fixed degree 6 / at most 8 / any degree, random bonds or fields.
-template <bool STAGED, int RV, bool DISORDER>
+// replicas per thread, fixed degree 6 / at most 8 / any degree, random bonds or
+// fields, lanes per site a power of two or not.
+template <bool STAGED, int RV, bool DISORDER, bool NP2>
 KernelFn pick_deg(const BatchedShape &B)
 {
     if (!STAGED && B.block > kMaxWarps * 32) {
-        if (B.fixed_deg == 6) return batched_kernel_wide<RV, 6, DISORDER>;
-        if (B.max_deg <= 8) return batched_kernel_wide<RV, -8, DISORDER>;
-        return batched_kernel_wide<RV, 0, DISORDER>;
+        if (B.fixed_deg == 6) return batched_kernel_wide<RV, 6, DISORDER, NP2>;
+        if (B.max_deg <= 8) return batched_kernel_wide<RV, -8, DISORDER, NP2>;
+        return batched_kernel_wide<RV, 0, DISORDER, NP2>;
     }
-    if (B.fixed_deg == 6) return batched_kernel<STAGED, RV, 6, DISORDER>;
-    if (B.max_deg <= 8) return batched_kernel<STAGED, RV, -8, DISORDER>;
-    return batched_kernel<STAGED, RV, 0, DISORDER>;
+    if (B.fixed_deg == 6) return batched_kernel<STAGED, RV, 6, DISORDER, NP2>;
+    if (B.max_deg <= 8) return batched_kernel<STAGED, RV, -8, DISORDER, NP2>;
+    return batched_kernel<STAGED, RV, 0, DISORDER, NP2>;
 }
 
 template <bool DISORDER>
 KernelFn pick_kernel_d(const BatchedShape &B)
 {
-    const bool rv2 = B.Rg >= 2;
-    if (B.staged) return rv2 ? pick_deg<true, 2, DISORDER>(B) : pick_deg<true, 1, DISORDER>(B);
-    return rv2 ? pick_deg<false, 2, DISORDER>(B) : pick_deg<false, 1, DISORDER>(B);
+    // groups are a power of two (one or two replicas a thread) or even (two)
+    const bool rv2 = B.Rg % 2 == 0;
+    const int lps = rv2 ? B.Rg / 2 : B.Rg;
+    if (lps & (lps - 1))
+        return B.staged ? pick_deg<true, 2, DISORDER, true>(B) : pick_deg<false, 2, DISORDER, true>(B);
+    if (B.staged) return rv2 ? pick_deg<true, 2, DISORDER, false>(B) : pick_deg<true, 1, DISORDER, false>(B);
+    return rv2 ? pick_deg<false, 2, DISORDER, false>(B) : pick_deg<false, 1, DISORDER, false>(B);
 }
 
 KernelFn pick_kernel(const BatchedShape &B) { return B.disorder ? pick_kernel_d<true>(B) : pick_kernel_d<false>(B); }
@@ -615,9 +731,13 @@ cudaError_t launch_batched(const DevPlan &P, const PlanShape &, const BatchedSha
     bp.unit_begin = unit_begin;
     bp.G = B.G;
     bp.Rg = B.Rg;
-    bp.rv = (B.Rg >= 2) ? 2 : 1;
+    bp.rv = (B.Rg % 2 == 0) ? 2 : 1;
+    bp.lps = B.Rg / bp.rv;
+    bp.spr = B.block / bp.lps;
+    bp.act = bp.spr * bp.lps;
+    bp.pow2 = (bp.lps & (bp.lps - 1)) == 0 ? 1 : 0;
     bp.log2lps = 0;
-    while ((1 << bp.log2lps) < B.Rg / bp.rv) ++bp.log2lps;
+    while ((1 << bp.log2lps) < bp.lps) ++bp.log2lps;
     bp.n_sweeps = n_sweeps;
     bp.ops = ops;
     bp.measure_every = measure_every;

@@ -29,7 +29,7 @@ struct PlanShape {
 // Batched-engine launch shape chosen by the tuner.
 struct BatchedShape {
     int G = 1;              // CTAs per cluster (one team per replica group)
-    int Rg = 1;             // replicas per group (power of two, divides every R)
+    int Rg = 1;             // replicas per group (divides every R, <= 32; a power of two, or even in the global shape)
     int block = 512;        // threads per CTA
     bool staged = false;    // CSR rows of each CTA's chunks held in shared memory
     int owned_max = 0;      // largest number of sites one CTA owns

@@ -320,7 +320,10 @@ bool resident_fit_o3(const xyl_plan *p, const std::vector<int> &samples, int g, 
 // run in the resident shape with one CTA per group.
 int apply_shape(xyl_plan *p, Part &part, int g, int G, int block, int stage, int resident, int waves = 0)
 {
-    if (g < 1 || g > 32 || (g & (g - 1))) return fail(XYL_EINVAL, "group=%d must be a power of two <= 32", g);
+    if (g < 1 || g > 32) return fail(XYL_EINVAL, "group=%d must be in [1, 32]", g);
+    if ((g & (g - 1)) && (resident || p->shape.dim == 3 || g % 2))
+        return fail(XYL_EINVAL, "group=%d: a group that is not a power of two must be even and runs in the "
+                    "global-memory shape", g);
     for (int si : part.samples)
         if (p->hs[si].R % g) return fail(XYL_EINVAL, "group=%d does not divide n_temps=%d", g, p->hs[si].R);
     if (G < 1 || G > 16) return fail(XYL_EINVAL, "cluster=%d must be in [1, 16]", G);
@@ -1591,7 +1594,10 @@ int xyl_autotune(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_ev
             if ((p->resident_req < 0 && res) || (p->resident_req > 0 && !res)) continue;
             for (int waves = 0; waves <= (res ? 0 : 1); ++waves) {
                 if (waves ? !try_waves : p->waves_req > 0) continue;
-                for (int g = 1; g <= 32; g *= 2) {
+                for (int g = 1; g <= 32; ++g) {
+                    // resident: powers of two; global memory: also even groups from 6
+                    // (one group per sample where n_temps is not a power of two)
+                    if ((g & (g - 1)) && (res || g % 2 || g < 6)) continue;
                     bool divides = true;
                     for (int si : part.samples) divides &= (p->hs[si].R % g == 0);
                     if (!divides) continue;

@@ -680,6 +680,63 @@ def test_replica_pairs_same_spins_in_every_shape(env):
             assert np.array_equal(got, ref), shp
 
 
+def _twenty_slots(wl, L=48):
+    """Two L x L samples of C4's family (rho = 3) with C4's 20 temperatures."""
+    return wl.Config("T20", [(L, 3.0, 0), (L, 3.0, 1)], wl.geometric_temperatures(1.5, 3.5, 20))
+
+
+# global-memory shapes whose lanes per site (group / 2 replicas per thread)
+# are not a power of two: one group per sample (20), two (10), a block that
+# leaves threads without a lane (1024 = 102 x 10 + 4), rows staged
+NON_POW2 = [dict(group=20, cluster=2, block=640, resident=-1), dict(group=10, cluster=3, block=640, resident=-1),
+            dict(group=20, cluster=4, block=1024, resident=-1), dict(group=10, cluster=1, block=512, resident=-1),
+            dict(group=10, cluster=2, block=640, resident=-1, stage=0)]
+
+
+def test_groups_of_any_size_give_the_same_spins(env):
+    """Replica groups whose lanes per site are not a power of two (20 slots:
+    groups of 20 or 10) perform the same per-site arithmetic as the
+    power-of-two groups and the FP32 plain engine, bit for bit; their CTA
+    sums (thread order instead of warp shuffles) agree with the power-of-two
+    shape's to FP32 rounding, the Metropolis counts exactly."""
+    xyl, wl = env
+    cfg = _twenty_slots(wl)
+    graphs = wl.build_graphs(cfg)
+    ref = None
+    for eng, shp in [(xyl.FP32_BATCHED, dict(group=4, cluster=2, block=640, resident=-1))] + \
+            [(xyl.FP32_BATCHED, shp) for shp in NON_POW2] + [(xyl.FP32_PLAIN, {})]:
+        p, _ = wl.make_plan(cfg, eng, graphs=graphs, **shp)
+        if eng == xyl.FP32_BATCHED:
+            t = p.tuning()
+            assert (t["group"], t["resident"]) == (shp["group"], -1), shp
+        p.bind()
+        p.init_spins()
+        p.sweep(6, NO_PT, 2)
+        spins = np.stack([p.spins(k, r) for k in range(2) for r in range(20)])
+        st = p.read_observables()
+        if ref is None:
+            ref = (spins, st)
+            continue
+        assert np.array_equal(spins, ref[0]), shp
+        assert np.array_equal(st["met_acc"], ref[1]["met_acc"]) and np.array_equal(st["met_try"], ref[1]["met_try"])
+        np.testing.assert_allclose(st["acc"], ref[1]["acc"], rtol=2e-5, atol=2e-5, err_msg=str(shp))
+        assert p.status() == (0, 6)
+
+
+@pytest.mark.parametrize("shape", NON_POW2[:3], ids=["g20", "g10", "g20-1024"])
+def test_fp32_parity_groups_of_any_size(env, orc, shape):
+    """With parallel tempering and measurement: every replica-sweep of both
+    samples against the oracle (24-bit draws) under the traced parity rule."""
+    xyl, wl = env
+    cfg = _twenty_slots(wl, L=32)
+    plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, **shape)
+    plan.bind()
+    plan.init_spins()
+    sims = {k: _oracle_for(orc, wl, cfg, k, u24=True) for k in range(2)}
+    _report(f"T20 {shape}", _fp32_per_sweep(plan, sims, [0, 1], 6, ALL, lambda s: 32 * 32))
+    assert plan.status() == (0, 6)
+
+
 def test_autotune_restores_state(env):
     xyl, wl = env
     cfg = wl.config("C2")

@@ -229,6 +229,21 @@ def test_fields_are_validated(xyl):
     assert p.workspace_bytes == q.workspace_bytes + 64 * 8 - 256
 
 
+def test_group_sizes_are_validated(xyl):
+    """The global-memory shape takes a power of two or an even group dividing
+    every n_temps (up to 32); the resident shape only powers of two."""
+    g = xyl.build_graph_csr(16, 6, 3.5, 1, 0)
+    temps = [1.0] * 20
+    for group in (20, 10, 4, 2, 1):
+        t = xyl.Plan([(g, 0, temps, temps)], engine=xyl.FP32_BATCHED, device="cpu", group=group, cluster=2,
+                     resident=-1).tuning()
+        assert (t["group"], t["resident"]) == (group, -1)
+    for group, resident in ((3, -1), (5, -1), (40, -1), (10, 1), (20, 1)):
+        with pytest.raises(xyl.XylError) as e:
+            xyl.Plan([(g, 0, temps, temps)], engine=xyl.FP32_BATCHED, device="cpu", group=group, resident=resident)
+        assert e.value.code == xyl.EINVAL, (group, resident)
+
+
 def test_o3_plans_are_validated(xyl):
     g = xyl.build_graph_csr(8, 6, 3.5, 1, 0)
     for engine, kw in ((xyl.FP32_BATCHED, {"spin_dim": 3, "resident": -1}), (xyl.FP32_PLAIN, {"spin_dim": 4})):
