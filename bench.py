@@ -5,8 +5,8 @@ over every colour class, parallel-tempering swap attempt after every sweep, an
 FP64 measurement every `measure_every` sweeps) of the workload's full batch.
 Default workload C5: 128 Levy graphs, L=512 (262144 sites each), z=6, rho in
 {2.5, 4.5}, 32 temperatures geometric in [1.5, 3.5]; C2 (one graph, L=128, 16
-temperatures) and C3 (768 graphs, L=64, 24 temperatures) are measured in the
-same run.  A site-update is one Metropolis or one overrelaxation update of one
+temperatures), C3 (768 graphs, L=64, 24 temperatures) and C4 (48 graphs of six
+sizes L=32..192, 20 temperatures) are measured in the same run.  A site-update is one Metropolis or one overrelaxation update of one
 spin of one replica.
 
 Prints ONE JSON line (rank 0).  `--impl reference` times the sequential CPU
@@ -602,7 +602,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="C5")
-    ap.add_argument("--extra-configs", default="C2,C3",
+    ap.add_argument("--extra-configs", default="C2,C3,C4",
                     help="comma-separated workloads also measured (shorter) and reported in the same line; '' = none")
     ap.add_argument("--extra-steps", type=int, default=5)
     ap.add_argument("--sweeps-per-step", type=int, default=0, help="0 = calibrate to about 50 ms per step")
