@@ -6,8 +6,9 @@ FP64 measurement every `measure_every` sweeps) of the workload's full batch.
 Default workload C5: 128 Levy graphs, L=512 (262144 sites each), z=6, rho in
 {2.5, 4.5}, 32 temperatures geometric in [1.5, 3.5]; C2 (one graph, L=128, 16
 temperatures), C3 (768 graphs, L=64, 24 temperatures) and C4 (48 graphs of six
-sizes L=32..192, 20 temperatures) are measured in the same run.  A site-update is one Metropolis or one overrelaxation update of one
-spin of one replica.
+sizes L=32..192, 20 temperatures) are measured in the same run.  A
+site-update is one Metropolis or one overrelaxation update of one spin of one
+replica.
 
 Prints ONE JSON line (rank 0).  `--impl reference` times the sequential CPU
 oracle on the same workload instead.
