@@ -409,11 +409,11 @@ def roofline_for(plan, cfg, per_launch_updates, avg_launch_s, name, spins_live_b
                  "write per update")
     elif spins_live_bytes <= L2_BYTES:
         bound, b, peak, kind = "l2", models["gather"], L2_STREAM_PROBE_GBS, "own probe: L2-resident stream read"
-        basis = f"a launch wave's spins ({spins_live_bytes / 2**20:.0f} MiB) stay in L2: gather model"
+        basis = f"the spins resident at once ({spins_live_bytes / 2**20:.0f} MiB) stay in L2: gather model"
     else:
         bound, b, peak, kind = "hbm", models["hbm_compulsory"], hbm_peak, hbm_kind
-        basis = (f"a launch wave's spins ({spins_live_bytes / 2**30:.2f} GiB) exceed L2: compulsory model, each spin "
-                 "read and written once per pass")
+        basis = (f"the spins resident at once ({spins_live_bytes / 2**30:.2f} GiB) exceed L2: compulsory model, each "
+                 "spin read and written once per pass")
     a = b * per_launch_updates / avg_launch_s / 1e9
     prof = _profile_traffic(kernel, name)
     traffic = None
@@ -451,12 +451,14 @@ def fp64_bound(name):
 
 
 def spins_live_bytes(plan, cfg):
-    """Bytes of spins the units of one launch wave keep live (all of them when
-    one wave runs the whole batch; the plain engines run it all at once)."""
+    """Bytes of spins the units resident on the GPU at once keep live: a launch
+    wave's units when they wait on one another, else as many clusters as fit
+    (each runs all of a launch's sweeps while resident); the plain engines
+    keep the whole batch live."""
     units = plan.unit_count()
     frac = 1.0
     if units and plan.part_count() == 1:
-        frac = min(1.0, plan.wave_units() / units)
+        frac = min(1.0, plan.live_units() / units)
     return frac * cfg.spins_per_sweep() * (8 if cfg.spin_dim == 2 else 16)
 
 

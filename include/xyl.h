@@ -370,6 +370,15 @@ int32_t xyl_unit_count(const xyl_plan *p);
 int32_t xyl_wave_units(const xyl_plan *p);
 
 /*
+ * Work units of part 0 of a bound batched plan that are resident on the GPU at
+ * once: the whole wave when its clusters wait on one another, else as many
+ * clusters as fit (the hardware starts the others as those finish, each unit
+ * running all of a launch's sweeps while resident).  Their spins are what a
+ * launch keeps live at a time.  0 for other engines or before bind.
+ */
+int32_t xyl_live_units(const xyl_plan *p);
+
+/*
  * Mixed sizes in one batch (App. B "Computational speed": the cost of a sweep
  * follows the graph's size and colour count, so each size wants its own
  * launch shape).  When the library chooses the shape (xyl_tuning resident,

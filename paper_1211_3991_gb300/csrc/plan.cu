@@ -59,6 +59,7 @@ struct Part {
     std::vector<int2> units;    // (sample, group) per unit, sample by sample
     int u0 = 0;                 // its first unit in the plan's unit table
     int wave_units = 0;         // units one launch runs together
+    int live_units = 0;         // units resident on the GPU at once (their spins: the live set)
     bool barrier_free = false;  // no cluster waits on another: may run beside other parts
 };
 
@@ -522,6 +523,7 @@ int configure_part(xyl_plan *p, Part &part, cudaStream_t st)
             // a cluster is a whole sample and never waits on another: one
             // launch, the hardware queues the clusters that do not fit yet
             part.wave_units = n_units;
+            part.live_units = std::min(n_units, clusters * B.gpc);
             part.barrier_free = true;
         } else {
             // the clusters of a sample meet at a global barrier: a wave holds
@@ -532,6 +534,7 @@ int configure_part(xyl_plan *p, Part &part, cudaStream_t st)
                 return fail(XYL_EINVAL, "batched: %d resident clusters of %d CTAs cannot be co-resident (max %d)",
                             per_sample, B.cpc, clusters);
             part.wave_units = samples_per_wave * n_groups;
+            part.live_units = part.wave_units;
             part.barrier_free = false;
         }
         if (B.G > 1) {
@@ -578,12 +581,14 @@ int configure_part(xyl_plan *p, Part &part, cudaStream_t st)
                         B.G, clusters);
         if (B.l2_waves) samples_per_wave = std::min(samples_per_wave, l2_wave_samples(p, part));
         part.wave_units = samples_per_wave * n_groups;
+        part.live_units = part.wave_units;
         part.barrier_free = false;
     } else {
         // one group per sample: clusters never wait on one another, so a launch
         // may hold more than fit at once (the hardware queues them), unless
         // its waves are sized to L2
         part.wave_units = B.l2_waves ? std::min(n_units, l2_wave_samples(p, part)) : n_units;
+        part.live_units = std::min(part.wave_units, clusters);
         part.barrier_free = true;
     }
     return XYL_OK;
@@ -1129,6 +1134,11 @@ int32_t xyl_unit_count(const xyl_plan *p)
 int32_t xyl_wave_units(const xyl_plan *p)
 {
     return (p && p->engine == XYL_FP32_BATCHED && p->bound) ? (int32_t)p->parts[0].wave_units : 0;
+}
+
+int32_t xyl_live_units(const xyl_plan *p)
+{
+    return (p && p->engine == XYL_FP32_BATCHED && p->bound) ? (int32_t)p->parts[0].live_units : 0;
 }
 
 int32_t xyl_part_count(const xyl_plan *p)

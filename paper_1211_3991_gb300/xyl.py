@@ -32,7 +32,7 @@ EXPORTED = (
     "xyl_last_launch_count", "xyl_plan_free", "xyl_sweep_units", "xyl_unit_count", "xyl_autotune",
     "xyl_get_tuning", "xyl_sweep_noalloc", "xyl_build_levy_bonds", "xyl_walk_returns", "xyl_graph_set_couplings",
     "xyl_graph_export_couplings", "xyl_graph_set_fields", "xyl_graph_set_fields3", "xyl_philox", "xyl_read_drift",
-    "xyl_get_delta", "xyl_tune_delta", "xyl_wave_units", "xyl_part_count", "xyl_get_part_tuning",
+    "xyl_get_delta", "xyl_tune_delta", "xyl_wave_units", "xyl_live_units", "xyl_part_count", "xyl_get_part_tuning",
     "xyl_set_part_tuning", "xyl_check_plan",
 )
 
@@ -115,6 +115,7 @@ def load():
             "xyl_get_delta": ([P, i32, pf64], C.c_int),
             "xyl_tune_delta": ([P, i32, i32, u32, f64, pf64, P], C.c_int),
             "xyl_wave_units": ([P], C.c_int32),
+            "xyl_live_units": ([P], C.c_int32),
             "xyl_part_count": ([P], C.c_int32),
             "xyl_get_part_tuning": ([P, i32, C.POINTER(Tuning), pi32], C.c_int),
             "xyl_set_part_tuning": ([P, i32, C.POINTER(Tuning), P], C.c_int),
@@ -313,6 +314,10 @@ class Plan:
 
     def wave_units(self) -> int:
         return int(load().xyl_wave_units(self.handle))
+
+    def live_units(self) -> int:
+        """xyl_live_units: units of part 0 resident on the GPU at once."""
+        return int(load().xyl_live_units(self.handle))
 
     def part_count(self) -> int:
         return int(load().xyl_part_count(self.handle))

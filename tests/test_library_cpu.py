@@ -345,6 +345,9 @@ def test_calls_before_bind_report_the_call_order(xyl):
     for name, call in calls.items():
         assert call(h) == xyl.ESTATE, name
         assert call(None) == xyl.EINVAL, name
+    # counts of a plan not yet bound (or no plan) are 0
+    for name in ("xyl_wave_units", "xyl_live_units"):
+        assert getattr(lib, name)(h) == 0 and getattr(lib, name)(None) == 0, name
 
 
 def test_mixed_sizes_run_as_parts(xyl):
