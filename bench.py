@@ -475,7 +475,8 @@ def measure_workload(args, name, xyl, wl, dev, stream, flush, rank, world, steps
     cfg = wl.shard(cfg, rank, world)
     graphs = wl.build_graphs(cfg)
     engine_name = "FP32_BATCHED"
-    tune = dict(block=args.block, cluster=args.cluster, group=args.group, resident=args.resident, waves=args.waves)
+    tune = dict(block=args.block, cluster=args.cluster, group=args.group, resident=args.resident, waves=args.waves,
+                span=args.span)
     if not full:
         tune = {}
     plan, _ = wl.make_plan(cfg, getattr(xyl, engine_name), graphs=graphs, **tune)
@@ -617,6 +618,8 @@ def main():
                     help="1 = spins in shared memory for a launch, -1 = global-memory shape, 0 = library/autotuner")
     ap.add_argument("--waves", type=int, default=0, choices=[-1, 0, 1],
                     help="global-memory shape: 1 = launch waves sized to L2, -1 = never, 0 = library/autotuner")
+    ap.add_argument("--span", type=int, default=0,
+                    help="global-memory shape: clusters per replica group (0 = library/autotuner)")
     ap.add_argument("--ref-sweeps", type=int, default=0,
                     help="oracle sweeps per step of --impl reference (0 = about 1 s of the workload's sample)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample: oracle time to run")
@@ -725,7 +728,7 @@ def plan_shape(plan):
     t = plan.tuning()
     out = {"spins_in_shared_memory": t["resident"] > 0, "units": plan.unit_count(), "replicas_per_group": t["group"],
            "ctas_per_cluster": t["cluster"], "threads_per_cta": t["block"], "csr_in_shared_memory": t["stage"] > 0,
-           "l2_sized_waves": t["waves"] > 0, "units_per_launch": plan.wave_units()}
+           "l2_sized_waves": t["waves"] > 0, "clusters_per_group": t["span"], "units_per_launch": plan.wave_units()}
     if plan.part_count() > 1:
         # a mixed-size batch: one launch shape per size, largest first (the keys above are part 0's)
         out["parts"] = [plan.part_tuning(k) for k in range(plan.part_count())]

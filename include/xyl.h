@@ -233,6 +233,10 @@ typedef struct {
     int32_t spin_dim;        /* spin components: 0 or 2 = XY; 3 = O(3) (see below) */
     int32_t waves;           /* batched engine, global-memory shape: 1 = cap each launch wave to the samples whose
                                 spins and tables fit in L2, -1 = never, 0 = library's choice (never) */
+    int32_t span;            /* batched engine, global-memory shape: clusters per replica group (0 or 1 = one); above
+                                one, the group's cluster x span CTAs share its colour chunks and meet at a bounded
+                                global barrier after every colour phase, so few samples can hold the whole GPU while
+                                their spins stay in L2 for a launch's sweeps; all must be resident at once */
 } xyl_tuning;
 
 /*

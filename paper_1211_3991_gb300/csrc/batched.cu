@@ -11,6 +11,10 @@
 // neighbour's row.  Thread t serves lane t % lps of sites t / lps, t / lps +
 // spr, ... (spr = block / lps sites per round; with lps not a power of two the
 // last block % lps threads idle).
+// With span > 1 a unit is G x span CTAs in span clusters, which meet after
+// every colour phase at a bounded barrier on a per-unit counter in global
+// memory (the whole GPU can then work on one sample while its spins stay in
+// L2 for the launch's sweeps).
 // Spins are interleaved [sample][site][replica] float2 in global memory and
 // stay L2-resident for the batch sizes this engine serves; they are read and
 // written through L2 (ld/st .cg), and colour phases are separated by cluster
@@ -42,9 +46,11 @@ namespace {
 constexpr unsigned int kBarrierPolls = 1u << 21;  // about a second of polling
 
 struct BatchedParams {
-    const int2 *units;   // (sample, group) per cluster
+    const int2 *units;   // (sample, group) per unit
+    unsigned int *unit_ctr;  // span > 1: per unit of the launch, arrivals at its phase barriers (zeroed before)
     int unit_begin;
     int G, Rg;
+    int span;            // clusters per unit (G x span CTAs share a unit's colour chunks)
     int rv;              // replicas one thread updates (1 or 2)
     int lps;             // lanes that share a site (Rg / rv)
     int log2lps;         // log2(lps) when lps is a power of two
@@ -429,15 +435,46 @@ __device__ __forceinline__ void measure_own_sites(const DevPlan &P, const DevSam
     }
 }
 
+// span > 1: the clusters of a unit meet.  Every thread makes its spin writes
+// visible GPU-wide, the cluster synchronises, its first thread adds the
+// cluster's arrival to the unit's counter and waits (bounded) until all span
+// clusters have arrived at this barrier, then tells its cluster the outcome
+// before the cluster synchronises again.  False after a timeout (the status
+// word then holds XYL_ETIMEOUT).
+template <class SS>
+__device__ __forceinline__ bool unit_barrier(const DevPlan &P, SS &sh, cg::cluster_group &cluster,
+                                             const BatchedParams &bp, unsigned int *ctr, unsigned int &arrivals,
+                                             int rank)
+{
+    __threadfence();
+    cluster.sync();
+    arrivals += (unsigned int)bp.span;
+    if (rank == 0 && threadIdx.x == 0) {
+        atomicAdd(ctr, 1u);
+        int failed = 0;
+        if (!wait_counter_at_least(ctr, arrivals, kBarrierPolls)) {
+            atomicExch(P.status, XYL_ETIMEOUT);
+            failed = 1;
+        }
+        __threadfence();
+        for (int k = 0; k < bp.G; ++k) *cluster.map_shared_rank(&sh.abort_flag, k) = failed;
+    }
+    cluster.sync();
+    return *(volatile int *)&sh.abort_flag == 0;
+}
+
 template <bool STAGED, int RV, int DEG, bool DISORDER, bool NP2, class SS>
 __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams &bp, SS &sh,
                                            const Staged &stg, cg::cluster_group &cluster, int s, int group,
-                                           int rank)
+                                           int rank, int cta, unsigned int *unit_ctr)
 {
     const DevSample d = P.samples[s];
     const int R = d.R;
     const int n_groups = R / bp.Rg;
-    const bool leader = (group == 0 && rank == 0);
+    const int ctas = bp.G * bp.span;  // CTAs of one unit
+    const bool leader = (group == 0 && cta == 0);
+    const bool sample_barrier = n_groups > 1 || bp.span > 1;
+    unsigned int arrivals = 0;
     // replica offset within the group of this thread's lane (threads past
     // spr * lps have no lane and update nothing)
     const int lane_rep = NP2 ? ((int)threadIdx.x < bp.act ? ((int)threadIdx.x % bp.lps) * RV : 0)
@@ -465,9 +502,14 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
                 if (orx) phase<true, false, STAGED, RV, DEG, DISORDER, NP2>(P, d, sh, bp, stg, c, t, ln, first);
                 else phase<true, true, STAGED, RV, DEG, DISORDER, NP2>(P, d, sh, bp, stg, c, t, ln, first);
                 if (orx || c + 1 < d.Q) {
-                    cluster_arrive();
-                    if (c + 1 < d.Q) first = first_draw<STAGED, NP2>(P, d, sh, bp, stg, c + 1, t, ln.r0);
-                    cluster_wait();
+                    if (bp.span == 1) {
+                        cluster_arrive();
+                        if (c + 1 < d.Q) first = first_draw<STAGED, NP2>(P, d, sh, bp, stg, c + 1, t, ln.r0);
+                        cluster_wait();
+                    } else {
+                        if (c + 1 < d.Q) first = first_draw<STAGED, NP2>(P, d, sh, bp, stg, c + 1, t, ln.r0);
+                        if (!unit_barrier(P, sh, cluster, bp, unit_ctr, arrivals, rank)) return;
+                    }
                 }
             }
         }
@@ -475,7 +517,10 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
             const Words4 none{0u, 0u, 0u, 0u};
             for (int c = 0; c < d.Q; ++c) {
                 phase<false, true, STAGED, RV, DEG, DISORDER, NP2>(P, d, sh, bp, stg, c, t, ln, none);
-                if (c + 1 < d.Q) cluster.sync();
+                if (c + 1 < d.Q) {
+                    if (bp.span == 1) cluster.sync();
+                    else if (!unit_barrier(P, sh, cluster, bp, unit_ctr, arrivals, rank)) return;
+                }
             }
         }
         // this CTA's sums: fused energies, Metropolis counts, and on measurement
@@ -518,7 +563,7 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
             if (met) cta_count_np2<RV>(sh, bp, ln.acc, P.met_acc + d.rep_off, group * bp.Rg);
             if (measure) measure_own_sites<RV, NP2>(P, d, sh, bp, ln.r0, lane_rep, obs_g);
         }
-        if (n_groups > 1) {
+        if (sample_barrier) {
             // every CTA of the sample signs in once its sums are out; the first
             // CTA of each cluster waits for all of them (bounded) and tells the
             // other CTAs of its cluster the outcome through their shared memory
@@ -527,7 +572,7 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
             if (threadIdx.x == 0) atomicAdd(&P.barrier[s], 1u);
             if (rank == 0 && threadIdx.x == 0) {
                 int failed = 0;
-                if (!wait_counter_at_least(&P.barrier[s], (unsigned int)(bp.G * n_groups * (it + 1)), kBarrierPolls)) {
+                if (!wait_counter_at_least(&P.barrier[s], (unsigned int)(ctas * n_groups * (it + 1)), kBarrierPolls)) {
                     atomicExch(P.status, XYL_ETIMEOUT);
                     failed = 1;
                 }
@@ -538,13 +583,13 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
         cluster_arrive();
         if (met) first = first_draw<STAGED, NP2>(P, d, sh, bp, stg, 0, t + 1u, ln.r0);  // next sweep's first draw
         cluster_wait();
-        if (n_groups > 1 && *(volatile int *)&sh.abort_flag) break;
+        if (sample_barrier && *(volatile int *)&sh.abort_flag) break;
         for (int k = threadIdx.x; k < R; k += blockDim.x) sh.E[k] = __ldcg(obs_s + (size_t)k * kObsStride + kObsE);
         __syncthreads();
         pt_and_record(P, d, sh.E, sh.rep_at, sh.slot_of, t, bp.ops, leader, met, measure, obs_s);
         // clear this group's slots of the buffer the next sweep fills: every
         // reader of it finished before the barrier just passed
-        if (rank == 0) {
+        if (cta == 0) {
             double *nxt = P.obs + ((size_t)(buf ^ 1) * P.total_R + d.rep_off + group * bp.Rg) * kObsStride;
             for (int q = threadIdx.x; q < bp.Rg * kObsStride; q += blockDim.x) nxt[q] = 0.0;
         }
@@ -560,7 +605,9 @@ __device__ __forceinline__ void batched_body(const DevPlan &P, const BatchedPara
     __shared__ SharedStateT<MW> sh;
     extern __shared__ int dyn[];
     cg::cluster_group cluster = cg::this_cluster();
-    const int unit = bp.unit_begin + (int)(blockIdx.x / bp.G);
+    const int ctas = bp.G * bp.span;                  // CTAs of one unit, span clusters
+    const int unit = bp.unit_begin + (int)(blockIdx.x / ctas);
+    const int cta = (int)(blockIdx.x % ctas);         // which chunk of the unit's classes
     const int rank = (int)cluster.block_rank();
     const int2 ug = bp.units[unit];
     const int s = ug.x, group = ug.y;
@@ -580,8 +627,8 @@ __device__ __forceinline__ void batched_body(const DevPlan &P, const BatchedPara
         for (int c = 0; c < d.Q; ++c) {
             int cb = P.color_ptr[d.color_off + c], ce = P.color_ptr[d.color_off + c + 1];
             checked_class(P, cb, ce, d.N);
-            const int chunk = (ce - cb + bp.G - 1) / bp.G;
-            const int lo = min(ce, cb + rank * chunk), hi = min(ce, lo + chunk);
+            const int chunk = (ce - cb + ctas - 1) / ctas;
+            const int lo = min(ce, cb + cta * chunk), hi = min(ce, lo + chunk);
             sh.cls_cb[c] = cb;
             sh.cls_lo[c] = lo;
             sh.cls_hi[c] = hi;
@@ -611,7 +658,8 @@ __device__ __forceinline__ void batched_body(const DevPlan &P, const BatchedPara
         stg = Staged{col, deg, site};
         __syncthreads();
     }
-    run_sweeps<STAGED, RV, DEG, DISORDER, NP2>(P, bp, sh, stg, cluster, s, group, rank);
+    run_sweeps<STAGED, RV, DEG, DISORDER, NP2>(P, bp, sh, stg, cluster, s, group, rank, cta,
+                                               bp.unit_ctr + (unit - bp.unit_begin));
 }
 
 // Up to 672 threads with 96 registers each, or, rows in global memory only,
@@ -722,13 +770,20 @@ cudaError_t batched_max_active_clusters(const PlanShape &, const BatchedShape &B
 }
 
 cudaError_t launch_batched(const DevPlan &P, const PlanShape &, const BatchedShape &B, const int2 *d_units,
-                           int unit_begin, int unit_count, int n_sweeps, uint32_t ops, int measure_every,
-                           cudaStream_t st)
+                           unsigned int *unit_ctr, int unit_begin, int unit_count, int n_sweeps, uint32_t ops,
+                           int measure_every, cudaStream_t st)
 {
     if (unit_count <= 0) return cudaSuccess;
+    if (B.span > 1) {
+        // the phase barriers count arrivals from zero in every launch
+        const cudaError_t e = cudaMemsetAsync(unit_ctr, 0, (size_t)unit_count * sizeof(unsigned int), st);
+        if (e != cudaSuccess) return e;
+    }
     BatchedParams bp;
     bp.units = d_units;
+    bp.unit_ctr = unit_ctr;
     bp.unit_begin = unit_begin;
+    bp.span = B.span;
     bp.G = B.G;
     bp.Rg = B.Rg;
     bp.rv = (B.Rg % 2 == 0) ? 2 : 1;
@@ -747,7 +802,7 @@ cudaError_t launch_batched(const DevPlan &P, const PlanShape &, const BatchedSha
     bp.fixed_deg = B.fixed_deg;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
-    cfg.gridDim = dim3((unsigned)(B.G * unit_count), 1, 1);
+    cfg.gridDim = dim3((unsigned)(B.G * B.span * unit_count), 1, 1);
     cfg.blockDim = dim3((unsigned)B.block, 1, 1);
     cfg.dynamicSmemBytes = B.smem_bytes;
     cfg.stream = st;

@@ -29,6 +29,8 @@ struct PlanShape {
 // Batched-engine launch shape chosen by the tuner.
 struct BatchedShape {
     int G = 1;              // CTAs per cluster (one team per replica group)
+    int span = 1;           // global-memory shape: clusters per replica group (above 1 they meet at a
+                            // bounded global barrier after every colour phase)
     int Rg = 1;             // replicas per group (divides every R, <= 32; a power of two, or even in the global shape)
     int block = 512;        // threads per CTA
     bool staged = false;    // CSR rows of each CTA's chunks held in shared memory
@@ -81,8 +83,8 @@ cudaError_t launch_o3_recompute(const DevPlan &P, const PlanShape &S, int renorm
 
 // Batched engine: one launch per wave of samples; `units` lists (sample, group) per cluster.
 cudaError_t launch_batched(const DevPlan &P, const PlanShape &S, const BatchedShape &B, const int2 *d_units,
-                           int unit_begin, int unit_count, int n_sweeps, uint32_t ops, int measure_every,
-                           cudaStream_t st);
+                           unsigned int *unit_ctr, int unit_begin, int unit_count, int n_sweeps, uint32_t ops,
+                           int measure_every, cudaStream_t st);
 cudaError_t batched_max_active_clusters(const PlanShape &S, const BatchedShape &B, int *clusters);
 size_t batched_static_smem_bytes();
 

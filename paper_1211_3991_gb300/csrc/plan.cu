@@ -60,6 +60,7 @@ struct Part {
     int u0 = 0;                 // its first unit in the plan's unit table
     int wave_units = 0;         // units one launch runs together
     int live_units = 0;         // units resident on the GPU at once (their spins: the live set)
+    int max_clusters = 0;       // clusters of its shape that can be resident at once
     bool barrier_free = false;  // no cluster waits on another: may run beside other parts
 };
 
@@ -83,7 +84,7 @@ struct xyl_plan {
     DevPlan dev{};
     Region r_samples, r_row_ptr, r_col, r_perm, r_color_ptr, r_phase, r_spins, r_beta, r_delta, r_slot_of, r_rep_at,
         r_obs, r_last_E, r_acc, r_met_acc, r_met_try, r_pt_acc, r_pt_try, r_sweep, r_status, r_barrier, r_drift,
-        r_units, r_push, r_field, r_check;
+        r_units, r_push, r_field, r_check, r_unit_ctr;
     cudaStream_t capture_stream = nullptr;
     // parts that run side by side: one stream and one event each, and the fork event
     std::vector<cudaStream_t> part_streams;
@@ -162,6 +163,7 @@ void layout(xyl_plan *p)
     take(p->r_drift, 2 * sizeof(double));  // the recorded drift, and a save slot for xyl_write_spins
     take(p->r_check, sizeof(unsigned long long));  // violation count of xyl_check_plan
     take(p->r_units, std::max<size_t>(p->total_R, 1) * sizeof(int2));  // the most units any shape makes
+    take(p->r_unit_ctr, std::max<size_t>(p->total_R, 1) * sizeof(unsigned int));  // phase-barrier arrivals per unit
     take(p->r_push, p->total_N * sizeof(uint16_t));
     // random fields: one vector per site, only when some sample has them
     // (O(3): padded 4-vectors, like the spins)
@@ -319,8 +321,11 @@ bool resident_fit_o3(const xyl_plan *p, const std::vector<int> &samples, int g, 
 // cluster, `block` threads per CTA; stage < 0 disables shared-memory staging;
 // resident != 0 asks for the resident shape (G is then ignored).  O(3) spins
 // run in the resident shape with one CTA per group.
-int apply_shape(xyl_plan *p, Part &part, int g, int G, int block, int stage, int resident, int waves = 0)
+int apply_shape(xyl_plan *p, Part &part, int g, int G, int block, int stage, int resident, int waves = 0,
+                int span = 1)
 {
+    if (span < 1 || (span > 1 && (resident || p->shape.dim == 3)))
+        return fail(XYL_EINVAL, "span=%d: clusters per group above 1 run in the global-memory shape only", span);
     if (g < 1 || g > 32) return fail(XYL_EINVAL, "group=%d must be in [1, 32]", g);
     if ((g & (g - 1)) && (resident || p->shape.dim == 3 || g % 2))
         return fail(XYL_EINVAL, "group=%d: a group that is not a power of two must be even and runs in the "
@@ -333,6 +338,7 @@ int apply_shape(xyl_plan *p, Part &part, int g, int G, int block, int stage, int
     BatchedShape &B = part.B;
     B = BatchedShape{};
     B.G = G;
+    B.span = span;
     B.Rg = g;
     B.block = block;
     B.disorder = p->shape.disorder;
@@ -370,7 +376,7 @@ int apply_shape(xyl_plan *p, Part &part, int g, int G, int block, int stage, int
     for (int si : part.samples) {
         const HostSample &h = p->hs[si];
         int o = 0;
-        for (int c = 0; c < h.Q; ++c) o += (h.color_ptr[c + 1] - h.color_ptr[c] + G - 1) / G;
+        for (int c = 0; c < h.Q; ++c) o += (h.color_ptr[c + 1] - h.color_ptr[c] + G * span - 1) / (G * span);
         owned = std::max(owned, o);
     }
     B.owned_max = owned;
@@ -407,6 +413,10 @@ int pick_part_shape(xyl_plan *p, Part &part, const xyl_tuning *tune)
 {
     const int mode = tune ? tune->resident : 0;
     const int stage = tune ? tune->stage : 0;
+    const int span = (tune && tune->span > 0) ? tune->span : 1;
+    if (tune && tune->span < 0) return fail(XYL_EINVAL, "span=%d must be >= 0", tune->span);
+    if (span > 1 && (mode > 0 || p->shape.dim == 3))
+        return fail(XYL_EINVAL, "span=%d: clusters per group above 1 run in the global-memory shape only", span);
     int block = 512;
     if (tune && tune->block > 0) block = tune->block;
     if (p->shape.dim == 3) {
@@ -423,7 +433,7 @@ int pick_part_shape(xyl_plan *p, Part &part, const xyl_tuning *tune)
         return fail(XYL_EINVAL, "O(3) resident shape does not fit this batch (equal n_temps, a group's spins, 12 B "
                     "a site, within %zu B of shared memory)", kResidentDynLimitBytes);
     }
-    if (mode >= 0) {
+    if (mode >= 0 && span == 1) {
         // resident: the largest group that fits with all groups of a sample in
         // one cluster (pairs of replicas share a Philox block); a caller's
         // group or cluster width is taken as given
@@ -456,7 +466,7 @@ int pick_part_shape(xyl_plan *p, Part &part, const xyl_tuning *tune)
     const double items_per_phase = (double)max_N * g / std::max(1, p->shape.max_Q);
     while (G < 16 && items_per_phase / (G * 2) >= 1024.0) G *= 2;
     if (tune && tune->cluster > 0) G = tune->cluster;
-    return apply_shape(p, part, g, G, block, stage, 0, tune ? tune->waves : 0);
+    return apply_shape(p, part, g, G, block, stage, 0, tune ? tune->waves : 0, span);
 }
 
 void gather_units(xyl_plan *p);
@@ -465,7 +475,8 @@ void gather_units(xyl_plan *p);
 // the library chooses the shapes and the sizes differ, else one part.
 int pick_batched_shape(xyl_plan *p, const xyl_tuning *tune)
 {
-    const bool caller_shape = tune && (tune->resident != 0 || tune->group > 0 || tune->cluster > 0 || tune->block > 0);
+    const bool caller_shape = tune && (tune->resident != 0 || tune->group > 0 || tune->cluster > 0 || tune->block > 0 ||
+                                       tune->span > 0);
     std::vector<int> sizes;
     for (auto &h : p->hs) sizes.push_back(h.N);
     std::sort(sizes.begin(), sizes.end(), std::greater<int>());
@@ -566,6 +577,7 @@ int configure_part(xyl_plan *p, Part &part, cudaStream_t st)
     if (clusters < 1)
         return fail(XYL_EINVAL, "batched: a cluster of %d CTAs x %d threads (%zu B shared) cannot be resident",
                     B.G, B.block, B.smem_bytes);
+    part.max_clusters = clusters;
     const int n_groups = h0.R / B.Rg;
     bool uniform_groups = true;
     int groups_max = 1;
@@ -573,12 +585,13 @@ int configure_part(xyl_plan *p, Part &part, cudaStream_t st)
         uniform_groups &= (p->hs[si].R / B.Rg == n_groups);
         groups_max = std::max(groups_max, p->hs[si].R / B.Rg);
     }
-    if (groups_max > 1) {
+    if (groups_max > 1 || B.span > 1) {
         if (!uniform_groups) return fail(XYL_EINVAL, "batched: several groups per sample need equal n_temps");
-        int samples_per_wave = clusters / n_groups;
+        // every cluster of a sample (its groups x span) must be resident at once
+        int samples_per_wave = clusters / (n_groups * B.span);
         if (samples_per_wave < 1)
-            return fail(XYL_EINVAL, "batched: %d clusters of %d CTAs cannot be co-resident (max %d)", n_groups,
-                        B.G, clusters);
+            return fail(XYL_EINVAL, "batched: %d clusters of %d CTAs cannot be co-resident (max %d)",
+                        n_groups * B.span, B.G, clusters);
         if (B.l2_waves) samples_per_wave = std::min(samples_per_wave, l2_wave_samples(p, part));
         part.wave_units = samples_per_wave * n_groups;
         part.live_units = part.wave_units;
@@ -886,7 +899,8 @@ int launch_units(xyl_plan *p, const DevPlan &P, const Part &part, int u_begin, i
             XYL_CUDA(launch_resident(P, part.B, at<int2>(p, p->r_units), u, c, n, ops, measure_every, st),
                      "sweep: resident launch");
         else
-            XYL_CUDA(launch_batched(P, p->shape, part.B, at<int2>(p, p->r_units), u, c, n, ops, measure_every, st),
+            XYL_CUDA(launch_batched(P, p->shape, part.B, at<int2>(p, p->r_units), at<unsigned int>(p, p->r_unit_ctr),
+                                    u, c, n, ops, measure_every, st),
                      "sweep: batched launch");
         ++*launches;
     }
@@ -1524,6 +1538,7 @@ int xyl_get_part_tuning(const xyl_plan *p, int32_t part, xyl_tuning *out, int32_
     out->stage = B.staged ? 1 : -1;
     out->resident = B.resident ? 1 : -1;
     out->waves = B.l2_waves ? 1 : -1;
+    out->span = B.span;
     if (n_samples) *n_samples = (int32_t)p->parts[part].samples.size();
     return XYL_OK;
 }
@@ -1539,7 +1554,7 @@ int xyl_set_part_tuning(xyl_plan *p, int32_t part, const xyl_tuning *t, void *st
     Part &pt = p->parts[part];
     const Part keep = pt;
     int rc = apply_shape(p, pt, t->group, t->cluster, t->block, t->stage, t->resident > 0 ? 1 : 0,
-                         t->waves > 0 ? 1 : 0);
+                         t->waves > 0 ? 1 : 0, t->span > 0 ? t->span : 1);
     if (!rc && p->bound) {
         cudaStream_t st = as_stream(stream);
         rc = configure_part(p, pt, st);
@@ -1590,7 +1605,7 @@ int xyl_autotune(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_ev
         const int keep_stage = part.stage_mode;
         float best_ms = -1.f;
         int best_g = keep.Rg, best_G = keep.G, best_block = keep.block, best_res = keep.resident ? 1 : 0;
-        int best_waves = keep.l2_waves ? 1 : 0;
+        int best_waves = keep.l2_waves ? 1 : 0, best_span = keep.span;
         size_t live = 0;
         int64_t spins = 0;
         for (int si : part.samples) {
@@ -1623,44 +1638,56 @@ int xyl_autotune(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_ev
                         for (int block : {128, 256, 384, 512, 640, 768, 1024}) {
                             if (res ? block == 128 : block == 384) continue;
                             if (!res && large && block < 512) continue;  // large samples: many items per CTA
-                            if (apply_shape(p, part, g, G, block, keep_stage, res, waves) ||
-                                configure_part(p, part, st) || finish_configure(p, st))
-                                continue;
-                            float ms = 0.f, rep_ms = 0.f;
-                            bool ok = true;
-                            for (int rep = 0; rep < 2 && ok; ++rep) {
-                                // a shape already 1.5x slower than the best on its first timing cannot win
-                                if (rep == 1 && best_ms > 0.f && ms > 1.5f * best_ms) break;
-                                int64_t launches = 0;
-                                XYL_CUDA(cudaMemsetAsync(p->ws + p->r_barrier.off, 0, p->r_barrier.bytes, st),
-                                         "xyl_autotune");
-                                XYL_CUDA(cudaEventRecord(e0, st), "xyl_autotune: record");
-                                if (launch_units(p, p->dev, part, part.u0, (int)part.units.size(), n_sweeps, ops,
-                                                 measure_every, st, &launches)) {
-                                    ok = false;
-                                    break;
+                            // one unit per span of clusters: span 1, and (one group per sample,
+                            // large samples) a sample spread over every cluster that fits, or half
+                            int spans[3] = {1, 0, 0};
+                            for (int k = 0; k < 3; ++k) {
+                                const int span = spans[k];
+                                if (span < 1) continue;
+                                if (apply_shape(p, part, g, G, block, keep_stage, res, waves, span) ||
+                                    configure_part(p, part, st) || finish_configure(p, st))
+                                    continue;
+                                if (k == 0 && !res && !waves && large && G <= 8 && units == (int64_t)part.samples.size()) {
+                                    spans[1] = part.max_clusters;
+                                    spans[2] = part.max_clusters / 2;
                                 }
-                                XYL_CUDA(cudaEventRecord(e1, st), "xyl_autotune: record");
-                                XYL_CUDA(cudaEventSynchronize(e1), "xyl_autotune: sync");
-                                XYL_CUDA(cudaEventElapsedTime(&rep_ms, e0, e1), "xyl_autotune: time");
-                                ms = rep == 0 ? rep_ms : std::min(ms, rep_ms);  // the faster of the two timings
-                                int32_t status = 0;
-                                XYL_CUDA(cudaMemcpy(&status, p->ws + p->r_status.off, sizeof(status),
-                                                    cudaMemcpyDeviceToHost), "xyl_autotune: status");
-                                if (status) {
-                                    ok = false;
-                                    XYL_CUDA(cudaMemset(p->ws + p->r_status.off, 0, sizeof(int32_t)),
-                                             "xyl_autotune: status");
+                                float ms = 0.f, rep_ms = 0.f;
+                                bool ok = true;
+                                for (int rep = 0; rep < 2 && ok; ++rep) {
+                                    // a shape already 1.5x slower than the best on its first timing cannot win
+                                    if (rep == 1 && best_ms > 0.f && ms > 1.5f * best_ms) break;
+                                    int64_t launches = 0;
+                                    XYL_CUDA(cudaMemsetAsync(p->ws + p->r_barrier.off, 0, p->r_barrier.bytes, st),
+                                             "xyl_autotune");
+                                    XYL_CUDA(cudaEventRecord(e0, st), "xyl_autotune: record");
+                                    if (launch_units(p, p->dev, part, part.u0, (int)part.units.size(), n_sweeps, ops,
+                                                     measure_every, st, &launches)) {
+                                        ok = false;
+                                        break;
+                                    }
+                                    XYL_CUDA(cudaEventRecord(e1, st), "xyl_autotune: record");
+                                    XYL_CUDA(cudaEventSynchronize(e1), "xyl_autotune: sync");
+                                    XYL_CUDA(cudaEventElapsedTime(&rep_ms, e0, e1), "xyl_autotune: time");
+                                    ms = rep == 0 ? rep_ms : std::min(ms, rep_ms);  // the faster of the two timings
+                                    int32_t status = 0;
+                                    XYL_CUDA(cudaMemcpy(&status, p->ws + p->r_status.off, sizeof(status),
+                                                        cudaMemcpyDeviceToHost), "xyl_autotune: status");
+                                    if (status) {
+                                        ok = false;
+                                        XYL_CUDA(cudaMemset(p->ws + p->r_status.off, 0, sizeof(int32_t)),
+                                                 "xyl_autotune: status");
+                                    }
                                 }
-                            }
-                            clear_error();
-                            if (ok && (best_ms < 0.f || ms < best_ms)) {
-                                best_ms = ms;
-                                best_g = g;
-                                best_G = G;
-                                best_block = block;
-                                best_res = res;
-                                best_waves = waves;
+                                clear_error();
+                                if (ok && (best_ms < 0.f || ms < best_ms)) {
+                                    best_ms = ms;
+                                    best_g = g;
+                                    best_G = G;
+                                    best_block = block;
+                                    best_res = res;
+                                    best_waves = waves;
+                                    best_span = span;
+                                }
                             }
                         }
                     }
@@ -1668,7 +1695,8 @@ int xyl_autotune(xyl_plan *p, int32_t n_sweeps, uint32_t ops, int32_t measure_ev
             }
         }
         any |= best_ms >= 0.f;
-        if ((rc = apply_shape(p, part, best_g, best_G, best_block, keep_stage, best_res, best_waves))) return rc;
+        if ((rc = apply_shape(p, part, best_g, best_G, best_block, keep_stage, best_res, best_waves, best_span)))
+            return rc;
         if ((rc = configure_part(p, part, st))) return rc;
     }
     cudaEventDestroy(e0);

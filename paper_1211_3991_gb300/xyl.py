@@ -51,7 +51,7 @@ class Sample(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("block", C.c_int32), ("cluster", C.c_int32), ("group", C.c_int32),
                 ("recompute_every", C.c_int32), ("stage", C.c_int32), ("resident", C.c_int32),
-                ("spin_dim", C.c_int32), ("waves", C.c_int32)]
+                ("spin_dim", C.c_int32), ("waves", C.c_int32), ("span", C.c_int32)]
 
 
 _lib = None
@@ -256,7 +256,7 @@ class Plan:
     ``samples``: list of (Graph, sample_id, beta[list], delta[list])."""
 
     def __init__(self, samples, engine=FP32_BATCHED, seed=0, block=0, cluster=0, group=0, recompute_every=0,
-                 stage=0, resident=0, device=None, spin_dim=2, waves=0):
+                 stage=0, resident=0, device=None, spin_dim=2, waves=0, span=0):
         import torch
         lib = load()
         self._keep = []
@@ -271,7 +271,7 @@ class Plan:
             arr[k] = Sample(g.handle, sid, len(b), _p(b, C.c_double), _p(d, C.c_double))
             self.n_temps.append(len(b))
             self.sizes.append(g.n)
-        tune = Tuning(block, cluster, group, recompute_every, stage, resident, spin_dim, waves)
+        tune = Tuning(block, cluster, group, recompute_every, stage, resident, spin_dim, waves, span)
         self.dim = int(spin_dim)
         h = C.c_void_p(); nbytes = C.c_size_t()
         _check(lib.xyl_plan_create(arr, len(samples), engine, seed, C.byref(tune), C.byref(h), C.byref(nbytes)))
@@ -323,9 +323,10 @@ class Plan:
         return int(load().xyl_part_count(self.handle))
 
     def set_part_tuning(self, part, t, stream=None):
-        """xyl_set_part_tuning: a launch shape for one part (keys block, cluster, group, stage, resident, waves)."""
+        """xyl_set_part_tuning: a launch shape for one part (keys block, cluster, group, stage, resident, waves,
+        span)."""
         tune = Tuning(int(t["block"]), int(t["cluster"]), int(t["group"]), 0, int(t.get("stage", 0)),
-                      int(t["resident"]), self.dim, int(t.get("waves", 0)))
+                      int(t["resident"]), self.dim, int(t.get("waves", 0)), int(t.get("span", 1)))
         _check(load().xyl_set_part_tuning(self.handle, int(part), C.byref(tune), _stream(stream)))
 
     def signature(self) -> str:
@@ -365,7 +366,7 @@ class Plan:
         n = C.c_int32()
         _check(load().xyl_get_part_tuning(self.handle, int(part), C.byref(t), C.byref(n)))
         return {"block": t.block, "cluster": t.cluster, "group": t.group, "stage": t.stage,
-                "resident": t.resident, "waves": t.waves, "samples": n.value}
+                "resident": t.resident, "waves": t.waves, "span": t.span, "samples": n.value}
 
     def autotune(self, n_sweeps, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1, stream=None) -> dict:
         t = Tuning()
@@ -379,7 +380,7 @@ class Plan:
         _check(load().xyl_get_tuning(self.handle, C.byref(t)))
         return {"block": t.block, "cluster": t.cluster, "group": t.group, "stage": t.stage,
                 "resident": t.resident, "recompute_every": t.recompute_every, "spin_dim": t.spin_dim,
-                "waves": t.waves}
+                "waves": t.waves, "span": t.span}
 
     # same method names as the oracle sampler, so tests drive both the same way
     def sweeps(self, n, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1):

@@ -57,7 +57,7 @@ int main(void)
         xyl_plan_free(p);
     }
     /* O(3) spins: plain engines, and the batched engine's resident shape only */
-    xyl_tuning o3 = { 0, 0, 0, 0, 0, 0, 3, 0 };
+    xyl_tuning o3 = { 0, 0, 0, 0, 0, 0, 3, 0, 0 };
     xyl_plan *p = NULL;
     size_t bytes = 0;
     CHECK(xyl_plan_create(s, 2, XYL_FP32_PLAIN, 7, &o3, &p, &bytes));

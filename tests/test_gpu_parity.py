@@ -737,6 +737,67 @@ def test_fp32_parity_groups_of_any_size(env, orc, shape):
     assert plan.status() == (0, 6)
 
 
+# global-memory shapes whose replica group spans several clusters (span): the
+# span clusters of a group share its colour chunks and meet at a bounded
+# global barrier after every colour phase
+SPREAD = [dict(group=16, cluster=2, block=512, resident=-1, span=4),
+          dict(group=16, cluster=1, block=1024, resident=-1, span=12),
+          dict(group=8, cluster=4, block=640, resident=-1, span=3)]
+
+
+def test_groups_spread_over_clusters_give_the_same_spins(env):
+    """A group spread over several clusters performs the same per-site
+    arithmetic as one cluster per group, bit for bit (Metropolis +
+    overrelaxation); its sums agree to FP32 rounding, its Metropolis counts
+    exactly."""
+    xyl, wl = env
+    cfg = wl.config("C2")
+    graphs = wl.build_graphs(cfg)
+    ref = None
+    for shp in [dict(group=16, cluster=2, block=512, resident=-1)] + SPREAD:
+        p, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, graphs=graphs, **shp)
+        assert p.tuning()["span"] == shp.get("span", 1), shp
+        p.bind()
+        p.init_spins()
+        p.sweep(6, NO_PT, 2)
+        spins = np.stack([p.spins(0, r) for r in range(cfg.n_temps)])
+        st = p.read_observables()
+        assert p.status() == (0, 6), shp
+        if ref is None:
+            ref = (spins, st)
+            continue
+        assert np.array_equal(spins, ref[0]), shp
+        assert np.array_equal(st["met_acc"], ref[1]["met_acc"]), shp
+        np.testing.assert_allclose(st["acc"], ref[1]["acc"], rtol=2e-5, atol=2e-5, err_msg=str(shp))
+
+
+@pytest.mark.parametrize("shape", SPREAD[:2], ids=["span4", "span12"])
+def test_fp32_parity_groups_spread_over_clusters(env, orc, shape):
+    """With parallel tempering and measurement, against the oracle (24-bit
+    draws) under the traced parity rule."""
+    xyl, wl = env
+    cfg = wl.config("C2")
+    plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, **shape)
+    plan.bind()
+    plan.init_spins()
+    sims = {0: _oracle_for(orc, wl, cfg, 0, u24=True)}
+    _report(f"C2 {shape}", _fp32_per_sweep(plan, sims, [0], 6, ALL, lambda s: 128 * 128))
+    assert plan.status() == (0, 6)
+
+
+def test_spread_shape_at_full_size(env, orc):
+    """Two C5 samples (L=512, 32 temperatures), each spread over eight
+    8-CTA clusters of 1024 threads: both against the oracle for two sweeps."""
+    xyl, wl = env
+    cfg = wl.first_samples(wl.config("C5"), 2)
+    plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, group=32, cluster=8, block=1024, resident=-1, span=8)
+    plan.bind()
+    plan.init_spins()
+    sims = {k: _oracle_for(orc, wl, cfg, k, u24=True) for k in range(2)}
+    _report("C5x2 span 8", _fp32_per_sweep(plan, sims, [0, 1], 2, ALL, lambda s: 512 * 512))
+    assert plan.status() == (0, 2)
+
+
 def test_autotune_restores_state(env):
     xyl, wl = env
     cfg = wl.config("C2")

@@ -244,6 +244,21 @@ def test_group_sizes_are_validated(xyl):
         assert e.value.code == xyl.EINVAL, (group, resident)
 
 
+def test_span_is_validated(xyl):
+    """Clusters per replica group above one: global-memory shape only."""
+    g = xyl.build_graph_csr(16, 6, 3.5, 1, 0)
+    temps = [1.0] * 16
+    t = xyl.Plan([(g, 0, temps, temps)], engine=xyl.FP32_BATCHED, device="cpu", group=16, cluster=2, resident=-1,
+                 span=4).tuning()
+    assert (t["span"], t["cluster"], t["resident"]) == (4, 2, -1)
+    assert xyl.Plan([(g, 0, temps, temps)], engine=xyl.FP32_BATCHED, device="cpu", group=16,
+                    resident=-1).tuning()["span"] == 1
+    for kw in (dict(resident=1, span=2), dict(resident=-1, span=-1)):
+        with pytest.raises(xyl.XylError) as e:
+            xyl.Plan([(g, 0, temps, temps)], engine=xyl.FP32_BATCHED, device="cpu", group=16, **kw)
+        assert e.value.code == xyl.EINVAL, kw
+
+
 def test_o3_plans_are_validated(xyl):
     g = xyl.build_graph_csr(8, 6, 3.5, 1, 0)
     for engine, kw in ((xyl.FP32_BATCHED, {"spin_dim": 3, "resident": -1}), (xyl.FP32_PLAIN, {"spin_dim": 4})):
