@@ -234,7 +234,8 @@ typedef struct {
     int32_t waves;           /* batched engine, global-memory shape: 1 = cap each launch wave to the samples whose
                                 spins and tables fit in L2, -1 = never, 0 = library's choice (never) */
     int32_t span;            /* batched engine, global-memory shape: clusters per replica group (0 or 1 = one); above
-                                one, the group's cluster x span CTAs share its colour chunks and meet at a bounded
+                                one (group a power of two >= 2), the group's cluster x span CTAs share its colour
+                                chunks and meet at a bounded
                                 global barrier after every colour phase, so few samples can hold the whole GPU while
                                 their spins stay in L2 for a launch's sweeps; all must be resident at once */
 } xyl_tuning;

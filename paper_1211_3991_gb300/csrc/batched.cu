@@ -463,7 +463,7 @@ __device__ __forceinline__ bool unit_barrier(const DevPlan &P, SS &sh, cg::clust
     return *(volatile int *)&sh.abort_flag == 0;
 }
 
-template <bool STAGED, int RV, int DEG, bool DISORDER, bool NP2, class SS>
+template <bool STAGED, int RV, int DEG, bool DISORDER, bool NP2, bool SPAN, class SS>
 __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams &bp, SS &sh,
                                            const Staged &stg, cg::cluster_group &cluster, int s, int group,
                                            int rank, int cta, unsigned int *unit_ctr)
@@ -471,9 +471,9 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
     const DevSample d = P.samples[s];
     const int R = d.R;
     const int n_groups = R / bp.Rg;
-    const int ctas = bp.G * bp.span;  // CTAs of one unit
+    const int ctas = SPAN ? bp.G * bp.span : bp.G;  // CTAs of one unit
     const bool leader = (group == 0 && cta == 0);
-    const bool sample_barrier = n_groups > 1 || bp.span > 1;
+    const bool sample_barrier = n_groups > 1 || SPAN;
     unsigned int arrivals = 0;
     // replica offset within the group of this thread's lane (threads past
     // spr * lps have no lane and update nothing)
@@ -502,7 +502,7 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
                 if (orx) phase<true, false, STAGED, RV, DEG, DISORDER, NP2>(P, d, sh, bp, stg, c, t, ln, first);
                 else phase<true, true, STAGED, RV, DEG, DISORDER, NP2>(P, d, sh, bp, stg, c, t, ln, first);
                 if (orx || c + 1 < d.Q) {
-                    if (bp.span == 1) {
+                    if constexpr (!SPAN) {
                         cluster_arrive();
                         if (c + 1 < d.Q) first = first_draw<STAGED, NP2>(P, d, sh, bp, stg, c + 1, t, ln.r0);
                         cluster_wait();
@@ -518,7 +518,7 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
             for (int c = 0; c < d.Q; ++c) {
                 phase<false, true, STAGED, RV, DEG, DISORDER, NP2>(P, d, sh, bp, stg, c, t, ln, none);
                 if (c + 1 < d.Q) {
-                    if (bp.span == 1) cluster.sync();
+                    if constexpr (!SPAN) cluster.sync();
                     else if (!unit_barrier(P, sh, cluster, bp, unit_ctr, arrivals, rank)) return;
                 }
             }
@@ -599,13 +599,13 @@ __device__ __forceinline__ void run_sweeps(const DevPlan &P, const BatchedParams
     if (leader && threadIdx.x == 0) P.sweep[s] = t;
 }
 
-template <bool STAGED, int RV, int DEG, bool DISORDER, bool NP2, int MW>
+template <bool STAGED, int RV, int DEG, bool DISORDER, bool NP2, bool SPAN, int MW>
 __device__ __forceinline__ void batched_body(const DevPlan &P, const BatchedParams &bp)
 {
     __shared__ SharedStateT<MW> sh;
     extern __shared__ int dyn[];
     cg::cluster_group cluster = cg::this_cluster();
-    const int ctas = bp.G * bp.span;                  // CTAs of one unit, span clusters
+    const int ctas = SPAN ? bp.G * bp.span : bp.G;    // CTAs of one unit, span clusters
     const int unit = bp.unit_begin + (int)(blockIdx.x / ctas);
     const int cta = (int)(blockIdx.x % ctas);         // which chunk of the unit's classes
     const int rank = (int)cluster.block_rank();
@@ -658,7 +658,7 @@ __device__ __forceinline__ void batched_body(const DevPlan &P, const BatchedPara
         stg = Staged{col, deg, site};
         __syncthreads();
     }
-    run_sweeps<STAGED, RV, DEG, DISORDER, NP2>(P, bp, sh, stg, cluster, s, group, rank, cta,
+    run_sweeps<STAGED, RV, DEG, DISORDER, NP2, SPAN>(P, bp, sh, stg, cluster, s, group, rank, cta,
                                                bp.unit_ctr + (unit - bp.unit_begin));
 }
 
@@ -666,46 +666,51 @@ __device__ __forceinline__ void batched_body(const DevPlan &P, const BatchedPara
 // up to 1024 threads with 64 registers each (more warps to cover the latency
 // of the neighbour gathers).
 // NP2: lanes per site not a power of two (even groups of 6, 10, 12, ... replicas).
-template <bool STAGED, int RV, int DEG, bool DISORDER, bool NP2>
+// SPAN: a unit spans several clusters (phase barriers through global memory).
+template <bool STAGED, int RV, int DEG, bool DISORDER, bool NP2, bool SPAN>
 __global__ void __maxnreg__(96) batched_kernel(DevPlan P, BatchedParams bp)
 {
-    batched_body<STAGED, RV, DEG, DISORDER, NP2, kMaxWarps>(P, bp);
+    batched_body<STAGED, RV, DEG, DISORDER, NP2, SPAN, kMaxWarps>(P, bp);
 }
 
-template <int RV, int DEG, bool DISORDER, bool NP2>
+template <int RV, int DEG, bool DISORDER, bool NP2, bool SPAN>
 __global__ void __launch_bounds__(1024, 1) batched_kernel_wide(DevPlan P, BatchedParams bp)
 {
-    batched_body<false, RV, DEG, DISORDER, NP2, kMaxWarpsWide>(P, bp);
+    batched_body<false, RV, DEG, DISORDER, NP2, SPAN, kMaxWarpsWide>(P, bp);
 }
 
 using KernelFn = void (*)(DevPlan, BatchedParams);
 
 // The specialisation for a launch shape: CSR staged or not, one or two
 // replicas per thread, fixed degree 6 / at most 8 / any degree, random bonds or
-// fields, lanes per site a power of two or not.
-template <bool STAGED, int RV, bool DISORDER, bool NP2>
+// fields, lanes per site a power of two or not, one cluster per unit or several.
+template <bool STAGED, int RV, bool DISORDER, bool NP2, bool SPAN>
 KernelFn pick_deg(const BatchedShape &B)
 {
     if (!STAGED && B.block > kMaxWarps * 32) {
-        if (B.fixed_deg == 6) return batched_kernel_wide<RV, 6, DISORDER, NP2>;
-        if (B.max_deg <= 8) return batched_kernel_wide<RV, -8, DISORDER, NP2>;
-        return batched_kernel_wide<RV, 0, DISORDER, NP2>;
+        if (B.fixed_deg == 6) return batched_kernel_wide<RV, 6, DISORDER, NP2, SPAN>;
+        if (B.max_deg <= 8) return batched_kernel_wide<RV, -8, DISORDER, NP2, SPAN>;
+        return batched_kernel_wide<RV, 0, DISORDER, NP2, SPAN>;
     }
-    if (B.fixed_deg == 6) return batched_kernel<STAGED, RV, 6, DISORDER, NP2>;
-    if (B.max_deg <= 8) return batched_kernel<STAGED, RV, -8, DISORDER, NP2>;
-    return batched_kernel<STAGED, RV, 0, DISORDER, NP2>;
+    if (B.fixed_deg == 6) return batched_kernel<STAGED, RV, 6, DISORDER, NP2, SPAN>;
+    if (B.max_deg <= 8) return batched_kernel<STAGED, RV, -8, DISORDER, NP2, SPAN>;
+    return batched_kernel<STAGED, RV, 0, DISORDER, NP2, SPAN>;
 }
 
 template <bool DISORDER>
 KernelFn pick_kernel_d(const BatchedShape &B)
 {
-    // groups are a power of two (one or two replicas a thread) or even (two)
+    // groups are a power of two (one or two replicas a thread) or even (two);
+    // a unit over several clusters takes a power of two of at least two
     const bool rv2 = B.Rg % 2 == 0;
     const int lps = rv2 ? B.Rg / 2 : B.Rg;
+    if (B.span > 1)
+        return B.staged ? pick_deg<true, 2, DISORDER, false, true>(B) : pick_deg<false, 2, DISORDER, false, true>(B);
     if (lps & (lps - 1))
-        return B.staged ? pick_deg<true, 2, DISORDER, true>(B) : pick_deg<false, 2, DISORDER, true>(B);
-    if (B.staged) return rv2 ? pick_deg<true, 2, DISORDER, false>(B) : pick_deg<true, 1, DISORDER, false>(B);
-    return rv2 ? pick_deg<false, 2, DISORDER, false>(B) : pick_deg<false, 1, DISORDER, false>(B);
+        return B.staged ? pick_deg<true, 2, DISORDER, true, false>(B) : pick_deg<false, 2, DISORDER, true, false>(B);
+    if (B.staged)
+        return rv2 ? pick_deg<true, 2, DISORDER, false, false>(B) : pick_deg<true, 1, DISORDER, false, false>(B);
+    return rv2 ? pick_deg<false, 2, DISORDER, false, false>(B) : pick_deg<false, 1, DISORDER, false, false>(B);
 }
 
 KernelFn pick_kernel(const BatchedShape &B) { return B.disorder ? pick_kernel_d<true>(B) : pick_kernel_d<false>(B); }

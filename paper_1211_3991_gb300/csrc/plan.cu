@@ -326,6 +326,8 @@ int apply_shape(xyl_plan *p, Part &part, int g, int G, int block, int stage, int
 {
     if (span < 1 || (span > 1 && (resident || p->shape.dim == 3)))
         return fail(XYL_EINVAL, "span=%d: clusters per group above 1 run in the global-memory shape only", span);
+    if (span > 1 && (g < 2 || (g & (g - 1))))
+        return fail(XYL_EINVAL, "span=%d: a group over several clusters takes a power of two >= 2 (group=%d)", span, g);
     if (g < 1 || g > 32) return fail(XYL_EINVAL, "group=%d must be in [1, 32]", g);
     if ((g & (g - 1)) && (resident || p->shape.dim == 3 || g % 2))
         return fail(XYL_EINVAL, "group=%d: a group that is not a power of two must be even and runs in the "
