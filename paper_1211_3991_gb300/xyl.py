@@ -341,8 +341,10 @@ class Plan:
     def autotune_cached(self, path, n_sweeps=4, ops=OP_MET | OP_OR | OP_PT | OP_MEASURE, measure_every=1,
                         stream=None):
         """The launch shapes an earlier xyl_autotune chose for a batch with this
-        signature, read from the JSON file `path`; on a miss, autotune and add
-        them.  Returns (per-part shapes, True if they came from the file)."""
+        signature, read from the JSON file `path`; on a miss, or when a cached
+        shape does not fit this GPU (e.g. fewer clusters can be resident),
+        autotune and store the result.  Returns (per-part shapes, True if they
+        came from the file)."""
         import json
         cache = {}
         if os.path.exists(path):
@@ -350,9 +352,12 @@ class Plan:
                 cache = json.load(f)
         key = self.signature()
         if key in cache and len(cache[key]["parts"]) == self.part_count():
-            for k, t in enumerate(cache[key]["parts"]):
-                self.set_part_tuning(k, t, stream=stream)
-            return cache[key]["parts"], True
+            try:
+                for k, t in enumerate(cache[key]["parts"]):
+                    self.set_part_tuning(k, t, stream=stream)
+                return cache[key]["parts"], True
+            except XylError:
+                pass  # a part keeps its previous shape; tune them all below
         self.autotune(n_sweeps, ops, measure_every, stream=stream)
         parts = [{k: v for k, v in self.part_tuning(i).items() if k != "samples"} for i in range(self.part_count())]
         cache[key] = {"parts": parts, "sizes": sorted(set(self.sizes)), "slots": sorted(set(self.n_temps))}

@@ -798,6 +798,25 @@ def test_spread_shape_at_full_size(env, orc):
     assert plan.status() == (0, 2)
 
 
+def test_cache_entry_that_does_not_fit_is_retuned(env, tmp_path):
+    """A cached launch shape that cannot run on this GPU (more clusters per
+    group than can be resident) is replaced by a fresh autotune, not raised."""
+    import json
+    xyl, wl = env
+    cfg = wl.config("G1")
+    plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED)
+    plan.bind()
+    plan.init_spins()
+    path = tmp_path / "cache.json"
+    bad = {"block": 256, "cluster": 1, "group": 4, "stage": -1, "resident": -1, "waves": -1, "span": 100000}
+    path.write_text(json.dumps({plan.signature(): {"parts": [bad], "sizes": [256], "slots": [4]}}))
+    parts, hit = plan.autotune_cached(str(path), 2)
+    assert not hit and parts[0]["span"] < 100000
+    assert json.loads(path.read_text())[plan.signature()]["parts"] == parts
+    plan.sweep(3)
+    assert plan.status() == (0, 3)
+
+
 def test_autotune_restores_state(env):
     xyl, wl = env
     cfg = wl.config("C2")
