@@ -382,6 +382,7 @@ def walk_bench(args):
 
 # Secondary ceilings measured on this GB300 by the project's own probes (CUDA
 # events, 2.07 GHz): MEASURED_PEAKS.json holds only the HBM copy and BF16 GEMM.
+# on-chip peaks, measured by `python bench.py --probe-peaks` (paper_1211_3991_gb300/peaks.py) on a GB300
 SMEM_GATHER_PROBE_GBS = 15000.0  # random 8-byte gathers from shared memory, 128 KB per CTA, every SM
 L2_STREAM_PROBE_GBS = 19300.0    # streaming reads of a 64 MiB L2-resident buffer
 L2_BYTES = 126 << 20             # L2 capacity usable for a resident working set
@@ -634,6 +635,8 @@ def main():
     ap.add_argument("--tune-rounds", type=int, default=6)
     ap.add_argument("--tune-sweeps", type=int, default=40)
     ap.add_argument("--measure-every", type=int, default=32, help="sweeps between measurements (the paper: 32)")
+    ap.add_argument("--probe-peaks", action="store_true",
+                    help="measure the on-chip peaks the roofline uses (paper_1211_3991_gb300/peaks.py) and exit")
     ap.add_argument("--workload", default="sweep", choices=["sweep", "walk"],
                     help="sweep: the Monte Carlo sampler (default); walk: random walks for the spectral dimension")
     ap.add_argument("--max-samples", type=int, default=0,
@@ -641,6 +644,13 @@ def main():
     ap.add_argument("--walkers", type=int, default=1 << 20)
     ap.add_argument("--walk-steps", type=int, default=1000)
     args = ap.parse_args()
+    if args.probe_peaks:
+        # the on-chip peaks of the roofline (L2 stream, shared-memory gathers), measured here
+        from paper_1211_3991_gb300 import peaks
+        print(json.dumps({"probe": "on-chip peaks", **peaks.measure(),
+                          "used_by_roofline": {"l2_stream_read_GBps": L2_STREAM_PROBE_GBS,
+                                               "smem_random_8B_gather_GBps": SMEM_GATHER_PROBE_GBS}}))
+        return
     if args.workload == "walk":
         if args.impl == "reference":
             raise SystemExit("--impl reference times the sampler workload only")
