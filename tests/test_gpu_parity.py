@@ -364,15 +364,25 @@ def test_beta_zero_exact_moments(env, engine_name):
 
 # --------------------------------------------------------------- full-size configurations
 @pytest.mark.parametrize("name,sampled,resident", [("C3", [0, 400, 767], 1), ("C3", [1, 511], -1),
-                                                    ("C4", [0, 47], 0), ("C5", [70], 0)])
+                                                    ("C4", [0, 47], 0), ("C5", [70], 0),
+                                                    ("C3", [2, 700], "bench"), ("C4", [5, 44], "bench"),
+                                                    ("C5", [3, 127], "bench")])
 def test_full_size_batched_sampled_parity(env, orc, name, sampled, resident):
-    """Whole batch in the benchmark's launch configuration; sampled samples are
-    re-run by the oracle from the same seeds; every sample obeys the invariants."""
+    """Whole batch in a given launch configuration (resident "bench": the shapes
+    the benchmark takes from the committed autotune cache, e.g. C5 spread over
+    the whole GPU); sampled samples are re-run by the oracle from the same
+    seeds; every sample obeys the invariants."""
+    import os
     xyl, wl = env
     cfg = wl.config(name)
-    plan, graphs = wl.make_plan(cfg, xyl.FP32_BATCHED, resident=resident)
-    assert plan.tuning()["resident"] == (1 if resident == 1 else -1) or resident == 0
+    bench_shape = resident == "bench"
+    plan, graphs = wl.make_plan(cfg, xyl.FP32_BATCHED, resident=0 if bench_shape else resident)
+    assert bench_shape or plan.tuning()["resident"] == (1 if resident == 1 else -1) or resident == 0
     plan.bind()
+    if bench_shape:
+        cache = os.path.join(os.path.dirname(xyl.__file__), "autotune_cache.json")
+        _, hit = plan.autotune_cached(cache)
+        assert hit, "the committed cache holds this batch's shapes"
     plan.init_spins()
     sims = {k: _oracle_for(orc, wl, cfg, k, u24=True) for k in sampled}
     n_sweeps = 2 if name == "C5" else 3
