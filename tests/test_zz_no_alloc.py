@@ -53,7 +53,8 @@ def _twins(xyl, wl, cfg, shape):
 
 @pytest.mark.parametrize("shape", [dict(resident=1), dict(resident=1, cluster=4), dict(resident=-1),
                                    dict(resident=1, cluster=4, recompute_every=5),
-                                   dict(resident=-1, recompute_every=5)])
+                                   dict(resident=-1, recompute_every=5),
+                                   dict(resident=-1, group=16, cluster=2, block=640, span=8)])
 def test_noalloc_sweep_matches_sweep_twice(env, shape):
     xyl, wl = env
     cfg = wl.config("C2")
