@@ -383,6 +383,9 @@ def test_full_size_batched_sampled_parity(env, orc, name, sampled, resident):
         cache = os.path.join(os.path.dirname(xyl.__file__), "autotune_cache.json")
         _, hit = plan.autotune_cached(cache)
         assert hit, "the committed cache holds this batch's shapes"
+        if name == "C3":
+            # one group per sample, never waiting on another: all 768 in one launch, as many resident as fit
+            assert plan.wave_units() == 768 and 0 < plan.live_units() < 768
     plan.init_spins()
     sims = {k: _oracle_for(orc, wl, cfg, k, u24=True) for k in sampled}
     n_sweeps = 2 if name == "C5" else 3
@@ -802,6 +805,8 @@ def test_spread_shape_at_full_size(env, orc):
     cfg = wl.first_samples(wl.config("C5"), 2)
     plan, _ = wl.make_plan(cfg, xyl.FP32_BATCHED, group=32, cluster=8, block=1024, resident=-1, span=8)
     plan.bind()
+    # the 8 clusters of a sample wait on one another: a wave is whole samples, all resident
+    assert plan.unit_count() == 2 and plan.wave_units() == plan.live_units() >= 1
     plan.init_spins()
     sims = {k: _oracle_for(orc, wl, cfg, k, u24=True) for k in range(2)}
     _report("C5x2 span 8", _fp32_per_sweep(plan, sims, [0, 1], 2, ALL, lambda s: 512 * 512))
