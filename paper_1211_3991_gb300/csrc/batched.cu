@@ -2,7 +2,8 @@
 // cycles for a batch of samples.
 //
 // Work decomposition.  The replicas of a sample are split into groups of Rg
-// (any divisor of the sample's replica count up to 32).  Each (sample, group)
+// (a power of two, or an even divisor of the sample's replica count, up to
+// 32).  Each (sample, group)
 // unit is owned by one thread-block cluster of G CTAs.  Inside a unit, every
 // colour class is cut into G contiguous chunks; CTA k updates chunk k for all
 // Rg replicas.  A thread updates RV replicas (2 when Rg is even, else 1) of
@@ -15,8 +16,10 @@
 // every colour phase at a bounded barrier on a per-unit counter in global
 // memory (the whole GPU can then work on one sample while its spins stay in
 // L2 for the launch's sweeps).
-// Spins are interleaved [sample][site][replica] float2 in global memory and
-// stay L2-resident for the batch sizes this engine serves; they are read and
+// Spins are interleaved [sample][site][replica] float2 in global memory; they
+// stay L2-resident while the units resident at once fit L2 (a launch wave of
+// whole samples, or the clusters that fit when units never wait on one
+// another, each running all the launch's sweeps on its unit); they are read and
 // written through L2 (ld/st .cg), and colour phases are separated by cluster
 // barriers (release/acquire at cluster scope).  When they fit, the CSR rows
 // and random-stream site ids of a CTA's chunks are staged once per launch in
